@@ -1,0 +1,165 @@
+"""Seeded synthetic inputs and workload descriptions.
+
+This module is shared by the CUDA path's tests/benchmark and by the FP64 oracle.
+It holds only input generation and the plain description of each workload (the
+kernel graph, the factor kinds, the sizes and the seeds); it holds none of the
+method's arithmetic (no kernel maps, no partitions, no contractions).
+
+Workloads stand in for the paper's experiments (HOIF chains at n <= 1e4, motif
+adjacency at n <= 2e4; Section 4) with the shapes named below.  All draws use
+numpy's PCG64 ``default_rng``.
+
+Graph convention: vertices 0..m-1; an edge ``(a, b, f)`` is the ordered pair
+factor ``F_f(x_a, x_b)`` (the paper's multiplicative decomposition, Section 3.1,
+with signature tuples of length 2); a unary ``(v, f)`` is ``f(x_v)`` (tuple of
+length 1).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# Factor kinds (same numbering as include/ustat.h).
+RBF = 0        # exp(-||x - y||^2 / h)
+LINEAR = 1     # (x . y) / h
+TANH_DOT = 2   # tanh(x . w), unary
+MATRIX = 3     # caller-supplied n x n matrix
+VECTOR = 4     # caller-supplied length-n vector
+
+
+@dataclass
+class Factor:
+    kind: int
+    param: float = 1.0
+    data: np.ndarray | None = None   # w for TANH_DOT, the matrix/vector for MATRIX/VECTOR
+
+
+@dataclass
+class Graph:
+    m: int
+    edges: list = field(default_factory=list)   # (a, b, factor_id)
+    unary: list = field(default_factory=list)   # (v, factor_id)
+
+
+def normal_X(n: int, d: int, seed: int) -> np.ndarray:
+    """n x d iid N(0, 1), float64, row-major."""
+    return np.random.default_rng(seed).standard_normal((n, d))
+
+
+def student_t_X(n: int, d: int, seed: int, df: float = 5.0) -> np.ndarray:
+    """n x d iid Student-t(df), rounded to float32 (the stored values are the sample)."""
+    return np.random.default_rng(seed).standard_t(df, (n, d)).astype(np.float32)
+
+
+def tanh_weight(d: int, seed: int = 1) -> np.ndarray:
+    """w ~ N(0, I_d / d), float64."""
+    return np.random.default_rng(seed).standard_normal(d) / np.sqrt(d)
+
+
+def batched_sizes(count: int = 512, lo: int = 256, hi: int = 4096, seed: int = 0) -> np.ndarray:
+    """Sample sizes n_i ~ uniform integers in [lo, hi] (inclusive)."""
+    return np.random.default_rng(seed).integers(lo, hi + 1, count)
+
+
+def cycle(m: int, factor: int = 0) -> Graph:
+    return Graph(m, [(i, (i + 1) % m, factor) for i in range(m)], [])
+
+
+def path(m: int, factor: int = 0) -> Graph:
+    return Graph(m, [(i, i + 1, factor) for i in range(m - 1)], [])
+
+
+def complete(m: int, factor: int = 0) -> Graph:
+    return Graph(m, [(a, b, factor) for a in range(m) for b in range(a + 1, m)], [])
+
+
+def triangle_graph() -> Graph:
+    return cycle(3)
+
+
+def cycle4_graph() -> Graph:
+    return cycle(4)
+
+
+def path5_chord_graph() -> Graph:
+    """Path 1-2-3-4-5 plus chord 1-3, unary factor 1 on vertex 5 (0-based: 4)."""
+    return Graph(5, [(0, 1, 0), (1, 2, 0), (2, 3, 0), (3, 4, 0), (0, 2, 0)], [(4, 1)])
+
+
+def k4_plus_cycle_graph() -> Graph:
+    """K4 on 1..4 plus edges 4-5, 5-6, 6-1 (0-based K4 on 0..3, then 3-4, 4-5, 5-0)."""
+    g = complete(4)
+    return Graph(6, g.edges + [(3, 4, 0), (4, 5, 0), (5, 0, 0)], [])
+
+
+def rbf(d: int) -> Factor:
+    return Factor(RBF, float(2 * d))
+
+
+def linear(d: int) -> Factor:
+    return Factor(LINEAR, float(d))
+
+
+@dataclass
+class Workload:
+    name: str
+    graph: Graph
+    factors: list
+    n: int
+    d: int
+    X: np.ndarray
+
+
+def workload(name: str, n: int | None = None) -> Workload:
+    """The five workloads, by name.  ``n`` overrides the sample size (same seed and
+    distribution, first ``n`` draws are NOT reused: the whole sample is redrawn)."""
+    if name == "triangle_rbf":
+        n = 200 if n is None else n
+        d = 8
+        return Workload(name, triangle_graph(), [rbf(d)], n, d, normal_X(n, d, 0))
+    if name == "c4_rbf":
+        n = 4096 if n is None else n
+        d = 32
+        return Workload(name, cycle4_graph(), [rbf(d)], n, d, normal_X(n, d, 0))
+    if name == "path5_chord_linear_tanh":
+        n = 16384 if n is None else n
+        d = 64
+        w = tanh_weight(d, 1)
+        return Workload(name, path5_chord_graph(), [linear(d), Factor(TANH_DOT, 1.0, w)], n, d,
+                        student_t_X(n, d, 0))
+    if name == "k4_cycle_rbf":
+        n = 1024 if n is None else n
+        d = 32
+        return Workload(name, k4_plus_cycle_graph(), [rbf(d)], n, d, normal_X(n, d, 0))
+    raise KeyError(name)
+
+
+def batched_workload(count: int = 512, d: int = 16, lo: int = 256, hi: int = 4096):
+    """Independent samples of uneven size: list of (n_i, X_i) with X_i ~ N(0,1),
+    n_i from seed 0 and sample i from seed 1000 + i."""
+    sizes = batched_sizes(count, lo, hi, 0)
+    return [(int(n), normal_X(int(n), d, 1000 + i)) for i, n in enumerate(sizes)]
+
+
+def ternary_vector(n: int, seed: int) -> np.ndarray:
+    """Entries uniform in {-1, 0, 1}, float64 (integer-valued factor inputs)."""
+    return np.random.default_rng(seed).integers(-1, 2, n).astype(np.float64)
+
+
+def random_connected_graph(rng: np.random.Generator, m: int, p: float, max_unary: int = 2) -> Graph:
+    """Connected G(m, p): edges kept with probability p, a random spanning tree
+    added so the graph is connected; up to ``max_unary`` unary factors (id 1)."""
+    keep = set()
+    for a in range(m):
+        for b in range(a + 1, m):
+            if rng.random() < p:
+                keep.add((a, b))
+    perm = rng.permutation(m)
+    for i in range(1, m):
+        a, b = int(perm[i]), int(perm[rng.integers(0, i)])
+        keep.add((min(a, b), max(a, b)))
+    edges = [(a, b, 0) for (a, b) in sorted(keep)]
+    nu = int(rng.integers(0, max_unary + 1))
+    unary = [(int(v), 1) for v in rng.choice(m, nu, replace=False)]
+    return Graph(m, edges, unary)
