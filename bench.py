@@ -1,0 +1,320 @@
+"""Benchmark: exact order-m U-statistic evaluations per second on GB300.
+
+A step is one evaluation of the whole path for one sample: tensorization of the
+RBF kernel matrix from X, every partition's restricted V-statistic (the shared
+K K product on the tensor cores, the n^2 reductions), and the Moebius combination
+into U.  Default workload: the 4-cycle RBF kernel, m = 4, n = 4096, d = 32,
+X ~ N(0, 1) seed 0, all 15 partitions, split-bf16 tensor-core contractions.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P] [--impl reference]
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+the host cores on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "U-stat evals/s and TFLOP/s, mixed-prec vs FP64 on GB300 at rel err ≤1e-8"
+WORKLOADS = {
+    "c4_rbf": "m=4 4-cycle kernel K12 K23 K34 K41, RBF K = exp(-||x-y||^2/(2d)), X n=4096 x d=32 iid N(0,1) "
+              "float64 seed 0, all 15 partitions",
+}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.4)
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() in ("active", "yes", "1"):
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_eval(w):
+    from oracle import ustat_oracle as uo
+    t0 = time.perf_counter()
+    r = uo.ustat(w.graph, w.factors, w.X)
+    return r, time.perf_counter() - t0
+
+
+def host_cores():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        if info:
+            return int(max(i.get("num_threads", 1) for i in info))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def run_reference(args):
+    """The oracle (FP64 CPU, as it stands) on the host cores: each step is one full
+    evaluation of the workload; the number of timed steps is capped so the run
+    ends within a few minutes."""
+    import synth
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = synth.workload(args.workload)
+    for _ in range(min(args.warmup, 1)):
+        oracle_eval(w)
+    times = []
+    budget = 150.0
+    t_start = time.perf_counter()
+    for _ in range(args.steps):
+        _, dt = oracle_eval(w)
+        times.append(dt)
+        if time.perf_counter() - t_start + dt > budget:
+            break
+    tot = sum(times)
+    value = len(times) / tot
+    cores = host_cores()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus,
+            "steps": len(times), "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "n": w.n, "d": w.d},
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                             "sample": "%d full evaluations of the workload (steps capped to ~%ds)" % (
+                                 len(times), int(budget))},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--precision", default="bf16x3")
+    ap.add_argument("--workload", default="c4_rbf")
+    ap.add_argument("--impl", default="engine")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2508_12627_gb300 import build as B
+    B.build()
+    from paper_2508_12627_gb300 import engine, ustat as us
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = synth.workload(args.workload)
+    eng = engine.Engine(w.graph, w.factors, precision=args.precision, device=dev)
+    Xd = eng.to_device(w.X)
+    out = torch.empty(2 + eng.n_parts, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        eng.launch(Xd, out)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, L2 flushed (256 MiB write) before each, CUDA events per step
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    us.profile_enable(True)
+    us.profile_collect()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        eng.launch(Xd, out)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - t0
+    us.profile_enable(False)
+    prof = us.profile_collect()
+    clk = clocks.stop() if clocks else None
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    tot_ms = float(sum(step_ms))
+    if dist:
+        t = torch.tensor([tot_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    result = out.cpu().numpy()
+
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+
+    n, d = w.n, w.d
+    value = world * args.steps / (tot_ms / 1e3)
+    fl_plan, fl_naive = eng.plan.flops(n)
+    peaks, peak_src = load_peaks()
+    launches = sum(c for (_, c) in prof.values())
+    # dominant kernel: the n^3 contraction
+    gemm_ms, gemm_cnt = prof.get("gemm", (0.0, 0))
+    red_ms, red_cnt = prof.get("gemm_red", (0.0, 0))
+    g_ms, g_cnt = gemm_ms + red_ms, gemm_cnt + red_cnt
+    per_launch_s = (g_ms / max(1, g_cnt)) / 1e3
+    alg_flops = 2.0 * n ** 3
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    products = {"bf16x3": 6.0, "tf32": 2.0, "fp32": None, "fp64": None}[args.precision]
+    roof = None
+    if g_cnt and products:
+        achieved = alg_flops / per_launch_s / 1e12
+        peak = bf16_peak / products
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "tc_gemm_kernel (%s)" % args.precision,
+                "peak_note": "%s bf16 dense %.1f TFLOP/s (%s) / %g tensor products per algorithmic "
+                             "multiply-add" % (peak_src, bf16_peak, "burst", products),
+                "per_launch_ms": per_launch_s * 1e3}
+    prof_share = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+                  for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+
+    # ---- end to end: host X (pinned) -> ustat_eval_host -> host U, V
+    import ctypes
+    Xh = torch.as_tensor(np.ascontiguousarray(w.X)).pin_memory()
+    Uh = (ctypes.c_double * 2)()
+    Vh = (ctypes.c_double * eng.n_parts)()
+    for _ in range(2):
+        eng.evaluate_host(Xh, Uh, Vh)
+    ke = min(args.steps, 100)
+    t1 = time.perf_counter()
+    for _ in range(ke):
+        eng.evaluate_host(Xh, Uh, Vh)
+    e2e_s = (time.perf_counter() - t1) / ke
+
+    # ---- the plain FP64 GPU form of the same evaluation
+    fp64 = None
+    if args.precision != "fp64":
+        e64 = engine.Engine(w.graph, w.factors, precision="fp64", device=dev)
+        o64 = torch.empty(2 + e64.n_parts, dtype=torch.float64, device=dev)
+        e64.launch(Xd, o64)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        s.record(stream)
+        for _ in range(reps):
+            e64.launch(Xd, o64)
+        e.record(stream)
+        torch.cuda.synchronize()
+        ms64 = s.elapsed_time(e) / reps
+        fp64 = {"evals_per_s": 1e3 / ms64, "ms_per_step": ms64, "speedup_of_this_mode": (1e3 / ms64) and value / (
+            1e3 / ms64)}
+
+    # ---- CPU baseline: the FP64 oracle on the host cores, and the error of this run
+    cpu = None
+    err = None
+    if not args.no_cpu_baseline:
+        ref, dt = oracle_eval(w)
+        cpu = {"value": 1.0 / dt, "unit": "evals/s", "cores": host_cores(), "kind": "oracle",
+               "sample": "one full evaluation of the workload (n=%d, all %d partitions)" % (n, eng.n_parts)}
+        V = result[2:]
+        Vr = np.asarray(ref["V"])
+        err = {"U_sum": abs(result[0] - ref["U_sum"]) / abs(ref["U_sum"]),
+               "V_max": float(np.max(np.abs(V - Vr) / np.abs(Vr)))}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "n": n, "d": d, "precision": args.precision,
+                   "partitions": eng.n_parts, "l2": "flushed (256 MiB write) before every timed step",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "tflops": {"algorithmic_plan": fl_plan * value / 1e12, "algorithmic_unshared": fl_naive * value / 1e12},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": 1.0 / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": int(Xh.numel() * Xh.element_size()),
+                "d2h_bytes_per_step": 8 * (2 + eng.n_parts)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "fp64_gpu": fp64,
+        "rel_err_vs_oracle": err,
+        "wall_s_timed_region": wall,
+        "profile": prof_share,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

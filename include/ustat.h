@@ -1,0 +1,208 @@
+/*
+ * ustat.h -- C ABI of the GB300 (sm_103a) engine for exact higher-order
+ * U-statistics whose kernel factors over a graph (arXiv 2508.12627).
+ *
+ * What is computed (paper, Section 3.3, Algorithm 4 "Ustats"):
+ *   U_sum = sum over ordered distinct m-tuples of
+ *           prod_{edges (a,b,f)} F_f(x_a, x_b) * prod_{unary (v,g)} g(x_v)
+ *         = sum over partitions pi of [m] of mu_pi * V_pi,
+ *   mu_pi = (-1)^(m-|pi|) prod_{C in pi} (|C|-1)!      (Lemma "Decomposition of
+ *           U-Statistic into V-Statistics", Section 3.3),
+ *   V_pi  = the restricted V-statistic (Definition "Restricted V-Statistic"): the
+ *           same product summed over tuples that are equal within each block of pi,
+ *           evaluated as Einsum(T, A_pi) on the induced notation (Algorithm 3) by
+ *           summing out one index at a time along an elimination order (Section
+ *           3.2, Proposition "complexity_einsum").
+ *   U_mean = U_sum / (n (n-1) ... (n-m+1)).
+ *
+ * Conventions
+ *   - Vertices are 0-based.  Partitions are indexed in the lexicographic order of
+ *     their restricted growth strings (rgs[0] = 0, rgs[i] <= 1 + max(rgs[0..i-1])),
+ *     the order ustat_plan_info() reports.
+ *   - Device pointers are plain CUDA device addresses on the current device.
+ *     The caller owns X, every factor buffer, the workspace and the outputs.
+ *     The library owns plans (host memory) and never allocates device memory.
+ *   - Every function returns USTAT_OK (0) or a negative USTAT_ERR_* code; on error
+ *     no output is written.  ustat_strerror() names a code.
+ *   - Evaluation enqueues work on the given CUDA stream and returns without
+ *     synchronising (except ustat_eval_host, which synchronises the stream).
+ */
+#ifndef USTAT_H
+#define USTAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define USTAT_OK                   0
+#define USTAT_ERR_INVALID_ARG     -1  /* null pointer, bad graph, bad size or factor */
+#define USTAT_ERR_N_LT_M          -2  /* n < m: the paper's U-statistic needs m <= n (Section 2.1) */
+#define USTAT_ERR_TW_TOO_LARGE    -3  /* no elimination order with steps the engine executes */
+#define USTAT_ERR_WORKSPACE       -4  /* workspace null, too small or misaligned */
+#define USTAT_ERR_NONFINITE       -5  /* reserved */
+#define USTAT_ERR_CUDA            -6  /* a CUDA call failed (see ustat_last_cuda_error) */
+#define USTAT_ERR_DEVICE_TIMEOUT  -7  /* a bounded device wait ran out */
+#define USTAT_ERR_UNSUPPORTED     -8  /* m > 7, arity > 2, or a mode not built */
+
+/* ---- factor kinds (per factor id) ---- */
+#define USTAT_RBF       0  /* F(x,y) = exp(-||x-y||^2 / param); unit diagonal        */
+#define USTAT_LINEAR    1  /* F(x,y) = (x . y) / param                                 */
+#define USTAT_TANH_DOT  2  /* f(x) = tanh(x . w), w = data (device, d doubles); unary  */
+#define USTAT_MATRIX    3  /* F given as data: device n x n float64, row-major          */
+#define USTAT_VECTOR    4  /* f given as data: device n float64; unary                   */
+
+/* ---- precision modes of the contractions ---- */
+#define USTAT_FP64    0  /* all arithmetic in float64 (CUDA cores)                          */
+#define USTAT_FP32    1  /* float32 factors and GEMMs (CUDA cores), float64 reductions       */
+#define USTAT_TF32    2  /* GEMMs on tcgen05 kind::tf32, FP32 accumulation                   */
+#define USTAT_BF16X3  3  /* GEMMs on tcgen05 kind::f16 with three bf16 fixed-point slices per
+                            operand, exact integer accumulation of the leading slice product */
+
+/* ---- planners (choice of elimination order per partition) ---- */
+#define USTAT_PLAN_EXHAUSTIVE  0  /* minimum modelled cost over all orders (<= 8 blocks) */
+#define USTAT_PLAN_MINFILL     1  /* greedy minimum fill-in, ties by degree then label */
+
+/*
+ * The kernel graph: the multiplicative decomposition h = prod_k h_k(x[A_k]) of
+ * the paper's Section 3.1 with signature tuples of length 2 (edges) and 1
+ * (unary factors).  edge k is the ordered pair (edge_src[k], edge_dst[k]) with
+ * factor id edge_factor[k]; its value is F(x_src, x_dst).  factor_kind[f] is
+ * the USTAT_* kind of factor id f (pairwise kinds on edges, unary kinds on
+ * unary entries).  Repeated pairs are separate factors (multiplied).
+ */
+typedef struct {
+    int m;                     /* order of the U-statistic, 1 <= m <= 7          */
+    int n_edges;
+    const int *edge_src, *edge_dst, *edge_factor;
+    int n_unary;
+    const int *unary_vertex, *unary_factor;
+    int n_factors;
+    const int *factor_kind;
+} ustat_graph;
+
+typedef struct {
+    int precision;   /* USTAT_FP64 / FP32 / TF32 / BF16X3                            */
+    int sparsify;    /* 1: zero-diagonal tensors T~ and only partitions in Pi_m^A
+                        (Lemma "sparsification_trick", equation "quotient_set");
+                        V_pi of skipped partitions is reported as 0                   */
+    int planner;     /* USTAT_PLAN_*                                                  */
+    int cse;         /* 1: share identical contractions across partitions             */
+} ustat_options;
+
+/* Factor values: param as in the kind's formula; data as described per kind. */
+typedef struct {
+    int kind;
+    double param;
+    const void *data;
+} ustat_factor;
+
+typedef struct ustat_plan ustat_plan_t;
+
+/*
+ * Build a plan (host only, no CUDA call): partitions, Moebius coefficients, the
+ * quotient factor multigraph of each partition (Definition "Quotient Graph";
+ * Algorithm 3), an elimination order per partition, and the lowered program of
+ * device operations.  *out receives a plan owned by the library; free it with
+ * ustat_plan_destroy().
+ */
+int ustat_plan(const ustat_graph *graph, const ustat_options *opts, ustat_plan_t **out);
+void ustat_plan_destroy(ustat_plan_t *plan);
+
+/*
+ * Plan report.  Any output pointer may be NULL.
+ *   n_parts : number of partitions (Bell(m))
+ *   mu      : [n_parts] Moebius coefficients mu_pi
+ *   tw      : [n_parts] treewidth of the quotient graph G/pi (exact); -1 if skipped
+ *   rgs     : [n_parts * m] restricted growth strings
+ *   evaluated: [n_parts] 1 if V_pi is computed, 0 if skipped by sparsification
+ *   n_ops   : number of device operations in the lowered program
+ *   n_gemm  : number of n^3 contractions (stored + fused) in the program
+ *   n_gemm3 : number of n^4 contractions
+ */
+int ustat_plan_info(const ustat_plan_t *plan, int *n_parts, int *mu, int *tw, int *rgs,
+                    int *evaluated, int *n_ops, int *n_gemm, int *n_gemm3);
+
+/*
+ * Text listing of the lowered program, one operation per line
+ * ("<index> <op> out=<slot> ..."), NUL-terminated and truncated to buf_len.
+ * *needed (may be NULL) receives the full length including the NUL.
+ */
+int ustat_plan_describe(const ustat_plan_t *plan, char *buf, size_t buf_len, size_t *needed);
+
+/*
+ * Algorithmic flop count for sample size n (the paper's cost model, Appendix D,
+ * Lemma "complexity_one_index": eliminating an index with s neighbours costs
+ * 2 n^(s+1)): flops_plan counts the lowered program (after sharing), flops_naive
+ * counts every partition's own elimination without sharing.
+ */
+int ustat_plan_flops(const ustat_plan_t *plan, int64_t n, double *flops_plan, double *flops_naive);
+
+/* Device workspace bytes needed by ustat_eval for sample size n, dimension d. */
+int ustat_workspace_bytes(const ustat_plan_t *plan, int64_t n, int d, size_t *bytes);
+
+/*
+ * Evaluate U and every V_pi for one sample.
+ *   X       : device, n x d row-major, x_dtype 0 = float64, 1 = float32
+ *   factors : host array [n_factors] (the graph's factor ids), data pointers device
+ *   ws      : device workspace of at least ustat_workspace_bytes() bytes, 256-byte
+ *             aligned; its contents on entry are ignored
+ *   stream  : cudaStream_t (NULL = legacy default stream)
+ *   U_out   : device float64 [2] = {U_sum, U_mean}
+ *   V_out   : device float64 [n_parts] (V_pi in partition order) or NULL
+ * Errors: INVALID_ARG, N_LT_M (n < m), WORKSPACE, UNSUPPORTED, CUDA.
+ */
+int ustat_eval(ustat_plan_t *plan, const void *X, int x_dtype, int64_t n, int d,
+               const ustat_factor *factors, int n_factors, void *ws, size_t ws_bytes,
+               void *stream, double *U_out, double *V_out);
+
+/*
+ * Same computation with host inputs and outputs: X_host (n x d, x_dtype) is
+ * copied into the workspace, factor data stay device pointers, and U_host[2] /
+ * V_host[n_parts] (may be NULL) receive the results.  The workspace must hold
+ * ustat_workspace_bytes() + ustat_host_staging_bytes().  Synchronises the stream.
+ */
+int ustat_host_staging_bytes(const ustat_plan_t *plan, int64_t n, int d, size_t *bytes);
+int ustat_eval_host(ustat_plan_t *plan, const void *X_host, int x_dtype, int64_t n, int d,
+                    const ustat_factor *factors, int n_factors, void *ws, size_t ws_bytes,
+                    void *stream, double *U_host, double *V_host);
+
+/*
+ * Many independent samples, one plan: sample i has n[i] rows at X[i] (device,
+ * row-major, x_dtype), dimension d; results at U_out[2*i], V_out[i*n_parts].
+ * ws is split into equal per-sample regions sized for max(n) by the library.
+ */
+int ustat_eval_batch(ustat_plan_t *plan, const void *const *X, int x_dtype, const int64_t *n,
+                     int count, int d, const ustat_factor *factors, int n_factors, void *ws,
+                     size_t ws_bytes, void *stream, double *U_out, double *V_out);
+int ustat_batch_workspace_bytes(const ustat_plan_t *plan, const int64_t *n, int count, int d,
+                                size_t *bytes);
+
+/*
+ * Per-operation timing for measurement.  While enabled (per host thread), every
+ * device operation launched by ustat_eval on that thread is bracketed by a pair
+ * of CUDA events on the evaluation stream.  ustat_profile_collect() waits for
+ * the recorded events, adds their durations per operation kind into
+ * ms[kind] and launch counts into launches[kind] (arrays of ustat_profile_kinds()
+ * entries, may be NULL), names the kinds through ustat_profile_kind_name(), and
+ * resets the record.  Events are created once and reused; no device memory is
+ * allocated.
+ */
+int ustat_profile_enable(int enable);
+int ustat_profile_kinds(void);
+const char *ustat_profile_kind_name(int kind);
+int ustat_profile_collect(double *ms, int *launches);
+
+/* The last CUDA error string seen by the library in this thread ("" if none). */
+const char *ustat_last_cuda_error(void);
+const char *ustat_strerror(int code);
+/* Library version string. */
+const char *ustat_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* USTAT_H */

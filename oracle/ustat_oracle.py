@@ -314,19 +314,23 @@ def v_pi(sig, tensors, rgs) -> float:
     return einsum_eliminate(k, [(tup, tensors[f]) for tup, f in ind])
 
 
-def ustat(graph, factors, X, sparse: bool = False, partitions=None):
+def ustat(graph, factors, X, sparse: bool = False, partitions=None, absolute: bool = False):
     """Algorithm 4 (Ustats), returning a dict with
     ``U_sum`` (the paper's unnormalised sum over ordered distinct tuples),
     ``U_mean`` = U_sum / (n)_m, and per-partition ``rgs``, ``mu`` and ``V``.
 
     With ``sparse`` the tensors are T~ and only partitions in Pi_m^A are evaluated
     (the others are reported as V = 0); otherwise V_pi of the original tensors is
-    computed for every partition."""
+    computed for every partition.  With ``absolute`` every tensor is replaced by
+    its entrywise absolute value: V_pi is then the sum of |terms| of V_pi, the
+    scale against which rounding errors of a sum with cancellation are judged."""
     X = np.asarray(X)
     n = X.shape[0]
     m = graph.m
     sig = signature(graph)
     T = tensorize(graph, factors, X)
+    if absolute:
+        T = {f: np.abs(a) for f, a in T.items()}
     if sparse:
         T = {f: sparsify(a) for f, a in T.items()}
     parts = set_partitions(m) if partitions is None else partitions

@@ -1,0 +1,535 @@
+// C ABI (include/ustat.h): plans, workspace layout and the executor that walks
+// a plan's lowered program and launches one kernel per operation on the
+// caller's stream, ending with the Moebius combination (Algorithm 4).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "ustat_internal.h"
+
+using namespace ustat;
+
+namespace {
+
+thread_local std::string g_last_cuda_error;
+
+int cuda_fail(cudaError_t e) {
+    g_last_cuda_error = cudaGetErrorString(e);
+    return USTAT_ERR_CUDA;
+}
+
+// ---- optional per-operation event timing (ustat_profile_*)
+constexpr int kProfXconvert = OP_COUNT, kProfCombine = OP_COUNT + 1, kProfKinds = OP_COUNT + 2;
+struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+};
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    std::vector<ProfRec> recs;
+    cudaEvent_t get() {
+        if (used == pool.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+};
+thread_local Profiler g_prof;
+
+struct ProfScope {
+    cudaStream_t st;
+    ProfRec r{-1, nullptr, nullptr};
+    ProfScope(int kind, cudaStream_t s) : st(s) {
+        if (!g_prof.on) return;
+        r.kind = kind;
+        r.a = g_prof.get();
+        r.b = g_prof.get();
+        if (r.a) cudaEventRecord(r.a, st);
+    }
+    ~ProfScope() {
+        if (r.kind < 0 || !r.a || !r.b) return;
+        cudaEventRecord(r.b, st);
+        g_prof.recs.push_back(r);
+    }
+};
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Layout {
+    std::vector<size_t> off;     // per slot
+    std::vector<int> scal_index; // per slot: index into the scalar array (or -1)
+    size_t err_off = 0, scal_off = 0, zero_bytes = 0, xw_off = 0, total = 0;
+    int64_t ldp_slices = 0, ldp_prep = 0;
+};
+
+bool needs_xw(const Plan &P) {
+    for (auto &op : P.ops)
+        if (op.kind == OP_KBUILD) return true;
+    return false;
+}
+
+Layout make_layout(const Plan &P, int64_t n, int d) {
+    Layout L;
+    const size_t esz = P.precision == USTAT_FP64 ? 8 : 4;
+    L.ldp_slices = (int64_t)align_up((size_t)n, 64);
+    L.ldp_prep = (int64_t)align_up((size_t)n, 32);
+    L.off.assign(P.slots.size(), 0);
+    L.scal_index.assign(P.slots.size(), -1);
+    size_t cur = 0;
+    L.err_off = cur;
+    cur += 256;
+    L.scal_off = cur;
+    int ns = 0;
+    for (size_t s = 0; s < P.slots.size(); ++s)
+        if (P.slots[s].kind == S_SCAL) {
+            L.scal_index[s] = ns;
+            L.off[s] = cur + 8 * (size_t)ns;
+            ++ns;
+        }
+    cur = align_up(cur + 8 * (size_t)ns, 256);
+    for (size_t s = 0; s < P.slots.size(); ++s)
+        if (P.slots[s].kind == S_VEC) {
+            L.off[s] = cur;
+            cur = align_up(cur + 8 * (size_t)n, 256);
+        }
+    L.zero_bytes = cur;   // error word, scalars and vectors are cleared per evaluation
+    cur = align_up(cur, 1024);
+    if (needs_xw(P)) {
+        L.xw_off = cur;
+        cur = align_up(cur + esz * (size_t)n * d, 1024);
+    }
+    for (size_t s = 0; s < P.slots.size(); ++s) {
+        switch (P.slots[s].kind) {
+            case S_MAT:
+                L.off[s] = cur;
+                cur = align_up(cur + esz * (size_t)n * n, 1024);
+                break;
+            case S_SLICES:
+                L.off[s] = cur;
+                cur = align_up(cur + 3 * 2 * (size_t)n * L.ldp_slices + 4 * (size_t)n, 1024);
+                break;
+            case S_PREP:
+                L.off[s] = cur;
+                cur = align_up(cur + 4 * (size_t)n * L.ldp_prep, 1024);
+                break;
+            default:
+                break;
+        }
+    }
+    L.total = cur;
+    return L;
+}
+
+struct Ctx {
+    const Plan &P;
+    const Layout &L;
+    char *ws;
+    int64_t n;
+    int d;
+    bool fp64;
+    cudaStream_t st;
+    void *ptr(int slot) const { return slot < 0 ? nullptr : (void *)(ws + L.off[slot]); }
+    double *vec(int slot) const { return (double *)ptr(slot); }
+    // slices: [3][n][ldp] bf16 followed by float scales [n]
+    float *scales(int slot) const {
+        return (float *)(ws + L.off[slot] + 3 * 2 * (size_t)n * L.ldp_slices);
+    }
+};
+
+int check_graph_factors(const Plan &P, const ustat_factor *f, int nf, int d) {
+    if (nf != (int)P.factor_kind.size() || !f) return USTAT_ERR_INVALID_ARG;
+    for (int i = 0; i < nf; ++i) {
+        if (f[i].kind != P.factor_kind[i]) return USTAT_ERR_INVALID_ARG;
+        int k = f[i].kind;
+        if ((k == USTAT_RBF || k == USTAT_LINEAR) && !(f[i].param > 0.0)) return USTAT_ERR_INVALID_ARG;
+        if ((k == USTAT_TANH_DOT || k == USTAT_MATRIX || k == USTAT_VECTOR) && !f[i].data) return USTAT_ERR_INVALID_ARG;
+    }
+    (void)d;
+    return USTAT_OK;
+}
+
+int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f, double *U_out, double *V_out) {
+    const Plan &P = C.P;
+    const int64_t n = C.n;
+    cudaError_t e = cudaMemsetAsync(C.ws, 0, C.L.zero_bytes, C.st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int *err = (int *)(C.ws + C.L.err_off);
+    if (needs_xw(P)) {
+        ProfScope ps(kProfXconvert, C.st);
+        e = launch_xconvert(X, x_dtype, n, C.d, C.ws + C.L.xw_off, C.fp64, C.st);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    const int lead = split_lead_bits(n);
+    for (const Op &op : P.ops) {
+        ProfScope ps(op.kind, C.st);
+        switch (op.kind) {
+            case OP_KBUILD:
+                e = launch_kbuild(f[op.factor].kind, f[op.factor].param, C.ws + C.L.xw_off, C.fp64, n, C.d,
+                                  P.sparsify, C.ptr(op.out), C.st);
+                break;
+            case OP_LOADMAT:
+                e = launch_loadmat((const double *)f[op.factor].data, n, C.fp64, P.sparsify, C.ptr(op.out), C.st);
+                break;
+            case OP_UNARY:
+                e = launch_unary_tanh(X, x_dtype, n, C.d, (const double *)f[op.factor].data, C.vec(op.out), C.st);
+                break;
+            case OP_LOADVEC:
+                e = launch_copyvec((const double *)f[op.factor].data, n, C.vec(op.out), C.st);
+                break;
+            case OP_DIAG:
+                e = launch_diag(C.ptr(op.t[0].mat), C.fp64, n, C.vec(op.out), C.st);
+                break;
+            case OP_VMUL:
+                e = launch_vmul(C.vec(op.u), C.vec(op.a), n, C.vec(op.out), C.st);
+                break;
+            case OP_VSUM:
+                e = launch_vsum(C.vec(op.u), n, C.vec(op.out), C.st);
+                break;
+            case OP_HADAMARD:
+            case OP_GEMV:
+            case OP_FREDUCE: {
+                TileTerms tt{};
+                tt.nt = op.nt;
+                for (int t = 0; t < op.nt; ++t) {
+                    tt.M[t] = C.ptr(op.t[t].mat);
+                    tt.trans[t] = P.slots[op.t[t].mat].symmetric ? 0 : op.t[t].trans;
+                }
+                if (op.kind == OP_HADAMARD)
+                    e = launch_tile_op(TILE_HADAMARD, tt, C.fp64, n, nullptr, nullptr, C.ptr(op.out), C.st);
+                else if (op.kind == OP_GEMV)
+                    e = launch_tile_op(TILE_GEMV, tt, C.fp64, n, C.vec(op.u), nullptr, C.ptr(op.out), C.st);
+                else
+                    e = launch_tile_op(TILE_FREDUCE, tt, C.fp64, n, C.vec(op.a), C.vec(op.b), C.ptr(op.out), C.st);
+                break;
+            }
+            case OP_SPLIT:
+            case OP_PREP: {
+                const Term t = op.t[0];
+                const int tr = P.slots[t.mat].symmetric ? 1 : t.trans;
+                if (op.kind == OP_SPLIT)
+                    e = launch_split((const float *)C.ptr(t.mat), tr, C.vec(op.u), n, C.L.ldp_slices, lead,
+                                     C.ptr(op.out), C.scales(op.out), C.st);
+                else
+                    e = launch_prep((const float *)C.ptr(t.mat), tr, C.vec(op.u), n, C.L.ldp_prep,
+                                    (float *)C.ptr(op.out), C.st);
+                break;
+            }
+            case OP_GEMM:
+            case OP_GEMM_RED: {
+                const bool red = op.kind == OP_GEMM_RED;
+                if (P.precision == USTAT_BF16X3 || P.precision == USTAT_TF32) {
+                    TcGemmArgs g{};
+                    g.n = n;
+                    g.ldp = P.precision == USTAT_BF16X3 ? C.L.ldp_slices : C.L.ldp_prep;
+                    g.opA = C.ptr(op.opA);
+                    g.opB = C.ptr(op.opB);
+                    g.scaleA = P.precision == USTAT_BF16X3 ? C.scales(op.opA) : nullptr;
+                    g.scaleB = P.precision == USTAT_BF16X3 ? C.scales(op.opB) : nullptr;
+                    g.lead_bits = lead;
+                    g.err = err;
+                    if (red) {
+                        g.red = (double *)C.ptr(op.out);
+                        g.W = (const float *)C.ptr(op.W.mat);
+                        g.transW = (op.W.mat >= 0 && !P.slots[op.W.mat].symmetric) ? op.W.trans : 0;
+                        g.a = C.vec(op.a);
+                        g.b = C.vec(op.b);
+                    } else {
+                        g.C = (float *)C.ptr(op.out);
+                    }
+                    e = P.precision == USTAT_BF16X3 ? launch_gemm_bf16x3(g, C.st) : launch_gemm_tf32(g, C.st);
+                } else {
+                    SimtGemmArgs g{};
+                    g.n = n;
+                    g.A = C.ptr(op.A.mat);
+                    g.transA = P.slots[op.A.mat].symmetric ? 0 : op.A.trans;
+                    g.B = C.ptr(op.B.mat);
+                    g.transB = P.slots[op.B.mat].symmetric ? 0 : op.B.trans;
+                    g.u = C.vec(op.u);
+                    if (red) {
+                        g.red = (double *)C.ptr(op.out);
+                        g.W = C.ptr(op.W.mat);
+                        g.transW = (op.W.mat >= 0 && !P.slots[op.W.mat].symmetric) ? op.W.trans : 0;
+                        g.a = C.vec(op.a);
+                        g.b = C.vec(op.b);
+                    } else {
+                        g.C = C.ptr(op.out);
+                    }
+                    e = launch_gemm_simt(g, C.fp64, C.st);
+                }
+                break;
+            }
+            case OP_GEMM3: {
+                SimtGemmArgs g{};
+                auto tr = [&](const Term &t) { return (t.mat >= 0 && !P.slots[t.mat].symmetric) ? t.trans : 0; };
+                g.n = n;
+                g.gemm3 = 1;
+                g.A = C.ptr(op.A.mat);
+                g.transA = tr(op.A);
+                g.B = C.ptr(op.B.mat);
+                g.transB = tr(op.B);
+                g.u = C.vec(op.u);
+                g.Ab = C.ptr(op.Ab.mat);
+                g.transAb = tr(op.Ab);
+                g.red = (double *)C.ptr(op.out);
+                g.W = C.ptr(op.W.mat);
+                g.transW = tr(op.W);
+                g.Wbc = C.ptr(op.Wbc.mat);
+                g.transWbc = tr(op.Wbc);
+                g.Wbd = C.ptr(op.Wbd.mat);
+                g.transWbd = tr(op.Wbd);
+                g.ub = C.vec(op.ub);
+                g.a = C.vec(op.a);
+                g.b = C.vec(op.b);
+                e = launch_gemm_simt(g, C.fp64, C.st);
+                break;
+            }
+            default:
+                return USTAT_ERR_UNSUPPORTED;
+        }
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    // Moebius combination
+    static thread_local CombineTable tab;
+    tab.nparts = (int)P.parts.size();
+    tab.m = P.m;
+    for (int p = 0; p < tab.nparts; ++p) {
+        const PartRec &pr = P.parts[p];
+        tab.mu[p] = pr.mu;
+        tab.nfree[p] = (unsigned char)pr.nfree;
+        tab.evaluated[p] = (unsigned char)pr.evaluated;
+        for (int q = 0; q < kCombineMaxScal; ++q)
+            tab.sid[p][q] = (q < pr.nscal) ? (unsigned short)C.L.scal_index[pr.scal[q]] : (unsigned short)0xffff;
+    }
+    {
+        ProfScope ps(kProfCombine, C.st);
+        e = launch_combine(tab, (const double *)(C.ws + C.L.scal_off), err, n, U_out, V_out, C.st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    return USTAT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ustat_plan(const ustat_graph *graph, const ustat_options *opts, ustat_plan_t **out) {
+    if (!graph || !opts || !out) return USTAT_ERR_INVALID_ARG;
+    ustat_plan_t *p = new (std::nothrow) ustat_plan_t();
+    if (!p) return USTAT_ERR_INVALID_ARG;
+    int rc = build_plan(graph, opts, &p->p);
+    if (rc != USTAT_OK) {
+        delete p;
+        return rc;
+    }
+    if ((int)p->p.parts.size() > kCombineMaxParts) {
+        delete p;
+        return USTAT_ERR_UNSUPPORTED;
+    }
+    *out = p;
+    return USTAT_OK;
+}
+
+void ustat_plan_destroy(ustat_plan_t *plan) { delete plan; }
+
+int ustat_plan_info(const ustat_plan_t *plan, int *n_parts, int *mu, int *tw, int *rgs, int *evaluated, int *n_ops,
+                    int *n_gemm, int *n_gemm3) {
+    if (!plan) return USTAT_ERR_INVALID_ARG;
+    const Plan &P = plan->p;
+    if (n_parts) *n_parts = (int)P.parts.size();
+    for (size_t i = 0; i < P.parts.size(); ++i) {
+        if (mu) mu[i] = P.parts[i].mu;
+        if (tw) tw[i] = P.parts[i].tw;
+        if (evaluated) evaluated[i] = P.parts[i].evaluated;
+        if (rgs)
+            for (int q = 0; q < P.m; ++q) rgs[i * P.m + q] = P.parts[i].rgs[q];
+    }
+    if (n_ops) *n_ops = (int)P.ops.size();
+    if (n_gemm) *n_gemm = P.n_gemm;
+    if (n_gemm3) *n_gemm3 = P.n_gemm3;
+    return USTAT_OK;
+}
+
+int ustat_plan_flops(const ustat_plan_t *plan, int64_t n, double *flops_plan, double *flops_naive) {
+    if (!plan || n < 1) return USTAT_ERR_INVALID_ARG;
+    const Plan &P = plan->p;
+    const double dn = (double)n;
+    double fp = 0.0, fn = 0.0;
+    for (auto &op : P.ops) fp += op.coef * std::pow(dn, op.npow);
+    for (auto &pr : P.parts)
+        if (pr.evaluated)
+            for (int q = 0; q < 5; ++q) fn += pr.naive_coef[q] * std::pow(dn, q + 1);
+    if (flops_plan) *flops_plan = fp;
+    if (flops_naive) *flops_naive = fn;
+    return USTAT_OK;
+}
+
+int ustat_workspace_bytes(const ustat_plan_t *plan, int64_t n, int d, size_t *bytes) {
+    if (!plan || !bytes || n < 1 || d < 1) return USTAT_ERR_INVALID_ARG;
+    *bytes = make_layout(plan->p, n, d).total;
+    return USTAT_OK;
+}
+
+int ustat_eval(ustat_plan_t *plan, const void *X, int x_dtype, int64_t n, int d, const ustat_factor *factors,
+               int n_factors, void *ws, size_t ws_bytes, void *stream, double *U_out, double *V_out) {
+    if (!plan || !X || !U_out || d < 1 || n < 1 || (x_dtype != 0 && x_dtype != 1)) return USTAT_ERR_INVALID_ARG;
+    const Plan &P = plan->p;
+    if (n < P.m) return USTAT_ERR_N_LT_M;
+    if (n > (int64_t)1 << 20) return USTAT_ERR_UNSUPPORTED;
+    int rc = check_graph_factors(P, factors, n_factors, d);
+    if (rc != USTAT_OK) return rc;
+    Layout L = make_layout(P, n, d);
+    if (!ws || ws_bytes < L.total || ((uintptr_t)ws % 256) != 0) return USTAT_ERR_WORKSPACE;
+    Ctx C{P, L, (char *)ws, n, d, P.precision == USTAT_FP64, (cudaStream_t)stream};
+    return run_program(C, X, x_dtype, factors, U_out, V_out);
+}
+
+int ustat_host_staging_bytes(const ustat_plan_t *plan, int64_t n, int d, size_t *bytes) {
+    if (!plan || !bytes || n < 1 || d < 1) return USTAT_ERR_INVALID_ARG;
+    *bytes = align_up(8 * (size_t)n * d, 1024) + align_up(8 * (2 + plan->p.parts.size()), 1024);
+    return USTAT_OK;
+}
+
+int ustat_eval_host(ustat_plan_t *plan, const void *X_host, int x_dtype, int64_t n, int d,
+                    const ustat_factor *factors, int n_factors, void *ws, size_t ws_bytes, void *stream,
+                    double *U_host, double *V_host) {
+    if (!plan || !X_host || !U_host || d < 1 || n < 1 || (x_dtype != 0 && x_dtype != 1)) return USTAT_ERR_INVALID_ARG;
+    const Plan &P = plan->p;
+    if (n < P.m) return USTAT_ERR_N_LT_M;
+    size_t main_bytes = make_layout(P, n, d).total, stage = 0;
+    ustat_host_staging_bytes(plan, n, d, &stage);
+    if (!ws || ws_bytes < main_bytes + stage) return USTAT_ERR_WORKSPACE;
+    char *xs = (char *)ws + main_bytes;
+    double *outs = (double *)(xs + align_up(8 * (size_t)n * d, 1024));
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t xbytes = (x_dtype == 0 ? 8 : 4) * (size_t)n * d;
+    cudaError_t e = cudaMemcpyAsync(xs, X_host, xbytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int rc = ustat_eval(plan, xs, x_dtype, n, d, factors, n_factors, ws, main_bytes, stream, outs, outs + 2);
+    if (rc != USTAT_OK) return rc;
+    e = cudaMemcpyAsync(U_host, outs, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && V_host)
+        e = cudaMemcpyAsync(V_host, outs + 2, P.parts.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return USTAT_OK;
+}
+
+int ustat_batch_workspace_bytes(const ustat_plan_t *plan, const int64_t *n, int count, int d, size_t *bytes) {
+    if (!plan || !n || count < 1 || !bytes) return USTAT_ERR_INVALID_ARG;
+    int64_t mx = 0;
+    for (int i = 0; i < count; ++i) mx = std::max(mx, n[i]);
+    return ustat_workspace_bytes(plan, mx, d, bytes);
+}
+
+int ustat_eval_batch(ustat_plan_t *plan, const void *const *X, int x_dtype, const int64_t *n, int count, int d,
+                     const ustat_factor *factors, int n_factors, void *ws, size_t ws_bytes, void *stream,
+                     double *U_out, double *V_out) {
+    if (!plan || !X || !n || count < 1 || !U_out) return USTAT_ERR_INVALID_ARG;
+    const int np = (int)plan->p.parts.size();
+    for (int i = 0; i < count; ++i) {
+        int rc = ustat_eval(plan, X[i], x_dtype, n[i], d, factors, n_factors, ws, ws_bytes, stream, U_out + 2 * i,
+                            V_out ? V_out + (size_t)i * np : nullptr);
+        if (rc != USTAT_OK) return rc;
+    }
+    return USTAT_OK;
+}
+
+int ustat_profile_enable(int enable) {
+    g_prof.on = enable != 0;
+    return USTAT_OK;
+}
+
+int ustat_profile_kinds(void) { return kProfKinds; }
+
+const char *ustat_profile_kind_name(int kind) {
+    if (kind == kProfXconvert) return "xconvert";
+    if (kind == kProfCombine) return "combine";
+    return op_name(kind);
+}
+
+int ustat_profile_collect(double *ms, int *launches) {
+    for (auto &r : g_prof.recs) {
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e != cudaSuccess) return cuda_fail(e);
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, r.a, r.b);
+        if (e != cudaSuccess) return cuda_fail(e);
+        if (ms) ms[r.kind] += t;
+        if (launches) launches[r.kind] += 1;
+    }
+    g_prof.recs.clear();
+    g_prof.used = 0;
+    return USTAT_OK;
+}
+
+const char *ustat_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
+
+const char *ustat_strerror(int code) {
+    switch (code) {
+        case USTAT_OK: return "ok";
+        case USTAT_ERR_INVALID_ARG: return "invalid argument";
+        case USTAT_ERR_N_LT_M: return "sample size n is smaller than the order m";
+        case USTAT_ERR_TW_TOO_LARGE: return "no executable elimination order (treewidth too large)";
+        case USTAT_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+        case USTAT_ERR_NONFINITE: return "non-finite input";
+        case USTAT_ERR_CUDA: return "CUDA error";
+        case USTAT_ERR_DEVICE_TIMEOUT: return "bounded device wait ran out";
+        case USTAT_ERR_UNSUPPORTED: return "unsupported";
+        default: return "unknown error";
+    }
+}
+
+const char *ustat_version(void) { return "ustat-gb300 0.1"; }
+
+}  // extern "C"
+
+extern "C" int ustat_plan_describe(const ustat_plan_t *plan, char *buf, size_t buf_len, size_t *needed) {
+    if (!plan) return USTAT_ERR_INVALID_ARG;
+    const Plan &P = plan->p;
+    std::string s;
+    char line[512];
+    auto term = [&](const Term &t) -> std::string {
+        if (t.mat < 0) return "1";
+        return "M" + std::to_string(t.mat) + (t.trans ? "^T" : "");
+    };
+    auto vec = [&](int v) -> std::string { return v < 0 ? "1" : "v" + std::to_string(v); };
+    for (size_t i = 0; i < P.ops.size(); ++i) {
+        const Op &o = P.ops[i];
+        std::string ts;
+        for (int t = 0; t < o.nt; ++t) ts += (t ? "," : "") + term(o.t[t]);
+        snprintf(line, sizeof(line),
+                 "%zu %s out=%d f=%d terms=[%s] u=%s a=%s b=%s A=%s B=%s W=%s Ab=%s Wbc=%s Wbd=%s ub=%s opA=%d opB=%d\n",
+                 i, op_name(o.kind), o.out, o.factor, ts.c_str(), vec(o.u).c_str(), vec(o.a).c_str(),
+                 vec(o.b).c_str(), term(o.A).c_str(), term(o.B).c_str(), term(o.W).c_str(), term(o.Ab).c_str(),
+                 term(o.Wbc).c_str(), term(o.Wbd).c_str(), vec(o.ub).c_str(), o.opA, o.opB);
+        s += line;
+    }
+    for (size_t p = 0; p < P.parts.size(); ++p) {
+        const PartRec &r = P.parts[p];
+        std::string rg, sc;
+        for (int q = 0; q < P.m; ++q) rg += std::to_string(r.rgs[q]);
+        for (int q = 0; q < r.nscal; ++q) sc += (q ? "," : "") + std::to_string(r.scal[q]);
+        snprintf(line, sizeof(line), "part %zu rgs=%s mu=%d tw=%d eval=%d nfree=%d scal=[%s]\n", p, rg.c_str(), r.mu,
+                 r.tw, r.evaluated, r.nfree, sc.c_str());
+        s += line;
+    }
+    if (needed) *needed = s.size() + 1;
+    if (buf && buf_len) {
+        size_t k = std::min(buf_len - 1, s.size());
+        std::memcpy(buf, s.data(), k);
+        buf[k] = 0;
+    }
+    return USTAT_OK;
+}

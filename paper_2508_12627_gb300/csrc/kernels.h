@@ -1,0 +1,98 @@
+// Host-side launchers of the engine's CUDA kernels (internal).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ustat {
+
+// ---- tensorization and vector ops (k_elem.cu)
+// Xw = working copy of X: float64 when fp64, else float32 (row-major n x d).
+cudaError_t launch_xconvert(const void *X, int x_dtype, int64_t n, int d, void *Xw, bool fp64,
+                            cudaStream_t s);
+// K(i,j) = exp(-||x_i - x_j||^2 / param) (kind RBF) or (x_i . x_j) / param (LINEAR).
+cudaError_t launch_kbuild(int kind, double param, const void *Xw, bool fp64, int64_t n, int d,
+                          int zero_diag, void *K, cudaStream_t s);
+cudaError_t launch_loadmat(const double *src, int64_t n, bool fp64, int zero_diag, void *dst,
+                           cudaStream_t s);
+cudaError_t launch_unary_tanh(const void *X, int x_dtype, int64_t n, int d, const double *w,
+                              double *out, cudaStream_t s);
+cudaError_t launch_copyvec(const double *src, int64_t n, double *dst, cudaStream_t s);
+cudaError_t launch_diag(const void *M, bool fp64, int64_t n, double *out, cudaStream_t s);
+cudaError_t launch_vmul(const double *a, const double *b, int64_t n, double *out, cudaStream_t s);
+cudaError_t launch_vsum(const double *u, int64_t n, double *out, cudaStream_t s);
+
+// ---- tiled elementwise / reduction ops over up to 4 oriented matrix terms (k_hb.cu)
+enum TileMode : int { TILE_HADAMARD = 0, TILE_FREDUCE = 1, TILE_GEMV = 2 };
+struct TileTerms {
+    const void *M[4];
+    int trans[4];
+    int nt;
+};
+// HADAMARD: out(i,j) = prod_t term_t(i,j)                       (out: matrix)
+// FREDUCE : *out += sum_ij prod_t term_t(i,j) a(i) b(j)          (out: double scalar)
+// GEMV    : out(j) += sum_i a(i) prod_t term_t(i,j)              (out: double vector)
+cudaError_t launch_tile_op(int mode, const TileTerms &tt, bool fp64, int64_t n, const double *a,
+                           const double *b, void *out, cudaStream_t s);
+
+// ---- SIMT GEMMs in float32 / float64 (k_gemm_simt.cu)
+struct SimtGemmArgs {
+    int64_t n;
+    const void *A;  int transA;     // A(i, j)
+    const void *B;  int transB;     // B(i, k)
+    const double *u;                // along i, may be null
+    // epilogue
+    void *C;                        // store mode: C(j, k), row-major n x n
+    double *red;                    // reduce mode: *red += sum ...
+    const void *W;  int transW;     // weight W(j, k), may be null
+    const double *a, *b;            // along j / k, may be null
+    // GEMM3 (batched over index bb): u'(i) = u(i) Ab(i, bb); weights Wbc(bb, j), Wbd(bb, k), ub(bb)
+    const void *Ab; int transAb;
+    const void *Wbc; int transWbc;
+    const void *Wbd; int transWbd;
+    const double *ub;
+    int gemm3;
+};
+cudaError_t launch_gemm_simt(const SimtGemmArgs &g, bool fp64, cudaStream_t s);
+
+// ---- Moebius combination (k_elem.cu)
+constexpr int kCombineMaxParts = 877;
+constexpr int kCombineMaxScal = 6;
+struct CombineTable {
+    int nparts;
+    int m;
+    int mu[kCombineMaxParts];
+    unsigned short sid[kCombineMaxParts][kCombineMaxScal];   // scalar slot index, 0xffff = none
+    unsigned char nfree[kCombineMaxParts];
+    unsigned char evaluated[kCombineMaxParts];
+};
+// A non-zero *err (a bounded device wait gave up) turns U and V into NaN.
+cudaError_t launch_combine(const CombineTable &tab, const double *scal, const int *err, int64_t n,
+                           double *U_out, double *V_out, cudaStream_t s);
+
+// ---- tensor-core path (k_gemm_tc.cu)
+// digits of the leading bf16 slice for a contraction of length K (exact integer
+// accumulation of the leading product needs K * 4^w1 <= 2^24)
+int split_lead_bits(int64_t K);
+// Operand X(j, i) = M(i, j) u(i) (term orientation trans), written K-major:
+//   bf16x3 slices [3][n][ldp] plus float row scales [n]       (launch_split)
+//   float32 tf32-rounded copy [n][ldp]                        (launch_prep)
+cudaError_t launch_split(const float *M, int trans, const double *u, int64_t n, int64_t ldp,
+                         int lead_bits, void *slices, float *scales, cudaStream_t s);
+cudaError_t launch_prep(const float *M, int trans, const double *u, int64_t n, int64_t ldp,
+                        float *out, cudaStream_t s);
+struct TcGemmArgs {
+    int64_t n, ldp;
+    const void *opA; const float *scaleA;   // K-major operand of A (slices or prep)
+    const void *opB; const float *scaleB;
+    int lead_bits;
+    float *C;                                // store mode
+    double *red;                             // reduce mode
+    const float *W; int transW;
+    const double *a, *b;
+    int *err;                                // device error word (bounded waits)
+};
+cudaError_t launch_gemm_bf16x3(const TcGemmArgs &g, cudaStream_t s);
+cudaError_t launch_gemm_tf32(const TcGemmArgs &g, cudaStream_t s);
+
+}  // namespace ustat

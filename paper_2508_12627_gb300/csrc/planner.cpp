@@ -1,0 +1,825 @@
+// Planner: partitions, Moebius coefficients, quotient factor multigraphs,
+// elimination orders and the lowered program of device operations.
+//
+// Paper (arXiv 2508.12627) passages implemented here:
+//   - partitions of [m] (Section 2.3, Definition "Partition"), as restricted
+//     growth strings in lexicographic order;
+//   - mu_pi = (-1)^(m-|pi|) prod_C (|C|-1)! (Section 3.3, Lemma "Decomposition of
+//     U-Statistic into V-Statistics");
+//   - the induced notation A_pi (Algorithm 3): every index replaced by its block,
+//     kept here as a factor multigraph on the blocks (quotient graph, Definition
+//     "Quotient Graph", with parallel factors kept as Hadamard products and
+//     intra-block pairwise factors kept as their diagonal);
+//   - the sparsification filter Pi_m^A (Lemma "sparsification_trick" and
+//     equation "quotient_set");
+//   - Einsum by summing out one index at a time along an elimination order
+//     (Section 3.2, Proposition "complexity_einsum"; Appendix D): eliminating a
+//     vertex with s live neighbours costs 2 n^(s+1) and yields a factor on those
+//     neighbours;
+//   - treewidth (Definitions "Vertex Elimination" and "Treewidth"), computed
+//     exactly by dynamic programming over vertex subsets.
+#include <algorithm>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <set>
+#include <tuple>
+#include <vector>
+
+#include "ustat_internal.h"
+
+namespace ustat {
+
+const char *op_name(int k) {
+    static const char *names[] = {"kbuild", "loadmat", "unary",  "loadvec", "diag",
+                                  "vmul",   "hadamard", "gemv",  "vsum",    "gemm",
+                                  "gemm_red", "freduce", "gemm3", "split",  "prep"};
+    return (k >= 0 && k < OP_COUNT) ? names[k] : "?";
+}
+
+namespace {
+
+bool kind_pair(int k) { return k == USTAT_RBF || k == USTAT_LINEAR || k == USTAT_MATRIX; }
+bool kind_unary(int k) { return k == USTAT_TANH_DOT || k == USTAT_VECTOR; }
+bool kind_symmetric(int k) { return k == USTAT_RBF || k == USTAT_LINEAR; }
+bool kind_unit_diag(int k) { return k == USTAT_RBF; }
+
+int popc(uint32_t x) { return __builtin_popcount(x); }
+
+void enum_partitions(int m, std::vector<std::vector<int>> &out) {
+    std::vector<int> a(m, 0);
+    // iterative restricted-growth-string enumeration in lexicographic order
+    std::function<void(int, int)> rec = [&](int i, int top) {
+        if (i == m) {
+            out.push_back(a);
+            return;
+        }
+        for (int b = 0; b <= top + 1; ++b) {
+            a[i] = b;
+            rec(i + 1, std::max(top, b));
+        }
+    };
+    if (m == 0) return;
+    a[0] = 0;
+    rec(1, 0);
+}
+
+int mu_of(const std::vector<int> &rgs) {
+    int k = *std::max_element(rgs.begin(), rgs.end()) + 1;
+    std::vector<int> size(k, 0);
+    for (int b : rgs) size[b]++;
+    long long v = 1;
+    for (int s : size)
+        for (int t = 2; t < s; ++t) v *= t;
+    int sign = ((int)rgs.size() - k) % 2 ? -1 : 1;
+    return (int)(sign * v);
+}
+
+uint32_t component(int v, uint32_t alive, const uint32_t *adj) {
+    uint32_t seen = 1u << v, frontier = 1u << v;
+    while (frontier) {
+        int u = __builtin_ctz(frontier);
+        frontier &= frontier - 1;
+        uint32_t nb = adj[u] & alive & ~seen;
+        seen |= nb;
+        frontier |= nb;
+    }
+    return seen;
+}
+
+// Cost of an elimination order as counts of steps per power of n (index p means
+// n^(p+1)); compared from the highest power down, then by stored intermediates.
+struct Cost {
+    int c[5] = {0, 0, 0, 0, 0};
+    int stores = 0;
+    bool ok = true;
+    bool operator<(const Cost &o) const {
+        if (ok != o.ok) return ok;
+        for (int p = 4; p >= 0; --p)
+            if (c[p] != o.c[p]) return c[p] < o.c[p];
+        return stores < o.stores;
+    }
+};
+
+// Structural simulation.  A step with s neighbours is executable when s <= 2, or
+// when s == 3 and the step ends its connected component (the n^3 intermediate is
+// then consumed inside the same kernel).  A step that ends its component
+// ("terminal") eliminates the whole component: the remaining 1..3 vertices are
+// summed in the fused reduction.
+Cost simulate(int k, const uint32_t *adj0, const int *order) {
+    uint32_t adj[32];
+    std::memcpy(adj, adj0, sizeof(uint32_t) * k);
+    uint32_t alive = (k == 32) ? 0xffffffffu : ((1u << k) - 1);
+    Cost c;
+    for (int t = 0; t < k; ++t) {
+        int v = order[t];
+        if (!((alive >> v) & 1)) continue;
+        uint32_t nb = adj[v] & alive & ~(1u << v);
+        int s = popc(nb);
+        uint32_t comp = component(v, alive, adj);
+        bool terminal = popc(comp) == s + 1;
+        if (s >= 4 || (s == 3 && !terminal)) {
+            c.ok = false;
+            return c;
+        }
+        c.c[s]++;
+        if (s == 2 && !terminal) c.stores++;
+        if (terminal) {
+            alive &= ~comp;
+        } else {
+            alive &= ~(1u << v);
+            for (uint32_t r = nb; r; r &= r - 1) {
+                int w = __builtin_ctz(r);
+                adj[w] |= nb & ~(1u << w);
+            }
+        }
+    }
+    return c;
+}
+
+std::vector<int> exhaustive_order(int k, const uint32_t *adj, Cost *best_cost) {
+    std::vector<int> perm(k), best;
+    for (int i = 0; i < k; ++i) perm[i] = i;
+    Cost bc;
+    bc.ok = false;
+    do {
+        Cost c = simulate(k, adj, perm.data());
+        if (best.empty() || c < bc) {
+            bc = c;
+            best = perm;
+        }
+    } while (std::next_permutation(perm.begin(), perm.end()));
+    *best_cost = bc;
+    return best;
+}
+
+std::vector<int> minfill_order(int k, const uint32_t *adj0) {
+    uint32_t adj[32];
+    std::memcpy(adj, adj0, sizeof(uint32_t) * k);
+    uint32_t alive = (1u << k) - 1;
+    std::vector<int> order;
+    while (alive) {
+        int best = -1, bf = 1 << 30, bd = 1 << 30;
+        for (uint32_t r = alive; r; r &= r - 1) {
+            int v = __builtin_ctz(r);
+            uint32_t nb = adj[v] & alive & ~(1u << v);
+            int fill = 0;
+            for (uint32_t q = nb; q; q &= q - 1) {
+                int w = __builtin_ctz(q);
+                fill += popc(nb & ~adj[w] & ~(1u << w));
+            }
+            fill /= 2;
+            int deg = popc(nb);
+            if (fill < bf || (fill == bf && deg < bd)) {
+                best = v;
+                bf = fill;
+                bd = deg;
+            }
+        }
+        uint32_t nb = adj[best] & alive & ~(1u << best);
+        for (uint32_t r = nb; r; r &= r - 1) {
+            int w = __builtin_ctz(r);
+            adj[w] |= nb & ~(1u << w);
+        }
+        alive &= ~(1u << best);
+        order.push_back(best);
+    }
+    return order;
+}
+
+// ---------------------------------------------------------------- lowering
+
+struct Lowerer {
+    Plan &P;
+    std::map<std::vector<long long>, int> memo;   // op signature -> out slot
+    explicit Lowerer(Plan &p) : P(p) {}
+
+    int new_slot(int kind, int sym = 0) {
+        Slot s;
+        s.kind = kind;
+        s.symmetric = sym;
+        P.slots.push_back(s);
+        return (int)P.slots.size() - 1;
+    }
+    bool sym(int mat) const { return mat >= 0 && P.slots[mat].symmetric; }
+    Term canon(Term t) const {
+        if (t.mat >= 0 && sym(t.mat)) t.trans = 0;
+        return t;
+    }
+    Term flip(Term t) const {
+        if (t.mat < 0) return t;
+        t.trans ^= 1;
+        return canon(t);
+    }
+
+    static void put_term(std::vector<long long> &k, Term t) {
+        k.push_back(t.mat);
+        k.push_back(t.trans);
+    }
+
+    std::vector<long long> key_of(const Op &o) const {
+        std::vector<long long> k = {o.kind, o.factor, o.nt};
+        for (int i = 0; i < o.nt; ++i) put_term(k, o.t[i]);
+        k.push_back(o.u);
+        k.push_back(o.a);
+        k.push_back(o.b);
+        put_term(k, o.A);
+        put_term(k, o.B);
+        put_term(k, o.W);
+        put_term(k, o.Ab);
+        put_term(k, o.Wbc);
+        put_term(k, o.Wbd);
+        k.push_back(o.ub);
+        return k;
+    }
+
+    int out_kind(int opk) const {
+        switch (opk) {
+            case OP_KBUILD: case OP_LOADMAT: case OP_HADAMARD: case OP_GEMM: return S_MAT;
+            case OP_UNARY: case OP_LOADVEC: case OP_DIAG: case OP_VMUL: case OP_GEMV: return S_VEC;
+            case OP_SPLIT: return S_SLICES;
+            case OP_PREP: return S_PREP;
+            default: return S_SCAL;
+        }
+    }
+
+    int emit(Op o, int symmetric_out = 0) {
+        auto key = key_of(o);
+        if (P.cse) {
+            auto it = memo.find(key);
+            if (it != memo.end()) return it->second;
+        }
+        o.out = new_slot(out_kind(o.kind), symmetric_out);
+        P.ops.push_back(o);
+        if (!memo.count(key)) {
+            memo[key] = o.out;
+            if (trial_log) trial_log->push_back(key);
+        }
+        return o.out;
+    }
+
+    // Trial lowering: everything emitted after begin_trial() is undone by rollback().
+    std::vector<std::vector<long long>> *trial_log = nullptr;
+    size_t trial_ops = 0, trial_slots = 0;
+    std::vector<std::vector<long long>> log_store;
+    void begin_trial() {
+        trial_ops = P.ops.size();
+        trial_slots = P.slots.size();
+        log_store.clear();
+        trial_log = &log_store;
+    }
+    void rollback() {
+        P.ops.resize(trial_ops);
+        P.slots.resize(trial_slots);
+        for (auto &k : log_store) memo.erase(k);
+        log_store.clear();
+        trial_log = nullptr;
+    }
+
+    int vmul(std::vector<int> v) {
+        std::sort(v.begin(), v.end());
+        if (v.empty()) return -1;
+        int acc = v[0];
+        for (size_t i = 1; i < v.size(); ++i) {
+            Op o;
+            o.kind = OP_VMUL;
+            o.u = std::min(acc, v[i]);
+            o.a = std::max(acc, v[i]);
+            acc = emit(o);
+        }
+        return acc;
+    }
+
+    Term hadamard(std::vector<Term> ts) {
+        for (auto &t : ts) t = canon(t);
+        std::sort(ts.begin(), ts.end());
+        if (ts.empty()) return Term{};
+        if (ts.size() == 1) return ts[0];
+        while (ts.size() > 1) {
+            Op o;
+            o.kind = OP_HADAMARD;
+            int take = std::min((int)ts.size(), kMaxTerms);
+            bool all_sym = true;
+            for (int i = 0; i < take; ++i) {
+                o.t[i] = ts[i];
+                all_sym = all_sym && sym(ts[i].mat);
+            }
+            o.nt = take;
+            o.coef = take - 1;
+            o.npow = 2;
+            int out = emit(o, all_sym ? 1 : 0);
+            std::vector<Term> rest(ts.begin() + take, ts.end());
+            rest.push_back(Term{out, 0});
+            std::sort(rest.begin(), rest.end());
+            ts = rest;
+        }
+        return ts[0];
+    }
+
+    // reduce a term list to at most kMaxTerms - reserve entries
+    std::vector<Term> fit(std::vector<Term> ts, int reserve = 0) {
+        for (auto &t : ts) t = canon(t);
+        std::sort(ts.begin(), ts.end());
+        int cap = kMaxTerms - reserve;
+        if ((int)ts.size() <= cap) return ts;
+        std::vector<Term> head(ts.begin(), ts.begin() + (ts.size() - cap + 1));
+        std::vector<Term> out(ts.begin() + (ts.size() - cap + 1), ts.end());
+        out.push_back(hadamard(head));
+        std::sort(out.begin(), out.end());
+        return out;
+    }
+};
+
+struct QState {
+    int k = 0;
+    std::vector<std::vector<int>> vecs;
+    std::map<std::pair<int, int>, std::vector<Term>> E;   // key p < q; terms value(i_p, i_q)
+    uint32_t adj[32] = {0};
+};
+
+}  // namespace
+
+int exact_treewidth(int k, const std::vector<uint32_t> &adj) {
+    if (k <= 1) return 0;
+    // TW(S) = min_{v in S} max(TW(S \ v), |Q(S \ v, v)|), Q(S, v) = vertices outside
+    // S + v reachable from v through S.
+    std::vector<int> tw(1u << k, 0);
+    for (uint32_t S = 1; S < (1u << k); ++S) {
+        int best = 1 << 20;
+        for (uint32_t r = S; r; r &= r - 1) {
+            int v = __builtin_ctz(r);
+            uint32_t Sv = S & ~(1u << v);
+            uint32_t seen = 1u << v, fr = 1u << v, q = 0;
+            while (fr) {
+                int u = __builtin_ctz(fr);
+                fr &= fr - 1;
+                uint32_t nb = adj[u] & ~seen;
+                seen |= nb;
+                q |= nb & ~Sv;
+                fr |= nb & Sv;
+            }
+            q &= ~(1u << v);
+            int val = std::max(tw[Sv], popc(q));
+            best = std::min(best, val);
+        }
+        tw[S] = best;
+    }
+    return tw[(1u << k) - 1];
+}
+
+int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan) {
+    if (!g || !o || !plan) return USTAT_ERR_INVALID_ARG;
+    const int m = g->m;
+    if (m < 1) return USTAT_ERR_INVALID_ARG;
+    if (m > kMaxM) return USTAT_ERR_UNSUPPORTED;
+    if (g->n_factors < 1 || !g->factor_kind) return USTAT_ERR_INVALID_ARG;
+    if (g->n_edges < 0 || g->n_unary < 0) return USTAT_ERR_INVALID_ARG;
+    if (g->n_edges > 0 && (!g->edge_src || !g->edge_dst || !g->edge_factor)) return USTAT_ERR_INVALID_ARG;
+    if (g->n_unary > 0 && (!g->unary_vertex || !g->unary_factor)) return USTAT_ERR_INVALID_ARG;
+    if (o->precision < USTAT_FP64 || o->precision > USTAT_BF16X3) return USTAT_ERR_INVALID_ARG;
+    if (o->planner != USTAT_PLAN_EXHAUSTIVE && o->planner != USTAT_PLAN_MINFILL) return USTAT_ERR_INVALID_ARG;
+    Plan &P = *plan;
+    P = Plan();
+    P.m = m;
+    P.precision = o->precision;
+    P.sparsify = o->sparsify ? 1 : 0;
+    P.planner = o->planner;
+    P.cse = o->cse ? 1 : 0;
+    P.factor_kind.assign(g->factor_kind, g->factor_kind + g->n_factors);
+    for (int f = 0; f < g->n_factors; ++f)
+        if (P.factor_kind[f] < USTAT_RBF || P.factor_kind[f] > USTAT_VECTOR) return USTAT_ERR_INVALID_ARG;
+    std::vector<int> covered(m, 0);
+    for (int e = 0; e < g->n_edges; ++e) {
+        int a = g->edge_src[e], b = g->edge_dst[e], f = g->edge_factor[e];
+        if (a < 0 || a >= m || b < 0 || b >= m || f < 0 || f >= g->n_factors) return USTAT_ERR_INVALID_ARG;
+        if (!kind_pair(P.factor_kind[f])) return USTAT_ERR_INVALID_ARG;
+        if (a == b) return USTAT_ERR_INVALID_ARG;   // a signature tuple (a, a): not a graph edge
+        covered[a] = covered[b] = 1;
+    }
+    for (int e = 0; e < g->n_unary; ++e) {
+        int v = g->unary_vertex[e], f = g->unary_factor[e];
+        if (v < 0 || v >= m || f < 0 || f >= g->n_factors) return USTAT_ERR_INVALID_ARG;
+        if (!kind_unary(P.factor_kind[f])) return USTAT_ERR_INVALID_ARG;
+        covered[v] = 1;
+    }
+    // Definition "Multiplicative Decomposition": the tuples cover [m]
+    for (int v = 0; v < m; ++v)
+        if (!covered[v]) return USTAT_ERR_INVALID_ARG;
+
+    Lowerer L(P);
+    const bool tc = (P.precision == USTAT_TF32 || P.precision == USTAT_BF16X3);
+
+    // base tensors (Algorithm 1): one per factor id, created lazily
+    std::vector<int> base(g->n_factors, -1), diag(g->n_factors, -1);
+    auto base_of = [&](int f) {
+        if (base[f] >= 0) return base[f];
+        Op op;
+        op.factor = f;
+        int k = P.factor_kind[f];
+        if (k == USTAT_RBF || k == USTAT_LINEAR) op.kind = OP_KBUILD;
+        else if (k == USTAT_MATRIX) op.kind = OP_LOADMAT;
+        else if (k == USTAT_TANH_DOT) op.kind = OP_UNARY;
+        else op.kind = OP_LOADVEC;
+        op.npow = 2;
+        op.coef = 0;
+        base[f] = L.emit(op, kind_symmetric(k) ? 1 : 0);
+        return base[f];
+    };
+    auto diag_of = [&](int f) {
+        if (diag[f] >= 0) return diag[f];
+        Op op;
+        op.kind = OP_DIAG;
+        op.t[0] = Term{base_of(f), 0};
+        op.nt = 1;
+        diag[f] = L.emit(op);
+        return diag[f];
+    };
+
+    std::vector<std::vector<int>> parts;
+    enum_partitions(m, parts);
+    std::set<std::tuple<int, int, int, int, int>> products;   // n^3 products in the program
+    for (auto &rgs : parts) {
+        PartRec pr;
+        for (int i = 0; i < m; ++i) pr.rgs[i] = rgs[i];
+        int k = *std::max_element(rgs.begin(), rgs.end()) + 1;
+        pr.nblocks = k;
+        pr.mu = mu_of(rgs);
+        // exact treewidth of the simple quotient graph
+        std::vector<uint32_t> qadj(k, 0);
+        for (int e = 0; e < g->n_edges; ++e) {
+            int p = rgs[g->edge_src[e]], q = rgs[g->edge_dst[e]];
+            if (p != q) {
+                qadj[p] |= 1u << q;
+                qadj[q] |= 1u << p;
+            }
+        }
+        pr.tw = exact_treewidth(k, qadj);
+        // sparsification filter: no block holds both ends of a pairwise factor
+        if (P.sparsify) {
+            bool surv = true;
+            for (int e = 0; e < g->n_edges; ++e)
+                if (rgs[g->edge_src[e]] == rgs[g->edge_dst[e]]) surv = false;
+            if (!surv) {
+                pr.evaluated = 0;
+                P.parts.push_back(pr);
+                continue;
+            }
+        }
+        // quotient factor multigraph
+        QState Q;
+        Q.k = k;
+        Q.vecs.assign(k, {});
+        for (int e = 0; e < g->n_edges; ++e) {
+            int a = g->edge_src[e], b = g->edge_dst[e], f = g->edge_factor[e];
+            int p = rgs[a], q = rgs[b];
+            if (p == q) {
+                // intra-block pairwise factor: F(x_i, x_i) (Definition "Restricted
+                // V-Statistic"); an RBF factor has F(x, x) = 1 and drops out
+                if (!kind_unit_diag(P.factor_kind[f])) Q.vecs[p].push_back(diag_of(f));
+                continue;
+            }
+            Term t{base_of(f), 0};
+            if (p > q) {
+                std::swap(p, q);
+                t = L.flip(t);
+            }
+            Q.E[{p, q}].push_back(L.canon(t));
+            Q.adj[p] |= 1u << q;
+            Q.adj[q] |= 1u << p;
+        }
+        for (int e = 0; e < g->n_unary; ++e) Q.vecs[rgs[g->unary_vertex[e]]].push_back(base_of(g->unary_factor[e]));
+
+        // lower the partition along an order (Q is taken by value)
+        auto lower = [&](QState Q, const std::vector<int> &order, PartRec &pr) -> int {
+        auto oriented = [&](int p, int q) {
+            std::vector<Term> ts;
+            if (p < q) {
+                auto it = Q.E.find({p, q});
+                if (it != Q.E.end()) ts = it->second;
+            } else {
+                auto it = Q.E.find({q, p});
+                if (it != Q.E.end())
+                    for (auto t : it->second) ts.push_back(L.flip(t));
+            }
+            return ts;
+        };
+        auto add_scal = [&](int s) -> int {
+            if (pr.nscal >= kMaxScal) return USTAT_ERR_UNSUPPORTED;
+            pr.scal[pr.nscal++] = s;
+            return USTAT_OK;
+        };
+        uint32_t alive = (1u << k) - 1;
+        for (int v : order) {
+            if (!((alive >> v) & 1)) continue;
+            uint32_t nb = Q.adj[v] & alive & ~(1u << v);
+            int s = popc(nb);
+            uint32_t comp = component(v, alive, Q.adj);
+            bool terminal = popc(comp) == s + 1;
+            std::vector<int> nbs;
+            for (uint32_t r = nb; r; r &= r - 1) nbs.push_back(__builtin_ctz(r));
+            int rc = USTAT_OK;
+            if (s == 0) {
+                int u = L.vmul(Q.vecs[v]);
+                if (u < 0) {
+                    pr.nfree++;
+                } else {
+                    Op op;
+                    op.kind = OP_VSUM;
+                    op.u = u;
+                    op.coef = 1;
+                    op.npow = 1;
+                    rc = add_scal(L.emit(op));
+                }
+            } else if (s == 1) {
+                int w = nbs[0];
+                if (terminal) {
+                    Op op;
+                    op.kind = OP_FREDUCE;
+                    auto ts = L.fit(oriented(v, w));
+                    for (size_t i = 0; i < ts.size(); ++i) op.t[i] = ts[i];
+                    op.nt = (int)ts.size();
+                    op.a = L.vmul(Q.vecs[v]);
+                    op.b = L.vmul(Q.vecs[w]);
+                    op.coef = 2;
+                    op.npow = 2;
+                    rc = add_scal(L.emit(op));
+                } else {
+                    Op op;
+                    op.kind = OP_GEMV;
+                    auto ts = L.fit(oriented(v, w));
+                    for (size_t i = 0; i < ts.size(); ++i) op.t[i] = ts[i];
+                    op.nt = (int)ts.size();
+                    op.u = L.vmul(Q.vecs[v]);
+                    op.coef = 2;
+                    op.npow = 2;
+                    Q.vecs[w].push_back(L.emit(op));
+                }
+            } else if (s == 2) {
+                int w = nbs[0], x = nbs[1];
+                Term A = L.hadamard(oriented(v, w));
+                Term B = L.hadamard(oriented(v, x));
+                int u = L.vmul(Q.vecs[v]);
+                if (terminal) {
+                    Op op;
+                    op.kind = OP_GEMM_RED;
+                    op.A = A;
+                    op.B = B;
+                    op.u = u;
+                    op.W = L.hadamard(oriented(w, x));
+                    op.a = L.vmul(Q.vecs[w]);
+                    op.b = L.vmul(Q.vecs[x]);
+                    // canonical operand order: (A,B,W,a,b) ~ (B,A,W^T,b,a)
+                    if (B < A) {
+                        std::swap(op.A, op.B);
+                        op.W = L.flip(op.W);
+                        std::swap(op.a, op.b);
+                    }
+                    op.coef = 2;
+                    op.npow = 3;
+                    rc = add_scal(L.emit(op));
+                } else {
+                    Op op;
+                    op.kind = OP_GEMM;
+                    op.A = A;
+                    op.B = B;
+                    op.u = u;
+                    bool swapped = false;
+                    if (B < A) {
+                        std::swap(op.A, op.B);
+                        swapped = true;
+                    }
+                    op.coef = 2;
+                    op.npow = 3;
+                    int out = L.emit(op, (op.A == op.B) ? 1 : 0);
+                    Term T{out, swapped ? 1 : 0};
+                    T = L.canon(T);   // T(i_w, i_x) with w < x
+                    Q.E[{w, x}].push_back(T);
+                    Q.adj[w] |= 1u << x;
+                    Q.adj[x] |= 1u << w;
+                }
+            } else if (s == 3) {
+                int b = nbs[0], cc = nbs[1], d = nbs[2];
+                Op op;
+                op.kind = OP_GEMM3;
+                op.Ab = L.hadamard(oriented(v, b));
+                op.A = L.hadamard(oriented(v, cc));
+                op.B = L.hadamard(oriented(v, d));
+                op.u = L.vmul(Q.vecs[v]);
+                op.Wbc = L.hadamard(oriented(b, cc));
+                op.Wbd = L.hadamard(oriented(b, d));
+                op.W = L.hadamard(oriented(cc, d));
+                op.ub = L.vmul(Q.vecs[b]);
+                op.a = L.vmul(Q.vecs[cc]);
+                op.b = L.vmul(Q.vecs[d]);
+                op.coef = 2;
+                op.npow = 4;
+                rc = add_scal(L.emit(op));
+            } else {
+                return USTAT_ERR_TW_TOO_LARGE;
+            }
+            if (rc != USTAT_OK) return rc;
+            if (terminal) {
+                alive &= ~comp;
+            } else {
+                alive &= ~(1u << v);
+                for (int w : nbs) Q.adj[w] &= ~(1u << v);
+            }
+            // edges incident to v are consumed
+            for (auto it = Q.E.begin(); it != Q.E.end();) {
+                if (it->first.first == v || it->first.second == v) it = Q.E.erase(it);
+                else ++it;
+            }
+        }
+        return USTAT_OK;
+        };
+
+        // elimination order
+        std::vector<int> order;
+        Cost c;
+        if (P.planner == USTAT_PLAN_MINFILL) {
+            order = minfill_order(k, Q.adj);
+            c = simulate(k, Q.adj, order.data());
+            if (!c.ok) order = exhaustive_order(k, Q.adj, &c);
+        } else if (!P.cse) {
+            order = exhaustive_order(k, Q.adj, &c);
+        } else {
+            // Sharing-aware exhaustive search: every distinct feasible elimination
+            // sequence is lowered on trial against the program built so far and
+            // rolled back; the winner adds the fewest new n^4 steps, then the
+            // fewest new n^3 products (a product already in the program costs an
+            // n^2 pass), then the fewest new operations.
+            std::vector<int> perm(k);
+            for (int i = 0; i < k; ++i) perm[i] = i;
+            std::set<std::vector<int>> seen;
+            std::tuple<int, int, int, int> best_cost{1 << 30, 1 << 30, 1 << 30, 1 << 30};
+            do {
+                Cost cc = simulate(k, Q.adj, perm.data());
+                if (!cc.ok) continue;
+                // effective sequence: vertices at which a step happens
+                std::vector<int> eff;
+                {
+                    uint32_t adj2[32];
+                    std::memcpy(adj2, Q.adj, sizeof(uint32_t) * k);
+                    uint32_t al = (1u << k) - 1;
+                    for (int v : perm) {
+                        if (!((al >> v) & 1)) continue;
+                        eff.push_back(v);
+                        uint32_t nb = adj2[v] & al & ~(1u << v);
+                        uint32_t comp = component(v, al, adj2);
+                        if (popc(comp) == popc(nb) + 1) {
+                            al &= ~comp;
+                        } else {
+                            al &= ~(1u << v);
+                            for (uint32_t r = nb; r; r &= r - 1) adj2[__builtin_ctz(r)] |= nb & ~(1u << __builtin_ctz(r));
+                        }
+                    }
+                }
+                if (!seen.insert(eff).second) continue;
+                PartRec tr = pr;
+                L.begin_trial();
+                const size_t first = P.ops.size();
+                int rc = lower(Q, perm, tr);
+                int n4 = 0, n3 = 0, nother = 0;
+                std::set<std::tuple<int, int, int, int, int>> fresh;
+                for (size_t i = first; i < P.ops.size(); ++i) {
+                    const Op &op = P.ops[i];
+                    if (op.kind == OP_GEMM3) ++n4;
+                    else if (op.kind == OP_GEMM || op.kind == OP_GEMM_RED) {
+                        auto key = std::make_tuple(op.A.mat, op.A.trans, op.B.mat, op.B.trans, op.u);
+                        if (!products.count(key) && fresh.insert(key).second) ++n3;
+                        else ++nother;
+                    } else ++nother;
+                }
+                L.rollback();
+                if (rc != USTAT_OK) continue;
+                auto tc = std::make_tuple(n4, n3, cc.c[1] + cc.c[0], nother);
+                if (order.empty() || tc < best_cost) {
+                    best_cost = tc;
+                    order = perm;
+                    c = cc;
+                }
+            } while (std::next_permutation(perm.begin(), perm.end()));
+            if (order.empty()) c.ok = false;
+        }
+        if (!c.ok) return USTAT_ERR_TW_TOO_LARGE;
+        pr.naive_coef[0] = c.c[0];
+        for (int p = 1; p < 5; ++p) pr.naive_coef[p] = 2.0 * c.c[p];
+        {
+            const size_t first = P.ops.size();
+            int rc = lower(Q, order, pr);
+            if (rc != USTAT_OK) return rc;
+            for (size_t i = first; i < P.ops.size(); ++i) {
+                const Op &op = P.ops[i];
+                if (op.kind == OP_GEMM || op.kind == OP_GEMM_RED)
+                    products.insert(std::make_tuple(op.A.mat, op.A.trans, op.B.mat, op.B.trans, op.u));
+            }
+        }
+        P.parts.push_back(pr);
+    }
+
+    // ---- share n^3 products across partitions
+    if (P.cse) {
+        using Key = std::tuple<int, int, int, int, int>;
+        auto pkey = [](const Op &op) { return Key(op.A.mat, op.A.trans, op.B.mat, op.B.trans, op.u); };
+        std::map<Key, int> first_use, store_idx;
+        std::map<Key, int> red_count;
+        for (int i = 0; i < (int)P.ops.size(); ++i) {
+            const Op &op = P.ops[i];
+            if (op.kind != OP_GEMM && op.kind != OP_GEMM_RED) continue;
+            Key kk = pkey(op);
+            if (!first_use.count(kk)) first_use[kk] = i;
+            if (op.kind == OP_GEMM) store_idx[kk] = i;
+            else red_count[kk]++;
+        }
+        std::map<Key, int> stored_slot;
+        std::vector<Op> out;
+        for (int i = 0; i < (int)P.ops.size(); ++i) {
+            Op op = P.ops[i];
+            if (op.kind == OP_GEMM || op.kind == OP_GEMM_RED) {
+                Key kk = pkey(op);
+                bool shared = store_idx.count(kk) || red_count[kk] >= 2;
+                if (shared && first_use[kk] == i) {
+                    // the stored product goes where it is first needed
+                    if (store_idx.count(kk)) {
+                        Op st = P.ops[store_idx[kk]];
+                        out.push_back(st);
+                        stored_slot[kk] = st.out;
+                    } else {
+                        Op st = op;
+                        st.kind = OP_GEMM;
+                        st.W = Term{};
+                        st.a = st.b = -1;
+                        Slot sl;
+                        sl.kind = S_MAT;
+                        sl.symmetric = (st.A == st.B) ? 1 : 0;
+                        P.slots.push_back(sl);
+                        st.out = (int)P.slots.size() - 1;
+                        out.push_back(st);
+                        stored_slot[kk] = st.out;
+                    }
+                }
+                if (op.kind == OP_GEMM) {
+                    if (shared) continue;   // already placed
+                    out.push_back(op);
+                    continue;
+                }
+                if (shared) {
+                    Op fr;
+                    fr.kind = OP_FREDUCE;
+                    fr.out = op.out;
+                    fr.t[0] = Term{stored_slot[kk], 0};
+                    fr.nt = 1;
+                    if (op.W.mat >= 0) fr.t[fr.nt++] = op.W;
+                    fr.a = op.a;
+                    fr.b = op.b;
+                    fr.coef = 2;
+                    fr.npow = 2;
+                    out.push_back(fr);
+                    continue;
+                }
+            }
+            out.push_back(op);
+        }
+        P.ops.swap(out);
+    }
+
+    // ---- operands for the tensor-core GEMMs: K-major copies with the diagonal
+    //      scaling of the contracted index folded into A
+    if (tc) {
+        std::vector<Op> out;
+        std::map<std::tuple<int, int, int>, int> opmemo;
+        auto operand = [&](Term t, int u, std::vector<Op> &dst) {
+            auto key = std::make_tuple(t.mat, t.trans, u);
+            auto it = opmemo.find(key);
+            if (it != opmemo.end()) return it->second;
+            Op op;
+            op.kind = (P.precision == USTAT_BF16X3) ? OP_SPLIT : OP_PREP;
+            op.t[0] = t;
+            op.nt = 1;
+            op.u = u;
+            op.npow = 2;
+            Slot sl;
+            sl.kind = (P.precision == USTAT_BF16X3) ? S_SLICES : S_PREP;
+            P.slots.push_back(sl);
+            op.out = (int)P.slots.size() - 1;
+            dst.push_back(op);
+            opmemo[key] = op.out;
+            return op.out;
+        };
+        for (auto op : P.ops) {
+            if (op.kind == OP_GEMM || op.kind == OP_GEMM_RED) {
+                op.opA = operand(op.A, op.u, out);
+                op.opB = operand(op.B, -1, out);
+            }
+            out.push_back(op);
+        }
+        P.ops.swap(out);
+    }
+    for (auto &op : P.ops) {
+        if (op.kind == OP_GEMM || op.kind == OP_GEMM_RED) P.n_gemm++;
+        if (op.kind == OP_GEMM3) P.n_gemm3++;
+    }
+    return USTAT_OK;
+}
+
+}  // namespace ustat

@@ -1,0 +1,107 @@
+// Internal types shared by the planner (host) and the executor.  Not part of the ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ustat.h"
+
+namespace ustat {
+
+constexpr int kMaxM = 7;        // Bell(7) = 877 partitions
+constexpr int kMaxTerms = 4;    // matrix terms read by one elementwise / reduce op
+constexpr int kMaxScal = 6;     // scalar slots multiplied into one V_pi
+
+// One factor matrix read with an orientation: value(i, j) = M[i][j] (trans = 0)
+// or M[j][i] (trans = 1).
+struct Term {
+    int mat = -1;
+    int trans = 0;
+    bool operator==(const Term &o) const { return mat == o.mat && trans == o.trans; }
+    bool operator<(const Term &o) const { return mat != o.mat ? mat < o.mat : trans < o.trans; }
+};
+
+enum OpKind : int {
+    OP_KBUILD = 0,   // mat out = kernel map of factor f on X (RBF / LINEAR)
+    OP_LOADMAT,      // mat out = caller matrix of factor f (converted to the working type)
+    OP_UNARY,        // vec out = tanh(X w) of factor f
+    OP_LOADVEC,      // vec out = caller vector of factor f
+    OP_DIAG,         // vec out(i) = M(i, i) of t[0]
+    OP_VMUL,         // vec out = u[0] * u[1] (elementwise)
+    OP_HADAMARD,     // mat out(i, j) = prod_t t[t](i, j)
+    OP_GEMV,         // vec out(j) = sum_i u(i) prod_t t[t](i, j)
+    OP_VSUM,         // scal out += sum_i u(i)
+    OP_GEMM,         // mat out(j, k) = sum_i A(i, j) u(i) B(i, k)
+    OP_GEMM_RED,     // scal out += sum_jk [sum_i A(i,j) u(i) B(i,k)] W(j,k) a(j) b(k)
+    OP_FREDUCE,      // scal out += sum_jk prod_t t[t](j, k) a(j) b(k)
+    OP_GEMM3,        // scal out += sum_b ub(b) sum_cd [sum_a u(a) Ab(a,b) A(a,c) B(a,d)]
+                     //             W(c,d) Wbc(b,c) Wbd(b,d) a(c) b(d)
+    OP_SPLIT,        // operand out = bf16x3 fixed-point slices of the K-major operand
+                     //   X(j, i) = t[0](i, j) u(i)
+    OP_PREP,         // operand out = fp32 K-major copy X(j, i) = t[0](i, j) u(i) (tf32-rounded)
+    OP_COUNT
+};
+
+const char *op_name(int kind);
+
+struct Op {
+    int kind = 0;
+    int factor = -1;
+    int out = -1;                 // slot written
+    Term t[kMaxTerms];
+    int nt = 0;
+    int u = -1, a = -1, b = -1;   // vector slots (-1 = all ones)
+    Term A, B, W;                 // GEMM operands / weight (W.mat = -1 = all ones)
+    int opA = -1, opB = -1;       // operand slots for tensor-core GEMMs (SPLIT / PREP outputs)
+    // GEMM3 only
+    Term Ab, Wbc, Wbd;
+    int ub = -1;
+    double flops = 0.0;           // algorithmic flops per unit n-power (set by the planner)
+    int npow = 0;                 // flops = coef * n^npow
+    double coef = 0.0;
+};
+
+enum SlotKind : int { S_MAT = 0, S_VEC, S_SCAL, S_SLICES, S_PREP };
+
+struct Slot {
+    int kind = S_MAT;
+    int symmetric = 0;            // matrices only
+};
+
+struct PartRec {
+    int rgs[kMaxM];
+    int nblocks = 0;
+    int mu = 0;
+    int tw = -1;                  // exact treewidth of G/pi (simple quotient graph)
+    int evaluated = 1;            // 0: skipped by sparsification (V = 0)
+    int nfree = 0;                // blocks with no factor at all: factor n each
+    int nscal = 0;
+    int scal[kMaxScal];
+    double naive_coef[5] = {0, 0, 0, 0, 0};   // own elimination cost: sum coef * n^p
+};
+
+struct Plan {
+    int m = 0;
+    int precision = USTAT_FP64;
+    int sparsify = 0;
+    int planner = USTAT_PLAN_EXHAUSTIVE;
+    int cse = 1;
+    std::vector<int> factor_kind;   // per factor id
+    std::vector<Slot> slots;
+    std::vector<Op> ops;
+    std::vector<PartRec> parts;
+    int n_gemm = 0, n_gemm3 = 0;
+};
+
+// Planner entry (planner.cpp).  Returns a USTAT_* code.
+int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan);
+
+// Exact treewidth of a simple graph on k <= 16 vertices given as adjacency bitmasks.
+int exact_treewidth(int k, const std::vector<uint32_t> &adj);
+
+}  // namespace ustat
+
+struct ustat_plan {
+    ustat::Plan p;
+};

@@ -1,0 +1,86 @@
+"""Torch-facing convenience layer over the C ABI: device buffers come from torch,
+the stream is torch's current stream, and every computation runs in libustat.so.
+
+    eng = Engine(graph, factors, precision="bf16x3")
+    out = eng.evaluate(X)          # X: torch tensor on the GPU or a numpy array
+    out["U_sum"], out["U_mean"], out["V"]
+
+``factors`` is a list of objects with ``kind``, ``param`` and ``data`` (the
+TANH_DOT weight vector, the MATRIX / VECTOR values as arrays); their data is
+copied to the device once per sample size.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import ustat as us
+
+
+class Engine:
+    def __init__(self, graph, factors, precision="bf16x3", sparsify=False, planner=us.PLAN_EXHAUSTIVE, cse=True,
+                 device="cuda:0"):
+        self.graph = graph
+        self.factors = list(factors)
+        self.device = torch.device(device)
+        self.plan = us.Plan(graph, [f.kind for f in self.factors], precision=precision, sparsify=sparsify,
+                            planner=planner, cse=cse)
+        self.n_parts = self.plan.info["n_parts"]
+        self._ws = None
+        self._fdev = {}
+
+    # device copies of factor data, keyed by n (MATRIX / VECTOR data depend on n)
+    def factor_tuples(self, n):
+        out = []
+        keep = []
+        for f in self.factors:
+            ptr = 0
+            if f.data is not None:
+                key = (id(f), n)
+                t = self._fdev.get(key)
+                if t is None:
+                    t = torch.as_tensor(np.ascontiguousarray(f.data, dtype=np.float64), device=self.device)
+                    self._fdev[key] = t
+                keep.append(t)
+                ptr = t.data_ptr()
+            out.append((f.kind, f.param, ptr))
+        return out
+
+    def workspace(self, nbytes):
+        if self._ws is None or self._ws.numel() < nbytes:
+            self._ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+        return self._ws
+
+    def to_device(self, X):
+        if isinstance(X, torch.Tensor):
+            X = X.to(self.device)
+        else:
+            X = torch.as_tensor(np.ascontiguousarray(X), device=self.device)
+        if X.dtype not in (torch.float64, torch.float32):
+            X = X.to(torch.float64)
+        return X.contiguous()
+
+    def launch(self, X, out, stream=None):
+        """Enqueue one evaluation; ``out`` is a float64 device tensor of 2 + n_parts."""
+        n, d = X.shape
+        ws = self.workspace(self.plan.workspace_bytes(n, d))
+        st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        us.ustat_eval(self.plan, X.data_ptr(), 0 if X.dtype == torch.float64 else 1, n, d, self.factor_tuples(n),
+                      ws.data_ptr(), ws.numel(), st, out.data_ptr(), out.data_ptr() + 16)
+
+    def evaluate(self, X):
+        X = self.to_device(X)
+        out = torch.empty(2 + self.n_parts, dtype=torch.float64, device=self.device)
+        self.launch(X, out)
+        o = out.cpu().numpy()
+        return {"U_sum": float(o[0]), "U_mean": float(o[1]), "V": o[2:].copy()}
+
+    def evaluate_host(self, X_host_pinned, U_host, V_host):
+        """End-to-end call with host input and outputs (ustat_eval_host):
+        X_host_pinned is a pinned torch CPU tensor, U_host / V_host ctypes arrays."""
+        n, d = X_host_pinned.shape
+        need = self.plan.workspace_bytes(n, d) + self.plan.host_staging_bytes(n, d)
+        ws = self.workspace(need)
+        st = torch.cuda.current_stream(self.device).cuda_stream
+        us.ustat_eval_host(self.plan, X_host_pinned.data_ptr(), 0 if X_host_pinned.dtype == torch.float64 else 1,
+                           n, d, self.factor_tuples(n), ws.data_ptr(), ws.numel(), st, U_host, V_host)

@@ -1,0 +1,236 @@
+"""Thin ctypes binding of the C ABI in include/ustat.h (argument marshalling only).
+
+Every computation runs inside libustat.so; this module only converts Python
+objects to the C structs and pointers, and torch tensors to device addresses.
+Importing it loads the library; if the library is missing it raises, it never
+falls back to another implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libustat.so")
+
+# status codes / kinds / modes (mirrors include/ustat.h)
+USTAT_OK = 0
+USTAT_ERR_INVALID_ARG = -1
+USTAT_ERR_N_LT_M = -2
+USTAT_ERR_TW_TOO_LARGE = -3
+USTAT_ERR_WORKSPACE = -4
+USTAT_ERR_NONFINITE = -5
+USTAT_ERR_CUDA = -6
+USTAT_ERR_DEVICE_TIMEOUT = -7
+USTAT_ERR_UNSUPPORTED = -8
+
+RBF, LINEAR, TANH_DOT, MATRIX, VECTOR = 0, 1, 2, 3, 4
+FP64, FP32, TF32, BF16X3 = 0, 1, 2, 3
+PLAN_EXHAUSTIVE, PLAN_MINFILL = 0, 1
+PRECISION = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16x3": BF16X3}
+
+_P = ctypes.POINTER
+_i = ctypes.c_int
+_i64 = ctypes.c_int64
+_vp = ctypes.c_void_p
+_sz = ctypes.c_size_t
+_d = ctypes.c_double
+
+
+class ustat_graph(ctypes.Structure):
+    _fields_ = [("m", _i), ("n_edges", _i), ("edge_src", _P(_i)), ("edge_dst", _P(_i)),
+                ("edge_factor", _P(_i)), ("n_unary", _i), ("unary_vertex", _P(_i)),
+                ("unary_factor", _P(_i)), ("n_factors", _i), ("factor_kind", _P(_i))]
+
+
+class ustat_options(ctypes.Structure):
+    _fields_ = [("precision", _i), ("sparsify", _i), ("planner", _i), ("cse", _i)]
+
+
+class ustat_factor(ctypes.Structure):
+    _fields_ = [("kind", _i), ("param", _d), ("data", _vp)]
+
+
+EXPORTS = {
+    "ustat_plan": (_i, [_P(ustat_graph), _P(ustat_options), _P(_vp)]),
+    "ustat_plan_destroy": (None, [_vp]),
+    "ustat_plan_info": (_i, [_vp, _P(_i), _P(_i), _P(_i), _P(_i), _P(_i), _P(_i), _P(_i), _P(_i)]),
+    "ustat_plan_flops": (_i, [_vp, _i64, _P(_d), _P(_d)]),
+    "ustat_plan_describe": (_i, [_vp, ctypes.c_char_p, _sz, _P(_sz)]),
+    "ustat_workspace_bytes": (_i, [_vp, _i64, _i, _P(_sz)]),
+    "ustat_eval": (_i, [_vp, _vp, _i, _i64, _i, _P(ustat_factor), _i, _vp, _sz, _vp, _vp, _vp]),
+    "ustat_host_staging_bytes": (_i, [_vp, _i64, _i, _P(_sz)]),
+    "ustat_eval_host": (_i, [_vp, _vp, _i, _i64, _i, _P(ustat_factor), _i, _vp, _sz, _vp, _P(_d), _P(_d)]),
+    "ustat_eval_batch": (_i, [_vp, _P(_vp), _i, _P(_i64), _i, _i, _P(ustat_factor), _i, _vp, _sz, _vp,
+                              _vp, _vp]),
+    "ustat_batch_workspace_bytes": (_i, [_vp, _P(_i64), _i, _i, _P(_sz)]),
+    "ustat_profile_enable": (_i, [_i]),
+    "ustat_profile_kinds": (_i, []),
+    "ustat_profile_kind_name": (ctypes.c_char_p, [_i]),
+    "ustat_profile_collect": (_i, [_P(_d), _P(_i)]),
+    "ustat_last_cuda_error": (ctypes.c_char_p, []),
+    "ustat_strerror": (ctypes.c_char_p, [_i]),
+    "ustat_version": (ctypes.c_char_p, []),
+}
+
+
+def load(path: str = LIB_PATH):
+    if not os.path.exists(path):
+        raise RuntimeError("libustat.so is not built (%s); run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = load()
+    return _lib
+
+
+class UstatError(RuntimeError):
+    def __init__(self, code, where):
+        msg = lib().ustat_strerror(code).decode()
+        if code == USTAT_ERR_CUDA:
+            msg += ": " + lib().ustat_last_cuda_error().decode()
+        super().__init__("%s failed: %s (%d)" % (where, msg, code))
+        self.code = code
+
+
+def _check(rc, where):
+    if rc != USTAT_OK:
+        raise UstatError(rc, where)
+
+
+def _iarr(vals):
+    vals = list(vals)
+    return (_i * max(1, len(vals)))(*vals)
+
+
+class Plan:
+    """Owns a ustat_plan_t.  ``graph`` has ``m``, ``edges`` [(a, b, f)], ``unary``
+    [(v, f)]; ``factor_kinds`` lists the kind of every factor id."""
+
+    def __init__(self, graph, factor_kinds, precision="bf16x3", sparsify=False, planner=PLAN_EXHAUSTIVE,
+                 cse=True):
+        self._keep = [
+            _iarr(e[0] for e in graph.edges), _iarr(e[1] for e in graph.edges), _iarr(e[2] for e in graph.edges),
+            _iarr(u[0] for u in graph.unary), _iarr(u[1] for u in graph.unary), _iarr(factor_kinds)]
+        g = ustat_graph(graph.m, len(graph.edges), self._keep[0], self._keep[1], self._keep[2],
+                        len(graph.unary), self._keep[3], self._keep[4], len(factor_kinds), self._keep[5])
+        prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        o = ustat_options(prec, int(bool(sparsify)), int(planner), int(bool(cse)))
+        h = _vp()
+        _check(lib().ustat_plan(ctypes.byref(g), ctypes.byref(o), ctypes.byref(h)), "ustat_plan")
+        self.handle = h
+        self.m = graph.m
+        self.factor_kinds = list(factor_kinds)
+        self.precision = prec
+        self.info = self._info()
+
+    def _info(self):
+        L = lib()
+        nparts = _i()
+        _check(L.ustat_plan_info(self.handle, ctypes.byref(nparts), None, None, None, None, None, None, None),
+               "ustat_plan_info")
+        k = nparts.value
+        mu, tw, ev = (_i * k)(), (_i * k)(), (_i * k)()
+        rgs = (_i * (k * self.m))()
+        nops, ng, ng3 = _i(), _i(), _i()
+        _check(L.ustat_plan_info(self.handle, ctypes.byref(nparts), mu, tw, rgs, ev, ctypes.byref(nops),
+                                 ctypes.byref(ng), ctypes.byref(ng3)), "ustat_plan_info")
+        return {"n_parts": k, "mu": list(mu), "tw": list(tw), "evaluated": list(ev),
+                "rgs": [tuple(rgs[i * self.m:(i + 1) * self.m]) for i in range(k)],
+                "n_ops": nops.value, "n_gemm": ng.value, "n_gemm3": ng3.value}
+
+    def flops(self, n):
+        a, b = _d(), _d()
+        _check(lib().ustat_plan_flops(self.handle, int(n), ctypes.byref(a), ctypes.byref(b)), "ustat_plan_flops")
+        return a.value, b.value
+
+    def describe(self):
+        need = _sz()
+        _check(lib().ustat_plan_describe(self.handle, None, 0, ctypes.byref(need)), "ustat_plan_describe")
+        buf = ctypes.create_string_buffer(need.value)
+        _check(lib().ustat_plan_describe(self.handle, buf, need.value, None), "ustat_plan_describe")
+        return buf.value.decode()
+
+    def workspace_bytes(self, n, d):
+        s = _sz()
+        _check(lib().ustat_workspace_bytes(self.handle, int(n), int(d), ctypes.byref(s)), "ustat_workspace_bytes")
+        return s.value
+
+    def host_staging_bytes(self, n, d):
+        s = _sz()
+        _check(lib().ustat_host_staging_bytes(self.handle, int(n), int(d), ctypes.byref(s)),
+               "ustat_host_staging_bytes")
+        return s.value
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.ustat_plan_destroy(h)
+            self.handle = None
+
+
+def factor_array(factors):
+    """factors: list of (kind, param, device_pointer_or_0)."""
+    arr = (ustat_factor * len(factors))()
+    for i, (k, p, ptr) in enumerate(factors):
+        arr[i].kind = int(k)
+        arr[i].param = float(p)
+        arr[i].data = int(ptr) if ptr else None
+    return arr
+
+
+def ustat_eval(plan, X_ptr, x_dtype, n, d, factors, ws_ptr, ws_bytes, stream, U_ptr, V_ptr):
+    fa = factor_array(factors)
+    rc = lib().ustat_eval(plan.handle, X_ptr, x_dtype, n, d, fa, len(factors), ws_ptr, ws_bytes, stream,
+                          U_ptr, V_ptr)
+    _check(rc, "ustat_eval")
+
+
+def ustat_eval_host(plan, X_host_ptr, x_dtype, n, d, factors, ws_ptr, ws_bytes, stream, U_host, V_host):
+    fa = factor_array(factors)
+    rc = lib().ustat_eval_host(plan.handle, X_host_ptr, x_dtype, n, d, fa, len(factors), ws_ptr, ws_bytes,
+                               stream, U_host, V_host)
+    _check(rc, "ustat_eval_host")
+
+
+def ustat_eval_batch(plan, X_ptrs, x_dtype, ns, d, factors, ws_ptr, ws_bytes, stream, U_ptr, V_ptr):
+    fa = factor_array(factors)
+    xp = (_vp * len(X_ptrs))(*X_ptrs)
+    na = (_i64 * len(ns))(*ns)
+    rc = lib().ustat_eval_batch(plan.handle, xp, x_dtype, na, len(ns), d, fa, len(factors), ws_ptr, ws_bytes,
+                                stream, U_ptr, V_ptr)
+    _check(rc, "ustat_eval_batch")
+
+
+def batch_workspace_bytes(plan, ns, d):
+    s = _sz()
+    na = (_i64 * len(ns))(*ns)
+    _check(lib().ustat_batch_workspace_bytes(plan.handle, na, len(ns), d, ctypes.byref(s)),
+           "ustat_batch_workspace_bytes")
+    return s.value
+
+
+def profile_enable(on: bool):
+    _check(lib().ustat_profile_enable(int(bool(on))), "ustat_profile_enable")
+
+
+def profile_collect():
+    """Returns {kind_name: (total_ms, launches)} for the operations recorded since
+    the last call (only kinds that ran)."""
+    L = lib()
+    k = L.ustat_profile_kinds()
+    ms = (_d * k)()
+    cnt = (_i * k)()
+    _check(L.ustat_profile_collect(ms, cnt), "ustat_profile_collect")
+    return {L.ustat_profile_kind_name(i).decode(): (ms[i], cnt[i]) for i in range(k) if cnt[i]}

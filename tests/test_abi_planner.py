@@ -1,0 +1,125 @@
+"""Host-side checks of the C ABI: the library builds and loads, exports every
+symbol include/ustat.h declares, and its planner (no CUDA call) reproduces the
+partition structure the paper fixes.  The oracle's own partition, Moebius and
+treewidth functions are the comparison."""
+import collections
+import json
+import os
+import re
+
+import pytest
+
+import synth
+from oracle import ustat_oracle as uo
+from tests.conftest import GOLDEN, ROOT
+
+
+@pytest.fixture(scope="module")
+def us():
+    from paper_2508_12627_gb300 import build
+    build.build()
+    from paper_2508_12627_gb300 import ustat
+    return ustat
+
+
+def test_every_declared_symbol_is_exported(us):
+    hdr = open(os.path.join(ROOT, "include", "ustat.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    names = set(re.findall(r"^\s*(?:const\s+)?(?:int|void|char|size_t)\s*\*?\s*(ustat_\w+)\s*\(", hdr, flags=re.M))
+    assert len(names) >= 15
+    lib = us.lib()
+    for nm in sorted(names):
+        assert hasattr(lib, nm), nm
+    assert set(us.EXPORTS) == names
+
+
+def _plan(us, g, kinds, **kw):
+    return us.Plan(g, kinds, **kw)
+
+
+GRAPHS = {
+    "triangle": (synth.triangle_graph(), [uo.RBF]),
+    "c4": (synth.cycle4_graph(), [uo.RBF]),
+    "path5_chord": (synth.path5_chord_graph(), [uo.LINEAR, uo.TANH_DOT]),
+    "k4_cycle": (synth.k4_plus_cycle_graph(), [uo.RBF]),
+    "c5": (synth.cycle(5), [uo.RBF]),
+}
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_partitions_mu_treewidth_match_oracle(us, name):
+    g, kinds = GRAPHS[name]
+    p = _plan(us, g, kinds, precision="fp64")
+    info = p.info
+    parts = uo.set_partitions(g.m)
+    assert info["n_parts"] == len(parts)
+    assert info["rgs"] == parts
+    assert info["mu"] == [uo.mu_closed_form(r) for r in parts]
+    assert info["tw"] == [uo.treewidth_bruteforce(max(r) + 1, uo.quotient_edges(g, r)) for r in parts]
+    ps = _plan(us, g, kinds, precision="fp64", sparsify=True)
+    sig = uo.signature(g)
+    assert ps.info["evaluated"] == [int(uo.survives(sig, r)) for r in parts]
+
+
+def test_workload_treewidth_profiles(us):
+    # counts of partitions by quotient treewidth for the five workloads (full mode)
+    want = {"triangle": {0: 1, 1: 3, 2: 1}, "c4": {0: 1, 1: 9, 2: 5},
+            "path5_chord": {0: 1, 1: 31, 2: 20}, "c5": {0: 1, 1: 25, 2: 26},
+            "k4_cycle": {0: 1, 1: 48, 2: 128, 3: 26}}
+    for name, (g, kinds) in GRAPHS.items():
+        p = _plan(us, g, kinds, precision="bf16x3")
+        assert dict(collections.Counter(p.info["tw"])) == want[name], name
+
+
+@pytest.mark.parametrize("m", [4, 5, 6, 7])
+def test_chain_N_l_from_planner(us, m):
+    # Table 'HOIF_Nl' (Appendix H): N_l of the surviving partitions of a chain
+    gold = json.load(open(os.path.join(GOLDEN, "hoif_chain_table.json")))
+    p = _plan(us, synth.path(m), [uo.MATRIX], precision="fp64", sparsify=True)
+    c = collections.Counter(t for t, e in zip(p.info["tw"], p.info["evaluated"]) if e)
+    assert [c.get(l, 0) for l in (1, 2, 3, 4)] == gold["N_l_dp"][str(m)]
+
+
+def test_sharing_leaves_one_cube_product_for_c4(us):
+    # all five treewidth-2 partitions of the 4-cycle reduce against K K^T
+    p = _plan(us, synth.cycle4_graph(), [uo.RBF], precision="bf16x3")
+    assert p.info["n_gemm"] == 1
+    n = 4096
+    fp, fn = p.flops(n)
+    assert fn == pytest.approx(6 * 2 * n ** 3 + 2 * 2 * n ** 2 * 4 + 4 * n ** 2, rel=0.05)
+    assert fp < 1.01 * 2 * n ** 3 + 20 * n ** 2
+    q = _plan(us, synth.cycle4_graph(), [uo.RBF], precision="bf16x3", cse=False)
+    assert q.info["n_gemm"] >= 5
+
+
+def test_planners_agree_on_structure(us):
+    for name, (g, kinds) in GRAPHS.items():
+        a = _plan(us, g, kinds, precision="fp32", planner=us.PLAN_EXHAUSTIVE)
+        b = _plan(us, g, kinds, precision="fp32", planner=us.PLAN_MINFILL)
+        assert a.info["tw"] == b.info["tw"]
+        assert a.flops(1000)[0] <= b.flops(1000)[0] * 1.0001
+
+
+def test_invalid_graphs_are_rejected(us):
+    with pytest.raises(us.UstatError) as e:
+        _plan(us, synth.Graph(3, [(0, 3, 0)], []), [uo.RBF])
+    assert e.value.code == us.USTAT_ERR_INVALID_ARG
+    with pytest.raises(us.UstatError) as e:
+        _plan(us, synth.Graph(3, [(0, 1, 0)], []), [uo.RBF])   # vertex 2 not covered
+    assert e.value.code == us.USTAT_ERR_INVALID_ARG
+    with pytest.raises(us.UstatError) as e:
+        _plan(us, synth.path(8), [uo.RBF])
+    assert e.value.code == us.USTAT_ERR_UNSUPPORTED
+    with pytest.raises(us.UstatError) as e:
+        _plan(us, synth.Graph(2, [(0, 1, 0)], []), [uo.TANH_DOT])   # unary kind on an edge
+    assert e.value.code == us.USTAT_ERR_INVALID_ARG
+    with pytest.raises(us.UstatError) as e:
+        _plan(us, synth.complete(5), [uo.RBF])   # K5: treewidth 4
+    assert e.value.code == us.USTAT_ERR_TW_TOO_LARGE
+
+
+def test_workspace_bytes_scale(us):
+    p = _plan(us, synth.cycle4_graph(), [uo.RBF], precision="bf16x3")
+    a, b = p.workspace_bytes(1000, 32), p.workspace_bytes(2000, 32)
+    assert 3.5 < b / a < 4.5
+    assert p.host_staging_bytes(1000, 32) >= 8 * 1000 * 32

@@ -1,0 +1,141 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element
+by element (U_sum, U_mean and every V_pi), on seeded inputs that span several
+128 x 128 tiles and a ragged tail, plus edge cases.
+
+Tolerances (relative to the oracle's sum of absolute terms V_abs, which equals
+|V| for positive kernels such as the RBF):
+  fp64    1e-11   (float64 throughout; only summation order differs)
+  bf16x3  1e-8    (the split tensor-core path; the engine's accuracy target)
+  fp32    1e-6    (float32 factors and CUDA-core GEMMs)
+  tf32    2e-2    (10-bit mantissa operands: reported, not a target)
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import ustat_oracle as uo
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-11, "bf16x3": 1e-8, "fp32": 1e-6, "tf32": 2e-2}
+
+
+@pytest.fixture(scope="module")
+def eng_mod():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2508_12627_gb300 import build
+    build.build()
+    from paper_2508_12627_gb300 import engine
+    return engine
+
+
+def _oracle(w, sparse=False):
+    r = uo.ustat(w.graph, w.factors, w.X, sparse=sparse)
+    a = uo.ustat(w.graph, w.factors, w.X, sparse=sparse, absolute=True)
+    return r, a
+
+
+def _compare(out, ref, absref, tol, label):
+    Vabs = np.array(absref["V"])
+    V = np.array(ref["V"])
+    err = np.abs(out["V"] - V)
+    bad = err > tol * np.maximum(Vabs, 1e-300)
+    assert not bad.any(), (label, np.argwhere(bad).ravel()[:5], (err / np.maximum(Vabs, 1e-300)).max())
+    uabs = sum(abs(mu) * va for mu, va in zip(ref["mu"], absref["V"]))
+    assert abs(out["U_sum"] - ref["U_sum"]) <= tol * uabs, (label, out["U_sum"], ref["U_sum"])
+    if ref["U_sum"] != 0.0:
+        # U_mean = U_sum / (n)_m: the same relative agreement
+        ratio_out = out["U_mean"] / out["U_sum"]
+        ratio_ref = ref["U_mean"] / ref["U_sum"]
+        assert ratio_out == pytest.approx(ratio_ref, rel=1e-14), label
+
+
+CASES = [("triangle_rbf", 200), ("c4_rbf", 300), ("path5_chord_linear_tanh", 257), ("k4_cycle_rbf", 72)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "fp32", "tf32"])
+@pytest.mark.parametrize("name,n", CASES)
+def test_workloads_against_oracle(eng_mod, name, n, prec):
+    w = synth.workload(name, n=n)
+    ref, absref = _oracle(w)
+    eng = eng_mod.Engine(w.graph, w.factors, precision=prec)
+    out = eng.evaluate(w.X)
+    _compare(out, ref, absref, TOL[prec], "%s n=%d %s" % (name, n, prec))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+@pytest.mark.parametrize("n", [4, 5, 64, 127, 128, 129, 256, 385])
+def test_c4_sizes_and_ragged_tails(eng_mod, n, prec):
+    w = synth.workload("c4_rbf", n=n)
+    ref, absref = _oracle(w)
+    out = eng_mod.Engine(w.graph, w.factors, precision=prec).evaluate(w.X)
+    _compare(out, ref, absref, TOL[prec], "c4 n=%d %s" % (n, prec))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3"])
+def test_rank1_integer_factors_bit_exact(eng_mod, prec):
+    # K = u u^T with u in {-1, 0, 1}: every partial sum is an integer far below
+    # 2^24, so the float32 and split bf16 paths are exact too.
+    n = 200
+    u = synth.ternary_vector(n, 9)
+    facs = [synth.Factor(uo.MATRIX, data=np.outer(u, u)), synth.Factor(uo.VECTOR, data=u)]
+    for g in [synth.cycle4_graph(), synth.path5_chord_graph(), synth.triangle_graph()]:
+        ref = uo.ustat(g, facs, np.zeros((n, 1)))
+        out = eng_mod.Engine(g, facs, precision=prec).evaluate(np.zeros((n, 1)))
+        assert list(out["V"]) == ref["V"], (prec, g.m)
+        assert out["U_sum"] == ref["U_sum"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_asymmetric_matrix_factors(eng_mod, prec):
+    # caller-supplied asymmetric factors with mixed orientations (transposed reads)
+    n = 150
+    rng = np.random.default_rng(21)
+    facs = [synth.Factor(uo.MATRIX, data=rng.uniform(0.2, 1.0, (n, n))),
+            synth.Factor(uo.VECTOR, data=rng.uniform(0.5, 1.5, n)),
+            synth.Factor(uo.MATRIX, data=rng.uniform(0.2, 1.0, (n, n)))]
+    g = synth.Graph(4, [(0, 1, 0), (2, 1, 2), (2, 3, 0), (3, 0, 2), (0, 2, 0)], [(1, 1)])
+    X = np.zeros((n, 1))
+    ref = uo.ustat(g, facs, X)
+    out = eng_mod.Engine(g, facs, precision=prec).evaluate(X)
+    _compare(out, ref, ref, TOL[prec], "asym %s" % prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_sparse_mode_and_sharing_and_planners_agree(eng_mod, prec):
+    w = synth.workload("path5_chord_linear_tanh", n=200)
+    ref, absref = _oracle(w)
+    uabs = sum(abs(mu) * va for mu, va in zip(ref["mu"], absref["V"]))
+    from paper_2508_12627_gb300 import ustat as us
+    outs = [eng_mod.Engine(w.graph, w.factors, precision=prec, sparsify=sp, cse=cse, planner=pl).evaluate(w.X)
+            for sp in (False, True) for cse in (False, True) for pl in (us.PLAN_EXHAUSTIVE, us.PLAN_MINFILL)]
+    for o in outs:
+        assert abs(o["U_sum"] - ref["U_sum"]) <= TOL[prec] * uabs
+
+
+def test_n_smaller_than_m_is_an_error(eng_mod):
+    from paper_2508_12627_gb300 import ustat as us
+    w = synth.workload("c4_rbf", n=3)
+    with pytest.raises(us.UstatError) as e:
+        eng_mod.Engine(w.graph, w.factors, precision="bf16x3").evaluate(w.X)
+    assert e.value.code == us.USTAT_ERR_N_LT_M
+
+
+def test_row_permutation_invariance_on_gpu(eng_mod):
+    w = synth.workload("c4_rbf", n=333)
+    e = eng_mod.Engine(w.graph, w.factors, precision="bf16x3")
+    a = e.evaluate(w.X)
+    b = e.evaluate(w.X[np.random.default_rng(1).permutation(333)])
+    assert np.allclose(a["V"], b["V"], rtol=1e-9, atol=0)
+
+
+def test_c4_full_size_against_oracle(eng_mod):
+    # the 4-cycle RBF workload at n = 4096, d = 32, in the launch configuration the
+    # benchmark times: all 15 V_pi and U against the FP64 oracle
+    w = synth.workload("c4_rbf")
+    ref, absref = _oracle(w)
+    out = eng_mod.Engine(w.graph, w.factors, precision="bf16x3").evaluate(w.X)
+    _compare(out, ref, absref, 1e-8, "c4 full bf16x3")
