@@ -20,9 +20,116 @@ __global__ void xconvert_kernel(const void *X, int x_dtype, int64_t total, T *ou
     }
 }
 
+// exp(z) in float32 arithmetic with only one rounding that matters: the result is
+// within ~0.6 ulp of e^z and its rounding errors are symmetric (no mean bias), so
+// the n^2 kernel entries do not shift a V-statistic systematically.
+// Method: Cody-Waite reduction z = k ln2 + f with ln2 = L1 + L2 (L1 = 45426 / 2^16,
+// so k L1 is exact), |f| <= ln2 / 2; e^f = 1 + f + f^2 (1/2! + f/3! + ... + f^6/8!)
+// (Taylor, truncation error below 2^-32); 1 + f is summed as a double-float and the
+// final sum rounded once; e^z = 2^k e^f by exponent arithmetic.
+__device__ __forceinline__ float exp_unbiased(float z) {
+    if (z < -87.0f) return 0.0f;
+    const float k = rintf(z * 1.44269504088896341f);
+    const float L1 = 0.693145751953125f;           // 45426 / 65536
+    const float L2 = 1.42860682030941723212e-6f;    // ln 2 - L1
+    const float fh = fmaf(-k, L1, z);               // exact
+    const float fl = -k * L2;
+    const float f = fh + fl;
+    float q = 1.0f / 40320.0f;
+    q = fmaf(q, f, 1.0f / 5040.0f);
+    q = fmaf(q, f, 1.0f / 720.0f);
+    q = fmaf(q, f, 1.0f / 120.0f);
+    q = fmaf(q, f, 1.0f / 24.0f);
+    q = fmaf(q, f, 1.0f / 6.0f);
+    q = fmaf(q, f, 0.5f);
+    q = q * f * f;
+    const float sh = 1.0f + fh;                     // Fast2Sum (|1| >= |fh|)
+    const float sl = fh - (sh - 1.0f);
+    const float y = sh + ((sl + fl) + q);
+    const int ki = (int)k;
+    return y * __int_as_float((ki + 127) << 23);    // 2^k, k >= -126 here
+}
+
 // One 64 x 64 tile of K per block, 16 x 16 threads, 4 x 4 outputs per thread
 // (rows ty + 16 r, cols tx + 16 c).  X rows of both tile sides go through shared
-// memory in chunks of 32 coordinates.
+// memory in chunks of 32 coordinates.  Float32 version: the squared distance is
+// summed in float32 (its rounding errors are symmetric), the exponential is
+// exp_unbiased, and the linear kernel's dot product is accumulated as a
+// double-float (TwoProd by FMA, TwoSum) and rounded once.
+__global__ void __launch_bounds__(256) kbuild_f32_kernel(int kind, float inv_param, const float *__restrict__ X,
+                                                         int64_t n, int d, int zero_diag, float *__restrict__ K) {
+    __shared__ float xi[64][33];
+    __shared__ float xj[64][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int64_t i0 = (int64_t)blockIdx.y * 64, j0 = (int64_t)blockIdx.x * 64;
+    float acc[4][4], lo[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = lo[r][c] = 0.f;
+    const int tid = ty * 16 + tx;
+    for (int k0 = 0; k0 < d; k0 += 32) {
+        for (int e = tid; e < 64 * 32; e += 256) {
+            int rr = e / 32, kk = e % 32;
+            int64_t gi = i0 + rr, gj = j0 + rr;
+            xi[rr][kk] = (gi < n && k0 + kk < d) ? X[gi * d + k0 + kk] : 0.f;
+            xj[rr][kk] = (gj < n && k0 + kk < d) ? X[gj * d + k0 + kk] : 0.f;
+        }
+        __syncthreads();
+        const int kmax = min(32, d - k0);
+        for (int kk = 0; kk < kmax; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a[r] = xi[ty + 16 * r][kk];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) b[c] = xj[tx + 16 * c][kk];
+            if (kind == USTAT_RBF) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const float df = a[r] - b[c];
+                        acc[r][c] = fmaf(df, df, acc[r][c]);
+                    }
+            } else {
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const float p = a[r] * b[c];
+                        const float pe = fmaf(a[r], b[c], -p);
+                        const float t = acc[r][c] + p;
+                        const float bp = t - acc[r][c];
+                        const float se = (acc[r][c] - (t - bp)) + (p - bp);
+                        acc[r][c] = t;
+                        lo[r][c] += se + pe;
+                    }
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        int64_t gi = i0 + ty + 16 * r;
+        if (gi >= n) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            int64_t gj = j0 + tx + 16 * c;
+            if (gj >= n) continue;
+            float v;
+            if (kind == USTAT_RBF) {
+                v = (gi == gj) ? 1.0f : exp_unbiased(-acc[r][c] * inv_param);
+            } else {
+                const float s = acc[r][c] + lo[r][c];
+                v = s * inv_param;
+            }
+            if (zero_diag && gi == gj) v = 0.f;
+            K[gi * n + gj] = v;
+        }
+    }
+}
+
+// Float64 version (FP64 mode).
 template <typename T>
 __global__ void __launch_bounds__(256) kbuild_kernel(int kind, T inv_param, const T *__restrict__ X,
                                                      int64_t n, int d, int zero_diag, T *__restrict__ K) {
@@ -193,8 +300,8 @@ cudaError_t launch_kbuild(int kind, double param, const void *Xw, bool fp64, int
         kbuild_kernel<double><<<grid, block, 0, s>>>(kind, 1.0 / param, (const double *)Xw, n, d, zero_diag,
                                                      (double *)K);
     else
-        kbuild_kernel<float><<<grid, block, 0, s>>>(kind, (float)(1.0 / param), (const float *)Xw, n, d,
-                                                    zero_diag, (float *)K);
+        kbuild_f32_kernel<<<grid, block, 0, s>>>(kind, (float)(1.0 / param), (const float *)Xw, n, d, zero_diag,
+                                                 (float *)K);
     return cudaGetLastError();
 }
 

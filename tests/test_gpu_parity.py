@@ -116,6 +116,22 @@ def test_sparse_mode_and_sharing_and_planners_agree(eng_mod, prec):
         assert abs(o["U_sum"] - ref["U_sum"]) <= TOL[prec] * uabs
 
 
+@pytest.mark.parametrize("name", ["rbf", "linear"])
+def test_kernel_matrix_sum_has_no_bias(eng_mod, name):
+    # m = 2, one edge: U_sum = sum_{i != j} F(x_i, x_j).  A mean bias of the device's
+    # float32 kernel entries would show at full size (16.7M terms); symmetric
+    # rounding errors average out far below the split path's 1e-8 target.
+    n, d = 4096, 32
+    X = synth.normal_X(n, d, 3)
+    g = synth.Graph(2, [(0, 1, 0)], [])
+    f = [synth.rbf(d)] if name == "rbf" else [synth.linear(d)]
+    ref, absref = _oracle(synth.Workload("m2", g, f, n, d, X))
+    for prec in ("fp32", "bf16x3"):
+        out = eng_mod.Engine(g, f, precision=prec).evaluate(X)
+        uabs = sum(abs(mu) * va for mu, va in zip(ref["mu"], absref["V"]))
+        assert abs(out["U_sum"] - ref["U_sum"]) <= 1e-9 * uabs, (name, prec, out["U_sum"], ref["U_sum"])
+
+
 def test_n_smaller_than_m_is_an_error(eng_mod):
     from paper_2508_12627_gb300 import ustat as us
     w = synth.workload("c4_rbf", n=3)
