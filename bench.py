@@ -144,6 +144,24 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_capture(args):
+    """`args.capture` evaluations of the workload, nothing else (for ncu)."""
+    import torch
+
+    import synth
+    from paper_2508_12627_gb300 import build as B
+    B.build()
+    from paper_2508_12627_gb300 import engine
+    w = synth.workload(args.workload)
+    eng = engine.Engine(w.graph, w.factors, precision=args.precision)
+    Xd = eng.to_device(w.X)
+    out = torch.empty(2 + eng.n_parts, dtype=torch.float64, device="cuda")
+    for _ in range(args.capture):
+        eng.launch(Xd, out)
+    torch.cuda.synchronize()
+    print("capture done: U_sum %.17g" % out[0].item())
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -153,10 +171,15 @@ def main():
     ap.add_argument("--workload", default="c4_rbf")
     ap.add_argument("--impl", default="engine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--capture", type=int, default=0,
+                    help="only run this many evaluations (no timing, no JSON): for profiler captures")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.capture:
+        run_capture(args)
         return
 
     import numpy as np
@@ -229,14 +252,17 @@ def main():
     fl_plan, fl_naive = eng.plan.flops(n)
     peaks, peak_src = load_peaks()
     launches = sum(c for (_, c) in prof.values())
-    # dominant kernel: the n^3 contraction
-    gemm_ms, gemm_cnt = prof.get("gemm", (0.0, 0))
-    red_ms, red_cnt = prof.get("gemm_red", (0.0, 0))
-    g_ms, g_cnt = gemm_ms + red_ms, gemm_cnt + red_cnt
+    # dominant kernel: the n^3 contraction.  Its algorithmic flops: 2 n per
+    # product entry the algorithm needs (n^2 entries, or n (n + 1) / 2 for a
+    # symmetric product whose reductions are symmetric).
+    g_ms, g_cnt = prof.get("gemm", (0.0, 0))
     per_launch_s = (g_ms / max(1, g_cnt)) / 1e3
-    alg_flops = 2.0 * n ** 3
+    gemm_lines = [l for l in eng.plan.describe().splitlines() if " gemm " in l]
+    entries = [(n * (n + 1) / 2 if "sym=1" in l else n * n) for l in gemm_lines]
+    alg_flops = 2.0 * n * (sum(entries) / max(1, len(entries)))
     bf16_peak = peaks.get("bf16_tflops", 1900.0)
-    products = {"bf16x3": 6.0, "tf32": 2.0, "fp32": None, "fp64": None}[args.precision]
+    # tensor products per algorithmic multiply-add (tf32 runs at half the bf16 rate)
+    products = {"bf16x3": 6.0, "bf16x4": 10.0, "tf32": 2.0, "fp32": None, "fp64": None}[args.precision]
     roof = None
     if g_cnt and products:
         achieved = alg_flops / per_launch_s / 1e12

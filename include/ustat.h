@@ -61,6 +61,8 @@ extern "C" {
 #define USTAT_TF32    2  /* GEMMs on tcgen05 kind::tf32, FP32 accumulation                   */
 #define USTAT_BF16X3  3  /* GEMMs on tcgen05 kind::f16 with three bf16 fixed-point slices per
                             operand, exact integer accumulation of the leading slice product */
+#define USTAT_BF16X4  4  /* as BF16X3 with four slices (8 more bits per operand row) for
+                            factors whose rows span a wide dynamic range */
 
 /* ---- planners (choice of elimination order per partition) ---- */
 #define USTAT_PLAN_EXHAUSTIVE  0  /* minimum modelled cost over all orders (<= 8 blocks) */
@@ -85,7 +87,7 @@ typedef struct {
 } ustat_graph;
 
 typedef struct {
-    int precision;   /* USTAT_FP64 / FP32 / TF32 / BF16X3                            */
+    int precision;   /* USTAT_FP64 / FP32 / TF32 / BF16X3 / BF16X4                   */
     int sparsify;    /* 1: zero-diagonal tensors T~ and only partitions in Pi_m^A
                         (Lemma "sparsification_trick", equation "quotient_set");
                         V_pi of skipped partitions is reported as 0                   */

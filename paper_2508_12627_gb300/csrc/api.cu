@@ -117,7 +117,8 @@ Layout make_layout(const Plan &P, int64_t n, int d) {
                 break;
             case S_SLICES:
                 L.off[s] = cur;
-                cur = align_up(cur + 3 * 2 * (size_t)n * L.ldp_slices + 4 * (size_t)n, 1024);
+                cur = align_up(cur + split_planes_of(P.precision) * 2 * (size_t)n * L.ldp_slices + 4 * (size_t)n,
+                               1024);
                 break;
             case S_PREP:
                 L.off[s] = cur;
@@ -143,7 +144,7 @@ struct Ctx {
     double *vec(int slot) const { return (double *)ptr(slot); }
     // slices: [3][n][ldp] bf16 followed by float scales [n]
     float *scales(int slot) const {
-        return (float *)(ws + L.off[slot] + 3 * 2 * (size_t)n * L.ldp_slices);
+        return (float *)(ws + L.off[slot] + split_planes_of(P.precision) * 2 * (size_t)n * L.ldp_slices);
     }
 };
 
@@ -213,58 +214,86 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                     e = launch_tile_op(TILE_FREDUCE, tt, C.fp64, n, C.vec(op.a), C.vec(op.b), C.ptr(op.out), C.st);
                 break;
             }
+            case OP_MHB: {
+                MhbArgs g{};
+                g.n = n;
+                std::vector<int> mats;
+                auto mat_index = [&](int slot) {
+                    for (size_t q = 0; q < mats.size(); ++q)
+                        if (mats[q] == slot) return (int)q;
+                    mats.push_back(slot);
+                    return (int)mats.size() - 1;
+                };
+                const auto &grp = P.groups[op.group];
+                g.nops = (int)grp.size();
+                for (size_t q = 0; q < grp.size(); ++q) {
+                    const Op &m = grp[q];
+                    MhbOp &h = g.op[q];
+                    h.kind = m.kind == OP_GEMV ? TILE_GEMV : TILE_FREDUCE;
+                    h.nt = m.nt;
+                    for (int t = 0; t < m.nt; ++t) h.mat[t] = mat_index(m.t[t].mat);
+                    h.a = m.kind == OP_GEMV ? C.vec(m.u) : C.vec(m.a);
+                    h.b = m.kind == OP_GEMV ? nullptr : C.vec(m.b);
+                    h.out = (double *)C.ptr(m.out);
+                }
+                if (mats.size() > (size_t)kMhbMats) return USTAT_ERR_UNSUPPORTED;
+                g.nmat = (int)mats.size();
+                for (size_t q = 0; q < mats.size(); ++q) g.M[q] = C.ptr(mats[q]);
+                e = launch_mhb(g, C.fp64, C.st);
+                break;
+            }
             case OP_SPLIT:
             case OP_PREP: {
                 const Term t = op.t[0];
                 const int tr = P.slots[t.mat].symmetric ? 1 : t.trans;
                 if (op.kind == OP_SPLIT)
                     e = launch_split((const float *)C.ptr(t.mat), tr, C.vec(op.u), n, C.L.ldp_slices, lead,
-                                     C.ptr(op.out), C.scales(op.out), C.st);
+                                     split_planes_of(P.precision), C.ptr(op.out), C.scales(op.out), C.st);
                 else
                     e = launch_prep((const float *)C.ptr(t.mat), tr, C.vec(op.u), n, C.L.ldp_prep,
                                     (float *)C.ptr(op.out), C.st);
                 break;
             }
-            case OP_GEMM:
-            case OP_GEMM_RED: {
-                const bool red = op.kind == OP_GEMM_RED;
-                if (P.precision == USTAT_BF16X3 || P.precision == USTAT_TF32) {
+            case OP_GEMM: {
+                auto trW = [&](const Term &t) { return (t.mat >= 0 && !P.slots[t.mat].symmetric) ? t.trans : 0; };
+                if (is_tc_mode(P.precision)) {
+                    const bool split = is_split_mode(P.precision);
                     TcGemmArgs g{};
                     g.n = n;
-                    g.ldp = P.precision == USTAT_BF16X3 ? C.L.ldp_slices : C.L.ldp_prep;
+                    g.ldp = split ? C.L.ldp_slices : C.L.ldp_prep;
                     g.opA = C.ptr(op.opA);
                     g.opB = C.ptr(op.opB);
-                    g.scaleA = P.precision == USTAT_BF16X3 ? C.scales(op.opA) : nullptr;
-                    g.scaleB = P.precision == USTAT_BF16X3 ? C.scales(op.opB) : nullptr;
+                    g.scaleA = split ? C.scales(op.opA) : nullptr;
+                    g.scaleB = split ? C.scales(op.opB) : nullptr;
                     g.lead_bits = lead;
                     g.err = err;
-                    if (red) {
-                        g.red = (double *)C.ptr(op.out);
-                        g.W = (const float *)C.ptr(op.W.mat);
-                        g.transW = (op.W.mat >= 0 && !P.slots[op.W.mat].symmetric) ? op.W.trans : 0;
-                        g.a = C.vec(op.a);
-                        g.b = C.vec(op.b);
-                    } else {
-                        g.C = (float *)C.ptr(op.out);
+                    g.C = op.store ? (float *)C.ptr(op.out) : nullptr;
+                    g.nred = op.nred;
+                    for (int r = 0; r < op.nred; ++r) {
+                        const Red &R = op.red[r];
+                        g.red[r] = TcRed{(const float *)C.ptr(R.W.mat), trW(R.W), C.vec(R.a), C.vec(R.b), R.pow,
+                                         (double *)C.ptr(R.out)};
                     }
-                    e = P.precision == USTAT_BF16X3 ? launch_gemm_bf16x3(g, C.st) : launch_gemm_tf32(g, C.st);
+                    g.symmetric = op.symmetric;
+                    if (P.precision == USTAT_BF16X3) e = launch_gemm_bf16x3(g, C.st);
+                    else if (P.precision == USTAT_BF16X4) e = launch_gemm_bf16x4(g, C.st);
+                    else e = launch_gemm_tf32(g, C.st);
                 } else {
                     SimtGemmArgs g{};
                     g.n = n;
                     g.A = C.ptr(op.A.mat);
-                    g.transA = P.slots[op.A.mat].symmetric ? 0 : op.A.trans;
+                    g.transA = trW(op.A);
                     g.B = C.ptr(op.B.mat);
-                    g.transB = P.slots[op.B.mat].symmetric ? 0 : op.B.trans;
+                    g.transB = trW(op.B);
                     g.u = C.vec(op.u);
-                    if (red) {
-                        g.red = (double *)C.ptr(op.out);
-                        g.W = C.ptr(op.W.mat);
-                        g.transW = (op.W.mat >= 0 && !P.slots[op.W.mat].symmetric) ? op.W.trans : 0;
-                        g.a = C.vec(op.a);
-                        g.b = C.vec(op.b);
-                    } else {
-                        g.C = C.ptr(op.out);
+                    g.C = op.store ? C.ptr(op.out) : nullptr;
+                    g.nred = op.nred;
+                    for (int r = 0; r < op.nred; ++r) {
+                        const Red &R = op.red[r];
+                        g.red[r] = SimtRed{C.ptr(R.W.mat), trW(R.W), C.vec(R.a), C.vec(R.b), R.pow,
+                                           (double *)C.ptr(R.out)};
                     }
+                    g.symmetric = op.symmetric;
                     e = launch_gemm_simt(g, C.fp64, C.st);
                 }
                 break;
@@ -281,16 +310,13 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                 g.u = C.vec(op.u);
                 g.Ab = C.ptr(op.Ab.mat);
                 g.transAb = tr(op.Ab);
-                g.red = (double *)C.ptr(op.out);
-                g.W = C.ptr(op.W.mat);
-                g.transW = tr(op.W);
+                g.nred = 1;
+                g.red[0] = SimtRed{C.ptr(op.W.mat), tr(op.W), C.vec(op.a), C.vec(op.b), 1, (double *)C.ptr(op.out)};
                 g.Wbc = C.ptr(op.Wbc.mat);
                 g.transWbc = tr(op.Wbc);
                 g.Wbd = C.ptr(op.Wbd.mat);
                 g.transWbd = tr(op.Wbd);
                 g.ub = C.vec(op.ub);
-                g.a = C.vec(op.a);
-                g.b = C.vec(op.b);
                 e = launch_gemm_simt(g, C.fp64, C.st);
                 break;
             }
@@ -507,13 +533,31 @@ extern "C" int ustat_plan_describe(const ustat_plan_t *plan, char *buf, size_t b
     auto vec = [&](int v) -> std::string { return v < 0 ? "1" : "v" + std::to_string(v); };
     for (size_t i = 0; i < P.ops.size(); ++i) {
         const Op &o = P.ops[i];
-        std::string ts;
+        std::string ts, rs;
         for (int t = 0; t < o.nt; ++t) ts += (t ? "," : "") + term(o.t[t]);
-        snprintf(line, sizeof(line),
-                 "%zu %s out=%d f=%d terms=[%s] u=%s a=%s b=%s A=%s B=%s W=%s Ab=%s Wbc=%s Wbd=%s ub=%s opA=%d opB=%d\n",
-                 i, op_name(o.kind), o.out, o.factor, ts.c_str(), vec(o.u).c_str(), vec(o.a).c_str(),
-                 vec(o.b).c_str(), term(o.A).c_str(), term(o.B).c_str(), term(o.W).c_str(), term(o.Ab).c_str(),
-                 term(o.Wbc).c_str(), term(o.Wbd).c_str(), vec(o.ub).c_str(), o.opA, o.opB);
+        for (int r = 0; r < o.nred; ++r)
+            rs += (r ? ";" : "") + std::string("s") + std::to_string(o.red[r].out) + "+=C^" +
+                  std::to_string(o.red[r].pow) + "*" + term(o.red[r].W) + "*" + vec(o.red[r].a) + "*" +
+                  vec(o.red[r].b);
+        if (o.kind == OP_GEMM) {
+            snprintf(line, sizeof(line), "%zu gemm store=%d out=%d A=%s B=%s u=%s sym=%d opA=%d opB=%d red=[%s]\n", i,
+                     o.store, o.out, term(o.A).c_str(), term(o.B).c_str(), vec(o.u).c_str(), o.symmetric, o.opA,
+                     o.opB, rs.c_str());
+        } else if (o.kind == OP_MHB) {
+            std::string ms;
+            for (const Op &m : P.groups[o.group]) {
+                std::string mt;
+                for (int t = 0; t < m.nt; ++t) mt += (t ? "," : "") + term(m.t[t]);
+                ms += std::string(" ") + op_name(m.kind) + "(out=" + std::to_string(m.out) + " [" + mt + "] " +
+                      (m.kind == OP_GEMV ? "u=" + vec(m.u) : "a=" + vec(m.a) + " b=" + vec(m.b)) + ")";
+            }
+            snprintf(line, sizeof(line), "%zu mhb%s\n", i, ms.c_str());
+        } else
+            snprintf(line, sizeof(line),
+                     "%zu %s out=%d f=%d terms=[%s] u=%s a=%s b=%s A=%s B=%s W=%s Ab=%s Wbc=%s Wbd=%s ub=%s\n", i,
+                     op_name(o.kind), o.out, o.factor, ts.c_str(), vec(o.u).c_str(), vec(o.a).c_str(),
+                     vec(o.b).c_str(), term(o.A).c_str(), term(o.B).c_str(), term(o.W).c_str(), term(o.Ab).c_str(),
+                     term(o.Wbc).c_str(), term(o.Wbd).c_str(), vec(o.ub).c_str());
         s += line;
     }
     for (size_t p = 0; p < P.parts.size(); ++p) {

@@ -1,13 +1,15 @@
 // The s = 2 and s = 3 elimination steps (Appendix D: summing out an index with
 // two or three live neighbours) on CUDA cores, in float32 or float64:
 //
-//   C(j, k)  = sum_i A(i, j) u(i) B(i, k)                          (store)
-//   red     += sum_jk C(j, k) W(j, k) a(j) b(k)                    (fused reduce)
+//   C(j, k)  = sum_i A(i, j) u(i) B(i, k)                          (stored and/or)
+//   out_r   += sum_jk C(j, k)^p_r W_r(j, k) a_r(j) b_r(k)          (fused reductions)
 //   GEMM3   : for every bb, the same with u'(i) = u(i) Ab(i, bb) and the
-//             epilogue weights Wbc(bb, j), Wbd(bb, k), ub(bb)    (grid.z = bb)
+//             extra epilogue weights Wbc(bb, j), Wbd(bb, k), ub(bb)  (grid.z = bb)
 //
-// Register-blocked tiles (BM x BN, TM x TN per thread, 16 x 16 threads); the
-// reduce epilogue accumulates in float64 and adds one value per block.
+// Register-blocked tiles (BM x BN, TM x TN per thread, 16 x 16 threads).
+// Reductions accumulate in float64 and add one value per block and reduction.
+// With `symmetric` only tiles on or above the diagonal run and off-diagonal
+// tiles count twice.
 #include <cuda_runtime.h>
 
 #include "kcommon.cuh"
@@ -19,13 +21,15 @@ namespace {
 
 template <typename T, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__(256) simt_gemm_kernel(SimtGemmArgs g) {
+    static_assert(BM == BN, "square tiles");
     __shared__ T As[BK][BM];
     __shared__ T Bs[BK][BN];
-    __shared__ T rw[BM];   // epilogue row weights (reduce mode)
+    __shared__ T rw[BM];   // epilogue row weights
     __shared__ T cw[BN];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * 16 + tx;
     const int64_t n = g.n;
+    if (g.symmetric && blockIdx.y > blockIdx.x) return;
     const int64_t j0 = (int64_t)blockIdx.y * BM, k0 = (int64_t)blockIdx.x * BN;
     const int64_t bb = blockIdx.z;
     const T *A = (const T *)g.A;
@@ -89,55 +93,62 @@ __global__ void __launch_bounds__(256) simt_gemm_kernel(SimtGemmArgs g) {
                 if (k < n) C[j * n + k] = acc[r][c];
             }
         }
-        return;
     }
-    // fused reduction
-    const T *W = (const T *)g.W;
-    const T *Wbc = (const T *)g.Wbc;
-    const T *Wbd = (const T *)g.Wbd;
-    for (int e = tid; e < BM; e += 256) {
-        int64_t j = j0 + e;
-        T v = 0;
-        if (j < n) {
-            v = g.a ? (T)g.a[j] : T(1);
-            if (g.gemm3 && Wbc) v *= g.transWbc ? Wbc[j * n + bb] : Wbc[bb * n + j];
+    const double wgt = (g.symmetric && blockIdx.x != blockIdx.y) ? 2.0 : 1.0;
+    for (int q = 0; q < g.nred; ++q) {
+        const SimtRed &R = g.red[q];
+        const T *W = (const T *)R.W;
+        const T *Wbc = (const T *)g.Wbc;
+        const T *Wbd = (const T *)g.Wbd;
+        __syncthreads();
+        for (int e = tid; e < BM; e += 256) {
+            int64_t j = j0 + e;
+            T v = 0;
+            if (j < n) {
+                v = R.a ? (T)R.a[j] : T(1);
+                if (g.gemm3 && Wbc) v *= g.transWbc ? Wbc[j * n + bb] : Wbc[bb * n + j];
+            }
+            rw[e] = v;
         }
-        rw[e] = v;
-    }
-    for (int e = tid; e < BN; e += 256) {
-        int64_t k = k0 + e;
-        T v = 0;
-        if (k < n) {
-            v = g.b ? (T)g.b[k] : T(1);
-            if (g.gemm3 && Wbd) v *= g.transWbd ? Wbd[k * n + bb] : Wbd[bb * n + k];
+        for (int e = tid; e < BN; e += 256) {
+            int64_t k = k0 + e;
+            T v = 0;
+            if (k < n) {
+                v = R.b ? (T)R.b[k] : T(1);
+                if (g.gemm3 && Wbd) v *= g.transWbd ? Wbd[k * n + bb] : Wbd[bb * n + k];
+            }
+            cw[e] = v;
         }
-        cw[e] = v;
-    }
-    __syncthreads();
-    double s = 0.0;
+        __syncthreads();
+        double s = 0.0;
 #pragma unroll
-    for (int r = 0; r < TM; ++r) {
-        int64_t j = j0 + ty + 16 * r;
-        if (j >= n) continue;
-        T rowp = 0;
+        for (int r = 0; r < TM; ++r) {
+            int64_t j = j0 + ty + 16 * r;
+            if (j >= n) continue;
+            T rowp = 0;
 #pragma unroll
-        for (int c = 0; c < TN; ++c) {
-            int64_t k = k0 + tx + 16 * c;
-            if (k >= n) continue;
-            T w = cw[tx + 16 * c];
-            if (W) w *= g.transW ? W[k * n + j] : W[j * n + k];
-            rowp = fma(acc[r][c], w, rowp);
+            for (int c = 0; c < TN; ++c) {
+                int64_t k = k0 + tx + 16 * c;
+                if (k >= n) continue;
+                T w = cw[tx + 16 * c];
+                if (W) w *= R.transW ? W[k * n + j] : W[j * n + k];
+                const T x = R.pow == 2 ? acc[r][c] * acc[r][c] : acc[r][c];
+                rowp = fma(x, w, rowp);
+            }
+            s += (double)rowp * (double)rw[ty + 16 * r];
         }
-        s += (double)rowp * (double)rw[ty + 16 * r];
+        if (g.gemm3 && g.ub) s *= g.ub[bb];
+        s = block_sum(s * wgt);
+        if (tid == 0) atomicAdd(R.out, s);
     }
-    if (g.gemm3 && g.ub) s *= g.ub[bb];
-    s = block_sum(s);
-    if (tid == 0) atomicAdd(g.red, s);
 }
 
 }  // namespace
 
-cudaError_t launch_gemm_simt(const SimtGemmArgs &g, bool fp64, cudaStream_t s) {
+cudaError_t launch_gemm_simt(const SimtGemmArgs &g0, bool fp64, cudaStream_t s) {
+    SimtGemmArgs g = g0;
+    if (g.C || g.gemm3) g.symmetric = 0;
+    if (g.nred < 0 || g.nred > 4) return cudaErrorInvalidValue;
     const int64_t n = g.n;
     const unsigned zb = g.gemm3 ? (unsigned)n : 1u;
     dim3 block(16, 16);

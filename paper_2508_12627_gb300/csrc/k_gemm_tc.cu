@@ -1,29 +1,32 @@
 // Tensor-core (tcgen05 + TMA, sm_103a) form of the s = 2 elimination step
-// (Appendix D: summing out an index with two live neighbours is the matrix
-// product C(j, k) = sum_i A(i, j) u(i) B(i, k)), with either a stored C or the
-// fused reduction sum_jk C(j, k) W(j, k) a(j) b(k) of a component's last step.
+// (Appendix D: summing out an index with two live neighbours is the product
+// C(j, k) = sum_i A(i, j) u(i) B(i, k)).  The product is stored, reduced in the
+// epilogue against up to four weights (sum_jk C^p W a(j) b(k), p in {1, 2}), or
+// both, so products consumed only by reductions never reach global memory.
 //
-// BF16X3 mode.  Each K-major operand row X(j, .) is written as three bf16
+// Split-bf16 modes.  Each K-major operand row X(j, .) is written as S bf16
 // fixed-point slices relative to a power-of-two row scale s_j >= max |X(j, .)|:
-//     X(j, i) = s_j 2^-w (d1 + d2 2^-8 + d3 2^-16),  d1 in [-2^w, 2^w], |d2|,|d3| <= 128
-// with hi = d1 (an integer), mid = d2 2^-8, lo = d3 2^-16, each exact in bf16.
-// The product of two rows is accumulated as
-//     ACC_hi = sum_i hi_A hi_B                          (integers, exact in FP32
-//                                                        because n 4^w <= 2^24)
-//     ACC_lo = sum_i (hi mid + mid hi + hi lo + lo hi + mid mid)
-// and C = s_j s_k 2^-2w (ACC_hi + ACC_lo).  The dropped terms (mid lo, lo mid,
-// lo lo) are below 2^-24 of the leading product.  Exact accumulation of the
-// leading term removes the rounding bias of the tensor cores' FP32 accumulator,
-// which otherwise does not average out over the n^2 terms of a V-statistic.
+//     X(j, i) = s_j 2^-w (d1 + d2 2^-8 + d3 2^-16 [+ d4 2^-24]),
+//     d1 in [-2^w, 2^w], |d2|, |d3|, |d4| <= 128,
+// every slice exact in bf16.  The product of two rows is accumulated as
+//     ACC_hi = sum_i d1_A d1_B                   (integers: exact in FP32 because
+//                                                 n 4^w <= 2^24)
+//     ACC_lo = sum_i (all slice pairs of weight 2^-8 .. 2^-8(S-1))
+// and C = s_j s_k 2^-2w (ACC_hi + ACC_lo).  S = 3 (6 products) or S = 4 (10
+// products; 8 more bits for data whose rows span a wide dynamic range).  Exact
+// accumulation of the leading term removes the rounding bias of the FP32
+// accumulator, which would not average out over the n^2 terms of a V-statistic.
+// TF32 mode: one tf32 copy of each operand (rounded to nearest), one accumulator.
 //
-// TF32 mode: one tf32 operand copy (rounded to nearest), one accumulator.
-//
-// Kernel structure: one 128 x 128 output tile per CTA, 128 threads.  Thread 0
-// issues TMA loads into a 2- or 4-stage ring (128-byte swizzle), thread 32
-// issues the MMAs into TMEM (cta_group::1, M = 128, N = 128), then all four
-// warps drain their 32 TMEM lanes with tcgen05.ld for the epilogue.  Every
-// mbarrier wait is bounded; on time-out the CTA records an error, waits (again
-// bounded) for its own copies in flight, frees its TMEM and returns.
+// Kernel: persistent CTAs (one per SM), 192 threads.  Warp 0 streams A and B
+// tiles with TMA into a ring of shared-memory stages (128-byte swizzle), warp 1
+// issues tcgen05.mma (cta_group::1, M = 128, N = 128 or 64) into one of two TMEM
+// accumulator buffers, warps 2-5 drain the other buffer (tcgen05.ld) in the
+// epilogue, so the epilogue of one tile overlaps the main loop of the next.
+// With `symmetric` (C = C^T and every reduction symmetric) only tiles on or
+// above the diagonal are computed and off-diagonal tiles count twice.  Every
+// mbarrier wait is bounded: on time-out the CTA records an error, waits (again
+// bounded) for its copies in flight, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -49,34 +52,86 @@ namespace {
 
 // ------------------------------------------------------------------ split / prep
 
-// One block per 32 operand rows j.  Pass 1: row maxima |X(j, i)| over all i.
-// Pass 2: digits, written K-major through a shared-memory transpose when the
-// source is read along columns.
+__device__ __forceinline__ int row_exp(float m) {
+    // smallest e with m <= 2^e (m = f 2^e, f in [0.5, 1); f = 0.5 means m = 2^(e-1))
+    int e = 0;
+    if (m > 0.f) {
+        const float f = frexpf(m, &e);
+        if (f == 0.5f) e -= 1;
+    }
+    return e;
+}
+
+__device__ __forceinline__ void write_digits(float x, int lead_bits, int e, int planes, __nv_bfloat16 *dst,
+                                             int64_t plane_stride) {
+    float y = ldexpf(x, lead_bits - e);   // |y| <= 2^w, exact
+    float d = rintf(y);
+    dst[0] = __float2bfloat16_rn(d);
+    float scale = 1.f / 256.f;
+    for (int p = 1; p < planes; ++p) {
+        y = (y - d) * 256.f;              // exact
+        d = rintf(y);
+        dst[p * plane_stride] = __float2bfloat16_rn(d * scale);
+        scale *= (1.f / 256.f);
+    }
+}
+
+// Row-major source (X(j, i) = M[j][i] u(i)): one warp per operand row, two passes
+// (row maximum, then digits), fully coalesced.
+__global__ void __launch_bounds__(256) split_rows_kernel(const float *__restrict__ M, const double *__restrict__ u,
+                                                         int64_t n, int64_t ldp, int lead_bits, int planes,
+                                                         __nv_bfloat16 *__restrict__ slices,
+                                                         float *__restrict__ scales) {
+    const int lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (j >= n) return;
+    const float *row = M + j * n;
+    float mx = 0.f;
+    for (int64_t i = lane; i < n; i += 32) {
+        float x = row[i];
+        if (u) x *= (float)u[i];
+        mx = fmaxf(mx, fabsf(x));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int e = row_exp(mx);
+    if (lane == 0) scales[j] = ldexpf(1.f, e);
+    const int64_t plane = n * ldp;
+    for (int64_t i = lane; i < ldp; i += 32) {
+        float x = 0.f;
+        if (i < n) {
+            x = row[i];
+            if (u) x *= (float)u[i];
+        }
+        write_digits(x, lead_bits, e, planes, slices + j * ldp + i, plane);
+    }
+}
+
+// Column source (X(j, i) = M[i][j] u(i)) and the tf32 copy: one block per 32
+// operand rows, transposed through shared memory.
 template <bool kSplit>
-__global__ void __launch_bounds__(256) operand_kernel(const float *__restrict__ M, int trans,
-                                                      const double *__restrict__ u, int64_t n, int64_t ldp,
-                                                      int lead_bits, __nv_bfloat16 *__restrict__ slices,
-                                                      float *__restrict__ scales, float *__restrict__ prep) {
+__global__ void __launch_bounds__(256) operand_cols_kernel(const float *__restrict__ M, int trans,
+                                                           const double *__restrict__ u, int64_t n, int64_t ldp,
+                                                           int lead_bits, int planes,
+                                                           __nv_bfloat16 *__restrict__ slices,
+                                                           float *__restrict__ scales, float *__restrict__ prep) {
     __shared__ float tile[32][33];
     __shared__ float rmax[8][32];
     __shared__ int rexp[32];
     const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
     const int64_t j0 = (int64_t)blockIdx.x * 32;
-    // X(j, i) = M[i][j] u(i) (trans = 0: column j of M) or M[j][i] u(i) (trans = 1)
     auto val = [&](int64_t j, int64_t i) -> float {
         if (j >= n || i >= n) return 0.f;
         float x = trans ? M[j * n + i] : M[i * n + j];
         if (u) x *= (float)u[i];
         return x;
     };
-    int e_row = 0;
     if (kSplit) {
-        float mx = 0.f;   // thread handles column j0 + tx (trans = 0) or row-major reads
+        float mx = 0.f;
         if (!trans) {
             for (int64_t i = ty; i < n; i += 8) mx = fmaxf(mx, fabsf(val(j0 + tx, i)));
             rmax[ty][tx] = mx;
         } else {
-            // rows j0 + ty + 8 r, lanes walk i
             for (int r = 0; r < 4; ++r) {
                 float m2 = 0.f;
                 for (int64_t i = tx; i < n; i += 32) m2 = fmaxf(m2, fabsf(val(j0 + ty + 8 * r, i)));
@@ -93,33 +148,20 @@ __global__ void __launch_bounds__(256) operand_kernel(const float *__restrict__ 
             } else {
                 m = tile[tx][0];
             }
-            int e = 0;
-            if (m > 0.f) {
-                // smallest e with m <= 2^e (m = f 2^e, f in [0.5, 1); f = 0.5 means m = 2^(e-1))
-                const float f = frexpf(m, &e);
-                if (f == 0.5f) e -= 1;
-            }
+            const int e = row_exp(m);
             rexp[tx] = e;
             if (j0 + tx < n) scales[j0 + tx] = ldexpf(1.f, e);
         }
         __syncthreads();
     }
-    (void)e_row;
     const int64_t plane = n * ldp;
     for (int64_t i0 = 0; i0 < ldp; i0 += 32) {
-        // gather X(j0 + jj, i0 + ii) into tile[jj][ii]
         if (!trans) {
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                int ii = ty + 8 * r;
-                tile[tx][ii] = val(j0 + tx, i0 + ii);   // coalesced along j (tx)
-            }
+            for (int r = 0; r < 4; ++r) tile[tx][ty + 8 * r] = val(j0 + tx, i0 + ty + 8 * r);
         } else {
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                int jj = ty + 8 * r;
-                tile[jj][tx] = val(j0 + jj, i0 + tx);   // coalesced along i (tx)
-            }
+            for (int r = 0; r < 4; ++r) tile[ty + 8 * r][tx] = val(j0 + ty + 8 * r, i0 + tx);
         }
         __syncthreads();
 #pragma unroll
@@ -129,15 +171,7 @@ __global__ void __launch_bounds__(256) operand_kernel(const float *__restrict__ 
             if (j >= n) continue;
             const float x = tile[jj][tx];
             if (kSplit) {
-                const float y = ldexpf(x, lead_bits - rexp[jj]);   // |y| < 2^w, exact
-                const float d1 = rintf(y);
-                const float y2 = (y - d1) * 256.f;                  // exact
-                const float d2 = rintf(y2);
-                const float d3 = rintf((y2 - d2) * 256.f);
-                const int64_t o = j * ldp + i;
-                slices[o] = __float2bfloat16_rn(d1);
-                slices[plane + o] = __float2bfloat16_rn(d2 * (1.f / 256.f));
-                slices[2 * plane + o] = __float2bfloat16_rn(d3 * (1.f / 65536.f));
+                write_digits(x, lead_bits, rexp[jj], planes, slices + j * ldp + i, plane);
             } else {
                 uint32_t t;
                 asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(x));
@@ -158,6 +192,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -169,13 +206,31 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: gives up after ~2^22 polls with back-off (well over a second) or
-// as soon as another thread of the CTA has given up.
+// try_wait with a suspend-time hint: the thread sleeps in hardware until the
+// phase completes or about hint_ns pass, without spending issue slots.
+__device__ __forceinline__ bool mbar_try_wait_hint(uint32_t bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait.  mbarrier.try_wait suspends the thread in hardware until the
+// phase completes or a short time limit passes, so the loop needs no sleep (a
+// software sleep would add its wake-up latency to every pipeline hand-off).
+// Gives up after ~4e9 SM cycles (about two seconds) or as soon as another thread
+// of the CTA has given up.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
-    for (uint32_t it = 0; it < (1u << 22); ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_try_wait_hint(bar, parity, 100000u)) return true;
         if (*abort_flag) return false;
-        if (it > 64) __nanosleep(256);
+        if (clock64() - t0 > 4000000000LL) break;
     }
     *abort_flag = 1;
     return false;
@@ -205,9 +260,9 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
     return d;
 }
 
-template <int kKind>   // 0 = f16 (bf16 inputs), 1 = tf32
+template <bool kTf32>
 __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
-    if (kKind == 0)
+    if (!kTf32)
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
@@ -242,69 +297,102 @@ __host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t M, uint
     return (1u << 4) | (fmt << 7) | (fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
 
-constexpr int kBM = 128, kBN = 128;
+constexpr int kBM = 128;
+constexpr int kThreads = 192;
 
-template <int kKind>
-struct TcCfg;
-template <>
-struct TcCfg<0> {   // bf16x3: 64 bf16 (128 B) per row per stage, 3 planes
-    static constexpr int kBKElems = 64;
-    static constexpr int kPlanes = 3;
-    static constexpr int kStages = 2;
-    static constexpr int kTileBytes = kBM * 128;                 // one plane tile
-    static constexpr int kStageBytes = 2 * kPlanes * kTileBytes; // A + B
-    static constexpr int kTmemCols = 256;                        // hi + lo accumulators
-    static constexpr int kMmaK = 16;
-};
-template <>
-struct TcCfg<1> {   // tf32: 32 floats (128 B) per row per stage
-    static constexpr int kBKElems = 32;
-    static constexpr int kPlanes = 1;
-    static constexpr int kStages = 4;
-    static constexpr int kTileBytes = kBM * 128;
-    static constexpr int kStageBytes = 2 * kPlanes * kTileBytes;
-    static constexpr int kTmemCols = 128;
-    static constexpr int kMmaK = 8;
+template <int kMode>   // 0 = split bf16 x3, 1 = tf32, 2 = split bf16 x4
+struct Cfg {
+    static constexpr bool kTf32 = kMode == 1;
+    static constexpr int kPlanes = kMode == 0 ? 3 : (kMode == 1 ? 1 : 4);
+    static constexpr int kBN = kMode == 2 ? 64 : 128;
+    static constexpr int kBKElems = kTf32 ? 32 : 64;       // 128 bytes per row
+    static constexpr int kMmaK = kTf32 ? 8 : 16;            // 32 bytes per MMA k step
+    static constexpr int kATile = kBM * 128;                // one plane of A
+    static constexpr int kBTile = kBN * 128;                // one plane of B
+    static constexpr int kStageBytes = kPlanes * (kATile + kBTile);
+    static constexpr int kStages = kTf32 ? 6 : 2;
+    static constexpr int kAccCols = kTf32 ? kBN : 2 * kBN;  // hi (+ lo)
+    static constexpr int kTmemCols = 2 * kAccCols;          // double buffer
+    static constexpr int kSmem = kStages * kStageBytes + 1024 + 512;
 };
 
-template <int kKind>
-constexpr int tc_smem_bytes() {
-    return TcCfg<kKind>::kStages * TcCfg<kKind>::kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
-}
+// Tile t of the schedule, in closed form.  Full grid: grouped raster (8 tile
+// rows per group, column-major inside a group, so concurrently running CTAs share
+// A and B panels).  Symmetric: the upper triangle tm <= tn in row-major order.
+struct TileWalk {
+    int tiles_m, tiles_n, symmetric;
+    __device__ int count() const {
+        return symmetric ? tiles_m * (tiles_m + 1) / 2 : tiles_m * tiles_n;
+    }
+    __device__ void coords(int t, int &tm, int &tn) const {
+        if (symmetric) {
+            // row r starts at off(r) = r T - r (r - 1) / 2
+            const int T = tiles_m;
+            const double b = 2.0 * T + 1.0;
+            int r = (int)((b - sqrt(b * b - 8.0 * t)) * 0.5);
+            if (r < 0) r = 0;
+            while (r > 0 && r * T - r * (r - 1) / 2 > t) --r;
+            while (r + 1 < T && (r + 1) * T - (r + 1) * r / 2 <= t) ++r;
+            tm = r;
+            tn = r + (t - (r * T - r * (r - 1) / 2));
+            return;
+        }
+        const int G = 8;
+        const int per_group = G * tiles_n;
+        const int group = t / per_group;
+        const int first = group * G;
+        const int gm = min(G, tiles_m - first);
+        const int rr = t - group * per_group;
+        tm = first + rr % gm;
+        tn = rr / gm;
+    }
+};
 
-template <int kKind>
-__global__ void __launch_bounds__(128, 1)
+template <int kMode>
+__global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcGemmArgs g) {
-    using Cfg = TcCfg<kKind>;
+    using C = Cfg<kMode>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *gbase = smem_raw + (base - raw);
-    const uint32_t bar_base = base + Cfg::kStages * Cfg::kStageBytes;
+    const uint32_t bar_base = base + C::kStages * C::kStageBytes;
     auto full_bar = [&](int s) { return bar_base + 8u * s; };
-    auto empty_bar = [&](int s) { return bar_base + 8u * (Cfg::kStages + s); };
-    const uint32_t done_bar = bar_base + 8u * (2 * Cfg::kStages);
-    volatile uint32_t *tmem_holder = (volatile uint32_t *)(gbase + Cfg::kStages * Cfg::kStageBytes + 8 * (2 * Cfg::kStages + 1));
-    volatile int *abort_flag = (volatile int *)(tmem_holder + 1);
+    auto empty_bar = [&](int s) { return bar_base + 8u * (C::kStages + s); };
+    auto tfull_bar = [&](int b) { return bar_base + 8u * (2 * C::kStages + b); };
+    auto tempty_bar = [&](int b) { return bar_base + 8u * (2 * C::kStages + 2 + b); };
+    uint8_t *misc = gbase + C::kStages * C::kStageBytes + 8 * (2 * C::kStages + 4);
+    volatile uint32_t *tmem_holder = (volatile uint32_t *)misc;
+    volatile int *abort_flag = (volatile int *)(misc + 4);
+    volatile uint32_t *issued_cnt = (volatile uint32_t *)(misc + 8);
+    volatile uint32_t *consumed_cnt = (volatile uint32_t *)(misc + 12);
+    double *wred = (double *)(misc + 16);   // [4 warps][4 reductions]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t m0 = (int64_t)blockIdx.y * kBM, n0 = (int64_t)blockIdx.x * kBN;
-    const int num_k = (int)(g.ldp / Cfg::kBKElems);
+    const int64_t n = g.n;
+    const int num_k = (int)(g.ldp / C::kBKElems);
+    TileWalk walk{(int)((n + kBM - 1) / kBM), (int)((n + C::kBN - 1) / C::kBN), g.symmetric};
+    const int total_tiles = walk.count();
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < Cfg::kStages; ++s) {
+        for (int s = 0; s < C::kStages; ++s) {
             mbar_init(full_bar(s), 1);
             mbar_init(empty_bar(s), 1);
         }
-        mbar_init(done_bar, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull_bar(b), 1);
+            mbar_init(tempty_bar(b), 4);
+        }
         *abort_flag = 0;
+        *issued_cnt = 0;
+        *consumed_cnt = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32((const void *)tmem_holder)),
-                     "r"(Cfg::kTmemCols));
+                     "r"(C::kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     tc_fence_before();
@@ -312,121 +400,191 @@ __global__ void __launch_bounds__(128, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_holder;
 
-    int issued = 0;   // producer: number of k-blocks whose loads were issued
-    if (threadIdx.x == 0) {
-        // ---------------- TMA producer
-        for (int kb = 0; kb < num_k; ++kb) {
-            const int s = kb % Cfg::kStages;
-            if (kb >= Cfg::kStages) {
-                if (!mbar_wait(empty_bar(s), ((kb / Cfg::kStages) - 1) & 1, abort_flag)) break;
-            }
-            const uint32_t sa = base + s * Cfg::kStageBytes;
-            const uint32_t sb = sa + Cfg::kPlanes * Cfg::kTileBytes;
-            mbar_expect_tx(full_bar(s), Cfg::kStageBytes);
-            const int kc = kb * Cfg::kBKElems;
-            tma_load_3d(sa, &mapA, kc, (int)m0, 0, full_bar(s));
-            tma_load_3d(sb, &mapB, kc, (int)n0, 0, full_bar(s));
-            issued = kb + 1;
-        }
-    } else if (threadIdx.x == 32) {
-        // ---------------- MMA issuer
-        constexpr uint32_t idesc = make_idesc(kKind == 0 ? 1u : 2u, kBM, kBN);
-        const uint32_t d_hi = tmem, d_lo = tmem + 128;
-        bool ok = true;
-        for (int kb = 0; kb < num_k && ok; ++kb) {
-            const int s = kb % Cfg::kStages;
-            if (!mbar_wait(full_bar(s), (kb / Cfg::kStages) & 1, abort_flag)) {
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-            const uint32_t sa = base + s * Cfg::kStageBytes;
-            const uint32_t sb = sa + Cfg::kPlanes * Cfg::kTileBytes;
-#pragma unroll
-            for (int kk = 0; kk < Cfg::kBKElems / Cfg::kMmaK; ++kk) {
-                const uint32_t koff = kk * Cfg::kMmaK * (kKind == 0 ? 2 : 4);   // bytes along K
-                const uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
-                if (kKind == 0) {
-                    const uint64_t ah = desc_sw128(sa + koff), am = desc_sw128(sa + Cfg::kTileBytes + koff),
-                                   al = desc_sw128(sa + 2 * Cfg::kTileBytes + koff);
-                    const uint64_t bh = desc_sw128(sb + koff), bm = desc_sw128(sb + Cfg::kTileBytes + koff),
-                                   bl = desc_sw128(sb + 2 * Cfg::kTileBytes + koff);
-                    mma<0>(d_hi, ah, bh, idesc, acc0);
-                    mma<0>(d_lo, ah, bm, idesc, acc0);
-                    mma<0>(d_lo, am, bh, idesc, 1u);
-                    mma<0>(d_lo, ah, bl, idesc, 1u);
-                    mma<0>(d_lo, al, bh, idesc, 1u);
-                    mma<0>(d_lo, am, bm, idesc, 1u);
-                } else {
-                    mma<1>(d_hi, desc_sw128(sa + koff), desc_sw128(sb + koff), idesc, acc0);
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer
+            uint32_t it = 0;
+            for (int t = blockIdx.x; t < total_tiles && !*abort_flag; t += gridDim.x) {
+                int tm, tn;
+                walk.coords(t, tm, tn);
+                for (int kb = 0; kb < num_k; ++kb, ++it) {
+                    const int s = it % C::kStages;
+                    if (it >= (uint32_t)C::kStages &&
+                        !mbar_wait(empty_bar(s), ((it / C::kStages) - 1) & 1, abort_flag))
+                        break;
+                    const uint32_t sa = base + s * C::kStageBytes;
+                    const uint32_t sb = sa + C::kPlanes * C::kATile;
+                    mbar_expect_tx(full_bar(s), C::kStageBytes);
+                    tma_load_3d(sa, &mapA, kb * C::kBKElems, tm * kBM, 0, full_bar(s));
+                    tma_load_3d(sb, &mapB, kb * C::kBKElems, tn * C::kBN, 0, full_bar(s));
+                    *issued_cnt = it + 1;
                 }
             }
-            mma_commit(empty_bar(s));   // frees the stage when these MMAs complete
         }
-        mma_commit(done_bar);           // accumulators final (or the loop gave up)
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer
+            constexpr uint32_t idesc = make_idesc(C::kTf32 ? 2u : 1u, kBM, C::kBN);
+            uint32_t it = 0, tcount = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+                int tm, tn;
+                walk.coords(t, tm, tn);
+                const int buf = tcount & 1;
+                if (tcount >= 2 && !mbar_wait(tempty_bar(buf), ((tcount >> 1) - 1) & 1, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d_hi = tmem + buf * C::kAccCols, d_lo = d_hi + C::kBN;
+                for (int kb = 0; kb < num_k; ++kb, ++it) {
+                    const int s = it % C::kStages;
+                    if (!mbar_wait(full_bar(s), (it / C::kStages) & 1, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    *consumed_cnt = it + 1;
+                    tc_fence_after();
+                    const uint32_t sa = base + s * C::kStageBytes;
+                    const uint32_t sb = sa + C::kPlanes * C::kATile;
+#pragma unroll
+                    for (int kk = 0; kk < C::kBKElems / C::kMmaK; ++kk) {
+                        const uint32_t koff = kk * 32;
+                        const uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
+                        if constexpr (C::kTf32) {
+                            mma<true>(d_hi, desc_sw128(sa + koff), desc_sw128(sb + koff), idesc, acc0);
+                        } else {
+                            uint64_t ad[C::kPlanes], bd[C::kPlanes];
+#pragma unroll
+                            for (int p = 0; p < C::kPlanes; ++p) {
+                                ad[p] = desc_sw128(sa + p * C::kATile + koff);
+                                bd[p] = desc_sw128(sb + p * C::kBTile + koff);
+                            }
+                            mma<false>(d_hi, ad[0], bd[0], idesc, acc0);
+                            mma<false>(d_lo, ad[0], bd[1], idesc, acc0);
+                            mma<false>(d_lo, ad[1], bd[0], idesc, 1u);
+                            mma<false>(d_lo, ad[0], bd[2], idesc, 1u);
+                            mma<false>(d_lo, ad[2], bd[0], idesc, 1u);
+                            mma<false>(d_lo, ad[1], bd[1], idesc, 1u);
+                            if constexpr (C::kPlanes == 4) {
+                                mma<false>(d_lo, ad[0], bd[3], idesc, 1u);
+                                mma<false>(d_lo, ad[3], bd[0], idesc, 1u);
+                                mma<false>(d_lo, ad[1], bd[2], idesc, 1u);
+                                mma<false>(d_lo, ad[2], bd[1], idesc, 1u);
+                            }
+                        }
+                    }
+                    mma_commit(empty_bar(s));   // frees the stage when these MMAs complete
+                }
+                if (!ok) break;
+                mma_commit(tfull_bar(buf));     // accumulator buffer ready for the epilogue
+                ++tcount;
+            }
+        }
+    } else {
+        // ---------------- epilogue warps 2..5: TMEM lanes 32 (warp % 4) ..
+        const int q = warp & 3;
+        const int row = 32 * q + lane;
+        double total[4] = {0.0, 0.0, 0.0, 0.0};
+        uint32_t tcount = 0;
+        for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+            int tm, tn;
+            walk.coords(t, tm, tn);
+            const int buf = tcount & 1;
+            // one lane polls (with back-off: the main loop of a tile takes tens of
+            // microseconds) so the waiting warps leave the issue slots to the TMA
+            // and MMA warps
+            int waited = 0;
+            if (lane == 0) waited = mbar_wait(tfull_bar(buf), (tcount >> 1) & 1, abort_flag) ? 1 : 0;
+            waited = __shfl_sync(0xffffffffu, waited, 0);
+            if (!waited || *abort_flag) break;
+            tc_fence_after();
+            const int64_t j = (int64_t)tm * kBM + row;
+            const bool jok = j < n;
+            const float rs = jok ? (C::kTf32 ? 1.f : ldexpf(g.scaleA[j], -2 * g.lead_bits)) : 0.f;
+            const uint32_t taddr = tmem + buf * C::kAccCols + ((uint32_t)(32 * q) << 16);
+            double tile_acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 1
+            for (int c0 = 0; c0 < C::kBN; c0 += 16) {
+                uint32_t hi[16], lo[16];
+                tmem_ld16(taddr + c0, hi);
+                if (!C::kTf32) tmem_ld16(taddr + C::kBN + c0, lo);
+                tmem_wait_ld();
+                const int64_t k0 = (int64_t)tn * C::kBN + c0;
+                float v[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    float x = __uint_as_float(hi[c]);
+                    if (!C::kTf32) {
+                        const int64_t k = k0 + c;
+                        x = (x + __uint_as_float(lo[c])) * (k < n ? g.scaleB[k] : 0.f);
+                    }
+                    v[c] = x * rs;
+                }
+                if (g.C && jok) {
+#pragma unroll
+                    for (int c = 0; c < 16; ++c)
+                        if (k0 + c < n) g.C[j * n + k0 + c] = v[c];
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    if (r >= g.nred) break;
+                    const float *W = g.red[r].W;
+                    const double *bv = g.red[r].b;
+                    const int tW = g.red[r].transW, pw = g.red[r].pow;
+                    float part = 0.f;
+                    if (jok) {
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) {
+                            const int64_t k = k0 + c;
+                            if (k >= n) continue;
+                            float w = bv ? (float)bv[k] : 1.f;
+                            if (W) w *= tW ? W[k * n + j] : W[j * n + k];
+                            const float x = pw == 2 ? v[c] * v[c] : v[c];
+                            part = fmaf(x, w, part);
+                        }
+                    }
+                    tile_acc[r] += (double)part;
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty_bar(buf));
+            const double wgt = (g.symmetric && tm != tn) ? 2.0 : 1.0;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                if (r >= g.nred) break;
+                const double aj = (g.red[r].a && jok) ? g.red[r].a[j] : 1.0;
+                total[r] += tile_acc[r] * aj * wgt;
+            }
+            ++tcount;
+        }
+        // reduce the four epilogue warps' partial sums
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const double s = warp_sum(total[r]);
+            if (lane == 0) wred[(warp - 2) * 4 + r] = s;
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (warp == 2 && lane < g.nred && !*abort_flag) {
+            const double s = wred[lane] + wred[4 + lane] + wred[8 + lane] + wred[12 + lane];
+            atomicAdd(g.red[lane].out, s);
+        }
     }
     __syncwarp();
-
-    // ---------------- epilogue: warp w owns TMEM lanes (tile rows) 32w .. 32w + 31
-    const bool waited = mbar_wait(done_bar, 0, abort_flag);
-    // tcgen05.ld is warp-collective: decide per warp
-    const bool good = __all_sync(0xffffffffu, waited && !*abort_flag);
-    tc_fence_after();
-    const int64_t j = m0 + warp * 32 + lane;
-    double red = 0.0;
-    if (good) {
-        const float rs = (j < g.n) ? ((kKind == 0) ? ldexpf(g.scaleA[j], -2 * g.lead_bits) : 1.f) : 0.f;
-        const float aj = (g.a && j < g.n) ? (float)g.a[j] : 1.f;
-        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll 1
-        for (int c0 = 0; c0 < kBN; c0 += 16) {
-            uint32_t hi[16], lo[16];
-            tmem_ld16(lane_addr + c0, hi);
-            if (kKind == 0) tmem_ld16(lane_addr + 128 + c0, lo);
-            tmem_wait_ld();
-            float part = 0.f;
-#pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                const int64_t k = n0 + c0 + c;
-                float v = __uint_as_float(hi[c]);
-                if (kKind == 0) v = (v + __uint_as_float(lo[c])) * g.scaleB[k < g.n ? k : 0];
-                v *= rs;
-                if (g.C) {
-                    if (j < g.n && k < g.n) g.C[j * g.n + k] = v;
-                } else if (j < g.n && k < g.n) {
-                    float w = g.b ? (float)g.b[k] : 1.f;
-                    if (g.W) w *= g.transW ? g.W[k * g.n + j] : g.W[j * g.n + k];
-                    part = fmaf(v, w, part);
-                }
-            }
-            red += (double)part;
-        }
-        red *= (double)aj;
-    }
-    const bool failed = __syncthreads_or(!good);
-    if (failed) {
-        if (threadIdx.x == 0 && g.err) atomicExch(g.err, 1);
-        // wait (bounded) for this CTA's copies in flight before the smem goes away
-        if (threadIdx.x == 0) {
-            volatile int dummy = 0;
-            for (int kb = 0; kb < issued; ++kb) {
-                const int s = kb % Cfg::kStages;
-                // a stage is in flight if it was issued and never consumed; try each once
-                for (int it = 0; it < (1 << 20); ++it)
-                    if (mbar_try_wait(full_bar(s), (kb / Cfg::kStages) & 1)) break;
-            }
-            (void)dummy;
-        }
-    }
-    if (!g.C) {
-        red = block_sum(red);
-        if (threadIdx.x == 0 && !failed) atomicAdd(g.red, red);
-    }
     tc_fence_before();
+    __syncthreads();
+    if (*abort_flag && threadIdx.x == 0) {
+        if (g.err) atomicExch(g.err, 1);
+        // wait (bounded) for copies issued but never consumed before the smem goes away
+        for (uint32_t i = *consumed_cnt; i < *issued_cnt; ++i)
+            for (int it = 0; it < (1 << 20); ++it)
+                if (mbar_try_wait(full_bar(i % C::kStages), (i / C::kStages) & 1)) break;
+    }
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::kTmemCols));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::kTmemCols));
     }
 }
 
@@ -449,14 +607,14 @@ EncodeTiledFn get_encode() {
     return fn;
 }
 
-// planes x rows x ldp (innermost) tensor, box {128 bytes, 128 rows, planes}.
-bool make_map(CUtensorMap *map, const void *ptr, bool bf16, int planes, int64_t rows, int64_t ldp) {
+// planes x rows x ldp (innermost) tensor, box {128 bytes, box_rows, planes}.
+bool make_map(CUtensorMap *map, const void *ptr, bool bf16, int planes, int64_t rows, int64_t ldp, int box_rows) {
     EncodeTiledFn enc = get_encode();
     if (!enc) return false;
     const int esz = bf16 ? 2 : 4;
     cuuint64_t dims[3] = {(cuuint64_t)ldp, (cuuint64_t)rows, (cuuint64_t)planes};
     cuuint64_t strides[2] = {(cuuint64_t)(ldp * esz), (cuuint64_t)(rows * ldp * esz)};
-    cuuint32_t box[3] = {(cuuint32_t)(128 / esz), 128u, (cuuint32_t)planes};
+    cuuint32_t box[3] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows, (cuuint32_t)planes};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
                      const_cast<void *>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -465,43 +623,68 @@ bool make_map(CUtensorMap *map, const void *ptr, bool bf16, int planes, int64_t 
     return r == CUDA_SUCCESS;
 }
 
-template <int kKind>
-cudaError_t launch_tc(const TcGemmArgs &g, cudaStream_t s) {
+int sm_count() {
+    static int cnt[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 148;
+    if (!cnt[dev]) {
+        int c = 0;
+        if (cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c <= 0) c = 148;
+        cnt[dev] = c;
+    }
+    return cnt[dev];
+}
+
+template <int kMode>
+cudaError_t launch_tc(const TcGemmArgs &g0, cudaStream_t s) {
+    using C = Cfg<kMode>;
+    TcGemmArgs g = g0;
+    if (C::kBN != kBM || g.C) g.symmetric = 0;
+    if (g.nred < 0 || g.nred > 4) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
-    const bool bf16 = kKind == 0;
-    const int planes = bf16 ? 3 : 1;
-    if (!make_map(&ma, g.opA, bf16, planes, g.n, g.ldp) || !make_map(&mb, g.opB, bf16, planes, g.n, g.ldp))
+    const bool bf16 = !C::kTf32;
+    if (!make_map(&ma, g.opA, bf16, C::kPlanes, g.n, g.ldp, kBM) ||
+        !make_map(&mb, g.opB, bf16, C::kPlanes, g.n, g.ldp, C::kBN))
         return cudaErrorInvalidValue;
-    constexpr int smem = tc_smem_bytes<kKind>();
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<kKind>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             C::kSmem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    dim3 grid((unsigned)((g.n + kBN - 1) / kBN), (unsigned)((g.n + kBM - 1) / kBM));
-    tc_gemm_kernel<kKind><<<grid, 128, smem, s>>>(ma, mb, g);
+    const int64_t tm = (g.n + kBM - 1) / kBM, tn = (g.n + C::kBN - 1) / C::kBN;
+    const int64_t tiles = g.symmetric ? tm * (tm + 1) / 2 : tm * tn;
+    const int grid = (int)(tiles < sm_count() ? tiles : sm_count());
+    tc_gemm_kernel<kMode><<<grid, kThreads, C::kSmem, s>>>(ma, mb, g);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_split(const float *M, int trans, const double *u, int64_t n, int64_t ldp, int lead_bits,
-                         void *slices, float *scales, cudaStream_t s) {
-    dim3 grid((unsigned)((n + 31) / 32)), block(32, 8);
-    operand_kernel<true><<<grid, block, 0, s>>>(M, trans, u, n, ldp, lead_bits, (__nv_bfloat16 *)slices, scales,
-                                                nullptr);
+                         int planes, void *slices, float *scales, cudaStream_t s) {
+    if (trans) {
+        split_rows_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(M, u, n, ldp, lead_bits, planes,
+                                                                  (__nv_bfloat16 *)slices, scales);
+    } else {
+        dim3 grid((unsigned)((n + 31) / 32)), block(32, 8);
+        operand_cols_kernel<true><<<grid, block, 0, s>>>(M, 0, u, n, ldp, lead_bits, planes,
+                                                         (__nv_bfloat16 *)slices, scales, nullptr);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_prep(const float *M, int trans, const double *u, int64_t n, int64_t ldp, float *out,
                         cudaStream_t s) {
     dim3 grid((unsigned)((n + 31) / 32)), block(32, 8);
-    operand_kernel<false><<<grid, block, 0, s>>>(M, trans, u, n, ldp, 0, nullptr, nullptr, out);
+    operand_cols_kernel<false><<<grid, block, 0, s>>>(M, trans, u, n, ldp, 0, 1, nullptr, nullptr, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gemm_bf16x3(const TcGemmArgs &g, cudaStream_t s) { return launch_tc<0>(g, s); }
 cudaError_t launch_gemm_tf32(const TcGemmArgs &g, cudaStream_t s) { return launch_tc<1>(g, s); }
+cudaError_t launch_gemm_bf16x4(const TcGemmArgs &g, cudaStream_t s) { return launch_tc<2>(g, s); }
 
 }  // namespace ustat

@@ -89,7 +89,155 @@ __global__ void __launch_bounds__(256) tile_kernel(int mode, TileTerms tt, int64
     }
 }
 
+// Several reductions / GEMVs over the same (untransposed) matrices in one pass:
+// each block owns 512 columns and a slice of the rows; every warp reads whole
+// 512-column row segments (float4 when the row length allows it) of each
+// distinct matrix once and evaluates every operation on them.  Operation o
+// multiplies matrix m ex[o][m] times (the terms of a merged factor).
+template <typename T, bool kVec>
+__global__ void __launch_bounds__(256) mhb_kernel(MhbArgs g) {
+    constexpr int CB = 512;
+    __shared__ T bsm[kMhbOps][CB];
+    __shared__ float colred[8][CB];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t n = g.n;
+    const int64_t j0 = (int64_t)blockIdx.x * CB;
+    auto col = [&](int c) -> int { return kVec ? (4 * lane + 128 * (c >> 2) + (c & 3)) : (lane + 32 * c); };
+    for (int o = 0; o < g.nops; ++o)
+        for (int c = threadIdx.x; c < CB; c += 256) {
+            const int64_t j = j0 + c;
+            const double *bv = g.op[o].kind == TILE_FREDUCE ? g.op[o].b : nullptr;
+            bsm[o][c] = j < n ? (bv ? (T)bv[j] : T(1)) : T(0);
+        }
+    __syncthreads();
+    double facc[kMhbOps];
+    float gacc[kMhbGemv][16];
+#pragma unroll
+    for (int o = 0; o < kMhbOps; ++o) facc[o] = 0.0;
+#pragma unroll
+    for (int q = 0; q < kMhbGemv; ++q)
+#pragma unroll
+        for (int c = 0; c < 16; ++c) gacc[q][c] = 0.f;
+    for (int64_t i = (int64_t)blockIdx.y * 8 + warp; i < n; i += (int64_t)gridDim.y * 8) {
+        T vals[kMhbMats][16];
+#pragma unroll
+        for (int m = 0; m < kMhbMats; ++m) {
+            if (m >= g.nmat) break;
+            const T *row = (const T *)g.M[m] + i * n;
+            if constexpr (kVec) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int64_t j = j0 + 4 * lane + 128 * q;
+                    if (j + 3 < n) {
+                        const float4 v = *reinterpret_cast<const float4 *>(row + j);
+                        vals[m][4 * q + 0] = v.x;
+                        vals[m][4 * q + 1] = v.y;
+                        vals[m][4 * q + 2] = v.z;
+                        vals[m][4 * q + 3] = v.w;
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) vals[m][4 * q + e] = (j + e < n) ? row[j + e] : T(0);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const int64_t j = j0 + col(c);
+                    vals[m][c] = j < n ? row[j] : T(0);
+                }
+            }
+        }
+        int gi = 0;
+#pragma unroll
+        for (int o = 0; o < kMhbOps; ++o) {
+            if (o >= g.nops) break;
+            const double ai = g.op[o].a ? g.op[o].a[i] : 1.0;
+            T p[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) p[c] = T(1);
+#pragma unroll
+            for (int m = 0; m < kMhbMats; ++m) {
+                const int e = g.op[o].ex[m];
+                for (int r = 0; r < e; ++r)
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) p[c] *= vals[m][c];
+            }
+            if (g.op[o].kind == TILE_FREDUCE) {
+                T s = 0;
+#pragma unroll
+                for (int c = 0; c < 16; ++c) s = fma(p[c], bsm[o][col(c)], s);
+                facc[o] += (double)s * ai;
+            } else {
+                const float af = (float)ai;
+#pragma unroll
+                for (int q = 0; q < kMhbGemv; ++q)
+                    if (q == gi) {
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) gacc[q][c] = fmaf(af, (float)p[c], gacc[q][c]);
+                    }
+                ++gi;
+            }
+        }
+    }
+    // FREDUCE: block sums
+#pragma unroll
+    for (int o = 0; o < kMhbOps; ++o) {
+        if (o >= g.nops) break;
+        if (g.op[o].kind != TILE_FREDUCE) continue;
+        const double s = block_sum(facc[o]);
+        if (threadIdx.x == 0) atomicAdd(g.op[o].out, s);
+    }
+    // GEMV: column sums across the 8 warps
+    int gi = 0;
+    for (int o = 0; o < g.nops; ++o) {
+        if (g.op[o].kind != TILE_GEMV) continue;
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kMhbGemv; ++q)
+            if (q == gi) {
+#pragma unroll
+                for (int c = 0; c < 16; ++c) colred[warp][col(c)] = gacc[q][c];
+            }
+        __syncthreads();
+        for (int c = threadIdx.x; c < CB; c += 256) {
+            const int64_t j = j0 + c;
+            if (j >= n) continue;
+            double s = 0.0;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) s += (double)colred[w][c];
+            atomicAdd(g.op[o].out + j, s);
+        }
+        ++gi;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_mhb(const MhbArgs &g0, bool fp64, cudaStream_t s) {
+    MhbArgs g = g0;
+    if (g.nmat < 1 || g.nmat > kMhbMats || g.nops < 1 || g.nops > kMhbOps) return cudaErrorInvalidValue;
+    int ngemv = 0;
+    for (int o = 0; o < g.nops; ++o) {
+        for (int m = 0; m < kMhbMats; ++m) g.op[o].ex[m] = 0;
+        for (int t = 0; t < g.op[o].nt; ++t) {
+            const int m = g.op[o].mat[t];
+            if (m < 0 || m >= g.nmat) return cudaErrorInvalidValue;
+            g.op[o].ex[m]++;
+        }
+        if (g.op[o].kind == TILE_GEMV) ++ngemv;
+    }
+    if (ngemv > kMhbGemv) return cudaErrorInvalidValue;
+    const int64_t gx = (g.n + 511) / 512;
+    int64_t gy = (2 * 152 + gx - 1) / gx;
+    const int64_t maxgy = (g.n + 7) / 8;
+    if (gy > maxgy) gy = maxgy;
+    if (gy < 1) gy = 1;
+    dim3 grid((unsigned)gx, (unsigned)gy);
+    if (fp64) mhb_kernel<double, false><<<grid, 256, 0, s>>>(g);
+    else if (g.n % 4 == 0) mhb_kernel<float, true><<<grid, 256, 0, s>>>(g);
+    else mhb_kernel<float, false><<<grid, 256, 0, s>>>(g);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_tile_op(int mode, const TileTerms &tt, bool fp64, int64_t n, const double *a, const double *b,
                            void *out, cudaStream_t s) {

@@ -35,18 +35,49 @@ struct TileTerms {
 cudaError_t launch_tile_op(int mode, const TileTerms &tt, bool fp64, int64_t n, const double *a,
                            const double *b, void *out, cudaStream_t s);
 
+// ---- several reductions / GEMVs over the same matrices in one pass (k_hb.cu)
+// Every term is read untransposed (value(i, j) = M[i][j]).
+//   FREDUCE: *out += sum_ij prod_t M_t(i,j) a(i) b(j)
+//   GEMV   : out(j) += sum_i a(i) prod_t M_t(i,j)
+constexpr int kMhbMats = 4, kMhbOps = 6, kMhbGemv = 2;
+struct MhbOp {
+    int kind;             // TILE_FREDUCE or TILE_GEMV
+    int nt;
+    int mat[4];           // indices into MhbArgs::M
+    int ex[4];            // filled by launch_mhb: multiplicity of each matrix
+    const double *a, *b;
+    double *out;
+};
+struct MhbArgs {
+    int64_t n;
+    int nmat;
+    const void *M[kMhbMats];
+    int nops;
+    MhbOp op[kMhbOps];
+};
+cudaError_t launch_mhb(const MhbArgs &g, bool fp64, cudaStream_t s);
+
 // ---- SIMT GEMMs in float32 / float64 (k_gemm_simt.cu)
+// One fused reduction: *out += sum_jk C(j,k)^pow W(j,k) a(j) b(k)
+struct SimtRed {
+    const void *W;
+    int transW;
+    const double *a, *b;
+    int pow;
+    double *out;
+};
 struct SimtGemmArgs {
     int64_t n;
     const void *A;  int transA;     // A(i, j)
     const void *B;  int transB;     // B(i, k)
     const double *u;                // along i, may be null
     // epilogue
-    void *C;                        // store mode: C(j, k), row-major n x n
-    double *red;                    // reduce mode: *red += sum ...
-    const void *W;  int transW;     // weight W(j, k), may be null
-    const double *a, *b;            // along j / k, may be null
-    // GEMM3 (batched over index bb): u'(i) = u(i) Ab(i, bb); weights Wbc(bb, j), Wbd(bb, k), ub(bb)
+    void *C;                        // stored product C(j, k), row-major n x n (may be null)
+    int nred;                       // fused reductions (0..4)
+    SimtRed red[4];
+    int symmetric;                  // C = C^T, reductions symmetric: upper tiles only
+    // GEMM3 (batched over index bb; one reduction red[0]): u'(i) = u(i) Ab(i, bb),
+    // extra weights Wbc(bb, j), Wbd(bb, k), ub(bb)
     const void *Ab; int transAb;
     const void *Wbc; int transWbc;
     const void *Wbd; int transWbd;
@@ -74,25 +105,36 @@ cudaError_t launch_combine(const CombineTable &tab, const double *scal, const in
 // digits of the leading bf16 slice for a contraction of length K (exact integer
 // accumulation of the leading product needs K * 4^w1 <= 2^24)
 int split_lead_bits(int64_t K);
-// Operand X(j, i) = M(i, j) u(i) (term orientation trans), written K-major:
-//   bf16x3 slices [3][n][ldp] plus float row scales [n]       (launch_split)
-//   float32 tf32-rounded copy [n][ldp]                        (launch_prep)
+// Operand X(j, i) = M(i, j) u(i) (trans = 0: column j of M; trans = 1: row j),
+// written K-major:
+//   split bf16: `planes` slices [planes][n][ldp] plus float row scales [n]  (launch_split)
+//   float32 tf32-rounded copy [n][ldp]                                        (launch_prep)
 cudaError_t launch_split(const float *M, int trans, const double *u, int64_t n, int64_t ldp,
-                         int lead_bits, void *slices, float *scales, cudaStream_t s);
+                         int lead_bits, int planes, void *slices, float *scales, cudaStream_t s);
 cudaError_t launch_prep(const float *M, int trans, const double *u, int64_t n, int64_t ldp,
                         float *out, cudaStream_t s);
+// One fused reduction of the product C: *out += sum_jk C(j,k)^pow W(j,k) a(j) b(k)
+// (W, a, b may be null = all ones; W read with orientation transW).
+struct TcRed {
+    const float *W;
+    int transW;
+    const double *a, *b;
+    int pow;
+    double *out;
+};
 struct TcGemmArgs {
     int64_t n, ldp;
     const void *opA; const float *scaleA;   // K-major operand of A (slices or prep)
     const void *opB; const float *scaleB;
     int lead_bits;
-    float *C;                                // store mode
-    double *red;                             // reduce mode
-    const float *W; int transW;
-    const double *a, *b;
+    float *C;                                // stored product (may be null)
+    int nred;                                // fused reductions (0..4)
+    TcRed red[4];
+    int symmetric;                           // C = C^T and every reduction symmetric
     int *err;                                // device error word (bounded waits)
 };
 cudaError_t launch_gemm_bf16x3(const TcGemmArgs &g, cudaStream_t s);
+cudaError_t launch_gemm_bf16x4(const TcGemmArgs &g, cudaStream_t s);
 cudaError_t launch_gemm_tf32(const TcGemmArgs &g, cudaStream_t s);
 
 }  // namespace ustat

@@ -33,7 +33,7 @@ namespace ustat {
 const char *op_name(int k) {
     static const char *names[] = {"kbuild", "loadmat", "unary",  "loadvec", "diag",
                                   "vmul",   "hadamard", "gemv",  "vsum",    "gemm",
-                                  "gemm_red", "freduce", "gemm3", "split",  "prep"};
+                                  "gemm_red", "freduce", "gemm3", "split",  "prep", "mhb"};
     return (k >= 0 && k < OP_COUNT) ? names[k] : "?";
 }
 
@@ -376,7 +376,7 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan) {
     if (g->n_edges < 0 || g->n_unary < 0) return USTAT_ERR_INVALID_ARG;
     if (g->n_edges > 0 && (!g->edge_src || !g->edge_dst || !g->edge_factor)) return USTAT_ERR_INVALID_ARG;
     if (g->n_unary > 0 && (!g->unary_vertex || !g->unary_factor)) return USTAT_ERR_INVALID_ARG;
-    if (o->precision < USTAT_FP64 || o->precision > USTAT_BF16X3) return USTAT_ERR_INVALID_ARG;
+    if (o->precision < USTAT_FP64 || o->precision > USTAT_BF16X4) return USTAT_ERR_INVALID_ARG;
     if (o->planner != USTAT_PLAN_EXHAUSTIVE && o->planner != USTAT_PLAN_MINFILL) return USTAT_ERR_INVALID_ARG;
     Plan &P = *plan;
     P = Plan();
@@ -407,7 +407,7 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan) {
         if (!covered[v]) return USTAT_ERR_INVALID_ARG;
 
     Lowerer L(P);
-    const bool tc = (P.precision == USTAT_TF32 || P.precision == USTAT_BF16X3);
+    const bool tc = is_tc_mode(P.precision);
 
     // base tensors (Algorithm 1): one per factor id, created lazily
     std::vector<int> base(g->n_factors, -1), diag(g->n_factors, -1);
@@ -783,23 +783,141 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan) {
         P.ops.swap(out);
     }
 
+    // ---- execution form of the n^3 steps: a terminal GEMM_RED is a GEMM that
+    //      stores nothing and carries one fused reduction
+    for (auto &op : P.ops) {
+        if (op.kind != OP_GEMM_RED) continue;
+        Red r;
+        r.W = op.W;
+        r.a = op.a;
+        r.b = op.b;
+        r.pow = 1;
+        r.out = op.out;
+        op.kind = OP_GEMM;
+        op.store = 0;
+        op.nred = 1;
+        op.red[0] = r;
+        op.out = -1;
+    }
+
+    // ---- fuse reductions of a stored product into its GEMM: a product read only
+    //      by reductions sum_jk prod_t F_t(j,k) a(j) b(k) in which it appears once
+    //      or twice (with at most one other factor) is reduced in the GEMM's
+    //      epilogue and never written
+    if (P.cse) {
+        auto uses_slot = [](const Op &o, int s) {
+            for (int t = 0; t < o.nt; ++t)
+                if (o.t[t].mat == s) return true;
+            const Term *ts[] = {&o.A, &o.B, &o.W, &o.Ab, &o.Wbc, &o.Wbd};
+            for (auto *t : ts)
+                if (t->mat == s) return true;
+            for (int r = 0; r < o.nred; ++r)
+                if (o.red[r].W.mat == s) return true;
+            return false;
+        };
+        std::vector<char> dead(P.ops.size(), 0);
+        std::vector<size_t> place(P.ops.size());   // where each op is emitted
+        for (size_t i = 0; i < P.ops.size(); ++i) place[i] = i;
+        for (size_t gi = 0; gi < P.ops.size(); ++gi) {
+            Op &g = P.ops[gi];
+            if (g.kind != OP_GEMM || !g.store || g.out < 0) continue;
+            const int s = g.out;
+            const bool psym = P.slots[s].symmetric != 0;
+            std::vector<size_t> cons;
+            bool ok = true;
+            for (size_t j = 0; j < P.ops.size() && ok; ++j) {
+                if (j == gi || dead[j] || !uses_slot(P.ops[j], s)) continue;
+                const Op &c = P.ops[j];
+                if (c.kind != OP_FREDUCE) {
+                    ok = false;
+                    break;
+                }
+                int np = 0, trans0 = -1, ntrans = 0;
+                for (int t = 0; t < c.nt; ++t)
+                    if (c.t[t].mat == s) {
+                        ++np;
+                        trans0 = c.t[t].trans;
+                        ntrans += c.t[t].trans;
+                    }
+                if (np > 2 || c.nt - np > 1) ok = false;
+                if (np == 2 && ntrans == 1 && !psym) ok = false;
+                (void)trans0;
+                cons.push_back(j);
+            }
+            if (!ok || cons.empty() || g.nred + (int)cons.size() > kMaxRed) continue;
+            for (size_t j : cons) {
+                const Op &c = P.ops[j];
+                Red r;
+                int np = 0, tr = 0;
+                Term other;
+                for (int t = 0; t < c.nt; ++t) {
+                    if (c.t[t].mat == s) {
+                        ++np;
+                        tr = psym ? 0 : c.t[t].trans;
+                    } else {
+                        other = c.t[t];
+                    }
+                }
+                r.pow = np;
+                r.out = c.out;
+                if (!tr) {
+                    r.W = other;
+                    r.a = c.a;
+                    r.b = c.b;
+                } else {
+                    // sum_jk P(k,j) W(j,k) a(j) b(k) = sum_jk P(j,k) W(k,j) a(k) b(j)
+                    r.W = L.flip(other);
+                    r.a = c.b;
+                    r.b = c.a;
+                }
+                g.red[g.nred++] = r;
+                dead[j] = 1;
+                // the reductions' other inputs may be produced after the GEMM: it
+                // runs where its last absorbed reduction stood (nothing reads the
+                // unstored product, so moving it later is safe)
+                place[gi] = std::max(place[gi], j);
+            }
+            g.store = 0;
+        }
+        std::vector<std::vector<size_t>> at(P.ops.size());
+        for (size_t i = 0; i < P.ops.size(); ++i)
+            if (!dead[i]) at[place[i]].push_back(i);
+        std::vector<Op> out;
+        for (size_t p = 0; p < P.ops.size(); ++p)
+            for (size_t i : at[p]) out.push_back(P.ops[i]);
+        P.ops.swap(out);
+    }
+    // symmetric products with symmetric reductions only need tiles on or above
+    // the diagonal
+    for (auto &op : P.ops) {
+        if (op.kind != OP_GEMM || op.store || !(op.A == op.B)) continue;
+        bool sym = op.nred > 0;
+        for (int r = 0; r < op.nred; ++r) {
+            const Red &R = op.red[r];
+            if (R.a != R.b) sym = false;
+            if (R.W.mat >= 0 && !P.slots[R.W.mat].symmetric) sym = false;
+        }
+        op.symmetric = sym ? 1 : 0;
+    }
+
     // ---- operands for the tensor-core GEMMs: K-major copies with the diagonal
     //      scaling of the contracted index folded into A
     if (tc) {
         std::vector<Op> out;
         std::map<std::tuple<int, int, int>, int> opmemo;
+        const bool split = is_split_mode(P.precision);
         auto operand = [&](Term t, int u, std::vector<Op> &dst) {
             auto key = std::make_tuple(t.mat, t.trans, u);
             auto it = opmemo.find(key);
             if (it != opmemo.end()) return it->second;
             Op op;
-            op.kind = (P.precision == USTAT_BF16X3) ? OP_SPLIT : OP_PREP;
+            op.kind = split ? OP_SPLIT : OP_PREP;
             op.t[0] = t;
             op.nt = 1;
             op.u = u;
             op.npow = 2;
             Slot sl;
-            sl.kind = (P.precision == USTAT_BF16X3) ? S_SLICES : S_PREP;
+            sl.kind = split ? S_SLICES : S_PREP;
             P.slots.push_back(sl);
             op.out = (int)P.slots.size() - 1;
             dst.push_back(op);
@@ -807,17 +925,97 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan) {
             return op.out;
         };
         for (auto op : P.ops) {
-            if (op.kind == OP_GEMM || op.kind == OP_GEMM_RED) {
+            if (op.kind == OP_GEMM) {
                 op.opA = operand(op.A, op.u, out);
-                op.opB = operand(op.B, -1, out);
+                op.opB = (op.A == op.B && op.u < 0) ? op.opA : operand(op.B, -1, out);
             }
             out.push_back(op);
         }
         P.ops.swap(out);
     }
     for (auto &op : P.ops) {
-        if (op.kind == OP_GEMM || op.kind == OP_GEMM_RED) P.n_gemm++;
+        if (op.kind == OP_GEMM) {
+            P.n_gemm++;
+            if (op.symmetric) op.coef = 1.0;   // half the tiles: n^3 flops instead of 2 n^3
+        }
         if (op.kind == OP_GEMM3) P.n_gemm3++;
+    }
+
+    // ---- schedule by dependency level and merge the n^2 reductions / GEMVs of
+    //      one level that read the same few matrices into single passes
+    {
+        auto ins = [&](const Op &o) {
+            std::vector<int> v;
+            auto add = [&](int s) {
+                if (s >= 0) v.push_back(s);
+            };
+            for (int t = 0; t < o.nt; ++t) add(o.t[t].mat);
+            add(o.u), add(o.a), add(o.b), add(o.A.mat), add(o.B.mat), add(o.W.mat), add(o.Ab.mat);
+            add(o.Wbc.mat), add(o.Wbd.mat), add(o.ub), add(o.opA), add(o.opB);
+            for (int r = 0; r < o.nred; ++r) add(o.red[r].W.mat), add(o.red[r].a), add(o.red[r].b);
+            return v;
+        };
+        auto outs = [&](const Op &o) {
+            std::vector<int> v;
+            if (o.out >= 0 && (o.kind != OP_GEMM || o.store)) v.push_back(o.out);
+            for (int r = 0; r < o.nred; ++r) v.push_back(o.red[r].out);
+            return v;
+        };
+        std::map<int, int> producer;
+        std::vector<int> level(P.ops.size(), 0);
+        for (size_t i = 0; i < P.ops.size(); ++i) {
+            for (int s : ins(P.ops[i])) {
+                auto it = producer.find(s);
+                if (it != producer.end()) level[i] = std::max(level[i], level[it->second] + 1);
+            }
+            for (int s : outs(P.ops[i])) producer[s] = (int)i;
+        }
+        const bool can_group = P.precision != USTAT_FP64;
+        auto eligible = [&](const Op &o) {
+            if (!can_group || (o.kind != OP_FREDUCE && o.kind != OP_GEMV)) return false;
+            for (int t = 0; t < o.nt; ++t)
+                if (o.t[t].trans && !P.slots[o.t[t].mat].symmetric) return false;
+            return true;
+        };
+        const int maxlev = level.empty() ? 0 : *std::max_element(level.begin(), level.end());
+        std::vector<Op> out;
+        for (int L = 0; L <= maxlev; ++L) {
+            std::vector<Op> hb;
+            for (size_t i = 0; i < P.ops.size(); ++i) {
+                if (level[i] != L) continue;
+                if (eligible(P.ops[i])) hb.push_back(P.ops[i]);
+                else out.push_back(P.ops[i]);
+            }
+            // greedy packing: up to kMhbOps ops, 4 matrices, 2 GEMVs per pass
+            std::vector<char> used(hb.size(), 0);
+            for (size_t s = 0; s < hb.size(); ++s) {
+                if (used[s]) continue;
+                std::vector<Op> grp;
+                std::set<int> mats;
+                int ngemv = 0;
+                for (size_t t = s; t < hb.size(); ++t) {
+                    if (used[t] || grp.size() >= 6) continue;
+                    std::set<int> m2 = mats;
+                    for (int q = 0; q < hb[t].nt; ++q) m2.insert(hb[t].t[q].mat);
+                    const int g2 = ngemv + (hb[t].kind == OP_GEMV);
+                    if (m2.size() > 4 || g2 > 2) continue;
+                    mats = m2;
+                    ngemv = g2;
+                    grp.push_back(hb[t]);
+                    used[t] = 1;
+                }
+                Op m;
+                m.kind = OP_MHB;
+                m.group = (int)P.groups.size();
+                for (auto &g : grp) {
+                    m.coef += g.coef;
+                    m.npow = 2;
+                }
+                P.groups.push_back(grp);
+                out.push_back(m);
+            }
+        }
+        P.ops.swap(out);
     }
     return USTAT_OK;
 }

@@ -40,15 +40,27 @@ enum OpKind : int {
     OP_SPLIT,        // operand out = bf16x3 fixed-point slices of the K-major operand
                      //   X(j, i) = t[0](i, j) u(i)
     OP_PREP,         // operand out = fp32 K-major copy X(j, i) = t[0](i, j) u(i) (tf32-rounded)
+    OP_MHB,          // several FREDUCE / GEMV ops over the same matrices in one pass
     OP_COUNT
 };
 
 const char *op_name(int kind);
 
+// A reduction fused into a GEMM: out += sum_jk C(j,k)^pow W(j,k) a(j) b(k).
+struct Red {
+    Term W;
+    int a = -1, b = -1, pow = 1, out = -1;
+};
+constexpr int kMaxRed = 4;
+
 struct Op {
     int kind = 0;
     int factor = -1;
     int out = -1;                 // slot written
+    int store = 1;                // GEMM: write the product to `out`
+    int nred = 0;                 // GEMM: fused reductions
+    Red red[kMaxRed];
+    int symmetric = 0;            // GEMM: product and reductions symmetric (upper tiles only)
     Term t[kMaxTerms];
     int nt = 0;
     int u = -1, a = -1, b = -1;   // vector slots (-1 = all ones)
@@ -60,6 +72,7 @@ struct Op {
     double flops = 0.0;           // algorithmic flops per unit n-power (set by the planner)
     int npow = 0;                 // flops = coef * n^npow
     double coef = 0.0;
+    int group = -1;               // OP_MHB: index into Plan::groups
 };
 
 enum SlotKind : int { S_MAT = 0, S_VEC, S_SCAL, S_SLICES, S_PREP };
@@ -90,9 +103,14 @@ struct Plan {
     std::vector<int> factor_kind;   // per factor id
     std::vector<Slot> slots;
     std::vector<Op> ops;
+    std::vector<std::vector<Op>> groups;   // members of OP_MHB operations
     std::vector<PartRec> parts;
     int n_gemm = 0, n_gemm3 = 0;
 };
+
+inline bool is_split_mode(int precision) { return precision == USTAT_BF16X3 || precision == USTAT_BF16X4; }
+inline bool is_tc_mode(int precision) { return is_split_mode(precision) || precision == USTAT_TF32; }
+inline int split_planes_of(int precision) { return precision == USTAT_BF16X4 ? 4 : 3; }
 
 // Planner entry (planner.cpp).  Returns a USTAT_* code.
 int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan);

@@ -25,9 +25,9 @@ USTAT_ERR_DEVICE_TIMEOUT = -7
 USTAT_ERR_UNSUPPORTED = -8
 
 RBF, LINEAR, TANH_DOT, MATRIX, VECTOR = 0, 1, 2, 3, 4
-FP64, FP32, TF32, BF16X3 = 0, 1, 2, 3
+FP64, FP32, TF32, BF16X3, BF16X4 = 0, 1, 2, 3, 4
 PLAN_EXHAUSTIVE, PLAN_MINFILL = 0, 1
-PRECISION = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16x3": BF16X3}
+PRECISION = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16x3": BF16X3, "bf16x4": BF16X4}
 
 _P = ctypes.POINTER
 _i = ctypes.c_int
