@@ -176,8 +176,14 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
         ProfScope ps(op.kind, C.st);
         switch (op.kind) {
             case OP_KBUILD:
-                e = launch_kbuild(f[op.factor].kind, f[op.factor].param, C.ws + C.L.xw_off, C.fp64, n, C.d,
-                                  P.sparsify, C.ptr(op.out), C.st);
+                if (!C.fp64 && f[op.factor].kind == USTAT_RBF)
+                    e = launch_kbuild_rbf((const float *)(C.ws + C.L.xw_off), n, C.d, f[op.factor].param, P.sparsify,
+                                          (float *)C.ptr(op.out), op.opA >= 0 ? C.ptr(op.opA) : nullptr,
+                                          C.L.ldp_slices, lead, split_planes_of(P.precision),
+                                          op.opA >= 0 ? C.scales(op.opA) : nullptr, C.st);
+                else
+                    e = launch_kbuild(f[op.factor].kind, f[op.factor].param, C.ws + C.L.xw_off, C.fp64, n, C.d,
+                                      P.sparsify, C.ptr(op.out), C.st);
                 break;
             case OP_LOADMAT:
                 e = launch_loadmat((const double *)f[op.factor].data, n, C.fp64, P.sparsify, C.ptr(op.out), C.st);
@@ -326,20 +332,21 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
         if (e != cudaSuccess) return cuda_fail(e);
     }
     // Moebius combination
-    static thread_local CombineTable tab;
-    tab.nparts = (int)P.parts.size();
-    tab.m = P.m;
-    for (int p = 0; p < tab.nparts; ++p) {
+    static thread_local std::vector<CombineEntry> tab;
+    tab.resize(P.parts.size());
+    for (size_t p = 0; p < P.parts.size(); ++p) {
         const PartRec &pr = P.parts[p];
-        tab.mu[p] = pr.mu;
-        tab.nfree[p] = (unsigned char)pr.nfree;
-        tab.evaluated[p] = (unsigned char)pr.evaluated;
+        CombineEntry &en = tab[p];
+        en.mu = pr.mu;
+        en.nfree = (unsigned char)pr.nfree;
+        en.evaluated = (unsigned char)pr.evaluated;
         for (int q = 0; q < kCombineMaxScal; ++q)
-            tab.sid[p][q] = (q < pr.nscal) ? (unsigned short)C.L.scal_index[pr.scal[q]] : (unsigned short)0xffff;
+            en.sid[q] = (q < pr.nscal) ? (unsigned short)C.L.scal_index[pr.scal[q]] : (unsigned short)0xffff;
     }
     {
         ProfScope ps(kProfCombine, C.st);
-        e = launch_combine(tab, (const double *)(C.ws + C.L.scal_off), err, n, U_out, V_out, C.st);
+        e = launch_combine(tab.data(), (int)tab.size(), P.m, (const double *)(C.ws + C.L.scal_off), err, n, U_out,
+                           V_out, C.st);
     }
     if (e != cudaSuccess) return cuda_fail(e);
     return USTAT_OK;
@@ -552,7 +559,9 @@ extern "C" int ustat_plan_describe(const ustat_plan_t *plan, char *buf, size_t b
                       (m.kind == OP_GEMV ? "u=" + vec(m.u) : "a=" + vec(m.a) + " b=" + vec(m.b)) + ")";
             }
             snprintf(line, sizeof(line), "%zu mhb%s\n", i, ms.c_str());
-        } else
+        } else if (o.kind == OP_KBUILD)
+            snprintf(line, sizeof(line), "%zu kbuild out=%d f=%d slices=%d\n", i, o.out, o.factor, o.opA);
+        else
             snprintf(line, sizeof(line),
                      "%zu %s out=%d f=%d terms=[%s] u=%s a=%s b=%s A=%s B=%s W=%s Ab=%s Wbc=%s Wbd=%s ub=%s\n", i,
                      op_name(o.kind), o.out, o.factor, ts.c_str(), vec(o.u).c_str(), vec(o.a).c_str(),

@@ -1,6 +1,7 @@
 // Tensorization (the paper's Algorithm 1 for the kernel maps), vector operations
 // and the final Moebius combination U = sum_pi mu_pi V_pi (Section 3.3, Lemma
 // "Decomposition of U-Statistic into V-Statistics"; Algorithm 4).
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "kcommon.cuh"
@@ -129,6 +130,145 @@ __global__ void __launch_bounds__(256) kbuild_f32_kernel(int kind, float inv_par
     }
 }
 
+// RBF kernel matrix in float32, fused with its split into bf16 fixed-point
+// slices (the row scale is known: entries lie in (0, 1], so s_j = 1).
+// One block per 128 x 128 tile on or above the diagonal; the tile and its
+// mirror image are written from shared memory with coalesced stores.  The
+// squared distance is ||x_i||^2 + ||x_j||^2 - 2 x_i . x_j (float32; its rounding
+// errors are symmetric), the exponential exp_unbiased, the diagonal exactly 1.
+// slices == nullptr: K only.
+constexpr int kRbfT = 128;
+struct RbfArgs {
+    const float *X;
+    int64_t n;
+    int d;
+    float inv_h;
+    int zero_diag;
+    float *K;
+    __nv_bfloat16 *slices;   // [planes][n][ldp] or null
+    int64_t ldp;
+    int lead_bits, planes;
+    float *scales;
+};
+
+__global__ void __launch_bounds__(256) kbuild_rbf_tile_kernel(RbfArgs g) {
+    extern __shared__ float sm[];
+    float *xi = sm;                         // [128][33]
+    float *xj = xi + kRbfT * 33;            // [128][33]
+    float *S = xj + kRbfT * 33;             // [128][129]
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t n = g.n;
+    const int T = (int)((g.ldp + kRbfT - 1) / kRbfT);
+    // upper-triangle tile t -> (tm, tn), row-major: row r starts at r T - r (r - 1) / 2
+    const int t = blockIdx.x;
+    const double b = 2.0 * T + 1.0;
+    int tm = (int)((b - sqrt(b * b - 8.0 * t)) * 0.5);
+    if (tm < 0) tm = 0;
+    while (tm > 0 && tm * T - tm * (tm - 1) / 2 > t) --tm;
+    while (tm + 1 < T && (tm + 1) * T - (tm + 1) * tm / 2 <= t) ++tm;
+    const int tn = tm + (t - (tm * T - tm * (tm - 1) / 2));
+    const int64_t i0 = (int64_t)tm * kRbfT, j0 = (int64_t)tn * kRbfT;
+
+    // squared distances: 8 x 8 per thread (rows ty + 16 a, columns tx + 16 c)
+    float acc[8][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[a][c] = 0.f;
+    for (int k0 = 0; k0 < g.d; k0 += 32) {
+        __syncthreads();
+        for (int e = tid; e < kRbfT * 32; e += 256) {
+            const int rr = e >> 5, kk = e & 31;
+            const int64_t gi = i0 + rr, gj = j0 + rr;
+            xi[rr * 33 + kk] = (gi < n && k0 + kk < g.d) ? g.X[gi * g.d + k0 + kk] : 0.f;
+            xj[rr * 33 + kk] = (gj < n && k0 + kk < g.d) ? g.X[gj * g.d + k0 + kk] : 0.f;
+        }
+        __syncthreads();
+        const int kmax = min(32, g.d - k0);
+        for (int kk = 0; kk < kmax; ++kk) {
+            float av[8], bv[8];
+#pragma unroll
+            for (int a = 0; a < 8; ++a) av[a] = xi[(ty + 16 * a) * 33 + kk];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) bv[c] = xj[(tx + 16 * c) * 33 + kk];
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const float df = av[a] - bv[c];
+                    acc[a][c] = fmaf(df, df, acc[a][c]);
+                }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const int r = ty + 16 * a;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int cc = tx + 16 * c;
+            const int64_t gi = i0 + r, gj = j0 + cc;
+            float v;
+            if (gi == gj) v = g.zero_diag ? 0.f : 1.f;
+            else v = exp_unbiased(-acc[a][c] * g.inv_h);
+            S[r * 129 + cc] = (gi < n && gj < n) ? v : 0.f;
+        }
+    }
+    __syncthreads();
+    const int64_t plane = n * g.ldp;
+    const bool vec4 = (n % 4 == 0) && (g.ldp % 4 == 0);
+    const float lead_scale = __int_as_float((127 + g.lead_bits) << 23);   // 2^w
+    // the tile (rows i0.., cols j0..) and, off the diagonal, its mirror image;
+    // each thread writes 4 consecutive columns of one row
+    for (int pass = 0; pass < (tm == tn ? 1 : 2); ++pass) {
+        const int64_t r0 = pass ? j0 : i0, c0 = pass ? i0 : j0;
+        for (int e = tid; e < kRbfT * (kRbfT / 4); e += 256) {
+            const int r = e >> 5, c = (e & 31) * 4;
+            const int64_t gr = r0 + r, gc = c0 + c;
+            if (gr >= n) continue;
+            float v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = pass ? S[(c + q) * 129 + r] : S[r * 129 + c + q];
+            if (vec4 && gc + 3 < n) {
+                *reinterpret_cast<float4 *>(g.K + gr * n + gc) = make_float4(v[0], v[1], v[2], v[3]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (gc + q < n) g.K[gr * n + gc + q] = v[q];
+            }
+            if (g.slices) {
+                __nv_bfloat16 dg[4][4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float y = v[q] * lead_scale;            // row scale 1: |y| <= 2^w, exact
+                    float dd = rintf(y);
+                    dg[0][q] = __float2bfloat16_rn(dd);
+                    float sc = 1.f / 256.f;
+                    for (int p = 1; p < g.planes; ++p) {
+                        y = (y - dd) * 256.f;
+                        dd = rintf(y);
+                        dg[p][q] = __float2bfloat16_rn(dd * sc);
+                        sc *= (1.f / 256.f);
+                    }
+                }
+                __nv_bfloat16 *dst = g.slices + gr * g.ldp + gc;
+                for (int p = 0; p < g.planes; ++p) {
+                    if (vec4 && gc + 3 < g.ldp) {
+                        uint2 w;
+                        w.x = (uint32_t)__bfloat16_as_ushort(dg[p][0]) | ((uint32_t)__bfloat16_as_ushort(dg[p][1]) << 16);
+                        w.y = (uint32_t)__bfloat16_as_ushort(dg[p][2]) | ((uint32_t)__bfloat16_as_ushort(dg[p][3]) << 16);
+                        *reinterpret_cast<uint2 *>(dst + p * plane) = w;
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (gc + q < g.ldp) dst[p * plane + q] = dg[p][q];
+                    }
+                }
+            }
+        }
+    }
+    if (g.scales && tm == tn && tid < kRbfT && i0 + tid < n) g.scales[i0 + tid] = 1.f;
+}
+
 // Float64 version (FP64 mode).
 template <typename T>
 __global__ void __launch_bounds__(256) kbuild_kernel(int kind, T inv_param, const T *__restrict__ X,
@@ -249,32 +389,76 @@ struct Neumaier {
 };
 
 // V_pi = prod of its scalar slots * n^(free blocks); U_sum = sum_pi mu_pi V_pi;
-// U_mean = U_sum / (n)_m.  One thread: at most 877 terms.
-__global__ void combine_kernel(const CombineTable tab, const double *scal, const int *err, int64_t n,
-                               double *U_out, double *V_out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// U_mean = U_sum / (n)_m.  One block of 256 threads: the partitions' V are formed
+// in parallel, each thread sums its mu V terms with Neumaier compensation, and the
+// per-thread (sum, compensation) pairs are combined by one thread in a fixed
+// order (deterministic).  The table is a kernel parameter sized to the plan.
+template <int CAP>
+struct CombineTableT {
+    int nparts, m;
+    CombineEntry e[CAP];
+};
+
+// Sum of a and b split into the rounded sum and its exact rounding error (TwoSum).
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &e) {
+    s = a + b;
+    const double bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+template <int CAP>
+__global__ void __launch_bounds__(32) combine_kernel(const CombineTableT<CAP> tab, const double *scal,
+                                                     const int *err, int64_t n, double *U_out, double *V_out) {
+    // one warp: lane l forms V for partitions l, l + 32, ... and sums its mu V
+    // terms with Neumaier compensation; the 32 partial sums are then added by a
+    // shuffle tree whose rounding errors (TwoSum) are carried separately
+    const int lane = threadIdx.x;
     const bool bad = err && *err != 0;
-    Neumaier acc;
     const double dn = (double)n;
-    for (int p = 0; p < tab.nparts; ++p) {
+    const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+    Neumaier acc;
+    for (int p = lane; p < tab.nparts; p += 32) {
+        const CombineEntry en = tab.e[p];
         double v = 0.0;
-        if (tab.evaluated[p]) {
-            v = 1.0;
-            for (int q = 0; q < kCombineMaxScal; ++q) {
-                unsigned short s = tab.sid[p][q];
-                if (s != 0xffff) v *= scal[s];
-            }
-            for (int q = 0; q < tab.nfree[p]; ++q) v *= dn;
+        if (en.evaluated) {
+            double f[kCombineMaxScal];
+#pragma unroll
+            for (int q = 0; q < kCombineMaxScal; ++q) f[q] = en.sid[q] != 0xffff ? scal[en.sid[q]] : 1.0;
+            v = ((f[0] * f[1]) * (f[2] * f[3])) * (f[4] * f[5]);
+            for (int q = 0; q < en.nfree; ++q) v *= dn;
         }
-        if (bad) v = nan("");
+        if (bad) v = qnan;
         if (V_out) V_out[p] = v;
-        acc.add((double)tab.mu[p] * v);
+        acc.add((double)en.mu * v);
     }
-    double ff = 1.0;
-    for (int q = 0; q < tab.m; ++q) ff *= (dn - q);
-    const double u = bad ? nan("") : acc.value();
-    U_out[0] = u;
-    U_out[1] = u / ff;
+    double s = acc.s, c = acc.c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double s2 = __shfl_xor_sync(0xffffffffu, s, o);
+        const double c2 = __shfl_xor_sync(0xffffffffu, c, o);
+        double t, e;
+        two_sum(s, s2, t, e);
+        s = t;
+        c = c + c2 + e;
+    }
+    if (lane == 0) {
+        double ff = 1.0;
+        for (int q = 0; q < tab.m; ++q) ff *= (dn - q);
+        const double u = bad ? qnan : s + c;
+        U_out[0] = u;
+        U_out[1] = u / ff;
+    }
+}
+
+template <int CAP>
+cudaError_t combine_cap(const CombineEntry *entries, int nparts, int m, const double *scal, const int *err,
+                        int64_t n, double *U_out, double *V_out, cudaStream_t s) {
+    CombineTableT<CAP> tab;
+    tab.nparts = nparts;
+    tab.m = m;
+    for (int p = 0; p < nparts; ++p) tab.e[p] = entries[p];
+    combine_kernel<CAP><<<1, 32, 0, s>>>(tab, scal, err, n, U_out, V_out);
+    return cudaGetLastError();
 }
 
 int grid_for(int64_t total, int threads) {
@@ -302,6 +486,22 @@ cudaError_t launch_kbuild(int kind, double param, const void *Xw, bool fp64, int
     else
         kbuild_f32_kernel<<<grid, block, 0, s>>>(kind, (float)(1.0 / param), (const float *)Xw, n, d, zero_diag,
                                                  (float *)K);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kbuild_rbf(const float *Xw, int64_t n, int d, double param, int zero_diag, float *K,
+                              void *slices, int64_t ldp, int lead_bits, int planes, float *scales, cudaStream_t s) {
+    RbfArgs g{Xw, n, d, (float)(1.0 / param), zero_diag, K, (__nv_bfloat16 *)slices, slices ? ldp : n, lead_bits,
+              planes, slices ? scales : nullptr};
+    const int smem = (2 * kRbfT * 33 + kRbfT * 129) * 4;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(kbuild_rbf_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int64_t T = (g.ldp + kRbfT - 1) / kRbfT;
+    kbuild_rbf_tile_kernel<<<(unsigned)(T * (T + 1) / 2), 256, smem, s>>>(g);
     return cudaGetLastError();
 }
 
@@ -340,10 +540,13 @@ cudaError_t launch_vsum(const double *u, int64_t n, double *out, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_combine(const CombineTable &tab, const double *scal, const int *err, int64_t n, double *U_out,
-                           double *V_out, cudaStream_t s) {
-    combine_kernel<<<1, 32, 0, s>>>(tab, scal, err, n, U_out, V_out);
-    return cudaGetLastError();
+cudaError_t launch_combine(const CombineEntry *entries, int nparts, int m, const double *scal, const int *err,
+                           int64_t n, double *U_out, double *V_out, cudaStream_t s) {
+    if (nparts <= 16) return combine_cap<16>(entries, nparts, m, scal, err, n, U_out, V_out, s);
+    if (nparts <= 64) return combine_cap<64>(entries, nparts, m, scal, err, n, U_out, V_out, s);
+    if (nparts <= 256) return combine_cap<256>(entries, nparts, m, scal, err, n, U_out, V_out, s);
+    if (nparts <= kCombineMaxParts) return combine_cap<kCombineMaxParts>(entries, nparts, m, scal, err, n, U_out, V_out, s);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace ustat

@@ -64,7 +64,8 @@ __device__ __forceinline__ int row_exp(float m) {
 
 __device__ __forceinline__ void write_digits(float x, int lead_bits, int e, int planes, __nv_bfloat16 *dst,
                                              int64_t plane_stride) {
-    float y = ldexpf(x, lead_bits - e);   // |y| <= 2^w, exact
+    const int k = lead_bits - e;
+    float y = (k >= -126 && k <= 127) ? x * __int_as_float((127 + k) << 23) : ldexpf(x, k);   // |y| <= 2^w, exact
     float d = rintf(y);
     dst[0] = __float2bfloat16_rn(d);
     float scale = 1.f / 256.f;

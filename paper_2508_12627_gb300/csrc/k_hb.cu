@@ -95,14 +95,14 @@ __global__ void __launch_bounds__(256) tile_kernel(int mode, TileTerms tt, int64
 // distinct matrix once and evaluates every operation on them.  Operation o
 // multiplies matrix m ex[o][m] times (the terms of a merged factor).
 template <typename T, bool kVec>
-__global__ void __launch_bounds__(256) mhb_kernel(MhbArgs g) {
-    constexpr int CB = 512;
+__global__ void __launch_bounds__(256, 3) mhb_kernel(MhbArgs g) {
+    constexpr int CB = 256;   // columns per block: 8 per lane
     __shared__ T bsm[kMhbOps][CB];
     __shared__ float colred[8][CB];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t n = g.n;
     const int64_t j0 = (int64_t)blockIdx.x * CB;
-    auto col = [&](int c) -> int { return kVec ? (4 * lane + 128 * (c >> 2) + (c & 3)) : (lane + 32 * c); };
+    auto col = [&](int c) -> int { return kVec ? (4 * lane + 128 * (c >> 2) + (c & 3)) : (lane + 32 * c); };  // c < 8
     for (int o = 0; o < g.nops; ++o)
         for (int c = threadIdx.x; c < CB; c += 256) {
             const int64_t j = j0 + c;
@@ -111,22 +111,22 @@ __global__ void __launch_bounds__(256) mhb_kernel(MhbArgs g) {
         }
     __syncthreads();
     double facc[kMhbOps];
-    float gacc[kMhbGemv][16];
+    float gacc[kMhbGemv][8];
 #pragma unroll
     for (int o = 0; o < kMhbOps; ++o) facc[o] = 0.0;
 #pragma unroll
     for (int q = 0; q < kMhbGemv; ++q)
 #pragma unroll
-        for (int c = 0; c < 16; ++c) gacc[q][c] = 0.f;
+        for (int c = 0; c < 8; ++c) gacc[q][c] = 0.f;
     for (int64_t i = (int64_t)blockIdx.y * 8 + warp; i < n; i += (int64_t)gridDim.y * 8) {
-        T vals[kMhbMats][16];
+        T vals[kMhbMats][8];
 #pragma unroll
         for (int m = 0; m < kMhbMats; ++m) {
             if (m >= g.nmat) break;
             const T *row = (const T *)g.M[m] + i * n;
             if constexpr (kVec) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
+                for (int q = 0; q < 2; ++q) {
                     const int64_t j = j0 + 4 * lane + 128 * q;
                     if (j + 3 < n) {
                         const float4 v = *reinterpret_cast<const float4 *>(row + j);
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(256) mhb_kernel(MhbArgs g) {
                 }
             } else {
 #pragma unroll
-                for (int c = 0; c < 16; ++c) {
+                for (int c = 0; c < 8; ++c) {
                     const int64_t j = j0 + col(c);
                     vals[m][c] = j < n ? row[j] : T(0);
                 }
@@ -152,20 +152,20 @@ __global__ void __launch_bounds__(256) mhb_kernel(MhbArgs g) {
         for (int o = 0; o < kMhbOps; ++o) {
             if (o >= g.nops) break;
             const double ai = g.op[o].a ? g.op[o].a[i] : 1.0;
-            T p[16];
+            T p[8];
 #pragma unroll
-            for (int c = 0; c < 16; ++c) p[c] = T(1);
+            for (int c = 0; c < 8; ++c) p[c] = T(1);
 #pragma unroll
             for (int m = 0; m < kMhbMats; ++m) {
                 const int e = g.op[o].ex[m];
                 for (int r = 0; r < e; ++r)
 #pragma unroll
-                    for (int c = 0; c < 16; ++c) p[c] *= vals[m][c];
+                    for (int c = 0; c < 8; ++c) p[c] *= vals[m][c];
             }
             if (g.op[o].kind == TILE_FREDUCE) {
                 T s = 0;
 #pragma unroll
-                for (int c = 0; c < 16; ++c) s = fma(p[c], bsm[o][col(c)], s);
+                for (int c = 0; c < 8; ++c) s = fma(p[c], bsm[o][col(c)], s);
                 facc[o] += (double)s * ai;
             } else {
                 const float af = (float)ai;
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(256) mhb_kernel(MhbArgs g) {
                 for (int q = 0; q < kMhbGemv; ++q)
                     if (q == gi) {
 #pragma unroll
-                        for (int c = 0; c < 16; ++c) gacc[q][c] = fmaf(af, (float)p[c], gacc[q][c]);
+                        for (int c = 0; c < 8; ++c) gacc[q][c] = fmaf(af, (float)p[c], gacc[q][c]);
                     }
                 ++gi;
             }
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(256) mhb_kernel(MhbArgs g) {
         for (int q = 0; q < kMhbGemv; ++q)
             if (q == gi) {
 #pragma unroll
-                for (int c = 0; c < 16; ++c) colred[warp][col(c)] = gacc[q][c];
+                for (int c = 0; c < 8; ++c) colred[warp][col(c)] = gacc[q][c];
             }
         __syncthreads();
         for (int c = threadIdx.x; c < CB; c += 256) {
@@ -227,7 +227,7 @@ cudaError_t launch_mhb(const MhbArgs &g0, bool fp64, cudaStream_t s) {
         if (g.op[o].kind == TILE_GEMV) ++ngemv;
     }
     if (ngemv > kMhbGemv) return cudaErrorInvalidValue;
-    const int64_t gx = (g.n + 511) / 512;
+    const int64_t gx = (g.n + 255) / 256;
     int64_t gy = (2 * 152 + gx - 1) / gx;
     const int64_t maxgy = (g.n + 7) / 8;
     if (gy > maxgy) gy = maxgy;

@@ -13,6 +13,10 @@ cudaError_t launch_xconvert(const void *X, int x_dtype, int64_t n, int d, void *
 // K(i,j) = exp(-||x_i - x_j||^2 / param) (kind RBF) or (x_i . x_j) / param (LINEAR).
 cudaError_t launch_kbuild(int kind, double param, const void *Xw, bool fp64, int64_t n, int d,
                           int zero_diag, void *K, cudaStream_t s);
+// RBF kernel matrix (float32) fused with its split into `planes` bf16 slices of
+// row scale 1 (slices may be null: K only).
+cudaError_t launch_kbuild_rbf(const float *Xw, int64_t n, int d, double param, int zero_diag, float *K,
+                              void *slices, int64_t ldp, int lead_bits, int planes, float *scales, cudaStream_t s);
 cudaError_t launch_loadmat(const double *src, int64_t n, bool fp64, int zero_diag, void *dst,
                            cudaStream_t s);
 cudaError_t launch_unary_tanh(const void *X, int x_dtype, int64_t n, int d, const double *w,
@@ -89,17 +93,16 @@ cudaError_t launch_gemm_simt(const SimtGemmArgs &g, bool fp64, cudaStream_t s);
 // ---- Moebius combination (k_elem.cu)
 constexpr int kCombineMaxParts = 877;
 constexpr int kCombineMaxScal = 6;
-struct CombineTable {
-    int nparts;
-    int m;
-    int mu[kCombineMaxParts];
-    unsigned short sid[kCombineMaxParts][kCombineMaxScal];   // scalar slot index, 0xffff = none
-    unsigned char nfree[kCombineMaxParts];
-    unsigned char evaluated[kCombineMaxParts];
+struct CombineEntry {
+    int mu;
+    unsigned short sid[kCombineMaxScal];   // scalar slot index, 0xffff = none
+    unsigned char nfree;
+    unsigned char evaluated;
 };
+// V_pi = prod_q scal[sid] * n^nfree (0 if not evaluated); U = sum mu V.
 // A non-zero *err (a bounded device wait gave up) turns U and V into NaN.
-cudaError_t launch_combine(const CombineTable &tab, const double *scal, const int *err, int64_t n,
-                           double *U_out, double *V_out, cudaStream_t s);
+cudaError_t launch_combine(const CombineEntry *entries, int nparts, int m, const double *scal, const int *err,
+                           int64_t n, double *U_out, double *V_out, cudaStream_t s);
 
 // ---- tensor-core path (k_gemm_tc.cu)
 // digits of the leading bf16 slice for a contraction of length K (exact integer

@@ -932,6 +932,26 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan) {
             out.push_back(op);
         }
         P.ops.swap(out);
+        // an RBF kernel matrix has entries in (0, 1]: its unscaled split (row scale 1)
+        // is written by the kernel-matrix build itself
+        if (split) {
+            std::vector<char> fused(P.ops.size(), 0);
+            for (size_t i = 0; i < P.ops.size(); ++i) {
+                const Op &op = P.ops[i];
+                if (op.kind != OP_SPLIT || op.u >= 0) continue;
+                for (auto &kb : P.ops)
+                    if (kb.kind == OP_KBUILD && kb.out == op.t[0].mat && kb.opA < 0 &&
+                        P.factor_kind[kb.factor] == USTAT_RBF) {
+                        kb.opA = op.out;
+                        fused[i] = 1;
+                        break;
+                    }
+            }
+            std::vector<Op> kept;
+            for (size_t i = 0; i < P.ops.size(); ++i)
+                if (!fused[i]) kept.push_back(P.ops[i]);
+            P.ops.swap(kept);
+        }
     }
     for (auto &op : P.ops) {
         if (op.kind == OP_GEMM) {
@@ -951,13 +971,15 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan) {
             };
             for (int t = 0; t < o.nt; ++t) add(o.t[t].mat);
             add(o.u), add(o.a), add(o.b), add(o.A.mat), add(o.B.mat), add(o.W.mat), add(o.Ab.mat);
-            add(o.Wbc.mat), add(o.Wbd.mat), add(o.ub), add(o.opA), add(o.opB);
+            add(o.Wbc.mat), add(o.Wbd.mat), add(o.ub);
+            if (o.kind == OP_GEMM) add(o.opA), add(o.opB);
             for (int r = 0; r < o.nred; ++r) add(o.red[r].W.mat), add(o.red[r].a), add(o.red[r].b);
             return v;
         };
         auto outs = [&](const Op &o) {
             std::vector<int> v;
             if (o.out >= 0 && (o.kind != OP_GEMM || o.store)) v.push_back(o.out);
+            if (o.kind == OP_KBUILD && o.opA >= 0) v.push_back(o.opA);
             for (int r = 0; r < o.nred; ++r) v.push_back(o.red[r].out);
             return v;
         };
@@ -1016,6 +1038,30 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan) {
             }
         }
         P.ops.swap(out);
+
+        // every slot an operation reads is written by an earlier operation, and
+        // every scalar a partition multiplies is produced
+        std::vector<char> made(P.slots.size(), 0);
+        auto check_and_make = [&](const Op &o) {
+            for (int s : ins(o))
+                if (!made[s]) return false;
+            for (int s : outs(o)) made[s] = 1;
+            return true;
+        };
+        for (const Op &o : P.ops) {
+            if (o.kind == OP_MHB) {
+                for (const Op &m : P.groups[o.group])
+                    for (int s : ins(m))
+                        if (!made[s]) return USTAT_ERR_UNSUPPORTED;
+                for (const Op &m : P.groups[o.group])
+                    for (int s : outs(m)) made[s] = 1;
+            } else if (!check_and_make(o)) {
+                return USTAT_ERR_UNSUPPORTED;
+            }
+        }
+        for (const PartRec &pr : P.parts)
+            for (int q = 0; q < pr.nscal; ++q)
+                if (!made[pr.scal[q]]) return USTAT_ERR_UNSUPPORTED;
     }
     return USTAT_OK;
 }

@@ -123,3 +123,21 @@ def test_workspace_bytes_scale(us):
     a, b = p.workspace_bytes(1000, 32), p.workspace_bytes(2000, 32)
     assert 3.5 < b / a < 4.5
     assert p.host_staging_bytes(1000, 32) >= 8 * 1000 * 32
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16x3", "bf16x4"])
+def test_every_plan_is_well_formed(us, prec):
+    # ustat_plan checks that every slot an operation reads is written by an earlier
+    # operation and that every partition's scalars are produced; it returns an
+    # error otherwise.  Sweep graphs, modes and options.
+    graphs = [(synth.cycle4_graph(), [uo.RBF]), (synth.triangle_graph(), [uo.RBF]),
+              (synth.path5_chord_graph(), [uo.LINEAR, uo.TANH_DOT]), (synth.k4_plus_cycle_graph(), [uo.RBF]),
+              (synth.cycle(5), [uo.RBF]), (synth.path(7), [uo.MATRIX]),
+              (synth.Graph(4, [(0, 1, 0), (2, 1, 2), (2, 3, 0), (3, 0, 2), (0, 2, 0)], [(1, 1)]),
+               [uo.MATRIX, uo.VECTOR, uo.MATRIX])]
+    for g, kinds in graphs:
+        for sp in (False, True):
+            for cse in (False, True):
+                for pl in (us.PLAN_EXHAUSTIVE, us.PLAN_MINFILL):
+                    p = us.Plan(g, kinds, precision=prec, sparsify=sp, cse=cse, planner=pl)
+                    assert p.info["n_parts"] == len(uo.set_partitions(g.m))
