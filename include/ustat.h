@@ -184,6 +184,38 @@ int ustat_batch_workspace_bytes(const ustat_plan_t *plan, const int64_t *n, int 
                                 size_t *bytes);
 
 /*
+ * Evaluation that allocates nothing: for callers that must not call cudaMalloc
+ * (or any allocating routine) at evaluation time.  Examples are a service that
+ * reserves all its device memory at start-up and forbids allocation afterwards;
+ * a plug-in running inside a framework whose caching allocator owns the device
+ * memory, so that a cudaMalloc behind its back can fail or fragment the pool;
+ * and code on a latency-critical path, where an allocation may stall or
+ * synchronise the device.
+ *
+ * Instead of a caller-supplied workspace, this call uses one scratch array of
+ * USTAT_NOALLOC_MAX_BYTES that the library defines in device memory.  A GPU
+ * holds that array from the moment the driver loads the library's device code
+ * there (at the latest during the first call on that device) until the process
+ * exits.  The caller still passes X, the factors and the outputs (as for
+ * ustat_eval).
+ *   - Returns USTAT_ERR_WORKSPACE (and writes nothing) when the workspace this
+ *     evaluation needs, ustat_workspace_bytes(plan, n, d), exceeds
+ *     USTAT_NOALLOC_MAX_BYTES.
+ *   - The first call on a device is its set-up: it looks up the array's device
+ *     address for that device (the device must be current), which may load the
+ *     library's device code; make that first call before any stream capture.
+ *   - All calls share the one array, which keeps the previous call's contents;
+ *     the call clears what must start at zero itself.  Calls whose work
+ *     overlaps on the GPU (other streams, other host threads) race on the
+ *     array: order them on one stream or synchronise between them.
+ * The paper has no counterpart: this is a deployment variant of ustat_eval.
+ */
+#define USTAT_NOALLOC_MAX_BYTES (64u * 1024u * 1024u)
+int ustat_eval_noalloc(ustat_plan_t *plan, const void *X, int x_dtype, int64_t n, int d,
+                       const ustat_factor *factors, int n_factors, void *stream, double *U_out,
+                       double *V_out);
+
+/*
  * Per-operation timing for measurement.  While enabled (per host thread), every
  * device operation launched by ustat_eval on that thread is bracketed by a pair
  * of CUDA events on the evaluation stream.  ustat_profile_collect() waits for

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -585,4 +586,46 @@ extern "C" int ustat_plan_describe(const ustat_plan_t *plan, char *buf, size_t b
         buf[k] = 0;
     }
     return USTAT_OK;
+}
+
+// ---------------------------------------------------------------- no-allocation entry point
+// Scratch used in place of a caller workspace by ustat_eval_noalloc, for callers
+// that may not allocate device memory at evaluation time (a service that reserves
+// its memory at start-up, a plug-in inside another framework's allocator, a
+// latency-critical path where cudaMalloc may stall or synchronise).  In host
+// code the name below is a host-side stand-in, not a device address: the
+// device address is looked up per device with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[USTAT_NOALLOC_MAX_BYTES];
+
+namespace {
+constexpr int kNoallocMaxDevices = 64;
+void *g_noalloc_addr[kNoallocMaxDevices] = {nullptr};
+std::mutex g_noalloc_mu;
+}  // namespace
+
+extern "C" int ustat_eval_noalloc(ustat_plan_t *plan, const void *X, int x_dtype, int64_t n, int d,
+                                  const ustat_factor *factors, int n_factors, void *stream, double *U_out,
+                                  double *V_out) {
+    if (!plan || !X || !U_out || d < 1 || n < 1 || (x_dtype != 0 && x_dtype != 1)) return USTAT_ERR_INVALID_ARG;
+    size_t need = 0;
+    int rc = ustat_workspace_bytes(plan, n, d, &need);
+    if (rc != USTAT_OK) return rc;
+    if (need > (size_t)USTAT_NOALLOC_MAX_BYTES) return USTAT_ERR_WORKSPACE;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (dev < 0 || dev >= kNoallocMaxDevices) return USTAT_ERR_UNSUPPORTED;
+    void *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return cuda_fail(e);
+            g_noalloc_addr[dev] = p;
+        }
+        base = g_noalloc_addr[dev];
+    }
+    return ustat_eval(plan, X, x_dtype, n, d, factors, n_factors, base, (size_t)USTAT_NOALLOC_MAX_BYTES, stream, U_out,
+                      V_out);
 }

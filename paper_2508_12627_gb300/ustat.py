@@ -60,6 +60,7 @@ EXPORTS = {
     "ustat_workspace_bytes": (_i, [_vp, _i64, _i, _P(_sz)]),
     "ustat_eval": (_i, [_vp, _vp, _i, _i64, _i, _P(ustat_factor), _i, _vp, _sz, _vp, _vp, _vp]),
     "ustat_host_staging_bytes": (_i, [_vp, _i64, _i, _P(_sz)]),
+    "ustat_eval_noalloc": (_i, [_vp, _vp, _i, _i64, _i, _P(ustat_factor), _i, _vp, _vp, _vp]),
     "ustat_eval_host": (_i, [_vp, _vp, _i, _i64, _i, _P(ustat_factor), _i, _vp, _sz, _vp, _P(_d), _P(_d)]),
     "ustat_eval_batch": (_i, [_vp, _P(_vp), _i, _P(_i64), _i, _i, _P(ustat_factor), _i, _vp, _sz, _vp,
                               _vp, _vp]),
@@ -195,6 +196,15 @@ def ustat_eval(plan, X_ptr, x_dtype, n, d, factors, ws_ptr, ws_bytes, stream, U_
     rc = lib().ustat_eval(plan.handle, X_ptr, x_dtype, n, d, fa, len(factors), ws_ptr, ws_bytes, stream,
                           U_ptr, V_ptr)
     _check(rc, "ustat_eval")
+
+
+NOALLOC_MAX_BYTES = 64 * 1024 * 1024
+
+
+def ustat_eval_noalloc(plan, X_ptr, x_dtype, n, d, factors, stream, U_ptr, V_ptr):
+    fa = factor_array(factors)
+    rc = lib().ustat_eval_noalloc(plan.handle, X_ptr, x_dtype, n, d, fa, len(factors), stream, U_ptr, V_ptr)
+    _check(rc, "ustat_eval_noalloc")
 
 
 def ustat_eval_host(plan, X_host_ptr, x_dtype, n, d, factors, ws_ptr, ws_bytes, stream, U_host, V_host):
