@@ -177,14 +177,23 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
         ProfScope ps(op.kind, C.st);
         switch (op.kind) {
             case OP_KBUILD:
-                if (!C.fp64 && f[op.factor].kind == USTAT_RBF)
+                if (!C.fp64 && f[op.factor].kind == USTAT_RBF) {
+                    int rpow[kMaxRed], rvec[kMaxRed];
+                    double *rout[kMaxRed];
+                    for (int r = 0; r < op.nred; ++r) {
+                        rpow[r] = op.red[r].pow;
+                        rvec[r] = P.slots[op.red[r].out].kind == S_VEC;
+                        rout[r] = C.vec(op.red[r].out);   // scalar and vector slots are float64
+                    }
                     e = launch_kbuild_rbf((const float *)(C.ws + C.L.xw_off), n, C.d, f[op.factor].param, P.sparsify,
                                           (float *)C.ptr(op.out), op.opA >= 0 ? C.ptr(op.opA) : nullptr,
                                           C.L.ldp_slices, lead, split_planes_of(P.precision),
-                                          op.opA >= 0 ? C.scales(op.opA) : nullptr, C.st);
-                else
+                                          op.opA >= 0 ? C.scales(op.opA) : nullptr, op.nred, rpow, rvec, rout, C.st);
+                } else {
+                    if (op.nred) return USTAT_ERR_UNSUPPORTED;   // the planner fuses only into the RBF build
                     e = launch_kbuild(f[op.factor].kind, f[op.factor].param, C.ws + C.L.xw_off, C.fp64, n, C.d,
                                       P.sparsify, C.ptr(op.out), C.st);
+                }
                 break;
             case OP_LOADMAT:
                 e = launch_loadmat((const double *)f[op.factor].data, n, C.fp64, P.sparsify, C.ptr(op.out), C.st);
@@ -203,6 +212,9 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                 break;
             case OP_VSUM:
                 e = launch_vsum(C.vec(op.u), n, C.vec(op.out), C.st);
+                break;
+            case OP_VDOT:
+                e = launch_vdot(C.vec(op.u), C.vec(op.a), n, C.vec(op.out), C.st);
                 break;
             case OP_HADAMARD:
             case OP_GEMV:
@@ -560,8 +572,14 @@ extern "C" int ustat_plan_describe(const ustat_plan_t *plan, char *buf, size_t b
                       (m.kind == OP_GEMV ? "u=" + vec(m.u) : "a=" + vec(m.a) + " b=" + vec(m.b)) + ")";
             }
             snprintf(line, sizeof(line), "%zu mhb%s\n", i, ms.c_str());
-        } else if (o.kind == OP_KBUILD)
-            snprintf(line, sizeof(line), "%zu kbuild out=%d f=%d slices=%d\n", i, o.out, o.factor, o.opA);
+        } else if (o.kind == OP_KBUILD) {
+            std::string ks;
+            for (int r = 0; r < o.nred; ++r)
+                ks += (r ? ";" : "") + std::string(P.slots[o.red[r].out].kind == S_VEC ? "v" : "s") +
+                      std::to_string(o.red[r].out) + "+=K^" + std::to_string(o.red[r].pow);
+            snprintf(line, sizeof(line), "%zu kbuild out=%d f=%d slices=%d red=[%s]\n", i, o.out, o.factor, o.opA,
+                     ks.c_str());
+        }
         else
             snprintf(line, sizeof(line),
                      "%zu %s out=%d f=%d terms=[%s] u=%s a=%s b=%s A=%s B=%s W=%s Ab=%s Wbc=%s Wbd=%s ub=%s\n", i,

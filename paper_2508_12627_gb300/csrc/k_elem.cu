@@ -131,13 +131,27 @@ __global__ void __launch_bounds__(256) kbuild_f32_kernel(int kind, float inv_par
 }
 
 // RBF kernel matrix in float32, fused with its split into bf16 fixed-point
-// slices (the row scale is known: entries lie in (0, 1], so s_j = 1).
-// One block per 128 x 128 tile on or above the diagonal; the tile and its
-// mirror image are written from shared memory with coalesced stores.  The
-// squared distance is ||x_i||^2 + ||x_j||^2 - 2 x_i . x_j (float32; its rounding
-// errors are symmetric), the exponential exp_unbiased, the diagonal exactly 1.
+// slices (the row scale is known: entries lie in (0, 1], so every row scale is
+// 1) and with up to kRbfMaxRed reductions of its entrywise powers (a full sum
+// sum_ij K_ij^p into a float64 scalar, or row sums sum_j K_ij^p into a float64
+// vector).  One block per 128 x 128 tile on or above the diagonal.  Each thread
+// owns rows {4 ty + i, 64 + 4 ty + i} and columns {4 tx + j, 64 + 4 tx + j}
+// (i, j < 4), so it writes the tile with 16-byte row stores and, off the
+// diagonal, the mirror tile with 16-byte stores of its column quadruples; K is
+// exactly symmetric because (x_i - x_j)^2 = (x_j - x_i)^2 in every rounding.
+// The squared distance is a sum of squared differences (no Gram form: it would
+// cancel), the exponential exp_unbiased's steps, the diagonal exactly 1 (0 in
+// the sparsified mode).  The arithmetic runs on pairs of float32 with the
+// packed .f32x2 instructions (the same IEEE operations per lane, half the
+// instructions); the kernel is bound by instruction issue otherwise.
 // slices == nullptr: K only.
 constexpr int kRbfT = 128;
+constexpr int kRbfMaxRed = 4;
+struct RbfRed {
+    int pow;        // 1..4
+    int vec;        // 1: out[i] += sum_j K_ij^pow; 0: out[0] += sum_ij K_ij^pow
+    double *out;
+};
 struct RbfArgs {
     const float *X;
     int64_t n;
@@ -149,124 +163,373 @@ struct RbfArgs {
     int64_t ldp;
     int lead_bits, planes;
     float *scales;
+    int nred;
+    RbfRed red[kRbfMaxRed];
 };
 
-__global__ void __launch_bounds__(256) kbuild_rbf_tile_kernel(RbfArgs g) {
-    extern __shared__ float sm[];
-    float *xi = sm;                         // [128][33]
-    float *xj = xi + kRbfT * 33;            // [128][33]
-    float *S = xj + kRbfT * 33;             // [128][129]
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+// two float32 in one 64-bit register pair (first = low half)
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 f2_pack(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f32x2 r, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ f32x2 f2_add(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 f2_sub(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ f32x2 f2_splat(float a) { return f2_pack(a, a); }
+__device__ __forceinline__ f32x2 f2_rint(f32x2 a) {
+    float x, y;
+    f2_unpack(a, x, y);
+    return f2_pack(rintf(x), rintf(y));
+}
+
+// exp(-d2 * inv_h) for two squared distances: the steps of exp_unbiased, each
+// the same IEEE operation per lane
+__device__ __forceinline__ f32x2 f2_rbf(f32x2 d2, float inv_h) {
+    const f32x2 z = f2_mul(d2, f2_splat(-inv_h));
+    const f32x2 k = f2_rint(f2_mul(z, f2_splat(1.44269504088896341f)));
+    const f32x2 fh = f2_fma(k, f2_splat(-0.693145751953125f), z);   // exact
+    const f32x2 fl = f2_mul(k, f2_splat(-1.42860682030941723212e-6f));
+    const f32x2 f = f2_add(fh, fl);
+    f32x2 q = f2_fma(f2_splat(1.0f / 40320.0f), f, f2_splat(1.0f / 5040.0f));
+    q = f2_fma(q, f, f2_splat(1.0f / 720.0f));
+    q = f2_fma(q, f, f2_splat(1.0f / 120.0f));
+    q = f2_fma(q, f, f2_splat(1.0f / 24.0f));
+    q = f2_fma(q, f, f2_splat(1.0f / 6.0f));
+    q = f2_fma(q, f, f2_splat(0.5f));
+    q = f2_mul(f2_mul(q, f), f);
+    const f32x2 one = f2_splat(1.0f);
+    const f32x2 sh = f2_add(one, fh);                        // Fast2Sum (|1| >= |fh|)
+    const f32x2 sl = f2_sub(fh, f2_sub(sh, one));
+    const f32x2 y = f2_add(sh, f2_add(f2_add(sl, fl), q));
+    float k0, k1, z0, z1;
+    f2_unpack(k, k0, k1);
+    f2_unpack(z, z0, z1);
+    const f32x2 p2 = f2_pack(__int_as_float(((int)k0 + 127) << 23), __int_as_float(((int)k1 + 127) << 23));
+    float r0, r1;
+    f2_unpack(f2_mul(y, p2), r0, r1);
+    return f2_pack(z0 < -87.0f ? 0.0f : r0, z1 < -87.0f ? 0.0f : r1);
+}
+
+// one row of a thread's entries (four pairs); out of line with the four pairs
+// interleaved, so that the kernel's code stays small while each call still has
+// four independent dependency chains
+struct F2Row {
+    f32x2 v[4];
+};
+__device__ __noinline__ F2Row f2_rbf_row(F2Row d2, float inv_h) {
+    F2Row r;
+#pragma unroll
+    for (int h = 0; h < 4; ++h) r.v[h] = f2_rbf(d2.v[h], inv_h);
+    return r;
+}
+
+__device__ __forceinline__ int rbf_row(int a, int ty) { return 4 * ty + (a & 3) + 64 * (a >> 2); }
+
+// eight entries of row gr (columns gc..gc+3 and gc+64..gc+67) of K and of its
+// digit planes.  Digit p of y = K * 2^w is y_p rounded to a multiple of 2^-8p by
+// adding and subtracting 1.5 * 2^(23 - 8p) (round to nearest even, exact for
+// |y_p| < 2^(22 - 8p)); the remainder y_{p+1} = y_p - digit is exact.  Out of
+// line: the kernel calls it 16 times, and inlined copies outgrew the
+// instruction cache.
+__device__ __noinline__ void rbf_store_row(float *K, __nv_bfloat16 *slices, int64_t n, int64_t ldp, int planes,
+                                           float lead_scale, int64_t gr, int64_t gc, F2Row v) {
+    float *krow = K + gr * n;
+    const bool vec4 = (n % 4) == 0;
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+        const int64_t c = gc + 64 * hh;
+        float e[4];
+        f2_unpack(v.v[2 * hh], e[0], e[1]);
+        f2_unpack(v.v[2 * hh + 1], e[2], e[3]);
+        if (vec4 && c + 3 < n) {
+            *reinterpret_cast<float4 *>(krow + c) = make_float4(e[0], e[1], e[2], e[3]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (c + q < n) krow[c + q] = e[q];
+        }
+    }
+    if (!slices) return;
+    const f32x2 ls = f2_splat(lead_scale);
+    f32x2 y[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) y[h] = f2_mul(v.v[h], ls);   // row scale 1: |y| <= 2^w, exact
+    const int64_t plane = n * ldp;
+    __nv_bfloat16 *srow = slices + gr * ldp + gc;
+    float magic = 12582912.0f;   // 1.5 * 2^23
+    for (int p = 0; p < planes; ++p) {
+        const f32x2 mg = f2_splat(magic);
+        uint32_t w[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const f32x2 dgt = f2_sub(f2_add(y[h], mg), mg);
+            y[h] = f2_sub(y[h], dgt);
+            float d0, d1;
+            f2_unpack(dgt, d0, d1);
+            const __nv_bfloat162 b2 = __floats2bfloat162_rn(d0, d1);
+            w[h] = *reinterpret_cast<const uint32_t *>(&b2);
+        }
+        __nv_bfloat16 *dst = srow + p * plane;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int64_t c = gc + 64 * hh;
+            if (c + 3 < ldp) {
+                *reinterpret_cast<uint2 *>(dst + 64 * hh) = make_uint2(w[2 * hh], w[2 * hh + 1]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (c + q < ldp)
+                        dst[64 * hh + q] = __ushort_as_bfloat16((uint16_t)(w[2 * hh + (q >> 1)] >> (16 * (q & 1))));
+            }
+        }
+        magic *= (1.0f / 256.0f);
+    }
+}
+
+__global__ void __launch_bounds__(256, 2) kbuild_rbf_tile_kernel(RbfArgs g) {
+    // coordinates k of the tile's rows: xa[k][r] = (x, x) pairs for the rows,
+    // xb[k][r] for the columns; xa is reused by the reductions
+    __shared__ __align__(16) float2 xa[32][kRbfT];
+    __shared__ __align__(16) float xb[32][kRbfT];
+    __shared__ double dred[8];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, lane = tid & 31, warp = tid >> 5;
     const int64_t n = g.n;
     const int T = (int)((g.ldp + kRbfT - 1) / kRbfT);
     // upper-triangle tile t -> (tm, tn), row-major: row r starts at r T - r (r - 1) / 2
     const int t = blockIdx.x;
-    const double b = 2.0 * T + 1.0;
-    int tm = (int)((b - sqrt(b * b - 8.0 * t)) * 0.5);
+    const double bq = 2.0 * T + 1.0;
+    int tm = (int)((bq - sqrt(bq * bq - 8.0 * t)) * 0.5);
     if (tm < 0) tm = 0;
     while (tm > 0 && tm * T - tm * (tm - 1) / 2 > t) --tm;
     while (tm + 1 < T && (tm + 1) * T - (tm + 1) * tm / 2 <= t) ++tm;
     const int tn = tm + (t - (tm * T - tm * (tm - 1) / 2));
     const int64_t i0 = (int64_t)tm * kRbfT, j0 = (int64_t)tn * kRbfT;
+    const bool diag_tile = tm == tn;
 
-    // squared distances: 8 x 8 per thread (rows ty + 16 a, columns tx + 16 c)
-    float acc[8][8];
+    // acc[a][h]: row a, columns (2h, 2h + 1) of the thread's eight
+    f32x2 acc[8][4];
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[a][c] = 0.f;
+        for (int h = 0; h < 4; ++h) acc[a][h] = f2_splat(0.f);
+    const bool xvec = (g.d % 4) == 0;
     for (int k0 = 0; k0 < g.d; k0 += 32) {
         __syncthreads();
-        for (int e = tid; e < kRbfT * 32; e += 256) {
-            const int rr = e >> 5, kk = e & 31;
-            const int64_t gi = i0 + rr, gj = j0 + rr;
-            xi[rr * 33 + kk] = (gi < n && k0 + kk < g.d) ? g.X[gi * g.d + k0 + kk] : 0.f;
-            xj[rr * 33 + kk] = (gj < n && k0 + kk < g.d) ? g.X[gj * g.d + k0 + kk] : 0.f;
+        // stage rows i0.. and j0.., 32 coordinates, transposed (consecutive lanes:
+        // consecutive rows, so the shared-memory writes do not conflict)
+        for (int e = tid; e < 2 * kRbfT * 8; e += 256) {
+            const int opnd = e >> 10, row = e & (kRbfT - 1), kq = (e >> 7) & 7;
+            const int64_t gr = (opnd ? j0 : i0) + row;
+            const int k = k0 + 4 * kq;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (gr < n && k < g.d) {
+                const float *src = g.X + gr * g.d + k;
+                if (xvec) {
+                    v = *reinterpret_cast<const float4 *>(src);
+                } else {
+                    v.x = src[0];
+                    if (k + 1 < g.d) v.y = src[1];
+                    if (k + 2 < g.d) v.z = src[2];
+                    if (k + 3 < g.d) v.w = src[3];
+                }
+            }
+            if (opnd == 0) {
+                xa[4 * kq + 0][row] = make_float2(v.x, v.x);
+                xa[4 * kq + 1][row] = make_float2(v.y, v.y);
+                xa[4 * kq + 2][row] = make_float2(v.z, v.z);
+                xa[4 * kq + 3][row] = make_float2(v.w, v.w);
+            } else {
+                xb[4 * kq + 0][row] = v.x;
+                xb[4 * kq + 1][row] = v.y;
+                xb[4 * kq + 2][row] = v.z;
+                xb[4 * kq + 3][row] = v.w;
+            }
         }
         __syncthreads();
         const int kmax = min(32, g.d - k0);
         for (int kk = 0; kk < kmax; ++kk) {
-            float av[8], bv[8];
+            f32x2 av[8];
 #pragma unroll
-            for (int a = 0; a < 8; ++a) av[a] = xi[(ty + 16 * a) * 33 + kk];
+            for (int q = 0; q < 4; ++q) {
+                const int r = (q & 1) * 2 + (q >> 1) * 64 + 4 * ty;
+                const ulonglong2 pr = *reinterpret_cast<const ulonglong2 *>(&xa[kk][r]);
+                av[(q >> 1) * 4 + (q & 1) * 2] = pr.x;
+                av[(q >> 1) * 4 + (q & 1) * 2 + 1] = pr.y;
+            }
+            const ulonglong2 b0 = *reinterpret_cast<const ulonglong2 *>(&xb[kk][4 * tx]);
+            const ulonglong2 b1 = *reinterpret_cast<const ulonglong2 *>(&xb[kk][64 + 4 * tx]);
+            const f32x2 bv[4] = {b0.x, b0.y, b1.x, b1.y};
 #pragma unroll
-            for (int c = 0; c < 8; ++c) bv[c] = xj[(tx + 16 * c) * 33 + kk];
+            for (int a = 0; a < 8; ++a) {
 #pragma unroll
-            for (int a = 0; a < 8; ++a)
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const float df = av[a] - bv[c];
-                    acc[a][c] = fmaf(df, df, acc[a][c]);
+                for (int h = 0; h < 4; ++h) {
+                    const f32x2 df = f2_sub(av[a], bv[h]);
+                    acc[a][h] = f2_fma(df, df, acc[a][h]);
                 }
+            }
         }
     }
+    // entries: exp off the diagonal, the diagonal exactly, zero in the padding
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
-        const int r = ty + 16 * a;
+        F2Row d2;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int cc = tx + 16 * c;
-            const int64_t gi = i0 + r, gj = j0 + cc;
-            float v;
-            if (gi == gj) v = g.zero_diag ? 0.f : 1.f;
-            else v = exp_unbiased(-acc[a][c] * g.inv_h);
-            S[r * 129 + cc] = (gi < n && gj < n) ? v : 0.f;
+        for (int h = 0; h < 4; ++h) d2.v[h] = acc[a][h];
+        const F2Row e = f2_rbf_row(d2, g.inv_h);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) acc[a][h] = e.v[h];
+    }
+    if (diag_tile || i0 + kRbfT > n || j0 + kRbfT > n) {
+        const float dv = g.zero_diag ? 0.f : 1.f;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const int64_t gi = i0 + rbf_row(a, ty);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                float e0, e1;
+                f2_unpack(acc[a][h], e0, e1);
+                const int64_t gj0 = j0 + rbf_row(2 * h, tx), gj1 = j0 + rbf_row(2 * h + 1, tx);
+                if (gi == gj0) e0 = dv;
+                if (gi == gj1) e1 = dv;
+                if (gi >= n || gj0 >= n) e0 = 0.f;
+                if (gi >= n || gj1 >= n) e1 = 0.f;
+                acc[a][h] = f2_pack(e0, e1);
+            }
         }
     }
-    __syncthreads();
-    const int64_t plane = n * g.ldp;
-    const bool vec4 = (n % 4 == 0) && (g.ldp % 4 == 0);
-    const float lead_scale = __int_as_float((127 + g.lead_bits) << 23);   // 2^w
-    // the tile (rows i0.., cols j0..) and, off the diagonal, its mirror image;
-    // each thread writes 4 consecutive columns of one row
-    for (int pass = 0; pass < (tm == tn ? 1 : 2); ++pass) {
-        const int64_t r0 = pass ? j0 : i0, c0 = pass ? i0 : j0;
-        for (int e = tid; e < kRbfT * (kRbfT / 4); e += 256) {
-            const int r = e >> 5, c = (e & 31) * 4;
-            const int64_t gr = r0 + r, gc = c0 + c;
-            if (gr >= n) continue;
-            float v[4];
+
+    // fused reductions of K^p (block-uniform control flow)
+    if (g.nred > 0) {
+        __syncthreads();   // the staging buffer becomes the column-partial buffer
+        float *colpart = reinterpret_cast<float *>(&xa[0][0]);   // [8 warps][128]
+        for (int q = 0; q < g.nred; ++q) {
+            const int p = g.red[q].pow;
+            double *out = g.red[q].out;
+            f32x2 cq[4];
+            float rp[8];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] = pass ? S[(c + q) * 129 + r] : S[r * 129 + c + q];
-            if (vec4 && gc + 3 < n) {
-                *reinterpret_cast<float4 *>(g.K + gr * n + gc) = make_float4(v[0], v[1], v[2], v[3]);
+            for (int h = 0; h < 4; ++h) cq[h] = f2_splat(0.f);
+#pragma unroll
+            for (int a = 0; a < 8; ++a) {
+                f32x2 w[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) w[h] = acc[a][h];
+                for (int e = 1; e < p; ++e) {
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) w[h] = f2_mul(w[h], acc[a][h]);
+                }
+                float r0, r1;
+                f2_unpack(f2_add(f2_add(w[0], w[1]), f2_add(w[2], w[3])), r0, r1);
+                rp[a] = r0 + r1;
+#pragma unroll
+                for (int h = 0; h < 4; ++h) cq[h] = f2_add(cq[h], w[h]);
+            }
+            if (g.red[q].vec) {
+                // rows of this tile: reduce over the 16 lanes of one ty
+#pragma unroll
+                for (int a = 0; a < 8; ++a) {
+#pragma unroll
+                    for (int o = 8; o > 0; o >>= 1) rp[a] += __shfl_xor_sync(0xffffffffu, rp[a], o);
+                }
+                if (tx == 0) {
+#pragma unroll
+                    for (int a = 0; a < 8; ++a) {
+                        const int64_t gi = i0 + rbf_row(a, ty);
+                        if (gi < n) atomicAdd(out + gi, (double)rp[a]);
+                    }
+                }
+                if (!diag_tile) {
+                    // rows of the mirror tile = columns of this one
+                    float cv[8];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) f2_unpack(cq[h], cv[2 * h], cv[2 * h + 1]);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) cv[c] += __shfl_xor_sync(0xffffffffu, cv[c], 16);
+                    if (lane < 16) {
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) colpart[warp * kRbfT + rbf_row(c, tx)] = cv[c];
+                    }
+                    __syncthreads();
+                    if (tid < kRbfT && j0 + tid < n) {
+                        float s = 0.f;
+#pragma unroll
+                        for (int w = 0; w < 8; ++w) s += colpart[w * kRbfT + tid];
+                        atomicAdd(out + j0 + tid, (double)s);
+                    }
+                    __syncthreads();
+                }
             } else {
+                double s = (double)(((rp[0] + rp[1]) + (rp[2] + rp[3])) + ((rp[4] + rp[5]) + (rp[6] + rp[7])));
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (gc + q < n) g.K[gr * n + gc + q] = v[q];
-            }
-            if (g.slices) {
-                __nv_bfloat16 dg[4][4];
+                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == 0) dred[warp] = s;
+                __syncthreads();
+                if (tid == 0) {
+                    double tsum = 0.0;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    float y = v[q] * lead_scale;            // row scale 1: |y| <= 2^w, exact
-                    float dd = rintf(y);
-                    dg[0][q] = __float2bfloat16_rn(dd);
-                    float sc = 1.f / 256.f;
-                    for (int p = 1; p < g.planes; ++p) {
-                        y = (y - dd) * 256.f;
-                        dd = rintf(y);
-                        dg[p][q] = __float2bfloat16_rn(dd * sc);
-                        sc *= (1.f / 256.f);
-                    }
+                    for (int w = 0; w < 8; ++w) tsum += dred[w];
+                    atomicAdd(out, diag_tile ? tsum : 2.0 * tsum);
                 }
-                __nv_bfloat16 *dst = g.slices + gr * g.ldp + gc;
-                for (int p = 0; p < g.planes; ++p) {
-                    if (vec4 && gc + 3 < g.ldp) {
-                        uint2 w;
-                        w.x = (uint32_t)__bfloat16_as_ushort(dg[p][0]) | ((uint32_t)__bfloat16_as_ushort(dg[p][1]) << 16);
-                        w.y = (uint32_t)__bfloat16_as_ushort(dg[p][2]) | ((uint32_t)__bfloat16_as_ushort(dg[p][3]) << 16);
-                        *reinterpret_cast<uint2 *>(dst + p * plane) = w;
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            if (gc + q < g.ldp) dst[p * plane + q] = dg[p][q];
-                    }
-                }
+                __syncthreads();
             }
         }
     }
-    if (g.scales && tm == tn && tid < kRbfT && i0 + tid < n) g.scales[i0 + tid] = 1.f;
+
+    const float lead_scale = __int_as_float((127 + g.lead_bits) << 23);   // 2^w
+    float *K = g.K;
+    __nv_bfloat16 *slices = g.slices;
+    const int64_t ldp = g.ldp;
+    const int planes = g.planes;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const int64_t gr = i0 + rbf_row(a, ty);
+        if (gr >= n) continue;
+        F2Row v;
+#pragma unroll
+        for (int h = 0; h < 4; ++h) v.v[h] = acc[a][h];
+        rbf_store_row(K, slices, n, ldp, planes, lead_scale, gr, j0 + 4 * tx, v);
+    }
+    if (!diag_tile) {
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            float c0[8], c1[8];
+#pragma unroll
+            for (int a = 0; a < 8; ++a) f2_unpack(acc[a][h], c0[a], c1[a]);
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const float *cv = s ? c1 : c0;
+                const int64_t gr = j0 + rbf_row(2 * h + s, tx);
+                if (gr >= n) continue;
+                F2Row v;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v.v[q] = f2_pack(cv[2 * q], cv[2 * q + 1]);
+                rbf_store_row(K, slices, n, ldp, planes, lead_scale, gr, i0 + 4 * ty, v);
+            }
+        }
+    }
+    if (g.scales && diag_tile && tid < kRbfT && i0 + tid < n) g.scales[i0 + tid] = 1.f;
 }
 
 // Float64 version (FP64 mode).
@@ -372,6 +635,14 @@ __global__ void vsum_kernel(const double *u, int64_t n, double *out) {
     double s = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         s += u[i];
+    s = block_sum(s);
+    if (threadIdx.x == 0) atomicAdd(out, s);
+}
+
+__global__ void vdot_kernel(const double *u, const double *a, int64_t n, double *out) {
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s = fma(u[i], a[i], s);
     s = block_sum(s);
     if (threadIdx.x == 0) atomicAdd(out, s);
 }
@@ -490,18 +761,17 @@ cudaError_t launch_kbuild(int kind, double param, const void *Xw, bool fp64, int
 }
 
 cudaError_t launch_kbuild_rbf(const float *Xw, int64_t n, int d, double param, int zero_diag, float *K,
-                              void *slices, int64_t ldp, int lead_bits, int planes, float *scales, cudaStream_t s) {
+                              void *slices, int64_t ldp, int lead_bits, int planes, float *scales, int nred,
+                              const int *red_pow, const int *red_vec, double *const *red_out, cudaStream_t s) {
+    if (nred < 0 || nred > kRbfMaxRed || planes < 3 || planes > 4) return cudaErrorInvalidValue;
     RbfArgs g{Xw, n, d, (float)(1.0 / param), zero_diag, K, (__nv_bfloat16 *)slices, slices ? ldp : n, lead_bits,
-              planes, slices ? scales : nullptr};
-    const int smem = (2 * kRbfT * 33 + kRbfT * 129) * 4;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(kbuild_rbf_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
+              planes, slices ? scales : nullptr, nred, {}};
+    for (int q = 0; q < nred; ++q) {
+        if (red_pow[q] < 1 || red_pow[q] > 4) return cudaErrorInvalidValue;
+        g.red[q] = RbfRed{red_pow[q], red_vec[q], red_out[q]};
     }
     const int64_t T = (g.ldp + kRbfT - 1) / kRbfT;
-    kbuild_rbf_tile_kernel<<<(unsigned)(T * (T + 1) / 2), 256, smem, s>>>(g);
+    kbuild_rbf_tile_kernel<<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(g);
     return cudaGetLastError();
 }
 
@@ -537,6 +807,13 @@ cudaError_t launch_vsum(const double *u, int64_t n, double *out, cudaStream_t s)
     int g = (int)((n + 255) / 256);
     if (g > 152) g = 152;
     vsum_kernel<<<g, 256, 0, s>>>(u, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vdot(const double *u, const double *a, int64_t n, double *out, cudaStream_t s) {
+    int g = (int)((n + 255) / 256);
+    if (g > 152) g = 152;
+    vdot_kernel<<<g, 256, 0, s>>>(u, a, n, out);
     return cudaGetLastError();
 }
 

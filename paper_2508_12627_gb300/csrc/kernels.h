@@ -14,9 +14,12 @@ cudaError_t launch_xconvert(const void *X, int x_dtype, int64_t n, int d, void *
 cudaError_t launch_kbuild(int kind, double param, const void *Xw, bool fp64, int64_t n, int d,
                           int zero_diag, void *K, cudaStream_t s);
 // RBF kernel matrix (float32) fused with its split into `planes` bf16 slices of
-// row scale 1 (slices may be null: K only).
+// row scale 1 (slices may be null: K only) and with up to 4 reductions of its
+// entrywise powers: red_vec[q] ? red_out[q][i] += sum_j K_ij^red_pow[q]
+//                              : *red_out[q] += sum_ij K_ij^red_pow[q].
 cudaError_t launch_kbuild_rbf(const float *Xw, int64_t n, int d, double param, int zero_diag, float *K,
-                              void *slices, int64_t ldp, int lead_bits, int planes, float *scales, cudaStream_t s);
+                              void *slices, int64_t ldp, int lead_bits, int planes, float *scales, int nred,
+                              const int *red_pow, const int *red_vec, double *const *red_out, cudaStream_t s);
 cudaError_t launch_loadmat(const double *src, int64_t n, bool fp64, int zero_diag, void *dst,
                            cudaStream_t s);
 cudaError_t launch_unary_tanh(const void *X, int x_dtype, int64_t n, int d, const double *w,
@@ -25,6 +28,8 @@ cudaError_t launch_copyvec(const double *src, int64_t n, double *dst, cudaStream
 cudaError_t launch_diag(const void *M, bool fp64, int64_t n, double *out, cudaStream_t s);
 cudaError_t launch_vmul(const double *a, const double *b, int64_t n, double *out, cudaStream_t s);
 cudaError_t launch_vsum(const double *u, int64_t n, double *out, cudaStream_t s);
+// *out += sum_i u(i) a(i)
+cudaError_t launch_vdot(const double *u, const double *a, int64_t n, double *out, cudaStream_t s);
 
 // ---- tiled elementwise / reduction ops over up to 4 oriented matrix terms (k_hb.cu)
 enum TileMode : int { TILE_HADAMARD = 0, TILE_FREDUCE = 1, TILE_GEMV = 2 };

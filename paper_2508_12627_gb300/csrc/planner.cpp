@@ -33,7 +33,8 @@ namespace ustat {
 const char *op_name(int k) {
     static const char *names[] = {"kbuild", "loadmat", "unary",  "loadvec", "diag",
                                   "vmul",   "hadamard", "gemv",  "vsum",    "gemm",
-                                  "gemm_red", "freduce", "gemm3", "split",  "prep", "mhb"};
+                                  "gemm_red", "freduce", "gemm3", "split",  "prep", "mhb",
+                                  "vdot"};
     return (k >= 0 && k < OP_COUNT) ? names[k] : "?";
 }
 
@@ -959,6 +960,76 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan) {
             if (op.symmetric) op.coef = 1.0;   // half the tiles: n^3 flops instead of 2 n^3
         }
         if (op.kind == OP_GEMM3) P.n_gemm3++;
+    }
+
+    // ---- a reduction weighted by a vector on one index and by ones on the other
+    //      is a dot product with the one-sided sums of the same Hadamard product:
+    //      sum_jk T(j,k) a(j) = sum_j a(j) [sum_k T(j,k)], and a GEMV that forms
+    //      those sums may already exist.  Terms of symmetric slots are compared
+    //      without orientation.
+    {
+        auto canon = [&](const Op &o, bool flip) {
+            std::vector<std::pair<int, int>> v;
+            for (int t = 0; t < o.nt; ++t) {
+                const int tr = P.slots[o.t[t].mat].symmetric ? 0 : (o.t[t].trans ^ (flip ? 1 : 0));
+                v.emplace_back(o.t[t].mat, tr);
+            }
+            std::sort(v.begin(), v.end());
+            return v;
+        };
+        for (size_t i = 0; i < P.ops.size(); ++i) {
+            Op &fr = P.ops[i];
+            if (fr.kind != OP_FREDUCE || (fr.a >= 0) == (fr.b >= 0)) continue;
+            // b(k) weights the second index: GEMV sums over the first, out(k)
+            // a(j) weights the first index: GEMV of the transposed product
+            const auto want = canon(fr, fr.a >= 0);
+            for (size_t j = 0; j < i; ++j) {
+                const Op &gv = P.ops[j];
+                if (gv.kind != OP_GEMV || gv.u >= 0 || canon(gv, false) != want) continue;
+                Op vd;
+                vd.kind = OP_VDOT;
+                vd.out = fr.out;
+                vd.u = gv.out;
+                vd.a = fr.a >= 0 ? fr.a : fr.b;
+                vd.npow = 1;
+                vd.coef = 2;
+                fr = vd;
+                break;
+            }
+        }
+    }
+
+    // ---- entrywise-power reductions of an RBF kernel matrix (full sums, and the
+    //      row sums a GEMV with unit weights forms) are taken by the float32
+    //      kernel-matrix build while the entries are in registers
+    if (P.precision != USTAT_FP64) {
+        std::vector<char> dead(P.ops.size(), 0);
+        for (size_t i = 0; i < P.ops.size(); ++i) {
+            const Op &r = P.ops[i];
+            const bool full = r.kind == OP_FREDUCE && r.a < 0 && r.b < 0;
+            const bool rows = r.kind == OP_GEMV && r.u < 0;
+            if ((!full && !rows) || r.nt < 1 || r.nt > 4) continue;
+            const int s = r.t[0].mat;
+            bool same = true;
+            for (int t = 1; t < r.nt; ++t) same = same && r.t[t].mat == s;
+            if (!same) continue;
+            for (size_t k = 0; k < i; ++k) {
+                Op &kb = P.ops[k];
+                if (kb.kind != OP_KBUILD || kb.out != s || P.factor_kind[kb.factor] != USTAT_RBF ||
+                    kb.nred >= kMaxRed)
+                    continue;
+                Red rd;
+                rd.pow = r.nt;
+                rd.out = r.out;
+                kb.red[kb.nred++] = rd;
+                dead[i] = 1;
+                break;
+            }
+        }
+        std::vector<Op> kept;
+        for (size_t i = 0; i < P.ops.size(); ++i)
+            if (!dead[i]) kept.push_back(P.ops[i]);
+        P.ops.swap(kept);
     }
 
     // ---- schedule by dependency level and merge the n^2 reductions / GEMVs of

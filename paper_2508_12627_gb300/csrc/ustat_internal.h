@@ -41,6 +41,7 @@ enum OpKind : int {
                      //   X(j, i) = t[0](i, j) u(i)
     OP_PREP,         // operand out = fp32 K-major copy X(j, i) = t[0](i, j) u(i) (tf32-rounded)
     OP_MHB,          // several FREDUCE / GEMV ops over the same matrices in one pass
+    OP_VDOT,         // scal out += sum_i u(i) a(i)
     OP_COUNT
 };
 
@@ -58,7 +59,8 @@ struct Op {
     int factor = -1;
     int out = -1;                 // slot written
     int store = 1;                // GEMM: write the product to `out`
-    int nred = 0;                 // GEMM: fused reductions
+    int nred = 0;                 // GEMM / KBUILD: fused reductions (KBUILD: red[r].pow
+                                  // and red[r].out only; a vector out takes row sums)
     Red red[kMaxRed];
     int symmetric = 0;            // GEMM: product and reductions symmetric (upper tiles only)
     Term t[kMaxTerms];
