@@ -28,6 +28,9 @@ METRIC = "U-stat evals/s and TFLOP/s, mixed-prec vs FP64 on GB300 at rel err ≤
 WORKLOADS = {
     "c4_rbf": "m=4 4-cycle kernel K12 K23 K34 K41, RBF K = exp(-||x-y||^2/(2d)), X n=4096 x d=32 iid N(0,1) "
               "float64 seed 0, all 15 partitions",
+    "batched": "512 independent samples, n uniform in [256, 4096] (seed 0), X_i n_i x 16 iid N(0,1) float64 "
+               "(seed 1000+i), each evaluated for the m=4 4-cycle and the m=5 5-cycle RBF kernels (15 and 52 "
+               "partitions): 1024 U-statistics per step, one captured CUDA graph per kernel graph",
 }
 
 
@@ -162,6 +165,149 @@ def run_capture(args):
     print("capture done: U_sum %.17g" % out[0].item())
 
 
+def run_batched(args):
+    """The batched workload: every step replays two captured graphs (4-cycle and
+    5-cycle plans over the same 512 samples), after the autotuner has chosen the
+    lane count and the GEMM tile variants."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    import synth
+    from oracle import ustat_oracle as uo
+    from paper_2508_12627_gb300 import build as B
+    B.build()
+    from paper_2508_12627_gb300 import ustat as us
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    d = 16
+    ns = [int(v) for v in synth.batched_sizes(512, 256, 4096, 0)]
+    Xh = [synth.normal_X(n, d, 1000 + i) for i, n in enumerate(ns)]
+    offs = np.cumsum([0] + [n * d for n in ns])
+    host = torch.empty(int(offs[-1]), dtype=torch.float64).pin_memory()
+    for i, x in enumerate(Xh):
+        host[int(offs[i]):int(offs[i + 1])] = torch.from_numpy(x.ravel())
+    Xdev = host.to(dev)
+    xp = [Xdev.data_ptr() + 8 * int(offs[i]) for i in range(len(ns))]
+    facs = [(uo.RBF, 2.0 * d, 0)]
+    graphs = {"c4": synth.cycle4_graph(), "c5": synth.cycle(5)}
+    stream = torch.cuda.Stream(dev)
+    runs = {}
+    tune = {}
+    for name, g in graphs.items():
+        p = us.Plan(g, [uo.RBF], precision=args.precision)
+        b = us.Batched(p, ns, d, max_lanes=16)
+        ws = torch.empty(b.workspace_bytes(), dtype=torch.uint8, device=dev)
+        U = torch.empty((len(ns), 2), dtype=torch.float64, device=dev)
+        V = torch.empty((len(ns), p.info["n_parts"]), dtype=torch.float64, device=dev)
+        with torch.cuda.stream(stream):
+            lanes, ms = b.autotune(xp, 0, facs, ws.data_ptr(), ws.numel(), stream.cuda_stream, U.data_ptr(),
+                                   V.data_ptr())
+            b.capture(xp, 0, facs, ws.data_ptr(), ws.numel(), stream.cuda_stream, U.data_ptr(), V.data_ptr())
+        tv = [l for l in p.describe().splitlines() if l.startswith("tc_variant=")]
+        tune[name] = {"lanes": lanes, "tuned_ms": ms, "gemm_variants_by_size_class": tv[0][11:] if tv else None}
+        runs[name] = (p, b, ws, U, V)
+    torch.cuda.synchronize()
+
+    def step():
+        for name in graphs:
+            runs[name][1].replay(stream.cuda_stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            starts[k].record(stream)
+            step()
+            ends[k].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    tot_ms = float(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
+    evals = len(ns) * len(graphs)
+    value = evals * args.steps / (tot_ms / 1e3)
+
+    # algorithmic tensor-core work of a step: each GEMM entry costs 2 n multiply-adds
+    alg = 0.0
+    fl_plan = 0.0
+    for name, (p, b, ws, U, V) in runs.items():
+        gl = [l for l in p.describe().splitlines() if " gemm " in l]
+        for n in ns:
+            alg += sum(2.0 * n * (n * (n + 1) / 2 if "sym=1" in l else n * n) for l in gl)
+            fl_plan += p.flops(n)[0]
+    peaks, peak_src = load_peaks()
+    products = {"bf16x3": 6.0, "bf16x4": 10.0, "tf32": 2.0}.get(args.precision)
+    roof = None
+    if products:
+        achieved = alg / (tot_ms / args.steps / 1e3) / 1e12
+        peak = peaks.get("bf16_tflops_sustained", 1700.0) / products
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "tc_gemm_kernel (%s), all launches of a step" % args.precision,
+                "peak_note": "%s bf16 dense sustained %.1f TFLOP/s / %g tensor products per multiply-add; achieved "
+                             "= GEMM algorithmic flops of a step / whole step time (a lower bound on the GEMM's own "
+                             "rate)" % (peak_src, peaks.get("bf16_tflops_sustained", 1700.0), products)}
+
+    # end to end: pinned host X -> device, both graphs, U and V back to the host
+    Uh = {name: torch.empty(r[3].shape, dtype=torch.float64).pin_memory() for name, r in runs.items()}
+    Vh = {name: torch.empty(r[4].shape, dtype=torch.float64).pin_memory() for name, r in runs.items()}
+    ke = min(args.steps, 5)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for _ in range(ke):
+            Xdev.copy_(host, non_blocking=True)
+            step()
+            for name, r in runs.items():
+                Uh[name].copy_(r[3], non_blocking=True)
+                Vh[name].copy_(r[4], non_blocking=True)
+            stream.synchronize()
+    e2e_s = (time.perf_counter() - t1) / ke
+    d2h = sum(int(r[3].numel() + r[4].numel()) * 8 for r in runs.values())
+
+    # accuracy on the smallest samples against the oracle, and the CPU baseline:
+    # the oracle timed on the same few samples
+    order = np.argsort(ns)[:4]
+    cpu_t = 0.0
+    errs = []
+    for name, g in graphs.items():
+        V = runs[name][4].cpu().numpy()
+        for i in order:
+            t2 = time.perf_counter()
+            ref = uo.ustat(g, [synth.Factor(uo.RBF, 2.0 * d, None)], Xh[i])
+            cpu_t += time.perf_counter() - t2
+            errs.append(float(np.max(np.abs(V[i] - np.array(ref["V"])) / np.abs(np.array(ref["V"])))))
+    cpu = {"value": 2 * len(order) / cpu_t, "unit": "evals/s", "cores": host_cores(), "kind": "oracle",
+           "sample": "the 4 smallest samples (n=%s) for both kernel graphs" % [ns[i] for i in order]}
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": WORKLOADS["batched"], "samples": len(ns), "d": d, "precision": args.precision,
+                   "l2": "inputs and kernel matrices far larger than L2", "parallelism": "single",
+                   "tuning": tune},
+        "tflops": {"algorithmic_plan": fl_plan * args.steps / (tot_ms / 1e3) / 1e12},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": evals / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": int(host.numel() * 8),
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(args.steps * sum((r[0].info["n_ops"] + 2) * len(ns) for r in runs.values())),
+        "clocks": clk,
+        "rel_err_vs_oracle": {"V_max_smallest_samples": max(errs)},
+        "wall_s_timed_region": wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -180,6 +326,9 @@ def main():
         return
     if args.capture:
         run_capture(args)
+        return
+    if args.workload == "batched":
+        run_batched(args)
         return
 
     import numpy as np

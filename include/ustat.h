@@ -173,15 +173,67 @@ int ustat_eval_host(ustat_plan_t *plan, const void *X_host, int x_dtype, int64_t
                     void *stream, double *U_host, double *V_host);
 
 /*
- * Many independent samples, one plan: sample i has n[i] rows at X[i] (device,
- * row-major, x_dtype), dimension d; results at U_out[2*i], V_out[i*n_parts].
- * ws is split into equal per-sample regions sized for max(n) by the library.
+ * Many independent samples, one plan, one after another on `stream`: sample i
+ * has n[i] rows at X[i] (device, row-major, x_dtype), dimension d; results at
+ * U_out[2*i], V_out[i*n_parts].  One workspace region sized for max(n) is
+ * reused by every sample (ustat_batch_workspace_bytes).  Factor data are
+ * shared by all samples.  The concurrent, graph-captured form is the
+ * ustat_batched_* object below.
  */
 int ustat_eval_batch(ustat_plan_t *plan, const void *const *X, int x_dtype, const int64_t *n,
                      int count, int d, const ustat_factor *factors, int n_factors, void *ws,
                      size_t ws_bytes, void *stream, double *U_out, double *V_out);
 int ustat_batch_workspace_bytes(const ustat_plan_t *plan, const int64_t *n, int count, int d,
                                 size_t *bytes);
+
+/*
+ * Batched evaluation object: one plan over `count` independent samples of
+ * uneven size n[i] (dimension d), evaluated concurrently.  The paper treats one
+ * sample at a time; batching is this engine's.
+ *
+ * Schedule.  Samples are spread over `lanes` CUDA streams (lanes <= max_lanes)
+ * by longest-processing-time first on the plan's flop count at n[i]; each lane
+ * runs its samples in order in its own workspace region, so small samples of
+ * one lane overlap large samples of another.  The lanes fork from and join
+ * back into the caller's stream with events.
+ *
+ * Graph.  ustat_batched_capture records one whole batched evaluation (every
+ * sample, every partition, every lane) into a CUDA graph bound to the given X,
+ * factor and output pointers; ustat_batched_replay launches that graph on a
+ * stream (one host call per batch).  Capture needs a stream other than the
+ * legacy default stream and per-operation profiling off.
+ *
+ * Autotuning.  ustat_batched_autotune times the batch (eagerly, synchronising
+ * `stream`) for each lane count in {1, 2, 4, ...} <= max_lanes and for each
+ * tensor-core GEMM tile variant per size class, keeps the fastest, stores the
+ * GEMM choices in the plan (used by every later evaluation with that plan) and
+ * returns the chosen lane count and time.  Re-capture after autotuning.
+ *
+ * Ownership and errors.  The object keeps a pointer to `plan` (which must
+ * outlive it), its own copy of n[], its streams, events and graph.  The caller
+ * owns X, factors, the workspace (ustat_batched_workspace_bytes, for
+ * max_lanes lanes, 256-byte aligned) and U_out[2*count], V_out[count*n_parts].
+ * Factor kinds with per-sample data (MATRIX, VECTOR) are rejected
+ * (USTAT_ERR_UNSUPPORTED); n[i] < m gives USTAT_ERR_N_LT_M.  Streams are
+ * created on the device current at the first run.
+ */
+typedef struct ustat_batched ustat_batched_t;
+int ustat_batched_create(ustat_plan_t *plan, const int64_t *n, int count, int d, int max_lanes,
+                         ustat_batched_t **out);
+void ustat_batched_destroy(ustat_batched_t *b);
+int ustat_batched_workspace_bytes(const ustat_batched_t *b, size_t *bytes);
+/* lanes in use; lane_of[i] (may be NULL) receives sample i's lane */
+int ustat_batched_info(const ustat_batched_t *b, int *lanes, int *lane_of);
+int ustat_batched_set_lanes(ustat_batched_t *b, int lanes);
+int ustat_batched_run(ustat_batched_t *b, const void *const *X, int x_dtype, const ustat_factor *factors,
+                      int n_factors, void *ws, size_t ws_bytes, void *stream, double *U_out, double *V_out);
+int ustat_batched_capture(ustat_batched_t *b, const void *const *X, int x_dtype,
+                          const ustat_factor *factors, int n_factors, void *ws, size_t ws_bytes,
+                          void *stream, double *U_out, double *V_out);
+int ustat_batched_replay(ustat_batched_t *b, void *stream);
+int ustat_batched_autotune(ustat_batched_t *b, const void *const *X, int x_dtype,
+                           const ustat_factor *factors, int n_factors, void *ws, size_t ws_bytes,
+                           void *stream, double *U_out, double *V_out, int *lanes_out, double *ms_out);
 
 /*
  * Evaluation that allocates nothing: for callers that must not call cudaMalloc

@@ -294,7 +294,9 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                                          (double *)C.ptr(R.out)};
                     }
                     g.symmetric = op.symmetric;
-                    if (P.precision == USTAT_BF16X3) e = launch_gemm_bf16x3(g, C.st);
+                    const int var = P.tc_variant[tc_size_class(n)];
+                    g.group_rows = kGroupRows[var & 3];
+                    if (P.precision == USTAT_BF16X3) e = launch_gemm_bf16x3(g, ((var >> 2) & 1) && !op.symmetric, C.st);
                     else if (P.precision == USTAT_BF16X4) e = launch_gemm_bf16x4(g, C.st);
                     else e = launch_gemm_tf32(g, C.st);
                 } else {
@@ -588,6 +590,9 @@ extern "C" int ustat_plan_describe(const ustat_plan_t *plan, char *buf, size_t b
                      term(o.Wbc).c_str(), term(o.Wbd).c_str(), vec(o.ub).c_str());
         s += line;
     }
+    snprintf(line, sizeof(line), "tc_variant=[%d,%d,%d,%d]\n", P.tc_variant[0], P.tc_variant[1], P.tc_variant[2],
+             P.tc_variant[3]);
+    s += line;
     for (size_t p = 0; p < P.parts.size(); ++p) {
         const PartRec &r = P.parts[p];
         std::string rg, sc;
@@ -647,3 +652,291 @@ extern "C" int ustat_eval_noalloc(ustat_plan_t *plan, const void *X, int x_dtype
     return ustat_eval(plan, X, x_dtype, n, d, factors, n_factors, base, (size_t)USTAT_NOALLOC_MAX_BYTES, stream, U_out,
                       V_out);
 }
+
+// ---------------------------------------------------------------- batched evaluation
+// Samples spread over CUDA streams ("lanes") by longest-processing-time first,
+// each lane with its own workspace region; the lanes fork from and join into
+// the caller's stream.  A whole batch can be captured into one CUDA graph.
+struct ustat_batched {
+    ustat_plan_t *plan = nullptr;
+    int d = 0;
+    std::vector<int64_t> n;
+    int max_lanes = 1, lanes = 1;
+    std::vector<int> lane_of;
+    size_t lane_bytes = 0;
+    int device = -1;
+    std::vector<cudaStream_t> streams;   // max_lanes, created at the first run
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+void batched_schedule(ustat_batched *b) {
+    const Plan &P = b->plan->p;
+    const int cnt = (int)b->n.size();
+    std::vector<int> order(cnt);
+    std::vector<double> cost(cnt);
+    for (int i = 0; i < cnt; ++i) {
+        double fp = 0.0;
+        for (auto &op : P.ops) fp += op.coef * std::pow((double)b->n[i], op.npow);
+        // a fixed per-sample charge for the launches of small samples
+        cost[i] = fp + 2.0e9;
+        order[i] = i;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+    std::vector<double> load(b->lanes, 0.0);
+    b->lane_of.assign(cnt, 0);
+    for (int i : order) {
+        int best = 0;
+        for (int l = 1; l < b->lanes; ++l)
+            if (load[l] < load[best]) best = l;
+        b->lane_of[i] = best;
+        load[best] += cost[i];
+    }
+}
+
+int batched_setup(ustat_batched *b) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (b->device >= 0) return dev == b->device ? USTAT_OK : USTAT_ERR_INVALID_ARG;
+    b->streams.assign(b->max_lanes, nullptr);
+    b->joins.assign(b->max_lanes, nullptr);
+    for (int l = 0; l < b->max_lanes; ++l) {
+        e = cudaStreamCreateWithFlags(&b->streams[l], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->joins[l], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e);
+    b->device = dev;
+    return USTAT_OK;
+}
+
+int batched_body(ustat_batched *b, const void *const *X, int x_dtype, const ustat_factor *f, int nf, char *ws,
+                 cudaStream_t st, double *U_out, double *V_out) {
+    const Plan &P = b->plan->p;
+    const int np = (int)P.parts.size();
+    cudaError_t e = cudaEventRecord(b->fork, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    for (int l = 0; l < b->lanes; ++l) {
+        e = cudaStreamWaitEvent(b->streams[l], b->fork, 0);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    for (int l = 0; l < b->lanes; ++l) {
+        char *lws = ws + (size_t)l * b->lane_bytes;
+        for (size_t i = 0; i < b->n.size(); ++i) {
+            if (b->lane_of[i] != l) continue;
+            Layout L = make_layout(P, b->n[i], b->d);
+            Ctx C{P, L, lws, b->n[i], b->d, P.precision == USTAT_FP64, b->streams[l]};
+            int rc = run_program(C, X[i], x_dtype, f, U_out + 2 * i, V_out ? V_out + i * (size_t)np : nullptr);
+            if (rc != USTAT_OK) return rc;
+        }
+    }
+    for (int l = 0; l < b->lanes; ++l) {
+        e = cudaEventRecord(b->joins[l], b->streams[l]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->joins[l], 0);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return USTAT_OK;
+}
+
+int batched_check(ustat_batched *b, const void *const *X, int x_dtype, const ustat_factor *f, int nf, void *ws,
+                  size_t ws_bytes, double *U_out) {
+    if (!b || !X || !U_out || (x_dtype != 0 && x_dtype != 1)) return USTAT_ERR_INVALID_ARG;
+    const Plan &P = b->plan->p;
+    int rc = check_graph_factors(P, f, nf, b->d);
+    if (rc != USTAT_OK) return rc;
+    for (int i = 0; i < nf; ++i)
+        if (f[i].kind == USTAT_MATRIX || f[i].kind == USTAT_VECTOR) return USTAT_ERR_UNSUPPORTED;
+    for (size_t i = 0; i < b->n.size(); ++i)
+        if (!X[i]) return USTAT_ERR_INVALID_ARG;
+    if (!ws || ((uintptr_t)ws % 256) != 0 || ws_bytes < (size_t)b->max_lanes * b->lane_bytes)
+        return USTAT_ERR_WORKSPACE;
+    return batched_setup(b);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ustat_batched_create(ustat_plan_t *plan, const int64_t *n, int count, int d, int max_lanes,
+                         ustat_batched_t **out) {
+    if (!plan || !n || count < 1 || d < 1 || !out || max_lanes < 0 || max_lanes > 32) return USTAT_ERR_INVALID_ARG;
+    const Plan &P = plan->p;
+    for (int i = 0; i < count; ++i) {
+        if (n[i] < P.m) return USTAT_ERR_N_LT_M;
+        if (n[i] > (int64_t)1 << 20) return USTAT_ERR_UNSUPPORTED;
+    }
+    ustat_batched *b = new (std::nothrow) ustat_batched();
+    if (!b) return USTAT_ERR_INVALID_ARG;
+    b->plan = plan;
+    b->d = d;
+    b->n.assign(n, n + count);
+    b->max_lanes = max_lanes == 0 ? 8 : max_lanes;
+    b->lanes = std::min(b->max_lanes, count);
+    for (int i = 0; i < count; ++i) b->lane_bytes = std::max(b->lane_bytes, make_layout(P, n[i], d).total);
+    b->lane_bytes = align_up(b->lane_bytes, 256);
+    batched_schedule(b);
+    *out = b;
+    return USTAT_OK;
+}
+
+void ustat_batched_destroy(ustat_batched_t *b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto s : b->streams)
+        if (s) cudaStreamDestroy(s);
+    for (auto e : b->joins)
+        if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    delete b;
+}
+
+int ustat_batched_workspace_bytes(const ustat_batched_t *b, size_t *bytes) {
+    if (!b || !bytes) return USTAT_ERR_INVALID_ARG;
+    *bytes = (size_t)b->max_lanes * b->lane_bytes;
+    return USTAT_OK;
+}
+
+int ustat_batched_info(const ustat_batched_t *b, int *lanes, int *lane_of) {
+    if (!b) return USTAT_ERR_INVALID_ARG;
+    if (lanes) *lanes = b->lanes;
+    if (lane_of)
+        for (size_t i = 0; i < b->lane_of.size(); ++i) lane_of[i] = b->lane_of[i];
+    return USTAT_OK;
+}
+
+int ustat_batched_set_lanes(ustat_batched_t *b, int lanes) {
+    if (!b || lanes < 1 || lanes > b->max_lanes) return USTAT_ERR_INVALID_ARG;
+    b->lanes = std::min(lanes, (int)b->n.size());
+    batched_schedule(b);
+    return USTAT_OK;
+}
+
+int ustat_batched_run(ustat_batched_t *b, const void *const *X, int x_dtype, const ustat_factor *factors,
+                      int n_factors, void *ws, size_t ws_bytes, void *stream, double *U_out, double *V_out) {
+    int rc = batched_check(b, X, x_dtype, factors, n_factors, ws, ws_bytes, U_out);
+    if (rc != USTAT_OK) return rc;
+    return batched_body(b, X, x_dtype, factors, n_factors, (char *)ws, (cudaStream_t)stream, U_out, V_out);
+}
+
+int ustat_batched_capture(ustat_batched_t *b, const void *const *X, int x_dtype, const ustat_factor *factors,
+                          int n_factors, void *ws, size_t ws_bytes, void *stream, double *U_out, double *V_out) {
+    int rc = batched_check(b, X, x_dtype, factors, n_factors, ws, ws_bytes, U_out);
+    if (rc != USTAT_OK) return rc;
+    if (!stream || g_prof.on) return USTAT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    if (b->graph) {
+        cudaGraphDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e);
+    rc = batched_body(b, X, x_dtype, factors, n_factors, (char *)ws, st, U_out, V_out);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(st, &g);
+    if (rc != USTAT_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    b->graph = g;
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return USTAT_OK;
+}
+
+int ustat_batched_replay(ustat_batched_t *b, void *stream) {
+    if (!b || !b->exec) return USTAT_ERR_INVALID_ARG;
+    cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+    return e == cudaSuccess ? USTAT_OK : cuda_fail(e);
+}
+
+int ustat_batched_autotune(ustat_batched_t *b, const void *const *X, int x_dtype, const ustat_factor *factors,
+                           int n_factors, void *ws, size_t ws_bytes, void *stream, double *U_out, double *V_out,
+                           int *lanes_out, double *ms_out) {
+    int rc = batched_check(b, X, x_dtype, factors, n_factors, ws, ws_bytes, U_out);
+    if (rc != USTAT_OK) return rc;
+    if (g_prof.on) return USTAT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    Plan &P = b->plan->p;
+    cudaEvent_t t0, t1;
+    cudaError_t e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    if (e != cudaSuccess) return cuda_fail(e);
+    // time of one batched evaluation: the best of two after a warm-up
+    auto timed = [&](double *ms) -> int {
+        double best = 1e300;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaError_t ee = cudaEventRecord(t0, st);
+            if (ee != cudaSuccess) return cuda_fail(ee);
+            int r = batched_body(b, X, x_dtype, factors, n_factors, (char *)ws, st, U_out, V_out);
+            if (r != USTAT_OK) return r;
+            ee = cudaEventRecord(t1, st);
+            if (ee == cudaSuccess) ee = cudaEventSynchronize(t1);
+            if (ee != cudaSuccess) return cuda_fail(ee);
+            float f = 0.f;
+            cudaEventElapsedTime(&f, t0, t1);
+            if (rep > 0) best = std::min(best, (double)f);
+        }
+        *ms = best;
+        return USTAT_OK;
+    };
+    double best_ms = 1e300;
+    int best_lanes = b->lanes;
+    // lane count first (default GEMM variants), then the GEMM variant of each
+    // size class present in the batch, one class at a time
+    for (int L = 1; L <= std::min(b->max_lanes, (int)b->n.size()); L *= 2) {
+        b->lanes = L;
+        batched_schedule(b);
+        double ms = 0.0;
+        rc = timed(&ms);
+        if (rc != USTAT_OK) break;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_lanes = L;
+        }
+    }
+    b->lanes = best_lanes;
+    batched_schedule(b);
+    if (rc == USTAT_OK && is_tc_mode(P.precision)) {
+        bool present[4] = {false, false, false, false};
+        for (int64_t v : b->n) present[tc_size_class(v)] = true;
+        const int nvar = P.precision == USTAT_BF16X3 ? 8 : 4;
+        for (int c = 0; c < 4 && rc == USTAT_OK; ++c) {
+            if (!present[c]) continue;
+            int best_v = P.tc_variant[c];
+            for (int v = 0; v < nvar; ++v) {
+                if (v == best_v) continue;
+                const int keep = P.tc_variant[c];
+                P.tc_variant[c] = v;
+                double ms = 0.0;
+                rc = timed(&ms);
+                if (rc != USTAT_OK) break;
+                if (ms < best_ms * 0.995) {
+                    best_ms = ms;
+                    best_v = v;
+                }
+                P.tc_variant[c] = keep;
+            }
+            P.tc_variant[c] = best_v;
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (rc != USTAT_OK) return rc;
+    if (lanes_out) *lanes_out = b->lanes;
+    if (ms_out) *ms_out = best_ms;
+    return USTAT_OK;
+}
+
+}  // extern "C"

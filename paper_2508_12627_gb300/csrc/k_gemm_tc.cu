@@ -301,27 +301,29 @@ __host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t M, uint
 constexpr int kBM = 128;
 constexpr int kThreads = 192;
 
-template <int kMode>   // 0 = split bf16 x3, 1 = tf32, 2 = split bf16 x4
+// 0 = split bf16 x3, 128 x 128 tiles; 1 = tf32; 2 = split bf16 x4 (128 x 64);
+// 3 = split bf16 x3 with 128 x 64 tiles and a deeper pipeline
+template <int kMode>
 struct Cfg {
     static constexpr bool kTf32 = kMode == 1;
-    static constexpr int kPlanes = kMode == 0 ? 3 : (kMode == 1 ? 1 : 4);
-    static constexpr int kBN = kMode == 2 ? 64 : 128;
+    static constexpr int kPlanes = (kMode == 0 || kMode == 3) ? 3 : (kMode == 1 ? 1 : 4);
+    static constexpr int kBN = (kMode == 2 || kMode == 3) ? 64 : 128;
     static constexpr int kBKElems = kTf32 ? 32 : 64;       // 128 bytes per row
     static constexpr int kMmaK = kTf32 ? 8 : 16;            // 32 bytes per MMA k step
     static constexpr int kATile = kBM * 128;                // one plane of A
     static constexpr int kBTile = kBN * 128;                // one plane of B
     static constexpr int kStageBytes = kPlanes * (kATile + kBTile);
-    static constexpr int kStages = kTf32 ? 6 : 2;
+    static constexpr int kStages = kTf32 ? 6 : (kMode == 3 ? 3 : 2);
     static constexpr int kAccCols = kTf32 ? kBN : 2 * kBN;  // hi (+ lo)
     static constexpr int kTmemCols = 2 * kAccCols;          // double buffer
     static constexpr int kSmem = kStages * kStageBytes + 1024 + 512;
 };
 
-// Tile t of the schedule, in closed form.  Full grid: grouped raster (8 tile
+// Tile t of the schedule, in closed form.  Full grid: grouped raster (G tile
 // rows per group, column-major inside a group, so concurrently running CTAs share
 // A and B panels).  Symmetric: the upper triangle tm <= tn in row-major order.
 struct TileWalk {
-    int tiles_m, tiles_n, symmetric;
+    int tiles_m, tiles_n, symmetric, G;
     __device__ int count() const {
         return symmetric ? tiles_m * (tiles_m + 1) / 2 : tiles_m * tiles_n;
     }
@@ -338,7 +340,6 @@ struct TileWalk {
             tn = r + (t - (r * T - r * (r - 1) / 2));
             return;
         }
-        const int G = 8;
         const int per_group = G * tiles_n;
         const int group = t / per_group;
         const int first = group * G;
@@ -372,7 +373,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n = g.n;
     const int num_k = (int)(g.ldp / C::kBKElems);
-    TileWalk walk{(int)((n + kBM - 1) / kBM), (int)((n + C::kBN - 1) / C::kBN), g.symmetric};
+    TileWalk walk{(int)((n + kBM - 1) / kBM), (int)((n + C::kBN - 1) / C::kBN), g.symmetric,
+                  g.group_rows > 0 ? g.group_rows : 8};
     const int total_tiles = walk.count();
 
     if (threadIdx.x == 0) {
@@ -648,12 +650,14 @@ cudaError_t launch_tc(const TcGemmArgs &g0, cudaStream_t s) {
     if (!make_map(&ma, g.opA, bf16, C::kPlanes, g.n, g.ldp, kBM) ||
         !make_map(&mb, g.opB, bf16, C::kPlanes, g.n, g.ldp, C::kBN))
         return cudaErrorInvalidValue;
-    static bool attr = false;
-    if (!attr) {
+    static bool attr[64] = {false};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr[dev]) {
         cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              C::kSmem);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr[dev] = true;
     }
     const int64_t tm = (g.n + kBM - 1) / kBM, tn = (g.n + C::kBN - 1) / C::kBN;
     const int64_t tiles = g.symmetric ? tm * (tm + 1) / 2 : tm * tn;
@@ -684,7 +688,9 @@ cudaError_t launch_prep(const float *M, int trans, const double *u, int64_t n, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_gemm_bf16x3(const TcGemmArgs &g, cudaStream_t s) { return launch_tc<0>(g, s); }
+cudaError_t launch_gemm_bf16x3(const TcGemmArgs &g, int narrow, cudaStream_t s) {
+    return narrow ? launch_tc<3>(g, s) : launch_tc<0>(g, s);
+}
 cudaError_t launch_gemm_tf32(const TcGemmArgs &g, cudaStream_t s) { return launch_tc<1>(g, s); }
 cudaError_t launch_gemm_bf16x4(const TcGemmArgs &g, cudaStream_t s) { return launch_tc<2>(g, s); }
 

@@ -140,8 +140,11 @@ struct TcGemmArgs {
     TcRed red[4];
     int symmetric;                           // C = C^T and every reduction symmetric
     int *err;                                // device error word (bounded waits)
+    int group_rows;                          // tile rows per raster group (0: 8)
 };
-cudaError_t launch_gemm_bf16x3(const TcGemmArgs &g, cudaStream_t s);
+// narrow: 128 x 64 tiles with a three-stage pipeline instead of 128 x 128 (no
+// symmetric tile skipping)
+cudaError_t launch_gemm_bf16x3(const TcGemmArgs &g, int narrow, cudaStream_t s);
 cudaError_t launch_gemm_bf16x4(const TcGemmArgs &g, cudaStream_t s);
 cudaError_t launch_gemm_tf32(const TcGemmArgs &g, cudaStream_t s);
 

@@ -65,6 +65,16 @@ EXPORTS = {
     "ustat_eval_batch": (_i, [_vp, _P(_vp), _i, _P(_i64), _i, _i, _P(ustat_factor), _i, _vp, _sz, _vp,
                               _vp, _vp]),
     "ustat_batch_workspace_bytes": (_i, [_vp, _P(_i64), _i, _i, _P(_sz)]),
+    "ustat_batched_create": (_i, [_vp, _P(_i64), _i, _i, _i, _P(_vp)]),
+    "ustat_batched_destroy": (None, [_vp]),
+    "ustat_batched_workspace_bytes": (_i, [_vp, _P(_sz)]),
+    "ustat_batched_info": (_i, [_vp, _P(_i), _P(_i)]),
+    "ustat_batched_set_lanes": (_i, [_vp, _i]),
+    "ustat_batched_run": (_i, [_vp, _P(_vp), _i, _P(ustat_factor), _i, _vp, _sz, _vp, _vp, _vp]),
+    "ustat_batched_capture": (_i, [_vp, _P(_vp), _i, _P(ustat_factor), _i, _vp, _sz, _vp, _vp, _vp]),
+    "ustat_batched_replay": (_i, [_vp, _vp]),
+    "ustat_batched_autotune": (_i, [_vp, _P(_vp), _i, _P(ustat_factor), _i, _vp, _sz, _vp, _vp, _vp, _P(_i),
+                                    _P(_d)]),
     "ustat_profile_enable": (_i, [_i]),
     "ustat_profile_kinds": (_i, []),
     "ustat_profile_kind_name": (ctypes.c_char_p, [_i]),
@@ -229,6 +239,68 @@ def batch_workspace_bytes(plan, ns, d):
     _check(lib().ustat_batch_workspace_bytes(plan.handle, na, len(ns), d, ctypes.byref(s)),
            "ustat_batch_workspace_bytes")
     return s.value
+
+
+class Batched:
+    """Owns a ustat_batched_t: one plan over many samples of uneven size, run on
+    several streams, optionally captured into one CUDA graph.  Pointers are plain
+    integers (device addresses)."""
+
+    def __init__(self, plan, ns, d, max_lanes=0):
+        self.plan = plan   # keeps the plan alive
+        self.count = len(ns)
+        self.ns = [int(v) for v in ns]
+        na = (_i64 * self.count)(*self.ns)
+        h = _vp()
+        _check(lib().ustat_batched_create(plan.handle, na, self.count, int(d), int(max_lanes), ctypes.byref(h)),
+               "ustat_batched_create")
+        self.handle = h
+
+    def workspace_bytes(self):
+        s = _sz()
+        _check(lib().ustat_batched_workspace_bytes(self.handle, ctypes.byref(s)), "ustat_batched_workspace_bytes")
+        return s.value
+
+    def info(self):
+        lanes = _i()
+        lane_of = (_i * self.count)()
+        _check(lib().ustat_batched_info(self.handle, ctypes.byref(lanes), lane_of), "ustat_batched_info")
+        return lanes.value, list(lane_of)
+
+    def set_lanes(self, lanes):
+        _check(lib().ustat_batched_set_lanes(self.handle, int(lanes)), "ustat_batched_set_lanes")
+
+    def _args(self, X_ptrs, factors):
+        if len(X_ptrs) != self.count:
+            raise ValueError("one X pointer per sample")
+        return (_vp * self.count)(*X_ptrs), factor_array(factors)
+
+    def run(self, X_ptrs, x_dtype, factors, ws_ptr, ws_bytes, stream, U_ptr, V_ptr):
+        xp, fa = self._args(X_ptrs, factors)
+        _check(lib().ustat_batched_run(self.handle, xp, x_dtype, fa, len(factors), ws_ptr, ws_bytes, stream, U_ptr,
+                                       V_ptr), "ustat_batched_run")
+
+    def capture(self, X_ptrs, x_dtype, factors, ws_ptr, ws_bytes, stream, U_ptr, V_ptr):
+        xp, fa = self._args(X_ptrs, factors)
+        _check(lib().ustat_batched_capture(self.handle, xp, x_dtype, fa, len(factors), ws_ptr, ws_bytes, stream,
+                                           U_ptr, V_ptr), "ustat_batched_capture")
+
+    def replay(self, stream):
+        _check(lib().ustat_batched_replay(self.handle, stream), "ustat_batched_replay")
+
+    def autotune(self, X_ptrs, x_dtype, factors, ws_ptr, ws_bytes, stream, U_ptr, V_ptr):
+        xp, fa = self._args(X_ptrs, factors)
+        lanes, ms = _i(), _d()
+        _check(lib().ustat_batched_autotune(self.handle, xp, x_dtype, fa, len(factors), ws_ptr, ws_bytes, stream,
+                                            U_ptr, V_ptr, ctypes.byref(lanes), ctypes.byref(ms)),
+               "ustat_batched_autotune")
+        return lanes.value, ms.value
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.ustat_batched_destroy(h)
+            self.handle = None
 
 
 def profile_enable(on: bool):
