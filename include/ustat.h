@@ -236,6 +236,70 @@ int ustat_batched_autotune(ustat_batched_t *b, const void *const *X, int x_dtype
                            void *stream, double *U_out, double *V_out, int *lanes_out, double *ms_out);
 
 /*
+ * Learned elimination-order ranker.  The paper picks each Einsum's summation
+ * order with opt_einsum's greedy or dp search (Section 3.2; Appendix F compares
+ * the two).  This engine's exhaustive and min-fill planners are the fallback and
+ * the reference; the ranker is a small MLP cost model, trained on measured
+ * times that the planner's own candidates produce, that picks per partition the
+ * candidate of least predicted time.
+ *
+ * Candidates.  ustat_order_candidates lists the distinct feasible elimination
+ * sequences of partition `part` (restricted-growth-string index; -1 = the
+ * finest partition, i.e. the kernel graph's own contraction) with
+ * USTAT_RANK_FEATURES float features each (log2 n and its square; counts of the
+ * step kinds the sequence lowers to in isolation, of its symmetric n^3
+ * products, of all its steps and of its stored n x n intermediates; the
+ * Hadamard terms read; log2 of its flop count, of its n^3 and n^4 parts; the
+ * quotient's size).  Writes
+ * min(*count, max_cand) rows: orders[i*m ..] (block ids, -1 padded) and
+ * features[i*USTAT_RANK_FEATURES ..].  Host only.
+ *
+ * ustat_plan_contraction: a plan that evaluates only the finest partition's
+ * V-statistic (the other V_pi are reported as 0 and U is not the U-statistic)
+ * along `order` (m vertex ids; NULL = the planner's choice); the timing target
+ * of the ranker's training data.  Host only.
+ *
+ * MLP.  F = features inputs, two hidden ReLU layers of `hidden` units, one
+ * output; float32 parameters in one device array of ustat_mlp_param_count
+ * entries [W1 (hidden x F, row-major), b1, W2 (hidden x hidden), b2, w3, b3].
+ * ustat_mlp_forward: y[r] for the rows of X (rows x F, device).
+ * ustat_mlp_loss_grad: *loss = mean_r (y[r] - target[r])^2 and grad = its
+ * gradient w.r.t. the parameters (both device, overwritten); needs
+ * ustat_mlp_workspace_bytes of 256-byte aligned device workspace.
+ * ustat_mlp_adam: one Adam step (Kingma and Ba) at step number `step` >= 1,
+ * updating params, m and v in place.  F <= 32 and hidden <= 64.
+ *
+ * ustat_plan_learned: plan the U-statistic with, for every partition, the
+ * candidate of least predicted time under `params` (hidden units `hidden`,
+ * F = USTAT_RANK_FEATURES) at sample size n.  The features go through `ws`
+ * (ustat_rank_workspace_bytes, device) and the forward kernel runs on `stream`,
+ * which the call synchronises.  The rest of the planning (sharing, fusion) is
+ * as for ustat_plan.
+ */
+#define USTAT_RANK_FEATURES 20
+int ustat_order_candidates(const ustat_graph *graph, const ustat_options *opts, int64_t n, int part,
+                           int max_cand, int *count, int *orders, float *features);
+int ustat_plan_contraction(const ustat_graph *graph, const ustat_options *opts, const int *order,
+                           ustat_plan_t **out);
+/* the features of one given order of partition `part` (order: its block ids,
+ * -1 padded to m); and the order a plan chose for every partition
+ * (orders[n_parts*m], -1 padded; -1 rows for partitions not evaluated) */
+int ustat_order_features(const ustat_graph *graph, const ustat_options *opts, int64_t n, int part,
+                         const int *order, float *features);
+int ustat_plan_orders(const ustat_plan_t *plan, int *orders);
+int ustat_mlp_param_count(int features, int hidden);
+int ustat_mlp_workspace_bytes(int features, int hidden, int rows, size_t *bytes);
+int ustat_mlp_forward(const float *params, int features, int hidden, const float *X, int rows, float *y,
+                      void *stream);
+int ustat_mlp_loss_grad(const float *params, int features, int hidden, const float *X, const float *target,
+                        int rows, void *ws, size_t ws_bytes, float *grad, float *loss, void *stream);
+int ustat_mlp_adam(float *params, const float *grad, float *m, float *v, int count, float lr, float beta1,
+                   float beta2, float eps, int step, void *stream);
+int ustat_rank_workspace_bytes(const ustat_graph *graph, const ustat_options *opts, size_t *bytes);
+int ustat_plan_learned(const ustat_graph *graph, const ustat_options *opts, int64_t n, const float *params,
+                       int hidden, void *ws, size_t ws_bytes, void *stream, ustat_plan_t **out);
+
+/*
  * Evaluation that allocates nothing: for callers that must not call cudaMalloc
  * (or any allocating routine) at evaluation time.  Examples are a service that
  * reserves all its device memory at start-up and forbids allocation afterwards;

@@ -369,6 +369,8 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
 
 }  // namespace
 
+int ustat::record_cuda_error(int e) { return cuda_fail((cudaError_t)e); }
+
 extern "C" {
 
 int ustat_plan(const ustat_graph *graph, const ustat_options *opts, ustat_plan_t **out) {

@@ -19,6 +19,7 @@
 //   - treewidth (Definitions "Vertex Elimination" and "Treewidth"), computed
 //     exactly by dynamic programming over vertex subsets.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <functional>
 #include <map>
@@ -368,7 +369,53 @@ int exact_treewidth(int k, const std::vector<uint32_t> &adj) {
     return tw[(1u << k) - 1];
 }
 
-int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan) {
+// Features of the program one elimination sequence lowers to, in isolation
+// (no sharing with other partitions): log2 n (and its square); counts of each
+// step kind, of the n^3 products of an operand with itself (symmetric: half
+// the tiles), of all steps and of stored n x n intermediates; the Hadamard
+// terms read; the flop count of the whole sequence and of its n^3 and n^4
+// steps (log2); the quotient's size.  Scaled to O(1).
+void order_features(const std::vector<Op> &ops, size_t first, int k, int n_edges, int n_vecs, int64_t n,
+                    float *f) {
+    for (int i = 0; i < kRankFeatures; ++i) f[i] = 0.f;
+    const double dn = (double)(n < 2 ? 2 : n);
+    double fl = 0.0, fl3 = 0.0, fl4 = 0.0;
+    int cnt[OP_COUNT + 1] = {0};
+    int terms = 0, sym = 0, stored = 0;
+    for (size_t i = first; i < ops.size(); ++i) {
+        const Op &o = ops[i];
+        cnt[o.kind]++;
+        if ((o.kind == OP_GEMM || o.kind == OP_GEMM_RED) && o.A == o.B && o.u < 0) ++sym;
+        if (o.kind == OP_GEMM || o.kind == OP_HADAMARD) ++stored;
+        const double c = o.coef * std::pow(dn, o.npow);
+        fl += c;
+        if (o.npow == 3) fl3 += c;
+        if (o.npow == 4) fl4 += c;
+        if (o.kind == OP_HADAMARD || o.kind == OP_GEMV || o.kind == OP_FREDUCE) terms += o.nt;
+    }
+    f[0] = (float)(std::log2(dn) / 12.0);
+    f[1] = cnt[OP_GEMM] / 4.f;
+    f[2] = cnt[OP_GEMM_RED] / 4.f;
+    f[3] = cnt[OP_GEMM3] / 4.f;
+    f[4] = cnt[OP_GEMV] / 4.f;
+    f[5] = cnt[OP_FREDUCE] / 4.f;
+    f[6] = cnt[OP_HADAMARD] / 4.f;
+    f[7] = cnt[OP_VSUM] / 4.f;
+    f[8] = cnt[OP_VMUL] / 8.f;
+    f[9] = terms / 16.f;
+    f[10] = (float)(std::log2(1.0 + fl) / 48.0);
+    f[11] = (float)(std::log2(1.0 + fl3) / 48.0);
+    f[12] = (float)(std::log2(1.0 + fl4) / 48.0);
+    f[13] = k / 8.f;
+    f[14] = n_edges / 16.f;
+    f[15] = n_vecs / 8.f;
+    f[16] = sym / 4.f;
+    f[17] = (float)(ops.size() - first) / 16.f;
+    f[18] = stored / 8.f;
+    f[19] = f[0] * f[0];
+}
+
+int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan, const PlanRequest *req) {
     if (!g || !o || !plan) return USTAT_ERR_INVALID_ARG;
     const int m = g->m;
     if (m < 1) return USTAT_ERR_INVALID_ARG;
@@ -438,8 +485,11 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan) {
 
     std::vector<std::vector<int>> parts;
     enum_partitions(m, parts);
+    if (req && req->forced && req->forced->size() != parts.size()) return USTAT_ERR_INVALID_ARG;
+    if (req && req->collect) req->collect->assign(parts.size(), {});
     std::set<std::tuple<int, int, int, int, int>> products;   // n^3 products in the program
-    for (auto &rgs : parts) {
+    for (size_t pi = 0; pi < parts.size(); ++pi) {
+        const std::vector<int> &rgs = parts[pi];
         PartRec pr;
         for (int i = 0; i < m; ++i) pr.rgs[i] = rgs[i];
         int k = *std::max_element(rgs.begin(), rgs.end()) + 1;
@@ -455,6 +505,11 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan) {
             }
         }
         pr.tw = exact_treewidth(k, qadj);
+        if (req && req->finest_only && k != m) {
+            pr.evaluated = 0;
+            P.parts.push_back(pr);
+            continue;
+        }
         // sparsification filter: no block holds both ends of a pairwise factor
         if (P.sparsify) {
             bool surv = true;
@@ -634,10 +689,91 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan) {
         return USTAT_OK;
         };
 
+        // candidates for the learned ranker: every distinct feasible elimination
+        // sequence, lowered on trial in isolation (an empty memo: no sharing with
+        // other partitions) and described by its features
+        if (req && req->collect && (req->collect_part < 0 || req->collect_part == (int)pi)) {
+            int n_edges_q = 0, n_vecs_q = 0;
+            for (auto &kv : Q.E) n_edges_q += (int)kv.second.size();
+            for (auto &v : Q.vecs) n_vecs_q += (int)v.size();
+            if (req->feature_order) {
+                const std::vector<int> &fo = *req->feature_order;
+                if ((int)fo.size() != k) return USTAT_ERR_INVALID_ARG;
+                std::vector<int> chk = fo;
+                std::sort(chk.begin(), chk.end());
+                for (int i = 0; i < k; ++i)
+                    if (chk[i] != i) return USTAT_ERR_INVALID_ARG;
+                if (!simulate(k, Q.adj, fo.data()).ok) return USTAT_ERR_TW_TOO_LARGE;
+                auto saved = L.memo;
+                PartRec tr = pr;
+                L.memo.clear();
+                L.begin_trial();
+                const size_t first = P.ops.size();
+                int rc = lower(Q, fo, tr);
+                Candidate cd;
+                cd.order = fo;
+                order_features(P.ops, first, k, n_edges_q, n_vecs_q, req->n, cd.feat);
+                L.rollback();
+                L.memo = saved;
+                if (rc != USTAT_OK) return rc;
+                (*req->collect)[pi].push_back(cd);
+                return USTAT_OK;
+            }
+            std::vector<int> perm(k);
+            for (int i = 0; i < k; ++i) perm[i] = i;
+            std::set<std::vector<int>> seen;
+            auto saved = L.memo;
+            do {
+                Cost cc = simulate(k, Q.adj, perm.data());
+                if (!cc.ok) continue;
+                std::vector<int> eff;
+                {
+                    uint32_t adj2[32];
+                    std::memcpy(adj2, Q.adj, sizeof(uint32_t) * k);
+                    uint32_t al = (1u << k) - 1;
+                    for (int v : perm) {
+                        if (!((al >> v) & 1)) continue;
+                        eff.push_back(v);
+                        uint32_t nb = adj2[v] & al & ~(1u << v);
+                        uint32_t comp = component(v, al, adj2);
+                        if (popc(comp) == popc(nb) + 1) {
+                            al &= ~comp;
+                        } else {
+                            al &= ~(1u << v);
+                            for (uint32_t r = nb; r; r &= r - 1)
+                                adj2[__builtin_ctz(r)] |= nb & ~(1u << __builtin_ctz(r));
+                        }
+                    }
+                }
+                if (!seen.insert(eff).second) continue;
+                PartRec tr = pr;
+                L.memo.clear();
+                L.begin_trial();
+                const size_t first = P.ops.size();
+                int rc = lower(Q, perm, tr);
+                Candidate cd;
+                cd.order = perm;
+                order_features(P.ops, first, k, n_edges_q, n_vecs_q, req->n, cd.feat);
+                L.rollback();
+                if (rc == USTAT_OK) (*req->collect)[pi].push_back(cd);
+            } while (std::next_permutation(perm.begin(), perm.end()));
+            L.memo = saved;
+            if (req->collect_only && req->collect_part >= 0) return USTAT_OK;
+        }
+
         // elimination order
         std::vector<int> order;
         Cost c;
-        if (P.planner == USTAT_PLAN_MINFILL) {
+        if (req && req->forced && !(*req->forced)[pi].empty()) {
+            order = (*req->forced)[pi];
+            if ((int)order.size() != k) return USTAT_ERR_INVALID_ARG;
+            std::vector<int> chk = order;
+            std::sort(chk.begin(), chk.end());
+            for (int i = 0; i < k; ++i)
+                if (chk[i] != i) return USTAT_ERR_INVALID_ARG;
+            c = simulate(k, Q.adj, order.data());
+            if (!c.ok) return USTAT_ERR_TW_TOO_LARGE;
+        } else if (P.planner == USTAT_PLAN_MINFILL) {
             order = minfill_order(k, Q.adj);
             c = simulate(k, Q.adj, order.data());
             if (!c.ok) order = exhaustive_order(k, Q.adj, &c);
@@ -703,6 +839,7 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan) {
             if (order.empty()) c.ok = false;
         }
         if (!c.ok) return USTAT_ERR_TW_TOO_LARGE;
+        for (int i = 0; i < k; ++i) pr.order[i] = order[i];
         pr.naive_coef[0] = c.c[0];
         for (int p = 1; p < 5; ++p) pr.naive_coef[p] = 2.0 * c.c[p];
         {

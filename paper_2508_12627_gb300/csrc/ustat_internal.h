@@ -94,6 +94,7 @@ struct PartRec {
     int nscal = 0;
     int scal[kMaxScal];
     double naive_coef[5] = {0, 0, 0, 0, 0};   // own elimination cost: sum coef * n^p
+    int order[kMaxM] = {-1, -1, -1, -1, -1, -1, -1};   // elimination order of the quotient's blocks
 };
 
 struct Plan {
@@ -121,8 +122,38 @@ inline bool is_split_mode(int precision) { return precision == USTAT_BF16X3 || p
 inline bool is_tc_mode(int precision) { return is_split_mode(precision) || precision == USTAT_TF32; }
 inline int split_planes_of(int precision) { return precision == USTAT_BF16X4 ? 4 : 3; }
 
+// Features of one candidate elimination sequence of one partition, for the
+// learned order ranker (see order_features in planner.cpp).
+constexpr int kRankFeatures = 20;
+struct Candidate {
+    std::vector<int> order;   // block ids of the quotient, elimination order
+    float feat[kRankFeatures];
+};
+
+// Optional inputs / outputs of build_plan.
+struct PlanRequest {
+    // per partition (restricted-growth-string order): an elimination order to use
+    // instead of the planner's search (empty: search)
+    const std::vector<std::vector<int>> *forced = nullptr;
+    // evaluate only the partition with m blocks (every vertex distinct): the plan
+    // of the kernel graph's own contraction; the others are reported as 0
+    bool finest_only = false;
+    // if set: every evaluated partition's distinct elimination sequences with
+    // their features at sample size n (the plan is built as usual)
+    std::vector<std::vector<Candidate>> *collect = nullptr;
+    int collect_part = -1;   // >= 0: collect for this partition only
+    bool collect_only = false;   // stop after collecting (no plan)
+    // if set (with collect_part >= 0): the features of this one order of that
+    // partition instead of the candidate list
+    const std::vector<int> *feature_order = nullptr;
+    int64_t n = 1024;
+};
+
 // Planner entry (planner.cpp).  Returns a USTAT_* code.
-int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan);
+int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan, const PlanRequest *req = nullptr);
+
+// Records a CUDA error for ustat_last_cuda_error and returns USTAT_ERR_CUDA (api.cu).
+int record_cuda_error(int cuda_error);
 
 // Exact treewidth of a simple graph on k <= 16 vertices given as adjacency bitmasks.
 int exact_treewidth(int k, const std::vector<uint32_t> &adj);

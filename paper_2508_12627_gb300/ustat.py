@@ -35,6 +35,7 @@ _i64 = ctypes.c_int64
 _vp = ctypes.c_void_p
 _sz = ctypes.c_size_t
 _d = ctypes.c_double
+_f = ctypes.c_float
 
 
 class ustat_graph(ctypes.Structure):
@@ -75,6 +76,17 @@ EXPORTS = {
     "ustat_batched_replay": (_i, [_vp, _vp]),
     "ustat_batched_autotune": (_i, [_vp, _P(_vp), _i, _P(ustat_factor), _i, _vp, _sz, _vp, _vp, _vp, _P(_i),
                                     _P(_d)]),
+    "ustat_order_candidates": (_i, [_P(ustat_graph), _P(ustat_options), _i64, _i, _i, _P(_i), _P(_i), _P(_f)]),
+    "ustat_plan_contraction": (_i, [_P(ustat_graph), _P(ustat_options), _P(_i), _P(_vp)]),
+    "ustat_order_features": (_i, [_P(ustat_graph), _P(ustat_options), _i64, _i, _P(_i), _P(_f)]),
+    "ustat_plan_orders": (_i, [_vp, _P(_i)]),
+    "ustat_mlp_param_count": (_i, [_i, _i]),
+    "ustat_mlp_workspace_bytes": (_i, [_i, _i, _i, _P(_sz)]),
+    "ustat_mlp_forward": (_i, [_vp, _i, _i, _vp, _i, _vp, _vp]),
+    "ustat_mlp_loss_grad": (_i, [_vp, _i, _i, _vp, _vp, _i, _vp, _sz, _vp, _vp, _vp]),
+    "ustat_mlp_adam": (_i, [_vp, _vp, _vp, _vp, _i, _f, _f, _f, _f, _i, _vp]),
+    "ustat_rank_workspace_bytes": (_i, [_P(ustat_graph), _P(ustat_options), _P(_sz)]),
+    "ustat_plan_learned": (_i, [_P(ustat_graph), _P(ustat_options), _i64, _vp, _i, _vp, _sz, _vp, _P(_vp)]),
     "ustat_profile_enable": (_i, [_i]),
     "ustat_profile_kinds": (_i, []),
     "ustat_profile_kind_name": (ctypes.c_char_p, [_i]),
@@ -146,6 +158,18 @@ class Plan:
         self.precision = prec
         self.info = self._info()
 
+    @classmethod
+    def from_handle(cls, handle, graph, factor_kinds, precision):
+        """Wrap a ustat_plan_t made by another entry point (contraction or
+        learned plans)."""
+        self = cls.__new__(cls)
+        self.handle = handle
+        self.m = graph.m
+        self.factor_kinds = list(factor_kinds)
+        self.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        self.info = self._info()
+        return self
+
     def _info(self):
         L = lib()
         nparts = _i()
@@ -189,6 +213,114 @@ class Plan:
         if h is not None and _lib is not None:
             _lib.ustat_plan_destroy(h)
             self.handle = None
+
+
+def graph_struct(graph, factor_kinds):
+    """(ustat_graph, keep-alive arrays) for a synth.Graph-like object."""
+    keep = [_iarr(e[0] for e in graph.edges), _iarr(e[1] for e in graph.edges), _iarr(e[2] for e in graph.edges),
+            _iarr(u[0] for u in graph.unary), _iarr(u[1] for u in graph.unary), _iarr(factor_kinds)]
+    g = ustat_graph(graph.m, len(graph.edges), keep[0], keep[1], keep[2], len(graph.unary), keep[3], keep[4],
+                    len(factor_kinds), keep[5])
+    return g, keep
+
+
+def options_struct(precision="bf16x3", sparsify=False, planner=PLAN_EXHAUSTIVE, cse=True):
+    prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    return ustat_options(prec, int(bool(sparsify)), int(planner), int(bool(cse)))
+
+
+RANK_FEATURES = 20
+
+
+def order_candidates(graph, factor_kinds, n, part=-1, precision="bf16x3", max_cand=100000):
+    """Distinct elimination sequences of one partition (-1: the finest) with their
+    features: (orders [count x m], features [count x RANK_FEATURES])."""
+    g, keep = graph_struct(graph, factor_kinds)
+    o = options_struct(precision)
+    cnt = _i()
+    cap = min(max_cand, 5040)   # at most m! <= 7! sequences
+    orders = (_i * max(1, cap * graph.m))()
+    feats = (_f * max(1, cap * RANK_FEATURES))()
+    _check(lib().ustat_order_candidates(ctypes.byref(g), ctypes.byref(o), int(n), int(part), cap, ctypes.byref(cnt),
+                                        orders, feats), "ustat_order_candidates")
+    k = min(cnt.value, cap)
+    return ([list(orders[i * graph.m:(i + 1) * graph.m]) for i in range(k)],
+            [list(feats[i * RANK_FEATURES:(i + 1) * RANK_FEATURES]) for i in range(k)])
+
+
+def order_features(graph, factor_kinds, n, order, part=-1, precision="bf16x3"):
+    g, keep = graph_struct(graph, factor_kinds)
+    o = options_struct(precision)
+    oa = _iarr(list(order) + [-1] * (graph.m - len(order)))
+    feats = (_f * RANK_FEATURES)()
+    _check(lib().ustat_order_features(ctypes.byref(g), ctypes.byref(o), int(n), int(part), oa, feats),
+           "ustat_order_features")
+    return list(feats)
+
+
+def plan_orders(plan):
+    """The elimination order (block ids, -1 padded) the plan chose per partition."""
+    k = plan.info["n_parts"]
+    arr = (_i * (k * plan.m))()
+    _check(lib().ustat_plan_orders(plan.handle, arr), "ustat_plan_orders")
+    return [[v for v in arr[i * plan.m:(i + 1) * plan.m]] for i in range(k)]
+
+
+def plan_contraction(graph, factor_kinds, order=None, precision="bf16x3", planner=PLAN_EXHAUSTIVE):
+    g, keep = graph_struct(graph, factor_kinds)
+    o = options_struct(precision, planner=planner)
+    h = _vp()
+    oa = _iarr(order) if order is not None else None
+    _check(lib().ustat_plan_contraction(ctypes.byref(g), ctypes.byref(o), oa, ctypes.byref(h)),
+           "ustat_plan_contraction")
+    return Plan.from_handle(h, graph, factor_kinds, precision)
+
+
+def rank_workspace_bytes(graph, factor_kinds, precision="bf16x3"):
+    g, keep = graph_struct(graph, factor_kinds)
+    o = options_struct(precision)
+    s = _sz()
+    _check(lib().ustat_rank_workspace_bytes(ctypes.byref(g), ctypes.byref(o), ctypes.byref(s)),
+           "ustat_rank_workspace_bytes")
+    return s.value
+
+
+def plan_learned(graph, factor_kinds, n, params_ptr, hidden, ws_ptr, ws_bytes, stream, precision="bf16x3",
+                 cse=True):
+    g, keep = graph_struct(graph, factor_kinds)
+    o = options_struct(precision, cse=cse)
+    h = _vp()
+    _check(lib().ustat_plan_learned(ctypes.byref(g), ctypes.byref(o), int(n), params_ptr, int(hidden), ws_ptr,
+                                    ws_bytes, stream, ctypes.byref(h)), "ustat_plan_learned")
+    return Plan.from_handle(h, graph, factor_kinds, precision)
+
+
+def mlp_param_count(features, hidden):
+    c = lib().ustat_mlp_param_count(int(features), int(hidden))
+    if c < 0:
+        raise UstatError(c, "ustat_mlp_param_count")
+    return c
+
+
+def mlp_workspace_bytes(features, hidden, rows):
+    s = _sz()
+    _check(lib().ustat_mlp_workspace_bytes(int(features), int(hidden), int(rows), ctypes.byref(s)),
+           "ustat_mlp_workspace_bytes")
+    return s.value
+
+
+def mlp_forward(params_ptr, features, hidden, X_ptr, rows, y_ptr, stream):
+    _check(lib().ustat_mlp_forward(params_ptr, features, hidden, X_ptr, rows, y_ptr, stream), "ustat_mlp_forward")
+
+
+def mlp_loss_grad(params_ptr, features, hidden, X_ptr, t_ptr, rows, ws_ptr, ws_bytes, grad_ptr, loss_ptr, stream):
+    _check(lib().ustat_mlp_loss_grad(params_ptr, features, hidden, X_ptr, t_ptr, rows, ws_ptr, ws_bytes, grad_ptr,
+                                     loss_ptr, stream), "ustat_mlp_loss_grad")
+
+
+def mlp_adam(params_ptr, grad_ptr, m_ptr, v_ptr, count, lr, beta1, beta2, eps, step, stream):
+    _check(lib().ustat_mlp_adam(params_ptr, grad_ptr, m_ptr, v_ptr, count, lr, beta1, beta2, eps, step, stream),
+           "ustat_mlp_adam")
 
 
 def factor_array(factors):
