@@ -72,7 +72,17 @@ struct Layout {
     std::vector<int> scal_index; // per slot: index into the scalar array (or -1)
     size_t err_off = 0, scal_off = 0, zero_bytes = 0, xw_off = 0, total = 0;
     int64_t ldp_slices = 0, ldp_prep = 0;
+    // s = 3 steps on the tensor cores: digit planes of g3_nb A operands at a time
+    size_t g3_off = 0, g3_stride = 0;
+    int g3_nb = 0;
 };
+
+bool tc_gemm3(const Plan &P) {
+    if (!is_split_mode(P.precision)) return false;
+    for (auto &op : P.ops)
+        if (op.kind == OP_GEMM3) return true;
+    return false;
+}
 
 bool needs_xw(const Plan &P) {
     for (auto &op : P.ops)
@@ -128,6 +138,14 @@ Layout make_layout(const Plan &P, int64_t n, int d) {
             default:
                 break;
         }
+    }
+    if (tc_gemm3(P)) {
+        // about 256 MiB of A operands per batch, 1 to 64 of them
+        L.g3_stride = align_up(split_planes_of(P.precision) * 2 * (size_t)n * L.ldp_slices + 4 * (size_t)n, 1024);
+        L.g3_nb = (int)std::max<size_t>(1, std::min<size_t>(64, ((size_t)256 << 20) / L.g3_stride));
+        L.g3_nb = (int)std::min<int64_t>(L.g3_nb, n);
+        L.g3_off = cur;
+        cur = align_up(cur + L.g3_stride * L.g3_nb, 1024);
     }
     L.total = cur;
     return L;
@@ -320,8 +338,47 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                 break;
             }
             case OP_GEMM3: {
-                SimtGemmArgs g{};
                 auto tr = [&](const Term &t) { return (t.mat >= 0 && !P.slots[t.mat].symmetric) ? t.trans : 0; };
+                if (is_split_mode(P.precision)) {
+                    // tensor cores: g3_nb products at a time, their A operands split
+                    // per bb into the batch region (planes of all bb back to back)
+                    const int planes = split_planes_of(P.precision);
+                    const size_t plane_bytes = 2 * (size_t)n * C.L.ldp_slices;
+                    char *sl = C.ws + C.L.g3_off;
+                    float *sc = (float *)(sl + planes * plane_bytes * C.L.g3_nb);
+                    const int var = P.tc_variant[tc_size_class(n)];
+                    for (int64_t bb0 = 0; bb0 < n && e == cudaSuccess; bb0 += C.L.g3_nb) {
+                        const int nb = (int)std::min<int64_t>(C.L.g3_nb, n - bb0);
+                        e = launch_split_g3((const float *)C.ptr(op.A.mat), tr(op.A), C.vec(op.u),
+                                            (const float *)C.ptr(op.Ab.mat), tr(op.Ab), bb0, nb, n, C.L.ldp_slices,
+                                            lead, planes, sl, sc, C.st);
+                        if (e != cudaSuccess) break;
+                        TcGemmArgs g{};
+                        g.n = n;
+                        g.ldp = C.L.ldp_slices;
+                        g.opA = sl;
+                        g.scaleA = sc;
+                        g.opB = C.ptr(op.opB);
+                        g.scaleB = C.scales(op.opB);
+                        g.lead_bits = lead;
+                        g.err = err;
+                        g.nred = 1;
+                        g.red[0] = TcRed{(const float *)C.ptr(op.W.mat), tr(op.W), C.vec(op.a), C.vec(op.b), 1,
+                                         (double *)C.ptr(op.out)};
+                        g.batch = nb;
+                        g.bb0 = (int)bb0;
+                        g.Wbc = (const float *)C.ptr(op.Wbc.mat);
+                        g.transWbc = tr(op.Wbc);
+                        g.Wbd = (const float *)C.ptr(op.Wbd.mat);
+                        g.transWbd = tr(op.Wbd);
+                        g.ub = C.vec(op.ub);
+                        g.group_rows = kGroupRows[var & 3];
+                        if (P.precision == USTAT_BF16X3) e = launch_gemm_bf16x3(g, (var >> 2) & 1, C.st);
+                        else e = launch_gemm_bf16x4(g, C.st);
+                    }
+                    break;
+                }
+                SimtGemmArgs g{};
                 g.n = n;
                 g.gemm3 = 1;
                 g.A = C.ptr(op.A.mat);

@@ -110,21 +110,31 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const float *__restrict
 
 // Column source (X(j, i) = M[i][j] u(i)) and the tf32 copy: one block per 32
 // operand rows, transposed through shared memory.
+// With Mb (the s = 3 step): X(j, i) is further scaled by Ab(i, bb), bb = bb0 +
+// blockIdx.y, and the digits and scales of bb go to its own region.
 template <bool kSplit>
 __global__ void __launch_bounds__(256) operand_cols_kernel(const float *__restrict__ M, int trans,
                                                            const double *__restrict__ u, int64_t n, int64_t ldp,
                                                            int lead_bits, int planes,
                                                            __nv_bfloat16 *__restrict__ slices,
-                                                           float *__restrict__ scales, float *__restrict__ prep) {
+                                                           float *__restrict__ scales, float *__restrict__ prep,
+                                                           const float *__restrict__ Mb = nullptr, int transAb = 0,
+                                                           int64_t bb0 = 0) {
     __shared__ float tile[32][33];
     __shared__ float rmax[8][32];
     __shared__ int rexp[32];
     const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
     const int64_t j0 = (int64_t)blockIdx.x * 32;
+    const int64_t bb = bb0 + blockIdx.y;
+    if (Mb) {
+        slices += (int64_t)blockIdx.y * planes * n * ldp;
+        scales += (int64_t)blockIdx.y * n;
+    }
     auto val = [&](int64_t j, int64_t i) -> float {
         if (j >= n || i >= n) return 0.f;
         float x = trans ? M[j * n + i] : M[i * n + j];
         if (u) x *= (float)u[i];
+        if (Mb) x *= transAb ? Mb[bb * n + i] : Mb[i * n + bb];
         return x;
     };
     if (kSplit) {
@@ -323,11 +333,18 @@ struct Cfg {
 // rows per group, column-major inside a group, so concurrently running CTAs share
 // A and B panels).  Symmetric: the upper triangle tm <= tn in row-major order.
 struct TileWalk {
-    int tiles_m, tiles_n, symmetric, G;
-    __device__ int count() const {
+    int tiles_m, tiles_n, symmetric, G, batch;
+    __device__ int per_product() const {
         return symmetric ? tiles_m * (tiles_m + 1) / 2 : tiles_m * tiles_n;
     }
-    __device__ void coords(int t, int &tm, int &tn) const {
+    __device__ int count() const { return per_product() * (batch > 0 ? batch : 1); }
+    // batched: product t / per_product(), then the tile within it
+    __device__ void coords(int t, int &bl, int &tm, int &tn) const {
+        const int per = per_product();
+        bl = t / per;
+        coords1(t - bl * per, tm, tn);
+    }
+    __device__ void coords1(int t, int &tm, int &tn) const {
         if (symmetric) {
             // row r starts at off(r) = r T - r (r - 1) / 2
             const int T = tiles_m;
@@ -374,7 +391,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int64_t n = g.n;
     const int num_k = (int)(g.ldp / C::kBKElems);
     TileWalk walk{(int)((n + kBM - 1) / kBM), (int)((n + C::kBN - 1) / C::kBN), g.symmetric,
-                  g.group_rows > 0 ? g.group_rows : 8};
+                  g.group_rows > 0 ? g.group_rows : 8, g.batch};
     const int total_tiles = walk.count();
 
     if (threadIdx.x == 0) {
@@ -408,8 +425,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             // ---------------- TMA producer
             uint32_t it = 0;
             for (int t = blockIdx.x; t < total_tiles && !*abort_flag; t += gridDim.x) {
-                int tm, tn;
-                walk.coords(t, tm, tn);
+                int bl, tm, tn;
+                walk.coords(t, bl, tm, tn);
+                const int za = bl * C::kPlanes;   // the product's A planes (batched s = 3 step)
                 for (int kb = 0; kb < num_k; ++kb, ++it) {
                     const int s = it % C::kStages;
                     if (it >= (uint32_t)C::kStages &&
@@ -418,7 +436,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t sa = base + s * C::kStageBytes;
                     const uint32_t sb = sa + C::kPlanes * C::kATile;
                     mbar_expect_tx(full_bar(s), C::kStageBytes);
-                    tma_load_3d(sa, &mapA, kb * C::kBKElems, tm * kBM, 0, full_bar(s));
+                    tma_load_3d(sa, &mapA, kb * C::kBKElems, tm * kBM, za, full_bar(s));
                     tma_load_3d(sb, &mapB, kb * C::kBKElems, tn * C::kBN, 0, full_bar(s));
                     *issued_cnt = it + 1;
                 }
@@ -431,8 +449,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t it = 0, tcount = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
-                int tm, tn;
-                walk.coords(t, tm, tn);
                 const int buf = tcount & 1;
                 if (tcount >= 2 && !mbar_wait(tempty_bar(buf), ((tcount >> 1) - 1) & 1, abort_flag)) {
                     ok = false;
@@ -491,8 +507,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         double total[4] = {0.0, 0.0, 0.0, 0.0};
         uint32_t tcount = 0;
         for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
-            int tm, tn;
-            walk.coords(t, tm, tn);
+            int bl, tm, tn;
+            walk.coords(t, bl, tm, tn);
+            const int64_t bb = g.bb0 + bl;   // batched s = 3 step: this product's index
+            const float *Wbd = g.Wbd;
+            const int tWbd = g.transWbd;
             const int buf = tcount & 1;
             // one lane polls (with back-off: the main loop of a tile takes tens of
             // microseconds) so the waiting warps leave the issue slots to the TMA
@@ -504,7 +523,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             const int64_t j = (int64_t)tm * kBM + row;
             const bool jok = j < n;
-            const float rs = jok ? (C::kTf32 ? 1.f : ldexpf(g.scaleA[j], -2 * g.lead_bits)) : 0.f;
+            const float rs = jok ? (C::kTf32 ? 1.f : ldexpf(g.scaleA[(int64_t)bl * n + j], -2 * g.lead_bits)) : 0.f;
             const uint32_t taddr = tmem + buf * C::kAccCols + ((uint32_t)(32 * q) << 16);
             double tile_acc[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll 1
@@ -543,6 +562,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             if (k >= n) continue;
                             float w = bv ? (float)bv[k] : 1.f;
                             if (W) w *= tW ? W[k * n + j] : W[j * n + k];
+                            if (Wbd) w *= tWbd ? Wbd[k * n + bb] : Wbd[bb * n + k];
                             const float x = pw == 2 ? v[c] * v[c] : v[c];
                             part = fmaf(x, w, part);
                         }
@@ -553,12 +573,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty_bar(buf));
-            const double wgt = (g.symmetric && tm != tn) ? 2.0 : 1.0;
+            double wgt = (g.symmetric && tm != tn) ? 2.0 : 1.0;
+            if (g.ub) wgt *= g.ub[bb];
+            const double wbc = (g.Wbc && jok) ? (double)(g.transWbc ? g.Wbc[j * n + bb] : g.Wbc[bb * n + j]) : 1.0;
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 if (r >= g.nred) break;
                 const double aj = (g.red[r].a && jok) ? g.red[r].a[j] : 1.0;
-                total[r] += tile_acc[r] * aj * wgt;
+                total[r] += tile_acc[r] * aj * wbc * wgt;
             }
             ++tcount;
         }
@@ -610,12 +632,13 @@ EncodeTiledFn get_encode() {
     return fn;
 }
 
-// planes x rows x ldp (innermost) tensor, box {128 bytes, box_rows, planes}.
-bool make_map(CUtensorMap *map, const void *ptr, bool bf16, int planes, int64_t rows, int64_t ldp, int box_rows) {
+// total_planes x rows x ldp (innermost) tensor, box {128 bytes, box_rows, planes}.
+bool make_map_planes(CUtensorMap *map, const void *ptr, bool bf16, int planes, int total_planes, int64_t rows,
+                     int64_t ldp, int box_rows) {
     EncodeTiledFn enc = get_encode();
     if (!enc) return false;
     const int esz = bf16 ? 2 : 4;
-    cuuint64_t dims[3] = {(cuuint64_t)ldp, (cuuint64_t)rows, (cuuint64_t)planes};
+    cuuint64_t dims[3] = {(cuuint64_t)ldp, (cuuint64_t)rows, (cuuint64_t)total_planes};
     cuuint64_t strides[2] = {(cuuint64_t)(ldp * esz), (cuuint64_t)(rows * ldp * esz)};
     cuuint32_t box[3] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows, (cuuint32_t)planes};
     cuuint32_t estr[3] = {1, 1, 1};
@@ -647,8 +670,10 @@ cudaError_t launch_tc(const TcGemmArgs &g0, cudaStream_t s) {
     if (g.nred < 0 || g.nred > 4) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
     const bool bf16 = !C::kTf32;
-    if (!make_map(&ma, g.opA, bf16, C::kPlanes, g.n, g.ldp, kBM) ||
-        !make_map(&mb, g.opB, bf16, C::kPlanes, g.n, g.ldp, C::kBN))
+    if (g.batch > 0 && (g.C || g.nred != 1)) return cudaErrorInvalidValue;
+    const int za = g.batch > 0 ? g.batch : 1;
+    if (!make_map_planes(&ma, g.opA, bf16, C::kPlanes, za * C::kPlanes, g.n, g.ldp, kBM) ||
+        !make_map_planes(&mb, g.opB, bf16, C::kPlanes, C::kPlanes, g.n, g.ldp, C::kBN))
         return cudaErrorInvalidValue;
     static bool attr[64] = {false};
     int dev = 0;
@@ -660,7 +685,7 @@ cudaError_t launch_tc(const TcGemmArgs &g0, cudaStream_t s) {
         attr[dev] = true;
     }
     const int64_t tm = (g.n + kBM - 1) / kBM, tn = (g.n + C::kBN - 1) / C::kBN;
-    const int64_t tiles = g.symmetric ? tm * (tm + 1) / 2 : tm * tn;
+    const int64_t tiles = (g.symmetric ? tm * (tm + 1) / 2 : tm * tn) * za;
     const int grid = (int)(tiles < sm_count() ? tiles : sm_count());
     tc_gemm_kernel<kMode><<<grid, kThreads, C::kSmem, s>>>(ma, mb, g);
     return cudaGetLastError();
@@ -678,6 +703,16 @@ cudaError_t launch_split(const float *M, int trans, const double *u, int64_t n, 
         operand_cols_kernel<true><<<grid, block, 0, s>>>(M, 0, u, n, ldp, lead_bits, planes,
                                                          (__nv_bfloat16 *)slices, scales, nullptr);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_g3(const float *M, int trans, const double *u, const float *Mb, int transAb, int64_t bb0,
+                            int nb, int64_t n, int64_t ldp, int lead_bits, int planes, void *slices, float *scales,
+                            cudaStream_t s) {
+    if (nb < 1 || nb > 65535) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((n + 31) / 32), (unsigned)nb), block(32, 8);
+    operand_cols_kernel<true><<<grid, block, 0, s>>>(M, trans, u, n, ldp, lead_bits, planes,
+                                                     (__nv_bfloat16 *)slices, scales, nullptr, Mb, transAb, bb0);
     return cudaGetLastError();
 }
 

@@ -141,11 +141,26 @@ struct TcGemmArgs {
     int symmetric;                           // C = C^T and every reduction symmetric
     int *err;                                // device error word (bounded waits)
     int group_rows;                          // tile rows per raster group (0: 8)
+    // GEMM3 batch (s = 3 step on the tensor cores): `batch` > 0 products, one per
+    // bb = bb0 .. bb0 + batch - 1, whose A operands are consecutive in opA
+    // ([batch][planes][n][ldp], scales [batch][n]); one reduction red[0] with the
+    // extra weights Wbc(bb, j) on rows, Wbd(bb, k) on columns and ub(bb)
+    int batch, bb0;
+    const float *Wbc; int transWbc;
+    const float *Wbd; int transWbd;
+    const double *ub;
 };
 // narrow: 128 x 64 tiles with a three-stage pipeline instead of 128 x 128 (no
 // symmetric tile skipping)
 cudaError_t launch_gemm_bf16x3(const TcGemmArgs &g, int narrow, cudaStream_t s);
 cudaError_t launch_gemm_bf16x4(const TcGemmArgs &g, cudaStream_t s);
+// Digit planes of the s = 3 step's A operands for bb = bb0 .. bb0 + nb - 1:
+// X_bb(j, i) = A(i, j) u(i) Ab(i, bb) with A(i, j) = trans ? M[j][i] : M[i][j] and
+// Ab(i, bb) = transAb ? Mb[bb][i] : Mb[i][bb]; slices [nb][planes][n][ldp],
+// scales [nb][n].
+cudaError_t launch_split_g3(const float *M, int trans, const double *u, const float *Mb, int transAb, int64_t bb0,
+                            int nb, int64_t n, int64_t ldp, int lead_bits, int planes, void *slices, float *scales,
+                            cudaStream_t s);
 cudaError_t launch_gemm_tf32(const TcGemmArgs &g, cudaStream_t s);
 
 }  // namespace ustat

@@ -1067,6 +1067,9 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan, const P
                 op.opA = operand(op.A, op.u, out);
                 op.opB = (op.A == op.B && op.u < 0) ? op.opA : operand(op.B, -1, out);
             }
+            // the s = 3 step on the tensor cores (split modes): B is an ordinary
+            // operand; the A operands, scaled by Ab(., bb), are split per bb at run time
+            if (op.kind == OP_GEMM3 && split) op.opB = operand(op.B, -1, out);
             out.push_back(op);
         }
         P.ops.swap(out);
@@ -1181,6 +1184,7 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan, const P
             add(o.u), add(o.a), add(o.b), add(o.A.mat), add(o.B.mat), add(o.W.mat), add(o.Ab.mat);
             add(o.Wbc.mat), add(o.Wbd.mat), add(o.ub);
             if (o.kind == OP_GEMM) add(o.opA), add(o.opB);
+            if (o.kind == OP_GEMM3) add(o.opB);
             for (int r = 0; r < o.nred; ++r) add(o.red[r].W.mat), add(o.red[r].a), add(o.red[r].b);
             return v;
         };

@@ -190,3 +190,31 @@ def test_c4_full_size_against_oracle(eng_mod):
     ref, absref = _oracle(w)
     out = eng_mod.Engine(w.graph, w.factors, precision="bf16x3").evaluate(w.X)
     _compare(out, ref, absref, 1e-8, "c4 full bf16x3")
+
+
+K4C_N = 200
+
+
+@pytest.fixture(scope="module")
+def k4c_ref():
+    # three partitions of treewidth 3 (the first, a middle one and the finest) at
+    # n = 200, which the oracle evaluates in seconds
+    w = synth.workload("k4_cycle_rbf", K4C_N)
+    parts = uo.set_partitions(w.graph.m)
+    tw = [uo.treewidth_bruteforce(max(r) + 1, uo.quotient_edges(w.graph, r)) for r in parts]
+    idx = [i for i, t in enumerate(tw) if t == 3]
+    pick = [idx[0], idx[len(idx) // 2], idx[-1]]
+    sel = [parts[i] for i in pick]
+    return (w, pick, uo.ustat(w.graph, w.factors, w.X, partitions=sel),
+            uo.ustat(w.graph, w.factors, w.X, partitions=sel, absolute=True))
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x4", "fp32"])
+def test_k4_cycle_treewidth3_steps_multi_tile(eng_mod, k4c_ref, prec):
+    # the s = 3 steps (tensor cores in the split modes) over two 128-row tiles with a
+    # ragged tail, against the oracle element by element
+    w, pick, ref, absref = k4c_ref
+    out = eng_mod.Engine(w.graph, w.factors, precision=prec).evaluate(w.X)
+    for k, i in enumerate(pick):
+        err = abs(out["V"][i] - ref["V"][k])
+        assert err <= SMALL_N * absref["V"][k], (prec, i, err / absref["V"][k])
