@@ -98,6 +98,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x, dist=None, device=None):
+    """The largest value of x over all ranks: the whole job's time is the slowest
+    rank's (every rank evaluates its own replica of the workload)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, steps, max_ms):
+    """Whole-job throughput: the evaluations of all ranks over the slowest rank's time."""
+    return world * steps / (max_ms / 1e3)
+
+
 def oracle_eval(w):
     from oracle import ustat_oracle as uo
     t0 = time.perf_counter()
@@ -387,11 +403,7 @@ def main():
     prof = us.profile_collect()
     clk = clocks.stop() if clocks else None
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    tot_ms = float(sum(step_ms))
-    if dist:
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = max_over_ranks(float(sum(step_ms)), dist, dev)
     result = out.cpu().numpy()
 
     if rank != 0:
@@ -399,7 +411,7 @@ def main():
         return
 
     n, d = w.n, w.d
-    value = world * args.steps / (tot_ms / 1e3)
+    value = job_value(world, args.steps, tot_ms)
     fl_plan, fl_naive = eng.plan.flops(n)
     peaks, peak_src = load_peaks()
     launches = sum(c for (_, c) in prof.values())
@@ -494,16 +506,18 @@ def main():
     cpu = None
     err = None
     if not args.no_cpu_baseline:
-        # the oracle's cost grows like the plan's unshared elimination flops: time it
-        # at n = 48 first and, if the full size would take more than ~30 s, on a
-        # smaller sample of the same distribution sized for ~15 s, then scale
-        ns = n
-        _, t48 = oracle_eval(synth.workload(args.workload, 48))
-        rate = eng.plan.flops(48)[1] / max(t48, 1e-6)
-        if eng.plan.flops(n)[1] / rate > 30.0:
-            ns = 48
-            while ns < n and eng.plan.flops(int(ns * 1.1) + 1)[1] / rate < 15.0:
-                ns = int(ns * 1.1) + 1
+        # a bounded sample: the oracle on samples of the same distribution, doubling
+        # n while the next size is predicted (by the growth of the plan's unshared
+        # elimination flops) to take under ~20 s; the full size if it is reached
+        ns = min(n, 64)
+        t_ns = oracle_eval(synth.workload(args.workload, ns))[1]
+        while ns < n:
+            nxt = min(2 * ns, n)
+            if t_ns * eng.plan.flops(nxt)[1] / eng.plan.flops(ns)[1] > 20.0:
+                break
+            ns = nxt
+            if ns < n:
+                t_ns = oracle_eval(synth.workload(args.workload, ns))[1]
         if ns == n:
             ref, dt = oracle_eval(w)
             cpu = {"value": 1.0 / dt, "unit": "evals/s", "cores": host_cores(), "kind": "oracle",
@@ -513,8 +527,7 @@ def main():
             err = {"U_sum": abs(result[0] - ref["U_sum"]) / abs(ref["U_sum"]),
                    "V_max": float(np.max(np.abs(V - Vr) / np.abs(Vr)))}
         else:
-            ws_ = synth.workload(args.workload, ns)
-            _, dt = oracle_eval(ws_)
+            dt = t_ns
             scale = eng.plan.flops(n)[1] / eng.plan.flops(ns)[1]
             cpu = {"value": 1.0 / (dt * scale), "unit": "evals/s", "cores": host_cores(), "kind": "oracle",
                    "sample": "one full evaluation at n=%d (same distribution, all %d partitions), %.2f s, scaled "

@@ -349,9 +349,11 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                     const int var = P.tc_variant[tc_size_class(n)];
                     for (int64_t bb0 = 0; bb0 < n && e == cudaSuccess; bb0 += C.L.g3_nb) {
                         const int nb = (int)std::min<int64_t>(C.L.g3_nb, n - bb0);
-                        e = launch_split_g3((const float *)C.ptr(op.A.mat), tr(op.A), C.vec(op.u),
-                                            (const float *)C.ptr(op.Ab.mat), tr(op.Ab), bb0, nb, n, C.L.ldp_slices,
-                                            lead, planes, sl, sc, C.st);
+                        // symmetric sources are read along rows (A(i, j) = M[j][i])
+                        auto row_form = [&](const Term &t) { return P.slots[t.mat].symmetric ? 1 : t.trans; };
+                        e = launch_split_g3((const float *)C.ptr(op.A.mat), row_form(op.A), C.vec(op.u),
+                                            (const float *)C.ptr(op.Ab.mat), row_form(op.Ab), bb0, nb, n,
+                                            C.L.ldp_slices, lead, planes, sl, sc, C.st);
                         if (e != cudaSuccess) break;
                         TcGemmArgs g{};
                         g.n = n;

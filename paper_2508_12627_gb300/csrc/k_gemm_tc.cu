@@ -31,6 +31,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 
@@ -105,6 +106,81 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const float *__restrict
             if (u) x *= (float)u[i];
         }
         write_digits(x, lead_bits, e, planes, slices + j * ldp + i, plane);
+    }
+}
+
+// s = 3 A operands from a row-major source: X_bb(j, i) = M[j][i] s_bb(i) with
+// s_bb(i) = u(i) Ab(i, bb), Ab(i, bb) = transAb ? Mb[bb][i] : Mb[i][bb]; bb = bb0 +
+// blockIdx.y.  s_bb is staged in shared memory once per block; one warp per
+// operand row: the row maximum, then the digits of four consecutive entries per
+// lane with 8-byte stores (the same digits as write_digits).
+__global__ void __launch_bounds__(256) split_rows_g3_kernel(const float *__restrict__ M, const double *__restrict__ u,
+                                                            const float *__restrict__ Mb, int transAb, int64_t bb0,
+                                                            int64_t n, int64_t ldp, int lead_bits, int planes,
+                                                            __nv_bfloat16 *__restrict__ slices,
+                                                            float *__restrict__ scales) {
+    extern __shared__ float sv[];   // [n]
+    const int64_t bb = bb0 + blockIdx.y;
+    slices += (int64_t)blockIdx.y * planes * n * ldp;
+    scales += (int64_t)blockIdx.y * n;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        float v = transAb ? Mb[bb * n + i] : Mb[i * n + bb];
+        if (u) v *= (float)u[i];
+        sv[i] = v;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (j >= n) return;
+    const float *row = M + j * n;
+    const bool vec = (n % 4) == 0;
+    float mx = 0.f;
+    for (int64_t i = 4 * lane; i < n; i += 128) {
+        float x[4];
+        if (vec) {
+            const float4 r4 = *reinterpret_cast<const float4 *>(row + i);
+            x[0] = r4.x, x[1] = r4.y, x[2] = r4.z, x[3] = r4.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) x[q] = i + q < n ? row[i + q] : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (i + q < n) mx = fmaxf(mx, fabsf(x[q] * sv[i + q]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int e = row_exp(mx);
+    if (lane == 0) scales[j] = ldexpf(1.f, e);
+    const int k = lead_bits - e;
+    const bool pow2 = k >= -126 && k <= 127;
+    const float p2 = pow2 ? __int_as_float((127 + k) << 23) : 0.f;
+    const int64_t plane = n * ldp;
+    for (int64_t i = 4 * lane; i < ldp; i += 128) {
+        float y[4];
+        if (vec && i + 3 < n) {
+            const float4 r4 = *reinterpret_cast<const float4 *>(row + i);
+            y[0] = r4.x * sv[i], y[1] = r4.y * sv[i + 1], y[2] = r4.z * sv[i + 2], y[3] = r4.w * sv[i + 3];
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) y[q] = i + q < n ? row[i + q] * sv[i + q] : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) y[q] = pow2 ? y[q] * p2 : ldexpf(y[q], k);   // |y| <= 2^w, exact
+        float d[4];
+        float sc = 1.f;
+        for (int p = 0; p < planes; ++p) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (p > 0) y[q] = (y[q] - d[q]) * 256.f;   // exact
+                d[q] = rintf(y[q]);
+            }
+            const __nv_bfloat162 h01 = __floats2bfloat162_rn(d[0] * sc, d[1] * sc);
+            const __nv_bfloat162 h23 = __floats2bfloat162_rn(d[2] * sc, d[3] * sc);
+            *reinterpret_cast<uint2 *>(slices + p * plane + j * ldp + i) =
+                make_uint2(*reinterpret_cast<const uint32_t *>(&h01), *reinterpret_cast<const uint32_t *>(&h23));
+            sc *= (1.f / 256.f);
+        }
     }
 }
 
@@ -369,7 +445,8 @@ struct TileWalk {
 
 template <int kMode>
 __global__ void __launch_bounds__(kThreads, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcGemmArgs g) {
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                   const __grid_constant__ CUtensorMap mapB2, TcGemmArgs g) {
     using C = Cfg<kMode>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -392,7 +469,26 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int num_k = (int)(g.ldp / C::kBKElems);
     TileWalk walk{(int)((n + kBM - 1) / kBM), (int)((n + C::kBN - 1) / C::kBN), g.symmetric,
                   g.group_rows > 0 ? g.group_rows : 8, g.batch};
-    const int total_tiles = walk.count();
+    // work units: the tiles, except that the last g.split_tail tiles of the schedule
+    // are split into two halves of kBN / 2 columns, so that the last wave of the
+    // persistent grid is (nearly) full
+    const int n_tiles = walk.count();
+    const int split_tail = g.split_tail;
+    const int total_tiles = n_tiles + split_tail;
+    constexpr int kHalf = C::kBN / 2;
+    auto unit = [&](int t, int &bl, int &tm, int &tn, int &c_off, int &width) {
+        const int f = n_tiles - split_tail;
+        if (t < f) {
+            walk.coords(t, bl, tm, tn);
+            c_off = 0;
+            width = C::kBN;
+        } else {
+            const int v = t - f;
+            walk.coords(f + (v >> 1), bl, tm, tn);
+            c_off = (v & 1) * kHalf;
+            width = kHalf;
+        }
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::kStages; ++s) {
@@ -425,8 +521,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             // ---------------- TMA producer
             uint32_t it = 0;
             for (int t = blockIdx.x; t < total_tiles && !*abort_flag; t += gridDim.x) {
-                int bl, tm, tn;
-                walk.coords(t, bl, tm, tn);
+                int bl, tm, tn, c_off, width;
+                unit(t, bl, tm, tn, c_off, width);
                 const int za = bl * C::kPlanes;   // the product's A planes (batched s = 3 step)
                 for (int kb = 0; kb < num_k; ++kb, ++it) {
                     const int s = it % C::kStages;
@@ -435,9 +531,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     const uint32_t sa = base + s * C::kStageBytes;
                     const uint32_t sb = sa + C::kPlanes * C::kATile;
-                    mbar_expect_tx(full_bar(s), C::kStageBytes);
+                    mbar_expect_tx(full_bar(s), width == C::kBN ? C::kStageBytes
+                                                                : C::kPlanes * (C::kATile + C::kBTile / 2));
                     tma_load_3d(sa, &mapA, kb * C::kBKElems, tm * kBM, za, full_bar(s));
-                    tma_load_3d(sb, &mapB, kb * C::kBKElems, tn * C::kBN, 0, full_bar(s));
+                    if (width == C::kBN) tma_load_3d(sb, &mapB, kb * C::kBKElems, tn * C::kBN, 0, full_bar(s));
+                    else tma_load_3d(sb, &mapB2, kb * C::kBKElems, tn * C::kBN + c_off, 0, full_bar(s));
                     *issued_cnt = it + 1;
                 }
             }
@@ -445,10 +543,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer
-            constexpr uint32_t idesc = make_idesc(C::kTf32 ? 2u : 1u, kBM, C::kBN);
+            constexpr uint32_t idesc_full = make_idesc(C::kTf32 ? 2u : 1u, kBM, C::kBN);
+            constexpr uint32_t idesc_half = make_idesc(C::kTf32 ? 2u : 1u, kBM, kHalf);
             uint32_t it = 0, tcount = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+                int bl, tm, tn, c_off, width;
+                unit(t, bl, tm, tn, c_off, width);
+                const uint32_t idesc = width == C::kBN ? idesc_full : idesc_half;
+                const uint32_t b_plane = width == C::kBN ? C::kBTile : C::kBTile / 2;   // bytes per B plane
                 const int buf = tcount & 1;
                 if (tcount >= 2 && !mbar_wait(tempty_bar(buf), ((tcount >> 1) - 1) & 1, abort_flag)) {
                     ok = false;
@@ -477,7 +580,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                             for (int p = 0; p < C::kPlanes; ++p) {
                                 ad[p] = desc_sw128(sa + p * C::kATile + koff);
-                                bd[p] = desc_sw128(sb + p * C::kBTile + koff);
+                                bd[p] = desc_sw128(sb + p * b_plane + koff);
                             }
                             mma<false>(d_hi, ad[0], bd[0], idesc, acc0);
                             mma<false>(d_lo, ad[0], bd[1], idesc, acc0);
@@ -507,8 +610,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         double total[4] = {0.0, 0.0, 0.0, 0.0};
         uint32_t tcount = 0;
         for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
-            int bl, tm, tn;
-            walk.coords(t, bl, tm, tn);
+            int bl, tm, tn, c_off, width;
+            unit(t, bl, tm, tn, c_off, width);
             const int64_t bb = g.bb0 + bl;   // batched s = 3 step: this product's index
             const float *Wbd = g.Wbd;
             const int tWbd = g.transWbd;
@@ -527,12 +630,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t taddr = tmem + buf * C::kAccCols + ((uint32_t)(32 * q) << 16);
             double tile_acc[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll 1
-            for (int c0 = 0; c0 < C::kBN; c0 += 16) {
+            for (int c0 = 0; c0 < width; c0 += 16) {
                 uint32_t hi[16], lo[16];
                 tmem_ld16(taddr + c0, hi);
                 if (!C::kTf32) tmem_ld16(taddr + C::kBN + c0, lo);
                 tmem_wait_ld();
-                const int64_t k0 = (int64_t)tn * C::kBN + c0;
+                const int64_t k0 = (int64_t)tn * C::kBN + c_off + c0;
                 float v[16];
 #pragma unroll
                 for (int c = 0; c < 16; ++c) {
@@ -548,6 +651,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int c = 0; c < 16; ++c)
                         if (k0 + c < n) g.C[j * n + k0 + c] = v[c];
                 }
+                // the 16 columns lie inside the matrix and rows are 16-byte aligned:
+                // weights are read as float4
+                const bool full = (k0 + 16 <= n) && ((n & 3) == 0);
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
                     if (r >= g.nred) break;
@@ -556,15 +662,45 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int tW = g.red[r].transW, pw = g.red[r].pow;
                     float part = 0.f;
                     if (jok) {
+                        float w[16];
+                        if (W && !tW && full) {
+                            const float4 *p4 = reinterpret_cast<const float4 *>(W + j * n + k0);
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const float4 t4 = p4[q];
+                                w[4 * q] = t4.x, w[4 * q + 1] = t4.y, w[4 * q + 2] = t4.z, w[4 * q + 3] = t4.w;
+                            }
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 16; ++c) {
+                                const int64_t k = k0 + c;
+                                w[c] = k < n ? (W ? (tW ? W[k * n + j] : W[j * n + k]) : 1.f) : 0.f;
+                            }
+                        }
+                        if (bv) {
+#pragma unroll
+                            for (int c = 0; c < 16; ++c) w[c] *= k0 + c < n ? (float)bv[k0 + c] : 0.f;
+                        }
+                        if (Wbd) {
+                            if (!tWbd && full) {
+                                const float4 *p4 = reinterpret_cast<const float4 *>(Wbd + bb * n + k0);
+#pragma unroll
+                                for (int q = 0; q < 4; ++q) {
+                                    const float4 t4 = p4[q];
+                                    w[4 * q] *= t4.x, w[4 * q + 1] *= t4.y, w[4 * q + 2] *= t4.z, w[4 * q + 3] *= t4.w;
+                                }
+                            } else {
+#pragma unroll
+                                for (int c = 0; c < 16; ++c) {
+                                    const int64_t k = k0 + c;
+                                    if (k < n) w[c] *= tWbd ? Wbd[k * n + bb] : Wbd[bb * n + k];
+                                }
+                            }
+                        }
 #pragma unroll
                         for (int c = 0; c < 16; ++c) {
-                            const int64_t k = k0 + c;
-                            if (k >= n) continue;
-                            float w = bv ? (float)bv[k] : 1.f;
-                            if (W) w *= tW ? W[k * n + j] : W[j * n + k];
-                            if (Wbd) w *= tWbd ? Wbd[k * n + bb] : Wbd[bb * n + k];
                             const float x = pw == 2 ? v[c] * v[c] : v[c];
-                            part = fmaf(x, w, part);
+                            part = fmaf(x, w[c], part);
                         }
                     }
                     tile_acc[r] += (double)part;
@@ -672,8 +808,10 @@ cudaError_t launch_tc(const TcGemmArgs &g0, cudaStream_t s) {
     const bool bf16 = !C::kTf32;
     if (g.batch > 0 && (g.C || g.nred != 1)) return cudaErrorInvalidValue;
     const int za = g.batch > 0 ? g.batch : 1;
+    CUtensorMap mb2;
     if (!make_map_planes(&ma, g.opA, bf16, C::kPlanes, za * C::kPlanes, g.n, g.ldp, kBM) ||
-        !make_map_planes(&mb, g.opB, bf16, C::kPlanes, C::kPlanes, g.n, g.ldp, C::kBN))
+        !make_map_planes(&mb, g.opB, bf16, C::kPlanes, C::kPlanes, g.n, g.ldp, C::kBN) ||
+        !make_map_planes(&mb2, g.opB, bf16, C::kPlanes, C::kPlanes, g.n, g.ldp, C::kBN / 2))
         return cudaErrorInvalidValue;
     static bool attr[64] = {false};
     int dev = 0;
@@ -686,8 +824,17 @@ cudaError_t launch_tc(const TcGemmArgs &g0, cudaStream_t s) {
     }
     const int64_t tm = (g.n + kBM - 1) / kBM, tn = (g.n + C::kBN - 1) / C::kBN;
     const int64_t tiles = (g.symmetric ? tm * (tm + 1) / 2 : tm * tn) * za;
-    const int grid = (int)(tiles < sm_count() ? tiles : sm_count());
-    tc_gemm_kernel<kMode><<<grid, kThreads, C::kSmem, s>>>(ma, mb, g);
+    // half tiles for the last, partly filled wave: with R tiles left over after the
+    // full waves, split R of them when 2R still fits one wave (all of them, up to
+    // the SM count, when there is less than one wave)
+    const int64_t S = sm_count();
+    int64_t split = 0;
+    if (tiles <= S) split = std::min(tiles, S - tiles);
+    else if (tiles % S != 0 && 2 * (tiles % S) <= S) split = tiles % S;
+    g.split_tail = (int)split;
+    const int64_t units = tiles + split;
+    const int grid = (int)(units < S ? units : S);
+    tc_gemm_kernel<kMode><<<grid, kThreads, C::kSmem, s>>>(ma, mb, mb2, g);
     return cudaGetLastError();
 }
 
@@ -710,6 +857,25 @@ cudaError_t launch_split_g3(const float *M, int trans, const double *u, const fl
                             int nb, int64_t n, int64_t ldp, int lead_bits, int planes, void *slices, float *scales,
                             cudaStream_t s) {
     if (nb < 1 || nb > 65535) return cudaErrorInvalidValue;
+    if (trans && n <= 32768) {
+        // A(i, j) = M[j][i]: operand rows are source rows
+        const int smem = (int)(sizeof(float) * n);
+        if (smem > 48 * 1024) {
+            static bool attr[64] = {false};
+            int dev = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+            if (!attr[dev]) {
+                cudaError_t e = cudaFuncSetAttribute(split_rows_g3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     32768 * (int)sizeof(float));
+                if (e != cudaSuccess) return e;
+                attr[dev] = true;
+            }
+        }
+        dim3 grid((unsigned)((n + 7) / 8), (unsigned)nb);
+        split_rows_g3_kernel<<<grid, 256, smem, s>>>(M, u, Mb, transAb, bb0, n, ldp, lead_bits, planes,
+                                                    (__nv_bfloat16 *)slices, scales);
+        return cudaGetLastError();
+    }
     dim3 grid((unsigned)((n + 31) / 32), (unsigned)nb), block(32, 8);
     operand_cols_kernel<true><<<grid, block, 0, s>>>(M, trans, u, n, ldp, lead_bits, planes,
                                                      (__nv_bfloat16 *)slices, scales, nullptr, Mb, transAb, bb0);

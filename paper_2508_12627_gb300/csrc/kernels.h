@@ -146,6 +146,7 @@ struct TcGemmArgs {
     // ([batch][planes][n][ldp], scales [batch][n]); one reduction red[0] with the
     // extra weights Wbc(bb, j) on rows, Wbd(bb, k) on columns and ub(bb)
     int batch, bb0;
+    int split_tail;                          // set by the launcher: trailing tiles split in halves
     const float *Wbc; int transWbc;
     const float *Wbd; int transWbd;
     const double *ub;

@@ -1,0 +1,62 @@
+"""The multi-rank path of bench.py on CPU: world_size-2 gloo ranks.  Every rank
+evaluates its own replica of the workload (weak scaling, no data-path
+collective); the job's time is the slowest rank's and the value counts the
+evaluations of all ranks.  The reference arm runs on rank 0 only."""
+import io
+import os
+import socket
+import sys
+from contextlib import redirect_stdout
+
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # rank r "took" 10 (r + 1) ms for 4 steps
+    t = bench.max_over_ranks(10.0 * (rank + 1), dist, "cpu")
+    dist.barrier()
+    q.put((rank, t, bench.job_value(world, 4, t)))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_time():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    res = sorted(q.get(timeout=10) for _ in range(world))
+    assert [r[1] for r in res] == [20.0, 20.0]
+    assert res[0][2] == pytest.approx(2 * 4 / 0.020)
+
+
+def test_reference_arm_prints_on_rank_zero_only(monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "1")
+
+    class A:
+        workload, steps, warmup, gpus = "c4_rbf", 1, 1, 2
+
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        bench.run_reference(A())
+    assert buf.getvalue() == ""
