@@ -28,6 +28,11 @@ METRIC = "U-stat evals/s and TFLOP/s, mixed-prec vs FP64 on GB300 at rel err ≤
 WORKLOADS = {
     "c4_rbf": "m=4 4-cycle kernel K12 K23 K34 K41, RBF K = exp(-||x-y||^2/(2d)), X n=4096 x d=32 iid N(0,1) "
               "float64 seed 0, all 15 partitions",
+    "triangle_rbf": "m=3 triangle kernel K12 K23 K31, RBF K = exp(-||x-y||^2/(2d)), X n=200 x d=8 iid N(0,1) "
+                    "float64 seed 0, all 5 partitions",
+    "path5_chord_linear_tanh": "m=5 path 1-2-3-4-5 plus chord 1-3, linear K = x.y/d, unary tanh(x.w) on vertex 5 "
+                               "(w ~ N(0, I/d) seed 1), X n=16384 x d=64 iid Student-t(5) rounded to float32 seed "
+                               "0, all 52 partitions",
     "k4_cycle_rbf": "m=6 kernel graph K4 on vertices 1-4 plus edges 4-5, 5-6, 6-1 (treewidth 3), RBF K = "
                     "exp(-||x-y||^2/(2d)), X n=1024 x d=32 iid N(0,1) float64 seed 0, all 203 partitions",
     "batched": "512 independent samples, n uniform in [256, 4096] (seed 0), X_i n_i x 16 iid N(0,1) float64 "
@@ -501,6 +506,12 @@ def main():
         ms64 = s.elapsed_time(e) / reps
         fp64 = {"evals_per_s": 1e3 / ms64, "ms_per_step": ms64, "speedup_of_this_mode": (1e3 / ms64) and value / (
             1e3 / ms64)}
+        # this mode's results against the FP64 GPU form (itself checked against the
+        # oracle at smaller n by the parity tests): per-V relative differences
+        r64 = o64.cpu().numpy()
+        dv = np.abs(result[2:] - r64[2:]) / np.maximum(np.abs(r64[2:]), 1e-300)
+        fp64["rel_diff_of_this_mode"] = {"U_sum": float(abs(result[0] - r64[0]) / abs(r64[0])),
+                                         "V_max": float(dv.max()), "V_median": float(np.median(dv))}
 
     # ---- CPU baseline: the FP64 oracle on the host cores, and the error of this run
     cpu = None
