@@ -269,7 +269,7 @@ def run_batched(args):
             alg += sum(2.0 * n * (n * (n + 1) / 2 if "sym=1" in l else n * n) for l in gl)
             fl_plan += p.flops(n)[0]
     peaks, peak_src = load_peaks()
-    products = {"bf16x3": 6.0, "bf16x4": 10.0, "tf32": 2.0}.get(args.precision)
+    products = {"bf16x3": 6.0, "bf16x4": 10.0, "bf16x5": 15.0, "tf32": 2.0}.get(args.precision)
     roof = None
     if products:
         achieved = alg / (tot_ms / args.steps / 1e3) / 1e12
@@ -340,6 +340,9 @@ def main():
     ap.add_argument("--workload", default="c4_rbf")
     ap.add_argument("--impl", default="engine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="tensor-core GEMM variant for every size class (ustat_plan_set_variant)")
     ap.add_argument("--capture", type=int, default=0,
                     help="only run this many evaluations (no timing, no JSON): for profiler captures")
     args = ap.parse_args()
@@ -374,6 +377,8 @@ def main():
 
     w = synth.workload(args.workload)
     eng = engine.Engine(w.graph, w.factors, precision=args.precision, device=dev)
+    if args.variant is not None:
+        eng.plan.set_variant(args.variant)
     Xd = eng.to_device(w.X)
     out = torch.empty(2 + eng.n_parts, dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -430,7 +435,7 @@ def main():
     alg_flops = 2.0 * n * (sum(entries) / max(1, len(entries)))
     bf16_peak = peaks.get("bf16_tflops", 1900.0)
     # tensor products per algorithmic multiply-add (tf32 runs at half the bf16 rate)
-    products = {"bf16x3": 6.0, "bf16x4": 10.0, "tf32": 2.0, "fp32": None, "fp64": None}[args.precision]
+    products = {"bf16x3": 6.0, "bf16x4": 10.0, "bf16x5": 15.0, "tf32": 2.0, "fp32": None, "fp64": None}[args.precision]
     roof = None
     if g_cnt and products:
         achieved = alg_flops / per_launch_s / 1e12
@@ -491,7 +496,7 @@ def main():
 
     # ---- the plain FP64 GPU form of the same evaluation
     fp64 = None
-    if args.precision != "fp64":
+    if args.precision != "fp64" and not args.no_fp64:
         e64 = engine.Engine(w.graph, w.factors, precision="fp64", device=dev)
         o64 = torch.empty(2 + e64.n_parts, dtype=torch.float64, device=dev)
         e64.launch(Xd, o64)
@@ -550,6 +555,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "n": n, "d": d, "precision": args.precision,
+                   "gemm_variant": args.variant if args.variant is not None else "default",
                    "partitions": eng.n_parts, "l2": "flushed (256 MiB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single"},
         "tflops": {"algorithmic_plan": fl_plan * value / 1e12, "algorithmic_unshared": fl_naive * value / 1e12},

@@ -61,8 +61,11 @@ extern "C" {
 #define USTAT_TF32    2  /* GEMMs on tcgen05 kind::tf32, FP32 accumulation                   */
 #define USTAT_BF16X3  3  /* GEMMs on tcgen05 kind::f16 with three bf16 fixed-point slices per
                             operand, exact integer accumulation of the leading slice product */
-#define USTAT_BF16X4  4  /* as BF16X3 with four slices (8 more bits per operand row) for
-                            factors whose rows span a wide dynamic range */
+#define USTAT_BF16X4  4  /* as BF16X3 with four slices (8 more bits per operand row), for
+                            factors whose rows span a wide dynamic range; matrices stored
+                            and the GEMM epilogues evaluated in float64 */
+#define USTAT_BF16X5  5  /* as BF16X4 with five slices (16 more bits than BF16X3): heavy-
+                            tailed data whose sums are dominated by few terms */
 
 /* ---- planners (choice of elimination order per partition) ---- */
 #define USTAT_PLAN_EXHAUSTIVE  0  /* minimum modelled cost over all orders (<= 8 blocks) */
@@ -217,6 +220,17 @@ int ustat_batch_workspace_bytes(const ustat_plan_t *plan, const int64_t *n, int 
  * (USTAT_ERR_UNSUPPORTED); n[i] < m gives USTAT_ERR_N_LT_M.  Streams are
  * created on the device current at the first run.
  */
+/*
+ * Tensor-core GEMM variant of a plan for one size class (0: n <= 1024, 1: <= 2048,
+ * 2: <= 3072, 3: larger; -1: all): bits 0-1 pick the tile raster group (8, 4, 16
+ * or 2 tile rows), bits 2-3 the tile shape (0: 128 x 128 with 128-byte k-blocks;
+ * 1: 128 x 64, bf16x3 only; 2: 128 x 128 with 64-byte k-blocks and a deeper
+ * pipeline).  Results agree to the mode's tolerance across variants (the
+ * summation order inside the accumulators differs).  The autotuner below sets
+ * these itself.
+ */
+int ustat_plan_set_variant(ustat_plan_t *plan, int size_class, int variant);
+
 typedef struct ustat_batched ustat_batched_t;
 int ustat_batched_create(ustat_plan_t *plan, const int64_t *n, int count, int d, int max_lanes,
                          ustat_batched_t **out);

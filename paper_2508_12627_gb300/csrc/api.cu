@@ -92,7 +92,7 @@ bool needs_xw(const Plan &P) {
 
 Layout make_layout(const Plan &P, int64_t n, int d) {
     Layout L;
-    const size_t esz = P.precision == USTAT_FP64 ? 8 : 4;
+    const size_t esz = wide_storage(P.precision) ? 8 : 4;
     L.ldp_slices = (int64_t)align_up((size_t)n, 64);
     L.ldp_prep = (int64_t)align_up((size_t)n, 32);
     L.off.assign(P.slots.size(), 0);
@@ -223,7 +223,11 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                 e = launch_copyvec((const double *)f[op.factor].data, n, C.vec(op.out), C.st);
                 break;
             case OP_DIAG:
-                e = launch_diag(C.ptr(op.t[0].mat), C.fp64, n, C.vec(op.out), C.st);
+                if (op.factor >= 0 && f[op.factor].kind != USTAT_TANH_DOT && f[op.factor].kind != USTAT_VECTOR)
+                    e = launch_factor_diag(f[op.factor].kind, f[op.factor].param, X, x_dtype, C.d,
+                                           (const double *)f[op.factor].data, n, P.sparsify, C.vec(op.out), C.st);
+                else
+                    e = launch_diag(C.ptr(op.t[0].mat), C.fp64, n, C.vec(op.out), C.st);
                 break;
             case OP_VMUL:
                 e = launch_vmul(C.vec(op.u), C.vec(op.a), n, C.vec(op.out), C.st);
@@ -284,7 +288,7 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                 const Term t = op.t[0];
                 const int tr = P.slots[t.mat].symmetric ? 1 : t.trans;
                 if (op.kind == OP_SPLIT)
-                    e = launch_split((const float *)C.ptr(t.mat), tr, C.vec(op.u), n, C.L.ldp_slices, lead,
+                    e = launch_split(C.ptr(t.mat), C.fp64, tr, C.vec(op.u), n, C.L.ldp_slices, lead,
                                      split_planes_of(P.precision), C.ptr(op.out), C.scales(op.out), C.st);
                 else
                     e = launch_prep((const float *)C.ptr(t.mat), tr, C.vec(op.u), n, C.L.ldp_prep,
@@ -304,18 +308,22 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                     g.scaleB = split ? C.scales(op.opB) : nullptr;
                     g.lead_bits = lead;
                     g.err = err;
-                    g.C = op.store ? (float *)C.ptr(op.out) : nullptr;
+                    g.C = op.store ? C.ptr(op.out) : nullptr;
+                    g.wide = C.fp64;
                     g.nred = op.nred;
                     for (int r = 0; r < op.nred; ++r) {
                         const Red &R = op.red[r];
-                        g.red[r] = TcRed{(const float *)C.ptr(R.W.mat), trW(R.W), C.vec(R.a), C.vec(R.b), R.pow,
+                        g.red[r] = TcRed{C.ptr(R.W.mat), trW(R.W), C.vec(R.a), C.vec(R.b), R.pow,
                                          (double *)C.ptr(R.out)};
                     }
                     g.symmetric = op.symmetric;
                     const int var = P.tc_variant[tc_size_class(n)];
                     g.group_rows = kGroupRows[var & 3];
-                    if (P.precision == USTAT_BF16X3) e = launch_gemm_bf16x3(g, ((var >> 2) & 1) && !op.symmetric, C.st);
-                    else if (P.precision == USTAT_BF16X4) e = launch_gemm_bf16x4(g, C.st);
+                    int shape = (var >> 2) & 3;
+                    if (shape == 1 && op.symmetric) shape = 0;   // 128 x 64 tiles cannot skip symmetric tiles
+                    if (P.precision == USTAT_BF16X3) e = launch_gemm_bf16x3(g, shape, C.st);
+                    else if (P.precision == USTAT_BF16X4) e = launch_gemm_bf16x4(g, shape, C.st);
+                    else if (P.precision == USTAT_BF16X5) e = launch_gemm_bf16x5(g, C.st);
                     else e = launch_gemm_tf32(g, C.st);
                 } else {
                     SimtGemmArgs g{};
@@ -351,9 +359,8 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                         const int nb = (int)std::min<int64_t>(C.L.g3_nb, n - bb0);
                         // symmetric sources are read along rows (A(i, j) = M[j][i])
                         auto row_form = [&](const Term &t) { return P.slots[t.mat].symmetric ? 1 : t.trans; };
-                        e = launch_split_g3((const float *)C.ptr(op.A.mat), row_form(op.A), C.vec(op.u),
-                                            (const float *)C.ptr(op.Ab.mat), row_form(op.Ab), bb0, nb, n,
-                                            C.L.ldp_slices, lead, planes, sl, sc, C.st);
+                        e = launch_split_g3(C.ptr(op.A.mat), C.fp64, row_form(op.A), C.vec(op.u), C.ptr(op.Ab.mat),
+                                            row_form(op.Ab), bb0, nb, n, C.L.ldp_slices, lead, planes, sl, sc, C.st);
                         if (e != cudaSuccess) break;
                         TcGemmArgs g{};
                         g.n = n;
@@ -365,18 +372,20 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                         g.lead_bits = lead;
                         g.err = err;
                         g.nred = 1;
-                        g.red[0] = TcRed{(const float *)C.ptr(op.W.mat), tr(op.W), C.vec(op.a), C.vec(op.b), 1,
+                        g.red[0] = TcRed{C.ptr(op.W.mat), tr(op.W), C.vec(op.a), C.vec(op.b), 1,
                                          (double *)C.ptr(op.out)};
+                        g.wide = C.fp64;
                         g.batch = nb;
                         g.bb0 = (int)bb0;
-                        g.Wbc = (const float *)C.ptr(op.Wbc.mat);
+                        g.Wbc = C.ptr(op.Wbc.mat);
                         g.transWbc = tr(op.Wbc);
-                        g.Wbd = (const float *)C.ptr(op.Wbd.mat);
+                        g.Wbd = C.ptr(op.Wbd.mat);
                         g.transWbd = tr(op.Wbd);
                         g.ub = C.vec(op.ub);
                         g.group_rows = kGroupRows[var & 3];
-                        if (P.precision == USTAT_BF16X3) e = launch_gemm_bf16x3(g, (var >> 2) & 1, C.st);
-                        else e = launch_gemm_bf16x4(g, C.st);
+                        if (P.precision == USTAT_BF16X3) e = launch_gemm_bf16x3(g, (var >> 2) & 3, C.st);
+                        else if (P.precision == USTAT_BF16X5) e = launch_gemm_bf16x5(g, C.st);
+                        else e = launch_gemm_bf16x4(g, (var >> 2) & 3, C.st);
                     }
                     break;
                 }
@@ -499,7 +508,7 @@ int ustat_eval(ustat_plan_t *plan, const void *X, int x_dtype, int64_t n, int d,
     if (rc != USTAT_OK) return rc;
     Layout L = make_layout(P, n, d);
     if (!ws || ws_bytes < L.total || ((uintptr_t)ws % 256) != 0) return USTAT_ERR_WORKSPACE;
-    Ctx C{P, L, (char *)ws, n, d, P.precision == USTAT_FP64, (cudaStream_t)stream};
+    Ctx C{P, L, (char *)ws, n, d, wide_storage(P.precision), (cudaStream_t)stream};
     return run_program(C, X, x_dtype, factors, U_out, V_out);
 }
 
@@ -792,7 +801,7 @@ int batched_body(ustat_batched *b, const void *const *X, int x_dtype, const usta
         for (size_t i = 0; i < b->n.size(); ++i) {
             if (b->lane_of[i] != l) continue;
             Layout L = make_layout(P, b->n[i], b->d);
-            Ctx C{P, L, lws, b->n[i], b->d, P.precision == USTAT_FP64, b->streams[l]};
+            Ctx C{P, L, lws, b->n[i], b->d, wide_storage(P.precision), b->streams[l]};
             int rc = run_program(C, X[i], x_dtype, f, U_out + 2 * i, V_out ? V_out + i * (size_t)np : nullptr);
             if (rc != USTAT_OK) return rc;
         }
@@ -823,6 +832,14 @@ int batched_check(ustat_batched *b, const void *const *X, int x_dtype, const ust
 }  // namespace
 
 extern "C" {
+
+int ustat_plan_set_variant(ustat_plan_t *plan, int size_class, int variant) {
+    if (!plan || size_class < -1 || size_class > 3 || variant < 0 || variant > 15 || ((variant >> 2) & 3) == 3)
+        return USTAT_ERR_INVALID_ARG;
+    for (int c = 0; c < 4; ++c)
+        if (size_class < 0 || c == size_class) plan->p.tc_variant[c] = variant;
+    return USTAT_OK;
+}
 
 int ustat_batched_create(ustat_plan_t *plan, const int64_t *n, int count, int d, int max_lanes,
                          ustat_batched_t **out) {
@@ -972,11 +989,18 @@ int ustat_batched_autotune(ustat_batched_t *b, const void *const *X, int x_dtype
     if (rc == USTAT_OK && is_tc_mode(P.precision)) {
         bool present[4] = {false, false, false, false};
         for (int64_t v : b->n) present[tc_size_class(v)] = true;
-        const int nvar = P.precision == USTAT_BF16X3 ? 8 : 4;
+        // raster groups x tile shapes (bf16x3: 3 shapes; bf16x4: 2; tf32: 1)
+        std::vector<int> vars;
+        for (int shape = 0; shape < 3; ++shape) {
+            if (P.precision == USTAT_BF16X4 && shape == 1) continue;
+            if (P.precision == USTAT_BF16X5 && shape != 2) continue;
+            if (P.precision == USTAT_TF32 && shape > 0) continue;
+            for (int gr = 0; gr < 4; ++gr) vars.push_back(gr | (shape << 2));
+        }
         for (int c = 0; c < 4 && rc == USTAT_OK; ++c) {
             if (!present[c]) continue;
             int best_v = P.tc_variant[c];
-            for (int v = 0; v < nvar; ++v) {
+            for (int v : vars) {
                 if (v == best_v) continue;
                 const int keep = P.tc_variant[c];
                 P.tc_variant[c] = v;

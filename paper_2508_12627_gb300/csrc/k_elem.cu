@@ -626,6 +626,32 @@ __global__ void diag_kernel(const T *M, int64_t n, double *out) {
         out[i] = (double)M[i * n + i];
 }
 
+// Diagonal of a factor from its own data, in float64: x_i . x_i / param for the
+// linear kernel (X as given, float64 or float32), M[i][i] for a caller matrix;
+// 0 in the sparsified mode.  The stored working-precision matrix would round
+// every entry to float32 first, and a partition whose blocks merge all indices
+// multiplies several diagonal entries per term.
+__global__ void factor_diag_kernel(int kind, double inv_param, const void *X, int x_dtype, int d,
+                                   const double *Mc, int64_t n, int zero_diag, double *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double v = 0.0;
+        if (!zero_diag) {
+            if (kind == USTAT_LINEAR) {
+                for (int k = 0; k < d; ++k) {
+                    const double x = x_dtype == 0 ? ((const double *)X)[i * d + k] : (double)((const float *)X)[i * d + k];
+                    v = fma(x, x, v);
+                }
+                v *= inv_param;
+            } else if (kind == USTAT_RBF) {
+                v = 1.0;
+            } else {
+                v = Mc[i * n + i];
+            }
+        }
+        out[i] = v;
+    }
+}
+
 __global__ void vmul_kernel(const double *a, const double *b, int64_t n, double *out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = a[i] * b[i];
@@ -795,6 +821,12 @@ cudaError_t launch_copyvec(const double *src, int64_t n, double *dst, cudaStream
 cudaError_t launch_diag(const void *M, bool fp64, int64_t n, double *out, cudaStream_t s) {
     if (fp64) diag_kernel<double><<<grid_for(n, 256), 256, 0, s>>>((const double *)M, n, out);
     else diag_kernel<float><<<grid_for(n, 256), 256, 0, s>>>((const float *)M, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_factor_diag(int kind, double param, const void *X, int x_dtype, int d, const double *Mc,
+                               int64_t n, int zero_diag, double *out, cudaStream_t s) {
+    factor_diag_kernel<<<grid_for(n, 256), 256, 0, s>>>(kind, 1.0 / param, X, x_dtype, d, Mc, n, zero_diag, out);
     return cudaGetLastError();
 }
 

@@ -63,6 +63,31 @@ __device__ __forceinline__ int row_exp(float m) {
     return e;
 }
 
+__device__ __forceinline__ int row_exp(double m) {
+    int e = 0;
+    if (m > 0.0) {
+        const double f = frexp(m, &e);
+        if (f == 0.5) e -= 1;
+    }
+    return e;
+}
+
+// float64 source (the wide-storage mode): the same digits, computed in float64
+// (every step exact), of the value itself rather than of its float32 rounding
+__device__ __forceinline__ void write_digits(double x, int lead_bits, int e, int planes, __nv_bfloat16 *dst,
+                                             int64_t plane_stride) {
+    double y = ldexp(x, lead_bits - e);   // |y| <= 2^w, exact
+    double d = rint(y);
+    dst[0] = __double2bfloat16(d);
+    double scale = 1.0 / 256.0;
+    for (int p = 1; p < planes; ++p) {
+        y = (y - d) * 256.0;               // exact
+        d = rint(y);
+        dst[p * plane_stride] = __double2bfloat16(d * scale);
+        scale *= (1.0 / 256.0);
+    }
+}
+
 __device__ __forceinline__ void write_digits(float x, int lead_bits, int e, int planes, __nv_bfloat16 *dst,
                                              int64_t plane_stride) {
     const int k = lead_bits - e;
@@ -80,19 +105,20 @@ __device__ __forceinline__ void write_digits(float x, int lead_bits, int e, int 
 
 // Row-major source (X(j, i) = M[j][i] u(i)): one warp per operand row, two passes
 // (row maximum, then digits), fully coalesced.
-__global__ void __launch_bounds__(256) split_rows_kernel(const float *__restrict__ M, const double *__restrict__ u,
+template <typename T>
+__global__ void __launch_bounds__(256) split_rows_kernel(const T *__restrict__ M, const double *__restrict__ u,
                                                          int64_t n, int64_t ldp, int lead_bits, int planes,
                                                          __nv_bfloat16 *__restrict__ slices,
                                                          float *__restrict__ scales) {
     const int lane = threadIdx.x & 31;
     const int64_t j = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (j >= n) return;
-    const float *row = M + j * n;
-    float mx = 0.f;
+    const T *row = M + j * n;
+    T mx = 0;
     for (int64_t i = lane; i < n; i += 32) {
-        float x = row[i];
-        if (u) x *= (float)u[i];
-        mx = fmaxf(mx, fabsf(x));
+        T x = row[i];
+        if (u) x *= (T)u[i];
+        mx = fmax(mx, fabs(x));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -100,10 +126,10 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const float *__restrict
     if (lane == 0) scales[j] = ldexpf(1.f, e);
     const int64_t plane = n * ldp;
     for (int64_t i = lane; i < ldp; i += 32) {
-        float x = 0.f;
+        T x = 0;
         if (i < n) {
             x = row[i];
-            if (u) x *= (float)u[i];
+            if (u) x *= (T)u[i];
         }
         write_digits(x, lead_bits, e, planes, slices + j * ldp + i, plane);
     }
@@ -184,20 +210,50 @@ __global__ void __launch_bounds__(256) split_rows_g3_kernel(const float *__restr
     }
 }
 
+// The same for float64 sources (wide-storage mode): one warp per row, scalar.
+__global__ void __launch_bounds__(256) split_rows_g3_wide_kernel(const double *__restrict__ M,
+                                                                 const double *__restrict__ u,
+                                                                 const double *__restrict__ Mb, int transAb,
+                                                                 int64_t bb0, int64_t n, int64_t ldp, int lead_bits,
+                                                                 int planes, __nv_bfloat16 *__restrict__ slices,
+                                                                 float *__restrict__ scales) {
+    const int64_t bb = bb0 + blockIdx.y;
+    slices += (int64_t)blockIdx.y * planes * n * ldp;
+    scales += (int64_t)blockIdx.y * n;
+    const int lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (j >= n) return;
+    const double *row = M + j * n;
+    auto val = [&](int64_t i) -> double {
+        double x = row[i] * (transAb ? Mb[bb * n + i] : Mb[i * n + bb]);
+        if (u) x *= u[i];
+        return x;
+    };
+    double mx = 0.0;
+    for (int64_t i = lane; i < n; i += 32) mx = fmax(mx, fabs(val(i)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int e = row_exp(mx);
+    if (lane == 0) scales[j] = ldexpf(1.f, e);
+    const int64_t plane = n * ldp;
+    for (int64_t i = lane; i < ldp; i += 32)
+        write_digits(i < n ? val(i) : 0.0, lead_bits, e, planes, slices + j * ldp + i, plane);
+}
+
 // Column source (X(j, i) = M[i][j] u(i)) and the tf32 copy: one block per 32
 // operand rows, transposed through shared memory.
 // With Mb (the s = 3 step): X(j, i) is further scaled by Ab(i, bb), bb = bb0 +
 // blockIdx.y, and the digits and scales of bb go to its own region.
-template <bool kSplit>
-__global__ void __launch_bounds__(256) operand_cols_kernel(const float *__restrict__ M, int trans,
+template <bool kSplit, typename T = float>
+__global__ void __launch_bounds__(256) operand_cols_kernel(const T *__restrict__ M, int trans,
                                                            const double *__restrict__ u, int64_t n, int64_t ldp,
                                                            int lead_bits, int planes,
                                                            __nv_bfloat16 *__restrict__ slices,
                                                            float *__restrict__ scales, float *__restrict__ prep,
-                                                           const float *__restrict__ Mb = nullptr, int transAb = 0,
+                                                           const T *__restrict__ Mb = nullptr, int transAb = 0,
                                                            int64_t bb0 = 0) {
-    __shared__ float tile[32][33];
-    __shared__ float rmax[8][32];
+    __shared__ T tile[32][33];
+    __shared__ T rmax[8][32];
     __shared__ int rexp[32];
     const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
     const int64_t j0 = (int64_t)blockIdx.x * 32;
@@ -206,32 +262,32 @@ __global__ void __launch_bounds__(256) operand_cols_kernel(const float *__restri
         slices += (int64_t)blockIdx.y * planes * n * ldp;
         scales += (int64_t)blockIdx.y * n;
     }
-    auto val = [&](int64_t j, int64_t i) -> float {
-        if (j >= n || i >= n) return 0.f;
-        float x = trans ? M[j * n + i] : M[i * n + j];
-        if (u) x *= (float)u[i];
+    auto val = [&](int64_t j, int64_t i) -> T {
+        if (j >= n || i >= n) return T(0);
+        T x = trans ? M[j * n + i] : M[i * n + j];
+        if (u) x *= (T)u[i];
         if (Mb) x *= transAb ? Mb[bb * n + i] : Mb[i * n + bb];
         return x;
     };
     if (kSplit) {
-        float mx = 0.f;
+        T mx = 0;
         if (!trans) {
-            for (int64_t i = ty; i < n; i += 8) mx = fmaxf(mx, fabsf(val(j0 + tx, i)));
+            for (int64_t i = ty; i < n; i += 8) mx = fmax(mx, fabs(val(j0 + tx, i)));
             rmax[ty][tx] = mx;
         } else {
             for (int r = 0; r < 4; ++r) {
-                float m2 = 0.f;
-                for (int64_t i = tx; i < n; i += 32) m2 = fmaxf(m2, fabsf(val(j0 + ty + 8 * r, i)));
+                T m2 = 0;
+                for (int64_t i = tx; i < n; i += 32) m2 = fmax(m2, fabs(val(j0 + ty + 8 * r, i)));
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+                for (int o = 16; o > 0; o >>= 1) m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
                 if (tx == 0) tile[ty + 8 * r][0] = m2;
             }
         }
         __syncthreads();
         if (ty == 0) {
-            float m = 0.f;
+            T m = 0;
             if (!trans) {
-                for (int q = 0; q < 8; ++q) m = fmaxf(m, rmax[q][tx]);
+                for (int q = 0; q < 8; ++q) m = fmax(m, rmax[q][tx]);
             } else {
                 m = tile[tx][0];
             }
@@ -256,12 +312,12 @@ __global__ void __launch_bounds__(256) operand_cols_kernel(const float *__restri
             const int jj = ty + 8 * r;
             const int64_t j = j0 + jj, i = i0 + tx;
             if (j >= n) continue;
-            const float x = tile[jj][tx];
+            const T x = tile[jj][tx];
             if (kSplit) {
                 write_digits(x, lead_bits, rexp[jj], planes, slices + j * ldp + i, plane);
             } else {
                 uint32_t t;
-                asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(x));
+                asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"((float)x));
                 prep[j * ldp + i] = __uint_as_float(t);
             }
         }
@@ -335,15 +391,17 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Shared-memory matrix descriptor: K-major tile, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (SBO), descriptor version 1.
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+// Shared-memory matrix descriptor: K-major tile whose rows are kRowBytes long
+// (128: 128-byte swizzle, 8-row groups 1024 bytes apart; 64: 64-byte swizzle,
+// 8-row groups 512 bytes apart), descriptor version 1.
+template <int kRowBytes>
+__device__ __forceinline__ uint64_t desc_sw(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;             // LBO (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;   // SBO
-    d |= (uint64_t)1 << 46;             // version
-    d |= (uint64_t)2 << 61;             // SWIZZLE_128B
+    d |= (uint64_t)1 << 16;                         // LBO (unused for swizzled K-major)
+    d |= (uint64_t)((8 * kRowBytes) >> 4) << 32;    // SBO
+    d |= (uint64_t)1 << 46;                         // version
+    d |= (uint64_t)(kRowBytes == 128 ? 2 : 4) << 61;   // SWIZZLE_128B / SWIZZLE_64B
     return d;
 }
 
@@ -387,21 +445,34 @@ __host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t M, uint
 constexpr int kBM = 128;
 constexpr int kThreads = 192;
 
-// 0 = split bf16 x3, 128 x 128 tiles; 1 = tf32; 2 = split bf16 x4 (128 x 64);
-// 3 = split bf16 x3 with 128 x 64 tiles and a deeper pipeline
-template <int kMode>
+// 0 = split bf16 x3, 128 x 128 tiles, 128-byte rows, 2 stages;
+// 1 = tf32; 2 = split bf16 x4, 128 x 64 tiles, 2 stages;
+// 3 = split bf16 x3, 128 x 64 tiles, 3 stages;
+// 4 = split bf16 x3, 128 x 128 tiles, 64-byte rows (half the k-block), 4 stages;
+// 5 = split bf16 x4, 128 x 128 tiles, 64-byte rows, 3 stages;
+// 6 = split bf16 x5, 128 x 128 tiles, 64-byte rows, 2 stages
+// kWide (float64 storage, bf16x4 / bf16x5): one TMEM accumulator set per CTA
+// instead of two, laid out [hi | mid0 | mid1 | lo]: the two slice products of
+// weight 2^-8 alternate by k-block between mid0 and mid1 and the smaller ones go
+// to lo.  Tensor-core float32 accumulation truncates; splitting the dominant
+// correction terms over separate accumulators, each with fewer additions, cuts
+// the bias that truncation leaves in a long contraction.
+template <int kMode, bool kWide = false>
 struct Cfg {
     static constexpr bool kTf32 = kMode == 1;
-    static constexpr int kPlanes = (kMode == 0 || kMode == 3) ? 3 : (kMode == 1 ? 1 : 4);
+    static constexpr int kPlanes =
+        (kMode == 0 || kMode == 3 || kMode == 4) ? 3 : (kMode == 1 ? 1 : (kMode == 6 ? 5 : 4));
     static constexpr int kBN = (kMode == 2 || kMode == 3) ? 64 : 128;
-    static constexpr int kBKElems = kTf32 ? 32 : 64;       // 128 bytes per row
+    static constexpr int kRowBytes = (kMode == 4 || kMode == 5 || kMode == 6) ? 64 : 128;
+    static constexpr int kBKElems = kRowBytes / (kTf32 ? 4 : 2);
     static constexpr int kMmaK = kTf32 ? 8 : 16;            // 32 bytes per MMA k step
-    static constexpr int kATile = kBM * 128;                // one plane of A
-    static constexpr int kBTile = kBN * 128;                // one plane of B
+    static constexpr int kATile = kBM * kRowBytes;          // one plane of A
+    static constexpr int kBTile = kBN * kRowBytes;          // one plane of B
     static constexpr int kStageBytes = kPlanes * (kATile + kBTile);
-    static constexpr int kStages = kTf32 ? 6 : (kMode == 3 ? 3 : 2);
-    static constexpr int kAccCols = kTf32 ? kBN : 2 * kBN;  // hi (+ lo)
-    static constexpr int kTmemCols = 2 * kAccCols;          // double buffer
+    static constexpr int kStages = kTf32 ? 6 : (kMode == 3 ? 3 : (kMode == 4 ? 4 : (kMode == 5 ? 3 : 2)));
+    static constexpr int kBufs = kWide ? 1 : 2;             // accumulator sets
+    static constexpr int kAccCols = kTf32 ? kBN : (kWide ? 4 * kBN : 2 * kBN);   // hi (+ mid0, mid1) (+ lo)
+    static constexpr int kTmemCols = kBufs * kAccCols;
     static constexpr int kSmem = kStages * kStageBytes + 1024 + 512;
 };
 
@@ -443,11 +514,11 @@ struct TileWalk {
     }
 };
 
-template <int kMode>
+template <int kMode, bool kWide = false>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const __grid_constant__ CUtensorMap mapB2, TcGemmArgs g) {
-    using C = Cfg<kMode>;
+    using C = Cfg<kMode, kWide>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -552,13 +623,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                 unit(t, bl, tm, tn, c_off, width);
                 const uint32_t idesc = width == C::kBN ? idesc_full : idesc_half;
                 const uint32_t b_plane = width == C::kBN ? C::kBTile : C::kBTile / 2;   // bytes per B plane
-                const int buf = tcount & 1;
-                if (tcount >= 2 && !mbar_wait(tempty_bar(buf), ((tcount >> 1) - 1) & 1, abort_flag)) {
+                const int buf = tcount % C::kBufs;
+                if (tcount >= (uint32_t)C::kBufs &&
+                    !mbar_wait(tempty_bar(buf), ((tcount / C::kBufs) - 1) & 1, abort_flag)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d_hi = tmem + buf * C::kAccCols, d_lo = d_hi + C::kBN;
+                const uint32_t d_hi = tmem + buf * C::kAccCols;
+                const uint32_t d_lo = d_hi + (kWide ? 3 : 1) * C::kBN;
                 for (int kb = 0; kb < num_k; ++kb, ++it) {
                     const int s = it % C::kStages;
                     if (!mbar_wait(full_bar(s), (it / C::kStages) & 1, abort_flag)) {
@@ -574,25 +647,34 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const uint32_t koff = kk * 32;
                         const uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
                         if constexpr (C::kTf32) {
-                            mma<true>(d_hi, desc_sw128(sa + koff), desc_sw128(sb + koff), idesc, acc0);
+                            mma<true>(d_hi, desc_sw<C::kRowBytes>(sa + koff), desc_sw<C::kRowBytes>(sb + koff), idesc, acc0);
                         } else {
                             uint64_t ad[C::kPlanes], bd[C::kPlanes];
 #pragma unroll
                             for (int p = 0; p < C::kPlanes; ++p) {
-                                ad[p] = desc_sw128(sa + p * C::kATile + koff);
-                                bd[p] = desc_sw128(sb + p * b_plane + koff);
+                                ad[p] = desc_sw<C::kRowBytes>(sa + p * C::kATile + koff);
+                                bd[p] = desc_sw<C::kRowBytes>(sb + p * b_plane + koff);
                             }
+                            // leading product into its own accumulator; every slice
+                            // pair of weight 2^-8 .. 2^-8 (S - 1) into the other
                             mma<false>(d_hi, ad[0], bd[0], idesc, acc0);
-                            mma<false>(d_lo, ad[0], bd[1], idesc, acc0);
-                            mma<false>(d_lo, ad[1], bd[0], idesc, 1u);
-                            mma<false>(d_lo, ad[0], bd[2], idesc, 1u);
-                            mma<false>(d_lo, ad[2], bd[0], idesc, 1u);
-                            mma<false>(d_lo, ad[1], bd[1], idesc, 1u);
-                            if constexpr (C::kPlanes == 4) {
-                                mma<false>(d_lo, ad[0], bd[3], idesc, 1u);
-                                mma<false>(d_lo, ad[3], bd[0], idesc, 1u);
-                                mma<false>(d_lo, ad[1], bd[2], idesc, 1u);
-                                mma<false>(d_lo, ad[2], bd[1], idesc, 1u);
+                            if constexpr (kWide) {
+                                const uint32_t d_mid = d_hi + (1 + (kb & 1)) * C::kBN;
+                                const uint32_t accm = (kb > 1 || kk > 0) ? 1u : 0u;
+                                mma<false>(d_mid, ad[0], bd[1], idesc, accm);
+                                mma<false>(d_mid, ad[1], bd[0], idesc, 1u);
+                                if (C::kPlanes > 2) mma<false>(d_lo, ad[0], bd[2], idesc, acc0);
+                            } else {
+                                mma<false>(d_lo, ad[0], bd[1], idesc, acc0);
+                                mma<false>(d_lo, ad[1], bd[0], idesc, 1u);
+                            }
+#pragma unroll
+                            for (int sum = 2; sum < C::kPlanes; ++sum) {
+#pragma unroll
+                                for (int i = 0; i <= sum; ++i) {
+                                    if (kWide && sum == 2 && i == 0) continue;   // issued above
+                                    mma<false>(d_lo, ad[i], bd[sum - i], idesc, 1u);
+                                }
                             }
                         }
                     }
@@ -613,105 +695,159 @@ __global__ void __launch_bounds__(kThreads, 1)
             int bl, tm, tn, c_off, width;
             unit(t, bl, tm, tn, c_off, width);
             const int64_t bb = g.bb0 + bl;   // batched s = 3 step: this product's index
-            const float *Wbd = g.Wbd;
+            const float *Wbd = (const float *)g.Wbd;
             const int tWbd = g.transWbd;
-            const int buf = tcount & 1;
+            const int buf = tcount % C::kBufs;
             // one lane polls (with back-off: the main loop of a tile takes tens of
             // microseconds) so the waiting warps leave the issue slots to the TMA
             // and MMA warps
             int waited = 0;
-            if (lane == 0) waited = mbar_wait(tfull_bar(buf), (tcount >> 1) & 1, abort_flag) ? 1 : 0;
+            if (lane == 0) waited = mbar_wait(tfull_bar(buf), (tcount / C::kBufs) & 1, abort_flag) ? 1 : 0;
             waited = __shfl_sync(0xffffffffu, waited, 0);
             if (!waited || *abort_flag) break;
             tc_fence_after();
             const int64_t j = (int64_t)tm * kBM + row;
             const bool jok = j < n;
             const float rs = jok ? (C::kTf32 ? 1.f : ldexpf(g.scaleA[(int64_t)bl * n + j], -2 * g.lead_bits)) : 0.f;
+            const double rs_d = jok && !C::kTf32 ? ldexp((double)g.scaleA[(int64_t)bl * n + j], -2 * g.lead_bits) : 0.0;
             const uint32_t taddr = tmem + buf * C::kAccCols + ((uint32_t)(32 * q) << 16);
             double tile_acc[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll 1
             for (int c0 = 0; c0 < width; c0 += 16) {
-                uint32_t hi[16], lo[16];
+                uint32_t hi[16], lo[16], m0[16], m1[16];
                 tmem_ld16(taddr + c0, hi);
-                if (!C::kTf32) tmem_ld16(taddr + C::kBN + c0, lo);
+                if constexpr (kWide) {
+                    tmem_ld16(taddr + C::kBN + c0, m0);
+                    tmem_ld16(taddr + 2 * C::kBN + c0, m1);
+                    tmem_ld16(taddr + 3 * C::kBN + c0, lo);
+                } else {
+                    if (!C::kTf32) tmem_ld16(taddr + C::kBN + c0, lo);
+                }
                 tmem_wait_ld();
                 const int64_t k0 = (int64_t)tn * C::kBN + c_off + c0;
-                float v[16];
+                if constexpr (kWide) {
+                    // float64 storage: the entry, the weights and the partial sums in
+                    // float64 (hi is an exact integer sum, lo its small correction)
+                    double v[16];
 #pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                    float x = __uint_as_float(hi[c]);
-                    if (!C::kTf32) {
+                    for (int c = 0; c < 16; ++c) {
                         const int64_t k = k0 + c;
-                        x = (x + __uint_as_float(lo[c])) * (k < n ? g.scaleB[k] : 0.f);
+                        // mid1 holds the odd k-blocks' products: nothing when there is one
+                        const double x = (double)__uint_as_float(hi[c]) + (double)__uint_as_float(m0[c]) +
+                                         (num_k > 1 ? (double)__uint_as_float(m1[c]) : 0.0) +
+                                         (C::kPlanes > 2 ? (double)__uint_as_float(lo[c]) : 0.0);
+                        v[c] = k < n ? x * (double)g.scaleB[k] * rs_d : 0.0;
                     }
-                    v[c] = x * rs;
-                }
-                if (g.C && jok) {
+                    if (g.C && jok) {
+                        double *Cd = (double *)g.C;
 #pragma unroll
-                    for (int c = 0; c < 16; ++c)
-                        if (k0 + c < n) g.C[j * n + k0 + c] = v[c];
-                }
-                // the 16 columns lie inside the matrix and rows are 16-byte aligned:
-                // weights are read as float4
-                const bool full = (k0 + 16 <= n) && ((n & 3) == 0);
+                        for (int c = 0; c < 16; ++c)
+                            if (k0 + c < n) Cd[j * n + k0 + c] = v[c];
+                    }
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    if (r >= g.nred) break;
-                    const float *W = g.red[r].W;
-                    const double *bv = g.red[r].b;
-                    const int tW = g.red[r].transW, pw = g.red[r].pow;
-                    float part = 0.f;
-                    if (jok) {
-                        float w[16];
-                        if (W && !tW && full) {
-                            const float4 *p4 = reinterpret_cast<const float4 *>(W + j * n + k0);
-#pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                const float4 t4 = p4[q];
-                                w[4 * q] = t4.x, w[4 * q + 1] = t4.y, w[4 * q + 2] = t4.z, w[4 * q + 3] = t4.w;
-                            }
-                        } else {
+                    for (int r = 0; r < 4; ++r) {
+                        if (r >= g.nred) break;
+                        const double *W = (const double *)g.red[r].W;
+                        const double *bv = g.red[r].b;
+                        const double *Wbd = (const double *)g.Wbd;
+                        const int tW = g.red[r].transW, pw = g.red[r].pow;
+                        double part = 0.0;
+                        if (jok) {
 #pragma unroll
                             for (int c = 0; c < 16; ++c) {
                                 const int64_t k = k0 + c;
-                                w[c] = k < n ? (W ? (tW ? W[k * n + j] : W[j * n + k]) : 1.f) : 0.f;
+                                if (k >= n) continue;
+                                double w = bv ? bv[k] : 1.0;
+                                if (W) w *= tW ? W[k * n + j] : W[j * n + k];
+                                if (Wbd) w *= g.transWbd ? Wbd[k * n + bb] : Wbd[bb * n + k];
+                                const double x = pw == 2 ? v[c] * v[c] : v[c];
+                                part = fma(x, w, part);
                             }
                         }
-                        if (bv) {
-#pragma unroll
-                            for (int c = 0; c < 16; ++c) w[c] *= k0 + c < n ? (float)bv[k0 + c] : 0.f;
+                        tile_acc[r] += part;
+                    }
+                } else {
+                    float v[16];
+    #pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        float x = __uint_as_float(hi[c]);
+                        if (!C::kTf32) {
+                            const int64_t k = k0 + c;
+                            x = (x + __uint_as_float(lo[c])) * (k < n ? g.scaleB[k] : 0.f);
                         }
-                        if (Wbd) {
-                            if (!tWbd && full) {
-                                const float4 *p4 = reinterpret_cast<const float4 *>(Wbd + bb * n + k0);
-#pragma unroll
+                        v[c] = x * rs;
+                    }
+                    if (g.C && jok) {
+    #pragma unroll
+                        for (int c = 0; c < 16; ++c)
+                            if (k0 + c < n) ((float *)g.C)[j * n + k0 + c] = v[c];
+                    }
+                    // the 16 columns lie inside the matrix and rows are 16-byte aligned:
+                    // weights are read as float4
+                    const bool full = (k0 + 16 <= n) && ((n & 3) == 0);
+    #pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        if (r >= g.nred) break;
+                        const float *W = (const float *)g.red[r].W;
+                        const double *bv = g.red[r].b;
+                        const int tW = g.red[r].transW, pw = g.red[r].pow;
+                        float part = 0.f;
+                        if (jok) {
+                            float w[16];
+                            if (W && !tW && full) {
+                                const float4 *p4 = reinterpret_cast<const float4 *>(W + j * n + k0);
+    #pragma unroll
                                 for (int q = 0; q < 4; ++q) {
                                     const float4 t4 = p4[q];
-                                    w[4 * q] *= t4.x, w[4 * q + 1] *= t4.y, w[4 * q + 2] *= t4.z, w[4 * q + 3] *= t4.w;
+                                    w[4 * q] = t4.x, w[4 * q + 1] = t4.y, w[4 * q + 2] = t4.z, w[4 * q + 3] = t4.w;
                                 }
                             } else {
-#pragma unroll
+    #pragma unroll
                                 for (int c = 0; c < 16; ++c) {
                                     const int64_t k = k0 + c;
-                                    if (k < n) w[c] *= tWbd ? Wbd[k * n + bb] : Wbd[bb * n + k];
+                                    w[c] = k < n ? (W ? (tW ? W[k * n + j] : W[j * n + k]) : 1.f) : 0.f;
                                 }
                             }
+                            if (bv) {
+    #pragma unroll
+                                for (int c = 0; c < 16; ++c) w[c] *= k0 + c < n ? (float)bv[k0 + c] : 0.f;
+                            }
+                            if (Wbd) {
+                                if (!tWbd && full) {
+                                    const float4 *p4 = reinterpret_cast<const float4 *>(Wbd + bb * n + k0);
+    #pragma unroll
+                                    for (int q = 0; q < 4; ++q) {
+                                        const float4 t4 = p4[q];
+                                        w[4 * q] *= t4.x, w[4 * q + 1] *= t4.y, w[4 * q + 2] *= t4.z, w[4 * q + 3] *= t4.w;
+                                    }
+                                } else {
+    #pragma unroll
+                                    for (int c = 0; c < 16; ++c) {
+                                        const int64_t k = k0 + c;
+                                        if (k < n) w[c] *= tWbd ? Wbd[k * n + bb] : Wbd[bb * n + k];
+                                    }
+                                }
+                            }
+    #pragma unroll
+                            for (int c = 0; c < 16; ++c) {
+                                const float x = pw == 2 ? v[c] * v[c] : v[c];
+                                part = fmaf(x, w[c], part);
+                            }
                         }
-#pragma unroll
-                        for (int c = 0; c < 16; ++c) {
-                            const float x = pw == 2 ? v[c] * v[c] : v[c];
-                            part = fmaf(x, w[c], part);
-                        }
+                        tile_acc[r] += (double)part;
                     }
-                    tile_acc[r] += (double)part;
                 }
-            }
+                }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty_bar(buf));
             double wgt = (g.symmetric && tm != tn) ? 2.0 : 1.0;
             if (g.ub) wgt *= g.ub[bb];
-            const double wbc = (g.Wbc && jok) ? (double)(g.transWbc ? g.Wbc[j * n + bb] : g.Wbc[bb * n + j]) : 1.0;
+            double wbc = 1.0;
+            if (g.Wbc && jok) {
+                const int64_t wi = g.transWbc ? j * n + bb : bb * n + j;
+                wbc = kWide ? ((const double *)g.Wbc)[wi] : (double)((const float *)g.Wbc)[wi];
+            }
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 if (r >= g.nred) break;
@@ -768,19 +904,21 @@ EncodeTiledFn get_encode() {
     return fn;
 }
 
-// total_planes x rows x ldp (innermost) tensor, box {128 bytes, box_rows, planes}.
+// total_planes x rows x ldp (innermost) tensor, box {row_bytes, box_rows, planes},
+// swizzled to match (128 or 64 bytes).
 bool make_map_planes(CUtensorMap *map, const void *ptr, bool bf16, int planes, int total_planes, int64_t rows,
-                     int64_t ldp, int box_rows) {
+                     int64_t ldp, int box_rows, int row_bytes = 128) {
     EncodeTiledFn enc = get_encode();
     if (!enc) return false;
     const int esz = bf16 ? 2 : 4;
     cuuint64_t dims[3] = {(cuuint64_t)ldp, (cuuint64_t)rows, (cuuint64_t)total_planes};
     cuuint64_t strides[2] = {(cuuint64_t)(ldp * esz), (cuuint64_t)(rows * ldp * esz)};
-    cuuint32_t box[3] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows, (cuuint32_t)planes};
+    cuuint32_t box[3] = {(cuuint32_t)(row_bytes / esz), (cuuint32_t)box_rows, (cuuint32_t)planes};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
                      const_cast<void *>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
@@ -798,9 +936,9 @@ int sm_count() {
     return cnt[dev];
 }
 
-template <int kMode>
+template <int kMode, bool kWide = false>
 cudaError_t launch_tc(const TcGemmArgs &g0, cudaStream_t s) {
-    using C = Cfg<kMode>;
+    using C = Cfg<kMode, kWide>;
     TcGemmArgs g = g0;
     if (C::kBN != kBM || g.C) g.symmetric = 0;
     if (g.nred < 0 || g.nred > 4) return cudaErrorInvalidValue;
@@ -809,15 +947,15 @@ cudaError_t launch_tc(const TcGemmArgs &g0, cudaStream_t s) {
     if (g.batch > 0 && (g.C || g.nred != 1)) return cudaErrorInvalidValue;
     const int za = g.batch > 0 ? g.batch : 1;
     CUtensorMap mb2;
-    if (!make_map_planes(&ma, g.opA, bf16, C::kPlanes, za * C::kPlanes, g.n, g.ldp, kBM) ||
-        !make_map_planes(&mb, g.opB, bf16, C::kPlanes, C::kPlanes, g.n, g.ldp, C::kBN) ||
-        !make_map_planes(&mb2, g.opB, bf16, C::kPlanes, C::kPlanes, g.n, g.ldp, C::kBN / 2))
+    if (!make_map_planes(&ma, g.opA, bf16, C::kPlanes, za * C::kPlanes, g.n, g.ldp, kBM, C::kRowBytes) ||
+        !make_map_planes(&mb, g.opB, bf16, C::kPlanes, C::kPlanes, g.n, g.ldp, C::kBN, C::kRowBytes) ||
+        !make_map_planes(&mb2, g.opB, bf16, C::kPlanes, C::kPlanes, g.n, g.ldp, C::kBN / 2, C::kRowBytes))
         return cudaErrorInvalidValue;
     static bool attr[64] = {false};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<kMode, kWide>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              C::kSmem);
         if (e != cudaSuccess) return e;
         attr[dev] = true;
@@ -834,29 +972,51 @@ cudaError_t launch_tc(const TcGemmArgs &g0, cudaStream_t s) {
     g.split_tail = (int)split;
     const int64_t units = tiles + split;
     const int grid = (int)(units < S ? units : S);
-    tc_gemm_kernel<kMode><<<grid, kThreads, C::kSmem, s>>>(ma, mb, mb2, g);
+    tc_gemm_kernel<kMode, kWide><<<grid, kThreads, C::kSmem, s>>>(ma, mb, mb2, g);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_split(const float *M, int trans, const double *u, int64_t n, int64_t ldp, int lead_bits,
-                         int planes, void *slices, float *scales, cudaStream_t s) {
+cudaError_t launch_split(const void *M, bool wide, int trans, const double *u, int64_t n, int64_t ldp,
+                         int lead_bits, int planes, void *slices, float *scales, cudaStream_t s) {
     if (trans) {
-        split_rows_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(M, u, n, ldp, lead_bits, planes,
-                                                                  (__nv_bfloat16 *)slices, scales);
+        if (wide)
+            split_rows_kernel<double><<<(unsigned)((n + 7) / 8), 256, 0, s>>>(
+                (const double *)M, u, n, ldp, lead_bits, planes, (__nv_bfloat16 *)slices, scales);
+        else
+            split_rows_kernel<float><<<(unsigned)((n + 7) / 8), 256, 0, s>>>(
+                (const float *)M, u, n, ldp, lead_bits, planes, (__nv_bfloat16 *)slices, scales);
     } else {
         dim3 grid((unsigned)((n + 31) / 32)), block(32, 8);
-        operand_cols_kernel<true><<<grid, block, 0, s>>>(M, 0, u, n, ldp, lead_bits, planes,
-                                                         (__nv_bfloat16 *)slices, scales, nullptr);
+        if (wide)
+            operand_cols_kernel<true, double><<<grid, block, 0, s>>>((const double *)M, 0, u, n, ldp, lead_bits,
+                                                                     planes, (__nv_bfloat16 *)slices, scales, nullptr);
+        else
+            operand_cols_kernel<true, float><<<grid, block, 0, s>>>((const float *)M, 0, u, n, ldp, lead_bits, planes,
+                                                                    (__nv_bfloat16 *)slices, scales, nullptr);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_split_g3(const float *M, int trans, const double *u, const float *Mb, int transAb, int64_t bb0,
-                            int nb, int64_t n, int64_t ldp, int lead_bits, int planes, void *slices, float *scales,
-                            cudaStream_t s) {
+cudaError_t launch_split_g3(const void *Mv, bool wide, int trans, const double *u, const void *Mbv, int transAb,
+                            int64_t bb0, int nb, int64_t n, int64_t ldp, int lead_bits, int planes, void *slices,
+                            float *scales, cudaStream_t s) {
     if (nb < 1 || nb > 65535) return cudaErrorInvalidValue;
+    if (wide) {
+        if (trans) {
+            dim3 grid((unsigned)((n + 7) / 8), (unsigned)nb);
+            split_rows_g3_wide_kernel<<<grid, 256, 0, s>>>((const double *)Mv, u, (const double *)Mbv, transAb, bb0, n,
+                                                          ldp, lead_bits, planes, (__nv_bfloat16 *)slices, scales);
+        } else {
+            dim3 grid((unsigned)((n + 31) / 32), (unsigned)nb), block(32, 8);
+            operand_cols_kernel<true, double><<<grid, block, 0, s>>>((const double *)Mv, trans, u, n, ldp, lead_bits,
+                                                                     planes, (__nv_bfloat16 *)slices, scales, nullptr,
+                                                                     (const double *)Mbv, transAb, bb0);
+        }
+        return cudaGetLastError();
+    }
+    const float *M = (const float *)Mv, *Mb = (const float *)Mbv;
     if (trans && n <= 32768) {
         // A(i, j) = M[j][i]: operand rows are source rows
         const int smem = (int)(sizeof(float) * n);
@@ -877,7 +1037,7 @@ cudaError_t launch_split_g3(const float *M, int trans, const double *u, const fl
         return cudaGetLastError();
     }
     dim3 grid((unsigned)((n + 31) / 32), (unsigned)nb), block(32, 8);
-    operand_cols_kernel<true><<<grid, block, 0, s>>>(M, trans, u, n, ldp, lead_bits, planes,
+    operand_cols_kernel<true, float><<<grid, block, 0, s>>>(M, trans, u, n, ldp, lead_bits, planes,
                                                      (__nv_bfloat16 *)slices, scales, nullptr, Mb, transAb, bb0);
     return cudaGetLastError();
 }
@@ -885,14 +1045,23 @@ cudaError_t launch_split_g3(const float *M, int trans, const double *u, const fl
 cudaError_t launch_prep(const float *M, int trans, const double *u, int64_t n, int64_t ldp, float *out,
                         cudaStream_t s) {
     dim3 grid((unsigned)((n + 31) / 32)), block(32, 8);
-    operand_cols_kernel<false><<<grid, block, 0, s>>>(M, trans, u, n, ldp, 0, 1, nullptr, nullptr, out);
+    operand_cols_kernel<false, float><<<grid, block, 0, s>>>(M, trans, u, n, ldp, 0, 1, nullptr, nullptr, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gemm_bf16x3(const TcGemmArgs &g, int narrow, cudaStream_t s) {
-    return narrow ? launch_tc<3>(g, s) : launch_tc<0>(g, s);
+cudaError_t launch_gemm_bf16x3(const TcGemmArgs &g, int shape, cudaStream_t s) {
+    if (shape == 1) return launch_tc<3>(g, s);
+    if (shape == 2) return launch_tc<4>(g, s);
+    return launch_tc<0>(g, s);
 }
 cudaError_t launch_gemm_tf32(const TcGemmArgs &g, cudaStream_t s) { return launch_tc<1>(g, s); }
-cudaError_t launch_gemm_bf16x4(const TcGemmArgs &g, cudaStream_t s) { return launch_tc<2>(g, s); }
+cudaError_t launch_gemm_bf16x5(const TcGemmArgs &g, cudaStream_t s) {
+    if (!g.wide) return cudaErrorInvalidValue;
+    return launch_tc<6, true>(g, s);
+}
+cudaError_t launch_gemm_bf16x4(const TcGemmArgs &g, int shape, cudaStream_t s) {
+    if (g.wide) return shape == 2 ? launch_tc<5, true>(g, s) : launch_tc<2, true>(g, s);
+    return shape == 2 ? launch_tc<5>(g, s) : launch_tc<2>(g, s);
+}
 
 }  // namespace ustat

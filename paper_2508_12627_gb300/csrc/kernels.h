@@ -27,6 +27,10 @@ cudaError_t launch_unary_tanh(const void *X, int x_dtype, int64_t n, int d, cons
 cudaError_t launch_copyvec(const double *src, int64_t n, double *dst, cudaStream_t s);
 cudaError_t launch_diag(const void *M, bool fp64, int64_t n, double *out, cudaStream_t s);
 cudaError_t launch_vmul(const double *a, const double *b, int64_t n, double *out, cudaStream_t s);
+// out(i) = F(x_i, x_i) of factor kind `kind` from its own data in float64 (X for
+// LINEAR / RBF, the caller's matrix Mc for MATRIX); 0 when zero_diag.
+cudaError_t launch_factor_diag(int kind, double param, const void *X, int x_dtype, int d, const double *Mc,
+                               int64_t n, int zero_diag, double *out, cudaStream_t s);
 cudaError_t launch_vsum(const double *u, int64_t n, double *out, cudaStream_t s);
 // *out += sum_i u(i) a(i)
 cudaError_t launch_vdot(const double *u, const double *a, int64_t n, double *out, cudaStream_t s);
@@ -117,14 +121,14 @@ int split_lead_bits(int64_t K);
 // written K-major:
 //   split bf16: `planes` slices [planes][n][ldp] plus float row scales [n]  (launch_split)
 //   float32 tf32-rounded copy [n][ldp]                                        (launch_prep)
-cudaError_t launch_split(const float *M, int trans, const double *u, int64_t n, int64_t ldp,
+cudaError_t launch_split(const void *M, bool wide, int trans, const double *u, int64_t n, int64_t ldp,
                          int lead_bits, int planes, void *slices, float *scales, cudaStream_t s);
 cudaError_t launch_prep(const float *M, int trans, const double *u, int64_t n, int64_t ldp,
                         float *out, cudaStream_t s);
 // One fused reduction of the product C: *out += sum_jk C(j,k)^pow W(j,k) a(j) b(k)
 // (W, a, b may be null = all ones; W read with orientation transW).
 struct TcRed {
-    const float *W;
+    const void *W;                           // float, or double with `wide`
     int transW;
     const double *a, *b;
     int pow;
@@ -135,7 +139,7 @@ struct TcGemmArgs {
     const void *opA; const float *scaleA;   // K-major operand of A (slices or prep)
     const void *opB; const float *scaleB;
     int lead_bits;
-    float *C;                                // stored product (may be null)
+    void *C;                                 // stored product (may be null): float, double with `wide`
     int nred;                                // fused reductions (0..4)
     TcRed red[4];
     int symmetric;                           // C = C^T and every reduction symmetric
@@ -147,21 +151,28 @@ struct TcGemmArgs {
     // extra weights Wbc(bb, j) on rows, Wbd(bb, k) on columns and ub(bb)
     int batch, bb0;
     int split_tail;                          // set by the launcher: trailing tiles split in halves
-    const float *Wbc; int transWbc;
-    const float *Wbd; int transWbd;
+    const void *Wbc; int transWbc;
+    const void *Wbd; int transWbd;
     const double *ub;
+    // float64 storage (bf16x4 only): W, Wbc, Wbd and C are double, and the epilogue
+    // forms the entries and the reductions in float64
+    int wide;
 };
-// narrow: 128 x 64 tiles with a three-stage pipeline instead of 128 x 128 (no
-// symmetric tile skipping)
-cudaError_t launch_gemm_bf16x3(const TcGemmArgs &g, int narrow, cudaStream_t s);
-cudaError_t launch_gemm_bf16x4(const TcGemmArgs &g, cudaStream_t s);
+// shape: 0 = 128 x 128 tiles, 128-byte k-blocks, two stages; 1 = 128 x 64 tiles,
+// three stages (no symmetric tile skipping); 2 = 128 x 128 tiles, 64-byte
+// k-blocks, four stages (bf16x4: 0 = 128 x 64 tiles, two stages; 2 = 128 x 128
+// tiles, 64-byte k-blocks, three stages)
+cudaError_t launch_gemm_bf16x3(const TcGemmArgs &g, int shape, cudaStream_t s);
+cudaError_t launch_gemm_bf16x4(const TcGemmArgs &g, int shape, cudaStream_t s);
+// five slices, 128 x 128 tiles, 64-byte k-blocks; float64 storage only
+cudaError_t launch_gemm_bf16x5(const TcGemmArgs &g, cudaStream_t s);
 // Digit planes of the s = 3 step's A operands for bb = bb0 .. bb0 + nb - 1:
 // X_bb(j, i) = A(i, j) u(i) Ab(i, bb) with A(i, j) = trans ? M[j][i] : M[i][j] and
 // Ab(i, bb) = transAb ? Mb[bb][i] : Mb[i][bb]; slices [nb][planes][n][ldp],
 // scales [nb][n].
-cudaError_t launch_split_g3(const float *M, int trans, const double *u, const float *Mb, int transAb, int64_t bb0,
-                            int nb, int64_t n, int64_t ldp, int lead_bits, int planes, void *slices, float *scales,
-                            cudaStream_t s);
+cudaError_t launch_split_g3(const void *M, bool wide, int trans, const double *u, const void *Mb, int transAb,
+                            int64_t bb0, int nb, int64_t n, int64_t ldp, int lead_bits, int planes, void *slices,
+                            float *scales, cudaStream_t s);
 cudaError_t launch_gemm_tf32(const TcGemmArgs &g, cudaStream_t s);
 
 }  // namespace ustat

@@ -424,7 +424,7 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan, const P
     if (g->n_edges < 0 || g->n_unary < 0) return USTAT_ERR_INVALID_ARG;
     if (g->n_edges > 0 && (!g->edge_src || !g->edge_dst || !g->edge_factor)) return USTAT_ERR_INVALID_ARG;
     if (g->n_unary > 0 && (!g->unary_vertex || !g->unary_factor)) return USTAT_ERR_INVALID_ARG;
-    if (o->precision < USTAT_FP64 || o->precision > USTAT_BF16X4) return USTAT_ERR_INVALID_ARG;
+    if (o->precision < USTAT_FP64 || o->precision > USTAT_BF16X5) return USTAT_ERR_INVALID_ARG;
     if (o->planner != USTAT_PLAN_EXHAUSTIVE && o->planner != USTAT_PLAN_MINFILL) return USTAT_ERR_INVALID_ARG;
     Plan &P = *plan;
     P = Plan();
@@ -434,6 +434,12 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan, const P
     P.planner = o->planner;
     P.cse = o->cse ? 1 : 0;
     P.factor_kind.assign(g->factor_kind, g->factor_kind + g->n_factors);
+    // split modes: 128 x 128 tiles with 64-byte k-blocks and a deeper pipeline by
+    // default (measured on the n = 16384 products: 0.99 / 1.04 of the bf16x3 /
+    // bf16x4 ceilings against 0.92 / 0.67 with 128-byte k-blocks; equal on the
+    // symmetric 4096 product)
+    if (is_split_mode(P.precision))
+        for (int c = 0; c < 4; ++c) P.tc_variant[c] = 2 << 2;
     for (int f = 0; f < g->n_factors; ++f)
         if (P.factor_kind[f] < USTAT_RBF || P.factor_kind[f] > USTAT_VECTOR) return USTAT_ERR_INVALID_ARG;
     std::vector<int> covered(m, 0);
@@ -479,6 +485,7 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan, const P
         op.kind = OP_DIAG;
         op.t[0] = Term{base_of(f), 0};
         op.nt = 1;
+        op.factor = f;   // the diagonal is taken from the factor's own data, in float64
         diag[f] = L.emit(op);
         return diag[f];
     };
@@ -1075,7 +1082,7 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan, const P
         P.ops.swap(out);
         // an RBF kernel matrix has entries in (0, 1]: its unscaled split (row scale 1)
         // is written by the kernel-matrix build itself
-        if (split) {
+        if (split && !wide_storage(P.precision)) {
             std::vector<char> fused(P.ops.size(), 0);
             for (size_t i = 0; i < P.ops.size(); ++i) {
                 const Op &op = P.ops[i];
@@ -1142,7 +1149,7 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan, const P
     // ---- entrywise-power reductions of an RBF kernel matrix (full sums, and the
     //      row sums a GEMV with unit weights forms) are taken by the float32
     //      kernel-matrix build while the entries are in registers
-    if (P.precision != USTAT_FP64) {
+    if (!wide_storage(P.precision)) {
         std::vector<char> dead(P.ops.size(), 0);
         for (size_t i = 0; i < P.ops.size(); ++i) {
             const Op &r = P.ops[i];
@@ -1204,7 +1211,7 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan, const P
             }
             for (int s : outs(P.ops[i])) producer[s] = (int)i;
         }
-        const bool can_group = P.precision != USTAT_FP64;
+        const bool can_group = !wide_storage(P.precision);
         auto eligible = [&](const Op &o) {
             if (!can_group || (o.kind != OP_FREDUCE && o.kind != OP_GEMV)) return false;
             for (int t = 0; t < o.nt; ++t)

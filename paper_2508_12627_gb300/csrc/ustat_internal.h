@@ -109,18 +109,28 @@ struct Plan {
     std::vector<std::vector<Op>> groups;   // members of OP_MHB operations
     std::vector<PartRec> parts;
     int n_gemm = 0, n_gemm3 = 0;
-    // tensor-core GEMM variant per size class (tc_size_class): bit 2 = 128 x 64
-    // tiles (bf16x3), bits 0-1 = raster group index into kGroupRows; set by the
-    // batched autotuner, 0 = default
+    // tensor-core GEMM variant per size class (tc_size_class): bits 0-1 = raster
+    // group index into kGroupRows, bits 2-3 = tile shape (launch_gemm_bf16x3 /
+    // _bf16x4); set by the batched autotuner or ustat_plan_set_variant, 0 = default
     int tc_variant[4] = {0, 0, 0, 0};
 };
 
 constexpr int kGroupRows[4] = {8, 4, 16, 2};
 inline int tc_size_class(int64_t n) { return n <= 1024 ? 0 : (n <= 2048 ? 1 : (n <= 3072 ? 2 : 3)); }
 
-inline bool is_split_mode(int precision) { return precision == USTAT_BF16X3 || precision == USTAT_BF16X4; }
+inline bool is_split_mode(int precision) {
+    return precision == USTAT_BF16X3 || precision == USTAT_BF16X4 || precision == USTAT_BF16X5;
+}
 inline bool is_tc_mode(int precision) { return is_split_mode(precision) || precision == USTAT_TF32; }
-inline int split_planes_of(int precision) { return precision == USTAT_BF16X4 ? 4 : 3; }
+inline int split_planes_of(int precision) {
+    return precision == USTAT_BF16X5 ? 5 : (precision == USTAT_BF16X4 ? 4 : 3);
+}
+// matrices are stored in float64 in the FP64 mode and in the bf16x4 mode (whose
+// purpose is data of wide dynamic range: float32 storage would round the few
+// entries that dominate such sums), in float32 otherwise
+inline bool wide_storage(int precision) {
+    return precision == USTAT_FP64 || precision == USTAT_BF16X4 || precision == USTAT_BF16X5;
+}
 
 // Features of one candidate elimination sequence of one partition, for the
 // learned order ranker (see order_features in planner.cpp).

@@ -25,9 +25,9 @@ USTAT_ERR_DEVICE_TIMEOUT = -7
 USTAT_ERR_UNSUPPORTED = -8
 
 RBF, LINEAR, TANH_DOT, MATRIX, VECTOR = 0, 1, 2, 3, 4
-FP64, FP32, TF32, BF16X3, BF16X4 = 0, 1, 2, 3, 4
+FP64, FP32, TF32, BF16X3, BF16X4, BF16X5 = 0, 1, 2, 3, 4, 5
 PLAN_EXHAUSTIVE, PLAN_MINFILL = 0, 1
-PRECISION = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16x3": BF16X3, "bf16x4": BF16X4}
+PRECISION = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16x3": BF16X3, "bf16x4": BF16X4, "bf16x5": BF16X5}
 
 _P = ctypes.POINTER
 _i = ctypes.c_int
@@ -66,6 +66,7 @@ EXPORTS = {
     "ustat_eval_batch": (_i, [_vp, _P(_vp), _i, _P(_i64), _i, _i, _P(ustat_factor), _i, _vp, _sz, _vp,
                               _vp, _vp]),
     "ustat_batch_workspace_bytes": (_i, [_vp, _P(_i64), _i, _i, _P(_sz)]),
+    "ustat_plan_set_variant": (_i, [_vp, _i, _i]),
     "ustat_batched_create": (_i, [_vp, _P(_i64), _i, _i, _i, _P(_vp)]),
     "ustat_batched_destroy": (None, [_vp]),
     "ustat_batched_workspace_bytes": (_i, [_vp, _P(_sz)]),
@@ -196,6 +197,9 @@ class Plan:
         buf = ctypes.create_string_buffer(need.value)
         _check(lib().ustat_plan_describe(self.handle, buf, need.value, None), "ustat_plan_describe")
         return buf.value.decode()
+
+    def set_variant(self, variant, size_class=-1):
+        _check(lib().ustat_plan_set_variant(self.handle, int(size_class), int(variant)), "ustat_plan_set_variant")
 
     def workspace_bytes(self, n, d):
         s = _sz()

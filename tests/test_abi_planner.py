@@ -125,7 +125,7 @@ def test_workspace_bytes_scale(us):
     assert p.host_staging_bytes(1000, 32) >= 8 * 1000 * 32
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16x3", "bf16x4"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16x3", "bf16x4", "bf16x5"])
 def test_every_plan_is_well_formed(us, prec):
     # ustat_plan checks that every slot an operation reads is written by an earlier
     # operation and that every partition's scalars are produced; it returns an
