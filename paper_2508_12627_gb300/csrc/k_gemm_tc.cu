@@ -72,20 +72,23 @@ __device__ __forceinline__ int row_exp(double m) {
     return e;
 }
 
-// float64 source (the wide-storage mode): the same digits, computed in float64
-// (every step exact), of the value itself rather than of its float32 rounding
+// float64 source (the wide-storage mode), digits of the value itself rather than
+// of its float32 rounding.  y = x 2^(w - e) (|y| <= 2^w) is rounded once to a
+// multiple of 2^-8(planes - 1), as the integer q; its balanced base-256 digits
+// (each in [-128, 127], the leading one |d1| <= 2^w) are taken with integer
+// arithmetic, so that the only float64 operations are one scaling and one
+// conversion per entry.
 __device__ __forceinline__ void write_digits(double x, int lead_bits, int e, int planes, __nv_bfloat16 *dst,
                                              int64_t plane_stride) {
-    double y = ldexp(x, lead_bits - e);   // |y| <= 2^w, exact
-    double d = rint(y);
-    dst[0] = __double2bfloat16(d);
-    double scale = 1.0 / 256.0;
-    for (int p = 1; p < planes; ++p) {
-        y = (y - d) * 256.0;               // exact
-        d = rint(y);
-        dst[p * plane_stride] = __double2bfloat16(d * scale);
-        scale *= (1.0 / 256.0);
+    long long q = llrint(ldexp(x, lead_bits - e + 8 * (planes - 1)));   // the scaling is exact
+    float scale = __int_as_float((127 - 8 * (planes - 1)) << 23);       // 2^-8(planes - 1)
+    for (int p = planes - 1; p >= 1; --p) {
+        const int dp = (int)(((q + 128) & 255) - 128);
+        q = (q - dp) >> 8;                                               // exact
+        dst[p * plane_stride] = __float2bfloat16_rn((float)dp * scale);   // exact
+        scale *= 256.f;
     }
+    dst[0] = __float2bfloat16_rn((float)q);                              // |q| <= 2^w: exact
 }
 
 __device__ __forceinline__ void write_digits(float x, int lead_bits, int e, int planes, __nv_bfloat16 *dst,

@@ -434,12 +434,14 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan, const P
     P.planner = o->planner;
     P.cse = o->cse ? 1 : 0;
     P.factor_kind.assign(g->factor_kind, g->factor_kind + g->n_factors);
-    // split modes: 128 x 128 tiles with 64-byte k-blocks and a deeper pipeline by
-    // default (measured on the n = 16384 products: 0.99 / 1.04 of the bf16x3 /
-    // bf16x4 ceilings against 0.92 / 0.67 with 128-byte k-blocks; equal on the
-    // symmetric 4096 product)
+    // split modes above n = 1024: 128 x 128 tiles with 64-byte k-blocks and a
+    // deeper pipeline by default (measured on the n = 16384 products: 0.99 / 1.04
+    // of the bf16x3 / bf16x4 ceilings against 0.92 / 0.67 with 128-byte k-blocks;
+    // equal on the symmetric 4096 product); up to n = 1024 (short k loops, where
+    // 128-byte k-blocks measured 5 % faster on the batched s = 3 steps) 128-byte
+    // k-blocks, except bf16x5, which has only the 64-byte form
     if (is_split_mode(P.precision))
-        for (int c = 0; c < 4; ++c) P.tc_variant[c] = 2 << 2;
+        for (int c = 0; c < 4; ++c) P.tc_variant[c] = (c > 0 || P.precision == USTAT_BF16X5) ? 2 << 2 : 0;
     for (int f = 0; f < g->n_factors; ++f)
         if (P.factor_kind[f] < USTAT_RBF || P.factor_kind[f] > USTAT_VECTOR) return USTAT_ERR_INVALID_ARG;
     std::vector<int> covered(m, 0);
