@@ -41,6 +41,12 @@ WORKLOADS = {
 }
 
 
+# DRAM bytes (read + write) of one launch of the dominant kernel, from the ncu
+# capture summarised in profiles/ for the same workload, precision and kernel
+# version; a workload or kernel without a current capture reports null.
+TRAFFIC = {("c4_rbf", "bf16x3", None): 286.6e6}   # profiles/tc_gemm_bf16x3_c4_n4096.md
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -441,7 +447,8 @@ def main():
         achieved = alg_flops / per_launch_s / 1e12
         peak = bf16_peak / products
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "tc_gemm_kernel (%s)" % args.precision,
+                "traffic": TRAFFIC.get((args.workload, args.precision, args.variant)),
+                "kernel": "tc_gemm_kernel (%s)" % args.precision,
                 "peak_note": "%s bf16 dense %.1f TFLOP/s (%s) / %g tensor products per algorithmic "
                              "multiply-add" % (peak_src, bf16_peak, "burst", products),
                 "per_launch_ms": per_launch_s * 1e3}

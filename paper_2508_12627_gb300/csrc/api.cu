@@ -206,7 +206,8 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                     e = launch_kbuild_rbf((const float *)(C.ws + C.L.xw_off), n, C.d, f[op.factor].param, P.sparsify,
                                           (float *)C.ptr(op.out), op.opA >= 0 ? C.ptr(op.opA) : nullptr,
                                           C.L.ldp_slices, lead, split_planes_of(P.precision),
-                                          op.opA >= 0 ? C.scales(op.opA) : nullptr, op.nred, rpow, rvec, rout, C.st);
+                                          op.opA >= 0 ? C.scales(op.opA) : nullptr, op.nred, rpow, rvec, rout,
+                                          op.upper_only, C.st);
                 } else {
                     if (op.nred) return USTAT_ERR_UNSUPPORTED;   // the planner fuses only into the RBF build
                     e = launch_kbuild(f[op.factor].kind, f[op.factor].param, C.ws + C.L.xw_off, C.fp64, n, C.d,
@@ -649,8 +650,8 @@ extern "C" int ustat_plan_describe(const ustat_plan_t *plan, char *buf, size_t b
             for (int r = 0; r < o.nred; ++r)
                 ks += (r ? ";" : "") + std::string(P.slots[o.red[r].out].kind == S_VEC ? "v" : "s") +
                       std::to_string(o.red[r].out) + "+=K^" + std::to_string(o.red[r].pow);
-            snprintf(line, sizeof(line), "%zu kbuild out=%d f=%d slices=%d red=[%s]\n", i, o.out, o.factor, o.opA,
-                     ks.c_str());
+            snprintf(line, sizeof(line), "%zu kbuild out=%d f=%d slices=%d upper=%d red=[%s]\n", i, o.out, o.factor,
+                     o.opA, o.upper_only, ks.c_str());
         }
         else
             snprintf(line, sizeof(line),

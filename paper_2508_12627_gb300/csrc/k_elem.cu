@@ -165,6 +165,7 @@ struct RbfArgs {
     float *scales;
     int nred;
     RbfRed red[kRbfMaxRed];
+    int upper_only;   // K itself is read only on and above the diagonal: no mirror stores of K
 };
 
 // two float32 in one 64-bit register pair (first = low half)
@@ -255,10 +256,10 @@ __device__ __forceinline__ int rbf_row(int a, int ty) { return 4 * ty + (a & 3) 
 // instruction cache.
 __device__ __noinline__ void rbf_store_row(float *K, __nv_bfloat16 *slices, int64_t n, int64_t ldp, int planes,
                                            float lead_scale, int64_t gr, int64_t gc, F2Row v) {
-    float *krow = K + gr * n;
+    float *krow = K ? K + gr * n : nullptr;
     const bool vec4 = (n % 4) == 0;
 #pragma unroll
-    for (int hh = 0; hh < 2; ++hh) {
+    for (int hh = 0; hh < 2 && krow; ++hh) {
         const int64_t c = gc + 64 * hh;
         float e[4];
         f2_unpack(v.v[2 * hh], e[0], e[1]);
@@ -525,7 +526,7 @@ __global__ void __launch_bounds__(256, 2) kbuild_rbf_tile_kernel(RbfArgs g) {
                 F2Row v;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) v.v[q] = f2_pack(cv[2 * q], cv[2 * q + 1]);
-                rbf_store_row(K, slices, n, ldp, planes, lead_scale, gr, i0 + 4 * ty, v);
+                rbf_store_row(g.upper_only ? nullptr : K, slices, n, ldp, planes, lead_scale, gr, i0 + 4 * ty, v);
             }
         }
     }
@@ -788,10 +789,11 @@ cudaError_t launch_kbuild(int kind, double param, const void *Xw, bool fp64, int
 
 cudaError_t launch_kbuild_rbf(const float *Xw, int64_t n, int d, double param, int zero_diag, float *K,
                               void *slices, int64_t ldp, int lead_bits, int planes, float *scales, int nred,
-                              const int *red_pow, const int *red_vec, double *const *red_out, cudaStream_t s) {
-    if (nred < 0 || nred > kRbfMaxRed || planes < 3 || planes > 4) return cudaErrorInvalidValue;
+                              const int *red_pow, const int *red_vec, double *const *red_out, int upper_only,
+                              cudaStream_t s) {
+    if (nred < 0 || nred > kRbfMaxRed || planes < 3 || planes > 5) return cudaErrorInvalidValue;
     RbfArgs g{Xw, n, d, (float)(1.0 / param), zero_diag, K, (__nv_bfloat16 *)slices, slices ? ldp : n, lead_bits,
-              planes, slices ? scales : nullptr, nred, {}};
+              planes, slices ? scales : nullptr, nred, {}, upper_only};
     for (int q = 0; q < nred; ++q) {
         if (red_pow[q] < 1 || red_pow[q] > 4) return cudaErrorInvalidValue;
         g.red[q] = RbfRed{red_pow[q], red_vec[q], red_out[q]};

@@ -1181,6 +1181,39 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan, const P
         P.ops.swap(kept);
     }
 
+    // an RBF kernel matrix whose only readers are symmetric tensor-core GEMMs (which
+    // read it as the weight of their upper-triangle tiles; their operands are the
+    // digit planes the build writes) needs no stores below the diagonal
+    if (is_split_mode(P.precision) && !wide_storage(P.precision)) {
+        for (auto &kb : P.ops) {
+            if (kb.kind != OP_KBUILD || kb.opA < 0 || P.factor_kind[kb.factor] != USTAT_RBF) continue;
+            const int s = kb.out;
+            bool ok = true;
+            for (const Op &o : P.ops) {
+                if (&o == &kb) continue;
+                bool reads = false, as_weight = false;
+                for (int t = 0; t < o.nt; ++t) reads |= o.t[t].mat == s;
+                const Term *ts[] = {&o.W, &o.Ab, &o.Wbc, &o.Wbd};
+                for (auto *t : ts) reads |= t->mat == s;
+                for (int r = 0; r < o.nred; ++r) as_weight |= o.red[r].W.mat == s;
+                const bool operand = o.A.mat == s || o.B.mat == s;
+                if (o.kind == OP_GEMM) {
+                    // a GEMM reads its weights through red[] (o.W is the pre-fusion copy)
+                    if ((as_weight || operand) && !o.symmetric) ok = false;
+                } else if (reads || operand || as_weight || o.kind == OP_MHB || o.kind == OP_SPLIT ||
+                           o.kind == OP_PREP) {
+                    if (o.kind == OP_MHB) {
+                        for (const Op &m : P.groups[o.group])
+                            for (int t = 0; t < m.nt; ++t)
+                                if (m.t[t].mat == s) ok = false;
+                    } else if (reads || operand || as_weight || (o.nt > 0 && o.t[0].mat == s)) {
+                        ok = false;
+                    }
+                }
+            }
+            kb.upper_only = ok ? 1 : 0;
+        }
+    }
     // ---- schedule by dependency level and merge the n^2 reductions / GEMVs of
     //      one level that read the same few matrices into single passes
     {

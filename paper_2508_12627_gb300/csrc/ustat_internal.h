@@ -75,6 +75,7 @@ struct Op {
     int npow = 0;                 // flops = coef * n^npow
     double coef = 0.0;
     int group = -1;               // OP_MHB: index into Plan::groups
+    int upper_only = 0;           // KBUILD: its matrix is read only on and above the diagonal
 };
 
 enum SlotKind : int { S_MAT = 0, S_VEC, S_SCAL, S_SLICES, S_PREP };

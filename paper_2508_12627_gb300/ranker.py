@@ -7,7 +7,7 @@ planner's own candidate orders, training with the library's MLP kernels
 Each instance is a random connected kernel graph G(m, p) (m in 3..7, p in
 [0.3, 0.8], up to two unary factors) at a sample size n.  For the graph's own
 contraction (every vertex a distinct index) the instance measures the
-evaluation time of a few of its distinct elimination sequences
+evaluation time (CUDA events, median of two after a warm-up) of a few of its distinct elimination sequences
 (ustat_order_candidates) and of the plans the exhaustive and min-fill planners
 pick.  The network learns log(time) from a sequence's features; the planner
 then picks per partition the candidate of least predicted time
@@ -78,7 +78,7 @@ class Timer:
         us.ustat_eval(plan, X.data_ptr(), 0, n, self.d, self.factors(), self.ws.data_ptr(), self.ws.numel(),
                       self.stream.cuda_stream, self.out.data_ptr(), self.out.data_ptr() + 16)
 
-    def time(self, plan, n, reps=3):
+    def time(self, plan, n, reps=2):
         torch = self.torch
         self.run(plan, n)
         ts = []
