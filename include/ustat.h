@@ -221,13 +221,14 @@ int ustat_batch_workspace_bytes(const ustat_plan_t *plan, const int64_t *n, int 
  * created on the device current at the first run.
  */
 /*
- * Tensor-core GEMM variant of a plan for one size class (0: n <= 1024, 1: <= 2048,
- * 2: <= 3072, 3: larger; -1: all): bits 0-1 pick the tile raster group (8, 4, 16
- * or 2 tile rows), bits 2-3 the tile shape (0: 128 x 128 with 128-byte k-blocks;
- * 1: 128 x 64, bf16x3 only; 2: 128 x 128 with 64-byte k-blocks and a deeper
- * pipeline).  Results agree to the mode's tolerance across variants (the
- * summation order inside the accumulators differs).  The autotuner below sets
- * these itself.
+ * Kernel variant of a plan for one size class (0: n <= 1024, 1: <= 2048, 2: <= 3072,
+ * 3: larger; -1: all): bits 0-1 pick the tensor-core GEMM's tile raster group (8,
+ * 4, 16 or 2 tile rows), bits 2-3 its tile shape (0: 128 x 128 with 128-byte
+ * k-blocks; 1: 128 x 64, bf16x3 only; 2: 128 x 128 with 64-byte k-blocks and a
+ * deeper pipeline), bit 4 the RBF kernel-matrix build's tile (0: 128 x 128 with
+ * 256 threads; 1: 64 x 64 with 128 threads).  Results agree to the mode's
+ * tolerance across variants (summation orders differ).  The autotuner below
+ * sets these itself.
  */
 int ustat_plan_set_variant(ustat_plan_t *plan, int size_class, int variant);
 

@@ -207,7 +207,7 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                                           (float *)C.ptr(op.out), op.opA >= 0 ? C.ptr(op.opA) : nullptr,
                                           C.L.ldp_slices, lead, split_planes_of(P.precision),
                                           op.opA >= 0 ? C.scales(op.opA) : nullptr, op.nred, rpow, rvec, rout,
-                                          op.upper_only, C.st);
+                                          op.upper_only, (P.tc_variant[tc_size_class(n)] >> 4) & 1, C.st);
                 } else {
                     if (op.nred) return USTAT_ERR_UNSUPPORTED;   // the planner fuses only into the RBF build
                     e = launch_kbuild(f[op.factor].kind, f[op.factor].param, C.ws + C.L.xw_off, C.fp64, n, C.d,
@@ -835,7 +835,7 @@ int batched_check(ustat_batched *b, const void *const *X, int x_dtype, const ust
 extern "C" {
 
 int ustat_plan_set_variant(ustat_plan_t *plan, int size_class, int variant) {
-    if (!plan || size_class < -1 || size_class > 3 || variant < 0 || variant > 15 || ((variant >> 2) & 3) == 3)
+    if (!plan || size_class < -1 || size_class > 3 || variant < 0 || variant > 31 || ((variant >> 2) & 3) == 3)
         return USTAT_ERR_INVALID_ARG;
     for (int c = 0; c < 4; ++c)
         if (size_class < 0 || c == size_class) plan->p.tc_variant[c] = variant;
@@ -992,12 +992,16 @@ int ustat_batched_autotune(ustat_batched_t *b, const void *const *X, int x_dtype
         for (int64_t v : b->n) present[tc_size_class(v)] = true;
         // raster groups x tile shapes (bf16x3: 3 shapes; bf16x4: 2; tf32: 1)
         std::vector<int> vars;
-        for (int shape = 0; shape < 3; ++shape) {
-            if (P.precision == USTAT_BF16X4 && shape == 1) continue;
-            if (P.precision == USTAT_BF16X5 && shape != 2) continue;
-            if (P.precision == USTAT_TF32 && shape > 0) continue;
-            for (int gr = 0; gr < 4; ++gr) vars.push_back(gr | (shape << 2));
-        }
+        bool rbf_build = false;
+        for (auto &op : P.ops)
+            rbf_build |= op.kind == OP_KBUILD && P.factor_kind[op.factor] == USTAT_RBF && !wide_storage(P.precision);
+        for (int kb = 0; kb < (rbf_build ? 2 : 1); ++kb)
+            for (int shape = 0; shape < 3; ++shape) {
+                if (P.precision == USTAT_BF16X4 && shape == 1) continue;
+                if (P.precision == USTAT_BF16X5 && shape != 2) continue;
+                if (P.precision == USTAT_TF32 && shape > 0) continue;
+                for (int gr = 0; gr < 4; ++gr) vars.push_back(gr | (shape << 2) | (kb << 4));
+            }
         for (int c = 0; c < 4 && rc == USTAT_OK; ++c) {
             if (!present[c]) continue;
             int best_v = P.tc_variant[c];

@@ -254,13 +254,17 @@ __device__ __forceinline__ int rbf_row(int a, int ty) { return 4 * ty + (a & 3) 
 // |y_p| < 2^(22 - 8p)); the remainder y_{p+1} = y_p - digit is exact.  Out of
 // line: the kernel calls it 16 times, and inlined copies outgrew the
 // instruction cache.
+// (half: the column offset of the second quadruple, 64 for 128-wide tiles and 32
+// for 64-wide ones; nhalf = 1 stores the first quadruple only)
 __device__ __noinline__ void rbf_store_row(float *K, __nv_bfloat16 *slices, int64_t n, int64_t ldp, int planes,
-                                           float lead_scale, int64_t gr, int64_t gc, F2Row v) {
+                                           float lead_scale, int64_t gr, int64_t gc, F2Row v, int half = 64,
+                                           int nhalf = 2) {
     float *krow = K ? K + gr * n : nullptr;
     const bool vec4 = (n % 4) == 0;
 #pragma unroll
     for (int hh = 0; hh < 2 && krow; ++hh) {
-        const int64_t c = gc + 64 * hh;
+        if (hh >= nhalf) break;
+        const int64_t c = gc + half * hh;
         float e[4];
         f2_unpack(v.v[2 * hh], e[0], e[1]);
         f2_unpack(v.v[2 * hh + 1], e[2], e[3]);
@@ -295,14 +299,15 @@ __device__ __noinline__ void rbf_store_row(float *K, __nv_bfloat16 *slices, int6
         __nv_bfloat16 *dst = srow + p * plane;
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
-            const int64_t c = gc + 64 * hh;
+            if (hh >= nhalf) break;
+            const int64_t c = gc + half * hh;
             if (c + 3 < ldp) {
-                *reinterpret_cast<uint2 *>(dst + 64 * hh) = make_uint2(w[2 * hh], w[2 * hh + 1]);
+                *reinterpret_cast<uint2 *>(dst + half * hh) = make_uint2(w[2 * hh], w[2 * hh + 1]);
             } else {
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
                     if (c + q < ldp)
-                        dst[64 * hh + q] = __ushort_as_bfloat16((uint16_t)(w[2 * hh + (q >> 1)] >> (16 * (q & 1))));
+                        dst[half * hh + q] = __ushort_as_bfloat16((uint16_t)(w[2 * hh + (q >> 1)] >> (16 * (q & 1))));
             }
         }
         magic *= (1.0f / 256.0f);
@@ -531,6 +536,226 @@ __global__ void __launch_bounds__(256, 2) kbuild_rbf_tile_kernel(RbfArgs g) {
         }
     }
     if (g.scales && diag_tile && tid < kRbfT && i0 + tid < n) g.scales[i0 + tid] = 1.f;
+}
+
+
+// The same build on 64 x 64 tiles with 128 threads (4 x 8 entries per thread):
+// half the registers per thread, so four times as many warps per SM fit, for
+// the latency of the epilogue's dependent chains.  Thread (ty, tx), ty < 16,
+// tx < 8, owns rows 4 ty + i and columns {4 tx + j, 32 + 4 tx + j}.
+constexpr int kRbfT64 = 64;
+__global__ void __launch_bounds__(128, 8) kbuild_rbf_tile64_kernel(RbfArgs g) {
+    __shared__ __align__(16) float2 xa[32][kRbfT64];
+    __shared__ __align__(16) float xb[32][kRbfT64];
+    __shared__ double dred[4];
+    const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3, lane = tid & 31, warp = tid >> 5;
+    const int64_t n = g.n;
+    const int T = (int)((g.ldp + kRbfT64 - 1) / kRbfT64);
+    const int t = blockIdx.x;
+    const double bq = 2.0 * T + 1.0;
+    int tm = (int)((bq - sqrt(bq * bq - 8.0 * t)) * 0.5);
+    if (tm < 0) tm = 0;
+    while (tm > 0 && tm * T - tm * (tm - 1) / 2 > t) --tm;
+    while (tm + 1 < T && (tm + 1) * T - (tm + 1) * tm / 2 <= t) ++tm;
+    const int tn = tm + (t - (tm * T - tm * (tm - 1) / 2));
+    const int64_t i0 = (int64_t)tm * kRbfT64, j0 = (int64_t)tn * kRbfT64;
+    const bool diag_tile = tm == tn;
+
+    f32x2 acc[4][4];   // [row i][column pair h]: columns (2h, 2h + 1) of {4 tx .., 32 + 4 tx ..}
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int h = 0; h < 4; ++h) acc[a][h] = f2_splat(0.f);
+    const bool xvec = (g.d % 4) == 0;
+    for (int k0 = 0; k0 < g.d; k0 += 32) {
+        __syncthreads();
+        for (int e = tid; e < 2 * kRbfT64 * 8; e += 128) {
+            const int opnd = e >> 9, row = e & (kRbfT64 - 1), kq = (e >> 6) & 7;
+            const int64_t gr = (opnd ? j0 : i0) + row;
+            const int k = k0 + 4 * kq;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (gr < n && k < g.d) {
+                const float *src = g.X + gr * g.d + k;
+                if (xvec) {
+                    v = *reinterpret_cast<const float4 *>(src);
+                } else {
+                    v.x = src[0];
+                    if (k + 1 < g.d) v.y = src[1];
+                    if (k + 2 < g.d) v.z = src[2];
+                    if (k + 3 < g.d) v.w = src[3];
+                }
+            }
+            if (opnd == 0) {
+                xa[4 * kq + 0][row] = make_float2(v.x, v.x);
+                xa[4 * kq + 1][row] = make_float2(v.y, v.y);
+                xa[4 * kq + 2][row] = make_float2(v.z, v.z);
+                xa[4 * kq + 3][row] = make_float2(v.w, v.w);
+            } else {
+                xb[4 * kq + 0][row] = v.x;
+                xb[4 * kq + 1][row] = v.y;
+                xb[4 * kq + 2][row] = v.z;
+                xb[4 * kq + 3][row] = v.w;
+            }
+        }
+        __syncthreads();
+        const int kmax = min(32, g.d - k0);
+        for (int kk = 0; kk < kmax; ++kk) {
+            const ulonglong2 a01 = *reinterpret_cast<const ulonglong2 *>(&xa[kk][4 * ty]);
+            const ulonglong2 a23 = *reinterpret_cast<const ulonglong2 *>(&xa[kk][4 * ty + 2]);
+            const f32x2 av[4] = {a01.x, a01.y, a23.x, a23.y};
+            const ulonglong2 b0 = *reinterpret_cast<const ulonglong2 *>(&xb[kk][4 * tx]);
+            const ulonglong2 b1 = *reinterpret_cast<const ulonglong2 *>(&xb[kk][32 + 4 * tx]);
+            const f32x2 bv[4] = {b0.x, b0.y, b1.x, b1.y};
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const f32x2 df = f2_sub(av[a], bv[h]);
+                    acc[a][h] = f2_fma(df, df, acc[a][h]);
+                }
+        }
+    }
+    auto colof = [&](int c) { return 4 * tx + (c & 3) + 32 * (c >> 2); };   // c < 8
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        F2Row d2;
+#pragma unroll
+        for (int h = 0; h < 4; ++h) d2.v[h] = acc[a][h];
+        const F2Row e = f2_rbf_row(d2, g.inv_h);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) acc[a][h] = e.v[h];
+    }
+    if (diag_tile || i0 + kRbfT64 > n || j0 + kRbfT64 > n) {
+        const float dv = g.zero_diag ? 0.f : 1.f;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int64_t gi = i0 + 4 * ty + a;
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                float e0, e1;
+                f2_unpack(acc[a][h], e0, e1);
+                const int64_t gj0 = j0 + colof(2 * h), gj1 = j0 + colof(2 * h + 1);
+                if (gi == gj0) e0 = dv;
+                if (gi == gj1) e1 = dv;
+                if (gi >= n || gj0 >= n) e0 = 0.f;
+                if (gi >= n || gj1 >= n) e1 = 0.f;
+                acc[a][h] = f2_pack(e0, e1);
+            }
+        }
+    }
+
+    if (g.nred > 0) {
+        __syncthreads();
+        float *colpart = reinterpret_cast<float *>(&xa[0][0]);   // [4 warps][64]
+        for (int q = 0; q < g.nred; ++q) {
+            const int p = g.red[q].pow;
+            double *out = g.red[q].out;
+            f32x2 cq[4];
+            float rp[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) cq[h] = f2_splat(0.f);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                f32x2 w[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) w[h] = acc[a][h];
+                for (int e = 1; e < p; ++e) {
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) w[h] = f2_mul(w[h], acc[a][h]);
+                }
+                float r0, r1;
+                f2_unpack(f2_add(f2_add(w[0], w[1]), f2_add(w[2], w[3])), r0, r1);
+                rp[a] = r0 + r1;
+#pragma unroll
+                for (int h = 0; h < 4; ++h) cq[h] = f2_add(cq[h], w[h]);
+            }
+            if (g.red[q].vec) {
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+#pragma unroll
+                    for (int o = 4; o > 0; o >>= 1) rp[a] += __shfl_xor_sync(0xffffffffu, rp[a], o);
+                }
+                if (tx == 0) {
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const int64_t gi = i0 + 4 * ty + a;
+                        if (gi < n) atomicAdd(out + gi, (double)rp[a]);
+                    }
+                }
+                if (!diag_tile) {
+                    float cv[8];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) f2_unpack(cq[h], cv[2 * h], cv[2 * h + 1]);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        cv[c] += __shfl_xor_sync(0xffffffffu, cv[c], 8);
+                        cv[c] += __shfl_xor_sync(0xffffffffu, cv[c], 16);
+                    }
+                    if (lane < 8) {
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) colpart[warp * kRbfT64 + colof(c)] = cv[c];
+                    }
+                    __syncthreads();
+                    if (tid < kRbfT64 && j0 + tid < n) {
+                        const float sum = (colpart[tid] + colpart[kRbfT64 + tid]) +
+                                          (colpart[2 * kRbfT64 + tid] + colpart[3 * kRbfT64 + tid]);
+                        atomicAdd(out + j0 + tid, (double)sum);
+                    }
+                    __syncthreads();
+                }
+            } else {
+                double sd = (double)((rp[0] + rp[1]) + (rp[2] + rp[3]));
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
+                if (lane == 0) dred[warp] = sd;
+                __syncthreads();
+                if (tid == 0) {
+                    const double tsum = (dred[0] + dred[1]) + (dred[2] + dred[3]);
+                    atomicAdd(out, diag_tile ? tsum : 2.0 * tsum);
+                }
+                __syncthreads();
+            }
+        }
+    }
+
+    const float lead_scale = __int_as_float((127 + g.lead_bits) << 23);   // 2^w
+    float *K = g.K;
+    __nv_bfloat16 *slices = g.slices;
+    const int64_t ldp = g.ldp;
+    const int planes = g.planes;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int64_t gr = i0 + 4 * ty + a;
+        if (gr >= n) continue;
+        F2Row v;
+#pragma unroll
+        for (int h = 0; h < 4; ++h) v.v[h] = acc[a][h];
+        rbf_store_row(K, slices, n, ldp, planes, lead_scale, gr, j0 + 4 * tx, v, 32, 2);
+    }
+    // K below the diagonal is skipped only where no reader needs it: the readers
+    // of an upper-only K are symmetric GEMMs with 128-row tiles, whose diagonal
+    // tiles also read the lower 64 x 64 tile of each diagonal 128 x 128 block
+    const bool mirror_k = !g.upper_only || (tn == tm + 1 && (tm & 1) == 0);
+    if (!diag_tile) {
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            float c0[4], c1[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) f2_unpack(acc[a][h], c0[a], c1[a]);
+#pragma unroll
+            for (int sdx = 0; sdx < 2; ++sdx) {
+                const float *cv = sdx ? c1 : c0;
+                const int64_t gr = j0 + colof(2 * h + sdx);
+                if (gr >= n) continue;
+                F2Row v;
+                v.v[0] = f2_pack(cv[0], cv[1]);
+                v.v[1] = f2_pack(cv[2], cv[3]);
+                v.v[2] = v.v[3] = f2_splat(0.f);
+                rbf_store_row(mirror_k ? K : nullptr, slices, n, ldp, planes, lead_scale, gr, i0 + 4 * ty, v, 32, 1);
+            }
+        }
+    }
+    if (g.scales && diag_tile && tid < kRbfT64 && i0 + tid < n) g.scales[i0 + tid] = 1.f;
 }
 
 // Float64 version (FP64 mode).
@@ -790,7 +1015,7 @@ cudaError_t launch_kbuild(int kind, double param, const void *Xw, bool fp64, int
 cudaError_t launch_kbuild_rbf(const float *Xw, int64_t n, int d, double param, int zero_diag, float *K,
                               void *slices, int64_t ldp, int lead_bits, int planes, float *scales, int nred,
                               const int *red_pow, const int *red_vec, double *const *red_out, int upper_only,
-                              cudaStream_t s) {
+                              int tile64, cudaStream_t s) {
     if (nred < 0 || nred > kRbfMaxRed || planes < 3 || planes > 5) return cudaErrorInvalidValue;
     RbfArgs g{Xw, n, d, (float)(1.0 / param), zero_diag, K, (__nv_bfloat16 *)slices, slices ? ldp : n, lead_bits,
               planes, slices ? scales : nullptr, nred, {}, upper_only};
@@ -798,8 +1023,13 @@ cudaError_t launch_kbuild_rbf(const float *Xw, int64_t n, int d, double param, i
         if (red_pow[q] < 1 || red_pow[q] > 4) return cudaErrorInvalidValue;
         g.red[q] = RbfRed{red_pow[q], red_vec[q], red_out[q]};
     }
-    const int64_t T = (g.ldp + kRbfT - 1) / kRbfT;
-    kbuild_rbf_tile_kernel<<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(g);
+    if (tile64) {
+        const int64_t T = (g.ldp + kRbfT64 - 1) / kRbfT64;
+        kbuild_rbf_tile64_kernel<<<(unsigned)(T * (T + 1) / 2), 128, 0, s>>>(g);
+    } else {
+        const int64_t T = (g.ldp + kRbfT - 1) / kRbfT;
+        kbuild_rbf_tile_kernel<<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(g);
+    }
     return cudaGetLastError();
 }
 

@@ -20,7 +20,7 @@ cudaError_t launch_kbuild(int kind, double param, const void *Xw, bool fp64, int
 cudaError_t launch_kbuild_rbf(const float *Xw, int64_t n, int d, double param, int zero_diag, float *K,
                               void *slices, int64_t ldp, int lead_bits, int planes, float *scales, int nred,
                               const int *red_pow, const int *red_vec, double *const *red_out, int upper_only,
-                              cudaStream_t s);
+                              int tile64, cudaStream_t s);
 cudaError_t launch_loadmat(const double *src, int64_t n, bool fp64, int zero_diag, void *dst,
                            cudaStream_t s);
 cudaError_t launch_unary_tanh(const void *X, int x_dtype, int64_t n, int d, const double *w,

@@ -110,9 +110,10 @@ struct Plan {
     std::vector<std::vector<Op>> groups;   // members of OP_MHB operations
     std::vector<PartRec> parts;
     int n_gemm = 0, n_gemm3 = 0;
-    // tensor-core GEMM variant per size class (tc_size_class): bits 0-1 = raster
-    // group index into kGroupRows, bits 2-3 = tile shape (launch_gemm_bf16x3 /
-    // _bf16x4); set by the batched autotuner or ustat_plan_set_variant, 0 = default
+    // kernel variant per size class (tc_size_class): bits 0-1 = raster group index
+    // into kGroupRows, bits 2-3 = GEMM tile shape (launch_gemm_bf16x3 / _bf16x4),
+    // bit 4 = 64 x 64 tiles in the RBF kernel-matrix build; set by the batched
+    // autotuner or ustat_plan_set_variant
     int tc_variant[4] = {0, 0, 0, 0};
 };
 

@@ -104,11 +104,13 @@ def test_heavy_tailed_matrix_factor(eng_mod, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
-@pytest.mark.parametrize("n", [4, 5, 64, 127, 128, 129, 256, 385])
+@pytest.mark.parametrize("n", [4, 5, 64, 127, 128, 129, 256, 385, 1100, 2049])
 def test_c4_sizes_and_ragged_tails(eng_mod, n, prec):
     w = synth.workload("c4_rbf", n=n)
     ref, absref = _oracle(w)
-    out = eng_mod.Engine(w.graph, w.factors, precision=prec).evaluate(w.X)
+    eng = eng_mod.Engine(w.graph, w.factors, precision=prec)
+    eng.workspace(eng.plan.workspace_bytes(n, w.X.shape[1])).fill_(255)   # NaN bytes: no stale reads
+    out = eng.evaluate(w.X)
     _compare(out, ref, absref, tol_for("c4_rbf", prec, n), "c4 n=%d %s" % (n, prec))
 
 
@@ -190,7 +192,9 @@ def test_c4_full_size_against_oracle(eng_mod):
     # benchmark times: all 15 V_pi and U against the FP64 oracle
     w = synth.workload("c4_rbf")
     ref, absref = _oracle(w)
-    out = eng_mod.Engine(w.graph, w.factors, precision="bf16x3").evaluate(w.X)
+    eng = eng_mod.Engine(w.graph, w.factors, precision="bf16x3")
+    eng.workspace(eng.plan.workspace_bytes(w.n, w.d)).fill_(255)   # NaN bytes: no stale reads
+    out = eng.evaluate(w.X)
     _compare(out, ref, absref, 1e-8, "c4 full bf16x3")
 
 
@@ -254,3 +258,21 @@ def test_gemm_tile_variants(eng_mod, name, n, prec, shape):
         eng.plan.set_variant(gr | (shape << 2))
         out = eng.evaluate(w.X)
         _compare(out, ref, absref, tol_for(name, prec, n), (name, prec, shape, gr))
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
+@pytest.mark.parametrize("name,n", [("c4_rbf", 5), ("c4_rbf", 63), ("c4_rbf", 65), ("c4_rbf", 129), ("c4_rbf", 300),
+                                    ("triangle_rbf", 200), ("k4_cycle_rbf", 72)])
+def test_rbf_build_tile_variants(eng_mod, name, n, prec):
+    # the 64 x 64-tile form of the RBF kernel-matrix build (bit 4 of the plan
+    # variant): tiles, mirror, digit planes and fused reductions against the oracle
+    w = synth.workload(name, n)
+    ref, absref = _oracle(w)
+    for variant in (16, 0):
+        eng = eng_mod.Engine(w.graph, w.factors, precision=prec)
+        eng.plan.set_variant(variant)
+        # every workspace byte 0xff (a NaN in float32 and float64): a read of
+        # anything the evaluation did not write shows up in the result
+        eng.workspace(eng.plan.workspace_bytes(n, w.X.shape[1])).fill_(255)
+        out = eng.evaluate(w.X)
+        _compare(out, ref, absref, tol_for(name, prec, n), (name, n, prec, variant))
