@@ -210,8 +210,12 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                                           op.upper_only, (P.tc_variant[tc_size_class(n)] >> 4) & 1, C.st);
                 } else {
                     if (op.nred) return USTAT_ERR_UNSUPPORTED;   // the planner fuses only into the RBF build
-                    e = launch_kbuild(f[op.factor].kind, f[op.factor].param, C.ws + C.L.xw_off, C.fp64, n, C.d,
-                                      P.sparsify, C.ptr(op.out), C.st);
+                    if (C.fp64 && f[op.factor].kind == USTAT_LINEAR && x_dtype == 1)
+                        e = launch_kbuild_linear_wide((const float *)X, n, C.d, f[op.factor].param, P.sparsify,
+                                                      (double *)C.ptr(op.out), C.st);
+                    else
+                        e = launch_kbuild(f[op.factor].kind, f[op.factor].param, C.ws + C.L.xw_off, C.fp64, n, C.d,
+                                          P.sparsify, C.ptr(op.out), C.st);
                 }
                 break;
             case OP_LOADMAT:

@@ -57,8 +57,13 @@ __device__ __forceinline__ float exp_unbiased(float z) {
 // summed in float32 (its rounding errors are symmetric), the exponential is
 // exp_unbiased, and the linear kernel's dot product is accumulated as a
 // double-float (TwoProd by FMA, TwoSum) and rounded once.
+// With a float64 K (TO = double, the float64-storage modes, linear kernel of a
+// float32 X): the double-float dot product, exact products and a compensated
+// sum, goes to float64 unrounded and is divided in float64.
+template <typename TO>
 __global__ void __launch_bounds__(256) kbuild_f32_kernel(int kind, float inv_param, const float *__restrict__ X,
-                                                         int64_t n, int d, int zero_diag, float *__restrict__ K) {
+                                                         int64_t n, int d, int zero_diag, TO *__restrict__ K,
+                                                         double inv_param_d = 0.0) {
     __shared__ float xi[64][33];
     __shared__ float xj[64][33];
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -117,14 +122,16 @@ __global__ void __launch_bounds__(256) kbuild_f32_kernel(int kind, float inv_par
         for (int c = 0; c < 4; ++c) {
             int64_t gj = j0 + tx + 16 * c;
             if (gj >= n) continue;
-            float v;
-            if (kind == USTAT_RBF) {
+            TO v;
+            if constexpr (sizeof(TO) == 8) {
+                v = ((double)acc[r][c] + (double)lo[r][c]) * inv_param_d;
+            } else if (kind == USTAT_RBF) {
                 v = (gi == gj) ? 1.0f : exp_unbiased(-acc[r][c] * inv_param);
             } else {
                 const float s = acc[r][c] + lo[r][c];
                 v = s * inv_param;
             }
-            if (zero_diag && gi == gj) v = 0.f;
+            if (zero_diag && gi == gj) v = TO(0);
             K[gi * n + gj] = v;
         }
     }
@@ -1007,8 +1014,15 @@ cudaError_t launch_kbuild(int kind, double param, const void *Xw, bool fp64, int
         kbuild_kernel<double><<<grid, block, 0, s>>>(kind, 1.0 / param, (const double *)Xw, n, d, zero_diag,
                                                      (double *)K);
     else
-        kbuild_f32_kernel<<<grid, block, 0, s>>>(kind, (float)(1.0 / param), (const float *)Xw, n, d, zero_diag,
-                                                 (float *)K);
+        kbuild_f32_kernel<float><<<grid, block, 0, s>>>(kind, (float)(1.0 / param), (const float *)Xw, n, d,
+                                                        zero_diag, (float *)K);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kbuild_linear_wide(const float *X, int64_t n, int d, double param, int zero_diag, double *K,
+                                      cudaStream_t s) {
+    dim3 grid((unsigned)((n + 63) / 64), (unsigned)((n + 63) / 64)), block(16, 16);
+    kbuild_f32_kernel<double><<<grid, block, 0, s>>>(USTAT_LINEAR, 0.f, X, n, d, zero_diag, K, 1.0 / param);
     return cudaGetLastError();
 }
 

@@ -94,11 +94,13 @@ __global__ void __launch_bounds__(256) tile_kernel(int mode, TileTerms tt, int64
 // 512-column row segments (float4 when the row length allows it) of each
 // distinct matrix once and evaluates every operation on them.  Operation o
 // multiplies matrix m ex[o][m] times (the terms of a merged factor).
+// GEMV partial sums accumulate in the matrices' own type (float64 for float64
+// storage, whose point is to keep every rounding below float32's).
 template <typename T, bool kVec>
-__global__ void __launch_bounds__(256, 3) mhb_kernel(MhbArgs g) {
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) mhb_kernel(MhbArgs g) {
     constexpr int CB = 256;   // columns per block: 8 per lane
     __shared__ T bsm[kMhbOps][CB];
-    __shared__ float colred[8][CB];
+    __shared__ T colred[8][CB];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t n = g.n;
     const int64_t j0 = (int64_t)blockIdx.x * CB;
@@ -111,13 +113,13 @@ __global__ void __launch_bounds__(256, 3) mhb_kernel(MhbArgs g) {
         }
     __syncthreads();
     double facc[kMhbOps];
-    float gacc[kMhbGemv][8];
+    T gacc[kMhbGemv][8];
 #pragma unroll
     for (int o = 0; o < kMhbOps; ++o) facc[o] = 0.0;
 #pragma unroll
     for (int q = 0; q < kMhbGemv; ++q)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) gacc[q][c] = 0.f;
+        for (int c = 0; c < 8; ++c) gacc[q][c] = T(0);
     for (int64_t i = (int64_t)blockIdx.y * 8 + warp; i < n; i += (int64_t)gridDim.y * 8) {
         T vals[kMhbMats][8];
 #pragma unroll
@@ -168,12 +170,12 @@ __global__ void __launch_bounds__(256, 3) mhb_kernel(MhbArgs g) {
                 for (int c = 0; c < 8; ++c) s = fma(p[c], bsm[o][col(c)], s);
                 facc[o] += (double)s * ai;
             } else {
-                const float af = (float)ai;
+                const T af = (T)ai;
 #pragma unroll
                 for (int q = 0; q < kMhbGemv; ++q)
                     if (q == gi) {
 #pragma unroll
-                        for (int c = 0; c < 8; ++c) gacc[q][c] = fmaf(af, (float)p[c], gacc[q][c]);
+                        for (int c = 0; c < 8; ++c) gacc[q][c] = fma(af, p[c], gacc[q][c]);
                     }
                 ++gi;
             }

@@ -21,6 +21,10 @@ cudaError_t launch_kbuild_rbf(const float *Xw, int64_t n, int d, double param, i
                               void *slices, int64_t ldp, int lead_bits, int planes, float *scales, int nred,
                               const int *red_pow, const int *red_vec, double *const *red_out, int upper_only,
                               int tile64, cudaStream_t s);
+// Linear kernel of a float32 X into a float64 K (float64-storage modes): the
+// double-float dot product, unrounded.
+cudaError_t launch_kbuild_linear_wide(const float *X, int64_t n, int d, double param, int zero_diag, double *K,
+                                      cudaStream_t s);
 cudaError_t launch_loadmat(const double *src, int64_t n, bool fp64, int zero_diag, void *dst,
                            cudaStream_t s);
 cudaError_t launch_unary_tanh(const void *X, int x_dtype, int64_t n, int d, const double *w,

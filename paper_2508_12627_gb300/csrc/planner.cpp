@@ -1252,7 +1252,7 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan, const P
             }
             for (int s : outs(P.ops[i])) producer[s] = (int)i;
         }
-        const bool can_group = !wide_storage(P.precision);
+        const bool can_group = true;
         auto eligible = [&](const Op &o) {
             if (!can_group || (o.kind != OP_FREDUCE && o.kind != OP_GEMV)) return false;
             for (int t = 0; t < o.nt; ++t)
