@@ -185,7 +185,11 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
     cudaError_t e = cudaMemsetAsync(C.ws, 0, C.L.zero_bytes, C.st);
     if (e != cudaSuccess) return cuda_fail(e);
     int *err = (int *)(C.ws + C.L.err_off);
-    if (needs_xw(P)) {
+    // float32 storage with RBF builds only: they read the caller's X directly
+    bool direct_x = !C.fp64;
+    for (const Op &op : P.ops)
+        if (op.kind == OP_KBUILD && f[op.factor].kind != USTAT_RBF) direct_x = false;
+    if (needs_xw(P) && !direct_x) {
         ProfScope ps(kProfXconvert, C.st);
         e = launch_xconvert(X, x_dtype, n, C.d, C.ws + C.L.xw_off, C.fp64, C.st);
         if (e != cudaSuccess) return cuda_fail(e);
@@ -203,7 +207,10 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                         rvec[r] = P.slots[op.red[r].out].kind == S_VEC;
                         rout[r] = C.vec(op.red[r].out);   // scalar and vector slots are float64
                     }
-                    e = launch_kbuild_rbf((const float *)(C.ws + C.L.xw_off), n, C.d, f[op.factor].param, P.sparsify,
+                    const float *xf = direct_x ? (x_dtype == 1 ? (const float *)X : nullptr)
+                                               : (const float *)(C.ws + C.L.xw_off);
+                    const double *xd = direct_x && x_dtype == 0 ? (const double *)X : nullptr;
+                    e = launch_kbuild_rbf(xf, xd, n, C.d, f[op.factor].param, P.sparsify,
                                           (float *)C.ptr(op.out), op.opA >= 0 ? C.ptr(op.opA) : nullptr,
                                           C.L.ldp_slices, lead, split_planes_of(P.precision),
                                           op.opA >= 0 ? C.scales(op.opA) : nullptr, op.nred, rpow, rvec, rout,

@@ -160,7 +160,9 @@ struct RbfRed {
     double *out;
 };
 struct RbfArgs {
-    const float *X;
+    const float *X;          // float32 X, or
+    const double *Xd;        // float64 X, rounded to float32 as it is staged (no conversion pass)
+    int xvec;                // d % 4 == 0 and X 16-byte aligned: vector loads of X
     int64_t n;
     int d;
     float inv_h;
@@ -347,7 +349,7 @@ __global__ void __launch_bounds__(256, 2) kbuild_rbf_tile_kernel(RbfArgs g) {
     for (int a = 0; a < 8; ++a)
 #pragma unroll
         for (int h = 0; h < 4; ++h) acc[a][h] = f2_splat(0.f);
-    const bool xvec = (g.d % 4) == 0;
+    const bool xvec = g.xvec != 0;
     for (int k0 = 0; k0 < g.d; k0 += 32) {
         __syncthreads();
         // stage rows i0.. and j0.., 32 coordinates, transposed (consecutive lanes:
@@ -358,14 +360,28 @@ __global__ void __launch_bounds__(256, 2) kbuild_rbf_tile_kernel(RbfArgs g) {
             const int k = k0 + 4 * kq;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (gr < n && k < g.d) {
-                const float *src = g.X + gr * g.d + k;
-                if (xvec) {
-                    v = *reinterpret_cast<const float4 *>(src);
+                if (g.Xd) {
+                    const double *src = g.Xd + gr * g.d + k;
+                    if (xvec) {
+                        const double2 p0 = *reinterpret_cast<const double2 *>(src);
+                        const double2 p1 = *reinterpret_cast<const double2 *>(src + 2);
+                        v = make_float4((float)p0.x, (float)p0.y, (float)p1.x, (float)p1.y);
+                    } else {
+                        v.x = (float)src[0];
+                        if (k + 1 < g.d) v.y = (float)src[1];
+                        if (k + 2 < g.d) v.z = (float)src[2];
+                        if (k + 3 < g.d) v.w = (float)src[3];
+                    }
                 } else {
-                    v.x = src[0];
-                    if (k + 1 < g.d) v.y = src[1];
-                    if (k + 2 < g.d) v.z = src[2];
-                    if (k + 3 < g.d) v.w = src[3];
+                    const float *src = g.X + gr * g.d + k;
+                    if (xvec) {
+                        v = *reinterpret_cast<const float4 *>(src);
+                    } else {
+                        v.x = src[0];
+                        if (k + 1 < g.d) v.y = src[1];
+                        if (k + 2 < g.d) v.z = src[2];
+                        if (k + 3 < g.d) v.w = src[3];
+                    }
                 }
             }
             if (opnd == 0) {
@@ -573,7 +589,7 @@ __global__ void __launch_bounds__(128, 8) kbuild_rbf_tile64_kernel(RbfArgs g) {
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int h = 0; h < 4; ++h) acc[a][h] = f2_splat(0.f);
-    const bool xvec = (g.d % 4) == 0;
+    const bool xvec = g.xvec != 0;
     for (int k0 = 0; k0 < g.d; k0 += 32) {
         __syncthreads();
         for (int e = tid; e < 2 * kRbfT64 * 8; e += 128) {
@@ -582,14 +598,28 @@ __global__ void __launch_bounds__(128, 8) kbuild_rbf_tile64_kernel(RbfArgs g) {
             const int k = k0 + 4 * kq;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (gr < n && k < g.d) {
-                const float *src = g.X + gr * g.d + k;
-                if (xvec) {
-                    v = *reinterpret_cast<const float4 *>(src);
+                if (g.Xd) {
+                    const double *src = g.Xd + gr * g.d + k;
+                    if (xvec) {
+                        const double2 p0 = *reinterpret_cast<const double2 *>(src);
+                        const double2 p1 = *reinterpret_cast<const double2 *>(src + 2);
+                        v = make_float4((float)p0.x, (float)p0.y, (float)p1.x, (float)p1.y);
+                    } else {
+                        v.x = (float)src[0];
+                        if (k + 1 < g.d) v.y = (float)src[1];
+                        if (k + 2 < g.d) v.z = (float)src[2];
+                        if (k + 3 < g.d) v.w = (float)src[3];
+                    }
                 } else {
-                    v.x = src[0];
-                    if (k + 1 < g.d) v.y = src[1];
-                    if (k + 2 < g.d) v.z = src[2];
-                    if (k + 3 < g.d) v.w = src[3];
+                    const float *src = g.X + gr * g.d + k;
+                    if (xvec) {
+                        v = *reinterpret_cast<const float4 *>(src);
+                    } else {
+                        v.x = src[0];
+                        if (k + 1 < g.d) v.y = src[1];
+                        if (k + 2 < g.d) v.z = src[2];
+                        if (k + 3 < g.d) v.w = src[3];
+                    }
                 }
             }
             if (opnd == 0) {
@@ -1026,13 +1056,14 @@ cudaError_t launch_kbuild_linear_wide(const float *X, int64_t n, int d, double p
     return cudaGetLastError();
 }
 
-cudaError_t launch_kbuild_rbf(const float *Xw, int64_t n, int d, double param, int zero_diag, float *K,
-                              void *slices, int64_t ldp, int lead_bits, int planes, float *scales, int nred,
+cudaError_t launch_kbuild_rbf(const float *Xw, const double *Xd, int64_t n, int d, double param, int zero_diag,
+                              float *K, void *slices, int64_t ldp, int lead_bits, int planes, float *scales, int nred,
                               const int *red_pow, const int *red_vec, double *const *red_out, int upper_only,
                               int tile64, cudaStream_t s) {
-    if (nred < 0 || nred > kRbfMaxRed || planes < 3 || planes > 5) return cudaErrorInvalidValue;
-    RbfArgs g{Xw, n, d, (float)(1.0 / param), zero_diag, K, (__nv_bfloat16 *)slices, slices ? ldp : n, lead_bits,
-              planes, slices ? scales : nullptr, nred, {}, upper_only};
+    if (nred < 0 || nred > kRbfMaxRed || planes < 3 || planes > 5 || (!Xw && !Xd)) return cudaErrorInvalidValue;
+    const int xvec = (d % 4) == 0 && ((uintptr_t)(Xw ? (const void *)Xw : (const void *)Xd) % 16) == 0;
+    RbfArgs g{Xw, Xd, xvec, n, d, (float)(1.0 / param), zero_diag, K, (__nv_bfloat16 *)slices, slices ? ldp : n,
+              lead_bits, planes, slices ? scales : nullptr, nred, {}, upper_only};
     for (int q = 0; q < nred; ++q) {
         if (red_pow[q] < 1 || red_pow[q] > 4) return cudaErrorInvalidValue;
         g.red[q] = RbfRed{red_pow[q], red_vec[q], red_out[q]};

@@ -17,8 +17,9 @@ cudaError_t launch_kbuild(int kind, double param, const void *Xw, bool fp64, int
 // row scale 1 (slices may be null: K only) and with up to 4 reductions of its
 // entrywise powers: red_vec[q] ? red_out[q][i] += sum_j K_ij^red_pow[q]
 //                              : *red_out[q] += sum_ij K_ij^red_pow[q].
-cudaError_t launch_kbuild_rbf(const float *Xw, int64_t n, int d, double param, int zero_diag, float *K,
-                              void *slices, int64_t ldp, int lead_bits, int planes, float *scales, int nred,
+// X is read as float32 (Xw) or as float64 (Xd, rounded to float32 while staged).
+cudaError_t launch_kbuild_rbf(const float *Xw, const double *Xd, int64_t n, int d, double param, int zero_diag,
+                              float *K, void *slices, int64_t ldp, int lead_bits, int planes, float *scales, int nred,
                               const int *red_pow, const int *red_vec, double *const *red_out, int upper_only,
                               int tile64, cudaStream_t s);
 // Linear kernel of a float32 X into a float64 K (float64-storage modes): the

@@ -276,3 +276,36 @@ def test_rbf_build_tile_variants(eng_mod, name, n, prec):
         eng.workspace(eng.plan.workspace_bytes(n, w.X.shape[1])).fill_(255)
         out = eng.evaluate(w.X)
         _compare(out, ref, absref, tol_for(name, prec, n), (name, n, prec, variant))
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp32", "bf16x4"])
+def test_input_dtype_and_alignment(eng_mod, prec):
+    # X given as float64 or float32, at a 16-byte aligned address or 8 bytes off it
+    # (the RBF build reads the caller's X directly in the float32-storage modes)
+    import torch
+    from paper_2508_12627_gb300 import ustat as us
+    n = 300
+    w = synth.workload("c4_rbf", n)
+    ref, absref = _oracle(w)
+    eng = eng_mod.Engine(w.graph, w.factors, precision=prec)
+    d = w.X.shape[1]
+    for dt in (torch.float64, torch.float32):
+        x32 = torch.as_tensor(w.X).to(dt)
+        if dt == torch.float32:
+            # the oracle on the float32-rounded data
+            w2 = synth.Workload(w.name, w.graph, w.factors, n, d, x32.double().numpy())
+            r, ra = _oracle(w2)
+        else:
+            r, ra = ref, absref
+        for off in (0, 1):
+            buf = torch.empty(n * d + 2, dtype=dt, device="cuda")
+            X = buf[off:off + n * d].view(n, d)
+            X.copy_(x32)
+            out = torch.empty(2 + eng.n_parts, dtype=torch.float64, device="cuda")
+            ws = eng.workspace(eng.plan.workspace_bytes(n, d))
+            us.ustat_eval(eng.plan, X.data_ptr(), 0 if dt == torch.float64 else 1, n, d, eng.factor_tuples(n),
+                          ws.data_ptr(), ws.numel(), torch.cuda.current_stream().cuda_stream, out.data_ptr(),
+                          out.data_ptr() + 16)
+            o = out.cpu().numpy()
+            _compare({"U_sum": o[0], "U_mean": o[1], "V": o[2:]}, r, ra, tol_for("c4_rbf", prec, n),
+                     (prec, str(dt), off))
