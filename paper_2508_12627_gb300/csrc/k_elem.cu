@@ -265,9 +265,9 @@ __device__ __forceinline__ int rbf_row(int a, int ty) { return 4 * ty + (a & 3) 
 // instruction cache.
 // (half: the column offset of the second quadruple, 64 for 128-wide tiles and 32
 // for 64-wide ones; nhalf = 1 stores the first quadruple only)
+template <int nhalf = 2>
 __device__ __noinline__ void rbf_store_row(float *K, __nv_bfloat16 *slices, int64_t n, int64_t ldp, int planes,
-                                           float lead_scale, int64_t gr, int64_t gc, F2Row v, int half = 64,
-                                           int nhalf = 2) {
+                                           float lead_scale, int64_t gr, int64_t gc, F2Row v, int half = 64) {
     float *krow = K ? K + gr * n : nullptr;
     const bool vec4 = (n % 4) == 0;
 #pragma unroll
@@ -289,7 +289,7 @@ __device__ __noinline__ void rbf_store_row(float *K, __nv_bfloat16 *slices, int6
     const f32x2 ls = f2_splat(lead_scale);
     f32x2 y[4];
 #pragma unroll
-    for (int h = 0; h < 4; ++h) y[h] = f2_mul(v.v[h], ls);   // row scale 1: |y| <= 2^w, exact
+    for (int h = 0; h < 2 * nhalf; ++h) y[h] = f2_mul(v.v[h], ls);   // row scale 1: |y| <= 2^w, exact
     const int64_t plane = n * ldp;
     __nv_bfloat16 *srow = slices + gr * ldp + gc;
     float magic = 12582912.0f;   // 1.5 * 2^23
@@ -297,7 +297,7 @@ __device__ __noinline__ void rbf_store_row(float *K, __nv_bfloat16 *slices, int6
         const f32x2 mg = f2_splat(magic);
         uint32_t w[4];
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
+        for (int h = 0; h < 2 * nhalf; ++h) {
             const f32x2 dgt = f2_sub(f2_add(y[h], mg), mg);
             y[h] = f2_sub(y[h], dgt);
             float d0, d1;
@@ -767,7 +767,7 @@ __global__ void __launch_bounds__(128, 8) kbuild_rbf_tile64_kernel(RbfArgs g) {
         F2Row v;
 #pragma unroll
         for (int h = 0; h < 4; ++h) v.v[h] = acc[a][h];
-        rbf_store_row(K, slices, n, ldp, planes, lead_scale, gr, j0 + 4 * tx, v, 32, 2);
+        rbf_store_row<2>(K, slices, n, ldp, planes, lead_scale, gr, j0 + 4 * tx, v, 32);
     }
     // K below the diagonal is skipped only where no reader needs it: the readers
     // of an upper-only K are symmetric GEMMs with 128-row tiles, whose diagonal
@@ -788,7 +788,7 @@ __global__ void __launch_bounds__(128, 8) kbuild_rbf_tile64_kernel(RbfArgs g) {
                 v.v[0] = f2_pack(cv[0], cv[1]);
                 v.v[1] = f2_pack(cv[2], cv[3]);
                 v.v[2] = v.v[3] = f2_splat(0.f);
-                rbf_store_row(mirror_k ? K : nullptr, slices, n, ldp, planes, lead_scale, gr, i0 + 4 * ty, v, 32, 1);
+                rbf_store_row<1>(mirror_k ? K : nullptr, slices, n, ldp, planes, lead_scale, gr, i0 + 4 * ty, v, 32);
             }
         }
     }
