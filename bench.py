@@ -397,11 +397,11 @@ def main():
 
     # the whole evaluation captured once as a CUDA graph (the library's batched
     # form with one sample), replayed once per step
-    bat = us.Batched(eng.plan, [n], d, max_lanes=1)
+    bat = us.Batched(eng.plan, [w.n], w.d, max_lanes=1)
     ws_b = torch.empty(bat.workspace_bytes(), dtype=torch.uint8, device=dev)
     gstream = torch.cuda.Stream(dev)
     x_dt = 0 if Xd.dtype == torch.float64 else 1
-    facs = eng.factor_tuples(n)
+    facs = eng.factor_tuples(w.n)
     with torch.cuda.stream(gstream):
         bat.run([Xd.data_ptr()], x_dt, facs, ws_b.data_ptr(), ws_b.numel(), gstream.cuda_stream, out.data_ptr(),
                 out.data_ptr() + 16)
