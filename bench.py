@@ -319,7 +319,7 @@ def run_batched(args):
            "sample": "the 4 smallest samples (n=%s) for both kernel graphs" % [ns[i] for i in order]}
     line = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "eager_ms_per_step": eager_ms,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
         "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": WORKLOADS["batched"], "samples": len(ns), "d": d, "precision": args.precision,
