@@ -118,12 +118,34 @@ int ustat_plan(const ustat_graph *graph, const ustat_options *opts, ustat_plan_t
 void ustat_plan_destroy(ustat_plan_t *plan);
 
 /*
+ * A shard of the partition sum (U = sum over partitions of mu_pi V_pi, Lemma
+ * "Decomposition of U-Statistic into V-Statistics", Section 3.3): the plan of rank `shard` of `n_shards`, which
+ * evaluates its own partitions and reports V_pi = 0 for the others, so that the
+ * element-wise sum over all shards of U_out and V_out (a sum of 2 + Bell(m)
+ * float64 values, the one exchange step) gives the full result.
+ *   Partitions that share a contraction under opts->cse stay on one shard; the
+ *   groups go, costliest first, to the least loaded shard, each costed by the
+ *   program that evaluates it alone at sample size n (algorithmic flops, at
+ *   least one n^2 pass per operation).  The assignment is a function of the
+ *   arguments only, so every rank computes the same one.
+ *   owner : [Bell(m)] or NULL; receives each partition's shard, -1 for a
+ *           partition that no shard evaluates (skipped by sparsification)
+ *   *out  : a plan owned by the library, used like ustat_plan()'s; a shard with
+ *           no partition gives U = 0 and V = 0
+ * Errors as ustat_plan(); USTAT_ERR_INVALID_ARG if shard is not in [0, n_shards)
+ * or n < 1.  Host only, no CUDA call.
+ */
+int ustat_plan_shard(const ustat_graph *graph, const ustat_options *opts, int shard, int n_shards,
+                     int64_t n, int *owner, ustat_plan_t **out);
+
+/*
  * Plan report.  Any output pointer may be NULL.
  *   n_parts : number of partitions (Bell(m))
  *   mu      : [n_parts] Moebius coefficients mu_pi
  *   tw      : [n_parts] treewidth of the quotient graph G/pi (exact); -1 if skipped
  *   rgs     : [n_parts * m] restricted growth strings
- *   evaluated: [n_parts] 1 if V_pi is computed, 0 if skipped by sparsification
+ *   evaluated: [n_parts] 1 if V_pi is computed, 0 if skipped by sparsification or
+ *             left to another shard (ustat_plan_shard)
  *   n_ops   : number of device operations in the lowered program
  *   n_gemm  : number of n^3 contractions (stored + fused) in the program
  *   n_gemm3 : number of n^4 contractions

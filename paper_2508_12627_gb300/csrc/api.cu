@@ -75,6 +75,7 @@ struct Layout {
     // s = 3 steps on the tensor cores: digit planes of g3_nb A operands at a time
     size_t g3_off = 0, g3_stride = 0;
     int g3_nb = 0;
+    int g3_regions = 1;
 };
 
 bool tc_gemm3(const Plan &P) {
@@ -145,10 +146,57 @@ Layout make_layout(const Plan &P, int64_t n, int d) {
         L.g3_nb = (int)std::max<size_t>(1, std::min<size_t>(64, ((size_t)256 << 20) / L.g3_stride));
         L.g3_nb = (int)std::min<int64_t>(L.g3_nb, n);
         L.g3_off = cur;
-        cur = align_up(cur + L.g3_stride * L.g3_nb, 1024);
+        // two regions when there is more than one batch: the next batch's
+        // operands are split while the tensor cores work on the current one
+        L.g3_regions = L.g3_nb < n ? 2 : 1;
+        cur = align_up(cur + L.g3_stride * L.g3_nb * L.g3_regions, 1024);
     }
     L.total = cur;
     return L;
+}
+
+// A second stream and events per host thread and device: the operand split of
+// the next s = 3 batch runs on it while the current batch's GEMM runs on the
+// caller's stream (the GEMM's CTAs leave registers and shared memory for two
+// split CTAs per SM).  Every piece of work on it is joined back into the
+// caller's stream by an event, so the pair also records correctly into a CUDA
+// graph capture of the caller's stream.
+struct SideStream {
+    int dev = -1;
+    cudaStream_t st = nullptr;
+    cudaEvent_t ready = nullptr, split_done[2] = {nullptr, nullptr}, gemm_done[2] = {nullptr, nullptr};
+    ~SideStream() {
+        if (dev < 0) return;
+        int cur = -1;
+        if (cudaGetDevice(&cur) != cudaSuccess || cur != dev) return;   // leave them to the context
+        cudaEventDestroy(ready);
+        for (int h = 0; h < 2; ++h) {
+            cudaEventDestroy(split_done[h]);
+            cudaEventDestroy(gemm_done[h]);
+        }
+        cudaStreamDestroy(st);
+    }
+};
+thread_local SideStream g_side[16];
+
+cudaError_t side_stream(SideStream **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 16) return cudaErrorInvalidDevice;
+    SideStream &S = g_side[dev];
+    if (S.dev < 0) {
+        e = cudaStreamCreateWithFlags(&S.st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S.ready, cudaEventDisableTiming);
+        for (int h = 0; h < 2 && e == cudaSuccess; ++h) {
+            e = cudaEventCreateWithFlags(&S.split_done[h], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S.gemm_done[h], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return e;
+        S.dev = dev;
+    }
+    *out = &S;
+    return cudaSuccess;
 }
 
 struct Ctx {
@@ -362,17 +410,34 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                 if (is_split_mode(P.precision)) {
                     // tensor cores: g3_nb products at a time, their A operands split
                     // per bb into the batch region (planes of all bb back to back)
+                    // (two regions: batch k is split on the side stream into region
+                    // k % 2 once the GEMM of batch k - 2 has read it, and its GEMM
+                    // waits for that split)
                     const int planes = split_planes_of(P.precision);
                     const size_t plane_bytes = 2 * (size_t)n * C.L.ldp_slices;
-                    char *sl = C.ws + C.L.g3_off;
-                    float *sc = (float *)(sl + planes * plane_bytes * C.L.g3_nb);
                     const int var = P.tc_variant[tc_size_class(n)];
-                    for (int64_t bb0 = 0; bb0 < n && e == cudaSuccess; bb0 += C.L.g3_nb) {
+                    const bool two = C.L.g3_regions == 2;
+                    SideStream *S = nullptr;
+                    if (two) {
+                        e = side_stream(&S);
+                        if (e == cudaSuccess) e = cudaEventRecord(S->ready, C.st);
+                        if (e == cudaSuccess) e = cudaStreamWaitEvent(S->st, S->ready, 0);
+                    }
+                    int k = 0;
+                    for (int64_t bb0 = 0; bb0 < n && e == cudaSuccess; bb0 += C.L.g3_nb, ++k) {
                         const int nb = (int)std::min<int64_t>(C.L.g3_nb, n - bb0);
+                        const int h = two ? (k & 1) : 0;
+                        char *sl = C.ws + C.L.g3_off + (size_t)h * C.L.g3_stride * C.L.g3_nb;
+                        float *sc = (float *)(sl + planes * plane_bytes * C.L.g3_nb);
+                        cudaStream_t ss = two ? S->st : C.st;
+                        if (two && k >= 2) e = cudaStreamWaitEvent(ss, S->gemm_done[h], 0);
+                        if (e != cudaSuccess) break;
                         // symmetric sources are read along rows (A(i, j) = M[j][i])
                         auto row_form = [&](const Term &t) { return P.slots[t.mat].symmetric ? 1 : t.trans; };
                         e = launch_split_g3(C.ptr(op.A.mat), C.fp64, row_form(op.A), C.vec(op.u), C.ptr(op.Ab.mat),
-                                            row_form(op.Ab), bb0, nb, n, C.L.ldp_slices, lead, planes, sl, sc, C.st);
+                                            row_form(op.Ab), bb0, nb, n, C.L.ldp_slices, lead, planes, sl, sc, ss);
+                        if (e == cudaSuccess && two) e = cudaEventRecord(S->split_done[h], ss);
+                        if (e == cudaSuccess && two) e = cudaStreamWaitEvent(C.st, S->split_done[h], 0);
                         if (e != cudaSuccess) break;
                         TcGemmArgs g{};
                         g.n = n;
@@ -398,6 +463,7 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                         if (P.precision == USTAT_BF16X3) e = launch_gemm_bf16x3(g, (var >> 2) & 3, C.st);
                         else if (P.precision == USTAT_BF16X5) e = launch_gemm_bf16x5(g, C.st);
                         else e = launch_gemm_bf16x4(g, (var >> 2) & 3, C.st);
+                        if (e == cudaSuccess && two) e = cudaEventRecord(S->gemm_done[h], C.st);
                     }
                     break;
                 }
@@ -471,6 +537,132 @@ int ustat_plan(const ustat_graph *graph, const ustat_options *opts, ustat_plan_t
 }
 
 void ustat_plan_destroy(ustat_plan_t *plan) { delete plan; }
+
+namespace {
+// Modelled cost of a lowered program at sample size n: each operation's
+// algorithmic flops, and at least one n^2 pass per operation.
+double shard_cost(const Plan &P, int64_t n) {
+    const double dn = (double)n;
+    double c = 0.0;
+    for (auto &op : P.ops) c += std::max(op.coef * std::pow(dn, op.npow), dn * dn);
+    return c;
+}
+}  // namespace
+
+int ustat_plan_shard(const ustat_graph *graph, const ustat_options *opts, int shard, int n_shards, int64_t n,
+                     int *owner, ustat_plan_t **out) {
+    if (!graph || !opts || !out || n_shards < 1 || shard < 0 || shard >= n_shards || n < 1)
+        return USTAT_ERR_INVALID_ARG;
+    Plan full;
+    int rc = build_plan(graph, opts, &full);
+    if (rc != USTAT_OK) return rc;
+    const int np = (int)full.parts.size();
+    if (np > kCombineMaxParts) return USTAT_ERR_UNSUPPORTED;
+    // Groups: evaluated partitions that share a scalar (the same contraction,
+    // computed once under sharing) stay on one shard.
+    std::vector<int> root(np);
+    for (int i = 0; i < np; ++i) root[i] = i;
+    auto find = [&](int i) {
+        while (root[i] != i) i = root[i] = root[root[i]];
+        return i;
+    };
+    std::vector<int> first_user(full.slots.size(), -1);
+    for (int i = 0; i < np; ++i) {
+        const PartRec &pr = full.parts[i];
+        if (!pr.evaluated) continue;
+        for (int q = 0; q < pr.nscal; ++q) {
+            int &f = first_user[pr.scal[q]];
+            if (f < 0) f = i;
+            else root[find(i)] = find(f);
+        }
+    }
+    std::vector<std::vector<int>> groups;
+    std::vector<int> group_of(np, -1);
+    for (int i = 0; i < np; ++i) {
+        if (!full.parts[i].evaluated) continue;
+        int r = find(i);
+        if (group_of[r] < 0) {
+            group_of[r] = (int)groups.size();
+            groups.push_back({});
+        }
+        group_of[i] = group_of[r];
+        groups[group_of[i]].push_back(i);
+    }
+    // Cost of a set of groups: the program that evaluates that set alone.
+    auto cost_of = [&](const std::vector<char> &keep, double *c) {
+        PlanRequest req;
+        req.keep = &keep;
+        Plan gp;
+        int e = build_plan(graph, opts, &gp, &req);
+        *c = e == USTAT_OK ? shard_cost(gp, n) : 0.0;
+        return e;
+    };
+    std::vector<double> cost(groups.size(), 0.0);
+    std::vector<int> shard_of_group(groups.size(), 0);
+    if (n_shards > 1) {
+        for (size_t gi = 0; gi < groups.size(); ++gi) {
+            std::vector<char> keep(np, 0);
+            for (int i : groups[gi]) keep[i] = 1;
+            rc = cost_of(keep, &cost[gi]);
+            if (rc != USTAT_OK) return rc;
+        }
+        // Costliest group first, to the shard that minimises the largest shard
+        // cost plus the work the group adds there: a group whose products a
+        // shard already computes adds only its own passes, so sharing is kept
+        // unless splitting it shortens the longest shard by more than the work
+        // it repeats; independent groups go to the least loaded shard.  Ties:
+        // the smaller growth, the lower shard.
+        std::vector<int> by_cost(groups.size());
+        for (size_t gi = 0; gi < groups.size(); ++gi) by_cost[gi] = (int)gi;
+        std::stable_sort(by_cost.begin(), by_cost.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+        std::vector<std::vector<char>> keep_of(n_shards, std::vector<char>(np, 0));
+        std::vector<double> load(n_shards, 0.0);
+        double span = 0.0;
+        for (int gi : by_cost) {
+            int best = -1;
+            double best_load = 0.0, best_growth = 0.0, best_score = 0.0;
+            for (int r = 0; r < n_shards; ++r) {
+                double c = cost[gi];
+                if (load[r] > 0.0) {
+                    std::vector<char> k = keep_of[r];
+                    for (int i : groups[gi]) k[i] = 1;
+                    rc = cost_of(k, &c);
+                    if (rc != USTAT_OK) return rc;
+                }
+                double growth = c - load[r];
+                double score = std::max(span, c) + growth;
+                if (best < 0 || score < best_score || (score == best_score && growth < best_growth)) {
+                    best = r;
+                    best_load = c;
+                    best_growth = growth;
+                    best_score = score;
+                }
+                if (load[r] == 0.0) break;   // empty shards are alike: try the first only
+            }
+            shard_of_group[gi] = best;
+            load[best] = best_load;
+            span = std::max(span, best_load);
+            for (int i : groups[gi]) keep_of[best][i] = 1;
+        }
+    }
+    std::vector<char> keep(np, 0);
+    for (int i = 0; i < np; ++i) {
+        int r = group_of[i] < 0 ? -1 : shard_of_group[group_of[i]];
+        if (owner) owner[i] = r;
+        keep[i] = r == shard;
+    }
+    ustat_plan_t *p = new (std::nothrow) ustat_plan_t();
+    if (!p) return USTAT_ERR_INVALID_ARG;
+    PlanRequest req;
+    req.keep = &keep;
+    rc = build_plan(graph, opts, &p->p, &req);
+    if (rc != USTAT_OK) {
+        delete p;
+        return rc;
+    }
+    *out = p;
+    return USTAT_OK;
+}
 
 int ustat_plan_info(const ustat_plan_t *plan, int *n_parts, int *mu, int *tw, int *rgs, int *evaluated, int *n_ops,
                     int *n_gemm, int *n_gemm3) {

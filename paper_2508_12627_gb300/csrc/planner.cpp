@@ -501,6 +501,7 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan, const P
     std::vector<std::vector<int>> parts;
     enum_partitions(m, parts);
     if (req && req->forced && req->forced->size() != parts.size()) return USTAT_ERR_INVALID_ARG;
+    if (req && req->keep && req->keep->size() != parts.size()) return USTAT_ERR_INVALID_ARG;
     if (req && req->collect) req->collect->assign(parts.size(), {});
     std::set<std::tuple<int, int, int, int, int>> products;   // n^3 products in the program
     for (size_t pi = 0; pi < parts.size(); ++pi) {
@@ -520,7 +521,7 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan, const P
             }
         }
         pr.tw = exact_treewidth(k, qadj);
-        if (req && req->finest_only && k != m) {
+        if (req && ((req->finest_only && k != m) || (req->keep && !(*req->keep)[pi]))) {
             pr.evaluated = 0;
             P.parts.push_back(pr);
             continue;

@@ -90,7 +90,7 @@ struct PartRec {
     int nblocks = 0;
     int mu = 0;
     int tw = -1;                  // exact treewidth of G/pi (simple quotient graph)
-    int evaluated = 1;            // 0: skipped by sparsification (V = 0)
+    int evaluated = 1;            // 0: skipped by sparsification or left to another shard (V = 0)
     int nfree = 0;                // blocks with no factor at all: factor n each
     int nscal = 0;
     int scal[kMaxScal];
@@ -150,6 +150,9 @@ struct PlanRequest {
     // evaluate only the partition with m blocks (every vertex distinct): the plan
     // of the kernel graph's own contraction; the others are reported as 0
     bool finest_only = false;
+    // if set: evaluate only the partitions whose entry is nonzero (a shard of the
+    // partition sum); the others are reported as 0
+    const std::vector<char> *keep = nullptr;
     // if set: every evaluated partition's distinct elimination sequences with
     // their features at sample size n (the plan is built as usual)
     std::vector<std::vector<Candidate>> *collect = nullptr;

@@ -19,12 +19,15 @@ from . import ustat as us
 
 class Engine:
     def __init__(self, graph, factors, precision="bf16x3", sparsify=False, planner=us.PLAN_EXHAUSTIVE, cse=True,
-                 device="cuda:0"):
+                 device="cuda:0", shard=None):
+        """``shard=(rank, n_shards, n)``: evaluate only this rank's share of the
+        partition sum (ustat_plan_shard); ``evaluate_shards`` then sums the
+        ranks' results."""
         self.graph = graph
         self.factors = list(factors)
         self.device = torch.device(device)
         self.plan = us.Plan(graph, [f.kind for f in self.factors], precision=precision, sparsify=sparsify,
-                            planner=planner, cse=cse)
+                            planner=planner, cse=cse, shard=shard)
         self.n_parts = self.plan.info["n_parts"]
         self._ws = None
         self._fdev = {}
@@ -74,6 +77,27 @@ class Engine:
         self.launch(X, out)
         o = out.cpu().numpy()
         return {"U_sum": float(o[0]), "U_mean": float(o[1]), "V": o[2:].copy()}
+
+    @staticmethod
+    def reduce_shards(out, group=None):
+        """The exchange step of a sharded evaluation: ``out`` (2 + Bell(m)
+        float64: U_sum, U_mean, V) holds this rank's partitions and zeros
+        elsewhere; one all-reduce (sum) over the ranks of ``group`` gives every
+        rank the full result, since U_sum, U_mean and each V_pi are linear in
+        the per-partition terms (Lemma "Decomposition of U-Statistic into
+        V-Statistics")."""
+        import torch.distributed as dist
+        dist.all_reduce(out, op=dist.ReduceOp.SUM, group=group)
+        o = out.cpu().numpy()
+        return {"U_sum": float(o[0]), "U_mean": float(o[1]), "V": o[2:].copy()}
+
+    def evaluate_shards(self, X, group=None):
+        """This rank's shard on its GPU, then the all-reduce of the 2 + Bell(m)
+        results (NCCL for device tensors)."""
+        X = self.to_device(X)
+        out = torch.empty(2 + self.n_parts, dtype=torch.float64, device=self.device)
+        self.launch(X, out)
+        return self.reduce_shards(out, group)
 
     def evaluate_host(self, X_host_pinned, U_host, V_host):
         """End-to-end call with host input and outputs (ustat_eval_host):

@@ -27,6 +27,7 @@ USTAT_ERR_UNSUPPORTED = -8
 RBF, LINEAR, TANH_DOT, MATRIX, VECTOR = 0, 1, 2, 3, 4
 FP64, FP32, TF32, BF16X3, BF16X4, BF16X5 = 0, 1, 2, 3, 4, 5
 PLAN_EXHAUSTIVE, PLAN_MINFILL = 0, 1
+MAX_PARTS = 877   # Bell(7): partitions of the largest supported order m = 7
 PRECISION = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16x3": BF16X3, "bf16x4": BF16X4, "bf16x5": BF16X5}
 
 _P = ctypes.POINTER
@@ -55,6 +56,7 @@ class ustat_factor(ctypes.Structure):
 EXPORTS = {
     "ustat_plan": (_i, [_P(ustat_graph), _P(ustat_options), _P(_vp)]),
     "ustat_plan_destroy": (None, [_vp]),
+    "ustat_plan_shard": (_i, [_P(ustat_graph), _P(ustat_options), _i, _i, _i64, _P(_i), _P(_vp)]),
     "ustat_plan_info": (_i, [_vp, _P(_i), _P(_i), _P(_i), _P(_i), _P(_i), _P(_i), _P(_i), _P(_i)]),
     "ustat_plan_flops": (_i, [_vp, _i64, _P(_d), _P(_d)]),
     "ustat_plan_describe": (_i, [_vp, ctypes.c_char_p, _sz, _P(_sz)]),
@@ -140,10 +142,12 @@ def _iarr(vals):
 
 class Plan:
     """Owns a ustat_plan_t.  ``graph`` has ``m``, ``edges`` [(a, b, f)], ``unary``
-    [(v, f)]; ``factor_kinds`` lists the kind of every factor id."""
+    [(v, f)]; ``factor_kinds`` lists the kind of every factor id.  With
+    ``shard=(rank, n_shards, n)`` the plan is that rank's shard of the partition
+    sum (ustat_plan_shard) and ``owner`` lists each partition's shard."""
 
     def __init__(self, graph, factor_kinds, precision="bf16x3", sparsify=False, planner=PLAN_EXHAUSTIVE,
-                 cse=True):
+                 cse=True, shard=None):
         self._keep = [
             _iarr(e[0] for e in graph.edges), _iarr(e[1] for e in graph.edges), _iarr(e[2] for e in graph.edges),
             _iarr(u[0] for u in graph.unary), _iarr(u[1] for u in graph.unary), _iarr(factor_kinds)]
@@ -152,12 +156,21 @@ class Plan:
         prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
         o = ustat_options(prec, int(bool(sparsify)), int(planner), int(bool(cse)))
         h = _vp()
-        _check(lib().ustat_plan(ctypes.byref(g), ctypes.byref(o), ctypes.byref(h)), "ustat_plan")
+        self.owner = None
+        if shard is None:
+            _check(lib().ustat_plan(ctypes.byref(g), ctypes.byref(o), ctypes.byref(h)), "ustat_plan")
+        else:
+            rank, n_shards, n = shard
+            own = (_i * MAX_PARTS)()
+            _check(lib().ustat_plan_shard(ctypes.byref(g), ctypes.byref(o), int(rank), int(n_shards), int(n), own,
+                                          ctypes.byref(h)), "ustat_plan_shard")
         self.handle = h
         self.m = graph.m
         self.factor_kinds = list(factor_kinds)
         self.precision = prec
         self.info = self._info()
+        if shard is not None:
+            self.owner = list(own[:self.info["n_parts"]])
 
     @classmethod
     def from_handle(cls, handle, graph, factor_kinds, precision):

@@ -220,10 +220,32 @@ def test_k4_cycle_treewidth3_steps_multi_tile(eng_mod, k4c_ref, prec):
     # the s = 3 steps (tensor cores in the split modes) over two 128-row tiles with a
     # ragged tail, against the oracle element by element
     w, pick, ref, absref = k4c_ref
-    out = eng_mod.Engine(w.graph, w.factors, precision=prec).evaluate(w.X)
+    eng = eng_mod.Engine(w.graph, w.factors, precision=prec)
+    eng.workspace(eng.plan.workspace_bytes(w.n, w.d)).fill_(255)   # NaN bytes: no stale reads
+    out = eng.evaluate(w.X)
     for k, i in enumerate(pick):
         err = abs(out["V"][i] - ref["V"][k])
         assert err <= SMALL_N * absref["V"][k], (prec, i, err / absref["V"][k])
+
+
+def test_k4_cycle_full_size_two_split_regions(eng_mod):
+    # n = 1024 in the launch configuration bench.py times: 25 batches of s = 3
+    # operands, each split on a second stream into one of two alternating regions
+    # while the tensor cores work on the batch before; with the workspace poisoned
+    # (NaN bytes) the treewidth-3 V_pi and U match the float32 CUDA-core path
+    # (no split, no second stream), each within 5e-7 of the exact value
+    w = synth.workload("k4_cycle_rbf")
+    eng = eng_mod.Engine(w.graph, w.factors, precision="bf16x3")
+    eng.workspace(eng.plan.workspace_bytes(w.n, w.d)).fill_(255)
+    out = eng.evaluate(w.X)
+    ref = eng_mod.Engine(w.graph, w.factors, precision="fp32").evaluate(w.X)
+    tw = eng.plan.info["tw"]
+    idx = [i for i, t in enumerate(tw) if t == 3]
+    assert len(idx) == 26
+    for i in idx:
+        assert abs(out["V"][i] - ref["V"][i]) <= 1e-6 * abs(ref["V"][i]), (i, out["V"][i], ref["V"][i])
+    assert np.all(np.isfinite(out["V"]))
+    assert abs(out["U_sum"] - ref["U_sum"]) <= 1e-6 * np.abs(ref["V"]) @ np.abs(eng.plan.info["mu"])
 
 
 def test_path5_full_size_sampled_partitions(eng_mod):
