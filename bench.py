@@ -470,7 +470,20 @@ def main():
     gemm_lines = [l for l in eng.plan.describe().splitlines() if " gemm " in l]
     entries = [(n * (n + 1) / 2 if "sym=1" in l else n * n) for l in gemm_lines]
     alg_flops = 2.0 * n * (sum(entries) / max(1, len(entries)))
-    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    kernel_note = "tc_gemm_kernel (%s)" % args.precision
+    g3_ms, g3_cnt = prof.get("gemm3", (0.0, 0))
+    if g3_ms > g_ms:
+        # the n^4 steps dominate: one step is n products of n x n x n (2 n^4
+        # flops), timed as a whole (its batched GEMM launches and the operand
+        # splits that overlap them)
+        g_ms, g_cnt = g3_ms, g3_cnt
+        per_launch_s = (g3_ms / g3_cnt) / 1e3
+        alg_flops = 2.0 * float(n) ** 4
+        kernel_note = "tc_gemm_kernel (%s), one s = 3 step of batched launches" % args.precision
+    # the burst peak for a kernel in a short timed region, the sustained one (a
+    # seconds-long loop under the power cap) once the timed region lasts 0.5 s
+    sustained = tot_ms >= 500.0
+    bf16_peak = peaks.get("bf16_tflops_sustained", 1700.0) if sustained else peaks.get("bf16_tflops", 1900.0)
     # tensor products per algorithmic multiply-add (tf32 runs at half the bf16 rate)
     products = {"bf16x3": 6.0, "bf16x4": 10.0, "bf16x5": 15.0, "tf32": 2.0, "fp32": None, "fp64": None}[args.precision]
     roof = None
@@ -479,9 +492,10 @@ def main():
         peak = bf16_peak / products
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": TRAFFIC.get((args.workload, args.precision, args.variant)),
-                "kernel": "tc_gemm_kernel (%s)" % args.precision,
+                "kernel": kernel_note,
                 "peak_note": "%s bf16 dense %.1f TFLOP/s (%s) / %g tensor products per algorithmic "
-                             "multiply-add" % (peak_src, bf16_peak, "burst", products),
+                             "multiply-add" % (peak_src, bf16_peak, "sustained" if sustained else "burst",
+                                               products),
                 "per_launch_ms": per_launch_s * 1e3}
     prof_share = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
                   for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}

@@ -155,21 +155,23 @@ Layout make_layout(const Plan &P, int64_t n, int d) {
     return L;
 }
 
-// A second stream and events per host thread and device: the operand split of
-// the next s = 3 batch runs on it while the current batch's GEMM runs on the
-// caller's stream (the GEMM's CTAs leave registers and shared memory for two
-// split CTAs per SM).  Every piece of work on it is joined back into the
-// caller's stream by an event, so the pair also records correctly into a CUDA
-// graph capture of the caller's stream.
+// A second stream, of the highest priority, and events per host thread and
+// device: the GEMMs of the s = 3 batches run on it while the operand split of
+// the next batch runs on the caller's stream.  At equal priority the split's
+// many short CTAs would take every SM as the previous GEMM drains and keep the
+// persistent GEMM waiting; with the GEMM first, the split fills what the GEMM's
+// CTAs leave of each SM (registers and shared memory for two split CTAs).
+// Every piece of work on the second stream is joined back into the caller's
+// stream by an event, so the pair also records correctly into a CUDA graph
+// capture of the caller's stream.
 struct SideStream {
     int dev = -1;
     cudaStream_t st = nullptr;
-    cudaEvent_t ready = nullptr, split_done[2] = {nullptr, nullptr}, gemm_done[2] = {nullptr, nullptr};
+    cudaEvent_t split_done[2] = {nullptr, nullptr}, gemm_done[2] = {nullptr, nullptr};
     ~SideStream() {
         if (dev < 0) return;
         int cur = -1;
         if (cudaGetDevice(&cur) != cudaSuccess || cur != dev) return;   // leave them to the context
-        cudaEventDestroy(ready);
         for (int h = 0; h < 2; ++h) {
             cudaEventDestroy(split_done[h]);
             cudaEventDestroy(gemm_done[h]);
@@ -186,8 +188,9 @@ cudaError_t side_stream(SideStream **out) {
     if (dev < 0 || dev >= 16) return cudaErrorInvalidDevice;
     SideStream &S = g_side[dev];
     if (S.dev < 0) {
-        e = cudaStreamCreateWithFlags(&S.st, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S.ready, cudaEventDisableTiming);
+        int least = 0, greatest = 0;
+        e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&S.st, cudaStreamNonBlocking, greatest);
         for (int h = 0; h < 2 && e == cudaSuccess; ++h) {
             e = cudaEventCreateWithFlags(&S.split_done[h], cudaEventDisableTiming);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S.gemm_done[h], cudaEventDisableTiming);
@@ -410,9 +413,9 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                 if (is_split_mode(P.precision)) {
                     // tensor cores: g3_nb products at a time, their A operands split
                     // per bb into the batch region (planes of all bb back to back)
-                    // (two regions: batch k is split on the side stream into region
-                    // k % 2 once the GEMM of batch k - 2 has read it, and its GEMM
-                    // waits for that split)
+                    // (two regions: batch k is split into region k % 2 once the GEMM
+                    // of batch k - 2 has read it; its GEMM runs on the second stream
+                    // after that split, beside the split of batch k + 1)
                     const int planes = split_planes_of(P.precision);
                     const size_t plane_bytes = 2 * (size_t)n * C.L.ldp_slices;
                     const int var = P.tc_variant[tc_size_class(n)];
@@ -420,24 +423,23 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                     SideStream *S = nullptr;
                     if (two) {
                         e = side_stream(&S);
-                        if (e == cudaSuccess) e = cudaEventRecord(S->ready, C.st);
-                        if (e == cudaSuccess) e = cudaStreamWaitEvent(S->st, S->ready, 0);
+                        if (e != cudaSuccess) break;
                     }
-                    int k = 0;
+                    const cudaStream_t gs = two ? S->st : C.st;
+                    int k = 0, last = 0;
                     for (int64_t bb0 = 0; bb0 < n && e == cudaSuccess; bb0 += C.L.g3_nb, ++k) {
                         const int nb = (int)std::min<int64_t>(C.L.g3_nb, n - bb0);
                         const int h = two ? (k & 1) : 0;
                         char *sl = C.ws + C.L.g3_off + (size_t)h * C.L.g3_stride * C.L.g3_nb;
                         float *sc = (float *)(sl + planes * plane_bytes * C.L.g3_nb);
-                        cudaStream_t ss = two ? S->st : C.st;
-                        if (two && k >= 2) e = cudaStreamWaitEvent(ss, S->gemm_done[h], 0);
+                        if (two && k >= 2) e = cudaStreamWaitEvent(C.st, S->gemm_done[h], 0);
                         if (e != cudaSuccess) break;
                         // symmetric sources are read along rows (A(i, j) = M[j][i])
                         auto row_form = [&](const Term &t) { return P.slots[t.mat].symmetric ? 1 : t.trans; };
                         e = launch_split_g3(C.ptr(op.A.mat), C.fp64, row_form(op.A), C.vec(op.u), C.ptr(op.Ab.mat),
-                                            row_form(op.Ab), bb0, nb, n, C.L.ldp_slices, lead, planes, sl, sc, ss);
-                        if (e == cudaSuccess && two) e = cudaEventRecord(S->split_done[h], ss);
-                        if (e == cudaSuccess && two) e = cudaStreamWaitEvent(C.st, S->split_done[h], 0);
+                                            row_form(op.Ab), bb0, nb, n, C.L.ldp_slices, lead, planes, sl, sc, C.st);
+                        if (e == cudaSuccess && two) e = cudaEventRecord(S->split_done[h], C.st);
+                        if (e == cudaSuccess && two) e = cudaStreamWaitEvent(gs, S->split_done[h], 0);
                         if (e != cudaSuccess) break;
                         TcGemmArgs g{};
                         g.n = n;
@@ -460,11 +462,15 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                         g.transWbd = tr(op.Wbd);
                         g.ub = C.vec(op.ub);
                         g.group_rows = kGroupRows[var & 3];
-                        if (P.precision == USTAT_BF16X3) e = launch_gemm_bf16x3(g, (var >> 2) & 3, C.st);
-                        else if (P.precision == USTAT_BF16X5) e = launch_gemm_bf16x5(g, C.st);
-                        else e = launch_gemm_bf16x4(g, (var >> 2) & 3, C.st);
-                        if (e == cudaSuccess && two) e = cudaEventRecord(S->gemm_done[h], C.st);
+                        if (P.precision == USTAT_BF16X3) e = launch_gemm_bf16x3(g, (var >> 2) & 3, gs);
+                        else if (P.precision == USTAT_BF16X5) e = launch_gemm_bf16x5(g, gs);
+                        else e = launch_gemm_bf16x4(g, (var >> 2) & 3, gs);
+                        if (e == cudaSuccess && two) e = cudaEventRecord(S->gemm_done[h], gs);
+                        last = h;
                     }
+                    // join: the caller's stream waits for the last GEMM (the second
+                    // stream runs its GEMMs in order)
+                    if (e == cudaSuccess && two) e = cudaStreamWaitEvent(C.st, S->gemm_done[last], 0);
                     break;
                 }
                 SimtGemmArgs g{};

@@ -1006,6 +1006,25 @@ cudaError_t launch_split_g3(const void *Mv, bool wide, int trans, const double *
                             int64_t bb0, int nb, int64_t n, int64_t ldp, int lead_bits, int planes, void *slices,
                             float *scales, cudaStream_t s) {
     if (nb < 1 || nb > 65535) return cudaErrorInvalidValue;
+    {
+        // The split of the next batch runs beside the persistent GEMM, which holds
+        // most of each SM's shared memory: these kernels ask for the same L1 /
+        // shared-memory split, so that their CTAs can share an SM with the GEMM's.
+        static bool carve[64] = {false};
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        if (!carve[dev]) {
+            const void *fns[] = {(const void *)split_rows_g3_kernel, (const void *)split_rows_g3_wide_kernel,
+                                 (const void *)operand_cols_kernel<true, double>,
+                                 (const void *)operand_cols_kernel<true, float>};
+            for (const void *f : fns) {
+                cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                                     (int)cudaSharedmemCarveoutMaxShared);
+                if (e != cudaSuccess) return e;
+            }
+            carve[dev] = true;
+        }
+    }
     if (wide) {
         if (trans) {
             dim3 grid((unsigned)((n + 7) / 8), (unsigned)nb);
