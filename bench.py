@@ -35,6 +35,9 @@ WORKLOADS = {
                                "0, all 52 partitions",
     "k4_cycle_rbf": "m=6 kernel graph K4 on vertices 1-4 plus edges 4-5, 5-6, 6-1 (treewidth 3), RBF K = "
                     "exp(-||x-y||^2/(2d)), X n=1024 x d=32 iid N(0,1) float64 seed 0, all 203 partitions",
+    "motifs4_er": "induced counts of the six connected 4-vertex motifs (3-star, path, paw, 4-cycle, diamond, "
+                  "4-clique; the paper's r3..r8) in an Erdos-Renyi graph G(n=2000, p=0.1) (seed 0): kernel A on the "
+                  "motif's edges, B = 1 - A on the other pairs, all 15 partitions each; 6 U-statistics per step",
     "batched": "512 independent samples, n uniform in [256, 4096] (seed 0), X_i n_i x 16 iid N(0,1) float64 "
                "(seed 1000+i), each evaluated for the m=4 4-cycle and the m=5 5-cycle RBF kernels (15 and 52 "
                "partitions): 1024 U-statistics per step, one captured CUDA graph per kernel graph",
@@ -338,6 +341,161 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+MOTIF_N, MOTIF_P = 2000, 0.1
+
+
+def motif_oracle_sample(budget_s=20.0):
+    """The oracle on the six connected 4-vertex motifs of G(n_s, 0.1), n_s doubled
+    from 32 while the next size is predicted (n^4 growth of the treewidth-3 step)
+    to take under ``budget_s``; seconds per motif at n_s and n_s."""
+    import numpy as np
+
+    import synth
+    from oracle import ustat_oracle as uo
+
+    def run(ns):
+        A = synth.er_adjacency(ns, MOTIF_P, 0)
+        t0 = time.perf_counter()
+        for nm in synth.CONNECTED4:
+            g, fn = synth.motif_graph(nm)
+            uo.ustat(g, synth.motif_factors(fn, A), np.zeros((ns, 1)))
+        return (time.perf_counter() - t0) / len(synth.CONNECTED4)
+
+    ns = 32
+    t = run(ns)
+    while 2 * ns <= MOTIF_N and t * 16 * len(synth.CONNECTED4) < budget_s:
+        ns *= 2
+        t = run(ns)
+    return t, ns
+
+
+def run_motifs(args):
+    """Motif counting (the paper's 4-vertex motif example at its size): every step
+    counts the six connected 4-vertex motifs of one graph, six U-statistics whose
+    treewidth-3 steps run on the tensor cores; counts of a 0 / 1 matrix are exact
+    integers."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2508_12627_gb300 import build as B
+    B.build()
+    from paper_2508_12627_gb300 import motifs, ustat as us
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    args.steps = min(args.steps, 20)   # a step is about 0.7 s
+    n = MOTIF_N
+    A = synth.er_adjacency(n, MOTIF_P, 0)
+    mc = motifs.MotifCounter(A, precision=args.precision, device=dev)
+    todo = [synth.MOTIFS[nm] for nm in synth.CONNECTED4]
+    outs = []
+    for k, e in todo:
+        p, _, _ = mc.plan(k, e)
+        if args.variant is not None:
+            p.set_variant(args.variant)
+        outs.append(torch.empty(2 + p.info["n_parts"], dtype=torch.float64, device=dev))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        return [mc.launch(k, e, o, stream) for (k, e), o in zip(todo, outs)]
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    us.profile_enable(True)
+    us.profile_collect()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        auts = step()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    us.profile_enable(False)
+    prof = us.profile_collect()
+    clk = clocks.stop()
+    tot_ms = float(sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)))
+    evals = len(todo)
+    value = evals * args.steps / (tot_ms / 1e3)
+    U = [float(o[0].item()) for o in outs]
+    counts = {nm: u / a for nm, u, a in zip(synth.CONNECTED4, U, auts)}
+    exact = all(u % a == 0 and abs(u) < 2.0 ** 53 for u, a in zip(U, auts))
+
+    # roofline: the treewidth-3 steps (n products of n x n x n per step, 2 n^4
+    # flops), each timed as a whole by the library's per-operation events
+    peaks, peak_src = load_peaks()
+    products = {"bf16x3": 6.0, "bf16x4": 10.0, "bf16x5": 15.0, "tf32": 2.0}.get(args.precision)
+    g3_ms, _ = prof.get("gemm3", (0.0, 0))
+    g3_ops = args.steps * sum(mc.plan(k, e)[0].info["n_gemm3"] for k, e in todo)
+    roof = None
+    if products and g3_ms > 0.0 and g3_ops:
+        sustained = tot_ms >= 500.0
+        bf16 = peaks.get("bf16_tflops_sustained", 1700.0) if sustained else peaks.get("bf16_tflops", 1900.0)
+        per = g3_ms / g3_ops / 1e3
+        achieved = 2.0 * float(n) ** 4 / per / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": bf16 / products, "unit": "TFLOP/s",
+                "frac": achieved / (bf16 / products), "traffic": None,
+                "kernel": "tc_gemm_kernel (%s), one s = 3 step of batched launches" % args.precision,
+                "peak_note": "%s bf16 dense %.1f TFLOP/s (%s) / %g tensor products per algorithmic multiply-add"
+                             % (peak_src, bf16, "sustained" if sustained else "burst", products),
+                "per_launch_ms": per * 1e3}
+    fl = sum(mc.plan(k, e)[0].flops(n)[0] for k, e in todo)
+
+    # end to end: A and B from pinned host memory, the six counts, U back to the host
+    Ah = torch.from_numpy(A).pin_memory()
+    Bh = torch.from_numpy(1.0 - A).pin_memory()
+    Uh = torch.empty((evals, 2), dtype=torch.float64).pin_memory()
+    ke = min(args.steps, 5)
+    t1 = time.perf_counter()
+    for _ in range(ke):
+        mc.set_graph(Ah, Bh, non_blocking=True)
+        step()
+        for i, o in enumerate(outs):
+            Uh[i].copy_(o[:2], non_blocking=True)
+        stream.synchronize()
+    e2e_s = (time.perf_counter() - t1) / ke
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        t_s, ns = motif_oracle_sample()
+        scale = sum(mc.plan(k, e)[0].flops(n)[1] for k, e in todo) / sum(
+            mc.plan(k, e)[0].flops(ns)[1] for k, e in todo)
+        cpu = {"value": 1.0 / (t_s * scale), "unit": "evals/s", "cores": host_cores(), "kind": "oracle",
+               "sample": "the six motif counts of G(n=%d, 0.1), %.2f s per count, scaled by the ratio %.3g of the "
+                         "unshared elimination flops at n=%d" % (ns, t_s, scale, n)}
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS["motifs4_er"], "n": n, "p": MOTIF_P, "precision": args.precision,
+                   "gemm_variant": args.variant if args.variant is not None else "default",
+                   "l2": "flushed (256 MiB write) before every timed step", "launch": "eager, one stream",
+                   "parallelism": "single"},
+        "tflops": {"algorithmic_plan": fl * args.steps / (tot_ms / 1e3) / 1e12},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": evals / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": 2 * n * n * 8,
+                "d2h_bytes_per_step": evals * 16},
+        "gpu_launches": int(sum(c for (_, c) in prof.values())),
+        "clocks": clk,
+        "counts": counts,
+        "counts_exact_integers": exact,
+        "wall_s_timed_region": wall,
+        "profile": {k_: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+                    for k_, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -362,6 +520,9 @@ def main():
         return
     if args.workload == "batched":
         run_batched(args)
+        return
+    if args.workload == "motifs4_er":
+        run_motifs(args)
         return
 
     import numpy as np
@@ -471,13 +632,14 @@ def main():
     entries = [(n * (n + 1) / 2 if "sym=1" in l else n * n) for l in gemm_lines]
     alg_flops = 2.0 * n * (sum(entries) / max(1, len(entries)))
     kernel_note = "tc_gemm_kernel (%s)" % args.precision
-    g3_ms, g3_cnt = prof.get("gemm3", (0.0, 0))
+    g3_ms, _ = prof.get("gemm3", (0.0, 0))
     if g3_ms > g_ms:
         # the n^4 steps dominate: one step is n products of n x n x n (2 n^4
         # flops), timed as a whole (its batched GEMM launches and the operand
         # splits that overlap them)
-        g_ms, g_cnt = g3_ms, g3_cnt
-        per_launch_s = (g3_ms / g3_cnt) / 1e3
+        g_cnt = eng.plan.info["n_gemm3"] * args.steps
+        g_ms = g3_ms
+        per_launch_s = (g3_ms / g_cnt) / 1e3
         alg_flops = 2.0 * float(n) ** 4
         kernel_note = "tc_gemm_kernel (%s), one s = 3 step of batched launches" % args.precision
     # the burst peak for a kernel in a short timed region, the sustained one (a

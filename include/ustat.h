@@ -373,7 +373,8 @@ int ustat_eval_noalloc(ustat_plan_t *plan, const void *X, int x_dtype, int64_t n
  * device operation launched by ustat_eval on that thread is bracketed by a pair
  * of CUDA events on the evaluation stream.  ustat_profile_collect() waits for
  * the recorded events, adds their durations per operation kind into
- * ms[kind] and launch counts into launches[kind] (arrays of ustat_profile_kinds()
+ * ms[kind] and the kernel launches they made into launches[kind] (one per
+ * operation, two per batch of a treewidth-3 step; arrays of ustat_profile_kinds()
  * entries, may be NULL), names the kinds through ustat_profile_kind_name(), and
  * resets the record.  Events are created once and reused; no device memory is
  * allocated.

@@ -31,6 +31,7 @@ constexpr int kProfXconvert = OP_COUNT, kProfCombine = OP_COUNT + 1, kProfKinds 
 struct ProfRec {
     int kind;
     cudaEvent_t a, b;
+    int kernels;
 };
 struct Profiler {
     bool on = false;
@@ -50,7 +51,8 @@ thread_local Profiler g_prof;
 
 struct ProfScope {
     cudaStream_t st;
-    ProfRec r{-1, nullptr, nullptr};
+    ProfRec r{-1, nullptr, nullptr, 1};
+    int kernels = 1;   // kernel launches of the operation (set by operations that make several)
     ProfScope(int kind, cudaStream_t s) : st(s) {
         if (!g_prof.on) return;
         r.kind = kind;
@@ -61,6 +63,7 @@ struct ProfScope {
     ~ProfScope() {
         if (r.kind < 0 || !r.a || !r.b) return;
         cudaEventRecord(r.b, st);
+        r.kernels = kernels;
         g_prof.recs.push_back(r);
     }
 };
@@ -468,6 +471,7 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                         if (e == cudaSuccess && two) e = cudaEventRecord(S->gemm_done[h], gs);
                         last = h;
                     }
+                    ps.kernels = 2 * k;   // a split and a GEMM per batch
                     // join: the caller's stream waits for the last GEMM (the second
                     // stream runs its GEMMs in order)
                     if (e == cudaSuccess && two) e = cudaStreamWaitEvent(C.st, S->gemm_done[last], 0);
@@ -795,7 +799,7 @@ int ustat_profile_collect(double *ms, int *launches) {
         e = cudaEventElapsedTime(&t, r.a, r.b);
         if (e != cudaSuccess) return cuda_fail(e);
         if (ms) ms[r.kind] += t;
-        if (launches) launches[r.kind] += 1;
+        if (launches) launches[r.kind] += r.kernels;
     }
     g_prof.recs.clear();
     g_prof.used = 0;

@@ -163,3 +163,72 @@ def random_connected_graph(rng: np.random.Generator, m: int, p: float, max_unary
     nu = int(rng.integers(0, max_unary + 1))
     unary = [(int(v), 1) for v in rng.choice(m, nu, replace=False)]
     return Graph(m, edges, unary)
+
+
+# --------------------------------------------------------------------------------------
+# Motif counts (Section 4.2 and its appendix): an Erdos-Renyi adjacency matrix A and
+# B = 1 - A; an induced motif r on k vertices is the U-statistic of the kernel that
+# puts A on the motif's edges and B on every other pair, divided by |Aut(r)|.
+# --------------------------------------------------------------------------------------
+
+def er_adjacency(n: int, p: float, seed: int) -> np.ndarray:
+    """Adjacency matrix of G(n, p): each of the n (n - 1) / 2 pairs is an edge
+    independently with probability p (the pair i < j decided by the draw in row
+    i, column j).  Symmetric, 0 / 1, float64, zero diagonal."""
+    rng = np.random.default_rng(seed)
+    A = np.zeros((n, n), dtype=np.float64)
+    cols = np.arange(n)
+    for r0 in range(0, n, 1024):
+        r1 = min(n, r0 + 1024)
+        blk = rng.random((r1 - r0, n)) < p
+        blk &= cols[None, :] > np.arange(r0, r1)[:, None]
+        A[r0:r1] = blk
+    A += A.T
+    return A
+
+
+# name: (k, edges of the motif on vertices 0..k-1).  The eleven graphs on four
+# vertices and the four on three, up to isomorphism; the paper's r1..r8 are
+# vshape, triangle, star3, path4, paw, cycle4, diamond, clique4.
+MOTIFS = {
+    "empty3": (3, []),
+    "edge3": (3, [(0, 1)]),
+    "vshape": (3, [(0, 1), (1, 2)]),
+    "triangle": (3, [(0, 1), (1, 2), (0, 2)]),
+    "empty4": (4, []),
+    "edge4": (4, [(0, 1)]),
+    "matching4": (4, [(0, 1), (2, 3)]),
+    "vshape4": (4, [(0, 1), (1, 2)]),
+    "triangle4": (4, [(0, 1), (1, 2), (0, 2)]),
+    "star3": (4, [(0, 1), (0, 2), (0, 3)]),
+    "path4": (4, [(0, 1), (1, 2), (2, 3)]),
+    "paw": (4, [(0, 1), (0, 2), (1, 2), (2, 3)]),
+    "cycle4": (4, [(0, 1), (1, 2), (2, 3), (0, 3)]),
+    "diamond": (4, [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3)]),
+    "clique4": (4, [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]),
+}
+CONNECTED4 = ["star3", "path4", "paw", "cycle4", "diamond", "clique4"]
+
+
+def motif_graph(name: str):
+    """The kernel graph of an induced motif: an edge (a, b) for every pair of the
+    k vertices, with factor "A" on the motif's edges and "B" elsewhere.  Returns
+    (Graph, the matrix name of each factor id)."""
+    k, medges = MOTIFS[name]
+    on = {frozenset(e) for e in medges}
+    names = []
+    edges = []
+    for a in range(k):
+        for b in range(a + 1, k):
+            s = "A" if frozenset((a, b)) in on else "B"
+            if s not in names:
+                names.append(s)
+            edges.append((a, b, names.index(s)))
+    return Graph(k, edges), names
+
+
+def motif_factors(names, A: np.ndarray, B: np.ndarray | None = None) -> list:
+    """MATRIX factors for a motif graph's factor names; B = 1 - A unless given."""
+    if "B" in names and B is None:
+        B = 1.0 - A
+    return [Factor(MATRIX, 1.0, A if s == "A" else B) for s in names]
