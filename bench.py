@@ -38,6 +38,9 @@ WORKLOADS = {
     "motifs4_er": "induced counts of the six connected 4-vertex motifs (3-star, path, paw, 4-cycle, diamond, "
                   "4-clique; the paper's r3..r8) in an Erdos-Renyi graph G(n=2000, p=0.1) (seed 0): kernel A on the "
                   "motif's edges, B = 1 - A on the other pairs, all 15 partitions each; 6 U-statistics per step",
+    "dcov_sectors": "squared distance covariance dCov^2 of all 55 pairs among 11 synthetic sector return "
+                    "matrices (n=138 months, 20-70 stocks each, market and sector factors plus t(4) noise, seed 0), "
+                    "each as four exact U-statistics of the two distance matrices: 220 U-statistics per step",
     "batched": "512 independent samples, n uniform in [256, 4096] (seed 0), X_i n_i x 16 iid N(0,1) float64 "
                "(seed 1000+i), each evaluated for the m=4 4-cycle and the m=5 5-cycle RBF kernels (15 and 52 "
                "partitions): 1024 U-statistics per step, one captured CUDA graph per kernel graph",
@@ -496,6 +499,132 @@ def run_motifs(args):
     print(json.dumps(line), flush=True)
 
 
+def run_dcov(args):
+    """dCov^2 of every pair of the 11 sector return matrices at n = 138 (the
+    distance-covariance example's size): four U-statistics per pair, launched
+    eagerly on one stream; the distance matrices are computed on the host."""
+    import math
+
+    import numpy as np
+    import torch
+
+    import synth
+    from oracle import ustat_oracle as uo
+    from paper_2508_12627_gb300 import build as B
+    B.build()
+    from paper_2508_12627_gb300 import dcov, ustat as us
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    R = synth.sector_returns()
+    n = R[0].shape[0]
+    Dh = [dcov.distances(r) for r in R]
+    Dd = [torch.from_numpy(d).to(dev) for d in Dh]
+    pairs = [(i, j) for i in range(len(R)) for j in range(i + 1, len(R))]
+    dc = dcov.DCov2(n, precision=args.precision, device=dev)
+    outs = [[torch.empty_like(o) for o in dc.out] for _ in pairs]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        for (i, j), o in zip(pairs, outs):
+            dc.launch(Dd[i], Dd[j], o, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    tot_ms = float(sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)))
+    evals = 4 * len(pairs)
+    value = evals * args.steps / (tot_ms / 1e3)
+    vals = [dc.combine([float(x[0].item()) for x in o]) for o in outs]
+
+    # per-operation profile of one more step (not timed above)
+    us.profile_enable(True)
+    us.profile_collect()
+    step()
+    torch.cuda.synchronize()
+    us.profile_enable(False)
+    prof = us.profile_collect()
+    launches = sum(c for (_, c) in prof.values())
+    peaks, peak_src = load_peaks()
+    products = {"bf16x3": 6.0, "bf16x4": 10.0, "bf16x5": 15.0, "tf32": 2.0}.get(args.precision)
+    g_ms, g_cnt = prof.get("gemm", (0.0, 0))
+    roof = None
+    if products and g_cnt:
+        per = g_ms / g_cnt / 1e3
+        achieved = 2.0 * float(n) ** 3 / per / 1e12
+        peak = peaks.get("bf16_tflops", 1900.0) / products
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "tc_gemm_kernel (%s)" % args.precision,
+                "peak_note": "%s bf16 dense %.1f TFLOP/s (burst) / %g tensor products per multiply-add; at n = %d "
+                             "every kernel is a few microseconds and the step is bound by launch latency"
+                             % (peak_src, peaks.get("bf16_tflops", 1900.0), products, n),
+                "per_launch_ms": per * 1e3}
+
+    # end to end: the 11 distance matrices from pinned host memory, 220 U-statistics, the U_sums back
+    Dp = [torch.from_numpy(d).pin_memory() for d in Dh]
+    Uh = torch.empty((len(pairs), 4), dtype=torch.float64).pin_memory()
+    ke = min(args.steps, 20)
+    t1 = time.perf_counter()
+    for _ in range(ke):
+        for d, s_ in zip(Dd, Dp):
+            d.copy_(s_, non_blocking=True)
+        step()
+        for p_, o in enumerate(outs):
+            for t_, x in enumerate(o):
+                Uh[p_, t_].copy_(x[0], non_blocking=True)
+        stream.synchronize()
+    e2e_s = (time.perf_counter() - t1) / ke
+
+    cpu = None
+    err = None
+    if not args.no_cpu_baseline:
+        t2 = time.perf_counter()
+        ref = []
+        for i, j in pairs:
+            F = [synth.Factor(synth.MATRIX, 1.0, Dh[i]), synth.Factor(synth.MATRIX, 1.0, Dh[j])]
+            u = [uo.ustat(synth.Graph(k, e), F, np.zeros((n, 1)))["U_sum"] for _, k, e in dcov.TERMS]
+            ref.append(math.fsum(c(n) * x for (c, _, _), x in zip(dcov.TERMS, u)) / math.perm(n, 4))
+        dt = time.perf_counter() - t2
+        cpu = {"value": evals / dt, "unit": "evals/s", "cores": host_cores(), "kind": "oracle",
+               "sample": "the whole step: all 55 pairs, four U-statistics each, %.2f s" % dt}
+        err = {"dcov2_max_abs_err_over_scale": max(abs(v - r) / sc for (v, sc), r in zip(vals, ref))}
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS["dcov_sectors"], "n": n, "pairs": len(pairs), "precision": args.precision,
+                   "l2": "flushed (256 MiB write) before every timed step", "launch": "eager, one stream",
+                   "parallelism": "single"},
+        "dcov2_per_s": len(pairs) * args.steps / (tot_ms / 1e3),
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": evals / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": int(sum(d.nbytes for d in Dh)),
+                "d2h_bytes_per_step": 8 * evals},
+        "gpu_launches": int(launches * args.steps),
+        "clocks": clk,
+        "rel_err_vs_oracle": err,
+        "dcov2_first_pairs": [v for v, _ in vals[:3]],
+        "wall_s_timed_region": wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -523,6 +652,9 @@ def main():
         return
     if args.workload == "motifs4_er":
         run_motifs(args)
+        return
+    if args.workload == "dcov_sectors":
+        run_dcov(args)
         return
 
     import numpy as np

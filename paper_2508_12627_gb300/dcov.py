@@ -1,0 +1,102 @@
+"""Squared distance covariance as a combination of exact U-statistics (the
+distance-covariance example of Section 4.3).  With a_ij = ||x_i - x_j|| and
+b_ij = ||y_i - y_j||, the paper writes dCov^2 as the order-4 U-statistic
+
+    dCov^2 = 1/(n)_4 * sum over ordered distinct (i, j, k, l) of
+             a_ij b_kl + a_ij b_ij - a_ij b_ik - a_ij b_jl .
+
+A product that does not touch every one of the four indices sums the untouched
+ones out over the values distinct from the others: a_ij b_ij leaves two
+(a factor (n - 2)(n - 3)), a_ij b_ik and a_ij b_jl leave one (a factor n - 3).
+So dCov^2 is a combination of four kernel graphs, each evaluated exactly by the
+engine from the two distance matrices (MATRIX factors):
+
+    (n)_4 dCov^2 = U_4[a_01 b_23] + (n-2)(n-3) U_2[a_01 b_01]
+                   - (n-3) U_3[a_01 b_02] - (n-3) U_3[a_01 b_12]
+
+where U_k[.] is the sum over ordered distinct k-tuples.  The distance matrices
+are computed on the host from X and Y (float64 differences); the four U_sums
+come back to the host, which forms the combination with a compensated sum.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+from . import ustat as us
+
+# (coefficient in n, order k, edges (a, b, factor): factor 0 = a, 1 = b)
+TERMS = [
+    (lambda n: 1.0, 4, [(0, 1, 0), (2, 3, 1)]),
+    (lambda n: float((n - 2) * (n - 3)), 2, [(0, 1, 0), (0, 1, 1)]),
+    (lambda n: -float(n - 3), 3, [(0, 1, 0), (0, 2, 1)]),
+    (lambda n: -float(n - 3), 3, [(0, 1, 0), (1, 2, 1)]),
+]
+
+
+class _Graph:
+    def __init__(self, m, edges):
+        self.m = m
+        self.edges = edges
+        self.unary = []
+
+
+def distances(Z):
+    """n x n Euclidean distances between the rows of Z (float64)."""
+    Z = np.asarray(Z, dtype=np.float64)
+    if Z.ndim == 1:
+        Z = Z[:, None]
+    D = Z[:, None, :] - Z[None, :, :]
+    return np.sqrt(np.einsum("ijk,ijk->ij", D, D))
+
+
+class DCov2:
+    """The four plans for sample size n, device copies of a and b, one workspace."""
+
+    def __init__(self, n, precision="fp64", device="cuda:0"):
+        if n < 4:
+            raise ValueError("dCov^2 needs n >= 4")
+        self.n = n
+        self.device = torch.device(device)
+        self.plans = [us.Plan(_Graph(k, e), [us.MATRIX, us.MATRIX], precision=precision) for _, k, e in TERMS]
+        self.coef = [c(n) for c, _, _ in TERMS]
+        need = max(256, max(p.workspace_bytes(n, 1) for p in self.plans))
+        self.ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+        self.a = torch.empty((n, n), dtype=torch.float64, device=self.device)
+        self.b = torch.empty_like(self.a)
+        self.X = torch.zeros((n, 1), dtype=torch.float64, device=self.device)
+        self.out = [torch.empty(2 + p.info["n_parts"], dtype=torch.float64, device=self.device) for p in self.plans]
+
+    def set(self, a, b, non_blocking=False):
+        """Distance matrices (numpy arrays or host / device tensors), n x n."""
+        for dst, src in ((self.a, a), (self.b, b)):
+            if not isinstance(src, torch.Tensor):
+                src = torch.from_numpy(np.ascontiguousarray(src, dtype=np.float64))
+            dst.copy_(src, non_blocking=non_blocking)
+
+    def launch(self, a=None, b=None, out=None, stream=None):
+        """Enqueue the four U-statistics: of the device distance matrices a and b
+        (n x n float64; default: the copies made by set()) into out (four float64
+        device tensors of 2 + Bell(k); default: this object's)."""
+        st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        a = self.a if a is None else a
+        b = self.b if b is None else b
+        facs = [(us.MATRIX, 1.0, a.data_ptr()), (us.MATRIX, 1.0, b.data_ptr())]
+        for p, o in zip(self.plans, self.out if out is None else out):
+            us.ustat_eval(p, self.X.data_ptr(), 0, self.n, 1, facs, self.ws.data_ptr(), self.ws.numel(), st,
+                          o.data_ptr(), o.data_ptr() + 16)
+
+    def combine(self, U_sums):
+        """dCov^2 from the four U_sums, and the scale sum |coef U| / (n)_4 against
+        which its rounding is judged."""
+        ff = float(math.perm(self.n, 4))
+        terms = [c * u for c, u in zip(self.coef, U_sums)]
+        return math.fsum(terms) / ff, math.fsum(abs(t) for t in terms) / ff
+
+    def evaluate(self, X, Y):
+        """dCov^2(X, Y) for n paired samples (rows); returns (value, scale)."""
+        self.set(distances(X), distances(Y))
+        self.launch()
+        return self.combine([float(o[0].item()) for o in self.out])

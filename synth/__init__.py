@@ -232,3 +232,26 @@ def motif_factors(names, A: np.ndarray, B: np.ndarray | None = None) -> list:
     if "B" in names and B is None:
         B = 1.0 - A
     return [Factor(MATRIX, 1.0, A if s == "A" else B) for s in names]
+
+
+# --------------------------------------------------------------------------------------
+# Distance covariance (Section 4.3): a synthetic stand-in for monthly log-returns of the
+# stocks of 11 sectors over n = 138 months.
+# --------------------------------------------------------------------------------------
+
+def sector_returns(n: int = 138, sectors: int = 11, seed: int = 0) -> list:
+    """One n x p_k matrix per sector, p_k uniform in [20, 70]: a market factor
+    (sd 0.04) and a sector factor (sd 0.03) with loadings uniform in [0.5, 1.5],
+    plus Student-t(4) noise scaled by 0.05; float64."""
+    rng = np.random.default_rng(seed)
+    dims = rng.integers(20, 71, sectors)
+    market = 0.04 * rng.standard_normal(n)
+    out = []
+    for k in range(sectors):
+        s = 0.03 * rng.standard_normal(n)
+        p = int(dims[k])
+        beta = rng.uniform(0.5, 1.5, p)
+        gamma = rng.uniform(0.5, 1.5, p)
+        eps = 0.05 * rng.standard_t(4.0, (n, p))
+        out.append(market[:, None] * beta[None, :] + s[:, None] * gamma[None, :] + eps)
+    return out
