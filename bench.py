@@ -41,6 +41,10 @@ WORKLOADS = {
     "dcov_sectors": "squared distance covariance dCov^2 of all 55 pairs among 11 synthetic sector return "
                     "matrices (n=138 months, 20-70 stocks each, market and sector factors plus t(4) noise, seed 0), "
                     "each as four exact U-statistics of the two distance matrices: 220 U-statistics per step",
+    "hoif_chain": "HOIF chain U-statistics U(h_j), j = 2..7 (chains g...g f of j - 1 pairwise factors, all Bell(j) "
+                  "partitions each), n=10000: phi(Z) = sqrt(2) Z with Z ~ N(0, I_16), A ~ Bernoulli(1/2), "
+                  "Y = Z.beta + N(0,1) (seed 0); G = Psi Psi', F = Psi Theta' formed on the host; 6 U-statistics "
+                  "per step",
     "batched": "512 independent samples, n uniform in [256, 4096] (seed 0), X_i n_i x 16 iid N(0,1) float64 "
                "(seed 1000+i), each evaluated for the m=4 4-cycle and the m=5 5-cycle RBF kernels (15 and 52 "
                "partitions): 1024 U-statistics per step, one captured CUDA graph per kernel graph",
@@ -625,6 +629,135 @@ def run_dcov(args):
     print(json.dumps(line), flush=True)
 
 
+def run_hoif(args):
+    """The HOIF example's chain U-statistics at the largest n of its table: every
+    step evaluates U(h_j) for j = 2..7 from the factor matrices G and F, each
+    order timed on its own as well."""
+    import numpy as np
+    import torch
+
+    import synth
+    from oracle import ustat_oracle as uo
+    from paper_2508_12627_gb300 import build as B
+    B.build()
+    from paper_2508_12627_gb300 import hoif, ustat as us
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    args.steps = min(args.steps, 5)   # a step is about a second
+    n = 10000
+    orders = list(range(2, 8))
+    phi, A, Y = synth.hoif_sample(n, seed=0)
+    G, F = hoif.factor_matrices(phi, A, Y)
+    hc = hoif.HoifChains(n, orders=orders, precision=args.precision, device=dev)
+    hc.set(G, F)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        for j in orders:
+            hc.launch(j, stream)
+    torch.cuda.synchronize()
+    ev = {j: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)] for j in orders}
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    us.profile_enable(True)
+    us.profile_collect()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        for j in orders:
+            a_, b_ = ev[j][k]
+            a_.record(stream)
+            hc.launch(j, stream)
+            b_.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    us.profile_enable(False)
+    prof = us.profile_collect()
+    clk = clocks.stop()
+    per_order = {j: sum(a_.elapsed_time(b_) for a_, b_ in ev[j]) / args.steps for j in orders}
+    tot_ms = sum(per_order.values()) * args.steps
+    value = len(orders) * args.steps / (tot_ms / 1e3)
+    U = {j: float(hc.out[j][0].item()) for j in orders}
+
+    peaks, peak_src = load_peaks()
+    products = {"bf16x3": 6.0, "bf16x4": 10.0, "bf16x5": 15.0, "tf32": 2.0}.get(args.precision)
+    g_ms, g_cnt = prof.get("gemm", (0.0, 0))
+    roof = None
+    if products and g_cnt:
+        sustained = tot_ms >= 500.0
+        bf16 = peaks.get("bf16_tflops_sustained", 1700.0) if sustained else peaks.get("bf16_tflops", 1900.0)
+        per = g_ms / g_cnt / 1e3
+        # a product stored or reduced in full: 2 n^3 flops (symmetric ones count
+        # their upper tiles only, so this is a lower bound on their rate)
+        achieved = 2.0 * float(n) ** 3 / per / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": bf16 / products, "unit": "TFLOP/s",
+                "frac": achieved / (bf16 / products), "traffic": None,
+                "kernel": "tc_gemm_kernel (%s), the n^3 products of all orders" % args.precision,
+                "peak_note": "%s bf16 dense %.1f TFLOP/s (%s) / %g tensor products per multiply-add"
+                             % (peak_src, bf16, "sustained" if sustained else "burst", products),
+                "per_launch_ms": per * 1e3}
+    fl = sum(hc.plans[j][0].flops(n)[0] for j in orders)
+
+    # end to end: G and F from pinned host memory, the six U-statistics, U back
+    Gh = torch.from_numpy(G).pin_memory()
+    Fh = torch.from_numpy(F).pin_memory()
+    Uh = torch.empty((len(orders), 2), dtype=torch.float64).pin_memory()
+    ke = min(args.steps, 3)
+    t1 = time.perf_counter()
+    for _ in range(ke):
+        hc.set(Gh, Fh, non_blocking=True)
+        for i, j in enumerate(orders):
+            hc.launch(j, stream)
+            Uh[i].copy_(hc.out[j][:2], non_blocking=True)
+        stream.synchronize()
+    e2e_s = (time.perf_counter() - t1) / ke
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        def oracle_all(ns):
+            ph, a, y = synth.hoif_sample(ns, seed=0)
+            Gs, Fs = hoif.factor_matrices(ph, a, y)
+            t = time.perf_counter()
+            for j in orders:
+                fs = [synth.Factor(synth.MATRIX, 1.0, Fs)] if j == 2 else [
+                    synth.Factor(synth.MATRIX, 1.0, Gs), synth.Factor(synth.MATRIX, 1.0, Fs)]
+                uo.ustat(synth.hoif_chain_graph(j), fs, np.zeros((ns, 1)))
+            return time.perf_counter() - t
+
+        ns = 64
+        t_s = oracle_all(ns)
+        while 2 * ns <= n and t_s * 8 < 20.0:
+            ns *= 2
+            t_s = oracle_all(ns)
+        scale = sum(hc.plans[j][0].flops(n)[1] for j in orders) / sum(hc.plans[j][0].flops(ns)[1] for j in orders)
+        cpu = {"value": len(orders) / (t_s * scale), "unit": "evals/s", "cores": host_cores(), "kind": "oracle",
+               "sample": "U(h_j), j = 2..7, at n=%d (same distribution), %.2f s, scaled by the ratio %.3g of the "
+                         "unshared elimination flops at n=%d" % (ns, t_s, scale, n)}
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS["hoif_chain"], "n": n, "orders": orders, "precision": args.precision,
+                   "l2": "inputs (two n x n float64 matrices, 1.6 GB) and every product far larger than L2",
+                   "launch": "eager, one stream", "parallelism": "single"},
+        "ms_per_order": per_order,
+        "tflops": {"algorithmic_plan": fl * args.steps / (tot_ms / 1e3) / 1e12},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": len(orders) / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": int(2 * n * n * 8),
+                "d2h_bytes_per_step": 16 * len(orders)},
+        "gpu_launches": int(sum(c for (_, c) in prof.values())),
+        "clocks": clk,
+        "U_sum": U,
+        "wall_s_timed_region": wall,
+        "profile": {k_: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+                    for k_, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -655,6 +788,9 @@ def main():
         return
     if args.workload == "dcov_sectors":
         run_dcov(args)
+        return
+    if args.workload == "hoif_chain":
+        run_hoif(args)
         return
 
     import numpy as np

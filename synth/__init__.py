@@ -255,3 +255,31 @@ def sector_returns(n: int = 138, sectors: int = 11, seed: int = 0) -> list:
         eps = 0.05 * rng.standard_t(4.0, (n, p))
         out.append(market[:, None] * beta[None, :] + s[:, None] * gamma[None, :] + eps)
     return out
+
+
+# --------------------------------------------------------------------------------------
+# Higher-order influence functions (Section 4.1): chain U-statistics of the pairwise
+# factors g(X_1, X_2) = A_1 phi(Z_1)' A_2 phi(Z_2) and f(X_1, X_2) = A_1 phi(Z_1)' phi(Z_2) Y_2.
+# --------------------------------------------------------------------------------------
+
+def hoif_sample(n: int, k: int = 16, seed: int = 0):
+    """An unconfounded observational sample with a k-dimensional dictionary:
+    Z ~ N(0, I_k), treatment A ~ Bernoulli(1/2) independent of Z, outcome
+    Y = Z . beta + N(0, 1) with beta ~ N(0, I_k / k), and phi(Z) = sqrt(2) Z, so
+    that the mean of A phi(Z) phi(Z)' is the identity (the paper's simplifying
+    assumption).  Returns (phi, A, Y): n x k, n, n, float64."""
+    rng = np.random.default_rng(seed)
+    Z = rng.standard_normal((n, k))
+    A = (rng.random(n) < 0.5).astype(np.float64)
+    beta = rng.standard_normal(k) / np.sqrt(k)
+    Y = Z @ beta + rng.standard_normal(n)
+    return np.sqrt(2.0) * Z, A, Y
+
+
+def hoif_chain_graph(j: int) -> Graph:
+    """The kernel graph of h_j (the paper's equation for the HOIF kernel): the
+    chain 0 - 1 - ... - (j-1), factor 0 = g on its first j - 2 edges and factor
+    1 = f on the last one (for j = 2 only f, as factor id 0)."""
+    if j == 2:
+        return Graph(2, [(0, 1, 0)])
+    return Graph(j, [(v, v + 1, 0) for v in range(j - 2)] + [(j - 2, j - 1, 1)])
