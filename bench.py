@@ -565,19 +565,17 @@ def run_dcov(args):
     prof = us.profile_collect()
     launches = sum(c for (_, c) in prof.values())
     peaks, peak_src = load_peaks()
-    products = {"bf16x3": 6.0, "bf16x4": 10.0, "bf16x5": 15.0, "tf32": 2.0}.get(args.precision)
-    g_ms, g_cnt = prof.get("gemm", (0.0, 0))
-    roof = None
-    if products and g_cnt:
-        per = g_ms / g_cnt / 1e3
-        achieved = 2.0 * float(n) ** 3 / per / 1e12
-        peak = peaks.get("bf16_tflops", 1900.0) / products
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "tc_gemm_kernel (%s)" % args.precision,
-                "peak_note": "%s bf16 dense %.1f TFLOP/s (burst) / %g tensor products per multiply-add; at n = %d "
-                             "every kernel is a few microseconds and the step is bound by launch latency"
-                             % (peak_src, peaks.get("bf16_tflops", 1900.0), products, n),
-                "per_launch_ms": per * 1e3}
+    # Every kernel graph of dCov^2 is a forest (treewidth 1): no n^3 product,
+    # only n^2 passes.  Algorithmic bytes: each U-statistic reads its two
+    # distance matrices once, in the storage type of the mode.
+    esz = 8 if args.precision in ("fp64", "bf16x4", "bf16x5") else 4
+    alg_bytes = evals * 2 * n * n * esz
+    achieved = alg_bytes / (tot_ms / args.steps / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
+            "frac": achieved / peaks.get("hbm_gbs", 6800.0), "traffic": None,
+            "kernel": "the whole step (%d launches): n^2 passes over L2-resident 138 x 138 matrices" % launches,
+            "peak_note": "%s HBM copy bandwidth; at n = %d every kernel takes a few microseconds and the step is "
+                         "bound by launch latency, not by memory" % (peak_src, n)}
 
     # end to end: the 11 distance matrices from pinned host memory, 220 U-statistics, the U_sums back
     Dp = [torch.from_numpy(d).pin_memory() for d in Dh]
@@ -688,9 +686,12 @@ def run_hoif(args):
         sustained = tot_ms >= 500.0
         bf16 = peaks.get("bf16_tflops_sustained", 1700.0) if sustained else peaks.get("bf16_tflops", 1900.0)
         per = g_ms / g_cnt / 1e3
-        # a product stored or reduced in full: 2 n^3 flops (symmetric ones count
-        # their upper tiles only, so this is a lower bound on their rate)
-        achieved = 2.0 * float(n) ** 3 / per / 1e12
+        # algorithmic flops of the n^3 products of one step: 2 n per product
+        # entry the algorithm needs (n (n + 1) / 2 entries for a symmetric
+        # product whose reductions are symmetric), averaged over the launches
+        lines = [l for j in orders for l in hc.plans[j][0].describe().splitlines() if " gemm " in l]
+        ent = [(n * (n + 1) / 2 if "sym=1" in l else float(n) * n) for l in lines]
+        achieved = 2.0 * n * (sum(ent) / max(1, len(ent))) / per / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": bf16 / products, "unit": "TFLOP/s",
                 "frac": achieved / (bf16 / products), "traffic": None,
                 "kernel": "tc_gemm_kernel (%s), the n^3 products of all orders" % args.precision,
