@@ -44,12 +44,18 @@ class _Graph:
 
 
 def distances(Z):
-    """n x n Euclidean distances between the rows of Z (float64)."""
+    """n x n Euclidean distances between the rows of Z (float64), from the
+    coordinate differences (no cancellation), a block of rows at a time."""
     Z = np.asarray(Z, dtype=np.float64)
     if Z.ndim == 1:
         Z = Z[:, None]
-    D = Z[:, None, :] - Z[None, :, :]
-    return np.sqrt(np.einsum("ijk,ijk->ij", D, D))
+    n, p = Z.shape
+    out = np.empty((n, n))
+    rows = max(1, (1 << 24) // max(1, n * p))
+    for r0 in range(0, n, rows):
+        D = Z[r0:r0 + rows, None, :] - Z[None, :, :]
+        out[r0:r0 + rows] = np.sqrt(np.einsum("ijk,ijk->ij", D, D))
+    return out
 
 
 class DCov2:

@@ -77,6 +77,17 @@ def test_special_cases():
     assert abs(u_centred(_dist(X @ Q.T + 3.0), b) - u_centred(a, b)) <= 1e-12 * abs(u_centred(a, b))
 
 
+def test_binding_distances_follow_the_definition():
+    pytest.importorskip("torch")
+    from paper_2508_12627_gb300 import dcov
+    rng = np.random.default_rng(5)
+    for n, p in [(138, 40), (700, 60)]:                          # one block, several blocks of rows
+        Z = rng.standard_normal((n, p))
+        D = dcov.distances(Z)
+        assert np.max(np.abs(D - _dist(Z))) <= 1e-13 * np.max(D) and np.array_equal(D, D.T)
+    assert np.array_equal(dcov.distances(np.arange(5.0)), np.abs(np.subtract.outer(np.arange(5.0), np.arange(5.0))))
+
+
 def test_sector_returns_shape():
     R = synth.sector_returns()
     assert len(R) == 11 and all(r.shape[0] == 138 and 20 <= r.shape[1] <= 70 for r in R)
