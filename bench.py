@@ -153,35 +153,145 @@ def host_cores():
     return os.cpu_count() or 1
 
 
-def run_reference(args):
-    """The oracle (FP64 CPU, as it stands) on the host cores: each step is one full
-    evaluation of the workload; the number of timed steps is capped so the run
-    ends within a few minutes."""
+# the reference arm's time limits: the whole run, and one step (a bounded sample)
+REFERENCE_BUDGET_S = 150.0
+REFERENCE_STEP_S = 20.0
+
+
+def max_treewidth(graph):
+    """The largest exact treewidth over the quotients G/pi (the oracle's own
+    functions): the oracle's time grows as n^(M + 1)."""
+    from oracle import ustat_oracle as uo
+    return max(uo.treewidth_bruteforce(max(r) + 1, uo.quotient_edges(graph, r)) for r in uo.set_partitions(graph.m))
+
+
+def _sized(run_at, n_full, n0, expo, step_s):
+    """The largest sample size from n0 doubling up to n_full whose oracle step is
+    predicted (growth n^expo) to take under step_s; returns (n_s, seconds at n_s)."""
+    ns = min(n0, n_full)
+    t = run_at(ns)
+    while ns < n_full:
+        nxt = min(2 * ns, n_full)
+        if t * (nxt / ns) ** expo > step_s:
+            break
+        ns = nxt
+        t = run_at(ns)
+    return ns, t
+
+
+def reference_step(workload, step_s):
+    """One step of the oracle on a bounded sample of the workload: (run, evals of
+    the full step, time scale from the sample to the full step, description)."""
+    import numpy as np
+
     import synth
+    from oracle import ustat_oracle as uo
+
+    def timed(f):
+        def g(*a):
+            t0 = time.perf_counter()
+            f(*a)
+            return time.perf_counter() - t0
+        return g
+
+    if workload == "motifs4_er":
+        def run_at(ns):
+            A = synth.er_adjacency(ns, MOTIF_P, 0)
+            for nm in synth.CONNECTED4:
+                g, fn = synth.motif_graph(nm)
+                uo.ustat(g, synth.motif_factors(fn, A), np.zeros((ns, 1)))
+        ns, _ = _sized(timed(run_at), MOTIF_N, 32, 4, step_s)
+        return (lambda: run_at(ns)), len(synth.CONNECTED4), (MOTIF_N / ns) ** 4, \
+            "the six motif counts at n=%d, time scaled by (%d/%d)^4" % (ns, MOTIF_N, ns)
+    if workload == "hoif_chain":
+        n_full = 10000
+
+        def run_at(ns):
+            phi, a, y = synth.hoif_sample(ns, seed=0)
+            Psi, Theta = a[:, None] * phi, phi * y[:, None]
+            G, F = Psi @ Psi.T, Psi @ Theta.T
+            for j in range(2, 8):
+                fs = [synth.Factor(synth.MATRIX, 1.0, F)] if j == 2 else [
+                    synth.Factor(synth.MATRIX, 1.0, G), synth.Factor(synth.MATRIX, 1.0, F)]
+                uo.ustat(synth.hoif_chain_graph(j), fs, np.zeros((ns, 1)))
+        ns, _ = _sized(timed(run_at), n_full, 64, 3, step_s)
+        return (lambda: run_at(ns)), 6, (n_full / ns) ** 3, \
+            "U(h_j), j = 2..7, at n=%d, time scaled by (%d/%d)^3" % (ns, n_full, ns)
+    if workload == "dcov_sectors":
+        import math
+        R = synth.sector_returns()
+        n = R[0].shape[0]
+        D = [np.sqrt(((r[:, None, :] - r[None, :, :]) ** 2).sum(-1)) for r in R]
+        terms = [(4, [(0, 1, 0), (2, 3, 1)]), (2, [(0, 1, 0), (0, 1, 1)]), (3, [(0, 1, 0), (0, 2, 1)]),
+                 (3, [(0, 1, 0), (1, 2, 1)])]
+        pairs = [(i, j) for i in range(len(R)) for j in range(i + 1, len(R))]
+
+        def run():
+            for i, j in pairs:
+                F = [synth.Factor(synth.MATRIX, 1.0, D[i]), synth.Factor(synth.MATRIX, 1.0, D[j])]
+                u = [uo.ustat(synth.Graph(k, e), F, np.zeros((n, 1)))["U_sum"] for k, e in terms]
+                math.fsum(c * x for c, x in zip([1.0, (n - 2) * (n - 3), -(n - 3), -(n - 3)], u))
+        return run, 4 * len(pairs), 1.0, "the whole step: all %d pairs, four U-statistics each" % len(pairs)
+    if workload == "batched":
+        d = 16
+        ns = [int(v) for v in synth.batched_sizes(512, 256, 4096, 0)]
+        order = [int(i) for i in np.argsort(ns)[:4]]
+        Xs = {i: synth.normal_X(ns[i], d, 1000 + i) for i in order}
+        graphs = [synth.cycle4_graph(), synth.cycle(5)]
+        fac = [synth.Factor(uo.RBF, 2.0 * d, None)]
+
+        def run():
+            for g in graphs:
+                for i in order:
+                    uo.ustat(g, fac, Xs[i])
+        scale = sum(float(v) ** 3 for v in ns) / sum(float(ns[i]) ** 3 for i in order)
+        return run, 2 * len(ns), scale, "the 4 smallest samples (n=%s) for both kernel graphs, time scaled by " \
+            "sum n^3 over all 512 samples / sum n^3 over these" % [ns[i] for i in order]
+    w = synth.workload(workload)
+    expo = max_treewidth(w.graph) + 1
+
+    def run_at(ns):
+        oracle_eval(synth.workload(workload, ns))
+    ns, _ = _sized(timed(run_at), w.n, 64, expo, step_s)
+    ws = synth.workload(workload, ns)
+    if ns == w.n:
+        return (lambda: oracle_eval(ws)), 1, 1.0, "one full evaluation of the workload (n=%d)" % w.n
+    return (lambda: oracle_eval(ws)), 1, (w.n / ns) ** expo, \
+        "one evaluation at n=%d (same distribution), time scaled by (%d/%d)^%d (largest quotient treewidth + 1)" % (
+            ns, w.n, ns, expo)
+
+
+def run_reference(args):
+    """The oracle (FP64 CPU, as it stands) on the host cores: each step is the
+    workload's step on a bounded sample (the full step when it fits the per-step
+    limit), its time scaled to the full step by the oracle's cost growth; the
+    number of timed steps is capped so the run ends within a few minutes."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = synth.workload(args.workload)
+    run, evals, scale, sample = reference_step(args.workload, REFERENCE_STEP_S)
     for _ in range(min(args.warmup, 1)):
-        oracle_eval(w)
+        run()
     times = []
-    budget = 150.0
     t_start = time.perf_counter()
-    for _ in range(args.steps):
-        _, dt = oracle_eval(w)
+    for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        run()
+        dt = time.perf_counter() - t0
         times.append(dt)
-        if time.perf_counter() - t_start + dt > budget:
+        if time.perf_counter() - t_start + dt > REFERENCE_BUDGET_S:
             break
-    tot = sum(times)
-    value = len(times) / tot
+    t_step = sum(times) / len(times) * scale
+    value = evals / t_step
     cores = host_cores()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus,
-            "steps": len(times), "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * tot / len(times),
+            "steps": len(times), "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * t_step,
+            "sample_ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload], "n": w.n, "d": w.d},
+            "config": {"workload": WORKLOADS[args.workload]},
             "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
-                             "sample": "%d full evaluations of the workload (steps capped to ~%ds)" % (
-                                 len(times), int(budget))},
+                             "sample": "%s; %d timed steps (capped to ~%ds)" % (sample, len(times),
+                                                                                 int(REFERENCE_BUDGET_S))},
             "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -60,3 +60,30 @@ def test_reference_arm_prints_on_rank_zero_only(monkeypatch):
     with redirect_stdout(buf):
         bench.run_reference(A())
     assert buf.getvalue() == ""
+
+
+@pytest.mark.parametrize("workload", ["c4_rbf", "triangle_rbf", "k4_cycle_rbf", "path5_chord_linear_tanh",
+                                      "motifs4_er", "hoif_chain", "dcov_sectors", "batched"])
+def test_reference_arm_bounded_sample_for_every_workload(monkeypatch, workload):
+    # every workload's reference line with small time limits: one bounded sample
+    # per step, scaled to the full step, the contract's keys
+    sys.path.insert(0, ROOT)
+    import json
+
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setattr(bench, "REFERENCE_STEP_S", 0.3)
+    monkeypatch.setattr(bench, "REFERENCE_BUDGET_S", 1.0)
+
+    class A:
+        steps, warmup, gpus = 2, 1, 1
+
+    A.workload = workload
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        bench.run_reference(A())
+    line = json.loads(buf.getvalue())
+    assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "evals/s"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["higher_is_better"] is True
+    assert line["ms_per_step"] >= line["sample_ms_per_step"] * 0.999
