@@ -598,10 +598,20 @@ int ustat_plan_shard(const ustat_graph *graph, const ustat_options *opts, int sh
         group_of[i] = group_of[r];
         groups[group_of[i]].push_back(i);
     }
-    // Cost of a set of groups: the program that evaluates that set alone.
+    // Cost of a set of groups: the program that evaluates that set alone.  With
+    // many partitions (m = 7: 877) these estimates are many, and each partition
+    // is lowered along the elimination order the full plan chose for it instead
+    // of searching again; groups without an n^3 product then skip the estimate.
+    const bool many = np > 256;
+    std::vector<std::vector<int>> forced(np);
+    if (many)
+        for (int i = 0; i < np; ++i)
+            if (full.parts[i].evaluated)
+                forced[i].assign(full.parts[i].order, full.parts[i].order + full.parts[i].nblocks);
     auto cost_of = [&](const std::vector<char> &keep, double *c) {
         PlanRequest req;
         req.keep = &keep;
+        if (many) req.forced = &forced;
         Plan gp;
         int e = build_plan(graph, opts, &gp, &req);
         *c = e == USTAT_OK ? shard_cost(gp, n) : 0.0;
@@ -628,7 +638,17 @@ int ustat_plan_shard(const ustat_graph *graph, const ustat_options *opts, int sh
         std::vector<std::vector<char>> keep_of(n_shards, std::vector<char>(np, 0));
         std::vector<double> load(n_shards, 0.0);
         double span = 0.0;
+        const double dn = (double)n;
         for (int gi : by_cost) {
+            if (many && cost[gi] < dn * dn * dn) {
+                // no n^3 product: its n^2 passes go to the least loaded shard
+                int r = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+                shard_of_group[gi] = r;
+                load[r] += cost[gi];
+                span = std::max(span, load[r]);
+                for (int i : groups[gi]) keep_of[r][i] = 1;
+                continue;
+            }
             int best = -1;
             double best_load = 0.0, best_growth = 0.0, best_score = 0.0;
             for (int r = 0; r < n_shards; ++r) {

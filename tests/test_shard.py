@@ -156,3 +156,21 @@ def test_shards_on_one_gpu_sum_to_the_full_result(us, name, n, N, prec):
     assert abs(tot[0] - full["U_sum"]) <= tol * uabs
     ref = uo.ustat(w.graph, w.factors, w.X)
     assert abs(tot[0] - ref["U_sum"]) <= tol * uabs
+
+
+def test_order_seven_chain_shards_cover_once_and_plan_quickly(us):
+    # m = 7 (877 partitions): the estimates lower along the full plan's orders
+    import time
+
+    from paper_2508_12627_gb300 import hoif
+    g, names = hoif.chain_graph(7)
+    t0 = time.time()
+    plans = [us.Plan(g, [us.MATRIX] * len(names), shard=(r, 2, 10000)) for r in range(2)]
+    assert time.time() - t0 < 60.0
+    owner = plans[0].owner
+    assert plans[1].owner == owner and set(owner) == {0, 1}
+    for r, p in enumerate(plans):
+        assert p.info["evaluated"] == [int(o == r) for o in owner]
+    full = us.Plan(g, [us.MATRIX] * len(names))
+    f = [p.flops(10000)[0] for p in plans]
+    assert max(f) <= 1.2 * full.flops(10000)[0] / 2
