@@ -1151,6 +1151,12 @@ int ustat_batched_capture(ustat_batched_t *b, const void *const *X, int x_dtype,
         cudaGraphDestroy(b->graph);
         b->graph = nullptr;
     }
+    if (tc_gemm3(b->plan->p)) {
+        // the treewidth-3 steps' second stream and events, created before the capture
+        SideStream *side = nullptr;
+        cudaError_t es = side_stream(&side);
+        if (es != cudaSuccess) return cuda_fail(es);
+    }
     cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e);
     rc = batched_body(b, X, x_dtype, factors, n_factors, (char *)ws, st, U_out, V_out);
