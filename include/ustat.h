@@ -187,6 +187,16 @@ int ustat_eval(ustat_plan_t *plan, const void *X, int x_dtype, int64_t n, int d,
                void *stream, double *U_out, double *V_out);
 
 /*
+ * Device status of the last evaluation that used workspace ws on stream: waits for
+ * the stream, reads the workspace's error word (its first 4 bytes) and sets
+ * *device_status to USTAT_OK, or to USTAT_ERR_DEVICE_TIMEOUT when a bounded device
+ * wait (an mbarrier wait of the tensor-core GEMM) gave up; that evaluation's U and
+ * V are then NaN.  Host call; blocks until the stream's work is done.  Errors:
+ * USTAT_ERR_INVALID_ARG for a NULL ws or device_status, USTAT_ERR_CUDA.
+ */
+int ustat_status(const void *ws, void *stream, int *device_status);
+
+/*
  * Same computation with host inputs and outputs: X_host (n x d, x_dtype) is
  * copied into the workspace, factor data stay device pointers, and U_host[2] /
  * V_host[n_parts] (may be NULL) receive the results.  The workspace must hold

@@ -726,6 +726,17 @@ int ustat_plan_flops(const ustat_plan_t *plan, int64_t n, double *flops_plan, do
     return USTAT_OK;
 }
 
+int ustat_status(const void *ws, void *stream, int *device_status) {
+    if (!ws || !device_status) return USTAT_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int word = 0;   // every workspace layout starts with the error word (Layout::err_off = 0)
+    e = cudaMemcpy(&word, ws, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *device_status = word != 0 ? USTAT_ERR_DEVICE_TIMEOUT : USTAT_OK;
+    return USTAT_OK;
+}
+
 int ustat_workspace_bytes(const ustat_plan_t *plan, int64_t n, int d, size_t *bytes) {
     if (!plan || !bytes || n < 1 || d < 1) return USTAT_ERR_INVALID_ARG;
     *bytes = make_layout(plan->p, n, d).total;

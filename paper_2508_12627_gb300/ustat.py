@@ -61,6 +61,7 @@ EXPORTS = {
     "ustat_plan_flops": (_i, [_vp, _i64, _P(_d), _P(_d)]),
     "ustat_plan_describe": (_i, [_vp, ctypes.c_char_p, _sz, _P(_sz)]),
     "ustat_workspace_bytes": (_i, [_vp, _i64, _i, _P(_sz)]),
+    "ustat_status": (_i, [_vp, _vp, _P(_i)]),
     "ustat_eval": (_i, [_vp, _vp, _i, _i64, _i, _P(ustat_factor), _i, _vp, _sz, _vp, _vp, _vp]),
     "ustat_host_staging_bytes": (_i, [_vp, _i64, _i, _P(_sz)]),
     "ustat_eval_noalloc": (_i, [_vp, _vp, _i, _i64, _i, _P(ustat_factor), _i, _vp, _vp, _vp]),
@@ -355,6 +356,14 @@ def ustat_eval(plan, X_ptr, x_dtype, n, d, factors, ws_ptr, ws_bytes, stream, U_
     rc = lib().ustat_eval(plan.handle, X_ptr, x_dtype, n, d, fa, len(factors), ws_ptr, ws_bytes, stream,
                           U_ptr, V_ptr)
     _check(rc, "ustat_eval")
+
+
+def status(ws_ptr, stream):
+    """ustat_status: USTAT_OK, or USTAT_ERR_DEVICE_TIMEOUT if a bounded device wait of
+    the last evaluation in this workspace gave up (waits for the stream)."""
+    st = _i()
+    _check(lib().ustat_status(ws_ptr, stream, ctypes.byref(st)), "ustat_status")
+    return st.value
 
 
 NOALLOC_MAX_BYTES = 64 * 1024 * 1024

@@ -118,6 +118,13 @@ def test_invalid_graphs_are_rejected(us):
     assert e.value.code == us.USTAT_ERR_TW_TOO_LARGE
 
 
+def test_status_rejects_a_missing_workspace(us):
+    # argument checks come before any CUDA call
+    with pytest.raises(us.UstatError) as e:
+        us.status(0, 0)
+    assert e.value.code == us.USTAT_ERR_INVALID_ARG
+
+
 def test_workspace_bytes_scale(us):
     p = _plan(us, synth.cycle4_graph(), [uo.RBF], precision="bf16x3")
     a, b = p.workspace_bytes(1000, 32), p.workspace_bytes(2000, 32)

@@ -171,6 +171,16 @@ def test_kernel_matrix_sum_has_no_bias(eng_mod, name):
         assert abs(out["U_sum"] - ref["U_sum"]) <= 1e-9 * uabs, (name, prec, out["U_sum"], ref["U_sum"])
 
 
+def test_status_after_an_evaluation_is_ok(eng_mod):
+    import torch
+    from paper_2508_12627_gb300 import ustat as us
+    w = synth.workload("c4_rbf", 300)
+    eng = eng_mod.Engine(w.graph, w.factors, precision="bf16x3")
+    out = eng.evaluate(w.X)
+    assert np.isfinite(out["U_sum"])
+    assert us.status(eng._ws.data_ptr(), torch.cuda.current_stream().cuda_stream) == us.USTAT_OK
+
+
 def test_n_smaller_than_m_is_an_error(eng_mod):
     from paper_2508_12627_gb300 import ustat as us
     w = synth.workload("c4_rbf", n=3)
