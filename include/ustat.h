@@ -25,7 +25,7 @@
  *   - Every function returns USTAT_OK (0) or a negative USTAT_ERR_* code; on error
  *     no output is written.  ustat_strerror() names a code.
  *   - Evaluation enqueues work on the given CUDA stream and returns without
- *     synchronising (except ustat_eval_host, which synchronises the stream).
+ *     synchronising (ustat_eval_host and ustat_status synchronise the stream).
  */
 #ifndef USTAT_H
 #define USTAT_H
