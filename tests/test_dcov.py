@@ -112,3 +112,19 @@ def test_dcov_at_n_138_against_oracle_and_closed_form(precision, tol):
         for g, r in zip(got_terms, ref_terms):               # every term is a sum of positive products
             assert abs(g - r) <= tol * abs(r), (precision, i, j, g, r)
         assert abs(val - u_centred(a, b)) <= tol * scale, (precision, i, j, val, u_centred(a, b), scale)
+
+
+def test_planted_coefficient_mistakes_fail_the_pins():
+    pytest.importorskip("torch")
+    rng = np.random.default_rng(9)
+    n = 9
+    a, b = _dist(rng.standard_normal((n, 2))), _dist(rng.standard_normal((n, 2)))
+    us_, coef = oracle_terms(a, b)
+    want = brute(a, b)
+    good = math.fsum(c * u for c, u in zip(coef, us_)) / math.perm(n, 4)
+    assert abs(good - want) <= 1e-12 * abs(want)
+    for bad in ([coef[0], coef[1] / (n - 3), coef[2], coef[3]],      # (n - 2) instead of (n - 2)(n - 3)
+                [coef[0], coef[1], coef[2] * (n - 2) / (n - 3), coef[3]],
+                [coef[0], coef[1], coef[2], -coef[3]]):
+        d = math.fsum(c * u for c, u in zip(bad, us_)) / math.perm(n, 4)
+        assert abs(d - want) > 1e-6 * abs(want)

@@ -254,3 +254,35 @@ def test_four_vertex_census_at_n_2000():
         assert o[0] % aut == 0 and o[0] < 2.0 ** 53
         counts[nm] = int(o[0]) // aut
     census_identities(counts, A, 4)
+
+
+def test_planted_mistakes_fail_the_pins():
+    # a wrong automorphism count or a swapped A / B edge breaks the brute-force pin
+    A = synth.er_adjacency(9, 0.5, 7)
+    brute = brute_census(A, 4)
+    k, e = synth.MOTIFS["paw"]
+    u, _ = oracle_count("paw", A)
+    assert u == brute["paw"] * _aut(k, e)
+    assert u != brute["paw"] * (_aut(k, e) * 2)               # |Aut| of the paw taken as 4
+    g, fn = synth.motif_graph("paw")
+    swapped = synth.Graph(g.m, [(a, b, 1 - f) if (a, b) == (2, 3) else (a, b, f) for a, b, f in g.edges])
+    r = uo.ustat(swapped, synth.motif_factors(fn, A), np.zeros((9, 1)))
+    assert r["U_sum"] != u                                      # the tail edge read from B instead of A
+
+
+def test_five_vertex_clique_exceeds_the_engines_treewidth():
+    # K5 needs a step with four neighbours: the planner refuses it before any device work
+    pytest.importorskip("torch")
+    from paper_2508_12627_gb300 import build
+    build.build()
+    from paper_2508_12627_gb300 import motifs, ustat as us
+    edges = [(a, b) for a in range(5) for b in range(a + 1, 5)]
+    g, names = motifs.kernel_graph(5, edges)
+    with pytest.raises(us.UstatError) as e:
+        us.Plan(g, [us.MATRIX] * len(names))
+    assert e.value.code == us.USTAT_ERR_TW_TOO_LARGE
+    # every induced 5-vertex motif carries A or B on all ten pairs, so its kernel
+    # graph is K5 whatever the motif: the induced 5-cycle is refused as well
+    g, names = motifs.kernel_graph(5, [(0, 1), (1, 2), (2, 3), (3, 4), (0, 4)])
+    with pytest.raises(us.UstatError):
+        us.Plan(g, [us.MATRIX] * len(names))
