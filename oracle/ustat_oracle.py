@@ -229,13 +229,18 @@ def min_degree_order(n_vertices, tensors):
     return order
 
 
-def einsum_eliminate(n_vertices, tensors, order=None) -> float:
+def einsum_eliminate(n_vertices, tensors, order=None, trace=None) -> float:
     """Einsum(T, A) with empty output: sum out one index at a time.
 
     ``tensors`` is a list of (axes, array).  Step for index v: multiply every
     tensor that carries v and sum over v; the product is a new tensor on the other
     indices it carried.  The product-and-sum of a vector on v with matrices on
-    (v, w) and (v, x) is done by a matrix product; anything else by numpy.einsum."""
+    (v, w) and (v, x) is done by a matrix product; anything else by numpy.einsum.
+
+    With ``trace`` (a list), each step appends the sorted index tuples of the
+    tensors left after it, () standing for a scalar it produced: the Einsum
+    notation sequence A_1, ..., A_m of Appendix D (Definition "Einsum Notation
+    Sequence")."""
     work = [_canonical(ax, a) for ax, a in tensors]
     if order is None:
         order = min_degree_order(n_vertices, work)
@@ -254,6 +259,8 @@ def einsum_eliminate(n_vertices, tensors, order=None) -> float:
             work.append((ax_out, arr))
         else:
             scalar *= float(arr)
+        if trace is not None:
+            trace.append(sorted(ax for ax, _ in work) + ([] if ax_out else [()]))
     for ax, a in work:   # only 0-d tensors can remain
         assert not ax
         scalar *= float(a)

@@ -393,3 +393,19 @@ def test_n_equals_m_and_small_n():
     w = synth.workload("c4_rbf", n=3)
     r = uo.ustat(w.graph, w.factors, w.X)
     assert abs(r["U_sum"]) <= 1e-12 * max(abs(v) for v in r["V"])
+
+
+def test_einsum_notation_sequence_of_k4():
+    # Appendix D, the example after Definition "Einsum Notation Sequence": the
+    # oracle's elimination of K4 under sigma = (1, 2, 3, 4) leaves exactly the
+    # printed tuple lists, and its value is the full contraction
+    g = _golden("einsum_sequence_k4.json")
+    rng = np.random.default_rng(0)
+    n = 5
+    tens = [(tuple(v - 1 for v in t), rng.random((n, n))) for t in g["signature"]]
+    trace = []
+    val = uo.einsum_eliminate(4, tens, order=[v - 1 for v in g["sigma"]], trace=trace)
+    want = [sorted(tuple(v - 1 for v in t) for t in step) for step in g["sequence"][1:]]
+    assert trace == want
+    full = np.einsum("ab,ac,ad,bc,bd,cd->", *[a for _, a in tens])
+    assert abs(val - full) <= 1e-12 * abs(full)
