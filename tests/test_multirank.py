@@ -87,3 +87,26 @@ def test_reference_arm_bounded_sample_for_every_workload(monkeypatch, workload):
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["higher_is_better"] is True
     assert line["ms_per_step"] >= line["sample_ms_per_step"] * 0.999
+
+
+def test_sample_sizing_and_growth_exponents():
+    sys.path.insert(0, ROOT)
+    import bench
+    import synth
+    # the oracle's growth n^(M + 1) from the largest quotient treewidth M
+    assert bench.max_treewidth(synth.cycle4_graph()) == 2
+    assert bench.max_treewidth(synth.triangle_graph()) == 2
+    assert bench.max_treewidth(synth.k4_plus_cycle_graph()) == 3
+    assert bench.max_treewidth(synth.path5_chord_graph()) == 2
+    # doubling stops before the predicted time passes the limit, and at the full size
+    calls = []
+
+    def fake(n):
+        calls.append(n)
+        return 1e-10 * n ** 3
+
+    assert bench._sized(fake, 4096, 64, 3, 20.0) == (4096, 1e-10 * 4096 ** 3) and calls[-1] == 4096
+    calls.clear()
+    ns, t = bench._sized(fake, 10 ** 6, 64, 3, 20.0)
+    assert ns == 4096 and t == 1e-10 * 4096 ** 3 and 1e-10 * 8192 ** 3 > 20.0
+    assert calls == [64, 128, 256, 512, 1024, 2048, 4096]
