@@ -121,7 +121,9 @@ def measure_instance(timer, g, rng, max_cand=5):
     return rec
 
 
-def generate(count, seed, budget_s, timer=None, log=None):
+def generate(count, seed, budget_s, timer=None, log=None, on_record=None):
+    """Up to ``count`` measured instances within ``budget_s``; ``on_record`` (if
+    given) receives each record as soon as it is measured."""
     timer = timer or Timer()
     rng = np.random.default_rng(seed)
     recs = []
@@ -136,6 +138,8 @@ def generate(count, seed, budget_s, timer=None, log=None):
             raise
         if r is not None:
             recs.append(r)
+            if on_record:
+                on_record(r)
         if log and len(recs) % 250 == 0:
             log("%d instances, %.0f s" % (len(recs), time.time() - t0))
     return recs
@@ -198,6 +202,47 @@ class MLP:
     def numpy(self):
         return self.params.cpu().numpy().astype(np.float64)
 
+    def save(self, path):
+        """Checkpoint: parameters, Adam moments and step count."""
+        save_checkpoint(path, self.params.cpu().numpy(), self.m.cpu().numpy(), self.v.cpu().numpy(), self.step_no)
+
+    @classmethod
+    def restore(cls, path, hidden=HIDDEN):
+        """A network in the state save() wrote; train() continues from it."""
+        c = load_checkpoint(path)
+        net = cls(hidden=hidden, params=c["params"])
+        net.m.copy_(net.torch.from_numpy(c["m"]))
+        net.v.copy_(net.torch.from_numpy(c["v"]))
+        net.step_no = c["step"]
+        return net
+
+
+def save_checkpoint(path, params, m, v, step):
+    """The network's training state: parameters, Adam moments and step count
+    (float32 arrays as trained, written without rounding)."""
+    np.savez(path, params=np.asarray(params, dtype=np.float32), m=np.asarray(m, dtype=np.float32),
+             v=np.asarray(v, dtype=np.float32), step=np.int64(step))
+
+
+def load_checkpoint(path):
+    with np.load(path) as z:
+        return {"params": z["params"].copy(), "m": z["m"].copy(), "v": z["v"].copy(), "step": int(z["step"])}
+
+
+def append_records(path, recs):
+    """Timing records, one JSON object per line, appended: an interrupted data
+    generation keeps what it measured."""
+    with open(path, "a") as f:
+        for r in recs:
+            f.write(json.dumps(r) + "\n")
+
+
+def read_records(path):
+    if not os.path.exists(path):
+        return []
+    with open(path) as f:
+        return [json.loads(line) for line in f if line.strip()]
+
 
 def regrets(recs, score):
     """Per instance: the measured candidate the scorer picks, its time over the
@@ -229,6 +274,10 @@ def main():
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--out", default=WEIGHTS)
+    ap.add_argument("--data", default=None,
+                    help="JSONL file of timing records: the records already in it are used, new ones are appended "
+                         "as they are measured (an interrupted run resumes)")
+    ap.add_argument("--checkpoint", default=None, help="write the trained network's state (npz) here")
     args = ap.parse_args()
     import torch
     from . import build
@@ -239,7 +288,11 @@ def main():
         print(s, flush=True)
 
     timer = Timer()
-    recs = generate(args.graphs, args.seed, args.budget, timer, log)
+    recs = read_records(args.data) if args.data else []
+    if len(recs) < args.graphs:
+        # a resumed run draws its graphs from a seed offset by the records it has
+        recs += generate(args.graphs - len(recs), args.seed + len(recs), args.budget, timer, log,
+                         on_record=(lambda r: append_records(args.data, [r])) if args.data else None)
     rng = np.random.default_rng(args.seed + 1)
     idx = rng.permutation(len(recs))
     n_test = max(1, len(recs) // 5)
@@ -249,6 +302,8 @@ def main():
     y = [math.log(t) for r in train for t in r["ms"]]
     net = MLP()
     hist = net.train(X, y, steps=args.steps, log=log)
+    if args.checkpoint:
+        net.save(args.checkpoint)
     params = net.numpy()
     reg = regrets(test, lambda F: net.predict(F))
     log("held-out regret %s" % json.dumps(reg))

@@ -135,3 +135,20 @@ def test_network_beats_the_flop_count_pick_on_held_out_instances():
     assert len(wts["held_out"]) >= 50
     assert reg["learned"] < reg["analytic"]
     assert reg["learned"] <= reg["minfill"]
+
+
+def test_checkpoint_and_record_files_round_trip(tmp_path):
+    # host side only: the training state and the timing records survive a write
+    # and a read unchanged
+    from paper_2508_12627_gb300 import ranker
+    rng = np.random.default_rng(1)
+    p, m, v = (rng.normal(0, 1, 100).astype(np.float32) for _ in range(3))
+    ranker.save_checkpoint(tmp_path / "c.npz", p, m, v, 1234)
+    c = ranker.load_checkpoint(tmp_path / "c.npz")
+    assert c["step"] == 1234 and all(np.array_equal(c[k], x) for k, x in (("params", p), ("m", m), ("v", v)))
+    f = tmp_path / "recs.jsonl"
+    assert ranker.read_records(f) == []
+    recs = [{"n": 256, "ms": [0.5, 0.25], "features": [[0.1] * 20, [0.2] * 20]}, {"n": 512, "ms": [1.0]}]
+    ranker.append_records(f, recs[:1])
+    ranker.append_records(f, recs[1:])
+    assert ranker.read_records(f) == recs
