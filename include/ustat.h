@@ -139,6 +139,20 @@ int ustat_plan_shard(const ustat_graph *graph, const ustat_options *opts, int sh
                      int64_t n, int *owner, ustat_plan_t **out);
 
 /*
+ * Plan serialisation, for caching plans between processes (planning an order-7
+ * graph searches thousands of orders per partition).  ustat_plan_serialize writes
+ * the plan into buf (host memory, buf_len bytes; buf may be NULL to query the
+ * size) and sets *needed to the bytes it takes.  ustat_plan_deserialize builds a
+ * library-owned plan from such bytes; it checks the format, the sizes of the
+ * records (a plan written by a build with other record layouts is refused) and
+ * that every reference inside the plan is in range.  Errors:
+ * USTAT_ERR_INVALID_ARG (NULL plan or out, buf_len too small, bytes that are not
+ * a plan of this build).  Host only.
+ */
+int ustat_plan_serialize(const ustat_plan_t *plan, void *buf, size_t buf_len, size_t *needed);
+int ustat_plan_deserialize(const void *buf, size_t len, ustat_plan_t **out);
+
+/*
  * Plan report.  Any output pointer may be NULL.
  *   n_parts : number of partitions (Bell(m))
  *   mu      : [n_parts] Moebius coefficients mu_pi

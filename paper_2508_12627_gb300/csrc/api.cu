@@ -10,6 +10,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "kernels.h"
@@ -689,6 +690,157 @@ int ustat_plan_shard(const ustat_graph *graph, const ustat_options *opts, int sh
     if (rc != USTAT_OK) {
         delete p;
         return rc;
+    }
+    *out = p;
+    return USTAT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// Plan serialisation: a header that names the format and the sizes of the
+// records it copies (so a plan written by a build with other record layouts is
+// refused), the scalar fields, then each vector as a count and its records.
+constexpr uint32_t kPlanMagic = 0x50545355u;   // "USTP"
+constexpr uint32_t kPlanFormat = 1;
+static_assert(std::is_trivially_copyable<Op>::value && std::is_trivially_copyable<Slot>::value &&
+                  std::is_trivially_copyable<PartRec>::value,
+              "plan records are copied byte for byte");
+
+struct Writer {
+    std::vector<char> b;
+    template <typename T> void put(const T &v) {
+        const char *p = (const char *)&v;
+        b.insert(b.end(), p, p + sizeof(T));
+    }
+    template <typename T> void vec(const std::vector<T> &v) {
+        put<uint64_t>(v.size());
+        const char *p = (const char *)v.data();
+        b.insert(b.end(), p, p + sizeof(T) * v.size());
+    }
+};
+
+struct Reader {
+    const char *p;
+    size_t left;
+    bool ok = true;
+    template <typename T> T get() {
+        T v{};
+        if (left < sizeof(T)) {
+            ok = false;
+            return v;
+        }
+        std::memcpy(&v, p, sizeof(T));
+        p += sizeof(T);
+        left -= sizeof(T);
+        return v;
+    }
+    template <typename T> void vec(std::vector<T> &v) {
+        uint64_t n = get<uint64_t>();
+        if (!ok || n > left / (sizeof(T) ? sizeof(T) : 1)) {
+            ok = false;
+            return;
+        }
+        v.resize(n);
+        std::memcpy(v.data(), p, sizeof(T) * n);
+        p += sizeof(T) * n;
+        left -= sizeof(T) * n;
+    }
+};
+
+void write_plan(const Plan &P, Writer &w) {
+    w.put(kPlanMagic);
+    w.put(kPlanFormat);
+    w.put<uint32_t>(sizeof(Op));
+    w.put<uint32_t>(sizeof(Slot));
+    w.put<uint32_t>(sizeof(PartRec));
+    w.put<int32_t>(P.m);
+    w.put<int32_t>(P.precision);
+    w.put<int32_t>(P.sparsify);
+    w.put<int32_t>(P.planner);
+    w.put<int32_t>(P.cse);
+    w.put<int32_t>(P.n_gemm);
+    w.put<int32_t>(P.n_gemm3);
+    for (int c = 0; c < 4; ++c) w.put<int32_t>(P.tc_variant[c]);
+    w.vec(P.factor_kind);
+    w.vec(P.slots);
+    w.vec(P.ops);
+    w.vec(P.parts);
+    w.put<uint64_t>(P.groups.size());
+    for (auto &g : P.groups) w.vec(g);
+}
+}  // namespace
+
+extern "C" {
+
+int ustat_plan_serialize(const ustat_plan_t *plan, void *buf, size_t buf_len, size_t *needed) {
+    if (!plan) return USTAT_ERR_INVALID_ARG;
+    Writer w;
+    write_plan(plan->p, w);
+    if (needed) *needed = w.b.size();
+    if (!buf) return USTAT_OK;
+    if (buf_len < w.b.size()) return USTAT_ERR_INVALID_ARG;
+    std::memcpy(buf, w.b.data(), w.b.size());
+    return USTAT_OK;
+}
+
+int ustat_plan_deserialize(const void *buf, size_t len, ustat_plan_t **out) {
+    if (!buf || !out) return USTAT_ERR_INVALID_ARG;
+    Reader r{(const char *)buf, len};
+    if (r.get<uint32_t>() != kPlanMagic || r.get<uint32_t>() != kPlanFormat || r.get<uint32_t>() != sizeof(Op) ||
+        r.get<uint32_t>() != sizeof(Slot) || r.get<uint32_t>() != sizeof(PartRec) || !r.ok)
+        return USTAT_ERR_INVALID_ARG;
+    ustat_plan_t *p = new (std::nothrow) ustat_plan_t();
+    if (!p) return USTAT_ERR_INVALID_ARG;
+    Plan &P = p->p;
+    P.m = r.get<int32_t>();
+    P.precision = r.get<int32_t>();
+    P.sparsify = r.get<int32_t>();
+    P.planner = r.get<int32_t>();
+    P.cse = r.get<int32_t>();
+    P.n_gemm = r.get<int32_t>();
+    P.n_gemm3 = r.get<int32_t>();
+    for (int c = 0; c < 4; ++c) P.tc_variant[c] = r.get<int32_t>();
+    r.vec(P.factor_kind);
+    r.vec(P.slots);
+    r.vec(P.ops);
+    r.vec(P.parts);
+    uint64_t ng = r.get<uint64_t>();
+    if (r.ok && ng <= r.left) {
+        P.groups.resize(ng);
+        for (auto &g : P.groups) r.vec(g);
+    } else {
+        r.ok = false;
+    }
+    // every record must refer to what the plan holds
+    bool valid = r.ok && r.left == 0 && P.m >= 1 && P.m <= kMaxM && P.precision >= USTAT_FP64 &&
+                 P.precision <= USTAT_BF16X5 && (int)P.parts.size() <= kCombineMaxParts;
+    const int nslots = (int)P.slots.size(), nf = (int)P.factor_kind.size();
+    auto slot_ok = [&](int s) { return s >= -1 && s < nslots; };
+    auto term_ok = [&](const Term &t) { return slot_ok(t.mat); };
+    auto op_ok = [&](const Op &o) {
+        bool ok = o.kind >= 0 && o.kind < OP_COUNT && slot_ok(o.out) && o.factor >= -1 && o.factor < nf &&
+                  o.nt >= 0 && o.nt <= kMaxTerms && o.nred >= 0 && o.nred <= kMaxRed && slot_ok(o.u) &&
+                  slot_ok(o.a) && slot_ok(o.b) && term_ok(o.A) && term_ok(o.B) && term_ok(o.W) && slot_ok(o.opA) &&
+                  slot_ok(o.opB) && term_ok(o.Ab) && term_ok(o.Wbc) && term_ok(o.Wbd) && slot_ok(o.ub) &&
+                  o.group >= -1 && o.group < (int)P.groups.size();
+        for (int t = 0; t < kMaxTerms; ++t) ok = ok && term_ok(o.t[t]);
+        for (int q = 0; q < kMaxRed; ++q) ok = ok && term_ok(o.red[q].W) && slot_ok(o.red[q].out) &&
+                                                slot_ok(o.red[q].a) && slot_ok(o.red[q].b);
+        return ok;
+    };
+    for (size_t i = 0; valid && i < P.ops.size(); ++i) valid = op_ok(P.ops[i]);
+    for (size_t g = 0; valid && g < P.groups.size(); ++g)
+        for (auto &o : P.groups[g]) valid = valid && op_ok(o);
+    for (size_t i = 0; valid && i < P.parts.size(); ++i) {
+        const PartRec &pr = P.parts[i];
+        valid = pr.nscal >= 0 && pr.nscal <= kMaxScal;
+        for (int q = 0; valid && q < pr.nscal; ++q) valid = pr.scal[q] >= 0 && pr.scal[q] < nslots;
+    }
+    for (int k : P.factor_kind) valid = valid && k >= USTAT_RBF && k <= USTAT_VECTOR;
+    if (!valid) {
+        delete p;
+        return USTAT_ERR_INVALID_ARG;
     }
     *out = p;
     return USTAT_OK;

@@ -57,6 +57,8 @@ EXPORTS = {
     "ustat_plan": (_i, [_P(ustat_graph), _P(ustat_options), _P(_vp)]),
     "ustat_plan_destroy": (None, [_vp]),
     "ustat_plan_shard": (_i, [_P(ustat_graph), _P(ustat_options), _i, _i, _i64, _P(_i), _P(_vp)]),
+    "ustat_plan_serialize": (_i, [_vp, _vp, _sz, _P(_sz)]),
+    "ustat_plan_deserialize": (_i, [_vp, _sz, _P(_vp)]),
     "ustat_plan_info": (_i, [_vp, _P(_i), _P(_i), _P(_i), _P(_i), _P(_i), _P(_i), _P(_i), _P(_i)]),
     "ustat_plan_flops": (_i, [_vp, _i64, _P(_d), _P(_d)]),
     "ustat_plan_describe": (_i, [_vp, ctypes.c_char_p, _sz, _P(_sz)]),
@@ -179,6 +181,7 @@ class Plan:
         learned plans)."""
         self = cls.__new__(cls)
         self.handle = handle
+        self.owner = None
         self.m = graph.m
         self.factor_kinds = list(factor_kinds)
         self.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
@@ -199,6 +202,21 @@ class Plan:
         return {"n_parts": k, "mu": list(mu), "tw": list(tw), "evaluated": list(ev),
                 "rgs": [tuple(rgs[i * self.m:(i + 1) * self.m]) for i in range(k)],
                 "n_ops": nops.value, "n_gemm": ng.value, "n_gemm3": ng3.value}
+
+    def to_bytes(self):
+        """The plan serialised (ustat_plan_serialize), for a cache."""
+        need = _sz()
+        _check(lib().ustat_plan_serialize(self.handle, None, 0, ctypes.byref(need)), "ustat_plan_serialize")
+        buf = ctypes.create_string_buffer(need.value)
+        _check(lib().ustat_plan_serialize(self.handle, buf, need.value, None), "ustat_plan_serialize")
+        return buf.raw
+
+    @classmethod
+    def from_bytes(cls, data, graph, factor_kinds, precision):
+        """A plan read back from to_bytes() (ustat_plan_deserialize)."""
+        h = _vp()
+        _check(lib().ustat_plan_deserialize(data, len(data), ctypes.byref(h)), "ustat_plan_deserialize")
+        return cls.from_handle(h, graph, factor_kinds, precision)
 
     def flops(self, n):
         a, b = _d(), _d()

@@ -118,6 +118,39 @@ def test_invalid_graphs_are_rejected(us):
     assert e.value.code == us.USTAT_ERR_TW_TOO_LARGE
 
 
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "bf16x4"])
+def test_plan_serialisation_round_trip(us, name, prec):
+    g, kinds = GRAPHS[name]
+    p = _plan(us, g, kinds, precision=prec)
+    p.set_variant(17, 1)
+    data = p.to_bytes()
+    q = us.Plan.from_bytes(data, g, kinds, prec)
+    assert q.describe() == p.describe() and q.info == p.info
+    assert q.flops(3000) == p.flops(3000) and q.workspace_bytes(3000, 16) == p.workspace_bytes(3000, 16)
+    assert us.plan_orders(q) == us.plan_orders(p)
+    assert q.to_bytes() == data
+
+
+def test_plan_deserialisation_refuses_other_bytes(us):
+    g, kinds = GRAPHS["k4_cycle"]
+    data = _plan(us, g, kinds).to_bytes()
+    bad = [b"", data[:-1], data + b"\0", b"XXXX" + data[4:], data[:8] + bytes([data[8] ^ 1]) + data[9:]]
+    # the first operation's output slot pointed past the plan's slots: after the
+    # 64-byte header come the factor kinds and the 8-byte slots, each a count and
+    # its records, then the operations (kind, factor, out, ...)
+    import struct
+    nf = struct.unpack_from("<Q", data, 64)[0]
+    ns = struct.unpack_from("<Q", data, 72 + 4 * nf)[0]
+    at = 72 + 4 * nf + 8 + 8 * ns + 8 + 8
+    assert struct.unpack_from("<i", data, at)[0] in range(ns)
+    bad.append(data[:at] + struct.pack("<i", ns + 5) + data[at + 4:])
+    for blob in bad:
+        with pytest.raises(us.UstatError) as e:
+            us.Plan.from_bytes(blob, g, kinds, "bf16x3")
+        assert e.value.code == us.USTAT_ERR_INVALID_ARG
+
+
 def test_status_rejects_a_missing_workspace(us):
     # argument checks come before any CUDA call
     with pytest.raises(us.UstatError) as e:
