@@ -19,15 +19,35 @@ from . import ustat as us
 
 class Engine:
     def __init__(self, graph, factors, precision="bf16x3", sparsify=False, planner=us.PLAN_EXHAUSTIVE, cse=True,
-                 device="cuda:0", shard=None):
+                 device="cuda:0", shard=None, plan_cache=None):
         """``shard=(rank, n_shards, n)``: evaluate only this rank's share of the
         partition sum (ustat_plan_shard); ``evaluate_shards`` then sums the
-        ranks' results."""
+        ranks' results.  ``plan_cache``: a directory where plans are kept as
+        serialised bytes, keyed by everything that determines them."""
         self.graph = graph
         self.factors = list(factors)
         self.device = torch.device(device)
-        self.plan = us.Plan(graph, [f.kind for f in self.factors], precision=precision, sparsify=sparsify,
-                            planner=planner, cse=cse, shard=shard)
+        kinds = [f.kind for f in self.factors]
+        self.plan = None
+        self.plan_cached = False
+        path = None
+        if plan_cache is not None and shard is None:
+            import hashlib
+            import os
+            key = repr((graph.m, sorted(tuple(e) for e in graph.edges), sorted(tuple(u) for u in graph.unary), kinds,
+                        precision, bool(sparsify), int(planner), bool(cse), us.version()))
+            os.makedirs(plan_cache, exist_ok=True)
+            path = os.path.join(plan_cache, hashlib.sha256(key.encode()).hexdigest()[:32] + ".plan")
+            if os.path.exists(path):
+                with open(path, "rb") as f:
+                    self.plan = us.Plan.from_bytes(f.read(), graph, kinds, precision)
+                self.plan_cached = True
+        if self.plan is None:
+            self.plan = us.Plan(graph, kinds, precision=precision, sparsify=sparsify, planner=planner, cse=cse,
+                                shard=shard)
+            if path is not None:
+                with open(path, "wb") as f:
+                    f.write(self.plan.to_bytes())
         self.n_parts = self.plan.info["n_parts"]
         self._ws = None
         self._fdev = {}

@@ -376,6 +376,11 @@ def ustat_eval(plan, X_ptr, x_dtype, n, d, factors, ws_ptr, ws_bytes, stream, U_
     _check(rc, "ustat_eval")
 
 
+def version():
+    """The library's version string (ustat_version)."""
+    return lib().ustat_version().decode()
+
+
 def status(ws_ptr, stream):
     """ustat_status: USTAT_OK, or USTAT_ERR_DEVICE_TIMEOUT if a bounded device wait of
     the last evaluation in this workspace gave up (waits for the stream)."""

@@ -181,3 +181,15 @@ def test_every_plan_is_well_formed(us, prec):
                 for pl in (us.PLAN_EXHAUSTIVE, us.PLAN_MINFILL):
                     p = us.Plan(g, kinds, precision=prec, sparsify=sp, cse=cse, planner=pl)
                     assert p.info["n_parts"] == len(uo.set_partitions(g.m))
+
+
+def test_engine_plan_cache(us, tmp_path):
+    # planning only (no device work): the second engine reads the plan the first wrote
+    from paper_2508_12627_gb300 import engine
+    w = synth.workload("k4_cycle_rbf", 16)
+    a = engine.Engine(w.graph, w.factors, precision="bf16x3", plan_cache=str(tmp_path))
+    b = engine.Engine(w.graph, w.factors, precision="bf16x3", plan_cache=str(tmp_path))
+    c = engine.Engine(w.graph, w.factors, precision="bf16x4", plan_cache=str(tmp_path))
+    assert not a.plan_cached and b.plan_cached and not c.plan_cached
+    assert b.plan.describe() == a.plan.describe() and b.n_parts == a.n_parts == 203
+    assert len(list(tmp_path.iterdir())) == 2
