@@ -21,8 +21,9 @@ Everything here follows the paper (arXiv 2508.12627) step by step, in float64:
   (Section 3.3, the identity right after Example "A_pi").
 * Einsum evaluated by summing out one index at a time along an elimination order
   (Section 3.2, Proposition "complexity_einsum" and its proof in Appendix D);
-  a matrix product is used as a library primitive for the sum of
-  (vector on v) x (matrix on v,w) x (matrix on v,x) over v.
+  a matrix product is used as a library primitive for the sum over v of
+  (vector on v) x (matrices on (v,w), (v,x)) and, with the (w, x) pairs as rows,
+  x (matrix on (v,y)).
 * Sparsified tensors T~ (Lemma "sparsification_trick") and the surviving set
   Pi_m^A (Remark after it, equation "quotient_set").
 * Algorithm 4 (Ustats): U = sum_pi mu_pi V_pi.
@@ -234,8 +235,9 @@ def einsum_eliminate(n_vertices, tensors, order=None, trace=None) -> float:
 
     ``tensors`` is a list of (axes, array).  Step for index v: multiply every
     tensor that carries v and sum over v; the product is a new tensor on the other
-    indices it carried.  The product-and-sum of a vector on v with matrices on
-    (v, w) and (v, x) is done by a matrix product; anything else by numpy.einsum.
+    indices it carried.  The product-and-sum of a vector on v with two or three
+    matrices on (v, w), (v, x) [, (v, y)] is done by a matrix product; anything
+    else by numpy.einsum.
 
     With ``trace`` (a list), each step appends the sorted index tuples of the
     tensors left after it, () standing for a scalar it produced: the Einsum
@@ -275,7 +277,7 @@ def _sum_out(v, group):
     vec = merged.pop((v,), None)
     others = sorted({b for ax in merged for b in ax if b != v})
     mats = {ax: a for ax, a in merged.items() if len(ax) == 2}
-    if len(mats) == len(merged) and len(others) <= 2 and all(len(ax) == 2 for ax in merged):
+    if len(mats) == len(merged) and len(others) <= 3 and all(len(ax) == 2 for ax in merged):
         # vector and matrices on (v, w): orient every matrix as M[v_index, w_index]
         oriented = []
         for ax, a in mats.items():
@@ -292,6 +294,15 @@ def _sum_out(v, group):
             (w, A), (x, B) = sorted(oriented, key=lambda t: t[0])
             Bs = B * u[:, None] if u is not None else B
             return (w, x), A.T @ Bs
+        if len(oriented) == 3:
+            # three neighbours: T(w, x, y) = sum_v u(v) A(v, w) B(v, x) C(v, y), the
+            # same sum with the (w, x) pairs laid out as the rows of one matrix
+            (w, A), (x, B), (y, C) = sorted(oriented, key=lambda t: t[0])
+            P = A[:, :, None] * B[:, None, :]
+            if u is not None:
+                P *= u[:, None, None]
+            T = P.reshape(P.shape[0], -1).T @ C
+            return (w, x, y), T.reshape(A.shape[1], B.shape[1], C.shape[1])
     # generic: numpy.einsum over the group
     letters = {}
     for ax in list(merged) + ([(v,)] if vec is not None else []):
