@@ -315,22 +315,32 @@ def run_capture(args):
 
 
 def run_batched(args):
+    """The batched workload as its own bench line."""
+    import torch
+
+    from paper_2508_12627_gb300 import build as B
+    B.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    line = batched_measure(args.precision, dev, args.steps, args.warmup, full_line=True)
+    print(json.dumps(line), flush=True)
+
+
+def batched_measure(precision, dev, steps, warmup, full_line):
     """The batched workload: every step replays two captured graphs (4-cycle and
     5-cycle plans over the same 512 samples), after the autotuner has chosen the
-    lane count and the GEMM tile variants."""
-    import ctypes
-
+    lane count and the GEMM tile variants.  Returns the bench line (full_line),
+    or a short summary for the per-configuration table."""
     import numpy as np
     import torch
 
     import synth
-    from oracle import ustat_oracle as uo
-    from paper_2508_12627_gb300 import build as B
-    B.build()
     from paper_2508_12627_gb300 import ustat as us
 
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
-    torch.cuda.set_device(dev)
+    class A:
+        pass
+    args = A()
+    args.precision, args.steps, args.warmup = precision, steps, warmup
     d = 16
     ns = [int(v) for v in synth.batched_sizes(512, 256, 4096, 0)]
     Xh = [synth.normal_X(n, d, 1000 + i) for i, n in enumerate(ns)]
@@ -340,13 +350,13 @@ def run_batched(args):
         host[int(offs[i]):int(offs[i + 1])] = torch.from_numpy(x.ravel())
     Xdev = host.to(dev)
     xp = [Xdev.data_ptr() + 8 * int(offs[i]) for i in range(len(ns))]
-    facs = [(uo.RBF, 2.0 * d, 0)]
+    facs = [(synth.RBF, 2.0 * d, 0)]
     graphs = {"c4": synth.cycle4_graph(), "c5": synth.cycle(5)}
     stream = torch.cuda.Stream(dev)
     runs = {}
     tune = {}
     for name, g in graphs.items():
-        p = us.Plan(g, [uo.RBF], precision=args.precision)
+        p = us.Plan(g, [synth.RBF], precision=args.precision)
         b = us.Batched(p, ns, d, max_lanes=16)
         ws = torch.empty(b.workspace_bytes(), dtype=torch.uint8, device=dev)
         U = torch.empty((len(ns), 2), dtype=torch.float64, device=dev)
@@ -370,8 +380,9 @@ def run_batched(args):
     torch.cuda.synchronize()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    clocks = ClockSampler(dev.index or 0)
-    clocks.start()
+    clocks = ClockSampler(dev.index or 0) if full_line else None
+    if clocks:
+        clocks.start()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
@@ -381,10 +392,30 @@ def run_batched(args):
             ends[k].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks else None
     tot_ms = float(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
     evals = len(ns) * len(graphs)
     value = evals * args.steps / (tot_ms / 1e3)
+    # accuracy: the samples whose values the oracle stored (the smallest, the
+    # largest and six more), relative to the sum of absolute terms
+    gold = stored_values("batched")
+    errs = {}
+    if gold:
+        for name in graphs:
+            Vd = runs[name][4].cpu().numpy()
+            Ud = runs[name][3].cpu().numpy()
+            e_v, e_u = 0.0, 0.0
+            for rec in gold["samples"]:
+                if rec["graph"] != name:
+                    continue
+                i = rec["index"]
+                e_v = max(e_v, float(np.max(np.abs(Vd[i] - np.array(rec["V"])) / np.array(rec["V_abs"]))))
+                e_u = max(e_u, abs(float(Ud[i, 0]) - rec["U_sum"]) / rec["U_abs"])
+            errs[name] = {"V_max": e_v, "U_sum": e_u}
+    err = {"per_graph": errs, "samples": "the %d stored samples per kernel graph of tests/golden/workload_batched.json "
+           "(n from %d to %d)" % (len({r["index"] for r in gold["samples"]}),
+                                  min(r["n"] for r in gold["samples"]), max(r["n"] for r in gold["samples"])),
+           "relative_to": "sum of |terms| (V_abs; = |V| for the RBF kernel)"} if gold else None
 
     # algorithmic tensor-core work of a step: each GEMM entry costs 2 n multiply-adds
     alg = 0.0
@@ -405,6 +436,11 @@ def run_batched(args):
                 "peak_note": "%s bf16 dense sustained %.1f TFLOP/s / %g tensor products per multiply-add; achieved "
                              "= GEMM algorithmic flops of a step / whole step time (a lower bound on the GEMM's own "
                              "rate)" % (peak_src, peaks.get("bf16_tflops_sustained", 1700.0), products)}
+    if not full_line:
+        return {"workload": WORKLOADS["batched"], "precision": args.precision, "evals_per_s": value,
+                "ms_per_step": tot_ms / args.steps, "evals_per_step": evals, "steps": args.steps,
+                "launch": "two CUDA graph replays per step (one per kernel graph), autotuned lanes and GEMM variants",
+                "tuning": tune, "roofline": roof, "rel_err_vs_oracle": err}
 
     # end to end: pinned host X -> device, both graphs, U and V back to the host
     Uh = {name: torch.empty(r[3].shape, dtype=torch.float64).pin_memory() for name, r in runs.items()}
@@ -423,18 +459,15 @@ def run_batched(args):
     e2e_s = (time.perf_counter() - t1) / ke
     d2h = sum(int(r[3].numel() + r[4].numel()) * 8 for r in runs.values())
 
-    # accuracy on the smallest samples against the oracle, and the CPU baseline:
-    # the oracle timed on the same few samples
+    # the CPU baseline: the oracle timed on the four smallest samples
+    from oracle import ustat_oracle as uo
     order = np.argsort(ns)[:4]
     cpu_t = 0.0
-    errs = []
     for name, g in graphs.items():
-        V = runs[name][4].cpu().numpy()
         for i in order:
             t2 = time.perf_counter()
-            ref = uo.ustat(g, [synth.Factor(uo.RBF, 2.0 * d, None)], Xh[i])
+            uo.ustat(g, [synth.Factor(synth.RBF, 2.0 * d, None)], Xh[i])
             cpu_t += time.perf_counter() - t2
-            errs.append(float(np.max(np.abs(V[i] - np.array(ref["V"])) / np.abs(np.array(ref["V"])))))
     cpu = {"value": 2 * len(order) / cpu_t, "unit": "evals/s", "cores": host_cores(), "kind": "oracle",
            "sample": "the 4 smallest samples (n=%s) for both kernel graphs" % [ns[i] for i in order]}
     line = {
@@ -452,10 +485,10 @@ def run_batched(args):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(args.steps * sum((r[0].info["n_ops"] + 2) * len(ns) for r in runs.values())),
         "clocks": clk,
-        "rel_err_vs_oracle": {"V_max_smallest_samples": max(errs)},
+        "rel_err_vs_oracle": err,
         "wall_s_timed_region": wall,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 MOTIF_N, MOTIF_P = 2000, 0.1
@@ -881,6 +914,206 @@ def run_hoif(args):
     print(json.dumps(line), flush=True)
 
 
+GOLDEN_DIR = os.path.join(ROOT, "tests", "golden")
+
+
+def stored_values(name):
+    """The oracle's values of a workload at its full size, as written by
+    tests/golden/make_workload_golden.py (None when the file is absent)."""
+    path = os.path.join(GOLDEN_DIR, "workload_%s.json" % name)
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        return json.load(f)
+
+
+def rel_err_vs_stored(name, result):
+    """This run's U_sum and V_pi against the stored oracle values: the largest
+    |V - V*| / V_abs (V_abs the same contraction on |factors|, the scale of the
+    rounding of a sum with cancellation), the same relative to |V*|, and U's."""
+    import numpy as np
+    g = stored_values(name)
+    if g is None:
+        return None
+    V, Vs, Va = np.asarray(result[2:]), np.asarray(g["V"]), np.asarray(g["V_abs"])
+    return {"V_max": float(np.max(np.abs(V - Vs) / Va)),
+            "V_max_rel_to_abs_V": float(np.max(np.abs(V - Vs) / np.maximum(np.abs(Vs), 1e-300))),
+            "U_sum": float(abs(result[0] - g["U_sum"]) / g["U_abs"]),
+            "reference": "tests/golden/workload_%s.json (FP64 oracle, n=%d)" % (name, g["n"])}
+
+
+PRODUCTS = {"bf16x3": 6.0, "bf16x4": 10.0, "bf16x5": 15.0, "tf32": 2.0, "fp32": None, "fp64": None}
+
+
+def dominant_roofline(eng, n, precision, prof, nprof, sustained, workload=None, variant=None):
+    """Roofline of the dominant kernel from the per-operation profile of nprof
+    eager evaluations: the tensor-core GEMM (algorithmic flops 2 n per product
+    entry: n (n + 1) / 2 entries for a symmetric product, n^2 otherwise; also
+    given with the plain 2 n^3 count of a product), or, where the s = 3 steps
+    dominate, one whole s = 3 step (2 n^4 flops)."""
+    peaks, peak_src = load_peaks()
+    g_ms, g_cnt = prof.get("gemm", (0.0, 0))
+    per_launch_s = (g_ms / max(1, g_cnt)) / 1e3
+    gemm_lines = [l for l in eng.plan.describe().splitlines() if " gemm " in l]
+    entries = [(n * (n + 1) / 2 if "sym=1" in l else n * n) for l in gemm_lines]
+    alg_flops = 2.0 * n * (sum(entries) / max(1, len(entries)))
+    plain_flops = 2.0 * float(n) ** 3
+    kernel_note = "tc_gemm_kernel (%s)" % precision
+    g3_ms, _ = prof.get("gemm3", (0.0, 0))
+    if g3_ms > g_ms:
+        g_cnt = eng.plan.info["n_gemm3"] * nprof
+        g_ms = g3_ms
+        per_launch_s = (g3_ms / g_cnt) / 1e3
+        alg_flops = plain_flops = 2.0 * float(n) ** 4
+        kernel_note = "tc_gemm_kernel (%s), one s = 3 step of batched launches" % precision
+    bf16_peak = peaks.get("bf16_tflops_sustained", 1700.0) if sustained else peaks.get("bf16_tflops", 1900.0)
+    products = PRODUCTS.get(precision)
+    if not (g_cnt and products):
+        return None
+    achieved = alg_flops / per_launch_s / 1e12
+    peak = bf16_peak / products
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": TRAFFIC.get((workload, precision, variant)), "kernel": kernel_note,
+            "peak_note": "%s bf16 dense %.1f TFLOP/s (%s) / %g tensor products per algorithmic multiply-add" % (
+                peak_src, bf16_peak, "sustained" if sustained else "burst", products),
+            "per_launch_ms": per_launch_s * 1e3,
+            "algorithmic_flops_per_launch": alg_flops,
+            "plain_2n3_count": {"flops_per_launch": plain_flops, "achieved": plain_flops / per_launch_s / 1e12,
+                                "frac": plain_flops / per_launch_s / 1e12 / peak,
+                                "note": "every product counted as 2 n^3 (2 n^4 per s = 3 step), the scope table's "
+                                        "count; a symmetric product computes only n (n + 1) / 2 of its n^2 entries, "
+                                        "so this count can exceed the peak"}}
+
+
+def measure_extra_peaks(dev):
+    """The dense TF32 and FP64 matrix-multiply rates of this GPU (torch.matmul,
+    8192^3, best of 3, CUDA events): the denominators for the tf32 mode and for
+    the FP64 comparator, which the driver's peak file does not hold."""
+    import torch
+    out = {}
+    old = torch.backends.cuda.matmul.allow_tf32
+    try:
+        for key, dt, tf32 in (("tf32_tflops", torch.float32, True), ("fp64_tflops", torch.float64, False)):
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            N = 8192
+            a = torch.randn(N, N, dtype=dt, device=dev)
+            b = torch.randn(N, N, dtype=dt, device=dev)
+            torch.matmul(a, b)
+            best = None
+            for _ in range(3):
+                s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s.record()
+                torch.matmul(a, b)
+                e.record()
+                torch.cuda.synchronize()
+                t = s.elapsed_time(e) / 1e3
+                best = t if best is None else min(best, t)
+            out[key] = 2.0 * N ** 3 / best / 1e12
+            del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old
+    out["how"] = "torch.matmul 8192^3 (2 N^3 flops), best of 3, CUDA events, in this run"
+    return out
+
+
+def measure_workload(name, precision, dev, steps, warmup, with_fp64, fp64_peak=None):
+    """One single-sample workload at its full size: graph-replay time over `steps`
+    (L2 flushed before each), the dominant kernel's roofline from one profiled
+    eager pass, the error against the stored oracle values, and the plain FP64
+    GPU form's time with its fraction of the measured FP64 matmul rate."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2508_12627_gb300 import engine, ustat as us
+    w = synth.workload(name)
+    eng = engine.Engine(w.graph, w.factors, precision=precision, device=dev)
+    Xd = eng.to_device(w.X)
+    out = torch.empty(2 + eng.n_parts, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(warmup):
+        eng.launch(Xd, out)
+    torch.cuda.synchronize()
+    bat = us.Batched(eng.plan, [w.n], w.d, max_lanes=1)
+    ws_b = torch.empty(bat.workspace_bytes(), dtype=torch.uint8, device=dev)
+    gstream = torch.cuda.Stream(dev)
+    x_dt = 0 if Xd.dtype == torch.float64 else 1
+    facs = eng.factor_tuples(w.n)
+    with torch.cuda.stream(gstream):
+        bat.capture([Xd.data_ptr()], x_dt, facs, ws_b.data_ptr(), ws_b.numel(), gstream.cuda_stream, out.data_ptr(),
+                    out.data_ptr() + 16)
+        bat.replay(gstream.cuda_stream)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    with torch.cuda.stream(gstream):
+        for k in range(steps):
+            flush.zero_()
+            starts[k].record(gstream)
+            bat.replay(gstream.cuda_stream)
+            ends[k].record(gstream)
+    torch.cuda.synchronize()
+    tot_ms = float(sum(a.elapsed_time(b) for a, b in zip(starts, ends)))
+    result = out.cpu().numpy()
+    del ws_b, bat
+    # one eager pass with per-operation events: the kernel breakdown
+    stream = torch.cuda.current_stream(dev)
+    us.profile_enable(True)
+    us.profile_collect()
+    flush.zero_()
+    eng.launch(Xd, out)
+    torch.cuda.synchronize()
+    us.profile_enable(False)
+    prof = us.profile_collect()
+    ms = tot_ms / steps
+    fl_plan, fl_naive = eng.plan.flops(w.n)
+    rec = {"workload": WORKLOADS[name], "n": w.n, "d": w.d, "partitions": eng.n_parts, "precision": precision,
+           "evals_per_s": 1e3 / ms, "ms_per_eval": ms, "steps": steps,
+           "launch": "one CUDA graph replay per evaluation, L2 flushed before each",
+           "tflops": {"algorithmic_plan": fl_plan / ms / 1e9, "algorithmic_unshared": fl_naive / ms / 1e9},
+           "roofline": dominant_roofline(eng, w.n, precision, prof, 1, tot_ms >= 500.0, name),
+           "profile_ms": {k: v[0] for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
+           "rel_err_vs_oracle": rel_err_vs_stored(name, result)}
+    del eng
+    if with_fp64:
+        e64 = engine.Engine(w.graph, w.factors, precision="fp64", device=dev)
+        o64 = torch.empty(2 + e64.n_parts, dtype=torch.float64, device=dev)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        e64.launch(Xd, o64)
+        e.record(stream)
+        torch.cuda.synchronize()
+        ms64 = s.elapsed_time(e)
+        ach = fl_plan / (ms64 / 1e3) / 1e12
+        rec["fp64_gpu"] = {"ms_per_eval": ms64, "evals_per_s": 1e3 / ms64, "speedup_of_this_mode": ms64 / ms,
+                           "algorithmic_tflops": ach,
+                           "frac_of_measured_fp64_matmul": (ach / fp64_peak) if fp64_peak else None,
+                           "rel_err_vs_oracle": rel_err_vs_stored(name, o64.cpu().numpy()),
+                           "note": "one evaluation, eager launch (no flush)"}
+        del e64
+    torch.cuda.empty_cache()
+    return rec
+
+
+# the per-configuration table of the default run: each single-sample workload in
+# the mode that meets the 1e-8 target there (bf16x4 stores the treewidth-3 and
+# heavy-tailed workloads' products in float64), plus bf16x3 where it is faster
+CONFIG_TABLE = [("triangle_rbf", "bf16x3", 50, True), ("k4_cycle_rbf", "bf16x4", 3, True),
+                ("k4_cycle_rbf", "bf16x3", 3, False), ("path5_chord_linear_tanh", "bf16x4", 3, True),
+                ("path5_chord_linear_tanh", "bf16x3", 3, False)]
+
+
+def config_table(dev, with_fp64):
+    """Every configuration besides the headline one, at its full size, on this GPU."""
+    peaks = measure_extra_peaks(dev)
+    out = {"measured_peaks": peaks}
+    for name, prec, steps, fp64 in CONFIG_TABLE:
+        out["%s/%s" % (name, prec)] = measure_workload(name, prec, dev, steps, 2, with_fp64 and fp64,
+                                                       peaks.get("fp64_tflops"))
+    out["batched/bf16x3"] = batched_measure("bf16x3", dev, 3, 3, full_line=False)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -891,6 +1124,8 @@ def main():
     ap.add_argument("--impl", default="engine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the table of the other configurations (default workload only)")
     ap.add_argument("--variant", type=int, default=None,
                     help="tensor-core GEMM variant for every size class (ustat_plan_set_variant)")
     ap.add_argument("--capture", type=int, default=0,
@@ -1012,44 +1247,10 @@ def main():
     n, d = w.n, w.d
     value = job_value(world, args.steps, tot_ms)
     fl_plan, fl_naive = eng.plan.flops(n)
-    peaks, peak_src = load_peaks()
     launches = sum(c for (_, c) in prof.values())
-    # dominant kernel: the n^3 contraction.  Its algorithmic flops: 2 n per
-    # product entry the algorithm needs (n^2 entries, or n (n + 1) / 2 for a
-    # symmetric product whose reductions are symmetric).
-    g_ms, g_cnt = prof.get("gemm", (0.0, 0))
-    per_launch_s = (g_ms / max(1, g_cnt)) / 1e3
-    gemm_lines = [l for l in eng.plan.describe().splitlines() if " gemm " in l]
-    entries = [(n * (n + 1) / 2 if "sym=1" in l else n * n) for l in gemm_lines]
-    alg_flops = 2.0 * n * (sum(entries) / max(1, len(entries)))
-    kernel_note = "tc_gemm_kernel (%s)" % args.precision
-    g3_ms, _ = prof.get("gemm3", (0.0, 0))
-    if g3_ms > g_ms:
-        # the n^4 steps dominate: one step is n products of n x n x n (2 n^4
-        # flops), timed as a whole (its batched GEMM launches and the operand
-        # splits that overlap them)
-        g_cnt = eng.plan.info["n_gemm3"] * args.steps
-        g_ms = g3_ms
-        per_launch_s = (g3_ms / g_cnt) / 1e3
-        alg_flops = 2.0 * float(n) ** 4
-        kernel_note = "tc_gemm_kernel (%s), one s = 3 step of batched launches" % args.precision
     # the burst peak for a kernel in a short timed region, the sustained one (a
     # seconds-long loop under the power cap) once the timed region lasts 0.5 s
-    sustained = tot_ms >= 500.0
-    bf16_peak = peaks.get("bf16_tflops_sustained", 1700.0) if sustained else peaks.get("bf16_tflops", 1900.0)
-    # tensor products per algorithmic multiply-add (tf32 runs at half the bf16 rate)
-    products = {"bf16x3": 6.0, "bf16x4": 10.0, "bf16x5": 15.0, "tf32": 2.0, "fp32": None, "fp64": None}[args.precision]
-    roof = None
-    if g_cnt and products:
-        achieved = alg_flops / per_launch_s / 1e12
-        peak = bf16_peak / products
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": TRAFFIC.get((args.workload, args.precision, args.variant)),
-                "kernel": kernel_note,
-                "peak_note": "%s bf16 dense %.1f TFLOP/s (%s) / %g tensor products per algorithmic "
-                             "multiply-add" % (peak_src, bf16_peak, "sustained" if sustained else "burst",
-                                               products),
-                "per_launch_ms": per_launch_s * 1e3}
+    roof = dominant_roofline(eng, n, args.precision, prof, args.steps, tot_ms >= 500.0, args.workload, args.variant)
     prof_share = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
                   for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
 
@@ -1115,7 +1316,7 @@ def main():
         torch.cuda.synchronize()
         ms64 = s.elapsed_time(e) / reps
         fp64 = {"evals_per_s": 1e3 / ms64, "ms_per_step": ms64, "speedup_of_this_mode": (1e3 / ms64) and value / (
-            1e3 / ms64)}
+            1e3 / ms64), "algorithmic_tflops": fl_plan / (ms64 / 1e3) / 1e12}
         # this mode's results against the FP64 GPU form (itself checked against the
         # oracle at smaller n by the parity tests): per-V relative differences
         r64 = o64.cpu().numpy()
@@ -1123,9 +1324,10 @@ def main():
         fp64["rel_diff_of_this_mode"] = {"U_sum": float(abs(result[0] - r64[0]) / abs(r64[0])),
                                          "V_max": float(dv.max()), "V_median": float(np.median(dv))}
 
-    # ---- CPU baseline: the FP64 oracle on the host cores, and the error of this run
+    # ---- CPU baseline: the FP64 oracle on the host cores; the error of this run
+    # against the oracle's stored values
     cpu = None
-    err = None
+    err = rel_err_vs_stored(args.workload, result)
     if not args.no_cpu_baseline:
         # a bounded sample: the oracle on samples of the same distribution, doubling
         # n while the next size is predicted (by the growth of the plan's unshared
@@ -1140,13 +1342,9 @@ def main():
             if ns < n:
                 t_ns = oracle_eval(synth.workload(args.workload, ns))[1]
         if ns == n:
-            ref, dt = oracle_eval(w)
+            _, dt = oracle_eval(w)
             cpu = {"value": 1.0 / dt, "unit": "evals/s", "cores": host_cores(), "kind": "oracle",
                    "sample": "one full evaluation of the workload (n=%d, all %d partitions)" % (n, eng.n_parts)}
-            V = result[2:]
-            Vr = np.asarray(ref["V"])
-            err = {"U_sum": abs(result[0] - ref["U_sum"]) / abs(ref["U_sum"]),
-                   "V_max": float(np.max(np.abs(V - Vr) / np.abs(Vr)))}
         else:
             dt = t_ns
             scale = eng.plan.flops(n)[1] / eng.plan.flops(ns)[1]
@@ -1154,6 +1352,15 @@ def main():
                    "sample": "one full evaluation at n=%d (same distribution, all %d partitions), %.2f s, scaled "
                              "by the ratio %.3g of the unshared elimination flops at n=%d" % (
                                  ns, eng.n_parts, dt, scale, n)}
+
+    # the other configurations at their full sizes (one GPU, rank 0 of a 1-GPU run)
+    configs = None
+    if args.workload == "c4_rbf" and world == 1 and not args.no_configs and args.variant is None:
+        configs = config_table(dev, not args.no_fp64)
+        if fp64 is not None:
+            fp64["frac_of_measured_fp64_matmul"] = fp64["algorithmic_tflops"] / configs["measured_peaks"][
+                "fp64_tflops"]
+            fp64["rel_err_vs_oracle"] = rel_err_vs_stored(args.workload, r64)
 
     line = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
@@ -1178,6 +1385,7 @@ def main():
         "rel_err_vs_oracle": err,
         "wall_s_timed_region": wall,
         "profile": prof_share,
+        "configs": configs,
     }
     print(json.dumps(line), flush=True)
     if dist:

@@ -43,7 +43,7 @@ extern "C" {
 #define USTAT_ERR_N_LT_M          -2  /* n < m: the paper's U-statistic needs m <= n (Section 2.1) */
 #define USTAT_ERR_TW_TOO_LARGE    -3  /* no elimination order with steps the engine executes */
 #define USTAT_ERR_WORKSPACE       -4  /* workspace null, too small or misaligned */
-#define USTAT_ERR_NONFINITE       -5  /* reserved */
+#define USTAT_ERR_NONFINITE       -5  /* an input value is NaN or infinite (ustat_status) */
 #define USTAT_ERR_CUDA            -6  /* a CUDA call failed (see ustat_last_cuda_error) */
 #define USTAT_ERR_DEVICE_TIMEOUT  -7  /* a bounded device wait ran out */
 #define USTAT_ERR_UNSUPPORTED     -8  /* m > 7, arity > 2, or a mode not built */
@@ -199,16 +199,39 @@ int ustat_workspace_bytes(const ustat_plan_t *plan, int64_t n, int d, size_t *by
 int ustat_eval(ustat_plan_t *plan, const void *X, int x_dtype, int64_t n, int d,
                const ustat_factor *factors, int n_factors, void *ws, size_t ws_bytes,
                void *stream, double *U_out, double *V_out);
+/* Treewidth-3 steps in the split modes run their GEMMs on a second stream that
+ * each host thread creates (with two events) at its first such evaluation on a
+ * device: on a new thread, make that first call before any stream capture. */
 
 /*
  * Device status of the last evaluation that used workspace ws on stream: waits for
  * the stream, reads the workspace's error word (its first 4 bytes) and sets
- * *device_status to USTAT_OK, or to USTAT_ERR_DEVICE_TIMEOUT when a bounded device
- * wait (an mbarrier wait of the tensor-core GEMM) gave up; that evaluation's U and
- * V are then NaN.  Host call; blocks until the stream's work is done.  Errors:
- * USTAT_ERR_INVALID_ARG for a NULL ws or device_status, USTAT_ERR_CUDA.
+ * *device_status to
+ *   USTAT_OK,
+ *   USTAT_ERR_DEVICE_TIMEOUT when a bounded device wait (an mbarrier wait of the
+ *     tensor-core GEMM) gave up, or else
+ *   USTAT_ERR_NONFINITE when an input value read by the evaluation (X, MATRIX or
+ *     VECTOR data, the TANH_DOT weights through x . w) is NaN or infinite: the
+ *     paper's U-statistic is a finite sum of finite terms (Section 2.1,
+ *     Definition "U-Statistic"), which such an input has not.
+ * In both error cases that evaluation's U and V are NaN.  Host call; blocks until
+ * the stream's work is done.  Errors: USTAT_ERR_INVALID_ARG for a NULL ws or
+ * device_status, USTAT_ERR_CUDA.
  */
 int ustat_status(const void *ws, void *stream, int *device_status);
+
+/*
+ * Test hook of the bounded device waits, off by default; not for production use.
+ * Every later tensor-core GEMM launched by this process gives up a wait after
+ * limit_cycles SM cycles (0 restores the default of about 4e9 cycles, two
+ * seconds) and, with stall_producer != 0, issues no TMA copy at all, so that its
+ * first wait runs out with nothing in flight: the evaluation then reports
+ * USTAT_ERR_DEVICE_TIMEOUT through ustat_status and NaN results, and a later
+ * evaluation with the hook off, on the same workspace, is correct again.  The
+ * setting is process-wide (not per thread); set it with no evaluation in flight.
+ * Errors: USTAT_ERR_INVALID_ARG for a negative limit.
+ */
+int ustat_debug_set_wait(long long limit_cycles, int stall_producer);
 
 /*
  * Same computation with host inputs and outputs: X_host (n x d, x_dtype) is
@@ -271,8 +294,10 @@ int ustat_batch_workspace_bytes(const ustat_plan_t *plan, const int64_t *n, int 
  * 3: larger; -1: all): bits 0-1 pick the tensor-core GEMM's tile raster group (8,
  * 4, 16 or 2 tile rows), bits 2-3 its tile shape (0: 128 x 128 with 128-byte
  * k-blocks; 1: 128 x 64, bf16x3 only; 2: 128 x 128 with 64-byte k-blocks and a
- * deeper pipeline), bit 4 the RBF kernel-matrix build's tile (0: 128 x 128 with
- * 256 threads; 1: 64 x 64 with 128 threads).  Results agree to the mode's
+ * deeper pipeline), bit 5 the RBF kernel-matrix build in the float32-storage
+ * modes (0: squared distances from the Gram matrix X X^T on the tensor cores;
+ * 1: direct differences on the CUDA cores), bit 4 the latter's tile (0: 128 x 128
+ * with 256 threads; 1: 64 x 64 with 128 threads).  Results agree to the mode's
  * tolerance across variants (summation orders differ).  The autotuner below
  * sets these itself.
  */
@@ -391,6 +416,15 @@ int ustat_plan_learned(const ustat_graph *graph, const ustat_options *opts, int6
 int ustat_eval_noalloc(ustat_plan_t *plan, const void *X, int x_dtype, int64_t n, int d,
                        const ustat_factor *factors, int n_factors, void *stream, double *U_out,
                        double *V_out);
+
+/*
+ * ustat_status for ustat_eval_noalloc, whose callers never see the scratch
+ * array's device address: waits for `stream` and reads the error word of the
+ * current device's array (the status of the last no-allocation evaluation on
+ * this device).  USTAT_OK when no such evaluation has run on this device yet.
+ * Errors: USTAT_ERR_INVALID_ARG (NULL device_status), USTAT_ERR_CUDA.
+ */
+int ustat_noalloc_status(void *stream, int *device_status);
 
 /*
  * Per-operation timing for measurement.  While enabled (per host thread), every

@@ -18,7 +18,8 @@ LIB = os.path.join(OUT_DIR, "libustat.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(os.path.dirname(HERE), "include")]
-SOURCES = ["api.cu", "planner.cpp", "k_elem.cu", "k_hb.cu", "k_gemm_simt.cu", "k_gemm_tc.cu", "ranker.cu"]
+SOURCES = ["api.cu", "planner.cpp", "k_elem.cu", "k_hb.cu", "k_gemm_simt.cu", "k_gemm_tc.cu", "k_gram_tc.cu",
+           "ranker.cu"]
 
 
 def _nvcc():

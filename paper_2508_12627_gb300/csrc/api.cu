@@ -75,6 +75,7 @@ struct Layout {
     std::vector<size_t> off;     // per slot
     std::vector<int> scal_index; // per slot: index into the scalar array (or -1)
     size_t err_off = 0, scal_off = 0, zero_bytes = 0, xw_off = 0, total = 0;
+    size_t kb_off = 0;   // scratch of the tensor-core RBF build (X digits, scales, norms)
     int64_t ldp_slices = 0, ldp_prep = 0;
     // s = 3 steps on the tensor cores: digit planes of g3_nb A operands at a time
     size_t g3_off = 0, g3_stride = 0;
@@ -86,6 +87,14 @@ bool tc_gemm3(const Plan &P) {
     if (!is_split_mode(P.precision)) return false;
     for (auto &op : P.ops)
         if (op.kind == OP_GEMM3) return true;
+    return false;
+}
+
+// an RBF kernel matrix built in float32 (the tensor-core Gram build's scratch)
+bool has_rbf_f32_build(const Plan &P) {
+    if (wide_storage(P.precision)) return false;
+    for (auto &op : P.ops)
+        if (op.kind == OP_KBUILD && op.factor >= 0 && P.factor_kind[op.factor] == USTAT_RBF) return true;
     return false;
 }
 
@@ -124,6 +133,10 @@ Layout make_layout(const Plan &P, int64_t n, int d) {
     if (needs_xw(P)) {
         L.xw_off = cur;
         cur = align_up(cur + esz * (size_t)n * d, 1024);
+    }
+    if (has_rbf_f32_build(P)) {
+        L.kb_off = cur;
+        cur = align_up(cur + kbuild_rbf_tc_scratch_bytes(n, d), 1024);
     }
     for (size_t s = 0; s < P.slots.size(); ++s) {
         switch (P.slots[s].kind) {
@@ -246,7 +259,7 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
         if (op.kind == OP_KBUILD && f[op.factor].kind != USTAT_RBF) direct_x = false;
     if (needs_xw(P) && !direct_x) {
         ProfScope ps(kProfXconvert, C.st);
-        e = launch_xconvert(X, x_dtype, n, C.d, C.ws + C.L.xw_off, C.fp64, C.st);
+        e = launch_xconvert(X, x_dtype, n, C.d, C.ws + C.L.xw_off, C.fp64, err, C.st);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     const int lead = split_lead_bits(n);
@@ -262,6 +275,18 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                         rvec[r] = P.slots[op.red[r].out].kind == S_VEC;
                         rout[r] = C.vec(op.red[r].out);   // scalar and vector slots are float64
                     }
+                    const int var = P.tc_variant[tc_size_class(n)];
+                    if (!((var >> 5) & 1) && C.d <= 256) {
+                        // default: squared distances from the Gram matrix on the tensor cores
+                        e = launch_kbuild_rbf_tc(X, x_dtype, n, C.d, f[op.factor].param, P.sparsify,
+                                                 (float *)C.ptr(op.out), op.opA >= 0 ? C.ptr(op.opA) : nullptr,
+                                                 C.L.ldp_slices, lead, split_planes_of(P.precision),
+                                                 op.opA >= 0 ? C.scales(op.opA) : nullptr, op.nred, rpow, rvec, rout,
+                                                 op.upper_only, C.ws + C.L.kb_off, err, C.st);
+                        ps.kernels = 2;
+                        break;
+                    }
+                    // variant bit 5: direct differences on the CUDA cores
                     const float *xf = direct_x ? (x_dtype == 1 ? (const float *)X : nullptr)
                                                : (const float *)(C.ws + C.L.xw_off);
                     const double *xd = direct_x && x_dtype == 0 ? (const double *)X : nullptr;
@@ -269,7 +294,7 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                                           (float *)C.ptr(op.out), op.opA >= 0 ? C.ptr(op.opA) : nullptr,
                                           C.L.ldp_slices, lead, split_planes_of(P.precision),
                                           op.opA >= 0 ? C.scales(op.opA) : nullptr, op.nred, rpow, rvec, rout,
-                                          op.upper_only, (P.tc_variant[tc_size_class(n)] >> 4) & 1, C.st);
+                                          op.upper_only, (var >> 4) & 1, err, C.st);
                 } else {
                     if (op.nred) return USTAT_ERR_UNSUPPORTED;   // the planner fuses only into the RBF build
                     if (C.fp64 && f[op.factor].kind == USTAT_LINEAR && x_dtype == 1)
@@ -281,13 +306,13 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                 }
                 break;
             case OP_LOADMAT:
-                e = launch_loadmat((const double *)f[op.factor].data, n, C.fp64, P.sparsify, C.ptr(op.out), C.st);
+                e = launch_loadmat((const double *)f[op.factor].data, n, C.fp64, P.sparsify, C.ptr(op.out), err, C.st);
                 break;
             case OP_UNARY:
-                e = launch_unary_tanh(X, x_dtype, n, C.d, (const double *)f[op.factor].data, C.vec(op.out), C.st);
+                e = launch_unary_tanh(X, x_dtype, n, C.d, (const double *)f[op.factor].data, C.vec(op.out), err, C.st);
                 break;
             case OP_LOADVEC:
-                e = launch_copyvec((const double *)f[op.factor].data, n, C.vec(op.out), C.st);
+                e = launch_copyvec((const double *)f[op.factor].data, n, C.vec(op.out), err, C.st);
                 break;
             case OP_DIAG:
                 if (op.factor >= 0 && f[op.factor].kind != USTAT_TANH_DOT && f[op.factor].kind != USTAT_VECTOR)
@@ -527,6 +552,14 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
 }  // namespace
 
 int ustat::record_cuda_error(int e) { return cuda_fail((cudaError_t)e); }
+
+// The status an evaluation's error word stands for: a bounded wait that gave up
+// first, then a non-finite input.
+int ustat::status_of_word(int word) {
+    if (word & kErrWordTimeout) return USTAT_ERR_DEVICE_TIMEOUT;
+    if (word & kErrWordNonfinite) return USTAT_ERR_NONFINITE;
+    return USTAT_OK;
+}
 
 extern "C" {
 
@@ -885,7 +918,7 @@ int ustat_status(const void *ws, void *stream, int *device_status) {
     int word = 0;   // every workspace layout starts with the error word (Layout::err_off = 0)
     e = cudaMemcpy(&word, ws, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e);
-    *device_status = word != 0 ? USTAT_ERR_DEVICE_TIMEOUT : USTAT_OK;
+    *device_status = status_of_word(word);
     return USTAT_OK;
 }
 
@@ -958,6 +991,12 @@ int ustat_eval_batch(ustat_plan_t *plan, const void *const *X, int x_dtype, cons
                             V_out ? V_out + (size_t)i * np : nullptr);
         if (rc != USTAT_OK) return rc;
     }
+    return USTAT_OK;
+}
+
+int ustat_debug_set_wait(long long limit_cycles, int stall_producer) {
+    if (limit_cycles < 0) return USTAT_ERR_INVALID_ARG;
+    set_tc_debug(limit_cycles, stall_producer);
     return USTAT_OK;
 }
 
@@ -1120,6 +1159,25 @@ extern "C" int ustat_eval_noalloc(ustat_plan_t *plan, const void *X, int x_dtype
                       V_out);
 }
 
+extern "C" int ustat_noalloc_status(void *stream, int *device_status) {
+    if (!device_status) return USTAT_ERR_INVALID_ARG;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (dev < 0 || dev >= kNoallocMaxDevices) return USTAT_ERR_UNSUPPORTED;
+    void *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        base = g_noalloc_addr[dev];
+    }
+    if (!base) {
+        // no evaluation on this device yet: nothing can have failed
+        *device_status = USTAT_OK;
+        return USTAT_OK;
+    }
+    return ustat_status(base, stream, device_status);
+}
+
 // ---------------------------------------------------------------- batched evaluation
 // Samples spread over CUDA streams ("lanes") by longest-processing-time first,
 // each lane with its own workspace region; the lanes fork from and join into
@@ -1231,7 +1289,7 @@ int batched_check(ustat_batched *b, const void *const *X, int x_dtype, const ust
 extern "C" {
 
 int ustat_plan_set_variant(ustat_plan_t *plan, int size_class, int variant) {
-    if (!plan || size_class < -1 || size_class > 3 || variant < 0 || variant > 31 || ((variant >> 2) & 3) == 3)
+    if (!plan || size_class < -1 || size_class > 3 || variant < 0 || variant > 63 || ((variant >> 2) & 3) == 3)
         return USTAT_ERR_INVALID_ARG;
     for (int c = 0; c < 4; ++c)
         if (size_class < 0 || c == size_class) plan->p.tc_variant[c] = variant;
@@ -1397,12 +1455,15 @@ int ustat_batched_autotune(ustat_batched_t *b, const void *const *X, int x_dtype
         bool rbf_build = false;
         for (auto &op : P.ops)
             rbf_build |= op.kind == OP_KBUILD && P.factor_kind[op.factor] == USTAT_RBF && !wide_storage(P.precision);
-        for (int kb = 0; kb < (rbf_build ? 2 : 1); ++kb)
+        // RBF builds: the tensor-core Gram build (bits 4-5 clear), or the CUDA-core
+        // build with either tile (bit 5 set, bit 4 the tile)
+        const int builds[3] = {0, 32, 48};
+        for (int kb = 0; kb < (rbf_build ? 3 : 1); ++kb)
             for (int shape = 0; shape < 3; ++shape) {
                 if (P.precision == USTAT_BF16X4 && shape == 1) continue;
                 if (P.precision == USTAT_BF16X5 && shape != 2) continue;
                 if (P.precision == USTAT_TF32 && shape > 0) continue;
-                for (int gr = 0; gr < 4; ++gr) vars.push_back(gr | (shape << 2) | (kb << 4));
+                for (int gr = 0; gr < 4; ++gr) vars.push_back(gr | (shape << 2) | builds[kb]);
             }
         for (int c = 0; c < 4 && rc == USTAT_OK; ++c) {
             if (!present[c]) continue;

@@ -6,19 +6,31 @@
 
 #include "kcommon.cuh"
 #include "kernels.h"
+#include "kmath.cuh"
 #include "../../include/ustat.h"
 
 namespace ustat {
 
 namespace {
 
+// Error-word bit of a non-finite input (bit 0 is a bounded wait that gave up).
+constexpr int kErrNonfinite = kErrWordNonfinite;
+
+// Records a non-finite input value in the error word.
+__device__ __forceinline__ void flag_nonfinite(bool bad, int *err) {
+    if (bad && err) atomicOr(err, kErrNonfinite);
+}
+
 template <typename T>
-__global__ void xconvert_kernel(const void *X, int x_dtype, int64_t total, T *out) {
+__global__ void xconvert_kernel(const void *X, int x_dtype, int64_t total, T *out, int *err) {
+    bool bad = false;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
         double v = x_dtype == 0 ? ((const double *)X)[t] : (double)((const float *)X)[t];
+        bad |= !isfinite(v);
         out[t] = (T)v;
     }
+    flag_nonfinite(bad, err);
 }
 
 // exp(z) in float32 arithmetic with only one rounding that matters: the result is
@@ -175,72 +187,8 @@ struct RbfArgs {
     int nred;
     RbfRed red[kRbfMaxRed];
     int upper_only;   // K itself is read only on and above the diagonal: no mirror stores of K
+    int *err;         // error word: the diagonal tiles flag a non-finite X
 };
-
-// two float32 in one 64-bit register pair (first = low half)
-typedef unsigned long long f32x2;
-__device__ __forceinline__ f32x2 f2_pack(float a, float b) {
-    f32x2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void f2_unpack(f32x2 r, float &a, float &b) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
-}
-__device__ __forceinline__ f32x2 f2_add(f32x2 a, f32x2 b) {
-    f32x2 r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f32x2 f2_sub(f32x2 a, f32x2 b) {
-    f32x2 r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b) {
-    f32x2 r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
-    f32x2 r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
-__device__ __forceinline__ f32x2 f2_splat(float a) { return f2_pack(a, a); }
-__device__ __forceinline__ f32x2 f2_rint(f32x2 a) {
-    float x, y;
-    f2_unpack(a, x, y);
-    return f2_pack(rintf(x), rintf(y));
-}
-
-// exp(-d2 * inv_h) for two squared distances: the steps of exp_unbiased, each
-// the same IEEE operation per lane
-__device__ __forceinline__ f32x2 f2_rbf(f32x2 d2, float inv_h) {
-    const f32x2 z = f2_mul(d2, f2_splat(-inv_h));
-    const f32x2 k = f2_rint(f2_mul(z, f2_splat(1.44269504088896341f)));
-    const f32x2 fh = f2_fma(k, f2_splat(-0.693145751953125f), z);   // exact
-    const f32x2 fl = f2_mul(k, f2_splat(-1.42860682030941723212e-6f));
-    const f32x2 f = f2_add(fh, fl);
-    f32x2 q = f2_fma(f2_splat(1.0f / 40320.0f), f, f2_splat(1.0f / 5040.0f));
-    q = f2_fma(q, f, f2_splat(1.0f / 720.0f));
-    q = f2_fma(q, f, f2_splat(1.0f / 120.0f));
-    q = f2_fma(q, f, f2_splat(1.0f / 24.0f));
-    q = f2_fma(q, f, f2_splat(1.0f / 6.0f));
-    q = f2_fma(q, f, f2_splat(0.5f));
-    q = f2_mul(f2_mul(q, f), f);
-    const f32x2 one = f2_splat(1.0f);
-    const f32x2 sh = f2_add(one, fh);                        // Fast2Sum (|1| >= |fh|)
-    const f32x2 sl = f2_sub(fh, f2_sub(sh, one));
-    const f32x2 y = f2_add(sh, f2_add(f2_add(sl, fl), q));
-    float k0, k1, z0, z1;
-    f2_unpack(k, k0, k1);
-    f2_unpack(z, z0, z1);
-    const f32x2 p2 = f2_pack(__int_as_float(((int)k0 + 127) << 23), __int_as_float(((int)k1 + 127) << 23));
-    float r0, r1;
-    f2_unpack(f2_mul(y, p2), r0, r1);
-    return f2_pack(z0 < -87.0f ? 0.0f : r0, z1 < -87.0f ? 0.0f : r1);
-}
 
 // one row of a thread's entries (four pairs); out of line with the four pairs
 // interleaved, so that the kernel's code stays small while each call still has
@@ -350,12 +298,16 @@ __global__ void __launch_bounds__(256, 2) kbuild_rbf_tile_kernel(RbfArgs g) {
 #pragma unroll
         for (int h = 0; h < 4; ++h) acc[a][h] = f2_splat(0.f);
     const bool xvec = g.xvec != 0;
+    // every row of X is staged once as the row side of its diagonal tile: that
+    // staging also checks it for non-finite values
+    bool bad = false;
     for (int k0 = 0; k0 < g.d; k0 += 32) {
         __syncthreads();
         // stage rows i0.. and j0.., 32 coordinates, transposed (consecutive lanes:
         // consecutive rows, so the shared-memory writes do not conflict)
         for (int e = tid; e < 2 * kRbfT * 8; e += 256) {
             const int opnd = e >> 10, row = e & (kRbfT - 1), kq = (e >> 7) & 7;
+            const bool check = diag_tile && opnd == 0;
             const int64_t gr = (opnd ? j0 : i0) + row;
             const int k = k0 + 4 * kq;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -366,11 +318,14 @@ __global__ void __launch_bounds__(256, 2) kbuild_rbf_tile_kernel(RbfArgs g) {
                         const double2 p0 = *reinterpret_cast<const double2 *>(src);
                         const double2 p1 = *reinterpret_cast<const double2 *>(src + 2);
                         v = make_float4((float)p0.x, (float)p0.y, (float)p1.x, (float)p1.y);
+                        if (check) bad |= !(isfinite(p0.x) && isfinite(p0.y) && isfinite(p1.x) && isfinite(p1.y));
                     } else {
-                        v.x = (float)src[0];
-                        if (k + 1 < g.d) v.y = (float)src[1];
-                        if (k + 2 < g.d) v.z = (float)src[2];
-                        if (k + 3 < g.d) v.w = (float)src[3];
+                        double q[4] = {src[0], 0.0, 0.0, 0.0};
+                        if (k + 1 < g.d) q[1] = src[1];
+                        if (k + 2 < g.d) q[2] = src[2];
+                        if (k + 3 < g.d) q[3] = src[3];
+                        v = make_float4((float)q[0], (float)q[1], (float)q[2], (float)q[3]);
+                        if (check) bad |= !(isfinite(q[0]) && isfinite(q[1]) && isfinite(q[2]) && isfinite(q[3]));
                     }
                 } else {
                     const float *src = g.X + gr * g.d + k;
@@ -382,6 +337,7 @@ __global__ void __launch_bounds__(256, 2) kbuild_rbf_tile_kernel(RbfArgs g) {
                         if (k + 2 < g.d) v.z = src[2];
                         if (k + 3 < g.d) v.w = src[3];
                     }
+                    if (check) bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w));
                 }
             }
             if (opnd == 0) {
@@ -420,6 +376,7 @@ __global__ void __launch_bounds__(256, 2) kbuild_rbf_tile_kernel(RbfArgs g) {
             }
         }
     }
+    if (diag_tile) flag_nonfinite(bad, g.err);
     // entries: exp off the diagonal, the diagonal exactly, zero in the padding
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
@@ -590,10 +547,12 @@ __global__ void __launch_bounds__(128, 8) kbuild_rbf_tile64_kernel(RbfArgs g) {
 #pragma unroll
         for (int h = 0; h < 4; ++h) acc[a][h] = f2_splat(0.f);
     const bool xvec = g.xvec != 0;
+    bool bad = false;   // as in the 128-tile form: diagonal tiles check X
     for (int k0 = 0; k0 < g.d; k0 += 32) {
         __syncthreads();
         for (int e = tid; e < 2 * kRbfT64 * 8; e += 128) {
             const int opnd = e >> 9, row = e & (kRbfT64 - 1), kq = (e >> 6) & 7;
+            const bool check = diag_tile && opnd == 0;
             const int64_t gr = (opnd ? j0 : i0) + row;
             const int k = k0 + 4 * kq;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -604,11 +563,14 @@ __global__ void __launch_bounds__(128, 8) kbuild_rbf_tile64_kernel(RbfArgs g) {
                         const double2 p0 = *reinterpret_cast<const double2 *>(src);
                         const double2 p1 = *reinterpret_cast<const double2 *>(src + 2);
                         v = make_float4((float)p0.x, (float)p0.y, (float)p1.x, (float)p1.y);
+                        if (check) bad |= !(isfinite(p0.x) && isfinite(p0.y) && isfinite(p1.x) && isfinite(p1.y));
                     } else {
-                        v.x = (float)src[0];
-                        if (k + 1 < g.d) v.y = (float)src[1];
-                        if (k + 2 < g.d) v.z = (float)src[2];
-                        if (k + 3 < g.d) v.w = (float)src[3];
+                        double q[4] = {src[0], 0.0, 0.0, 0.0};
+                        if (k + 1 < g.d) q[1] = src[1];
+                        if (k + 2 < g.d) q[2] = src[2];
+                        if (k + 3 < g.d) q[3] = src[3];
+                        v = make_float4((float)q[0], (float)q[1], (float)q[2], (float)q[3]);
+                        if (check) bad |= !(isfinite(q[0]) && isfinite(q[1]) && isfinite(q[2]) && isfinite(q[3]));
                     }
                 } else {
                     const float *src = g.X + gr * g.d + k;
@@ -620,6 +582,7 @@ __global__ void __launch_bounds__(128, 8) kbuild_rbf_tile64_kernel(RbfArgs g) {
                         if (k + 2 < g.d) v.z = src[2];
                         if (k + 3 < g.d) v.w = src[3];
                     }
+                    if (check) bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w));
                 }
             }
             if (opnd == 0) {
@@ -652,6 +615,7 @@ __global__ void __launch_bounds__(128, 8) kbuild_rbf_tile64_kernel(RbfArgs g) {
                 }
         }
     }
+    if (diag_tile) flag_nonfinite(bad, g.err);
     auto colof = [&](int c) { return 4 * tx + (c & 3) + 32 * (c >> 2); };   // c < 8
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
@@ -857,30 +821,42 @@ __global__ void __launch_bounds__(256) kbuild_kernel(int kind, T inv_param, cons
 }
 
 template <typename T>
-__global__ void loadmat_kernel(const double *src, int64_t n, int zero_diag, T *dst) {
+__global__ void loadmat_kernel(const double *src, int64_t n, int zero_diag, T *dst, int *err) {
     const int64_t total = n * n;
+    bool bad = false;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
-        T v = (T)src[t];
+        const double x = src[t];
+        bad |= !isfinite(x);
+        T v = (T)x;
         if (zero_diag && (t / n) == (t % n)) v = 0;
         dst[t] = v;
     }
+    flag_nonfinite(bad, err);
 }
 
-__global__ void unary_tanh_kernel(const void *X, int x_dtype, int64_t n, int d, const double *w, double *out) {
+__global__ void unary_tanh_kernel(const void *X, int x_dtype, int64_t n, int d, const double *w, double *out,
+                                  int *err) {
+    bool bad = false;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double s = 0.0;
         for (int k = 0; k < d; ++k) {
             double x = x_dtype == 0 ? ((const double *)X)[i * d + k] : (double)((const float *)X)[i * d + k];
             s = fma(x, w[k], s);
         }
+        bad |= !isfinite(s);   // a non-finite x or w makes the dot product non-finite
         out[i] = tanh(s);
     }
+    flag_nonfinite(bad, err);
 }
 
-__global__ void copyvec_kernel(const double *src, int64_t n, double *dst) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+__global__ void copyvec_kernel(const double *src, int64_t n, double *dst, int *err) {
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        bad |= !isfinite(src[i]);
         dst[i] = src[i];
+    }
+    flag_nonfinite(bad, err);
 }
 
 template <typename T>
@@ -1030,10 +1006,11 @@ int grid_for(int64_t total, int threads) {
 
 }  // namespace
 
-cudaError_t launch_xconvert(const void *X, int x_dtype, int64_t n, int d, void *Xw, bool fp64, cudaStream_t s) {
+cudaError_t launch_xconvert(const void *X, int x_dtype, int64_t n, int d, void *Xw, bool fp64, int *err,
+                            cudaStream_t s) {
     int64_t total = n * d;
-    if (fp64) xconvert_kernel<double><<<grid_for(total, 256), 256, 0, s>>>(X, x_dtype, total, (double *)Xw);
-    else xconvert_kernel<float><<<grid_for(total, 256), 256, 0, s>>>(X, x_dtype, total, (float *)Xw);
+    if (fp64) xconvert_kernel<double><<<grid_for(total, 256), 256, 0, s>>>(X, x_dtype, total, (double *)Xw, err);
+    else xconvert_kernel<float><<<grid_for(total, 256), 256, 0, s>>>(X, x_dtype, total, (float *)Xw, err);
     return cudaGetLastError();
 }
 
@@ -1059,11 +1036,11 @@ cudaError_t launch_kbuild_linear_wide(const float *X, int64_t n, int d, double p
 cudaError_t launch_kbuild_rbf(const float *Xw, const double *Xd, int64_t n, int d, double param, int zero_diag,
                               float *K, void *slices, int64_t ldp, int lead_bits, int planes, float *scales, int nred,
                               const int *red_pow, const int *red_vec, double *const *red_out, int upper_only,
-                              int tile64, cudaStream_t s) {
+                              int tile64, int *err, cudaStream_t s) {
     if (nred < 0 || nred > kRbfMaxRed || planes < 3 || planes > 5 || (!Xw && !Xd)) return cudaErrorInvalidValue;
     const int xvec = (d % 4) == 0 && ((uintptr_t)(Xw ? (const void *)Xw : (const void *)Xd) % 16) == 0;
     RbfArgs g{Xw, Xd, xvec, n, d, (float)(1.0 / param), zero_diag, K, (__nv_bfloat16 *)slices, slices ? ldp : n,
-              lead_bits, planes, slices ? scales : nullptr, nred, {}, upper_only};
+              lead_bits, planes, slices ? scales : nullptr, nred, {}, upper_only, err};
     for (int q = 0; q < nred; ++q) {
         if (red_pow[q] < 1 || red_pow[q] > 4) return cudaErrorInvalidValue;
         g.red[q] = RbfRed{red_pow[q], red_vec[q], red_out[q]};
@@ -1078,20 +1055,21 @@ cudaError_t launch_kbuild_rbf(const float *Xw, const double *Xd, int64_t n, int 
     return cudaGetLastError();
 }
 
-cudaError_t launch_loadmat(const double *src, int64_t n, bool fp64, int zero_diag, void *dst, cudaStream_t s) {
-    if (fp64) loadmat_kernel<double><<<grid_for(n * n, 256), 256, 0, s>>>(src, n, zero_diag, (double *)dst);
-    else loadmat_kernel<float><<<grid_for(n * n, 256), 256, 0, s>>>(src, n, zero_diag, (float *)dst);
+cudaError_t launch_loadmat(const double *src, int64_t n, bool fp64, int zero_diag, void *dst, int *err,
+                           cudaStream_t s) {
+    if (fp64) loadmat_kernel<double><<<grid_for(n * n, 256), 256, 0, s>>>(src, n, zero_diag, (double *)dst, err);
+    else loadmat_kernel<float><<<grid_for(n * n, 256), 256, 0, s>>>(src, n, zero_diag, (float *)dst, err);
     return cudaGetLastError();
 }
 
-cudaError_t launch_unary_tanh(const void *X, int x_dtype, int64_t n, int d, const double *w, double *out,
+cudaError_t launch_unary_tanh(const void *X, int x_dtype, int64_t n, int d, const double *w, double *out, int *err,
                               cudaStream_t s) {
-    unary_tanh_kernel<<<grid_for(n, 128), 128, 0, s>>>(X, x_dtype, n, d, w, out);
+    unary_tanh_kernel<<<grid_for(n, 128), 128, 0, s>>>(X, x_dtype, n, d, w, out, err);
     return cudaGetLastError();
 }
 
-cudaError_t launch_copyvec(const double *src, int64_t n, double *dst, cudaStream_t s) {
-    copyvec_kernel<<<grid_for(n, 256), 256, 0, s>>>(src, n, dst);
+cudaError_t launch_copyvec(const double *src, int64_t n, double *dst, int *err, cudaStream_t s) {
+    copyvec_kernel<<<grid_for(n, 256), 256, 0, s>>>(src, n, dst, err);
     return cudaGetLastError();
 }
 

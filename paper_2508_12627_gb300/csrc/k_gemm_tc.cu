@@ -26,7 +26,7 @@
 // With `symmetric` (C = C^T and every reduction symmetric) only tiles on or
 // above the diagonal are computed and off-diagonal tiles count twice.  Every
 // mbarrier wait is bounded: on time-out the CTA records an error, waits (again
-// bounded) for its copies in flight, frees its TMEM and returns.
+// bounded) for its MMAs and copies in flight, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -37,6 +37,8 @@
 
 #include "kcommon.cuh"
 #include "kernels.h"
+#include "kmath.cuh"
+#include "tc_ptx.cuh"
 
 namespace ustat {
 
@@ -52,59 +54,6 @@ int split_lead_bits(int64_t K) {
 namespace {
 
 // ------------------------------------------------------------------ split / prep
-
-__device__ __forceinline__ int row_exp(float m) {
-    // smallest e with m <= 2^e (m = f 2^e, f in [0.5, 1); f = 0.5 means m = 2^(e-1))
-    int e = 0;
-    if (m > 0.f) {
-        const float f = frexpf(m, &e);
-        if (f == 0.5f) e -= 1;
-    }
-    return e;
-}
-
-__device__ __forceinline__ int row_exp(double m) {
-    int e = 0;
-    if (m > 0.0) {
-        const double f = frexp(m, &e);
-        if (f == 0.5) e -= 1;
-    }
-    return e;
-}
-
-// float64 source (the wide-storage mode), digits of the value itself rather than
-// of its float32 rounding.  y = x 2^(w - e) (|y| <= 2^w) is rounded once to a
-// multiple of 2^-8(planes - 1), as the integer q; its balanced base-256 digits
-// (each in [-128, 127], the leading one |d1| <= 2^w) are taken with integer
-// arithmetic, so that the only float64 operations are one scaling and one
-// conversion per entry.
-__device__ __forceinline__ void write_digits(double x, int lead_bits, int e, int planes, __nv_bfloat16 *dst,
-                                             int64_t plane_stride) {
-    long long q = llrint(ldexp(x, lead_bits - e + 8 * (planes - 1)));   // the scaling is exact
-    float scale = __int_as_float((127 - 8 * (planes - 1)) << 23);       // 2^-8(planes - 1)
-    for (int p = planes - 1; p >= 1; --p) {
-        const int dp = (int)(((q + 128) & 255) - 128);
-        q = (q - dp) >> 8;                                               // exact
-        dst[p * plane_stride] = __float2bfloat16_rn((float)dp * scale);   // exact
-        scale *= 256.f;
-    }
-    dst[0] = __float2bfloat16_rn((float)q);                              // |q| <= 2^w: exact
-}
-
-__device__ __forceinline__ void write_digits(float x, int lead_bits, int e, int planes, __nv_bfloat16 *dst,
-                                             int64_t plane_stride) {
-    const int k = lead_bits - e;
-    float y = (k >= -126 && k <= 127) ? x * __int_as_float((127 + k) << 23) : ldexpf(x, k);   // |y| <= 2^w, exact
-    float d = rintf(y);
-    dst[0] = __float2bfloat16_rn(d);
-    float scale = 1.f / 256.f;
-    for (int p = 1; p < planes; ++p) {
-        y = (y - d) * 256.f;              // exact
-        d = rintf(y);
-        dst[p * plane_stride] = __float2bfloat16_rn(d * scale);
-        scale *= (1.f / 256.f);
-    }
-}
 
 // Row-major source (X(j, i) = M[j][i] u(i)): one warp per operand row, two passes
 // (row maximum, then digits), fully coalesced.
@@ -328,122 +277,7 @@ __global__ void __launch_bounds__(256) operand_cols_kernel(const T *__restrict__
     }
 }
 
-// ------------------------------------------------------------------ PTX wrappers
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// try_wait with a suspend-time hint: the thread sleeps in hardware until the
-// phase completes or about hint_ns pass, without spending issue slots.
-__device__ __forceinline__ bool mbar_try_wait_hint(uint32_t bar, uint32_t parity, uint32_t hint_ns) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity), "r"(hint_ns)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait.  mbarrier.try_wait suspends the thread in hardware until the
-// phase completes or a short time limit passes, so the loop needs no sleep (a
-// software sleep would add its wake-up latency to every pipeline hand-off).
-// Gives up after ~4e9 SM cycles (about two seconds) or as soon as another thread
-// of the CTA has given up.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = clock64();
-    for (;;) {
-        if (mbar_try_wait_hint(bar, parity, 100000u)) return true;
-        if (*abort_flag) return false;
-        if (clock64() - t0 > 4000000000LL) break;
-    }
-    *abort_flag = 1;
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
-                                            uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-        "[%5];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// Shared-memory matrix descriptor: K-major tile whose rows are kRowBytes long
-// (128: 128-byte swizzle, 8-row groups 1024 bytes apart; 64: 64-byte swizzle,
-// 8-row groups 512 bytes apart), descriptor version 1.
-template <int kRowBytes>
-__device__ __forceinline__ uint64_t desc_sw(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;                         // LBO (unused for swizzled K-major)
-    d |= (uint64_t)((8 * kRowBytes) >> 4) << 32;    // SBO
-    d |= (uint64_t)1 << 46;                         // version
-    d |= (uint64_t)(kRowBytes == 128 ? 2 : 4) << 61;   // SWIZZLE_128B / SWIZZLE_64B
-    return d;
-}
-
-template <bool kTf32>
-__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
-    if (!kTf32)
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
-    else
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-#define USTAT_R16(x) \
-    "=r"(x[0]), "=r"(x[1]), "=r"(x[2]), "=r"(x[3]), "=r"(x[4]), "=r"(x[5]), "=r"(x[6]), "=r"(x[7]), "=r"(x[8]), \
-        "=r"(x[9]), "=r"(x[10]), "=r"(x[11]), "=r"(x[12]), "=r"(x[13]), "=r"(x[14]), "=r"(x[15])
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];"
-        : USTAT_R16(r)
-        : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// Instruction descriptor: D = F32, A/B format (1 = BF16 for kind::f16, 2 = TF32),
-// both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t M, uint32_t N) {
-    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
-}
+using namespace tc;
 
 constexpr int kBM = 128;
 constexpr int kThreads = 192;
@@ -531,7 +365,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     auto empty_bar = [&](int s) { return bar_base + 8u * (C::kStages + s); };
     auto tfull_bar = [&](int b) { return bar_base + 8u * (2 * C::kStages + b); };
     auto tempty_bar = [&](int b) { return bar_base + 8u * (2 * C::kStages + 2 + b); };
-    uint8_t *misc = gbase + C::kStages * C::kStageBytes + 8 * (2 * C::kStages + 4);
+    const uint32_t abort_bar = bar_base + 8u * (2 * C::kStages + 4);   // MMAs in flight at an abort
+    uint8_t *misc = gbase + C::kStages * C::kStageBytes + 8 * (2 * C::kStages + 5);
     volatile uint32_t *tmem_holder = (volatile uint32_t *)misc;
     volatile int *abort_flag = (volatile int *)(misc + 4);
     volatile uint32_t *issued_cnt = (volatile uint32_t *)(misc + 8);
@@ -541,6 +376,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n = g.n;
     const int num_k = (int)(g.ldp / C::kBKElems);
+    const long long wlim = g.wait_limit > 0 ? g.wait_limit : kWaitLimit;
     TileWalk walk{(int)((n + kBM - 1) / kBM), (int)((n + C::kBN - 1) / C::kBN), g.symmetric,
                   g.group_rows > 0 ? g.group_rows : 8, g.batch};
     // work units: the tiles, except that the last g.split_tail tiles of the schedule
@@ -573,6 +409,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(tfull_bar(b), 1);
             mbar_init(tempty_bar(b), 4);
         }
+        mbar_init(abort_bar, 1);
         *abort_flag = 0;
         *issued_cnt = 0;
         *consumed_cnt = 0;
@@ -594,14 +431,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             // ---------------- TMA producer
             uint32_t it = 0;
-            for (int t = blockIdx.x; t < total_tiles && !*abort_flag; t += gridDim.x) {
+            // g.debug_stall (a test hook, off by default): issue no copy at all, so
+            // that the MMA warp's first wait runs out with nothing in flight
+            for (int t = g.debug_stall ? total_tiles : (int)blockIdx.x; t < total_tiles && !*abort_flag;
+                 t += gridDim.x) {
                 int bl, tm, tn, c_off, width;
                 unit(t, bl, tm, tn, c_off, width);
                 const int za = bl * C::kPlanes;   // the product's A planes (batched s = 3 step)
                 for (int kb = 0; kb < num_k; ++kb, ++it) {
                     const int s = it % C::kStages;
                     if (it >= (uint32_t)C::kStages &&
-                        !mbar_wait(empty_bar(s), ((it / C::kStages) - 1) & 1, abort_flag))
+                        !mbar_wait(empty_bar(s), ((it / C::kStages) - 1) & 1, abort_flag, wlim))
                         break;
                     const uint32_t sa = base + s * C::kStageBytes;
                     const uint32_t sb = sa + C::kPlanes * C::kATile;
@@ -628,7 +468,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t b_plane = width == C::kBN ? C::kBTile : C::kBTile / 2;   // bytes per B plane
                 const int buf = tcount % C::kBufs;
                 if (tcount >= (uint32_t)C::kBufs &&
-                    !mbar_wait(tempty_bar(buf), ((tcount / C::kBufs) - 1) & 1, abort_flag)) {
+                    !mbar_wait(tempty_bar(buf), ((tcount / C::kBufs) - 1) & 1, abort_flag, wlim)) {
                     ok = false;
                     break;
                 }
@@ -637,7 +477,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t d_lo = d_hi + (kWide ? 3 : 1) * C::kBN;
                 for (int kb = 0; kb < num_k; ++kb, ++it) {
                     const int s = it % C::kStages;
-                    if (!mbar_wait(full_bar(s), (it / C::kStages) & 1, abort_flag)) {
+                    if (!mbar_wait(full_bar(s), (it / C::kStages) & 1, abort_flag, wlim)) {
                         ok = false;
                         break;
                     }
@@ -705,7 +545,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // microseconds) so the waiting warps leave the issue slots to the TMA
             // and MMA warps
             int waited = 0;
-            if (lane == 0) waited = mbar_wait(tfull_bar(buf), (tcount / C::kBufs) & 1, abort_flag) ? 1 : 0;
+            if (lane == 0) waited = mbar_wait(tfull_bar(buf), (tcount / C::kBufs) & 1, abort_flag, wlim) ? 1 : 0;
             waited = __shfl_sync(0xffffffffu, waited, 0);
             if (!waited || *abort_flag) break;
             tc_fence_after();
@@ -874,12 +714,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncwarp();
     tc_fence_before();
     __syncthreads();
-    if (*abort_flag && threadIdx.x == 0) {
-        if (g.err) atomicExch(g.err, 1);
-        // wait (bounded) for copies issued but never consumed before the smem goes away
-        for (uint32_t i = *consumed_cnt; i < *issued_cnt; ++i)
-            for (int it = 0; it < (1 << 20); ++it)
-                if (mbar_try_wait(full_bar(i % C::kStages), (i / C::kStages) & 1)) break;
+    if (*abort_flag) {
+        if (warp == 1 && lane == 0) {
+            // MMAs issued before the abort may still read shared memory and write
+            // TMEM: one more commit by their issuing thread arrives on abort_bar
+            // once all of them are done; the TMEM is freed only after that
+            mma_commit(abort_bar);
+            mbar_drain(abort_bar, 0, wlim);
+        }
+        if (threadIdx.x == 0) {
+            if (g.err) atomicOr(g.err, kErrWordTimeout);
+            // wait (bounded in time) for the copies issued but never consumed, before
+            // the shared memory they land in is released
+            for (uint32_t i = *consumed_cnt; i < *issued_cnt; ++i)
+                if (!mbar_drain(full_bar(i % C::kStages), (i / C::kStages) & 1, wlim)) break;
+        }
     }
     __syncthreads();
     if (warp == 1) {
@@ -907,10 +756,10 @@ EncodeTiledFn get_encode() {
     return fn;
 }
 
-// total_planes x rows x ldp (innermost) tensor, box {row_bytes, box_rows, planes},
-// swizzled to match (128 or 64 bytes).
+}  // namespace
+
 bool make_map_planes(CUtensorMap *map, const void *ptr, bool bf16, int planes, int total_planes, int64_t rows,
-                     int64_t ldp, int box_rows, int row_bytes = 128) {
+                     int64_t ldp, int box_rows, int row_bytes) {
     EncodeTiledFn enc = get_encode();
     if (!enc) return false;
     const int esz = bf16 ? 2 : 4;
@@ -939,10 +788,17 @@ int sm_count() {
     return cnt[dev];
 }
 
+namespace {
+
+long long g_debug_wait_limit = 0;
+int g_debug_stall = 0;
+
 template <int kMode, bool kWide = false>
 cudaError_t launch_tc(const TcGemmArgs &g0, cudaStream_t s) {
     using C = Cfg<kMode, kWide>;
     TcGemmArgs g = g0;
+    g.wait_limit = g_debug_wait_limit;
+    g.debug_stall = g_debug_stall;
     if (C::kBN != kBM || g.C) g.symmetric = 0;
     if (g.nred < 0 || g.nred > 4) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
@@ -980,6 +836,13 @@ cudaError_t launch_tc(const TcGemmArgs &g0, cudaStream_t s) {
 }
 
 }  // namespace
+
+void set_tc_debug(long long wait_limit, int stall) {
+    g_debug_wait_limit = wait_limit > 0 ? wait_limit : 0;
+    g_debug_stall = stall != 0;
+}
+
+long long tc_debug_wait_limit() { return g_debug_wait_limit; }
 
 cudaError_t launch_split(const void *M, bool wide, int trans, const double *u, int64_t n, int64_t ldp,
                          int lead_bits, int planes, void *slices, float *scales, cudaStream_t s) {

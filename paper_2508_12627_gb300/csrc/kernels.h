@@ -7,8 +7,12 @@
 namespace ustat {
 
 // ---- tensorization and vector ops (k_elem.cu)
+// The kernels that read the caller's inputs (X, MATRIX and VECTOR data) set bit
+// kErrWordNonfinite of the device error word *err (may be null) when an input
+// value is NaN or infinite.
+constexpr int kErrWordTimeout = 1, kErrWordNonfinite = 2;
 // Xw = working copy of X: float64 when fp64, else float32 (row-major n x d).
-cudaError_t launch_xconvert(const void *X, int x_dtype, int64_t n, int d, void *Xw, bool fp64,
+cudaError_t launch_xconvert(const void *X, int x_dtype, int64_t n, int d, void *Xw, bool fp64, int *err,
                             cudaStream_t s);
 // K(i,j) = exp(-||x_i - x_j||^2 / param) (kind RBF) or (x_i . x_j) / param (LINEAR).
 cudaError_t launch_kbuild(int kind, double param, const void *Xw, bool fp64, int64_t n, int d,
@@ -21,16 +25,25 @@ cudaError_t launch_kbuild(int kind, double param, const void *Xw, bool fp64, int
 cudaError_t launch_kbuild_rbf(const float *Xw, const double *Xd, int64_t n, int d, double param, int zero_diag,
                               float *K, void *slices, int64_t ldp, int lead_bits, int planes, float *scales, int nred,
                               const int *red_pow, const int *red_vec, double *const *red_out, int upper_only,
-                              int tile64, cudaStream_t s);
+                              int tile64, int *err, cudaStream_t s);
+// The same RBF build with the squared distances from the Gram matrix X X^T on the
+// tensor cores (k_gram_tc.cu): X (float64 or float32, d <= 256) is read
+// directly; `scratch` (256-byte aligned, kbuild_rbf_tc_scratch_bytes) holds X's
+// digit planes, row scales and squared norms.
+size_t kbuild_rbf_tc_scratch_bytes(int64_t n, int d);
+cudaError_t launch_kbuild_rbf_tc(const void *X, int x_dtype, int64_t n, int d, double param, int zero_diag, float *K,
+                                 void *slices, int64_t ldp, int lead_bits, int planes, float *scales, int nred,
+                                 const int *red_pow, const int *red_vec, double *const *red_out, int upper_only,
+                                 void *scratch, int *err, cudaStream_t s);
 // Linear kernel of a float32 X into a float64 K (float64-storage modes): the
 // double-float dot product, unrounded.
 cudaError_t launch_kbuild_linear_wide(const float *X, int64_t n, int d, double param, int zero_diag, double *K,
                                       cudaStream_t s);
-cudaError_t launch_loadmat(const double *src, int64_t n, bool fp64, int zero_diag, void *dst,
+cudaError_t launch_loadmat(const double *src, int64_t n, bool fp64, int zero_diag, void *dst, int *err,
                            cudaStream_t s);
 cudaError_t launch_unary_tanh(const void *X, int x_dtype, int64_t n, int d, const double *w,
-                              double *out, cudaStream_t s);
-cudaError_t launch_copyvec(const double *src, int64_t n, double *dst, cudaStream_t s);
+                              double *out, int *err, cudaStream_t s);
+cudaError_t launch_copyvec(const double *src, int64_t n, double *dst, int *err, cudaStream_t s);
 cudaError_t launch_diag(const void *M, bool fp64, int64_t n, double *out, cudaStream_t s);
 cudaError_t launch_vmul(const double *a, const double *b, int64_t n, double *out, cudaStream_t s);
 // out(i) = F(x_i, x_i) of factor kind `kind` from its own data in float64 (X for
@@ -163,7 +176,17 @@ struct TcGemmArgs {
     // float64 storage (bf16x4 only): W, Wbc, Wbd and C are double, and the epilogue
     // forms the entries and the reductions in float64
     int wide;
+    // set by the launcher from set_tc_debug: the limit of every mbarrier wait in SM
+    // cycles (0: the default, about two seconds) and the stalled-producer test hook
+    long long wait_limit;
+    int debug_stall;
 };
+// Test hook of the bounded waits (off by default): every later tensor-core GEMM
+// launch of this process uses `wait_limit` cycles (0 = default) as its wait limit
+// and, with `stall`, issues no TMA copy, so its first wait runs out.
+void set_tc_debug(long long wait_limit, int stall);
+// The wait limit set by set_tc_debug (0: the default).
+long long tc_debug_wait_limit();
 // shape: 0 = 128 x 128 tiles, 128-byte k-blocks, two stages; 1 = 128 x 64 tiles,
 // three stages (no symmetric tile skipping); 2 = 128 x 128 tiles, 64-byte
 // k-blocks, four stages (bf16x4: 0 = 128 x 64 tiles, two stages; 2 = 128 x 128

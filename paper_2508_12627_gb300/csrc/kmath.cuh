@@ -1,0 +1,132 @@
+// Number formats shared by the kernels: the split-bf16 fixed-point digits of an
+// operand row, packed float32 pair arithmetic (.f32x2), and the RBF kernel map
+// exp(-d2 / h) in float32 with an unbiased exponential.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace ustat {
+
+__device__ __forceinline__ int row_exp(float m) {
+    // smallest e with m <= 2^e (m = f 2^e, f in [0.5, 1); f = 0.5 means m = 2^(e-1))
+    int e = 0;
+    if (m > 0.f) {
+        const float f = frexpf(m, &e);
+        if (f == 0.5f) e -= 1;
+    }
+    return e;
+}
+
+__device__ __forceinline__ int row_exp(double m) {
+    int e = 0;
+    if (m > 0.0) {
+        const double f = frexp(m, &e);
+        if (f == 0.5) e -= 1;
+    }
+    return e;
+}
+
+// float64 source (the wide-storage mode), digits of the value itself rather than
+// of its float32 rounding.  y = x 2^(w - e) (|y| <= 2^w) is rounded once to a
+// multiple of 2^-8(planes - 1), as the integer q; its balanced base-256 digits
+// (each in [-128, 127], the leading one |d1| <= 2^w) are taken with integer
+// arithmetic, so that the only float64 operations are one scaling and one
+// conversion per entry.
+__device__ __forceinline__ void write_digits(double x, int lead_bits, int e, int planes, __nv_bfloat16 *dst,
+                                             int64_t plane_stride) {
+    long long q = llrint(ldexp(x, lead_bits - e + 8 * (planes - 1)));   // the scaling is exact
+    float scale = __int_as_float((127 - 8 * (planes - 1)) << 23);       // 2^-8(planes - 1)
+    for (int p = planes - 1; p >= 1; --p) {
+        const int dp = (int)(((q + 128) & 255) - 128);
+        q = (q - dp) >> 8;                                               // exact
+        dst[p * plane_stride] = __float2bfloat16_rn((float)dp * scale);   // exact
+        scale *= 256.f;
+    }
+    dst[0] = __float2bfloat16_rn((float)q);                              // |q| <= 2^w: exact
+}
+
+__device__ __forceinline__ void write_digits(float x, int lead_bits, int e, int planes, __nv_bfloat16 *dst,
+                                             int64_t plane_stride) {
+    const int k = lead_bits - e;
+    float y = (k >= -126 && k <= 127) ? x * __int_as_float((127 + k) << 23) : ldexpf(x, k);   // |y| <= 2^w, exact
+    float d = rintf(y);
+    dst[0] = __float2bfloat16_rn(d);
+    float scale = 1.f / 256.f;
+    for (int p = 1; p < planes; ++p) {
+        y = (y - d) * 256.f;              // exact
+        d = rintf(y);
+        dst[p * plane_stride] = __float2bfloat16_rn(d * scale);
+        scale *= (1.f / 256.f);
+    }
+}
+
+
+// two float32 in one 64-bit register pair (first = low half)
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 f2_pack(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f32x2 r, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ f32x2 f2_add(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 f2_sub(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ f32x2 f2_splat(float a) { return f2_pack(a, a); }
+__device__ __forceinline__ f32x2 f2_rint(f32x2 a) {
+    float x, y;
+    f2_unpack(a, x, y);
+    return f2_pack(rintf(x), rintf(y));
+}
+
+// exp(-d2 * inv_h) for two squared distances: the steps of exp_unbiased, each
+// the same IEEE operation per lane
+__device__ __forceinline__ f32x2 f2_rbf(f32x2 d2, float inv_h) {
+    const f32x2 z = f2_mul(d2, f2_splat(-inv_h));
+    const f32x2 k = f2_rint(f2_mul(z, f2_splat(1.44269504088896341f)));
+    const f32x2 fh = f2_fma(k, f2_splat(-0.693145751953125f), z);   // exact
+    const f32x2 fl = f2_mul(k, f2_splat(-1.42860682030941723212e-6f));
+    const f32x2 f = f2_add(fh, fl);
+    f32x2 q = f2_fma(f2_splat(1.0f / 40320.0f), f, f2_splat(1.0f / 5040.0f));
+    q = f2_fma(q, f, f2_splat(1.0f / 720.0f));
+    q = f2_fma(q, f, f2_splat(1.0f / 120.0f));
+    q = f2_fma(q, f, f2_splat(1.0f / 24.0f));
+    q = f2_fma(q, f, f2_splat(1.0f / 6.0f));
+    q = f2_fma(q, f, f2_splat(0.5f));
+    q = f2_mul(f2_mul(q, f), f);
+    const f32x2 one = f2_splat(1.0f);
+    const f32x2 sh = f2_add(one, fh);                        // Fast2Sum (|1| >= |fh|)
+    const f32x2 sl = f2_sub(fh, f2_sub(sh, one));
+    const f32x2 y = f2_add(sh, f2_add(f2_add(sl, fl), q));
+    float k0, k1, z0, z1;
+    f2_unpack(k, k0, k1);
+    f2_unpack(z, z0, z1);
+    const f32x2 p2 = f2_pack(__int_as_float(((int)k0 + 127) << 23), __int_as_float(((int)k1 + 127) << 23));
+    float r0, r1;
+    f2_unpack(f2_mul(y, p2), r0, r1);
+    return f2_pack(z0 < -87.0f ? 0.0f : r0, z1 < -87.0f ? 0.0f : r1);
+}
+
+}  // namespace ustat

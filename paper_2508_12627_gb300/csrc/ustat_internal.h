@@ -169,6 +169,8 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan, const P
 
 // Records a CUDA error for ustat_last_cuda_error and returns USTAT_ERR_CUDA (api.cu).
 int record_cuda_error(int cuda_error);
+// The USTAT_* status that an evaluation's device error word stands for (api.cu).
+int status_of_word(int word);
 
 // Exact treewidth of a simple graph on k <= 16 vertices given as adjacency bitmasks.
 int exact_treewidth(int k, const std::vector<uint32_t> &adj);

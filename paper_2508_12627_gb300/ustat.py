@@ -64,6 +64,8 @@ EXPORTS = {
     "ustat_plan_describe": (_i, [_vp, ctypes.c_char_p, _sz, _P(_sz)]),
     "ustat_workspace_bytes": (_i, [_vp, _i64, _i, _P(_sz)]),
     "ustat_status": (_i, [_vp, _vp, _P(_i)]),
+    "ustat_debug_set_wait": (_i, [ctypes.c_longlong, _i]),
+    "ustat_noalloc_status": (_i, [_vp, _P(_i)]),
     "ustat_eval": (_i, [_vp, _vp, _i, _i64, _i, _P(ustat_factor), _i, _vp, _sz, _vp, _vp, _vp]),
     "ustat_host_staging_bytes": (_i, [_vp, _i64, _i, _P(_sz)]),
     "ustat_eval_noalloc": (_i, [_vp, _vp, _i, _i64, _i, _P(ustat_factor), _i, _vp, _vp, _vp]),
@@ -382,11 +384,25 @@ def version():
 
 
 def status(ws_ptr, stream):
-    """ustat_status: USTAT_OK, or USTAT_ERR_DEVICE_TIMEOUT if a bounded device wait of
-    the last evaluation in this workspace gave up (waits for the stream)."""
+    """ustat_status: USTAT_OK, USTAT_ERR_DEVICE_TIMEOUT if a bounded device wait of
+    the last evaluation in this workspace gave up, or USTAT_ERR_NONFINITE if it read
+    a NaN or infinite input (waits for the stream)."""
     st = _i()
     _check(lib().ustat_status(ws_ptr, stream, ctypes.byref(st)), "ustat_status")
     return st.value
+
+
+def noalloc_status(stream):
+    """ustat_noalloc_status: the status of the last ustat_eval_noalloc on the current
+    device (waits for the stream)."""
+    st = _i()
+    _check(lib().ustat_noalloc_status(stream, ctypes.byref(st)), "ustat_noalloc_status")
+    return st.value
+
+
+def debug_set_wait(limit_cycles=0, stall_producer=False):
+    """ustat_debug_set_wait: test hook of the bounded device waits (0, False = off)."""
+    _check(lib().ustat_debug_set_wait(int(limit_cycles), 1 if stall_producer else 0), "ustat_debug_set_wait")
 
 
 NOALLOC_MAX_BYTES = 64 * 1024 * 1024

@@ -194,15 +194,3 @@ def test_engine_plan_cache(us, tmp_path):
     assert b.plan.describe() == a.plan.describe() and b.n_parts == a.n_parts == 203
     assert len(list(tmp_path.iterdir())) == 2
 
-
-def test_readme_python_example_compiles_and_names_real_functions(us):
-    # the usage example in the README parses, and every binding it calls exists
-    import ast
-    text = open(os.path.join(ROOT, "README.md")).read()
-    code = text.split("```python\n", 1)[1].split("```", 1)[0]
-    tree = ast.parse(code)
-    from paper_2508_12627_gb300 import dcov, engine, hoif, motifs
-    mods = {"engine": engine, "us": us, "motifs": motifs, "hoif": hoif, "dcov": dcov, "synth": synth}
-    for node in ast.walk(tree):
-        if isinstance(node, ast.Attribute) and isinstance(node.value, ast.Name) and node.value.id in mods:
-            assert hasattr(mods[node.value.id], node.attr), (node.value.id, node.attr)

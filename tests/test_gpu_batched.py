@@ -148,3 +148,39 @@ def test_autotune_keeps_results(us):
     # accumulators: same 1e-8 target as every bf16x3 result
     v0, v1 = V0.cpu().numpy(), V.cpu().numpy()
     assert np.all(np.abs(v1 - v0) <= 1e-8 * np.abs(v0))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name", ["c4", "c5"])
+def test_full_batch_against_stored_oracle_values(us, name):
+    # the batched workload at its full size: all 512 samples (n uniform in
+    # [256, 4096], d = 16) in one captured graph on 16 lanes, in the launch
+    # configuration bench.py times; the samples whose values the oracle stored
+    # (tests/golden/make_workload_golden.py: the smallest, the largest and six
+    # more) match to 1e-8 of V_abs, and every sample's results are finite
+    import json
+    import os
+    import torch
+    with open(os.path.join(os.path.dirname(__file__), "golden", "workload_batched.json")) as f:
+        gold = json.load(f)
+    ns = [int(v) for v in synth.batched_sizes(512, 256, 4096, 0)]
+    g, p, Xs, Xd, b, ws, U, V, facs = _setup(us, name, "bf16x3", ns, max_lanes=16)
+    s2 = torch.cuda.Stream()
+    xp = [x.data_ptr() for x in Xd]
+    with torch.cuda.stream(s2):
+        b.capture(xp, 0, facs, ws.data_ptr(), ws.numel(), s2.cuda_stream, U.data_ptr(), V.data_ptr())
+        b.replay(s2.cuda_stream)
+    torch.cuda.synchronize()
+    Uh, Vh = U.cpu().numpy(), V.cpu().numpy()
+    assert np.all(np.isfinite(Uh)) and np.all(np.isfinite(Vh))
+    checked = 0
+    for rec in gold["samples"]:
+        if rec["graph"] != name:
+            continue
+        i = rec["index"]
+        assert rec["n"] == ns[i]
+        Vabs = np.array(rec["V_abs"])
+        assert np.all(np.abs(Vh[i] - np.array(rec["V"])) <= 1e-8 * Vabs), (name, i)
+        assert abs(Uh[i, 0] - rec["U_sum"]) <= 1e-8 * rec["U_abs"], (name, i)
+        checked += 1
+    assert checked == 8

@@ -19,7 +19,9 @@ SMALL_N = 5e-7: every factor entry is stored in float32 (relative rounding
 hence V_pi (a weighted mean of terms), is within 7 * 2^-24 = 4.2e-7; the 1e-8
 target relies on these independent roundings averaging out over many terms.
 """
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -52,6 +54,17 @@ def eng_mod():
     build.build()
     from paper_2508_12627_gb300 import engine
     return engine
+
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _stored(name):
+    """The oracle's values for a workload at its full size, written by
+    tests/golden/make_workload_golden.py (FP64 partition sum on synth's inputs)."""
+    with open(os.path.join(GOLDEN, "workload_%s.json" % name)) as f:
+        g = json.load(f)
+    return {"V": g["V"], "mu": g["mu"], "U_sum": g["U_sum"], "U_mean": g["U_mean"]}, {"V": g["V_abs"]}
 
 
 def _oracle(w, sparse=False):
@@ -103,7 +116,7 @@ def test_heavy_tailed_matrix_factor(eng_mod, prec):
     _compare(out, ref, absref, tol, "t2 %s" % prec)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "bf16x4"])
 @pytest.mark.parametrize("n", [4, 5, 64, 127, 128, 129, 256, 385, 1100, 2049])
 def test_c4_sizes_and_ragged_tails(eng_mod, n, prec):
     w = synth.workload("c4_rbf", n=n)
@@ -114,18 +127,56 @@ def test_c4_sizes_and_ragged_tails(eng_mod, n, prec):
     _compare(out, ref, absref, tol_for("c4_rbf", prec, n), "c4 n=%d %s" % (n, prec))
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3"])
-def test_rank1_integer_factors_bit_exact(eng_mod, prec):
-    # K = u u^T with u in {-1, 0, 1}: every partial sum is an integer far below
-    # 2^24, so the float32 and split bf16 paths are exact too.
-    n = 200
-    u = synth.ternary_vector(n, 9)
+def rank1_values(graph, u):
+    """V_pi for K = u u^T on every edge and the unary factor u, in closed form:
+    prod over the blocks B of pi of p_deg(B)(u), p_k = sum_i u_i^k, deg(B) the
+    number of factor slots (edge endpoints, unary factors) landing in B; and
+    U_sum = sum_pi mu_pi V_pi (exact integers)."""
+    ps = {}
+    V, U = [], 0
+    for rgs in uo.set_partitions(graph.m):
+        deg = [0] * (max(rgs) + 1)
+        for a, b, _ in graph.edges:
+            deg[rgs[a]] += 1
+            deg[rgs[b]] += 1
+        for a, _ in graph.unary:
+            deg[rgs[a]] += 1
+        v = 1
+        for k in deg:
+            if k not in ps:
+                ps[k] = int(np.sum(u.astype(np.int64) ** k))
+            v *= ps[k]
+        V.append(v)
+        U += uo.mu_closed_form(rgs) * v
+    return V, U
+
+
+def sparse_ternary(n, nnz, seed):
+    """u with exactly nnz entries of +-1 at random positions, 0 elsewhere: the power
+    sums stay small, so every partial sum of the float32 paths is an exact integer."""
+    rng = np.random.default_rng(seed)
+    u = np.zeros(n)
+    u[rng.choice(n, nnz, replace=False)] = rng.choice([-1.0, 1.0], nnz)
+    return u
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3", "bf16x4"])
+@pytest.mark.parametrize("n", [5, 64, 127, 129, 200, 385, 1100, 2049])
+def test_rank1_integer_factors_bit_exact(eng_mod, prec, n):
+    # K = u u^T with u in {-1, 0, 1}: every partial sum is an integer below 2^24,
+    # so the float32 and split bf16 paths are exact too -- at every ragged size
+    u = synth.ternary_vector(n, 9) if n <= 64 else sparse_ternary(n, 40, 9)
     facs = [synth.Factor(uo.MATRIX, data=np.outer(u, u)), synth.Factor(uo.VECTOR, data=u)]
-    for g in [synth.cycle4_graph(), synth.path5_chord_graph(), synth.triangle_graph()]:
-        ref = uo.ustat(g, facs, np.zeros((n, 1)))
-        out = eng_mod.Engine(g, facs, precision=prec).evaluate(np.zeros((n, 1)))
-        assert list(out["V"]) == ref["V"], (prec, g.m)
-        assert out["U_sum"] == ref["U_sum"]
+    graphs = [synth.cycle4_graph(), synth.path5_chord_graph(), synth.triangle_graph()]
+    if prec in ("bf16x3", "bf16x4") and 6 <= n <= 385:
+        graphs.append(synth.k4_plus_cycle_graph())
+    for g in graphs:
+        V, U = rank1_values(g, u)
+        eng = eng_mod.Engine(g, facs, precision=prec)
+        eng.workspace(eng.plan.workspace_bytes(n, 1)).fill_(255)   # NaN bytes: no stale reads
+        out = eng.evaluate(np.zeros((n, 1)))
+        assert list(out["V"]) == [float(v) for v in V], (prec, n, g.m)
+        assert out["U_sum"] == float(U)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
@@ -155,15 +206,19 @@ def test_sparse_mode_and_sharing_and_planners_agree(eng_mod, prec):
         assert abs(o["U_sum"] - ref["U_sum"]) <= tol_for(w.name, prec, w.n) * uabs
 
 
-@pytest.mark.parametrize("name", ["rbf", "linear"])
+@pytest.mark.parametrize("name", ["rbf", "linear", "rbf-near-pairs"])
 def test_kernel_matrix_sum_has_no_bias(eng_mod, name):
     # m = 2, one edge: U_sum = sum_{i != j} F(x_i, x_j).  A mean bias of the device's
     # float32 kernel entries would show at full size (16.7M terms); symmetric
-    # rounding errors average out far below the split path's 1e-8 target.
+    # rounding errors average out far below the split path's 1e-8 target.  With
+    # near pairs (every odd row a 1e-4 perturbation of the row before) the Gram
+    # form's squared distances cancel to ~1e-7 of the norms on half the rows.
     n, d = 4096, 32
     X = synth.normal_X(n, d, 3)
+    if name == "rbf-near-pairs":
+        X[1::2] = X[0::2] + 1e-4 * synth.normal_X(n // 2, d, 4)
     g = synth.Graph(2, [(0, 1, 0)], [])
-    f = [synth.rbf(d)] if name == "rbf" else [synth.linear(d)]
+    f = [synth.linear(d)] if name == "linear" else [synth.rbf(d)]
     ref, absref = _oracle(synth.Workload("m2", g, f, n, d, X))
     for prec in ("fp32", "bf16x3"):
         out = eng_mod.Engine(g, f, precision=prec).evaluate(X)
@@ -197,15 +252,25 @@ def test_row_permutation_invariance_on_gpu(eng_mod):
     assert np.allclose(a["V"], b["V"], rtol=SMALL_N, atol=0)
 
 
-def test_c4_full_size_against_oracle(eng_mod):
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x4"])
+def test_c4_full_size_against_oracle(eng_mod, prec):
     # the 4-cycle RBF workload at n = 4096, d = 32, in the launch configuration the
-    # benchmark times: all 15 V_pi and U against the FP64 oracle
+    # benchmark times: all 15 V_pi and U against the FP64 oracle's stored values
     w = synth.workload("c4_rbf")
-    ref, absref = _oracle(w)
-    eng = eng_mod.Engine(w.graph, w.factors, precision="bf16x3")
+    ref, absref = _stored("c4_rbf")
+    eng = eng_mod.Engine(w.graph, w.factors, precision=prec)
     eng.workspace(eng.plan.workspace_bytes(w.n, w.d)).fill_(255)   # NaN bytes: no stale reads
     out = eng.evaluate(w.X)
-    _compare(out, ref, absref, 1e-8, "c4 full bf16x3")
+    _compare(out, ref, absref, 1e-8, "c4 full " + prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "bf16x4", "fp32"])
+def test_triangle_full_size_against_oracle(eng_mod, prec):
+    # the triangle workload at its size n = 200 (every partition) in every 1e-8 mode
+    w = synth.workload("triangle_rbf")
+    ref, absref = _stored("triangle_rbf")
+    out = eng_mod.Engine(w.graph, w.factors, precision=prec).evaluate(w.X)
+    _compare(out, ref, absref, TOL[prec], "triangle full " + prec)
 
 
 K4C_N = 200
@@ -213,68 +278,81 @@ K4C_N = 200
 
 @pytest.fixture(scope="module")
 def k4c_ref():
-    # three partitions of treewidth 3 (the first, a middle one and the finest) at
-    # n = 200, which the oracle evaluates in seconds
+    # K4 + cycle at n = 200 (two 128-row tiles with a ragged tail): all 203
+    # partitions, 26 of them treewidth 3, which the oracle evaluates in seconds
     w = synth.workload("k4_cycle_rbf", K4C_N)
-    parts = uo.set_partitions(w.graph.m)
-    tw = [uo.treewidth_bruteforce(max(r) + 1, uo.quotient_edges(w.graph, r)) for r in parts]
-    idx = [i for i, t in enumerate(tw) if t == 3]
-    pick = [idx[0], idx[len(idx) // 2], idx[-1]]
-    sel = [parts[i] for i in pick]
-    return (w, pick, uo.ustat(w.graph, w.factors, w.X, partitions=sel),
-            uo.ustat(w.graph, w.factors, w.X, partitions=sel, absolute=True))
+    return w, uo.ustat(w.graph, w.factors, w.X)
 
 
 @pytest.mark.parametrize("prec", ["bf16x3", "bf16x4", "bf16x5", "fp32"])
 def test_k4_cycle_treewidth3_steps_multi_tile(eng_mod, k4c_ref, prec):
-    # the s = 3 steps (tensor cores in the split modes) over two 128-row tiles with a
-    # ragged tail, against the oracle element by element
-    w, pick, ref, absref = k4c_ref
+    # the s = 3 steps (tensor cores in the split modes) against the oracle element
+    # by element (RBF factors are positive: V_abs = V)
+    w, ref = k4c_ref
     eng = eng_mod.Engine(w.graph, w.factors, precision=prec)
     eng.workspace(eng.plan.workspace_bytes(w.n, w.d)).fill_(255)   # NaN bytes: no stale reads
     out = eng.evaluate(w.X)
-    for k, i in enumerate(pick):
-        err = abs(out["V"][i] - ref["V"][k])
-        assert err <= SMALL_N * absref["V"][k], (prec, i, err / absref["V"][k])
+    _compare(out, ref, ref, tol_for("k4_cycle_rbf", prec, K4C_N), "k4+cycle n=200 " + prec)
 
 
-def test_k4_cycle_full_size_two_split_regions(eng_mod):
-    # n = 1024 in the launch configuration bench.py times: 25 batches of s = 3
-    # operands, each split on a second stream into one of two alternating regions
-    # while the tensor cores work on the batch before; with the workspace poisoned
-    # (NaN bytes) the treewidth-3 V_pi and U match the float32 CUDA-core path
-    # (no split, no second stream), each within 5e-7 of the exact value
+# K4 + cycle at its full size n = 1024: 203 partitions, 26 of treewidth 3, whose
+# s = 3 steps run in 25 batches of 42 indices, each split on the caller's stream
+# into one of two alternating regions while the GEMM of the batch before runs on
+# a second stream.  bf16x4 (float64 storage) is the 1e-8 mode; bf16x3 stores the
+# intermediate n x n products in float32 (2^-24 per entry, up to seven entries
+# per term) and is held to the float32-storage bound.
+@pytest.mark.parametrize("prec,tol", [("bf16x4", 1e-8), ("bf16x5", 1e-8), ("bf16x3", SMALL_N)])
+def test_k4_cycle_full_size_against_oracle(eng_mod, prec, tol):
     w = synth.workload("k4_cycle_rbf")
-    eng = eng_mod.Engine(w.graph, w.factors, precision="bf16x3")
-    eng.workspace(eng.plan.workspace_bytes(w.n, w.d)).fill_(255)
+    ref, absref = _stored("k4_cycle_rbf")
+    eng = eng_mod.Engine(w.graph, w.factors, precision=prec)
+    eng.workspace(eng.plan.workspace_bytes(w.n, w.d)).fill_(255)   # NaN bytes: no stale reads
     out = eng.evaluate(w.X)
-    ref = eng_mod.Engine(w.graph, w.factors, precision="fp32").evaluate(w.X)
     tw = eng.plan.info["tw"]
-    idx = [i for i, t in enumerate(tw) if t == 3]
-    assert len(idx) == 26
-    for i in idx:
-        assert abs(out["V"][i] - ref["V"][i]) <= 1e-6 * abs(ref["V"][i]), (i, out["V"][i], ref["V"][i])
-    assert np.all(np.isfinite(out["V"]))
-    assert abs(out["U_sum"] - ref["U_sum"]) <= 1e-6 * np.abs(ref["V"]) @ np.abs(eng.plan.info["mu"])
+    assert sum(1 for t in tw if t == 3) == 26
+    _compare(out, ref, absref, tol, "k4+cycle full " + prec)
 
 
-def test_path5_full_size_sampled_partitions(eng_mod):
-    # the path + chord workload at its full size, n = 16384, in bf16x5 (the mode that
-    # meets 1e-8 on its heavy-tailed rows), in the launch configuration bench.py times:
-    # the oracle evaluates four partitions of treewidth <= 1 (its cost is n^2 for
-    # them), element by element against the engine's V_pi
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x4"])
+def test_k4_cycle_full_size_rank1_bit_exact(eng_mod, prec):
+    # the same graph and size with K = u u^T (48 nonzero +-1 entries): the 25
+    # batches, both split regions and both streams give the exact integers
+    n = 1024
+    g = synth.k4_plus_cycle_graph()
+    u = sparse_ternary(n, 48, 11)
+    facs = [synth.Factor(uo.MATRIX, data=np.outer(u, u))]
+    V, U = rank1_values(g, u)
+    eng = eng_mod.Engine(g, facs, precision=prec)
+    eng.workspace(eng.plan.workspace_bytes(n, 1)).fill_(255)
+    out = eng.evaluate(np.zeros((n, 1)))
+    assert list(out["V"]) == [float(v) for v in V]
+    assert out["U_sum"] == float(U)
+
+
+def test_path5_full_size_rank1_bit_exact(eng_mod):
+    # the path + chord graph at its full size n = 16384 with K = u u^T and the
+    # unary factor u (200 nonzero +-1 entries), bf16x3: its treewidth-2 products
+    # on the tensor cores give the exact integers
+    n = 16384
+    g = synth.path5_chord_graph()
+    u = sparse_ternary(n, 200, 12)
+    facs = [synth.Factor(uo.MATRIX, data=np.outer(u, u)), synth.Factor(uo.VECTOR, data=u)]
+    V, U = rank1_values(g, u)
+    out = eng_mod.Engine(g, facs, precision="bf16x3").evaluate(np.zeros((n, 1)))
+    assert list(out["V"]) == [float(v) for v in V]
+    assert out["U_sum"] == float(U)
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16x4", 1e-8), ("bf16x5", 1e-8), ("bf16x3", 1e-6)])
+def test_path5_full_size_against_oracle(eng_mod, prec, tol):
+    # the path + chord workload at its full size, n = 16384, d = 64, t(5) data: all
+    # 52 V_pi (20 of them treewidth-2 products on the tensor cores) and U against
+    # the oracle's stored values.  bf16x3 keeps 24 bits relative to each row's
+    # largest entry, which for these heavy-tailed rows is the 1e-6 class
     w = synth.workload("path5_chord_linear_tanh")
-    out = eng_mod.Engine(w.graph, w.factors, precision="bf16x5").evaluate(w.X)
-    parts = uo.set_partitions(w.graph.m)
-    tw = [uo.treewidth_bruteforce(max(r) + 1, uo.quotient_edges(w.graph, r)) for r in parts]
-    low = [i for i, t in enumerate(tw) if t <= 1]
-    pick = [low[0], low[len(low) // 3], low[2 * len(low) // 3], low[-1]]
-    sel = [parts[i] for i in pick]
-    ref = uo.ustat(w.graph, w.factors, w.X, partitions=sel)
-    absref = uo.ustat(w.graph, w.factors, w.X, partitions=sel, absolute=True)
-    for k, i in enumerate(pick):
-        err = abs(out["V"][i] - ref["V"][k])
-        assert err <= TOL["bf16x5"] * absref["V"][k], (parts[i], err / absref["V"][k])
+    ref, absref = _stored("path5_chord_linear_tanh")
+    out = eng_mod.Engine(w.graph, w.factors, precision=prec).evaluate(w.X)
+    _compare(out, ref, absref, tol, "path5 full " + prec)
 
 
 @pytest.mark.parametrize("prec,shape", [("bf16x3", 0), ("bf16x3", 1), ("bf16x3", 2), ("bf16x4", 0), ("bf16x4", 2),
@@ -296,11 +374,13 @@ def test_gemm_tile_variants(eng_mod, name, n, prec, shape):
 @pytest.mark.parametrize("name,n", [("c4_rbf", 5), ("c4_rbf", 63), ("c4_rbf", 65), ("c4_rbf", 129), ("c4_rbf", 300),
                                     ("triangle_rbf", 200), ("k4_cycle_rbf", 72)])
 def test_rbf_build_tile_variants(eng_mod, name, n, prec):
-    # the 64 x 64-tile form of the RBF kernel-matrix build (bit 4 of the plan
-    # variant): tiles, mirror, digit planes and fused reductions against the oracle
+    # every form of the RBF kernel-matrix build: the tensor-core Gram build (the
+    # default, variant 0) and the CUDA-core direct-difference build on 128 x 128 or
+    # 64 x 64 tiles (bits 5 and 4 of the plan variant): tiles, mirror, digit
+    # planes and fused reductions against the oracle
     w = synth.workload(name, n)
     ref, absref = _oracle(w)
-    for variant in (16, 0):
+    for variant in (0, 32, 48):
         eng = eng_mod.Engine(w.graph, w.factors, precision=prec)
         eng.plan.set_variant(variant)
         # every workspace byte 0xff (a NaN in float32 and float64): a read of
