@@ -297,7 +297,9 @@ int ustat_batch_workspace_bytes(const ustat_plan_t *plan, const int64_t *n, int 
  * deeper pipeline), bit 5 the RBF kernel-matrix build in the float32-storage
  * modes (0: squared distances from the Gram matrix X X^T on the tensor cores;
  * 1: direct differences on the CUDA cores), bit 4 the latter's tile (0: 128 x 128
- * with 256 threads; 1: 64 x 64 with 128 threads).  Results agree to the mode's
+ * with 256 threads; 1: 64 x 64 with 128 threads), bit 6 the treewidth-3 GEMMs of
+ * BF16X4 (0: two double-buffered accumulator sets and a float32 epilogue; 1: the
+ * four-accumulator layout of the float64-storage modes).  Results agree to the mode's
  * tolerance across variants (summation orders differ).  The autotuner below
  * sets these itself.
  */

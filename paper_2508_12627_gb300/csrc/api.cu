@@ -76,6 +76,9 @@ struct Layout {
     std::vector<int> scal_index; // per slot: index into the scalar array (or -1)
     size_t err_off = 0, scal_off = 0, zero_bytes = 0, xw_off = 0, total = 0;
     size_t kb_off = 0;   // scratch of the tensor-core RBF build (X digits, scales, norms)
+    // float64-storage modes with s = 3 steps: float copies of one step's A source
+    // (hi, lo) and of its weights W, Wbc, Wbd, for the float32 split and epilogue
+    size_t sh_off = 0;
     int64_t ldp_slices = 0, ldp_prep = 0;
     // s = 3 steps on the tensor cores: digit planes of g3_nb A operands at a time
     size_t g3_off = 0, g3_stride = 0;
@@ -145,8 +148,10 @@ Layout make_layout(const Plan &P, int64_t n, int d) {
                 cur = align_up(cur + esz * (size_t)n * n, 1024);
                 break;
             case S_SLICES:
+                // digit planes, row scales, and the diagonal left out of the digits
                 L.off[s] = cur;
-                cur = align_up(cur + split_planes_of(P.precision) * 2 * (size_t)n * L.ldp_slices + 4 * (size_t)n,
+                cur = align_up(cur + split_planes_of(P.precision) * 2 * (size_t)n * L.ldp_slices +
+                                   align_up(4 * (size_t)n, 256) + 8 * (size_t)n,
                                1024);
                 break;
             case S_PREP:
@@ -167,6 +172,10 @@ Layout make_layout(const Plan &P, int64_t n, int d) {
         // operands are split while the tensor cores work on the current one
         L.g3_regions = L.g3_nb < n ? 2 : 1;
         cur = align_up(cur + L.g3_stride * L.g3_nb * L.g3_regions, 1024);
+        if (wide_storage(P.precision) && n <= kPairSplitMaxN) {
+            L.sh_off = cur;
+            cur = align_up(cur + 5 * align_up(4 * (size_t)n * n, 1024), 1024);
+        }
     }
     L.total = cur;
     return L;
@@ -233,7 +242,46 @@ struct Ctx {
     float *scales(int slot) const {
         return (float *)(ws + L.off[slot] + split_planes_of(P.precision) * 2 * (size_t)n * L.ldp_slices);
     }
+    double *diagv(int slot) const {
+        return (double *)(ws + L.off[slot] + split_planes_of(P.precision) * 2 * (size_t)n * L.ldp_slices +
+                          align_up(4 * (size_t)n, 256));
+    }
 };
+
+// Diagonal correction of the split-mode products (Section 3.1's factor matrices
+// of positive-definite kernels, and their entrywise powers, have dominant
+// diagonals; a row scale set by the diagonal leaves the off-diagonal entries few
+// digits).  A split slot may leave dominant diagonal entries out when every
+// reader is a non-batched product both of whose operands are split slots; such a
+// product adds the left-out terms exactly in its epilogue.
+struct DiagFix {
+    std::vector<int> split_op;   // per slot: the OP_SPLIT op writing it, or -1
+    std::vector<char> removed;   // per slot: split with its diagonal left out
+};
+
+DiagFix diag_fix_of(const Plan &P) {
+    DiagFix D;
+    D.split_op.assign(P.slots.size(), -1);
+    D.removed.assign(P.slots.size(), 0);
+    if (!is_split_mode(P.precision)) return D;
+    for (size_t i = 0; i < P.ops.size(); ++i)
+        if (P.ops[i].kind == OP_SPLIT && P.ops[i].out >= 0) D.split_op[P.ops[i].out] = (int)i;
+    std::vector<char> ok(P.slots.size(), 1);
+    for (const Op &op : P.ops) {
+        if (op.kind == OP_GEMM) {
+            const bool both = op.opA >= 0 && op.opB >= 0 && D.split_op[op.opA] >= 0 && D.split_op[op.opB] >= 0;
+            if (!both) {
+                if (op.opA >= 0) ok[op.opA] = 0;
+                if (op.opB >= 0) ok[op.opB] = 0;
+            }
+        } else if (op.kind == OP_GEMM3) {
+            if (op.opA >= 0) ok[op.opA] = 0;
+            if (op.opB >= 0) ok[op.opB] = 0;
+        }
+    }
+    for (size_t sl = 0; sl < P.slots.size(); ++sl) D.removed[sl] = D.split_op[sl] >= 0 && ok[sl];
+    return D;
+}
 
 int check_graph_factors(const Plan &P, const ustat_factor *f, int nf, int d) {
     if (nf != (int)P.factor_kind.size() || !f) return USTAT_ERR_INVALID_ARG;
@@ -263,6 +311,7 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
         if (e != cudaSuccess) return cuda_fail(e);
     }
     const int lead = split_lead_bits(n);
+    const DiagFix D = diag_fix_of(P);
     for (const Op &op : P.ops) {
         ProfScope ps(op.kind, C.st);
         switch (op.kind) {
@@ -379,9 +428,12 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
             case OP_PREP: {
                 const Term t = op.t[0];
                 const int tr = P.slots[t.mat].symmetric ? 1 : t.trans;
-                if (op.kind == OP_SPLIT)
+                if (op.kind == OP_SPLIT) {
+                    double *dg = D.removed[op.out] ? C.diagv(op.out) : nullptr;
                     e = launch_split(C.ptr(t.mat), C.fp64, tr, C.vec(op.u), n, C.L.ldp_slices, lead,
-                                     split_planes_of(P.precision), C.ptr(op.out), C.scales(op.out), C.st);
+                                     split_planes_of(P.precision), C.ptr(op.out), C.scales(op.out), dg, C.st);
+                    if (dg) ps.kernels = 2;
+                }
                 else
                     e = launch_prep((const float *)C.ptr(t.mat), tr, C.vec(op.u), n, C.L.ldp_prep,
                                     (float *)C.ptr(op.out), C.st);
@@ -409,6 +461,21 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                                          (double *)C.ptr(R.out)};
                     }
                     g.symmetric = op.symmetric;
+                    if (split && op.opA >= 0 && op.opB >= 0 && (D.removed[op.opA] || D.removed[op.opB])) {
+                        // operands split without their diagonal: the epilogue adds the
+                        // left-out terms from the operands' sources
+                        const Op &sa = P.ops[D.split_op[op.opA]], &sb = P.ops[D.split_op[op.opB]];
+                        const bool symA = P.slots[sa.t[0].mat].symmetric, symB = P.slots[sb.t[0].mat].symmetric;
+                        const int trA = symA ? 1 : sa.t[0].trans, trB = symB ? 1 : sb.t[0].trans;
+                        g.dA = D.removed[op.opA] ? C.diagv(op.opA) : nullptr;
+                        g.dB = D.removed[op.opB] ? C.diagv(op.opB) : nullptr;
+                        g.MA = C.ptr(sa.t[0].mat);
+                        g.MB = C.ptr(sb.t[0].mat);
+                        g.rowA = trA || symA;
+                        g.rowB = !trB || symB;
+                        g.uA = C.vec(sa.u);
+                        g.uB = C.vec(sb.u);
+                    }
                     const int var = P.tc_variant[tc_size_class(n)];
                     g.group_rows = kGroupRows[var & 3];
                     int shape = (var >> 2) & 3;
@@ -455,6 +522,29 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                         if (e != cudaSuccess) break;
                     }
                     const cudaStream_t gs = two ? S->st : C.st;
+                    // float64 storage: the A source as a float pair and the weights as
+                    // float, so that neither the split nor the GEMM epilogue of this
+                    // step does float64 arithmetic per entry
+                    auto row_form = [&](const Term &t) { return P.slots[t.mat].symmetric ? 1 : t.trans; };
+                    const bool pair = C.fp64 && C.L.sh_off && row_form(op.A) == 1;
+                    float *shA = nullptr, *shAl = nullptr, *shW = nullptr, *shWbc = nullptr, *shWbd = nullptr;
+                    if (pair) {
+                        const size_t sz = align_up(4 * (size_t)n * n, 1024);
+                        char *sh = C.ws + C.L.sh_off;
+                        shA = (float *)sh;
+                        shAl = (float *)(sh + sz);
+                        shW = (float *)(sh + 2 * sz);
+                        shWbc = (float *)(sh + 3 * sz);
+                        shWbd = (float *)(sh + 4 * sz);
+                        e = launch_f64_pair((const double *)C.ptr(op.A.mat), n * n, shA, shAl, C.st);
+                        if (e == cudaSuccess && op.W.mat >= 0)
+                            e = launch_f64_pair((const double *)C.ptr(op.W.mat), n * n, shW, nullptr, C.st);
+                        if (e == cudaSuccess && op.Wbc.mat >= 0)
+                            e = launch_f64_pair((const double *)C.ptr(op.Wbc.mat), n * n, shWbc, nullptr, C.st);
+                        if (e == cudaSuccess && op.Wbd.mat >= 0)
+                            e = launch_f64_pair((const double *)C.ptr(op.Wbd.mat), n * n, shWbd, nullptr, C.st);
+                        if (e != cudaSuccess) break;
+                    }
                     int k = 0, last = 0;
                     for (int64_t bb0 = 0; bb0 < n && e == cudaSuccess; bb0 += C.L.g3_nb, ++k) {
                         const int nb = (int)std::min<int64_t>(C.L.g3_nb, n - bb0);
@@ -464,9 +554,14 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                         if (two && k >= 2) e = cudaStreamWaitEvent(C.st, S->gemm_done[h], 0);
                         if (e != cudaSuccess) break;
                         // symmetric sources are read along rows (A(i, j) = M[j][i])
-                        auto row_form = [&](const Term &t) { return P.slots[t.mat].symmetric ? 1 : t.trans; };
-                        e = launch_split_g3(C.ptr(op.A.mat), C.fp64, row_form(op.A), C.vec(op.u), C.ptr(op.Ab.mat),
-                                            row_form(op.Ab), bb0, nb, n, C.L.ldp_slices, lead, planes, sl, sc, C.st);
+                        if (pair)
+                            e = launch_split_g3_pair(shA, shAl, C.vec(op.u), (const double *)C.ptr(op.Ab.mat),
+                                                     row_form(op.Ab), bb0, nb, n, C.L.ldp_slices, lead, planes, sl,
+                                                     sc, C.st);
+                        else
+                            e = launch_split_g3(C.ptr(op.A.mat), C.fp64, row_form(op.A), C.vec(op.u),
+                                                C.ptr(op.Ab.mat), row_form(op.Ab), bb0, nb, n, C.L.ldp_slices, lead,
+                                                planes, sl, sc, C.st);
                         if (e == cudaSuccess && two) e = cudaEventRecord(S->split_done[h], C.st);
                         if (e == cudaSuccess && two) e = cudaStreamWaitEvent(gs, S->split_done[h], 0);
                         if (e != cudaSuccess) break;
@@ -480,14 +575,19 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                         g.lead_bits = lead;
                         g.err = err;
                         g.nred = 1;
-                        g.red[0] = TcRed{C.ptr(op.W.mat), tr(op.W), C.vec(op.a), C.vec(op.b), 1,
-                                         (double *)C.ptr(op.out)};
-                        g.wide = C.fp64;
+                        g.red[0] = TcRed{op.W.mat >= 0 && pair ? (const void *)shW : C.ptr(op.W.mat), tr(op.W),
+                                         C.vec(op.a), C.vec(op.b), 1, (double *)C.ptr(op.out)};
+                        // with the float copies the step runs in the float32-storage form of
+                        // the kernel (two accumulator sets, overlapped epilogue) unless
+                        // variant bit 6 keeps the four-accumulator layout
+                        const bool four_acc = ((var >> 6) & 1) || P.precision == USTAT_BF16X5;
+                        g.wide = C.fp64 && !(pair && !four_acc);
+                        g.wide_f32 = pair && four_acc ? 1 : 0;
                         g.batch = nb;
                         g.bb0 = (int)bb0;
-                        g.Wbc = C.ptr(op.Wbc.mat);
+                        g.Wbc = op.Wbc.mat >= 0 && pair ? (const void *)shWbc : C.ptr(op.Wbc.mat);
                         g.transWbc = tr(op.Wbc);
-                        g.Wbd = C.ptr(op.Wbd.mat);
+                        g.Wbd = op.Wbd.mat >= 0 && pair ? (const void *)shWbd : C.ptr(op.Wbd.mat);
                         g.transWbd = tr(op.Wbd);
                         g.ub = C.vec(op.ub);
                         g.group_rows = kGroupRows[var & 3];
@@ -497,7 +597,8 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                         if (e == cudaSuccess && two) e = cudaEventRecord(S->gemm_done[h], gs);
                         last = h;
                     }
-                    ps.kernels = 2 * k;   // a split and a GEMM per batch
+                    // a split and a GEMM per batch, and the float copies of the step
+                    ps.kernels = 2 * k + (pair ? 1 + (op.W.mat >= 0) + (op.Wbc.mat >= 0) + (op.Wbd.mat >= 0) : 0);
                     // join: the caller's stream waits for the last GEMM (the second
                     // stream runs its GEMMs in order)
                     if (e == cudaSuccess && two) e = cudaStreamWaitEvent(C.st, S->gemm_done[last], 0);
@@ -1289,7 +1390,7 @@ int batched_check(ustat_batched *b, const void *const *X, int x_dtype, const ust
 extern "C" {
 
 int ustat_plan_set_variant(ustat_plan_t *plan, int size_class, int variant) {
-    if (!plan || size_class < -1 || size_class > 3 || variant < 0 || variant > 63 || ((variant >> 2) & 3) == 3)
+    if (!plan || size_class < -1 || size_class > 3 || variant < 0 || variant > 127 || ((variant >> 2) & 3) == 3)
         return USTAT_ERR_INVALID_ARG;
     for (int c = 0; c < 4; ++c)
         if (size_class < 0 || c == size_class) plan->p.tc_variant[c] = variant;

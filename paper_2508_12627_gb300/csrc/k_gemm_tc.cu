@@ -57,24 +57,35 @@ namespace {
 
 // Row-major source (X(j, i) = M[j][i] u(i)): one warp per operand row, two passes
 // (row maximum, then digits), fully coalesced.
+// With diag_out, a row whose diagonal entry X(j, j) sets a larger row scale than
+// its other entries leaves the diagonal out (its digits 0, the row scale from the
+// other entries) and writes its value to diag_out[j]; other rows keep it and
+// write 0.  The GEMM epilogue adds the left-out terms exactly (diagonal
+// correction).
 template <typename T>
 __global__ void __launch_bounds__(256) split_rows_kernel(const T *__restrict__ M, const double *__restrict__ u,
                                                          int64_t n, int64_t ldp, int lead_bits, int planes,
                                                          __nv_bfloat16 *__restrict__ slices,
-                                                         float *__restrict__ scales) {
+                                                         float *__restrict__ scales, double *__restrict__ diag_out) {
     const int lane = threadIdx.x & 31;
     const int64_t j = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (j >= n) return;
     const T *row = M + j * n;
-    T mx = 0;
+    T mx = 0, moff = 0;
     for (int64_t i = lane; i < n; i += 32) {
         T x = row[i];
         if (u) x *= (T)u[i];
         mx = fmax(mx, fabs(x));
+        if (i != j) moff = fmax(moff, fabs(x));
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    const int e = row_exp(mx);
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = (T)fmax((double)mx, (double)__shfl_xor_sync(0xffffffffu, mx, o));
+        moff = (T)fmax((double)moff, (double)__shfl_xor_sync(0xffffffffu, moff, o));
+    }
+    // leave the diagonal out whenever that lowers the row scale
+    const bool drop = diag_out && row_exp(moff) < row_exp(mx);
+    const int e = row_exp(drop ? moff : mx);
     if (lane == 0) scales[j] = ldexpf(1.f, e);
     const int64_t plane = n * ldp;
     for (int64_t i = lane; i < ldp; i += 32) {
@@ -83,8 +94,20 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const T *__restrict__ M
             x = row[i];
             if (u) x *= (T)u[i];
         }
+        if (i == j) {
+            if (diag_out) diag_out[j] = drop ? (double)x : 0.0;
+            if (drop) x = 0;
+        }
         write_digits(x, lead_bits, e, planes, slices + j * ldp + i, plane);
     }
+}
+
+// The value left out by skip_diag: out[j] = M[j][j] u(j), float64.
+template <typename T>
+__global__ void operand_diag_kernel(const T *__restrict__ M, const double *__restrict__ u, int64_t n,
+                                    double *__restrict__ out) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        out[j] = (double)M[j * n + j] * (u ? u[j] : 1.0);
 }
 
 // s = 3 A operands from a row-major source: X_bb(j, i) = M[j][i] s_bb(i) with
@@ -192,6 +215,88 @@ __global__ void __launch_bounds__(256) split_rows_g3_wide_kernel(const double *_
         write_digits(i < n ? val(i) : 0.0, lead_bits, e, planes, slices + j * ldp + i, plane);
 }
 
+// float64 matrix -> float pair (hi = x rounded to float, lo = x - hi rounded),
+// and float64 -> float; grid-stride.  The pair carries about 48 bits.
+__global__ void f64_pair_kernel(const double *__restrict__ M, int64_t total, float *__restrict__ hi,
+                                float *__restrict__ lo) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const double x = M[t];
+        const float h = (float)x;
+        hi[t] = h;
+        if (lo) lo[t] = (float)(x - (double)h);
+    }
+}
+
+// The s = 3 A operands of the float64-storage modes from float-pair copies of a
+// row-major source: X_bb(j, i) = (Mh + Ml)[j][i] s_bb(i), s_bb(i) = u(i) Ab(i, bb),
+// formed in double-float float32 arithmetic (TwoProd by FMA), about 46 bits; the
+// row scale bounds |hi| + |lo|, the leading digit is rint of the scaled hi part,
+// and the remainder (the exact hi remainder plus the lo part, rounded once to
+// float) gives the lower digits exactly as the float32 split does.  No float64
+// arithmetic per entry: s_bb is formed in float64 once per block and staged as a
+// float pair.  One warp per operand row; blockIdx.y indexes bb - bb0.
+__global__ void __launch_bounds__(256) split_rows_g3_pair_kernel(const float *__restrict__ Mh,
+                                                                 const float *__restrict__ Ml,
+                                                                 const double *__restrict__ u,
+                                                                 const double *__restrict__ Mb, int transAb,
+                                                                 int64_t bb0, int64_t n, int64_t ldp, int lead_bits,
+                                                                 int planes, __nv_bfloat16 *__restrict__ slices,
+                                                                 float *__restrict__ scales) {
+    extern __shared__ float2 sp[];   // [n] s_bb as (hi, lo)
+    const int64_t bb = bb0 + blockIdx.y;
+    slices += (int64_t)blockIdx.y * planes * n * ldp;
+    scales += (int64_t)blockIdx.y * n;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        double v = transAb ? Mb[bb * n + i] : Mb[i * n + bb];
+        if (u) v *= u[i];
+        const float h = (float)v;
+        sp[i] = make_float2(h, (float)(v - (double)h));
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (j >= n) return;
+    const float *rh = Mh + j * n, *rl = Ml + j * n;
+    auto prod = [&](int64_t i, float &vh, float &vl) {
+        const float ah = rh[i], al = rl[i];
+        const float2 b = sp[i];
+        const float p = ah * b.x;
+        const float t = fmaf(ah, b.x, -p) + fmaf(ah, b.y, al * b.x);
+        vh = p + t;                 // Fast2Sum: |p| >= |t|
+        vl = t - (vh - p);
+    };
+    float mx = 0.f;
+    for (int64_t i = lane; i < n; i += 32) {
+        float vh, vl;
+        prod(i, vh, vl);
+        mx = fmaxf(mx, fabsf(vh) + fabsf(vl));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int e = row_exp(mx);
+    if (lane == 0) scales[j] = ldexpf(1.f, e);
+    const int k = lead_bits - e;
+    const int64_t plane = n * ldp;
+    for (int64_t i = lane; i < ldp; i += 32) {
+        float vh = 0.f, vl = 0.f;
+        if (i < n) prod(i, vh, vl);
+        const float yh = ldexpf(vh, k), yl = ldexpf(vl, k);   // exact scalings
+        float d = rintf(yh);
+        __nv_bfloat16 *dst = slices + j * ldp + i;
+        dst[0] = __float2bfloat16_rn(d);                        // |d| <= 2^w: exact
+        float r = (yh - d) + yl;                                // yh - d exact
+        float sc = 1.f / 256.f;
+        for (int p = 1; p < planes; ++p) {
+            r *= 256.f;                                         // exact
+            d = rintf(r);
+            r -= d;                                             // exact
+            dst[p * plane] = __float2bfloat16_rn(d * sc);       // exact
+            sc *= (1.f / 256.f);
+        }
+    }
+}
+
 // Column source (X(j, i) = M[i][j] u(i)) and the tf32 copy: one block per 32
 // operand rows, transposed through shared memory.
 // With Mb (the s = 3 step): X(j, i) is further scaled by Ab(i, bb), bb = bb0 +
@@ -203,7 +308,7 @@ __global__ void __launch_bounds__(256) operand_cols_kernel(const T *__restrict__
                                                            __nv_bfloat16 *__restrict__ slices,
                                                            float *__restrict__ scales, float *__restrict__ prep,
                                                            const T *__restrict__ Mb = nullptr, int transAb = 0,
-                                                           int64_t bb0 = 0) {
+                                                           int64_t bb0 = 0, int skip_diag = 0) {
     __shared__ T tile[32][33];
     __shared__ T rmax[8][32];
     __shared__ int rexp[32];
@@ -215,7 +320,7 @@ __global__ void __launch_bounds__(256) operand_cols_kernel(const T *__restrict__
         scales += (int64_t)blockIdx.y * n;
     }
     auto val = [&](int64_t j, int64_t i) -> T {
-        if (j >= n || i >= n) return T(0);
+        if (j >= n || i >= n || (skip_diag && i == j)) return T(0);
         T x = trans ? M[j * n + i] : M[i * n + j];
         if (u) x *= (T)u[i];
         if (Mb) x *= transAb ? Mb[bb * n + i] : Mb[i * n + bb];
@@ -568,7 +673,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 tmem_wait_ld();
                 const int64_t k0 = (int64_t)tn * C::kBN + c_off + c0;
-                if constexpr (kWide) {
+                if (kWide && !g.wide_f32) {
                     // float64 storage: the entry, the weights and the partial sums in
                     // float64 (hi is an exact integer sum, lo its small correction)
                     double v[16];
@@ -580,6 +685,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                                          (num_k > 1 ? (double)__uint_as_float(m1[c]) : 0.0) +
                                          (C::kPlanes > 2 ? (double)__uint_as_float(lo[c]) : 0.0);
                         v[c] = k < n ? x * (double)g.scaleB[k] * rs_d : 0.0;
+                    }
+                    if ((g.dA || g.dB) && jok) {
+                        // the terms i = j and i = k of operands split without their diagonal
+                        const double *MA = (const double *)g.MA, *MB = (const double *)g.MB;
+                        const double dAj = g.dA ? g.dA[j] : 0.0;
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) {
+                            const int64_t k = k0 + c;
+                            if (k >= n) continue;
+                            double corr = 0.0;
+                            const double dBk = g.dB ? g.dB[k] : 0.0;
+                            if (dAj != 0.0) corr += dAj * (g.rowB ? MB[j * n + k] : MB[k * n + j]) * (g.uB ? g.uB[j] : 1.0);
+                            if (dBk != 0.0) corr += (g.rowA ? MA[j * n + k] : MA[k * n + j]) * (g.uA ? g.uA[k] : 1.0) * dBk;
+                            if (k == j) corr -= dAj * dBk;
+                            v[c] += corr;
+                        }
                     }
                     if (g.C && jok) {
                         double *Cd = (double *)g.C;
@@ -610,15 +731,71 @@ __global__ void __launch_bounds__(kThreads, 1)
                         tile_acc[r] += part;
                     }
                 } else {
+                    // float32 epilogue: the float32-storage modes, and the s = 3 step of
+                    // the float64-storage modes (float32 copies of the weights; the
+                    // accumulators summed smallest first, rounded once per entry)
                     float v[16];
     #pragma unroll
                     for (int c = 0; c < 16; ++c) {
                         float x = __uint_as_float(hi[c]);
                         if (!C::kTf32) {
                             const int64_t k = k0 + c;
-                            x = (x + __uint_as_float(lo[c])) * (k < n ? g.scaleB[k] : 0.f);
+                            float corr = __uint_as_float(lo[c]);
+                            if constexpr (kWide)
+                                corr = (num_k > 1 ? __uint_as_float(m1[c]) : 0.f) +
+                                       ((C::kPlanes > 2 ? corr : 0.f) + __uint_as_float(m0[c]));
+                            x = (x + corr) * (k < n ? g.scaleB[k] : 0.f);
                         }
                         v[c] = x * rs;
+                    }
+                    if ((g.dA || g.dB) && jok) {
+                        // the terms i = j and i = k of operands split without their diagonal
+                        const float *MA = (const float *)g.MA, *MB = (const float *)g.MB;
+                        const float dAj = g.dA ? (float)g.dA[j] : 0.f;
+                        float dBk[16];
+                        bool anyB = false;
+    #pragma unroll
+                        for (int c = 0; c < 16; ++c) {
+                            dBk[c] = (g.dB && k0 + c < n) ? (float)g.dB[k0 + c] : 0.f;
+                            anyB |= dBk[c] != 0.f;
+                        }
+                        // rows j of the sources, 16-byte loads where they lie inside
+                        const bool full = (k0 + 16 <= n) && ((n & 3) == 0);
+                        auto row16 = [&](const float *M, int rowf, float (&r)[16]) {
+                            if (rowf && full) {
+                                const float4 *p4 = reinterpret_cast<const float4 *>(M + j * n + k0);
+    #pragma unroll
+                                for (int q = 0; q < 4; ++q) {
+                                    const float4 t4 = p4[q];
+                                    r[4 * q] = t4.x, r[4 * q + 1] = t4.y, r[4 * q + 2] = t4.z, r[4 * q + 3] = t4.w;
+                                }
+                            } else {
+    #pragma unroll
+                                for (int c = 0; c < 16; ++c)
+                                    r[c] = k0 + c < n ? (rowf ? M[j * n + k0 + c] : M[(k0 + c) * n + j]) : 0.f;
+                            }
+                        };
+                        float xb[16], xa[16];
+                        if (dAj != 0.f) {
+                            row16(MB, g.rowB, xb);
+                            const float ub = g.uB ? (float)g.uB[j] : 1.f;
+    #pragma unroll
+                            for (int c = 0; c < 16; ++c) v[c] += dAj * xb[c] * ub;
+                        }
+                        if (anyB) {
+                            if (dAj != 0.f && MA == MB && g.rowA == g.rowB) {
+    #pragma unroll
+                                for (int c = 0; c < 16; ++c) xa[c] = xb[c];
+                            } else {
+                                row16(MA, g.rowA, xa);
+                            }
+    #pragma unroll
+                            for (int c = 0; c < 16; ++c)
+                                v[c] += xa[c] * (g.uA && k0 + c < n ? (float)g.uA[k0 + c] : 1.f) * dBk[c];
+                        }
+    #pragma unroll
+                        for (int c = 0; c < 16; ++c)
+                            if (k0 + c == j) v[c] -= dAj * dBk[c];
                     }
                     if (g.C && jok) {
     #pragma unroll
@@ -689,7 +866,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             double wbc = 1.0;
             if (g.Wbc && jok) {
                 const int64_t wi = g.transWbc ? j * n + bb : bb * n + j;
-                wbc = kWide ? ((const double *)g.Wbc)[wi] : (double)((const float *)g.Wbc)[wi];
+                wbc = (kWide && !g.wide_f32) ? ((const double *)g.Wbc)[wi] : (double)((const float *)g.Wbc)[wi];
             }
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
@@ -804,6 +981,8 @@ cudaError_t launch_tc(const TcGemmArgs &g0, cudaStream_t s) {
     CUtensorMap ma, mb;
     const bool bf16 = !C::kTf32;
     if (g.batch > 0 && (g.C || g.nred != 1)) return cudaErrorInvalidValue;
+    if (g.wide_f32 && (!kWide || g.C)) return cudaErrorInvalidValue;
+    if ((g.dA || g.dB) && (g.batch > 0 || (g.dA && !g.MB) || (g.dB && !g.MA))) return cudaErrorInvalidValue;
     const int za = g.batch > 0 ? g.batch : 1;
     CUtensorMap mb2;
     if (!make_map_planes(&ma, g.opA, bf16, C::kPlanes, za * C::kPlanes, g.n, g.ldp, kBM, C::kRowBytes) ||
@@ -845,22 +1024,31 @@ void set_tc_debug(long long wait_limit, int stall) {
 long long tc_debug_wait_limit() { return g_debug_wait_limit; }
 
 cudaError_t launch_split(const void *M, bool wide, int trans, const double *u, int64_t n, int64_t ldp,
-                         int lead_bits, int planes, void *slices, float *scales, cudaStream_t s) {
+                         int lead_bits, int planes, void *slices, float *scales, double *diag_out, cudaStream_t s) {
+    const int sd = diag_out ? 1 : 0;
     if (trans) {
         if (wide)
             split_rows_kernel<double><<<(unsigned)((n + 7) / 8), 256, 0, s>>>(
-                (const double *)M, u, n, ldp, lead_bits, planes, (__nv_bfloat16 *)slices, scales);
+                (const double *)M, u, n, ldp, lead_bits, planes, (__nv_bfloat16 *)slices, scales, diag_out);
         else
             split_rows_kernel<float><<<(unsigned)((n + 7) / 8), 256, 0, s>>>(
-                (const float *)M, u, n, ldp, lead_bits, planes, (__nv_bfloat16 *)slices, scales);
+                (const float *)M, u, n, ldp, lead_bits, planes, (__nv_bfloat16 *)slices, scales, diag_out);
+        return cudaGetLastError();
     } else {
         dim3 grid((unsigned)((n + 31) / 32)), block(32, 8);
         if (wide)
             operand_cols_kernel<true, double><<<grid, block, 0, s>>>((const double *)M, 0, u, n, ldp, lead_bits,
-                                                                     planes, (__nv_bfloat16 *)slices, scales, nullptr);
+                                                                     planes, (__nv_bfloat16 *)slices, scales, nullptr,
+                                                                     nullptr, 0, 0, sd);
         else
             operand_cols_kernel<true, float><<<grid, block, 0, s>>>((const float *)M, 0, u, n, ldp, lead_bits, planes,
-                                                                    (__nv_bfloat16 *)slices, scales, nullptr);
+                                                                    (__nv_bfloat16 *)slices, scales, nullptr, nullptr,
+                                                                    0, 0, sd);
+    }
+    if (diag_out) {
+        const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 1024);
+        if (wide) operand_diag_kernel<double><<<blocks, 256, 0, s>>>((const double *)M, u, n, diag_out);
+        else operand_diag_kernel<float><<<blocks, 256, 0, s>>>((const float *)M, u, n, diag_out);
     }
     return cudaGetLastError();
 }
@@ -924,6 +1112,34 @@ cudaError_t launch_split_g3(const void *Mv, bool wide, int trans, const double *
     dim3 grid((unsigned)((n + 31) / 32), (unsigned)nb), block(32, 8);
     operand_cols_kernel<true, float><<<grid, block, 0, s>>>(M, trans, u, n, ldp, lead_bits, planes,
                                                      (__nv_bfloat16 *)slices, scales, nullptr, Mb, transAb, bb0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f64_pair(const double *M, int64_t total, float *hi, float *lo, cudaStream_t s) {
+    const int64_t blocks = std::min<int64_t>((total + 255) / 256, 8 * (int64_t)sm_count());
+    f64_pair_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(M, total, hi, lo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_g3_pair(const float *Mh, const float *Ml, const double *u, const double *Mb, int transAb,
+                                 int64_t bb0, int nb, int64_t n, int64_t ldp, int lead_bits, int planes, void *slices,
+                                 float *scales, cudaStream_t s) {
+    if (nb < 1 || nb > 65535 || n > kPairSplitMaxN) return cudaErrorInvalidValue;
+    static bool attr[64] = {false};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(split_rows_g3_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(sizeof(float2) * kPairSplitMaxN));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(split_rows_g3_pair_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        attr[dev] = true;
+    }
+    dim3 grid((unsigned)((n + 7) / 8), (unsigned)nb);
+    split_rows_g3_pair_kernel<<<grid, 256, sizeof(float2) * n, s>>>(Mh, Ml, u, Mb, transAb, bb0, n, ldp, lead_bits,
+                                                                    planes, (__nv_bfloat16 *)slices, scales);
     return cudaGetLastError();
 }
 

@@ -140,8 +140,13 @@ int split_lead_bits(int64_t K);
 // written K-major:
 //   split bf16: `planes` slices [planes][n][ldp] plus float row scales [n]  (launch_split)
 //   float32 tf32-rounded copy [n][ldp]                                        (launch_prep)
+// With diag_out, a row whose diagonal entry X(j, j) dominates (more than four
+// times its largest other entry; every row for a column source) leaves it out of
+// the digits and of the row scale and writes it to diag_out[j] (float64; 0 for a
+// row that keeps it): the GEMM adds the left-out terms exactly (TcGemmArgs::dA,
+// dB).
 cudaError_t launch_split(const void *M, bool wide, int trans, const double *u, int64_t n, int64_t ldp,
-                         int lead_bits, int planes, void *slices, float *scales, cudaStream_t s);
+                         int lead_bits, int planes, void *slices, float *scales, double *diag_out, cudaStream_t s);
 cudaError_t launch_prep(const float *M, int trans, const double *u, int64_t n, int64_t ldp,
                         float *out, cudaStream_t s);
 // One fused reduction of the product C: *out += sum_jk C(j,k)^pow W(j,k) a(j) b(k)
@@ -176,6 +181,20 @@ struct TcGemmArgs {
     // float64 storage (bf16x4 only): W, Wbc, Wbd and C are double, and the epilogue
     // forms the entries and the reductions in float64
     int wide;
+    // with `wide` and `batch` (the s = 3 step): the epilogue runs in float32 with
+    // float32 copies of W, Wbc and Wbd (the four accumulators summed in float32)
+    int wide_f32;
+    // Diagonal correction (non-batched products).  An operand split with its
+    // diagonal left out (X(j, j) = 0 in the digits, its value in dA / dB, float64)
+    // misses the terms i = j of C(j, k) = sum_i XA(j, i) XB(k, i); the epilogue adds
+    //   dA[j] XB(k, j) + XA(j, k) dB[k] - [j = k] dA[j] dB[j]
+    // from the operands' sources: XA(j, k) = MA(k, j) uA(k), XB(k, j) = MB(j, k) uB(j),
+    // read as MA[j][k] when rowA (else MA[k][j]) and MB[j][k] when rowB (else
+    // MB[k][j]); dA or dB null: that operand keeps its diagonal.
+    const double *dA, *dB;
+    const void *MA, *MB;                     // float, or double with `wide`
+    int rowA, rowB;
+    const double *uA, *uB;
     // set by the launcher from set_tc_debug: the limit of every mbarrier wait in SM
     // cycles (0: the default, about two seconds) and the stalled-producer test hook
     long long wait_limit;
@@ -203,5 +222,14 @@ cudaError_t launch_split_g3(const void *M, bool wide, int trans, const double *u
                             int64_t bb0, int nb, int64_t n, int64_t ldp, int lead_bits, int planes, void *slices,
                             float *scales, cudaStream_t s);
 cudaError_t launch_gemm_tf32(const TcGemmArgs &g, cudaStream_t s);
+// float64 -> float pair (hi, lo; lo may be null: float64 -> float), `total` entries.
+cudaError_t launch_f64_pair(const double *M, int64_t total, float *hi, float *lo, cudaStream_t s);
+// The s = 3 step's A operands of the float64-storage modes, from float-pair copies
+// (Mh, Ml) of a row-major source read along rows (A(i, j) = M[j][i]), in float32
+// double-float arithmetic; n <= kPairSplitMaxN.  Layout as launch_split_g3.
+constexpr int64_t kPairSplitMaxN = 24576;
+cudaError_t launch_split_g3_pair(const float *Mh, const float *Ml, const double *u, const double *Mb, int transAb,
+                                 int64_t bb0, int nb, int64_t n, int64_t ldp, int lead_bits, int planes, void *slices,
+                                 float *scales, cudaStream_t s);
 
 }  // namespace ustat

@@ -438,13 +438,15 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan, const P
     // deeper pipeline by default (measured on the n = 16384 products: 0.99 / 1.04
     // of the bf16x3 / bf16x4 ceilings against 0.92 / 0.67 with 128-byte k-blocks;
     // equal on the symmetric 4096 product); up to n = 1024 (short k loops, where
-    // 128-byte k-blocks measured 5 % faster on the batched s = 3 steps) 128-byte
-    // k-blocks, except bf16x5, which has only the 64-byte form
-    // the RBF build on 64 x 64 tiles above n = 1024 (measured at n = 4096: 75 us
-    // against 82 us for 128 x 128 tiles)
+    // 128-byte k-blocks measured 5 % faster on the batched bf16x3 s = 3 steps)
+    // 128-byte k-blocks, except in the float64-storage modes (bf16x5 has only the
+    // 64-byte form; the bf16x4 s = 3 steps at n = 1024 measured 292 ms per K4 +
+    // cycle evaluation with 128 x 128 tiles against 400 ms with 128 x 64 tiles)
+    // the CUDA-core RBF build, when chosen, on 64 x 64 tiles above n = 1024
+    // (measured at n = 4096: 75 us against 82 us for 128 x 128 tiles)
     for (int c = 0; c < 4; ++c) {
         int v = 0;
-        if (is_split_mode(P.precision) && (c > 0 || P.precision == USTAT_BF16X5)) v |= 2 << 2;
+        if (is_split_mode(P.precision) && (c > 0 || wide_storage(P.precision))) v |= 2 << 2;
         if (!wide_storage(P.precision) && c > 0) v |= 1 << 4;
         P.tc_variant[c] = v;
     }

@@ -298,10 +298,10 @@ def test_k4_cycle_treewidth3_steps_multi_tile(eng_mod, k4c_ref, prec):
 # K4 + cycle at its full size n = 1024: 203 partitions, 26 of treewidth 3, whose
 # s = 3 steps run in 25 batches of 42 indices, each split on the caller's stream
 # into one of two alternating regions while the GEMM of the batch before runs on
-# a second stream.  bf16x4 (float64 storage) is the 1e-8 mode; bf16x3 stores the
-# intermediate n x n products in float32 (2^-24 per entry, up to seven entries
-# per term) and is held to the float32-storage bound.
-@pytest.mark.parametrize("prec,tol", [("bf16x4", 1e-8), ("bf16x5", 1e-8), ("bf16x3", SMALL_N)])
+# a second stream.  Every split mode meets 1e-8 here: the products of entrywise
+# powers of K (dominant diagonals) are split without their diagonals, whose
+# terms the GEMM epilogue adds exactly.
+@pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-8), ("bf16x4", 1e-8), ("bf16x5", 1e-8)])
 def test_k4_cycle_full_size_against_oracle(eng_mod, prec, tol):
     w = synth.workload("k4_cycle_rbf")
     ref, absref = _stored("k4_cycle_rbf")
@@ -343,12 +343,13 @@ def test_path5_full_size_rank1_bit_exact(eng_mod):
     assert out["U_sum"] == float(U)
 
 
-@pytest.mark.parametrize("prec,tol", [("bf16x4", 1e-8), ("bf16x5", 1e-8), ("bf16x3", 1e-6)])
+@pytest.mark.parametrize("prec,tol", [("bf16x4", 1e-8), ("bf16x5", 1e-8), ("bf16x3", 2e-7)])
 def test_path5_full_size_against_oracle(eng_mod, prec, tol):
     # the path + chord workload at its full size, n = 16384, d = 64, t(5) data: all
     # 52 V_pi (20 of them treewidth-2 products on the tensor cores) and U against
-    # the oracle's stored values.  bf16x3 keeps 24 bits relative to each row's
-    # largest entry, which for these heavy-tailed rows is the 1e-6 class
+    # the oracle's stored values.  The float64-storage modes meet 1e-8; bf16x3
+    # stores the products of these heavy-tailed rows in float32, the float32
+    # CUDA-core mode's class (1.1e-7 measured for that mode)
     w = synth.workload("path5_chord_linear_tanh")
     ref, absref = _stored("path5_chord_linear_tanh")
     out = eng_mod.Engine(w.graph, w.factors, precision=prec).evaluate(w.X)
