@@ -199,6 +199,32 @@ int ustat_workspace_bytes(const ustat_plan_t *plan, int64_t n, int d, size_t *by
 int ustat_eval(ustat_plan_t *plan, const void *X, int x_dtype, int64_t n, int d,
                const ustat_factor *factors, int n_factors, void *ws, size_t ws_bytes,
                void *stream, double *U_out, double *V_out);
+/*
+ * Row shard of one evaluation over n_ranks ranks (one GPU each): U = sum_pi mu_pi
+ * V_pi is built from scalars that are sums over index tuples (Section 3.3, Lemma
+ * "Decomposition of U-Statistic into V-Statistics"; each V_pi is an Einsum over
+ * the restricted index set, Definition "Restricted V-Statistic"), so the index
+ * ranges of the heavy steps can be divided among ranks and the partial scalars
+ * summed.  ustat_eval_rows runs the plan on this rank: the n^3 products that feed
+ * only reductions are computed on the rank's contiguous range of their output
+ * tiles, the treewidth-3 steps (split modes) on its range of the eliminated
+ * index's values, everything else whole (X is replicated: the factor matrices
+ * are built on every rank).  It writes the plan's scalars, float64 on the device,
+ * scal_out[ustat_scalar_count()], such that the sum over ranks of scal_out is the
+ * unsharded evaluation's scalars (scalars every rank computes whole are 0 except on
+ * rank 0).  The caller sums the ranks' arrays (one all-reduce of that many
+ * doubles) and calls ustat_combine, which forms U_out[2] and V_out[n_parts] (may
+ * be NULL) on the device, as ustat_eval would.  n_ranks = 1 gives the whole
+ * evaluation's scalars.  Workspace as for ustat_eval.  Errors as ustat_eval, and
+ * USTAT_ERR_UNSUPPORTED for a plan whose steps read one of its scalars.
+ */
+int ustat_scalar_count(const ustat_plan_t *plan, int *count);
+int ustat_eval_rows(ustat_plan_t *plan, int rank, int n_ranks, const void *X, int x_dtype, int64_t n, int d,
+                    const ustat_factor *factors, int n_factors, void *ws, size_t ws_bytes, void *stream,
+                    double *scal_out);
+int ustat_combine(const ustat_plan_t *plan, const double *scal, int64_t n, void *stream, double *U_out,
+                  double *V_out);
+
 /* Treewidth-3 steps in the split modes run their GEMMs on a second stream that
  * each host thread creates (with two events) at its first such evaluation on a
  * device: on a new thread, make that first call before any stream capture. */

@@ -236,6 +236,9 @@ struct Ctx {
     int d;
     bool fp64;
     cudaStream_t st;
+    // row shard (ustat_eval_rows): this rank's share of the n^3 reduction products
+    // and of the treewidth-3 indices; nranks = 1 is a whole evaluation
+    int rank = 0, nranks = 1;
     void *ptr(int slot) const { return slot < 0 ? nullptr : (void *)(ws + L.off[slot]); }
     double *vec(int slot) const { return (double *)ptr(slot); }
     // slices: [3][n][ldp] bf16 followed by float scales [n]
@@ -295,7 +298,47 @@ int check_graph_factors(const Plan &P, const ustat_factor *f, int nf, int d) {
     return USTAT_OK;
 }
 
-int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f, double *U_out, double *V_out) {
+// The Moebius combination of a plan's scalars (one warp, float64, compensated).
+cudaError_t plan_combine(const Plan &P, const Layout &L, const double *scal, const int *err, int64_t n,
+                         double *U_out, double *V_out, cudaStream_t st) {
+    static thread_local std::vector<CombineEntry> tab;
+    tab.resize(P.parts.size());
+    for (size_t p = 0; p < P.parts.size(); ++p) {
+        const PartRec &pr = P.parts[p];
+        CombineEntry &en = tab[p];
+        en.mu = pr.mu;
+        en.nfree = (unsigned char)pr.nfree;
+        en.evaluated = (unsigned char)pr.evaluated;
+        for (int q = 0; q < kCombineMaxScal; ++q)
+            en.sid[q] = (q < pr.nscal) ? (unsigned short)L.scal_index[pr.scal[q]] : (unsigned short)0xffff;
+    }
+    return launch_combine(tab.data(), (int)tab.size(), P.m, scal, err, n, U_out, V_out, st);
+}
+
+// Row shard: the scalar slots written by sharded work (the reductions of products
+// that store nothing, computed on a range of their tiles, and the treewidth-3
+// steps, computed on a range of indices); every other scalar is computed whole on
+// every rank.  A plan whose steps read a scalar cannot be sharded this way.
+bool row_shard_slots(const Plan &P, std::vector<char> &sharded) {
+    sharded.assign(P.slots.size(), 0);
+    auto is_scal = [&](int s) { return s >= 0 && P.slots[s].kind == S_SCAL; };
+    for (const Op &op : P.ops) {
+        if (is_scal(op.u) || is_scal(op.a) || is_scal(op.b) || is_scal(op.ub)) return false;
+        for (int t = 0; t < op.nt; ++t)
+            if (is_scal(op.t[t].mat)) return false;
+    }
+    const bool tc = is_split_mode(P.precision) || P.precision == USTAT_TF32;
+    for (const Op &op : P.ops) {
+        if (op.kind == OP_GEMM && tc && !op.store)
+            for (int r = 0; r < op.nred; ++r)
+                if (is_scal(op.red[r].out)) sharded[op.red[r].out] = 1;
+        if (op.kind == OP_GEMM3 && is_split_mode(P.precision) && is_scal(op.out)) sharded[op.out] = 1;
+    }
+    return true;
+}
+
+int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f, double *U_out, double *V_out,
+                double *scal_out = nullptr) {
     const Plan &P = C.P;
     const int64_t n = C.n;
     cudaError_t e = cudaMemsetAsync(C.ws, 0, C.L.zero_bytes, C.st);
@@ -461,6 +504,10 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                                          (double *)C.ptr(R.out)};
                     }
                     g.symmetric = op.symmetric;
+                    if (C.nranks > 1 && !op.store) {
+                        g.shard_rank = C.rank;
+                        g.shard_count = C.nranks;
+                    }
                     if (split && op.opA >= 0 && op.opB >= 0 && (D.removed[op.opA] || D.removed[op.opB])) {
                         // operands split without their diagonal: the epilogue adds the
                         // left-out terms from the operands' sources
@@ -546,8 +593,10 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                         if (e != cudaSuccess) break;
                     }
                     int k = 0, last = 0;
-                    for (int64_t bb0 = 0; bb0 < n && e == cudaSuccess; bb0 += C.L.g3_nb, ++k) {
-                        const int nb = (int)std::min<int64_t>(C.L.g3_nb, n - bb0);
+                    // a row shard takes the indices bb_lo .. bb_hi - 1
+                    const int64_t bb_lo = n * C.rank / C.nranks, bb_hi = n * (C.rank + 1) / C.nranks;
+                    for (int64_t bb0 = bb_lo; bb0 < bb_hi && e == cudaSuccess; bb0 += C.L.g3_nb, ++k) {
+                        const int nb = (int)std::min<int64_t>(C.L.g3_nb, bb_hi - bb0);
                         const int h = two ? (k & 1) : 0;
                         char *sl = C.ws + C.L.g3_off + (size_t)h * C.L.g3_stride * C.L.g3_nb;
                         float *sc = (float *)(sl + planes * plane_bytes * C.L.g3_nb);
@@ -601,7 +650,7 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                     ps.kernels = 2 * k + (pair ? 1 + (op.W.mat >= 0) + (op.Wbc.mat >= 0) + (op.Wbd.mat >= 0) : 0);
                     // join: the caller's stream waits for the last GEMM (the second
                     // stream runs its GEMMs in order)
-                    if (e == cudaSuccess && two) e = cudaStreamWaitEvent(C.st, S->gemm_done[last], 0);
+                    if (e == cudaSuccess && two && k > 0) e = cudaStreamWaitEvent(C.st, S->gemm_done[last], 0);
                     break;
                 }
                 SimtGemmArgs g{};
@@ -629,22 +678,26 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
         }
         if (e != cudaSuccess) return cuda_fail(e);
     }
-    // Moebius combination
-    static thread_local std::vector<CombineEntry> tab;
-    tab.resize(P.parts.size());
-    for (size_t p = 0; p < P.parts.size(); ++p) {
-        const PartRec &pr = P.parts[p];
-        CombineEntry &en = tab[p];
-        en.mu = pr.mu;
-        en.nfree = (unsigned char)pr.nfree;
-        en.evaluated = (unsigned char)pr.evaluated;
-        for (int q = 0; q < kCombineMaxScal; ++q)
-            en.sid[q] = (q < pr.nscal) ? (unsigned short)C.L.scal_index[pr.scal[q]] : (unsigned short)0xffff;
+    if (scal_out) {
+        // row shard: this rank's scalars; the ones every rank computes whole count
+        // on rank 0 only, so that the ranks' arrays sum to the plan's scalars
+        int ns = 0;
+        for (size_t sl = 0; sl < P.slots.size(); ++sl) ns += P.slots[sl].kind == S_SCAL;
+        e = cudaMemcpyAsync(scal_out, C.ws + C.L.scal_off, 8 * (size_t)ns, cudaMemcpyDeviceToDevice, C.st);
+        if (e != cudaSuccess) return cuda_fail(e);
+        if (C.rank != 0) {
+            std::vector<char> sharded;
+            row_shard_slots(P, sharded);
+            for (size_t sl = 0; sl < P.slots.size() && e == cudaSuccess; ++sl)
+                if (P.slots[sl].kind == S_SCAL && !sharded[sl])
+                    e = cudaMemsetAsync(scal_out + C.L.scal_index[sl], 0, 8, C.st);
+            if (e != cudaSuccess) return cuda_fail(e);
+        }
+        return USTAT_OK;
     }
     {
         ProfScope ps(kProfCombine, C.st);
-        e = launch_combine(tab.data(), (int)tab.size(), P.m, (const double *)(C.ws + C.L.scal_off), err, n, U_out,
-                           V_out, C.st);
+        e = plan_combine(P, C.L, (const double *)(C.ws + C.L.scal_off), err, n, U_out, V_out, C.st);
     }
     if (e != cudaSuccess) return cuda_fail(e);
     return USTAT_OK;
@@ -1041,6 +1094,46 @@ int ustat_eval(ustat_plan_t *plan, const void *X, int x_dtype, int64_t n, int d,
     if (!ws || ws_bytes < L.total || ((uintptr_t)ws % 256) != 0) return USTAT_ERR_WORKSPACE;
     Ctx C{P, L, (char *)ws, n, d, wide_storage(P.precision), (cudaStream_t)stream};
     return run_program(C, X, x_dtype, factors, U_out, V_out);
+}
+
+int ustat_scalar_count(const ustat_plan_t *plan, int *count) {
+    if (!plan || !count) return USTAT_ERR_INVALID_ARG;
+    int ns = 0;
+    for (auto &sl : plan->p.slots) ns += sl.kind == S_SCAL;
+    *count = ns;
+    return USTAT_OK;
+}
+
+int ustat_eval_rows(ustat_plan_t *plan, int rank, int n_ranks, const void *X, int x_dtype, int64_t n, int d,
+                    const ustat_factor *factors, int n_factors, void *ws, size_t ws_bytes, void *stream,
+                    double *scal_out) {
+    if (!plan || !X || !scal_out || d < 1 || n < 1 || (x_dtype != 0 && x_dtype != 1) || n_ranks < 1 || rank < 0 ||
+        rank >= n_ranks)
+        return USTAT_ERR_INVALID_ARG;
+    const Plan &P = plan->p;
+    if (n < P.m) return USTAT_ERR_N_LT_M;
+    if (n > (int64_t)1 << 20) return USTAT_ERR_UNSUPPORTED;
+    std::vector<char> sharded;
+    if (!row_shard_slots(P, sharded)) return USTAT_ERR_UNSUPPORTED;
+    int rc = check_graph_factors(P, factors, n_factors, d);
+    if (rc != USTAT_OK) return rc;
+    Layout L = make_layout(P, n, d);
+    if (!ws || ws_bytes < L.total || ((uintptr_t)ws % 256) != 0) return USTAT_ERR_WORKSPACE;
+    Ctx C{P, L, (char *)ws, n, d, wide_storage(P.precision), (cudaStream_t)stream};
+    C.rank = rank;
+    C.nranks = n_ranks;
+    return run_program(C, X, x_dtype, factors, nullptr, nullptr, scal_out);
+}
+
+int ustat_combine(const ustat_plan_t *plan, const double *scal, int64_t n, void *stream, double *U_out,
+                  double *V_out) {
+    if (!plan || !scal || !U_out || n < 1) return USTAT_ERR_INVALID_ARG;
+    const Plan &P = plan->p;
+    if (n < P.m) return USTAT_ERR_N_LT_M;
+    Layout L = make_layout(P, n, 1);
+    cudaError_t e = plan_combine(P, L, scal, nullptr, n, U_out, V_out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return USTAT_OK;
 }
 
 int ustat_host_staging_bytes(const ustat_plan_t *plan, int64_t n, int d, size_t *bytes) {

@@ -487,19 +487,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     // work units: the tiles, except that the last g.split_tail tiles of the schedule
     // are split into two halves of kBN / 2 columns, so that the last wave of the
     // persistent grid is (nearly) full
-    const int n_tiles = walk.count();
+    // a row shard (g.tile_hi > 0) takes the tiles tile_lo .. tile_hi - 1 of the walk
+    const int t_lo = g.tile_hi > 0 ? g.tile_lo : 0;
+    const int n_tiles = g.tile_hi > 0 ? g.tile_hi - g.tile_lo : walk.count();
     const int split_tail = g.split_tail;
     const int total_tiles = n_tiles + split_tail;
     constexpr int kHalf = C::kBN / 2;
     auto unit = [&](int t, int &bl, int &tm, int &tn, int &c_off, int &width) {
         const int f = n_tiles - split_tail;
         if (t < f) {
-            walk.coords(t, bl, tm, tn);
+            walk.coords(t_lo + t, bl, tm, tn);
             c_off = 0;
             width = C::kBN;
         } else {
             const int v = t - f;
-            walk.coords(f + (v >> 1), bl, tm, tn);
+            walk.coords(t_lo + f + (v >> 1), bl, tm, tn);
             c_off = (v & 1) * kHalf;
             width = kHalf;
         }
@@ -999,7 +1001,16 @@ cudaError_t launch_tc(const TcGemmArgs &g0, cudaStream_t s) {
         attr[dev] = true;
     }
     const int64_t tm = (g.n + kBM - 1) / kBM, tn = (g.n + C::kBN - 1) / C::kBN;
-    const int64_t tiles = (g.symmetric ? tm * (tm + 1) / 2 : tm * tn) * za;
+    int64_t tiles = (g.symmetric ? tm * (tm + 1) / 2 : tm * tn) * za;
+    g.tile_lo = g.tile_hi = 0;
+    if (g.shard_count > 1) {
+        if (g.C || g.shard_rank < 0 || g.shard_rank >= g.shard_count) return cudaErrorInvalidValue;
+        const int64_t lo = tiles * g.shard_rank / g.shard_count, hi = tiles * (g.shard_rank + 1) / g.shard_count;
+        if (hi <= lo) return cudaSuccess;   // nothing in this range
+        g.tile_lo = (int)lo;
+        g.tile_hi = (int)hi;
+        tiles = hi - lo;
+    }
     // half tiles for the last, partly filled wave: with R tiles left over after the
     // full waves, split R of them when 2R still fits one wave (all of them, up to
     // the SM count, when there is less than one wave)

@@ -195,6 +195,12 @@ struct TcGemmArgs {
     const void *MA, *MB;                     // float, or double with `wide`
     int rowA, rowB;
     const double *uA, *uB;
+    // row shard: the product's tiles are divided into shard_count contiguous
+    // ranges of its walk and only range shard_rank is computed (shard_count > 1;
+    // reductions only: the ranks' scalars sum to the product's); the launcher sets
+    // tile_lo / tile_hi
+    int shard_rank, shard_count;
+    int tile_lo, tile_hi;
     // set by the launcher from set_tc_debug: the limit of every mbarrier wait in SM
     // cycles (0: the default, about two seconds) and the stalled-producer test hook
     long long wait_limit;

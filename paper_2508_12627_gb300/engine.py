@@ -119,6 +119,43 @@ class Engine:
         self.launch(X, out)
         return self.reduce_shards(out, group)
 
+    def scalars_rows(self, X, rank, n_ranks):
+        """This rank's row shard of one evaluation (ustat_eval_rows): a float64 device
+        tensor of the plan's scalars, which sums over the ranks to the whole
+        evaluation's scalars."""
+        X = self.to_device(X)
+        n, d = X.shape
+        ws = self.workspace(self.plan.workspace_bytes(n, d))
+        scal = torch.zeros(max(1, us.scalar_count(self.plan)), dtype=torch.float64, device=self.device)
+        st = torch.cuda.current_stream(self.device).cuda_stream
+        us.ustat_eval_rows(self.plan, rank, n_ranks, X.data_ptr(), 0 if X.dtype == torch.float64 else 1, n, d,
+                           self.factor_tuples(n), ws.data_ptr(), ws.numel(), st, scal.data_ptr())
+        return scal
+
+    def combine(self, scal, n):
+        """U and V from a plan's (summed) scalars (ustat_combine)."""
+        out = torch.empty(2 + self.n_parts, dtype=torch.float64, device=self.device)
+        st = torch.cuda.current_stream(self.device).cuda_stream
+        us.ustat_combine(self.plan, scal.data_ptr(), n, st, out.data_ptr(), out.data_ptr() + 16)
+        o = out.cpu().numpy()
+        return {"U_sum": float(o[0]), "U_mean": float(o[1]), "V": o[2:].copy()}
+
+    @staticmethod
+    def reduce_row_scalars(scal, group=None):
+        """The exchange step of a row-sharded evaluation: one all-reduce (sum) of the
+        ranks' scalar arrays (NCCL for device tensors)."""
+        import torch.distributed as dist
+        dist.all_reduce(scal, op=dist.ReduceOp.SUM, group=group)
+        return scal
+
+    def evaluate_rows(self, X, group=None):
+        """One evaluation row-sharded over the ranks of ``group`` (one GPU each):
+        this rank's share, the all-reduce of the scalars, the combination."""
+        import torch.distributed as dist
+        scal = self.scalars_rows(X, dist.get_rank(group), dist.get_world_size(group))
+        self.reduce_row_scalars(scal, group)
+        return self.combine(scal, X.shape[0])
+
     def evaluate_host(self, X_host_pinned, U_host, V_host):
         """End-to-end call with host input and outputs (ustat_eval_host):
         X_host_pinned is a pinned torch CPU tensor, U_host / V_host ctypes arrays."""

@@ -65,6 +65,9 @@ EXPORTS = {
     "ustat_workspace_bytes": (_i, [_vp, _i64, _i, _P(_sz)]),
     "ustat_status": (_i, [_vp, _vp, _P(_i)]),
     "ustat_debug_set_wait": (_i, [ctypes.c_longlong, _i]),
+    "ustat_scalar_count": (_i, [_vp, _P(_i)]),
+    "ustat_eval_rows": (_i, [_vp, _i, _i, _vp, _i, _i64, _i, _P(ustat_factor), _i, _vp, _sz, _vp, _vp]),
+    "ustat_combine": (_i, [_vp, _vp, _i64, _vp, _vp, _vp]),
     "ustat_noalloc_status": (_i, [_vp, _P(_i)]),
     "ustat_eval": (_i, [_vp, _vp, _i, _i64, _i, _P(ustat_factor), _i, _vp, _sz, _vp, _vp, _vp]),
     "ustat_host_staging_bytes": (_i, [_vp, _i64, _i, _P(_sz)]),
@@ -406,6 +409,24 @@ def debug_set_wait(limit_cycles=0, stall_producer=False):
 
 
 NOALLOC_MAX_BYTES = 64 * 1024 * 1024
+
+
+def scalar_count(plan):
+    """ustat_scalar_count: the length of a row shard's scalar array."""
+    c = _i()
+    _check(lib().ustat_scalar_count(plan.handle, ctypes.byref(c)), "ustat_scalar_count")
+    return c.value
+
+
+def ustat_eval_rows(plan, rank, n_ranks, X_ptr, x_dtype, n, d, factors, ws_ptr, ws_bytes, stream, scal_ptr):
+    fa = factor_array(factors)
+    rc = lib().ustat_eval_rows(plan.handle, rank, n_ranks, X_ptr, x_dtype, n, d, fa, len(factors), ws_ptr, ws_bytes,
+                               stream, scal_ptr)
+    _check(rc, "ustat_eval_rows")
+
+
+def ustat_combine(plan, scal_ptr, n, stream, U_ptr, V_ptr):
+    _check(lib().ustat_combine(plan.handle, scal_ptr, n, stream, U_ptr, V_ptr), "ustat_combine")
 
 
 def ustat_eval_noalloc(plan, X_ptr, x_dtype, n, d, factors, stream, U_ptr, V_ptr):

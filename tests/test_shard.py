@@ -174,3 +174,85 @@ def test_order_seven_chain_shards_cover_once_and_plan_quickly(us):
     full = us.Plan(g, [us.MATRIX] * len(names))
     f = [p.flops(10000)[0] for p in plans]
     assert max(f) <= 1.2 * full.flops(10000)[0] / 2
+
+
+# ---------------------------------------------------------------- row shards of one evaluation
+# (ustat_eval_rows / ustat_combine): each rank computes a contiguous range of the
+# tiles of every n^3 product that feeds only reductions and of the values of every
+# treewidth-3 step's eliminated index, the rest whole; the ranks' scalar arrays sum
+# to the whole evaluation's scalars.
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name,n,N,prec", [("c4_rbf", 1100, 2, "bf16x3"), ("c4_rbf", 1100, 3, "bf16x3"),
+                                           ("k4_cycle_rbf", 300, 2, "bf16x3"), ("k4_cycle_rbf", 300, 4, "bf16x4"),
+                                           ("path5_chord_linear_tanh", 300, 3, "bf16x4"),
+                                           ("triangle_rbf", 200, 2, "fp64")])
+def test_row_shards_on_one_gpu_sum_to_the_whole_evaluation(us, name, n, N, prec):
+    import torch
+    from paper_2508_12627_gb300.engine import Engine
+    w = synth.workload(name, n)
+    eng = Engine(w.graph, w.factors, precision=prec)
+    whole = eng.evaluate(w.X)
+    parts = [eng.scalars_rows(w.X, r, N) for r in range(N)]
+    torch.cuda.synchronize()
+    one = eng.scalars_rows(w.X, 0, 1)
+    tot = torch.stack(parts).sum(0)
+    got = eng.combine(tot, n)
+    a = uo.ustat(w.graph, w.factors, w.X, absolute=True)
+    Vabs = np.maximum(np.array(a["V"]), 1e-300)
+    # the same products in another grouping of the float64 atomic sums: agreement
+    # far below the modes' tolerances
+    assert np.all(np.abs(got["V"] - whole["V"]) <= 1e-12 * Vabs)
+    assert np.allclose(one.cpu().numpy(), tot.cpu().numpy(), rtol=1e-12, atol=1e-300)
+    ref = uo.ustat(w.graph, w.factors, w.X)
+    tol = {"fp64": 1e-11, "bf16x3": 5e-7, "bf16x4": 1e-8}[prec]
+    assert np.all(np.abs(got["V"] - np.array(ref["V"])) <= tol * Vabs)
+    if prec == "fp64":
+        # the CUDA-core products are not divided: rank 0 computes everything
+        assert np.array_equal(parts[0].cpu().numpy(), one.cpu().numpy())
+        assert all(not p.cpu().numpy().any() for p in parts[1:])
+    else:
+        # every rank has work in the sharded steps: no rank's array equals the whole
+        for p in parts:
+            assert not np.allclose(p.cpu().numpy(), one.cpu().numpy())
+
+
+def _row_rank(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    import torch
+    from paper_2508_12627_gb300.engine import Engine
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # a stand-in for a rank's scalar array (no GPU here): rank r holds the r-th
+    # term of a split of known values; the exchange must return their sum
+    full = np.linspace(-3.0, 7.0, 41) ** 3
+    noise = np.random.default_rng(7).standard_normal(41)
+    mine = torch.as_tensor(full / 2 + (noise if rank == 0 else -noise))
+    res = Engine.reduce_row_scalars(mine.clone())
+    dist.destroy_process_group()
+    q.put((rank, res.numpy().tolist()))
+
+
+def test_two_gloo_ranks_sum_their_row_scalars():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_row_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(300)
+        assert p.exitcode == 0
+    res = sorted(q.get(timeout=10) for _ in range(world))
+    full = np.linspace(-3.0, 7.0, 41) ** 3
+    for _, v in res:
+        assert np.allclose(v, full, rtol=1e-14, atol=1e-12)
+
+
+def test_row_shard_scalar_count_and_arguments(us):
+    w = synth.workload("k4_cycle_rbf", 64)
+    p = us.Plan(w.graph, [f.kind for f in w.factors], precision="bf16x3")
+    assert us.scalar_count(p) > 0
+    for rank, N in [(2, 2), (-1, 2), (0, 0)]:
+        with pytest.raises(us.UstatError):
+            us.ustat_eval_rows(p, rank, N, 256, 0, 64, 32, [(uo.RBF, 64.0, 0)], 256, 1 << 30, None, 256)
