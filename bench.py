@@ -43,8 +43,8 @@ WORKLOADS = {
                     "each as four exact U-statistics of the two distance matrices: 220 U-statistics per step",
     "hoif_chain": "HOIF chain U-statistics U(h_j), j = 2..7 (chains g...g f of j - 1 pairwise factors, all Bell(j) "
                   "partitions each), n=10000: phi(Z) = sqrt(2) Z with Z ~ N(0, I_16), A ~ Bernoulli(1/2), "
-                  "Y = Z.beta + N(0,1) (seed 0); G = Psi Psi', F = Psi Theta' formed on the host; 6 U-statistics "
-                  "per step",
+                  "Y = Z.beta + N(0,1) (seed 0); G = Psi Psi', F = Psi Theta' built on the device from the n x 16 "
+                  "terms; 6 U-statistics per step",
     "batched": "512 independent samples, n uniform in [256, 4096] (seed 0), X_i n_i x 16 iid N(0,1) float64 "
                "(seed 1000+i), each evaluated for the m=4 4-cycle and the m=5 5-cycle RBF kernels (15 and 52 "
                "partitions): 1024 U-statistics per step, one captured CUDA graph per kernel graph",
@@ -608,12 +608,11 @@ def run_motifs(args):
 
     # end to end: A and B from pinned host memory, the six counts, U back to the host
     Ah = torch.from_numpy(A).pin_memory()
-    Bh = torch.from_numpy(1.0 - A).pin_memory()
     Uh = torch.empty((evals, 2), dtype=torch.float64).pin_memory()
     ke = min(args.steps, 5)
     t1 = time.perf_counter()
     for _ in range(ke):
-        mc.set_graph(Ah, Bh, non_blocking=True)
+        mc.set_graph(Ah, non_blocking=True)   # B = 1 - A is formed on the device
         step()
         for i, o in enumerate(outs):
             Uh[i].copy_(o[:2], non_blocking=True)
@@ -642,7 +641,7 @@ def run_motifs(args):
         "tflops": {"algorithmic_plan": fl * args.steps / (tot_ms / 1e3) / 1e12},
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": evals / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": 2 * n * n * 8,
+        "e2e": {"value": evals / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": n * n * 8,
                 "d2h_bytes_per_step": evals * 16},
         "gpu_launches": int(sum(c for (_, c) in prof.values())),
         "clocks": clk,
@@ -657,8 +656,11 @@ def run_motifs(args):
 
 def run_dcov(args):
     """dCov^2 of every pair of the 11 sector return matrices at n = 138 (the
-    distance-covariance example's size): four U-statistics per pair, launched
-    eagerly on one stream; the distance matrices are computed on the host."""
+    distance-covariance example's size).  A step builds the 11 distance matrices
+    on the device from the return matrices (ustat_factor_matrix) and evaluates
+    four U-statistics per pair from them; the step's 231 library calls are
+    captured once into one CUDA graph that every step replays (with --eager,
+    launched one by one on the stream)."""
     import math
 
     import numpy as np
@@ -674,7 +676,7 @@ def run_dcov(args):
     torch.cuda.set_device(dev)
     R = synth.sector_returns()
     n = R[0].shape[0]
-    Dh = [dcov.distances(r) for r in R]
+    Dh = [np.ascontiguousarray(r, dtype=np.float64) for r in R]
     Dd = [torch.from_numpy(d).to(dev) for d in Dh]
     pairs = [(i, j) for i in range(len(R)) for j in range(i + 1, len(R))]
     dc = dcov.DCov2(n, precision=args.precision, device=dev)
@@ -682,9 +684,19 @@ def run_dcov(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step():
+    Dist = [torch.empty((n, n), dtype=torch.float64, device=dev) for _ in Dd]
+
+    def eager():
+        for d, D in zip(Dd, Dist):
+            dc.distance(d, D)
         for (i, j), o in zip(pairs, outs):
-            dc.launch(Dd[i], Dd[j], o, stream)
+            dc.launch_matrices(Dist[i], Dist[j], o)
+
+    if args.eager:
+        step = eager
+    else:
+        graph = dc.capture(eager)
+        step = graph.replay
 
     for _ in range(args.warmup):
         step()
@@ -708,14 +720,15 @@ def run_dcov(args):
     value = evals * args.steps / (tot_ms / 1e3)
     vals = [dc.combine([float(x[0].item()) for x in o]) for o in outs]
 
-    # per-operation profile of one more step (not timed above)
+    # per-operation profile of one more step (not timed above), launched eagerly:
+    # the graph replays the same kernels
     us.profile_enable(True)
     us.profile_collect()
-    step()
+    eager()
     torch.cuda.synchronize()
     us.profile_enable(False)
     prof = us.profile_collect()
-    launches = sum(c for (_, c) in prof.values())
+    launches = sum(c for (_, c) in prof.values()) + len(Dd)   # + one pairs kernel per distance matrix
     peaks, peak_src = load_peaks()
     # Every kernel graph of dCov^2 is a forest (treewidth 1): no n^3 product,
     # only n^2 passes.  Algorithmic bytes: each U-statistic reads its two
@@ -729,7 +742,7 @@ def run_dcov(args):
             "peak_note": "%s HBM copy bandwidth; at n = %d every kernel takes a few microseconds and the step is "
                          "bound by launch latency, not by memory" % (peak_src, n)}
 
-    # end to end: the 11 distance matrices from pinned host memory, 220 U-statistics, the U_sums back
+    # end to end: the 11 return matrices from pinned host memory, 220 U-statistics, the U_sums back
     Dp = [torch.from_numpy(d).pin_memory() for d in Dh]
     Uh = torch.empty((len(pairs), 4), dtype=torch.float64).pin_memory()
     ke = min(args.steps, 20)
@@ -750,7 +763,8 @@ def run_dcov(args):
         t2 = time.perf_counter()
         ref = []
         for i, j in pairs:
-            F = [synth.Factor(synth.MATRIX, 1.0, Dh[i]), synth.Factor(synth.MATRIX, 1.0, Dh[j])]
+            F = [synth.Factor(synth.DIST, float(Dh[i].shape[1]), Dh[i]),
+                 synth.Factor(synth.DIST, float(Dh[j].shape[1]), Dh[j])]
             u = [uo.ustat(synth.Graph(k, e), F, np.zeros((n, 1)))["U_sum"] for _, k, e in dcov.TERMS]
             ref.append(math.fsum(c(n) * x for (c, _, _), x in zip(dcov.TERMS, u)) / math.perm(n, 4))
         dt = time.perf_counter() - t2
@@ -763,7 +777,9 @@ def run_dcov(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
         "data": "synthetic",
         "config": {"workload": WORKLOADS["dcov_sectors"], "n": n, "pairs": len(pairs), "precision": args.precision,
-                   "l2": "flushed (256 MiB write) before every timed step", "launch": "eager, one stream",
+                   "l2": "flushed (256 MiB write) before every timed step",
+                   "launch": "eager, one stream" if args.eager else
+                   "one CUDA graph per step: 11 distance-matrix builds and 220 evaluations",
                    "parallelism": "single"},
         "dcov2_per_s": len(pairs) * args.steps / (tot_ms / 1e3),
         "roofline": roof,
@@ -798,9 +814,9 @@ def run_hoif(args):
     n = 10000
     orders = list(range(2, 8))
     phi, A, Y = synth.hoif_sample(n, seed=0)
-    G, F = hoif.factor_matrices(phi, A, Y)
-    hc = hoif.HoifChains(n, orders=orders, precision=args.precision, device=dev)
-    hc.set(G, F)
+    TG, TF = hoif.factor_terms(phi, A, Y)
+    hc = hoif.HoifChains(n, k=phi.shape[1], orders=orders, precision=args.precision, device=dev)
+    hc.set(TG, TF)
     stream = torch.cuda.current_stream(dev)
     for _ in range(args.warmup):
         for j in orders:
@@ -852,9 +868,10 @@ def run_hoif(args):
                 "per_launch_ms": per * 1e3}
     fl = sum(hc.plans[j][0].flops(n)[0] for j in orders)
 
-    # end to end: G and F from pinned host memory, the six U-statistics, U back
-    Gh = torch.from_numpy(G).pin_memory()
-    Fh = torch.from_numpy(F).pin_memory()
+    # end to end: the factor terms from pinned host memory (the device builds G and
+    # F in every evaluation), the six U-statistics, U back
+    Gh = torch.from_numpy(TG).pin_memory()
+    Fh = torch.from_numpy(TF).pin_memory()
     Uh = torch.empty((len(orders), 2), dtype=torch.float64).pin_memory()
     ke = min(args.steps, 3)
     t1 = time.perf_counter()
@@ -870,7 +887,8 @@ def run_hoif(args):
     if not args.no_cpu_baseline:
         def oracle_all(ns):
             ph, a, y = synth.hoif_sample(ns, seed=0)
-            Gs, Fs = hoif.factor_matrices(ph, a, y)
+            Psi, Theta = a[:, None] * ph, ph * y[:, None]
+            Gs, Fs = Psi @ Psi.T, Psi @ Theta.T
             t = time.perf_counter()
             for j in orders:
                 fs = [synth.Factor(synth.MATRIX, 1.0, Fs)] if j == 2 else [
@@ -896,13 +914,14 @@ def run_hoif(args):
         "dtype": args.precision,
         "data": "synthetic",
         "config": {"workload": WORKLOADS["hoif_chain"], "n": n, "orders": orders, "precision": args.precision,
-                   "l2": "inputs (two n x n float64 matrices, 1.6 GB) and every product far larger than L2",
+                   "l2": "the factor matrices built on the device (two n x n float64, 1.6 GB) and every product "
+                         "far larger than L2",
                    "launch": "eager, one stream", "parallelism": "single"},
         "ms_per_order": per_order,
         "tflops": {"algorithmic_plan": fl * args.steps / (tot_ms / 1e3) / 1e12},
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": len(orders) / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": int(2 * n * n * 8),
+        "e2e": {"value": len(orders) / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": int(Gh.numel() * 8 * 2),
                 "d2h_bytes_per_step": 16 * len(orders)},
         "gpu_launches": int(sum(c for (_, c) in prof.values())),
         "clocks": clk,
@@ -1128,6 +1147,8 @@ def main():
                     help="skip the table of the other configurations (default workload only)")
     ap.add_argument("--variant", type=int, default=None,
                     help="tensor-core GEMM variant for every size class (ustat_plan_set_variant)")
+    ap.add_argument("--eager", action="store_true",
+                    help="dCov workload: launch every evaluation eagerly instead of replaying one CUDA graph")
     ap.add_argument("--capture", type=int, default=0,
                     help="only run this many evaluations (no timing, no JSON): for profiler captures")
     args = ap.parse_args()

@@ -54,6 +54,15 @@ extern "C" {
 #define USTAT_TANH_DOT  2  /* f(x) = tanh(x . w), w = data (device, d doubles); unary  */
 #define USTAT_MATRIX    3  /* F given as data: device n x n float64, row-major          */
 #define USTAT_VECTOR    4  /* f given as data: device n float64; unary                   */
+/* Pairwise factors built on the device from the caller's data (the paper's
+ * tensorization, Section 3.1, Algorithm 1, of its application kernels):        */
+#define USTAT_DIST      5  /* F(i,j) = ||y_i - y_j||, data = Y (device n x param float64,
+                              row-major): the distance matrices of dCov, Section 4.3  */
+#define USTAT_LOWRANK   6  /* F(i,j) = sum_k P(i,k) Q(j,k), data = [P | Q] (device n x
+                              2 param float64, row-major): the HOIF factors g and f of
+                              Section 4.1 from their n x param dictionary terms        */
+#define USTAT_COMPLEMENT 7 /* F = 1 - A, data = A (device n x n float64, row-major):
+                              the non-edge factor of the motif kernels, Section 4.2   */
 
 /* ---- precision modes of the contractions ---- */
 #define USTAT_FP64    0  /* all arithmetic in float64 (CUDA cores)                          */
@@ -247,6 +256,29 @@ int ustat_combine(const ustat_plan_t *plan, const double *scal, int64_t n, void 
 int ustat_status(const void *ws, void *stream, int *device_status);
 
 /*
+ * The n x n matrix of one device-built factor, for a caller that evaluates several
+ * U-statistics over the same factor (the distance matrices of Section 4.3's
+ * distance-covariance example enter four U-statistics each): build it once here
+ * and pass it to those evaluations as a USTAT_MATRIX factor.  Same definition and
+ * arithmetic as the factor inside ustat_eval (the tensorization step of
+ * Section 3.2: the factor tensor formed from the sample):
+ *   kind  : USTAT_DIST (F(i,j) = ||y_i - y_j||, float64 coordinate differences),
+ *           USTAT_LOWRANK (F(i,j) = sum_k P(i,k) Q(j,k), float64 products) or
+ *           USTAT_COMPLEMENT (F = 1 - A); param and data as in ustat_factor
+ *           (device float64, row-major)
+ *   F     : device float64 n x n, row-major, every entry written (the diagonal too)
+ *   ws    : device, at least 256 bytes, 256-byte aligned: its first word is reset
+ *           and then collects the device status (non-finite data: NONFINITE),
+ *           read by ustat_status(ws, stream, ...)
+ * Asynchronous on stream; the caller owns every buffer.  Errors: INVALID_ARG
+ * (another kind, a NULL pointer, ws not 256-byte aligned, n < 1, for DIST /
+ * LOWRANK a param that is not an integer in [1, 4096]), UNSUPPORTED (n > 2^20),
+ * CUDA.
+ */
+int ustat_factor_matrix(int kind, double param, const double *data, int64_t n, double *F, void *ws,
+                        void *stream);
+
+/*
  * Test hook of the bounded device waits, off by default; not for production use.
  * Every later tensor-core GEMM launched by this process gives up a wait after
  * limit_cycles SM cycles (0 restores the default of about 4e9 cycles, two
@@ -325,7 +357,9 @@ int ustat_batch_workspace_bytes(const ustat_plan_t *plan, const int64_t *n, int 
  * 1: direct differences on the CUDA cores), bit 4 the latter's tile (0: 128 x 128
  * with 256 threads; 1: 64 x 64 with 128 threads), bit 6 the treewidth-3 GEMMs of
  * BF16X4 (0: two double-buffered accumulator sets and a float32 epilogue; 1: the
- * four-accumulator layout of the float64-storage modes).  Results agree to the mode's
+ * four-accumulator layout of the float64-storage modes), bit 7 turns off the diagonal
+ * correction of the split-mode products (faster where diagonals do not dominate,
+ * less accurate where they do; the autotuner never sets it).  Results agree to the mode's
  * tolerance across variants (summation orders differ).  The autotuner below
  * sets these itself.
  */

@@ -42,7 +42,7 @@ import math
 import numpy as np
 
 # Factor kinds (plain integers; the same numbering is used by the input module).
-RBF, LINEAR, TANH_DOT, MATRIX, VECTOR = 0, 1, 2, 3, 4
+RBF, LINEAR, TANH_DOT, MATRIX, VECTOR, DIST, LOWRANK, COMPLEMENT = 0, 1, 2, 3, 4, 5, 6, 7
 
 
 # --------------------------------------------------------------------------------------
@@ -126,7 +126,13 @@ def factor_tensor(kind: int, X: np.ndarray, param: float = 1.0, data=None) -> np
     RBF:      T(i, j) = exp(-||x_i - x_j||^2 / param), computed from the differences.
     LINEAR:   T(i, j) = (x_i . x_j) / param.
     TANH_DOT: T(i)    = tanh(x_i . w), w = data.
-    MATRIX / VECTOR: the given data (float64)."""
+    MATRIX / VECTOR: the given data (float64).
+    DIST:     T(i, j) = ||y_i - y_j|| for the rows of Y = data (the distance
+              matrices of dCov, Section 4.3).
+    LOWRANK:  T(i, j) = sum_k P(i, k) Q(j, k), data = [P | Q] with param = the
+              number of columns of P (the HOIF factors, Section 4.1).
+    COMPLEMENT: T = 1 - A, A = data (the motif kernels' non-edge factor,
+              Section 4.2)."""
     X = np.asarray(X, dtype=np.float64)
     if kind == RBF:
         diff = X[:, None, :] - X[None, :, :]
@@ -137,6 +143,17 @@ def factor_tensor(kind: int, X: np.ndarray, param: float = 1.0, data=None) -> np
         return np.tanh(X @ np.asarray(data, dtype=np.float64))
     if kind in (MATRIX, VECTOR):
         return np.asarray(data, dtype=np.float64)
+    if kind == DIST:
+        Y = np.asarray(data, dtype=np.float64)
+        Y = Y.reshape(Y.shape[0], -1)
+        diff = Y[:, None, :] - Y[None, :, :]
+        return np.sqrt(np.einsum("ijk,ijk->ij", diff, diff))
+    if kind == LOWRANK:
+        D = np.asarray(data, dtype=np.float64)
+        r = int(param)
+        return D[:, :r] @ D[:, r:2 * r].T
+    if kind == COMPLEMENT:
+        return 1.0 - np.asarray(data, dtype=np.float64)
     raise ValueError(kind)
 
 

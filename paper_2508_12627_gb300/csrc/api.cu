@@ -262,11 +262,12 @@ struct DiagFix {
     std::vector<char> removed;   // per slot: split with its diagonal left out
 };
 
-DiagFix diag_fix_of(const Plan &P) {
+DiagFix diag_fix_of(const Plan &P, int64_t n) {
     DiagFix D;
     D.split_op.assign(P.slots.size(), -1);
     D.removed.assign(P.slots.size(), 0);
-    if (!is_split_mode(P.precision)) return D;
+    // plan variant bit 7 turns the correction off for this size class
+    if (!is_split_mode(P.precision) || ((P.tc_variant[tc_size_class(n)] >> 7) & 1)) return D;
     for (size_t i = 0; i < P.ops.size(); ++i)
         if (P.ops[i].kind == OP_SPLIT && P.ops[i].out >= 0) D.split_op[P.ops[i].out] = (int)i;
     std::vector<char> ok(P.slots.size(), 1);
@@ -292,7 +293,14 @@ int check_graph_factors(const Plan &P, const ustat_factor *f, int nf, int d) {
         if (f[i].kind != P.factor_kind[i]) return USTAT_ERR_INVALID_ARG;
         int k = f[i].kind;
         if ((k == USTAT_RBF || k == USTAT_LINEAR) && !(f[i].param > 0.0)) return USTAT_ERR_INVALID_ARG;
-        if ((k == USTAT_TANH_DOT || k == USTAT_MATRIX || k == USTAT_VECTOR) && !f[i].data) return USTAT_ERR_INVALID_ARG;
+        if ((k == USTAT_TANH_DOT || k == USTAT_MATRIX || k == USTAT_VECTOR || k == USTAT_DIST || k == USTAT_LOWRANK ||
+             k == USTAT_COMPLEMENT) &&
+            !f[i].data)
+            return USTAT_ERR_INVALID_ARG;
+        // DIST and LOWRANK: param is the data's column count (a positive integer)
+        if ((k == USTAT_DIST || k == USTAT_LOWRANK) &&
+            !(f[i].param >= 1.0 && f[i].param <= 4096.0 && f[i].param == (double)(int)f[i].param))
+            return USTAT_ERR_INVALID_ARG;
     }
     (void)d;
     return USTAT_OK;
@@ -354,7 +362,7 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
         if (e != cudaSuccess) return cuda_fail(e);
     }
     const int lead = split_lead_bits(n);
-    const DiagFix D = diag_fix_of(P);
+    const DiagFix D = diag_fix_of(P, n);
     for (const Op &op : P.ops) {
         ProfScope ps(op.kind, C.st);
         switch (op.kind) {
@@ -398,7 +406,12 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                 }
                 break;
             case OP_LOADMAT:
-                e = launch_loadmat((const double *)f[op.factor].data, n, C.fp64, P.sparsify, C.ptr(op.out), err, C.st);
+                if (f[op.factor].kind == USTAT_DIST || f[op.factor].kind == USTAT_LOWRANK)
+                    e = launch_pairs(f[op.factor].kind, (const double *)f[op.factor].data, (int)f[op.factor].param, n,
+                                     C.fp64, P.sparsify, C.ptr(op.out), err, C.st);
+                else
+                    e = launch_loadmat((const double *)f[op.factor].data, n, C.fp64, P.sparsify,
+                                       f[op.factor].kind == USTAT_COMPLEMENT, C.ptr(op.out), err, C.st);
                 break;
             case OP_UNARY:
                 e = launch_unary_tanh(X, x_dtype, n, C.d, (const double *)f[op.factor].data, C.vec(op.out), err, C.st);
@@ -518,8 +531,10 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                         g.dB = D.removed[op.opB] ? C.diagv(op.opB) : nullptr;
                         g.MA = C.ptr(sa.t[0].mat);
                         g.MB = C.ptr(sb.t[0].mat);
-                        g.rowA = trA || symA;
-                        g.rowB = !trB || symB;
+                        // a symmetric source is read as M[k][j]: consecutive lanes (rows j)
+                        // then read consecutive addresses
+                        g.rowA = trA && !symA;
+                        g.rowB = !trB && !symB;
                         g.uA = C.vec(sa.u);
                         g.uB = C.vec(sb.u);
                     }
@@ -1024,7 +1039,7 @@ int ustat_plan_deserialize(const void *buf, size_t len, ustat_plan_t **out) {
         valid = pr.nscal >= 0 && pr.nscal <= kMaxScal;
         for (int q = 0; valid && q < pr.nscal; ++q) valid = pr.scal[q] >= 0 && pr.scal[q] < nslots;
     }
-    for (int k : P.factor_kind) valid = valid && k >= USTAT_RBF && k <= USTAT_VECTOR;
+    for (int k : P.factor_kind) valid = valid && k >= USTAT_RBF && k <= USTAT_COMPLEMENT;
     if (!valid) {
         delete p;
         return USTAT_ERR_INVALID_ARG;
@@ -1074,6 +1089,22 @@ int ustat_status(const void *ws, void *stream, int *device_status) {
     if (e != cudaSuccess) return cuda_fail(e);
     *device_status = status_of_word(word);
     return USTAT_OK;
+}
+
+int ustat_factor_matrix(int kind, double param, const double *data, int64_t n, double *F, void *ws,
+                        void *stream) {
+    if (!data || !F || !ws || n < 1 || ((uintptr_t)ws & 255)) return USTAT_ERR_INVALID_ARG;
+    if (n > (int64_t)1 << 20) return USTAT_ERR_UNSUPPORTED;
+    const bool pairs = kind == USTAT_DIST || kind == USTAT_LOWRANK;
+    if (!pairs && kind != USTAT_COMPLEMENT) return USTAT_ERR_INVALID_ARG;
+    if (pairs && !(param >= 1.0 && param <= 4096.0 && param == (double)(int)param)) return USTAT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int *err = (int *)ws;   // the error word, at offset 0 as in every evaluation workspace
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e == cudaSuccess)
+        e = pairs ? launch_pairs(kind, data, (int)param, n, true, 0, F, err, st)
+                  : launch_loadmat(data, n, true, 0, 1, F, err, st);
+    return e == cudaSuccess ? USTAT_OK : cuda_fail(e);
 }
 
 int ustat_workspace_bytes(const ustat_plan_t *plan, int64_t n, int d, size_t *bytes) {
@@ -1470,7 +1501,9 @@ int batched_check(ustat_batched *b, const void *const *X, int x_dtype, const ust
     int rc = check_graph_factors(P, f, nf, b->d);
     if (rc != USTAT_OK) return rc;
     for (int i = 0; i < nf; ++i)
-        if (f[i].kind == USTAT_MATRIX || f[i].kind == USTAT_VECTOR) return USTAT_ERR_UNSUPPORTED;
+        if (f[i].kind == USTAT_MATRIX || f[i].kind == USTAT_VECTOR || f[i].kind == USTAT_DIST ||
+            f[i].kind == USTAT_LOWRANK || f[i].kind == USTAT_COMPLEMENT)
+            return USTAT_ERR_UNSUPPORTED;   // data of one size, not per sample
     for (size_t i = 0; i < b->n.size(); ++i)
         if (!X[i]) return USTAT_ERR_INVALID_ARG;
     if (!ws || ((uintptr_t)ws % 256) != 0 || ws_bytes < (size_t)b->max_lanes * b->lane_bytes)
@@ -1483,7 +1516,7 @@ int batched_check(ustat_batched *b, const void *const *X, int x_dtype, const ust
 extern "C" {
 
 int ustat_plan_set_variant(ustat_plan_t *plan, int size_class, int variant) {
-    if (!plan || size_class < -1 || size_class > 3 || variant < 0 || variant > 127 || ((variant >> 2) & 3) == 3)
+    if (!plan || size_class < -1 || size_class > 3 || variant < 0 || variant > 255 || ((variant >> 2) & 3) == 3)
         return USTAT_ERR_INVALID_ARG;
     for (int c = 0; c < 4; ++c)
         if (size_class < 0 || c == size_class) plan->p.tc_variant[c] = variant;

@@ -820,15 +820,17 @@ __global__ void __launch_bounds__(256) kbuild_kernel(int kind, T inv_param, cons
     }
 }
 
+// A caller matrix as the storage type; with `complement`, the factor 1 - A (the
+// motif kernels' non-edge factor B = 1 - A, Section 4.2).
 template <typename T>
-__global__ void loadmat_kernel(const double *src, int64_t n, int zero_diag, T *dst, int *err) {
+__global__ void loadmat_kernel(const double *src, int64_t n, int zero_diag, int complement, T *dst, int *err) {
     const int64_t total = n * n;
     bool bad = false;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
         const double x = src[t];
         bad |= !isfinite(x);
-        T v = (T)x;
+        T v = (T)(complement ? 1.0 - x : x);
         if (zero_diag && (t / n) == (t % n)) v = 0;
         dst[t] = v;
     }
@@ -865,13 +867,70 @@ __global__ void diag_kernel(const T *M, int64_t n, double *out) {
         out[i] = (double)M[i * n + i];
 }
 
+// Pairwise factors built from caller data on 32 x 32 tiles (32 x 8 threads, four
+// entries per thread), float64 arithmetic, rows of both operands staged in shared
+// memory in chunks of 64 coordinates:
+//   PAIRS_LOWRANK: F(i, j) = sum_k P(i, k) Q(j, k), data = [P | Q] (n x 2r): the
+//     HOIF factors g = Psi Psi' and f = Psi Theta' of Section 4.1 from the n x r
+//     dictionary terms;
+//   PAIRS_DIST: F(i, j) = ||y_i - y_j|| from the coordinate differences, data = Y
+//     (n x r): the distance matrices of dCov (Section 4.3), diagonal exactly 0.
+enum { PAIRS_LOWRANK = 0, PAIRS_DIST = 1 };
+template <typename T>
+__global__ void __launch_bounds__(256) pairs_kernel(int mode, const double *__restrict__ D, int r, int64_t n,
+                                                    int zero_diag, T *__restrict__ dst, int *err) {
+    __shared__ double as[32][65], bs[32][65];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
+    const int ld = mode == PAIRS_LOWRANK ? 2 * r : r;
+    const int boff = mode == PAIRS_LOWRANK ? r : 0;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    bool bad = false;
+    for (int k0 = 0; k0 < r; k0 += 64) {
+        const int kc = min(64, r - k0);
+        __syncthreads();
+        for (int e = ty * 32 + tx; e < 32 * kc; e += 256) {
+            const int row = e / kc, k = e - row * kc;
+            const double av = i0 + row < n ? D[(i0 + row) * ld + k0 + k] : 0.0;
+            const double bv = j0 + row < n ? D[(j0 + row) * ld + boff + k0 + k] : 0.0;
+            bad |= !isfinite(av) || !isfinite(bv);
+            as[row][k] = av;
+            bs[row][k] = bv;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int rr = ty + 8 * q;
+            double a = acc[q];
+            if (mode == PAIRS_LOWRANK) {
+                for (int k = 0; k < kc; ++k) a = fma(as[rr][k], bs[tx][k], a);
+            } else {
+                for (int k = 0; k < kc; ++k) {
+                    const double df = as[rr][k] - bs[tx][k];
+                    a = fma(df, df, a);
+                }
+            }
+            acc[q] = a;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t i = i0 + ty + 8 * q, j = j0 + tx;
+        if (i >= n || j >= n) continue;
+        double v = mode == PAIRS_DIST ? sqrt(acc[q]) : acc[q];
+        if (i == j && (zero_diag || mode == PAIRS_DIST)) v = 0.0;
+        dst[i * n + j] = (T)v;
+    }
+    flag_nonfinite(bad, err);
+}
+
 // Diagonal of a factor from its own data, in float64: x_i . x_i / param for the
 // linear kernel (X as given, float64 or float32), M[i][i] for a caller matrix;
 // 0 in the sparsified mode.  The stored working-precision matrix would round
 // every entry to float32 first, and a partition whose blocks merge all indices
 // multiplies several diagonal entries per term.
 __global__ void factor_diag_kernel(int kind, double inv_param, const void *X, int x_dtype, int d,
-                                   const double *Mc, int64_t n, int zero_diag, double *out) {
+                                   const double *Mc, int64_t n, int zero_diag, double *out, int r) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double v = 0.0;
         if (!zero_diag) {
@@ -883,6 +942,12 @@ __global__ void factor_diag_kernel(int kind, double inv_param, const void *X, in
                 v *= inv_param;
             } else if (kind == USTAT_RBF) {
                 v = 1.0;
+            } else if (kind == USTAT_LOWRANK) {
+                for (int k = 0; k < r; ++k) v = fma(Mc[i * 2 * r + k], Mc[i * 2 * r + r + k], v);
+            } else if (kind == USTAT_DIST) {
+                v = 0.0;
+            } else if (kind == USTAT_COMPLEMENT) {
+                v = 1.0 - Mc[i * n + i];
             } else {
                 v = Mc[i * n + i];
             }
@@ -1055,10 +1120,22 @@ cudaError_t launch_kbuild_rbf(const float *Xw, const double *Xd, int64_t n, int 
     return cudaGetLastError();
 }
 
-cudaError_t launch_loadmat(const double *src, int64_t n, bool fp64, int zero_diag, void *dst, int *err,
-                           cudaStream_t s) {
-    if (fp64) loadmat_kernel<double><<<grid_for(n * n, 256), 256, 0, s>>>(src, n, zero_diag, (double *)dst, err);
-    else loadmat_kernel<float><<<grid_for(n * n, 256), 256, 0, s>>>(src, n, zero_diag, (float *)dst, err);
+cudaError_t launch_loadmat(const double *src, int64_t n, bool fp64, int zero_diag, int complement, void *dst,
+                           int *err, cudaStream_t s) {
+    if (fp64)
+        loadmat_kernel<double><<<grid_for(n * n, 256), 256, 0, s>>>(src, n, zero_diag, complement, (double *)dst, err);
+    else
+        loadmat_kernel<float><<<grid_for(n * n, 256), 256, 0, s>>>(src, n, zero_diag, complement, (float *)dst, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pairs(int kind, const double *data, int r, int64_t n, bool fp64, int zero_diag, void *dst,
+                         int *err, cudaStream_t s) {
+    if (r < 1 || (kind != USTAT_LOWRANK && kind != USTAT_DIST)) return cudaErrorInvalidValue;
+    const int mode = kind == USTAT_LOWRANK ? PAIRS_LOWRANK : PAIRS_DIST;
+    dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32)), block(32, 8);
+    if (fp64) pairs_kernel<double><<<grid, block, 0, s>>>(mode, data, r, n, zero_diag, (double *)dst, err);
+    else pairs_kernel<float><<<grid, block, 0, s>>>(mode, data, r, n, zero_diag, (float *)dst, err);
     return cudaGetLastError();
 }
 
@@ -1081,7 +1158,8 @@ cudaError_t launch_diag(const void *M, bool fp64, int64_t n, double *out, cudaSt
 
 cudaError_t launch_factor_diag(int kind, double param, const void *X, int x_dtype, int d, const double *Mc,
                                int64_t n, int zero_diag, double *out, cudaStream_t s) {
-    factor_diag_kernel<<<grid_for(n, 256), 256, 0, s>>>(kind, 1.0 / param, X, x_dtype, d, Mc, n, zero_diag, out);
+    factor_diag_kernel<<<grid_for(n, 256), 256, 0, s>>>(kind, 1.0 / param, X, x_dtype, d, Mc, n, zero_diag, out,
+                                                         (int)param);
     return cudaGetLastError();
 }
 

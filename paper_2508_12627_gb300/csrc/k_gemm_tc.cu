@@ -693,12 +693,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const double *MA = (const double *)g.MA, *MB = (const double *)g.MB;
                         const double dAj = g.dA ? g.dA[j] : 0.0;
 #pragma unroll
+                        const double uBj = g.uB ? g.uB[j] : 1.0;
                         for (int c = 0; c < 16; ++c) {
                             const int64_t k = k0 + c;
                             if (k >= n) continue;
                             double corr = 0.0;
                             const double dBk = g.dB ? g.dB[k] : 0.0;
-                            if (dAj != 0.0) corr += dAj * (g.rowB ? MB[j * n + k] : MB[k * n + j]) * (g.uB ? g.uB[j] : 1.0);
+                            if (dAj != 0.0) corr += dAj * (g.rowB ? MB[j * n + k] : MB[k * n + j]) * uBj;
                             if (dBk != 0.0) corr += (g.rowA ? MA[j * n + k] : MA[k * n + j]) * (g.uA ? g.uA[k] : 1.0) * dBk;
                             if (k == j) corr -= dAj * dBk;
                             v[c] += corr;

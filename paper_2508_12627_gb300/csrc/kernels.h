@@ -39,8 +39,12 @@ cudaError_t launch_kbuild_rbf_tc(const void *X, int x_dtype, int64_t n, int d, d
 // double-float dot product, unrounded.
 cudaError_t launch_kbuild_linear_wide(const float *X, int64_t n, int d, double param, int zero_diag, double *K,
                                       cudaStream_t s);
-cudaError_t launch_loadmat(const double *src, int64_t n, bool fp64, int zero_diag, void *dst, int *err,
-                           cudaStream_t s);
+cudaError_t launch_loadmat(const double *src, int64_t n, bool fp64, int zero_diag, int complement, void *dst,
+                           int *err, cudaStream_t s);
+// LOWRANK (data = [P | Q], n x 2r: F = P Q') or DIST (data = Y, n x r: F(i, j) =
+// ||y_i - y_j||) factor matrices in float64 arithmetic, stored in the mode's type.
+cudaError_t launch_pairs(int kind, const double *data, int r, int64_t n, bool fp64, int zero_diag, void *dst,
+                         int *err, cudaStream_t s);
 cudaError_t launch_unary_tanh(const void *X, int x_dtype, int64_t n, int d, const double *w,
                               double *out, int *err, cudaStream_t s);
 cudaError_t launch_copyvec(const double *src, int64_t n, double *dst, int *err, cudaStream_t s);

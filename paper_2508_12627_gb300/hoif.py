@@ -8,10 +8,11 @@ dictionary phi, the estimator's terms are U-statistics of the chain kernels
     g(X_a, X_b) = A_a phi(Z_a)' A_b phi(Z_b),   f(X_a, X_b) = A_a phi(Z_a)' phi(Z_b) Y_b,
 
 a chain of j - 1 pairwise factors (signature ((1, 2), ..., (j - 1, j))).  The
-factor matrices G = Psi Psi' (symmetric) and F = Psi Theta' (not symmetric),
-with Psi_i = A_i phi(Z_i) and Theta_i = phi(Z_i) Y_i, are formed on the host
-(n x k by k x n products) and enter the engine as MATRIX factors; every U_sum is
-then one exact evaluation (all Bell(j) restricted V-statistics and the Moebius
+factors G = Psi Psi' (symmetric) and F = Psi Theta' (not symmetric), with
+Psi_i = A_i phi(Z_i) and Theta_i = phi(Z_i) Y_i, enter the engine as LOWRANK
+factors: only the n x k terms Psi and Theta are uploaded, and the library builds
+the n x n matrices on the device (the tensorization step); every U_sum is then
+one exact evaluation (all Bell(j) restricted V-statistics and the Moebius
 combination) on the device.
 """
 from __future__ import annotations
@@ -39,35 +40,49 @@ def chain_graph(j):
     return _Graph(j, [(v, v + 1, 0) for v in range(j - 2)] + [(j - 2, j - 1, 1)]), ["g", "f"]
 
 
-def factor_matrices(phi, A, Y):
-    """G = Psi Psi' and F = Psi Theta' (float64, n x n)."""
+def factor_terms(phi, A, Y):
+    """The data of the two LOWRANK factors (float64, n x 2k): [Psi | Psi] for
+    g = Psi Psi' and [Psi | Theta] for f = Psi Theta'."""
     phi = np.asarray(phi, dtype=np.float64)
     Psi = np.asarray(A, dtype=np.float64)[:, None] * phi
     Theta = phi * np.asarray(Y, dtype=np.float64)[:, None]
-    return Psi @ Psi.T, Psi @ Theta.T
+    return np.ascontiguousarray(np.hstack([Psi, Psi])), np.ascontiguousarray(np.hstack([Psi, Theta]))
+
+
+def factor_matrices(phi, A, Y):
+    """G = Psi Psi' and F = Psi Theta' (float64, n x n), formed on the host: for
+    callers that hold the matrices themselves (the engine builds them from
+    factor_terms)."""
+    TG, TF = factor_terms(phi, A, Y)
+    k = TG.shape[1] // 2
+    return TG[:, :k] @ TG[:, k:].T, TF[:, :k] @ TF[:, k:].T
 
 
 class HoifChains:
-    """Device copies of G and F, one plan per chain length, one workspace."""
+    """Device copies of the n x 2k factor terms, one plan per chain length, one
+    workspace; the library builds G and F on the device in every evaluation."""
 
-    def __init__(self, n, orders=(2, 3, 4, 5, 6, 7), precision="bf16x4", device="cuda:0"):
+    def __init__(self, n, k=16, orders=(2, 3, 4, 5, 6, 7), precision="bf16x4", device="cuda:0"):
         self.n = n
+        self.k = k
         self.device = torch.device(device)
         self.orders = list(orders)
         self.plans = {}
         for j in self.orders:
             g, names = chain_graph(j)
-            self.plans[j] = (us.Plan(g, [us.MATRIX] * len(names), precision=precision), names)
+            self.plans[j] = (us.Plan(g, [us.LOWRANK] * len(names), precision=precision), names)
         need = max(256, max(p.workspace_bytes(n, 1) for p, _ in self.plans.values()))
         self.ws = torch.empty(need, dtype=torch.uint8, device=self.device)
-        self.G = torch.empty((n, n), dtype=torch.float64, device=self.device)
-        self.F = torch.empty_like(self.G)
+        self.TG = torch.empty((n, 2 * k), dtype=torch.float64, device=self.device)
+        self.TF = torch.empty_like(self.TG)
         self.X = torch.zeros((n, 1), dtype=torch.float64, device=self.device)
         self.out = {j: torch.empty(2 + p.info["n_parts"], dtype=torch.float64, device=self.device)
                     for j, (p, _) in self.plans.items()}
 
-    def set(self, G, F, non_blocking=False):
-        for dst, src in ((self.G, G), (self.F, F)):
+    def set(self, TG, TF, non_blocking=False):
+        """The factor terms [Psi | Psi] and [Psi | Theta] (numpy or host / device
+        tensors, n x 2k float64)."""
+        for dst, src in ((self.TG, TG), (self.TF, TF)):
             if not isinstance(src, torch.Tensor):
                 src = torch.from_numpy(np.ascontiguousarray(src, dtype=np.float64))
             dst.copy_(src, non_blocking=non_blocking)
@@ -76,14 +91,14 @@ class HoifChains:
         """Enqueue U(h_j): out[j] = U_sum, U_mean, V_pi."""
         p, names = self.plans[j]
         st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
-        facs = [(us.MATRIX, 1.0, (self.G if s == "g" else self.F).data_ptr()) for s in names]
+        facs = [(us.LOWRANK, float(self.k), (self.TG if s == "g" else self.TF).data_ptr()) for s in names]
         o = self.out[j]
         us.ustat_eval(p, self.X.data_ptr(), 0, self.n, 1, facs, self.ws.data_ptr(), self.ws.numel(), st,
                       o.data_ptr(), o.data_ptr() + 16)
 
     def evaluate(self, phi, A, Y):
         """U_sum of every chain order: {j: U_sum}."""
-        self.set(*factor_matrices(phi, A, Y))
+        self.set(*factor_terms(phi, A, Y))
         for j in self.orders:
             self.launch(j)
         return {j: float(self.out[j][0].item()) for j in self.orders}

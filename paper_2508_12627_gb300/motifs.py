@@ -12,9 +12,10 @@ B = 1 - A on every other pair of the k vertices, divided by |Aut(r)|:
 For 0 / 1 matrices every product entry, contraction and reduction of the
 split-BF16 path is an integer held exactly (digits of 0 and 1 are exact, the
 tensor-core accumulators sum at most n < 2^24 unit products, the reductions are
-float64), so the counts are exact integers below 2^53.  A and B are uploaded
-once (B computed on the host); the sample argument of ustat_eval is a dummy
-n x 1 column, which matrix factors do not read.
+float64), so the counts are exact integers below 2^53.  A is uploaded once; B
+enters as a COMPLEMENT factor of A, which the library forms on the device; the
+sample argument of ustat_eval is a dummy n x 1 column, which these factors do
+not read.  A caller-given B (other than 1 - A) is uploaded as a MATRIX factor.
 """
 from __future__ import annotations
 
@@ -56,8 +57,8 @@ def automorphisms(k, edges):
 
 
 class MotifCounter:
-    """Device copies of A and B = 1 - A, one plan per motif (cached), one shared
-    workspace."""
+    """The device copy of A (and of B only when the caller gives one), one plan per
+    motif (cached), one shared workspace."""
 
     def __init__(self, A, precision="bf16x3", device="cuda:0"):
         self.device = torch.device(device)
@@ -67,27 +68,31 @@ class MotifCounter:
             raise ValueError("A must be n x n")
         self.precision = precision
         self.A = torch.empty((self.n, self.n), dtype=torch.float64, device=self.device)
-        self.B = torch.empty_like(self.A)
+        self.B = None   # a caller-given B; None: B = 1 - A, formed on the device
         self.X = torch.zeros((self.n, 1), dtype=torch.float64, device=self.device)
         self.plans = {}
         self.ws = None
         self.set_graph(A)
 
     def set_graph(self, A, B=None, non_blocking=False):
-        """New adjacency matrix (numpy or a pinned host tensor); B = 1 - A unless given."""
-        if isinstance(A, torch.Tensor):
-            self.A.copy_(A, non_blocking=non_blocking)
-            self.B.copy_(B if B is not None else 1.0 - A, non_blocking=non_blocking)
+        """New adjacency matrix (numpy or a pinned host tensor); B = 1 - A (formed
+        on the device) unless given."""
+        src = A if isinstance(A, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(A, dtype=np.float64))
+        self.A.copy_(src, non_blocking=non_blocking)
+        if B is None:
+            self.B = None
         else:
-            self.A.copy_(torch.from_numpy(np.ascontiguousarray(A, dtype=np.float64)))
-            Bh = 1.0 - np.asarray(A, dtype=np.float64) if B is None else B
-            self.B.copy_(torch.from_numpy(np.ascontiguousarray(Bh, dtype=np.float64)))
+            if self.B is None:
+                self.B = torch.empty_like(self.A)
+            srcb = B if isinstance(B, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(B, dtype=np.float64))
+            self.B.copy_(srcb, non_blocking=non_blocking)
 
     def plan(self, k, edges):
-        key = (k, tuple(sorted(tuple(sorted(e)) for e in edges)))
+        key = (k, tuple(sorted(tuple(sorted(e)) for e in edges)), self.B is not None)
         if key not in self.plans:
             g, names = kernel_graph(k, edges)
-            p = us.Plan(g, [us.MATRIX] * len(names), precision=self.precision)
+            kinds = [us.MATRIX if s == "A" or self.B is not None else us.COMPLEMENT for s in names]
+            p = us.Plan(g, kinds, precision=self.precision)
             need = max(256, p.workspace_bytes(self.n, 1))
             if self.ws is None or self.ws.numel() < need:
                 self.ws = torch.empty(need, dtype=torch.uint8, device=self.device)
@@ -98,7 +103,9 @@ class MotifCounter:
         """Enqueue one count; ``out`` is a float64 device tensor of 2 + Bell(k):
         U_sum, U_mean and the V_pi.  Returns |Aut(r)|."""
         p, names, aut = self.plan(k, edges)
-        facs = [(us.MATRIX, 1.0, (self.A if s == "A" else self.B).data_ptr()) for s in names]
+        facs = [(us.MATRIX, 1.0, self.A.data_ptr()) if s == "A" else
+                ((us.MATRIX, 1.0, self.B.data_ptr()) if self.B is not None else (us.COMPLEMENT, 1.0, self.A.data_ptr()))
+                for s in names]
         st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
         us.ustat_eval(p, self.X.data_ptr(), 0, self.n, 1, facs, self.ws.data_ptr(), self.ws.numel(), st,
                       out.data_ptr(), out.data_ptr() + 16)

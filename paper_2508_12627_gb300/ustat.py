@@ -24,7 +24,7 @@ USTAT_ERR_CUDA = -6
 USTAT_ERR_DEVICE_TIMEOUT = -7
 USTAT_ERR_UNSUPPORTED = -8
 
-RBF, LINEAR, TANH_DOT, MATRIX, VECTOR = 0, 1, 2, 3, 4
+RBF, LINEAR, TANH_DOT, MATRIX, VECTOR, DIST, LOWRANK, COMPLEMENT = 0, 1, 2, 3, 4, 5, 6, 7
 FP64, FP32, TF32, BF16X3, BF16X4, BF16X5 = 0, 1, 2, 3, 4, 5
 PLAN_EXHAUSTIVE, PLAN_MINFILL = 0, 1
 MAX_PARTS = 877   # Bell(7): partitions of the largest supported order m = 7
@@ -64,6 +64,7 @@ EXPORTS = {
     "ustat_plan_describe": (_i, [_vp, ctypes.c_char_p, _sz, _P(_sz)]),
     "ustat_workspace_bytes": (_i, [_vp, _i64, _i, _P(_sz)]),
     "ustat_status": (_i, [_vp, _vp, _P(_i)]),
+    "ustat_factor_matrix": (_i, [_i, _d, _vp, _i64, _vp, _vp, _vp]),
     "ustat_debug_set_wait": (_i, [ctypes.c_longlong, _i]),
     "ustat_scalar_count": (_i, [_vp, _P(_i)]),
     "ustat_eval_rows": (_i, [_vp, _i, _i, _vp, _i, _i64, _i, _P(ustat_factor), _i, _vp, _sz, _vp, _vp]),
@@ -393,6 +394,14 @@ def status(ws_ptr, stream):
     st = _i()
     _check(lib().ustat_status(ws_ptr, stream, ctypes.byref(st)), "ustat_status")
     return st.value
+
+
+def factor_matrix(kind, param, data_ptr, n, F_ptr, ws_ptr, stream):
+    """ustat_factor_matrix: the n x n float64 matrix of a DIST, LOWRANK or
+    COMPLEMENT factor (device pointers), built on the stream into F_ptr; the
+    status word in ws_ptr (>= 256 bytes) is read by status()."""
+    _check(lib().ustat_factor_matrix(int(kind), float(param), data_ptr, int(n), F_ptr, ws_ptr, stream),
+           "ustat_factor_matrix")
 
 
 def noalloc_status(stream):

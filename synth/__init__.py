@@ -26,6 +26,9 @@ LINEAR = 1     # (x . y) / h
 TANH_DOT = 2   # tanh(x . w), unary
 MATRIX = 3     # caller-supplied n x n matrix
 VECTOR = 4     # caller-supplied length-n vector
+DIST = 5       # ||y_i - y_j|| between the rows of a caller-supplied n x p matrix Y
+LOWRANK = 6    # sum_k P(i, k) Q(j, k) from caller-supplied n x r matrices, data = [P | Q]
+COMPLEMENT = 7  # 1 - A for a caller-supplied n x n matrix A
 
 
 @dataclass

@@ -158,6 +158,17 @@ def test_status_rejects_a_missing_workspace(us):
     assert e.value.code == us.USTAT_ERR_INVALID_ARG
 
 
+def test_factor_matrix_argument_checks(us):
+    # rejected on the host before any CUDA call: a kind the call does not build,
+    # a non-integer or out-of-range column count, a NULL or unaligned workspace
+    for kind, param, ws in [(us.RBF, 1.0, 256), (us.MATRIX, 1.0, 256), (us.DIST, 2.5, 256),
+                            (us.LOWRANK, 0.0, 256), (us.DIST, 5000.0, 256), (us.DIST, 3.0, 0),
+                            (us.COMPLEMENT, 1.0, 128)]:
+        with pytest.raises(us.UstatError) as e:
+            us.factor_matrix(kind, param, 4096, 10, 8192, ws, 0)
+        assert e.value.code == us.USTAT_ERR_INVALID_ARG, (kind, param, ws)
+
+
 def test_workspace_bytes_scale(us):
     p = _plan(us, synth.cycle4_graph(), [uo.RBF], precision="bf16x3")
     a, b = p.workspace_bytes(1000, 32), p.workspace_bytes(2000, 32)

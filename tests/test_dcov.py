@@ -114,6 +114,46 @@ def test_dcov_at_n_138_against_oracle_and_closed_form(precision, tol):
         assert abs(val - u_centred(a, b)) <= tol * scale, (precision, i, j, val, u_centred(a, b), scale)
 
 
+@pytest.mark.gpu
+def test_dcov_graph_replay_matches_eager():
+    # the distance matrices of three samples and the evaluations of two pairs,
+    # captured into one CUDA graph: a replay on new sample contents gives what the
+    # eager launches give on them
+    import torch
+    from paper_2508_12627_gb300 import build
+    build.build()
+    from paper_2508_12627_gb300 import dcov
+    R = synth.sector_returns()
+    n = R[0].shape[0]
+    dc = dcov.DCov2(n)
+    Z = [torch.from_numpy(np.ascontiguousarray(R[i], dtype=np.float64)).cuda() for i in (0, 4, 9)]
+    D = [torch.empty((n, n), dtype=torch.float64, device="cuda") for _ in Z]
+    outs = [[torch.empty_like(o) for o in dc.out] for _ in range(2)]
+
+    def enqueue():
+        for z, d in zip(Z, D):
+            dc.distance(z, d)
+        dc.launch_matrices(D[0], D[1], outs[0])
+        dc.launch_matrices(D[2], D[0], outs[1])
+
+    graph = dc.capture(enqueue)
+    for z, i in zip(Z, (2, 6, 8)):
+        z.copy_(torch.from_numpy(np.ascontiguousarray(R[i], dtype=np.float64)))
+    graph.replay()
+    torch.cuda.synchronize()
+    got = [[float(x[0].item()) for x in o] for o in outs]
+    enqueue()
+    torch.cuda.synchronize()
+    want = [[float(x[0].item()) for x in o] for o in outs]
+    for g, w in zip(got, want):
+        assert g == pytest.approx(w, rel=1e-13, abs=0.0)
+    # and the replayed values are those of the new samples
+    a, b = _dist(R[2]), _dist(R[6])
+    ref_terms, _ = oracle_terms(a, b)
+    for g, r in zip(got[0], ref_terms):
+        assert abs(g - r) <= 1e-12 * abs(r)
+
+
 def test_planted_coefficient_mistakes_fail_the_pins():
     pytest.importorskip("torch")
     rng = np.random.default_rng(9)

@@ -23,11 +23,23 @@ def _factors(j, G, F):
     return [synth.Factor(M, 1.0, F)] if j == 2 else [synth.Factor(M, 1.0, G), synth.Factor(M, 1.0, F)]
 
 
+def _gf(phi, A, Y):
+    """g and f of the paper's HOIF kernel as matrices, from their definitions."""
+    Psi, Theta = A[:, None] * phi, phi * Y[:, None]
+    return Psi @ Psi.T, Psi @ Theta.T
+
+
 def test_factor_matrices_follow_the_definitions():
     pytest.importorskip("torch")
     from paper_2508_12627_gb300 import hoif
     phi, A, Y = synth.hoif_sample(40, k=5, seed=3)
     G, F = hoif.factor_matrices(phi, A, Y)
+    # the device factors' data: [Psi | Psi] and [Psi | Theta], whose low-rank
+    # products (the oracle's LOWRANK definition) are g and f
+    TG, TF = hoif.factor_terms(phi, A, Y)
+    assert TG.shape == (40, 10) and TF.shape == (40, 10)
+    assert np.allclose(uo.factor_tensor(uo.LOWRANK, np.zeros((40, 1)), 5, TG), G, rtol=1e-13, atol=1e-13)
+    assert np.allclose(uo.factor_tensor(uo.LOWRANK, np.zeros((40, 1)), 5, TF), F, rtol=1e-13, atol=1e-13)
     for a, b in [(0, 1), (3, 3), (7, 2), (39, 11)]:
         assert abs(G[a, b] - A[a] * A[b] * phi[a] @ phi[b]) <= 1e-12 * (1 + abs(G[a, b]))
         assert abs(F[a, b] - A[a] * (phi[a] @ phi[b]) * Y[b]) <= 1e-12 * (1 + abs(F[a, b]))
@@ -92,8 +104,7 @@ TOL = {"fp64": 1e-11, "bf16x4": 1e-8, "bf16x3": 1e-6}
 def small():
     n = 200
     phi, A, Y = synth.hoif_sample(n, seed=0)
-    from paper_2508_12627_gb300 import hoif
-    G, F = hoif.factor_matrices(phi, A, Y)
+    G, F = _gf(phi, A, Y)
     ref = {}
     for j in range(2, 8):
         fs = _factors(j, G, F)
@@ -135,7 +146,7 @@ def test_hoif_order5_full_size_sampled_partitions():
     hc = hoif.HoifChains(n, orders=(j,), precision="bf16x4")
     hc.evaluate(phi, A, Y)
     V = hc.out[j][2:].cpu().numpy()
-    G, F = hoif.factor_matrices(phi, A, Y)
+    G, F = _gf(phi, A, Y)
     g = synth.hoif_chain_graph(j)
     parts = uo.set_partitions(j)
     tw = [uo.treewidth_bruteforce(max(r) + 1, uo.quotient_edges(g, r)) for r in parts]

@@ -409,3 +409,22 @@ def test_einsum_notation_sequence_of_k4():
     assert trace == want
     full = np.einsum("ab,ac,ad,bc,bd,cd->", *[a for _, a in tens])
     assert abs(val - full) <= 1e-12 * abs(full)
+
+
+def test_device_built_factor_kinds_by_hand():
+    # DIST: points on a line at 0, 1, 3 -> |i - j|; points at the corners of a unit
+    # square -> 1 and sqrt 2.  LOWRANK: [P | Q] gives P Q'; rank one gives the outer
+    # product.  COMPLEMENT: 1 - A.
+    D = uo.factor_tensor(uo.DIST, np.zeros((3, 1)), 1, np.array([[0.0], [1.0], [3.0]]))
+    assert np.array_equal(D, np.array([[0, 1, 3], [1, 0, 2], [3, 2, 0]], dtype=float))
+    sq = uo.factor_tensor(uo.DIST, np.zeros((4, 1)), 2, np.array([[0.0, 0], [1, 0], [0, 1], [1, 1]]))
+    assert sq[0, 1] == 1.0 and sq[0, 3] == pytest.approx(math.sqrt(2.0), rel=1e-15) and sq[2, 2] == 0.0
+    u, v = np.array([1.0, 2.0, -1.0]), np.array([3.0, 0.5, 2.0])
+    L = uo.factor_tensor(uo.LOWRANK, np.zeros((3, 1)), 1, np.stack([u, v], axis=1))
+    assert np.array_equal(L, np.outer(u, v))
+    P = np.arange(6.0).reshape(3, 2)
+    Q = np.array([[1.0, -1.0], [0.5, 2.0], [0.0, 3.0]])
+    L2 = uo.factor_tensor(uo.LOWRANK, np.zeros((3, 1)), 2, np.hstack([P, Q]))
+    assert L2[2, 1] == P[2, 0] * Q[1, 0] + P[2, 1] * Q[1, 1]
+    A = np.array([[0.0, 1.0], [1.0, 0.0]])
+    assert np.array_equal(uo.factor_tensor(uo.COMPLEMENT, np.zeros((2, 1)), 1, A), np.array([[1.0, 0], [0, 1]]))
