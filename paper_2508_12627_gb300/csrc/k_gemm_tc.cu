@@ -32,6 +32,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cstdio>
 #include <cstring>
 
@@ -72,16 +73,35 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const T *__restrict__ M
     if (j >= n) return;
     const T *row = M + j * n;
     T mx = 0, moff = 0;
-    for (int64_t i = lane; i < n; i += 32) {
-        T x = row[i];
-        if (u) x *= (T)u[i];
-        mx = fmax(mx, fabs(x));
-        if (i != j) moff = fmax(moff, fabs(x));
-    }
+    if (std::is_same<T, double>::value && !u) {
+        // float64 without weights: the maxima of |x| as integer maxima of the bit
+        // patterns with the sign cleared (the same order for finite values)
+        unsigned long long bm = 0, bo = 0;
+        for (int64_t i = lane; i < n; i += 32) {
+            const unsigned long long a = (unsigned long long)__double_as_longlong((double)row[i]) & 0x7FFFFFFFFFFFFFFFull;
+            bm = a > bm ? a : bm;
+            if (i != j) bo = a > bo ? a : bo;
+        }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        mx = (T)fmax((double)mx, (double)__shfl_xor_sync(0xffffffffu, mx, o));
-        moff = (T)fmax((double)moff, (double)__shfl_xor_sync(0xffffffffu, moff, o));
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long tm = __shfl_xor_sync(0xffffffffu, bm, o), to = __shfl_xor_sync(0xffffffffu, bo, o);
+            bm = tm > bm ? tm : bm;
+            bo = to > bo ? to : bo;
+        }
+        mx = (T)__longlong_as_double((long long)bm);
+        moff = (T)__longlong_as_double((long long)bo);
+    } else {
+        for (int64_t i = lane; i < n; i += 32) {
+            T x = row[i];
+            if (u) x *= (T)u[i];
+            mx = fmax(mx, fabs(x));
+            if (i != j) moff = fmax(moff, fabs(x));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mx = (T)fmax((double)mx, (double)__shfl_xor_sync(0xffffffffu, mx, o));
+            moff = (T)fmax((double)moff, (double)__shfl_xor_sync(0xffffffffu, moff, o));
+        }
     }
     // leave the diagonal out whenever that lowers the row scale
     const bool drop = diag_out && row_exp(moff) < row_exp(mx);
@@ -659,7 +679,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int64_t j = (int64_t)tm * kBM + row;
             const bool jok = j < n;
             const float rs = jok ? (C::kTf32 ? 1.f : ldexpf(g.scaleA[(int64_t)bl * n + j], -2 * g.lead_bits)) : 0.f;
-            const double rs_d = jok && !C::kTf32 ? ldexp((double)g.scaleA[(int64_t)bl * n + j], -2 * g.lead_bits) : 0.0;
+            // the row's scale 2^row_e (with the leading digits' weight): scaleA holds
+            // powers of two (0 for a zero row, whose entries are then 0)
+            const float sa = jok && !C::kTf32 ? g.scaleA[(int64_t)bl * n + j] : 0.f;
+            const int row_e = sa != 0.f ? ilogbf(sa) - 2 * g.lead_bits : 0;
             const uint32_t taddr = tmem + buf * C::kAccCols + ((uint32_t)(32 * q) << 16);
             double tile_acc[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll 1
@@ -676,33 +699,52 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tmem_wait_ld();
                 const int64_t k0 = (int64_t)tn * C::kBN + c_off + c0;
                 if (kWide && !g.wide_f32) {
-                    // float64 storage: the entry, the weights and the partial sums in
-                    // float64 (hi is an exact integer sum, lo its small correction)
+                    // float64 storage.  The four accumulators are summed exactly in
+                    // float32 pairs (TwoSum; mid1 holds the odd k-blocks' products,
+                    // nothing when there is one), and each half becomes a float64
+                    // scaled by the power-of-two row and column scales through its
+                    // bit fields: one float64 addition per entry, where converting and
+                    // adding the accumulators in float64 took nine operations of this
+                    // part's slow float64 pipe
                     double v[16];
 #pragma unroll
                     for (int c = 0; c < 16; ++c) {
                         const int64_t k = k0 + c;
-                        // mid1 holds the odd k-blocks' products: nothing when there is one
-                        const double x = (double)__uint_as_float(hi[c]) + (double)__uint_as_float(m0[c]) +
-                                         (num_k > 1 ? (double)__uint_as_float(m1[c]) : 0.0) +
-                                         (C::kPlanes > 2 ? (double)__uint_as_float(lo[c]) : 0.0);
-                        v[c] = k < n ? x * (double)g.scaleB[k] * rs_d : 0.0;
+                        float s, t, t2;
+                        two_sum(__uint_as_float(hi[c]), __uint_as_float(m0[c]), s, t);
+                        if (num_k > 1) {
+                            two_sum(s, __uint_as_float(m1[c]), s, t2);
+                            t = __fadd_rn(t, t2);
+                        }
+                        if (C::kPlanes > 2) {
+                            two_sum(s, __uint_as_float(lo[c]), s, t2);
+                            t = __fadd_rn(t, t2);
+                        }
+                        const float sb = k < n ? g.scaleB[k] : 0.f;
+                        if (sb == 0.f || sa == 0.f) {
+                            v[c] = 0.0;
+                        } else {
+                            const int e = ilogbf(sb) + row_e;
+                            v[c] = f2d_scaled(s, e) + f2d_scaled(t, e);
+                        }
                     }
                     if ((g.dA || g.dB) && jok) {
-                        // the terms i = j and i = k of operands split without their diagonal
+                        // the terms i = j and i = k of operands split without their
+                        // diagonal, each one fused multiply-add
                         const double *MA = (const double *)g.MA, *MB = (const double *)g.MB;
                         const double dAj = g.dA ? g.dA[j] : 0.0;
+                        const double aj = dAj * (g.uB ? g.uB[j] : 1.0);
 #pragma unroll
-                        const double uBj = g.uB ? g.uB[j] : 1.0;
                         for (int c = 0; c < 16; ++c) {
                             const int64_t k = k0 + c;
                             if (k >= n) continue;
-                            double corr = 0.0;
+                            double w = v[c];
                             const double dBk = g.dB ? g.dB[k] : 0.0;
-                            if (dAj != 0.0) corr += dAj * (g.rowB ? MB[j * n + k] : MB[k * n + j]) * uBj;
-                            if (dBk != 0.0) corr += (g.rowA ? MA[j * n + k] : MA[k * n + j]) * (g.uA ? g.uA[k] : 1.0) * dBk;
-                            if (k == j) corr -= dAj * dBk;
-                            v[c] += corr;
+                            if (aj != 0.0) w = fma(aj, g.rowB ? MB[j * n + k] : MB[k * n + j], w);
+                            if (dBk != 0.0)
+                                w = fma(g.rowA ? MA[j * n + k] : MA[k * n + j], g.uA ? g.uA[k] * dBk : dBk, w);
+                            if (k == j) w -= dAj * dBk;
+                            v[c] = w;
                         }
                     }
                     if (g.C && jok) {

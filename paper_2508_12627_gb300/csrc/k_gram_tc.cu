@@ -147,12 +147,6 @@ __device__ __forceinline__ void upper_tile(int t, int T, int &tm, int &tn) {
     tn = r + (t - (r * T - r * (r - 1) / 2));
 }
 
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-
 // x^p for p in 1..4 (p uniform across the warp)
 __device__ __forceinline__ float powk(float x, int p) {
     const float x2 = x * x;

@@ -33,11 +33,33 @@ __device__ __forceinline__ int row_exp(double m) {
 // of its float32 rounding.  y = x 2^(w - e) (|y| <= 2^w) is rounded once to a
 // multiple of 2^-8(planes - 1), as the integer q; its balanced base-256 digits
 // (each in [-128, 127], the leading one |d1| <= 2^w) are taken with integer
-// arithmetic, so that the only float64 operations are one scaling and one
-// conversion per entry.
+// arithmetic: no float64 arithmetic per entry (this part's float64 pipe runs at
+// a small fraction of its float32 and integer rates).
+// rint(x 2^k), ties to even as llrint, for a float64 x with |x 2^k| < 2^53: the
+// integer mantissa shifted right with the round bit taken from the bits shifted
+// out (integer operations only); the arithmetic route for what this does not
+// cover (not finite, or a left shift).
+__device__ __forceinline__ long long rint_scaled(double x, int k) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 2047u);
+    unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    if (ex != 0) m |= 1ull << 52;
+    const int sh = 1075 - k - (ex != 0 ? ex : 1);   // x 2^k = m 2^-sh
+    if (ex == 2047 || sh < 0) return llrint(ldexp(x, k));
+    unsigned long long q = 0;
+    if (sh == 0) {
+        q = m;
+    } else if (sh < 64) {
+        q = m >> sh;
+        const unsigned long long r = m & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        if (r > half || (r == half && (q & 1ull))) ++q;
+    }
+    return (b >> 63) ? -(long long)q : (long long)q;
+}
+
 __device__ __forceinline__ void write_digits(double x, int lead_bits, int e, int planes, __nv_bfloat16 *dst,
                                              int64_t plane_stride) {
-    long long q = llrint(ldexp(x, lead_bits - e + 8 * (planes - 1)));   // the scaling is exact
+    long long q = rint_scaled(x, lead_bits - e + 8 * (planes - 1));   // the scaling is exact
     float scale = __int_as_float((127 - 8 * (planes - 1)) << 23);       // 2^-8(planes - 1)
     for (int p = planes - 1; p >= 1; --p) {
         const int dp = (int)(((q + 128) & 255) - 128);
@@ -63,6 +85,26 @@ __device__ __forceinline__ void write_digits(float x, int lead_bits, int e, int 
     }
 }
 
+// x 2^e as a float64, for a float32 x, by assembling the float64's bit fields:
+// integer operations only, exact (the float32 mantissa fits).  The arithmetic
+// route (conversion, then scaling) handles what the bit route does not: zero,
+// a float32 subnormal, infinity or NaN, or a result outside the normal float64
+// range.
+__device__ __forceinline__ double f2d_scaled(float x, int e) {
+    const uint32_t b = __float_as_uint(x);
+    const int ex = (int)((b >> 23) & 255u);
+    const int de = ex + (1023 - 127) + e;
+    if (ex == 0 || ex == 255 || de <= 0 || de >= 2047) return x == 0.f ? 0.0 : ldexp((double)x, e);
+    const uint32_t hw = (b & 0x80000000u) | ((uint32_t)de << 20) | ((b & 0x7FFFFFu) >> 3);
+    return __hiloint2double((int)hw, (int)(b << 29));
+}
+
+// s + t = a + b exactly, s = fl(a + b) (Knuth's TwoSum, six float32 operations)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &t) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
 
 // two float32 in one 64-bit register pair (first = low half)
 typedef unsigned long long f32x2;

@@ -137,8 +137,10 @@ def test_dcov_graph_replay_matches_eager():
         dc.launch_matrices(D[2], D[0], outs[1])
 
     graph = dc.capture(enqueue)
-    for z, i in zip(Z, (2, 6, 8)):
-        z.copy_(torch.from_numpy(np.ascontiguousarray(R[i], dtype=np.float64)))
+    # new contents of the same shapes: the rows in reverse order, rescaled
+    new = [np.ascontiguousarray(R[i][::-1] * 1.5, dtype=np.float64) for i in (0, 4, 9)]
+    for z, v in zip(Z, new):
+        z.copy_(torch.from_numpy(v))
     graph.replay()
     torch.cuda.synchronize()
     got = [[float(x[0].item()) for x in o] for o in outs]
@@ -148,7 +150,7 @@ def test_dcov_graph_replay_matches_eager():
     for g, w in zip(got, want):
         assert g == pytest.approx(w, rel=1e-13, abs=0.0)
     # and the replayed values are those of the new samples
-    a, b = _dist(R[2]), _dist(R[6])
+    a, b = _dist(new[0]), _dist(new[1])
     ref_terms, _ = oracle_terms(a, b)
     for g, r in zip(got[0], ref_terms):
         assert abs(g - r) <= 1e-12 * abs(r)
