@@ -256,6 +256,27 @@ int ustat_combine(const ustat_plan_t *plan, const double *scal, int64_t n, void 
 int ustat_status(const void *ws, void *stream, int *device_status);
 
 /*
+ * Memory-lean evaluation.  The tensorization step stores each pairwise factor as an
+ * n x n matrix and the products read it (the O(K n^2) space of Section 3.3's remark
+ * on space complexity and of the appendix "A Discussion on the Space Complexity").
+ * ustat_eval_lean stores no n x n object: the factor's rows are rebuilt from X in
+ * panels of panel_rows rows, and every product runs panel pair by panel pair on
+ * them, so the workspace is O(panel_rows x n) (a time-space trade: the factor rows
+ * of the column panels are rebuilt once per row panel).  Same results as ustat_eval
+ * (the same digits and per-entry accumulation; the reductions summed in another
+ * order).  Supported: bf16x3 plans whose n^2 objects are RBF factors (d <= 256)
+ * read only by s = 2 products that store nothing (for instance the triangle and the
+ * 4-cycle; USTAT_ERR_UNSUPPORTED otherwise).
+ *   panel_rows : a positive multiple of 128 (capped at n rounded up to 128)
+ *   ws         : device, ustat_lean_workspace_bytes() bytes, 256-byte aligned
+ * Other arguments, outputs, status word and errors as ustat_eval.
+ */
+int ustat_lean_workspace_bytes(const ustat_plan_t *plan, int64_t n, int d, int64_t panel_rows, size_t *bytes);
+int ustat_eval_lean(ustat_plan_t *plan, const void *X, int x_dtype, int64_t n, int d,
+                    const ustat_factor *factors, int n_factors, int64_t panel_rows, void *ws, size_t ws_bytes,
+                    void *stream, double *U_out, double *V_out);
+
+/*
  * The n x n matrix of one device-built factor, for a caller that evaluates several
  * U-statistics over the same factor (the distance matrices of Section 4.3's
  * distance-covariance example enter four U-statistics each): build it once here

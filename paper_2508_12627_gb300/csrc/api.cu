@@ -718,6 +718,218 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
     return USTAT_OK;
 }
 
+// ---------------------------------------------------------------- memory-lean evaluation
+// The tensorization step stores every pairwise factor as an n x n matrix, and the
+// s = 2 products read the stored matrices (the space bound of Section 3.3's
+// remark on space complexity and of the appendix on it: O(n^2) for the factors).
+// The lean form stores none: for plans whose n^2 objects are RBF factor matrices
+// (built on the tensor cores from X) read only by products that keep nothing but
+// their fused reductions, it walks the products panel by panel.  For a row panel
+// J and a column panel L of one product it builds the digit planes of the
+// factor's rows J and rows L (and, when a reduction weighs by the factor, its
+// float32 rows J) into two panel buffers, then runs the product's window (J, L):
+// the same digits, the same accumulation per entry, the reductions summed in
+// another order.  Memory O(panel x n); the factor rows of L are rebuilt once per
+// panel J, an O(n^3 d / panel) build beside the O(n^3) products.
+struct LeanPlan {
+    bool ok = false;
+    std::vector<int> kb_of;   // per slot: the RBF build op writing it (its matrix or digit planes), or -1
+    bool need_k = false;      // a product's reduction weighs by the factor matrix
+};
+
+LeanPlan lean_plan(const Plan &P) {
+    LeanPlan LP;
+    if (P.precision != USTAT_BF16X3) return LP;
+    LP.kb_of.assign(P.slots.size(), -1);
+    for (size_t i = 0; i < P.ops.size(); ++i) {
+        const Op &op = P.ops[i];
+        switch (op.kind) {
+            case OP_KBUILD:
+                if (P.factor_kind[op.factor] != USTAT_RBF) return LP;
+                if (op.out >= 0) LP.kb_of[op.out] = (int)i;
+                if (op.opA >= 0) LP.kb_of[op.opA] = (int)i;
+                break;
+            case OP_GEMM: {
+                if (op.store || op.opA < 0 || op.opB < 0 || LP.kb_of[op.opA] < 0 || LP.kb_of[op.opB] < 0)
+                    return LP;
+                if (op.symmetric && LP.kb_of[op.opA] != LP.kb_of[op.opB]) return LP;
+                for (int r = 0; r < op.nred; ++r) {
+                    const int w = op.red[r].W.mat;
+                    if (w < 0) continue;
+                    // the weight must be the A operand's factor (its rows J are built)
+                    if (LP.kb_of[w] != LP.kb_of[op.opA] || !P.slots[w].symmetric) return LP;
+                    LP.need_k = true;
+                }
+                break;
+            }
+            case OP_DIAG:
+                if (op.factor < 0) return LP;
+                break;
+            case OP_UNARY:
+            case OP_LOADVEC:
+            case OP_VMUL:
+            case OP_VSUM:
+            case OP_VDOT:
+                break;
+            default:
+                return LP;
+        }
+    }
+    LP.ok = true;
+    return LP;
+}
+
+struct LeanLayout {
+    Layout L;   // error word, scalars and vectors as in the stored form; kb_off the build's X scratch
+    size_t a_off = 0, a_sc = 0, b_off = 0, b_sc = 0, k_off = 0;
+};
+
+LeanLayout make_lean_layout(const Plan &P, int64_t n, int d, int64_t panel, bool need_k) {
+    LeanLayout LL;
+    LL.L = make_layout(P, n, d);   // only its scalar and vector part is used
+    Layout &L = LL.L;
+    size_t cur = align_up(L.zero_bytes, 1024);
+    L.kb_off = cur;
+    cur = align_up(cur + kbuild_rbf_tc_scratch_bytes(n, d), 1024);
+    const size_t planes = (size_t)split_planes_of(P.precision) * 2 * (size_t)panel * L.ldp_slices;
+    LL.a_off = cur;
+    cur = align_up(cur + planes, 1024);
+    LL.a_sc = cur;
+    cur = align_up(cur + 4 * (size_t)panel, 1024);
+    LL.b_off = cur;
+    cur = align_up(cur + planes, 1024);
+    LL.b_sc = cur;
+    cur = align_up(cur + 4 * (size_t)panel, 1024);
+    if (need_k) {
+        LL.k_off = cur;
+        cur = align_up(cur + 4 * (size_t)panel * n, 1024);
+    }
+    L.total = cur;
+    return LL;
+}
+
+int run_lean(const Plan &P, const LeanPlan &LP, const LeanLayout &LL, char *ws, int64_t n, int d, int64_t panel,
+             const void *X, int x_dtype, const ustat_factor *f, cudaStream_t st, double *U_out, double *V_out) {
+    const Layout &L = LL.L;
+    Ctx C{P, L, ws, n, d, false, st};
+    cudaError_t e = cudaMemsetAsync(ws, 0, L.zero_bytes, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int *err = (int *)(ws + L.err_off);
+    void *scratch = ws + L.kb_off;
+    const int lead = split_lead_bits(n);
+    const int planes = split_planes_of(P.precision);
+    const int64_t ldp = L.ldp_slices;
+    void *Apl = ws + LL.a_off, *Bpl = ws + LL.b_off;
+    float *Asc = (float *)(ws + LL.a_sc), *Bsc = (float *)(ws + LL.b_sc);
+    float *Kp = LL.k_off ? (float *)(ws + LL.k_off) : nullptr;
+    bool prepped = false;
+    auto prep = [&]() -> cudaError_t {
+        if (prepped) return cudaSuccess;
+        prepped = true;
+        return launch_gram_rbf_prep(X, x_dtype, n, d, scratch, err, st);
+    };
+    // rows r0 .. r0 + rows - 1 of factor `fi` into a panel: digit planes and scales,
+    // the float32 rows too when K is given
+    auto panel_build = [&](int fi, int64_t r0, int64_t rows, float *K, void *pl, float *sc) {
+        return launch_gram_rbf_window(n, d, f[fi].param, P.sparsify, K ? K - r0 * n : nullptr, pl, ldp, lead, planes,
+                                      sc - r0, 0, nullptr, nullptr, nullptr, r0, rows, 0, n, r0, rows * ldp, scratch,
+                                      err, st);
+    };
+    const int var = P.tc_variant[tc_size_class(n)];
+    for (const Op &op : P.ops) {
+        ProfScope ps(op.kind, st);
+        switch (op.kind) {
+            case OP_KBUILD: {
+                e = prep();
+                if (e != cudaSuccess || op.nred == 0) break;
+                // the build's fused reductions, panel by panel, nothing stored
+                int rpow[kMaxRed], rvec[kMaxRed];
+                double *rout[kMaxRed];
+                for (int r = 0; r < op.nred; ++r) {
+                    rpow[r] = op.red[r].pow;
+                    rvec[r] = P.slots[op.red[r].out].kind == S_VEC;
+                    rout[r] = C.vec(op.red[r].out);
+                }
+                for (int64_t r0 = 0; r0 < n && e == cudaSuccess; r0 += panel)
+                    e = launch_gram_rbf_window(n, d, f[op.factor].param, P.sparsify, nullptr, nullptr, ldp, lead,
+                                               planes, nullptr, op.nred, rpow, rvec, rout, r0,
+                                               std::min(panel, n - r0), 0, n, 0, 0, scratch, err, st);
+                break;
+            }
+            case OP_GEMM: {
+                e = prep();
+                const int fa = P.ops[LP.kb_of[op.opA]].factor, fb = P.ops[LP.kb_of[op.opB]].factor;
+                bool weighted = false;
+                for (int r = 0; r < op.nred; ++r) weighted |= op.red[r].W.mat >= 0;
+                int shape = (var >> 2) & 3;
+                if (shape == 1 && op.symmetric) shape = 0;
+                for (int64_t r0 = 0; r0 < n && e == cudaSuccess; r0 += panel) {
+                    const int64_t rj = std::min(panel, n - r0);
+                    e = panel_build(fa, r0, rj, weighted ? Kp : nullptr, Apl, Asc);
+                    for (int64_t c0 = op.symmetric ? r0 : 0; c0 < n && e == cudaSuccess; c0 += panel) {
+                        const int64_t rl = std::min(panel, n - c0);
+                        const bool same = c0 == r0 && fa == fb;
+                        if (!same) e = panel_build(fb, c0, rl, nullptr, Bpl, Bsc);
+                        if (e != cudaSuccess) break;
+                        TcGemmArgs g{};
+                        g.n = n;
+                        g.ldp = ldp;
+                        g.opA = Apl;
+                        g.scaleA = Asc - r0;
+                        g.opB = same ? Apl : Bpl;
+                        g.scaleB = (same ? Asc : Bsc) - c0;
+                        g.lead_bits = lead;
+                        g.err = err;
+                        g.nred = op.nred;
+                        for (int r = 0; r < op.nred; ++r) {
+                            const Red &R = op.red[r];
+                            g.red[r] = TcRed{R.W.mat >= 0 ? (const void *)(Kp - r0 * n) : nullptr, 0, C.vec(R.a),
+                                             C.vec(R.b), R.pow, (double *)C.ptr(R.out)};
+                        }
+                        g.symmetric = op.symmetric && c0 == r0;
+                        g.wscale = (op.symmetric && c0 != r0) ? 2.0 : 1.0;   // the mirror window
+                        g.row0 = r0;
+                        g.rows = rj;
+                        g.col0 = c0;
+                        g.cols = rl;
+                        g.group_rows = kGroupRows[var & 3];
+                        e = launch_gemm_bf16x3(g, shape, st);
+                    }
+                }
+                break;
+            }
+            case OP_UNARY:
+                e = launch_unary_tanh(X, x_dtype, n, d, (const double *)f[op.factor].data, C.vec(op.out), err, st);
+                break;
+            case OP_LOADVEC:
+                e = launch_copyvec((const double *)f[op.factor].data, n, C.vec(op.out), err, st);
+                break;
+            case OP_DIAG:
+                e = launch_factor_diag(f[op.factor].kind, f[op.factor].param, X, x_dtype, d,
+                                       (const double *)f[op.factor].data, n, P.sparsify, C.vec(op.out), st);
+                break;
+            case OP_VMUL:
+                e = launch_vmul(C.vec(op.u), C.vec(op.a), n, C.vec(op.out), st);
+                break;
+            case OP_VSUM:
+                e = launch_vsum(C.vec(op.u), n, C.vec(op.out), st);
+                break;
+            case OP_VDOT:
+                e = launch_vdot(C.vec(op.u), C.vec(op.a), n, C.vec(op.out), st);
+                break;
+            default:
+                return USTAT_ERR_UNSUPPORTED;
+        }
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    {
+        ProfScope ps(kProfCombine, st);
+        e = plan_combine(P, L, (const double *)(ws + L.scal_off), err, n, U_out, V_out, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    return USTAT_OK;
+}
+
 }  // namespace
 
 int ustat::record_cuda_error(int e) { return cuda_fail((cudaError_t)e); }
@@ -1154,6 +1366,34 @@ int ustat_eval_rows(ustat_plan_t *plan, int rank, int n_ranks, const void *X, in
     C.rank = rank;
     C.nranks = n_ranks;
     return run_program(C, X, x_dtype, factors, nullptr, nullptr, scal_out);
+}
+
+int ustat_lean_workspace_bytes(const ustat_plan_t *plan, int64_t n, int d, int64_t panel_rows, size_t *bytes) {
+    if (!plan || !bytes || n < 1 || d < 1 || panel_rows < 128 || panel_rows % 128 != 0) return USTAT_ERR_INVALID_ARG;
+    const LeanPlan LP = lean_plan(plan->p);
+    if (!LP.ok || d > 256) return USTAT_ERR_UNSUPPORTED;
+    *bytes = make_lean_layout(plan->p, n, d, std::min<int64_t>(panel_rows, align_up((size_t)n, 128)), LP.need_k)
+                 .L.total;
+    return USTAT_OK;
+}
+
+int ustat_eval_lean(ustat_plan_t *plan, const void *X, int x_dtype, int64_t n, int d, const ustat_factor *factors,
+                    int n_factors, int64_t panel_rows, void *ws, size_t ws_bytes, void *stream, double *U_out,
+                    double *V_out) {
+    if (!plan || !X || !U_out || d < 1 || n < 1 || (x_dtype != 0 && x_dtype != 1) || panel_rows < 128 ||
+        panel_rows % 128 != 0)
+        return USTAT_ERR_INVALID_ARG;
+    const Plan &P = plan->p;
+    if (n < P.m) return USTAT_ERR_N_LT_M;
+    if (n > (int64_t)1 << 20) return USTAT_ERR_UNSUPPORTED;
+    const LeanPlan LP = lean_plan(P);
+    if (!LP.ok || d > 256) return USTAT_ERR_UNSUPPORTED;
+    int rc = check_graph_factors(P, factors, n_factors, d);
+    if (rc != USTAT_OK) return rc;
+    const int64_t panel = std::min<int64_t>(panel_rows, align_up((size_t)n, 128));
+    LeanLayout LL = make_lean_layout(P, n, d, panel, LP.need_k);
+    if (!ws || ws_bytes < LL.L.total || ((uintptr_t)ws % 256) != 0) return USTAT_ERR_WORKSPACE;
+    return run_lean(P, LP, LL, (char *)ws, n, d, panel, X, x_dtype, factors, (cudaStream_t)stream, U_out, V_out);
 }
 
 int ustat_combine(const ustat_plan_t *plan, const double *scal, int64_t n, void *stream, double *U_out,

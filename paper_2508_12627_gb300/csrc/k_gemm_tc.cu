@@ -500,9 +500,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n = g.n;
+    // the window of the product this launch computes (the whole product by default)
+    const bool win = g.rows > 0;
+    const int64_t row0 = win ? g.row0 : 0, col0 = win ? g.col0 : 0;
+    const int64_t jend = win ? row0 + g.rows : n, kend = win ? col0 + g.cols : n;
     const int num_k = (int)(g.ldp / C::kBKElems);
     const long long wlim = g.wait_limit > 0 ? g.wait_limit : kWaitLimit;
-    TileWalk walk{(int)((n + kBM - 1) / kBM), (int)((n + C::kBN - 1) / C::kBN), g.symmetric,
+    TileWalk walk{(int)((jend - row0 + kBM - 1) / kBM), (int)((kend - col0 + C::kBN - 1) / C::kBN), g.symmetric,
                   g.group_rows > 0 ? g.group_rows : 8, g.batch};
     // work units: the tiles, except that the last g.split_tail tiles of the schedule
     // are split into two halves of kBN / 2 columns, so that the last wave of the
@@ -676,8 +680,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             waited = __shfl_sync(0xffffffffu, waited, 0);
             if (!waited || *abort_flag) break;
             tc_fence_after();
-            const int64_t j = (int64_t)tm * kBM + row;
-            const bool jok = j < n;
+            const int64_t j = row0 + (int64_t)tm * kBM + row;
+            const bool jok = j < jend;
             const float rs = jok ? (C::kTf32 ? 1.f : ldexpf(g.scaleA[(int64_t)bl * n + j], -2 * g.lead_bits)) : 0.f;
             // the row's scale 2^row_e (with the leading digits' weight): scaleA holds
             // powers of two (0 for a zero row, whose entries are then 0)
@@ -697,7 +701,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (!C::kTf32) tmem_ld16(taddr + C::kBN + c0, lo);
                 }
                 tmem_wait_ld();
-                const int64_t k0 = (int64_t)tn * C::kBN + c_off + c0;
+                const int64_t k0 = col0 + (int64_t)tn * C::kBN + c_off + c0;
                 if (kWide && !g.wide_f32) {
                     // float64 storage.  The four accumulators are summed exactly in
                     // float32 pairs (TwoSum; mid1 holds the odd k-blocks' products,
@@ -720,7 +724,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             two_sum(s, __uint_as_float(lo[c]), s, t2);
                             t = __fadd_rn(t, t2);
                         }
-                        const float sb = k < n ? g.scaleB[k] : 0.f;
+                        const float sb = k < kend ? g.scaleB[k] : 0.f;
                         if (sb == 0.f || sa == 0.f) {
                             v[c] = 0.0;
                         } else {
@@ -737,7 +741,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                         for (int c = 0; c < 16; ++c) {
                             const int64_t k = k0 + c;
-                            if (k >= n) continue;
+                            if (k >= kend) continue;
                             double w = v[c];
                             const double dBk = g.dB ? g.dB[k] : 0.0;
                             if (aj != 0.0) w = fma(aj, g.rowB ? MB[j * n + k] : MB[k * n + j], w);
@@ -751,7 +755,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         double *Cd = (double *)g.C;
 #pragma unroll
                         for (int c = 0; c < 16; ++c)
-                            if (k0 + c < n) Cd[j * n + k0 + c] = v[c];
+                            if (k0 + c < kend) Cd[j * n + k0 + c] = v[c];
                     }
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
@@ -765,7 +769,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                             for (int c = 0; c < 16; ++c) {
                                 const int64_t k = k0 + c;
-                                if (k >= n) continue;
+                                if (k >= kend) continue;
                                 double w = bv ? bv[k] : 1.0;
                                 if (W) w *= tW ? W[k * n + j] : W[j * n + k];
                                 if (Wbd) w *= g.transWbd ? Wbd[k * n + bb] : Wbd[bb * n + k];
@@ -789,7 +793,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             if constexpr (kWide)
                                 corr = (num_k > 1 ? __uint_as_float(m1[c]) : 0.f) +
                                        ((C::kPlanes > 2 ? corr : 0.f) + __uint_as_float(m0[c]));
-                            x = (x + corr) * (k < n ? g.scaleB[k] : 0.f);
+                            x = (x + corr) * (k < kend ? g.scaleB[k] : 0.f);
                         }
                         v[c] = x * rs;
                     }
@@ -801,11 +805,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                         bool anyB = false;
     #pragma unroll
                         for (int c = 0; c < 16; ++c) {
-                            dBk[c] = (g.dB && k0 + c < n) ? (float)g.dB[k0 + c] : 0.f;
+                            dBk[c] = (g.dB && k0 + c < kend) ? (float)g.dB[k0 + c] : 0.f;
                             anyB |= dBk[c] != 0.f;
                         }
                         // rows j of the sources, 16-byte loads where they lie inside
-                        const bool full = (k0 + 16 <= n) && ((n & 3) == 0);
+                        const bool full = (k0 + 16 <= kend) && ((n & 3) == 0);
                         auto row16 = [&](const float *M, int rowf, float (&r)[16]) {
                             if (rowf && full) {
                                 const float4 *p4 = reinterpret_cast<const float4 *>(M + j * n + k0);
@@ -817,7 +821,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             } else {
     #pragma unroll
                                 for (int c = 0; c < 16; ++c)
-                                    r[c] = k0 + c < n ? (rowf ? M[j * n + k0 + c] : M[(k0 + c) * n + j]) : 0.f;
+                                    r[c] = k0 + c < kend ? (rowf ? M[j * n + k0 + c] : M[(k0 + c) * n + j]) : 0.f;
                             }
                         };
                         float xb[16], xa[16];
@@ -836,7 +840,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             }
     #pragma unroll
                             for (int c = 0; c < 16; ++c)
-                                v[c] += xa[c] * (g.uA && k0 + c < n ? (float)g.uA[k0 + c] : 1.f) * dBk[c];
+                                v[c] += xa[c] * (g.uA && k0 + c < kend ? (float)g.uA[k0 + c] : 1.f) * dBk[c];
                         }
     #pragma unroll
                         for (int c = 0; c < 16; ++c)
@@ -845,11 +849,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (g.C && jok) {
     #pragma unroll
                         for (int c = 0; c < 16; ++c)
-                            if (k0 + c < n) ((float *)g.C)[j * n + k0 + c] = v[c];
+                            if (k0 + c < kend) ((float *)g.C)[j * n + k0 + c] = v[c];
                     }
                     // the 16 columns lie inside the matrix and rows are 16-byte aligned:
                     // weights are read as float4
-                    const bool full = (k0 + 16 <= n) && ((n & 3) == 0);
+                    const bool full = (k0 + 16 <= kend) && ((n & 3) == 0);
     #pragma unroll
                     for (int r = 0; r < 4; ++r) {
                         if (r >= g.nred) break;
@@ -870,12 +874,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     #pragma unroll
                                 for (int c = 0; c < 16; ++c) {
                                     const int64_t k = k0 + c;
-                                    w[c] = k < n ? (W ? (tW ? W[k * n + j] : W[j * n + k]) : 1.f) : 0.f;
+                                    w[c] = k < kend ? (W ? (tW ? W[k * n + j] : W[j * n + k]) : 1.f) : 0.f;
                                 }
                             }
                             if (bv) {
     #pragma unroll
-                                for (int c = 0; c < 16; ++c) w[c] *= k0 + c < n ? (float)bv[k0 + c] : 0.f;
+                                for (int c = 0; c < 16; ++c) w[c] *= k0 + c < kend ? (float)bv[k0 + c] : 0.f;
                             }
                             if (Wbd) {
                                 if (!tWbd && full) {
@@ -889,7 +893,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     #pragma unroll
                                     for (int c = 0; c < 16; ++c) {
                                         const int64_t k = k0 + c;
-                                        if (k < n) w[c] *= tWbd ? Wbd[k * n + bb] : Wbd[bb * n + k];
+                                        if (k < kend) w[c] *= tWbd ? Wbd[k * n + bb] : Wbd[bb * n + k];
                                     }
                                 }
                             }
@@ -906,7 +910,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty_bar(buf));
-            double wgt = (g.symmetric && tm != tn) ? 2.0 : 1.0;
+            double wgt = ((g.symmetric && tm != tn) ? 2.0 : 1.0) * (g.wscale != 0.0 ? g.wscale : 1.0);
             if (g.ub) wgt *= g.ub[bb];
             double wbc = 1.0;
             if (g.Wbc && jok) {
@@ -1030,9 +1034,17 @@ cudaError_t launch_tc(const TcGemmArgs &g0, cudaStream_t s) {
     if ((g.dA || g.dB) && (g.batch > 0 || (g.dA && !g.MB) || (g.dB && !g.MA))) return cudaErrorInvalidValue;
     const int za = g.batch > 0 ? g.batch : 1;
     CUtensorMap mb2;
-    if (!make_map_planes(&ma, g.opA, bf16, C::kPlanes, za * C::kPlanes, g.n, g.ldp, kBM, C::kRowBytes) ||
-        !make_map_planes(&mb, g.opB, bf16, C::kPlanes, C::kPlanes, g.n, g.ldp, C::kBN, C::kRowBytes) ||
-        !make_map_planes(&mb2, g.opB, bf16, C::kPlanes, C::kPlanes, g.n, g.ldp, C::kBN / 2, C::kRowBytes))
+    // a window: rows row0 .. row0 + rows - 1 and columns col0 .. col0 + cols - 1 of
+    // the product, reductions only; its operands hold just those rows
+    const bool win = g.rows > 0;
+    if (win && (g.cols < 1 || g.row0 < 0 || g.col0 < 0 || g.row0 + g.rows > g.n || g.col0 + g.cols > g.n ||
+                g.C || g.batch > 0 || g.dA || g.dB || g.shard_count > 1 ||
+                (g.symmetric && (g.row0 != g.col0 || g.rows != g.cols))))
+        return cudaErrorInvalidValue;
+    const int64_t ra = win ? g.rows : g.n, rb = win ? g.cols : g.n;
+    if (!make_map_planes(&ma, g.opA, bf16, C::kPlanes, za * C::kPlanes, ra, g.ldp, kBM, C::kRowBytes) ||
+        !make_map_planes(&mb, g.opB, bf16, C::kPlanes, C::kPlanes, rb, g.ldp, C::kBN, C::kRowBytes) ||
+        !make_map_planes(&mb2, g.opB, bf16, C::kPlanes, C::kPlanes, rb, g.ldp, C::kBN / 2, C::kRowBytes))
         return cudaErrorInvalidValue;
     static bool attr[64] = {false};
     int dev = 0;
@@ -1043,7 +1055,7 @@ cudaError_t launch_tc(const TcGemmArgs &g0, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         attr[dev] = true;
     }
-    const int64_t tm = (g.n + kBM - 1) / kBM, tn = (g.n + C::kBN - 1) / C::kBN;
+    const int64_t tm = (ra + kBM - 1) / kBM, tn = (rb + C::kBN - 1) / C::kBN;
     int64_t tiles = (g.symmetric ? tm * (tm + 1) / 2 : tm * tn) * za;
     g.tile_lo = g.tile_hi = 0;
     if (g.shard_count > 1) {

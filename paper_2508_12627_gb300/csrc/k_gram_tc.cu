@@ -89,6 +89,14 @@ struct GramArgs {
     GramRed red[kGMaxRed];
     int *err;
     long long wait_limit;
+    // window (memory-lean evaluation): the tiles of rows row0 .. row0 + rows - 1 and
+    // columns col0 .. col0 + cols - 1 (multiples of 128 for row0, col0), every one
+    // computed (no mirror); K may be null (not stored), and K, scales and the
+    // reduction vectors keep global indices (the caller offsets the pointers of
+    // buffers that hold only the window); the digit planes hold row j at
+    // (j - srow0), plane stride splane elements.  Used by the kWin form only.
+    int64_t row0, rows, col0, cols;
+    int64_t srow0, splane;
 };
 
 // Row i of X: its digits (kGP planes of ldx coordinates, zero beyond d), its
@@ -187,6 +195,9 @@ __device__ __forceinline__ float transpose_reduce16(float (&v)[16], int lane) {
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
+// kWin: the window form (a compile-time switch, so that the whole-matrix form
+// keeps its registers)
+template <bool kWin>
 __global__ void __launch_bounds__(kGThreads, 1) gram_rbf_kernel(const __grid_constant__ CUtensorMap mapX, GramArgs g) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -207,7 +218,19 @@ __global__ void __launch_bounds__(kGThreads, 1) gram_rbf_kernel(const __grid_con
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n = g.n;
     const int T = (int)((n + kGT - 1) / kGT);
-    const int total = T * (T + 1) / 2;
+    constexpr bool win = kWin;
+    const int tm0 = win ? (int)(g.row0 / kGT) : 0, tn0 = win ? (int)(g.col0 / kGT) : 0;
+    const int TN = win ? (int)((g.cols + kGT - 1) / kGT) : 0;
+    const int total = win ? (int)((g.rows + kGT - 1) / kGT) * TN : T * (T + 1) / 2;
+    const int64_t jend = win ? g.row0 + g.rows : n, kend = win ? g.col0 + g.cols : n;
+    auto tile_of = [&](int t, int &tm, int &tn) {
+        if (win) {
+            tm = tm0 + t / TN;
+            tn = tn0 + t % TN;
+        } else {
+            upper_tile(t, T, tm, tn);
+        }
+    };
     const long long wlim = g.wait_limit > 0 ? g.wait_limit : kGWaitLimit;
 
     if (threadIdx.x == 0) {
@@ -243,7 +266,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gram_rbf_kernel(const __grid_con
             uint32_t it = 0;
             for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
                 int tm, tn;
-                upper_tile(t, T, tm, tn);
+                tile_of(t, tm, tn);
                 for (int kb = 0; kb < g.num_k; ++kb, ++it) {
                     const int s = it % kGStages;
                     if (it >= (uint32_t)kGStages && !mbar_wait(empty_bar(s), ((it / kGStages) - 1) & 1, abort_flag, wlim))
@@ -320,7 +343,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gram_rbf_kernel(const __grid_con
         uint32_t tcount = 0;
         for (int t = blockIdx.x; t < total; t += gridDim.x) {
             int tm, tn;
-            upper_tile(t, T, tm, tn);
+            tile_of(t, tm, tn);
             const int buf = tcount & 1;
             // the warp's column data (scale and squared norm of each column's x),
             // fetched while the accumulator may still be in flight
@@ -338,9 +361,10 @@ __global__ void __launch_bounds__(kGThreads, 1) gram_rbf_kernel(const __grid_con
             if (!waited || *abort_flag) break;
             tc_fence_after();
             const bool diag = tm == tn;
+            const bool mirror = !win && !diag;   // the tile stands for its mirror too
             const int64_t j0 = (int64_t)tm * kGT + 32 * q;   // the warp's first row
             const int64_t j = j0 + lane;
-            const bool jok = j < n;
+            const bool jok = j < jend;
             const float sj = g.sx[j];
             const float2 nj = g.nrm[j];
             float rowsum[kGMaxRed] = {0.f, 0.f, 0.f, 0.f};
@@ -378,7 +402,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gram_rbf_kernel(const __grid_con
                 for (int c = 0; c < 16; ++c) {
                     const int64_t k = k0 + c;
                     if (k == j) v[c] = dv;
-                    if (!jok || k >= n) v[c] = 0.f;
+                    if (!jok || k >= kend) v[c] = 0.f;
                 }
                 // K: the warp's 32 tile rows through shared memory, 16-byte row pieces
 #pragma unroll
@@ -389,23 +413,23 @@ __global__ void __launch_bounds__(kGThreads, 1) gram_rbf_kernel(const __grid_con
                 for (int it = 0; it < 4; ++it) {
                     const int r = 8 * it + (lane >> 2), pc = lane & 3;
                     const int64_t jr = j0 + r, kc = k0 + 4 * pc;
-                    if (jr < n) {
+                    if (jr < jend && (!kWin || g.K)) {
                         float *dst = g.K + jr * n + kc;
                         const float e0 = stg.kf[r][4 * pc], e1 = stg.kf[r][4 * pc + 1], e2 = stg.kf[r][4 * pc + 2],
                                     e3 = stg.kf[r][4 * pc + 3];
-                        if (kvec && kc + 3 < n) {
+                        if (kvec && kc + 3 < kend) {
                             *reinterpret_cast<float4 *>(dst) = make_float4(e0, e1, e2, e3);
                         } else {
-                            if (kc < n) dst[0] = e0;
-                            if (kc + 1 < n) dst[1] = e1;
-                            if (kc + 2 < n) dst[2] = e2;
-                            if (kc + 3 < n) dst[3] = e3;
+                            if (kc < kend) dst[0] = e0;
+                            if (kc + 1 < kend) dst[1] = e1;
+                            if (kc + 2 < kend) dst[2] = e2;
+                            if (kc + 3 < kend) dst[3] = e3;
                         }
                     }
                 }
                 // the mirror of K, where K is read below the diagonal too: each store
                 // writes 32 consecutive floats of a mirror row
-                if (!diag && !g.upper_only && jok) {
+                if (mirror && !g.upper_only && jok) {
 #pragma unroll
                     for (int c = 0; c < 16; ++c)
                         if (k0 + c < n) g.K[(k0 + c) * n + j] = v[c];
@@ -413,7 +437,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gram_rbf_kernel(const __grid_con
                 // digit planes of K (row scale 1): y = K 2^w, digit p rounds y_p to a
                 // multiple of 2^-8p (add and subtract 1.5 * 2^(23 - 8p)), exact
                 if (g.slices) {
-                    const int64_t plane = n * g.ldp;
+                    const int64_t plane = kWin ? g.splane : n * g.ldp;
                     float y[16];
 #pragma unroll
                     for (int c = 0; c < 16; ++c) y[c] = v[c] * lead_scale;
@@ -431,7 +455,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gram_rbf_kernel(const __grid_con
                         __syncwarp();   // the previous plane's pieces are read
 #pragma unroll
                         for (int c2 = 0; c2 < 8; ++c2) stg.dr[lane][c2] = w[c2];
-                        if (!diag) {
+                        if (mirror) {
 #pragma unroll
                             for (int c2 = 0; c2 < 8; ++c2) {
                                 stg.dt[2 * c2][lane] = (unsigned short)(w[c2] & 0xffffu);
@@ -446,14 +470,14 @@ __global__ void __launch_bounds__(kGThreads, 1) gram_rbf_kernel(const __grid_con
                             for (int it = 0; it < 2; ++it) {
                                 const int r = 16 * it + (lane >> 1), pc = lane & 1;
                                 const int64_t jr = j0 + r;
-                                if (jr < n)
-                                    *reinterpret_cast<uint4 *>(pl + jr * g.ldp + k0 + 8 * pc) =
+                                if (jr < jend)
+                                    *reinterpret_cast<uint4 *>(pl + (kWin ? jr - g.srow0 : jr) * g.ldp + k0 + 8 * pc) =
                                         make_uint4(stg.dr[r][4 * pc], stg.dr[r][4 * pc + 1], stg.dr[r][4 * pc + 2],
                                                    stg.dr[r][4 * pc + 3]);
                             }
                         }
                         // mirror rows k0 .. k0 + 15, columns j0 .. j0 + 31: 64 B per row
-                        if (!diag) {
+                        if (mirror) {
 #pragma unroll
                             for (int it = 0; it < 2; ++it) {
                                 const int c = 8 * it + (lane >> 2), pc = lane & 3;
@@ -474,7 +498,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gram_rbf_kernel(const __grid_con
                         }
                         magic *= (1.0f / 256.0f);
                     }
-                    if (diag && cg == 0 && h == 0 && jok && g.scales) g.scales[j] = 1.f;
+                    if ((win ? tn == tn0 : diag) && cg == 0 && h == 0 && jok && g.scales) g.scales[j] = 1.f;
                 }
                 __syncwarp();   // the staging buffers are free for the next chunk
                 // fused reductions of entrywise powers of K
@@ -491,7 +515,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gram_rbf_kernel(const __grid_con
                     }
                     if (g.red[r].vec) {
                         rowsum[r] += sum;
-                        if (!diag) {
+                        if (mirror) {
                             // the mirror tile's rows: column sums of this tile
                             const float cs = transpose_reduce16(pv, lane);
                             const int col = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
@@ -512,7 +536,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gram_rbf_kernel(const __grid_con
                 if (g.red[r].vec) {
                     if (jok) atomicAdd(g.red[r].out + j, (double)rowsum[r]);
                 } else {
-                    tot[r] += (double)tsum[r] * (diag ? 1.0 : 2.0);
+                    tot[r] += (double)tsum[r] * (mirror ? 2.0 : 1.0);
                 }
             }
             ++tcount;
@@ -556,42 +580,53 @@ size_t kbuild_rbf_tc_scratch_bytes(int64_t n, int d) {
            (size_t)round_up((int64_t)kGP * n * ldx * 2, 1024);
 }
 
-cudaError_t launch_kbuild_rbf_tc(const void *X, int x_dtype, int64_t n, int d, double param, int zero_diag, float *K,
-                                 void *slices, int64_t ldp, int lead_bits, int planes, float *scales, int nred,
-                                 const int *red_pow, const int *red_vec, double *const *red_out, int upper_only,
-                                 void *scratch, int *err, cudaStream_t s) {
-    if (nred < 0 || nred > kGMaxRed || (slices && (planes < 3 || planes > 5)) || !X || !K || !scratch || d < 1 ||
-        d > 8 * kGBK || ((uintptr_t)scratch % 256) != 0 || (slices && ldp % 64 != 0))
-        return cudaErrorInvalidValue;
+namespace {
+
+// The scratch layout: X's row scales, squared norms and digit planes.
+struct GramScratch {
+    float *sx;
+    float2 *nrm;
+    __nv_bfloat16 *dig;
+    int ldx, lead_x;
+};
+
+GramScratch gram_scratch(void *scratch, int64_t n, int d) {
     const int64_t npad = round_up(n, kGT);
-    const int ldx = (int)round_up(d, kGBK);
+    GramScratch r;
+    r.ldx = (int)round_up(d, kGBK);
+    r.lead_x = split_lead_bits(r.ldx);
     char *p = (char *)scratch;
-    float *sx = (float *)p;
+    r.sx = (float *)p;
     p += round_up(npad * 4, 1024);
-    float2 *nrm = (float2 *)p;
+    r.nrm = (float2 *)p;
     p += round_up(npad * 8, 1024);
-    __nv_bfloat16 *dig = (__nv_bfloat16 *)p;
-    const int lead_x = split_lead_bits(ldx);
-    gram_xsplit_kernel<<<(unsigned)((npad + 7) / 8), 256, 0, s>>>(X, x_dtype, n, npad, d, ldx, lead_x, dig, sx, nrm,
-                                                                  err);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    r.dig = (__nv_bfloat16 *)p;
+    return r;
+}
+
+cudaError_t gram_launch(const GramScratch &gs, int64_t n, double param, int zero_diag, float *K, void *slices,
+                        int64_t ldp, int lead_bits, int planes, float *scales, int nred, const int *red_pow,
+                        const int *red_vec, double *const *red_out, int upper_only, int64_t row0, int64_t rows,
+                        int64_t col0, int64_t cols, int64_t srow0, int64_t splane, int *err, cudaStream_t s) {
     CUtensorMap map;
-    if (!make_map_planes(&map, dig, true, kGP, kGP, n, ldx, kGT, kGRowBytes)) return cudaErrorInvalidValue;
+    if (!make_map_planes(&map, gs.dig, true, kGP, kGP, n, gs.ldx, kGT, kGRowBytes)) return cudaErrorInvalidValue;
     static bool attr[64] = {false};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr[dev]) {
-        e = cudaFuncSetAttribute(gram_rbf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem);
+        cudaError_t e = cudaFuncSetAttribute(gram_rbf_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kGSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(gram_rbf_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem);
         if (e != cudaSuccess) return e;
         attr[dev] = true;
     }
     GramArgs g{};
     g.n = n;
-    g.num_k = ldx / kGBK;
-    g.lead_x = lead_x;
-    g.sx = sx;
-    g.nrm = nrm;
+    g.num_k = gs.ldx / kGBK;
+    g.lead_x = gs.lead_x;
+    g.sx = gs.sx;
+    g.nrm = gs.nrm;
     g.inv_h = (float)(1.0 / param);
     g.zero_diag = zero_diag;
     g.K = K;
@@ -608,12 +643,63 @@ cudaError_t launch_kbuild_rbf_tc(const void *X, int x_dtype, int64_t n, int d, d
     }
     g.err = err;
     g.wait_limit = tc_debug_wait_limit();
-    const int64_t T = npad / kGT;
-    const int64_t tiles = T * (T + 1) / 2;
+    g.row0 = row0;
+    g.rows = rows;
+    g.col0 = col0;
+    g.cols = cols;
+    g.srow0 = srow0;
+    g.splane = splane > 0 ? splane : n * g.ldp;
+    int64_t tiles;
+    if (rows > 0) {
+        tiles = ((rows + kGT - 1) / kGT) * ((cols + kGT - 1) / kGT);
+    } else {
+        const int64_t T = round_up(n, kGT) / kGT;
+        tiles = T * (T + 1) / 2;
+    }
     const int64_t S = sm_count();
     const int grid = (int)(tiles < S ? tiles : S);
-    gram_rbf_kernel<<<grid, kGThreads, kGSmem, s>>>(map, g);
+    if (rows > 0) gram_rbf_kernel<true><<<grid, kGThreads, kGSmem, s>>>(map, g);
+    else gram_rbf_kernel<false><<<grid, kGThreads, kGSmem, s>>>(map, g);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_gram_rbf_prep(const void *X, int x_dtype, int64_t n, int d, void *scratch, int *err,
+                                 cudaStream_t s) {
+    if (!X || !scratch || d < 1 || d > 8 * kGBK || ((uintptr_t)scratch % 256) != 0) return cudaErrorInvalidValue;
+    const GramScratch gs = gram_scratch(scratch, n, d);
+    const int64_t npad = round_up(n, kGT);
+    gram_xsplit_kernel<<<(unsigned)((npad + 7) / 8), 256, 0, s>>>(X, x_dtype, n, npad, d, gs.ldx, gs.lead_x, gs.dig,
+                                                                  gs.sx, gs.nrm, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gram_rbf_window(int64_t n, int d, double param, int zero_diag, float *K, void *slices,
+                                   int64_t ldp, int lead_bits, int planes, float *scales, int nred,
+                                   const int *red_pow, const int *red_vec, double *const *red_out, int64_t row0,
+                                   int64_t rows, int64_t col0, int64_t cols, int64_t srow0, int64_t splane,
+                                   void *scratch, int *err, cudaStream_t s) {
+    if (nred < 0 || nred > kGMaxRed || (slices && (planes < 3 || planes > 5)) || !scratch || d < 1 ||
+        d > 8 * kGBK || ((uintptr_t)scratch % 256) != 0 || (slices && ldp % 64 != 0) || rows < 1 || cols < 1 ||
+        row0 < 0 || col0 < 0 || row0 % kGT != 0 || col0 % kGT != 0 || row0 + rows > n || col0 + cols > n ||
+        (slices && (srow0 > row0 || splane < (row0 + rows - srow0) * ldp)))
+        return cudaErrorInvalidValue;
+    return gram_launch(gram_scratch(scratch, n, d), n, param, zero_diag, K, slices, ldp, lead_bits, planes, scales,
+                       nred, red_pow, red_vec, red_out, 0, row0, rows, col0, cols, srow0, splane, err, s);
+}
+
+cudaError_t launch_kbuild_rbf_tc(const void *X, int x_dtype, int64_t n, int d, double param, int zero_diag, float *K,
+                                 void *slices, int64_t ldp, int lead_bits, int planes, float *scales, int nred,
+                                 const int *red_pow, const int *red_vec, double *const *red_out, int upper_only,
+                                 void *scratch, int *err, cudaStream_t s) {
+    if (nred < 0 || nred > kGMaxRed || (slices && (planes < 3 || planes > 5)) || !X || !K || !scratch || d < 1 ||
+        d > 8 * kGBK || ((uintptr_t)scratch % 256) != 0 || (slices && ldp % 64 != 0))
+        return cudaErrorInvalidValue;
+    cudaError_t e = launch_gram_rbf_prep(X, x_dtype, n, d, scratch, err, s);
+    if (e != cudaSuccess) return e;
+    return gram_launch(gram_scratch(scratch, n, d), n, param, zero_diag, K, slices, ldp, lead_bits, planes, scales,
+                       nred, red_pow, red_vec, red_out, upper_only, 0, 0, 0, 0, 0, 0, err, s);
 }
 
 }  // namespace ustat

@@ -35,6 +35,21 @@ cudaError_t launch_kbuild_rbf_tc(const void *X, int x_dtype, int64_t n, int d, d
                                  void *slices, int64_t ldp, int lead_bits, int planes, float *scales, int nred,
                                  const int *red_pow, const int *red_vec, double *const *red_out, int upper_only,
                                  void *scratch, int *err, cudaStream_t s);
+// The same build in two parts, for the memory-lean evaluation: the prep (X's
+// digit planes, scales and norms into `scratch`, once per evaluation), then any
+// number of windows: the entries of rows row0 .. row0 + rows - 1 and columns
+// col0 .. col0 + cols - 1 (row0, col0 multiples of 128), each computed once (no
+// mirror).  K (may be null) and scales keep global indices (K[j * n + k],
+// scales[j]; the caller offsets pointers of buffers that hold only the window);
+// the digit planes hold row j at j - srow0 with plane stride splane elements;
+// reductions add every window entry once (vector reductions: row sums).
+cudaError_t launch_gram_rbf_prep(const void *X, int x_dtype, int64_t n, int d, void *scratch, int *err,
+                                 cudaStream_t s);
+cudaError_t launch_gram_rbf_window(int64_t n, int d, double param, int zero_diag, float *K, void *slices,
+                                   int64_t ldp, int lead_bits, int planes, float *scales, int nred,
+                                   const int *red_pow, const int *red_vec, double *const *red_out, int64_t row0,
+                                   int64_t rows, int64_t col0, int64_t cols, int64_t srow0, int64_t splane,
+                                   void *scratch, int *err, cudaStream_t s);
 // Linear kernel of a float32 X into a float64 K (float64-storage modes): the
 // double-float dot product, unrounded.
 cudaError_t launch_kbuild_linear_wide(const float *X, int64_t n, int d, double param, int zero_diag, double *K,
@@ -209,6 +224,16 @@ struct TcGemmArgs {
     // cycles (0: the default, about two seconds) and the stalled-producer test hook
     long long wait_limit;
     int debug_stall;
+    // window (memory-lean evaluation; rows = 0: the whole product): only rows
+    // row0 .. row0 + rows - 1 and columns col0 .. col0 + cols - 1 of the product,
+    // reductions only.  opA holds the digit planes of just those rows of A
+    // ([planes][rows][ldp]) and opB of those rows of B ([planes][cols][ldp]); every
+    // other array keeps global indices (scaleA[j], scaleB[k], W[j * n + k], the
+    // reduction vectors), so the caller offsets the pointers of arrays that hold
+    // only the window.  Symmetric needs row0 = col0 and rows = cols.  Every tile's
+    // reductions are multiplied by wscale (0: 1).
+    int64_t row0, col0, rows, cols;
+    double wscale;
 };
 // Test hook of the bounded waits (off by default): every later tensor-core GEMM
 // launch of this process uses `wait_limit` cycles (0 = default) as its wait limit

@@ -98,6 +98,20 @@ class Engine:
         o = out.cpu().numpy()
         return {"U_sum": float(o[0]), "U_mean": float(o[1]), "V": o[2:].copy()}
 
+    def evaluate_lean(self, X, panel_rows=4096):
+        """The memory-lean evaluation (ustat_eval_lean): no n x n factor or product is
+        stored; the factor rows are rebuilt from X in panels of panel_rows rows."""
+        X = self.to_device(X)
+        n, d = X.shape
+        ws = self.workspace(us.lean_workspace_bytes(self.plan, n, d, panel_rows))
+        out = torch.empty(2 + self.n_parts, dtype=torch.float64, device=self.device)
+        st = torch.cuda.current_stream(self.device).cuda_stream
+        us.ustat_eval_lean(self.plan, X.data_ptr(), 0 if X.dtype == torch.float64 else 1, n, d,
+                           self.factor_tuples(n), panel_rows, ws.data_ptr(), ws.numel(), st, out.data_ptr(),
+                           out.data_ptr() + 16)
+        o = out.cpu().numpy()
+        return {"U_sum": float(o[0]), "U_mean": float(o[1]), "V": o[2:].copy()}
+
     @staticmethod
     def reduce_shards(out, group=None):
         """The exchange step of a sharded evaluation: ``out`` (2 + Bell(m)

@@ -65,6 +65,8 @@ EXPORTS = {
     "ustat_workspace_bytes": (_i, [_vp, _i64, _i, _P(_sz)]),
     "ustat_status": (_i, [_vp, _vp, _P(_i)]),
     "ustat_factor_matrix": (_i, [_i, _d, _vp, _i64, _vp, _vp, _vp]),
+    "ustat_lean_workspace_bytes": (_i, [_vp, _i64, _i, _i64, _P(_sz)]),
+    "ustat_eval_lean": (_i, [_vp, _vp, _i, _i64, _i, _P(ustat_factor), _i, _i64, _vp, _sz, _vp, _vp, _vp]),
     "ustat_debug_set_wait": (_i, [ctypes.c_longlong, _i]),
     "ustat_scalar_count": (_i, [_vp, _P(_i)]),
     "ustat_eval_rows": (_i, [_vp, _i, _i, _vp, _i, _i64, _i, _P(ustat_factor), _i, _vp, _sz, _vp, _vp]),
@@ -394,6 +396,22 @@ def status(ws_ptr, stream):
     st = _i()
     _check(lib().ustat_status(ws_ptr, stream, ctypes.byref(st)), "ustat_status")
     return st.value
+
+
+def lean_workspace_bytes(plan, n, d, panel_rows):
+    """ustat_lean_workspace_bytes: the workspace of a memory-lean evaluation."""
+    s = _sz()
+    _check(lib().ustat_lean_workspace_bytes(plan.handle, int(n), int(d), int(panel_rows), ctypes.byref(s)),
+           "ustat_lean_workspace_bytes")
+    return s.value
+
+
+def ustat_eval_lean(plan, X_ptr, x_dtype, n, d, factors, panel_rows, ws_ptr, ws_bytes, stream, U_ptr, V_ptr):
+    """ustat_eval_lean: the evaluation with no n x n object stored (factor rows
+    rebuilt in panels of panel_rows rows); device pointers as ustat_eval."""
+    arr = factor_array(factors)
+    _check(lib().ustat_eval_lean(plan.handle, X_ptr, int(x_dtype), int(n), int(d), arr, len(factors),
+                                 int(panel_rows), ws_ptr, ws_bytes, stream, U_ptr, V_ptr), "ustat_eval_lean")
 
 
 def factor_matrix(kind, param, data_ptr, n, F_ptr, ws_ptr, stream):
