@@ -63,6 +63,10 @@ extern "C" {
                               Section 4.1 from their n x param dictionary terms        */
 #define USTAT_COMPLEMENT 7 /* F = 1 - A, data = A (device n x n float64, row-major):
                               the non-edge factor of the motif kernels, Section 4.2   */
+#define USTAT_GRAM      8  /* F(i,j) = sum_k P(i,k) P(j,k), data = P (device n x param
+                              float64, row-major): the symmetric HOIF factor g of
+                              Section 4.1; declared symmetric, so that the planner
+                              reads it untransposed and skips mirror product tiles  */
 
 /* ---- precision modes of the contractions ---- */
 #define USTAT_FP64    0  /* all arithmetic in float64 (CUDA cores)                          */
@@ -284,8 +288,9 @@ int ustat_eval_lean(ustat_plan_t *plan, const void *X, int x_dtype, int64_t n, i
  * arithmetic as the factor inside ustat_eval (the tensorization step of
  * Section 3.2: the factor tensor formed from the sample):
  *   kind  : USTAT_DIST (F(i,j) = ||y_i - y_j||, float64 coordinate differences),
- *           USTAT_LOWRANK (F(i,j) = sum_k P(i,k) Q(j,k), float64 products) or
- *           USTAT_COMPLEMENT (F = 1 - A); param and data as in ustat_factor
+ *           USTAT_LOWRANK (F(i,j) = sum_k P(i,k) Q(j,k), float64 products),
+ *           USTAT_GRAM (F(i,j) = sum_k P(i,k) P(j,k)) or USTAT_COMPLEMENT
+ *           (F = 1 - A); param and data as in ustat_factor
  *           (device float64, row-major)
  *   F     : device float64 n x n, row-major, every entry written (the diagonal too)
  *   ws    : device, at least 256 bytes, 256-byte aligned: its first word is reset
@@ -293,7 +298,7 @@ int ustat_eval_lean(ustat_plan_t *plan, const void *X, int x_dtype, int64_t n, i
  *           read by ustat_status(ws, stream, ...)
  * Asynchronous on stream; the caller owns every buffer.  Errors: INVALID_ARG
  * (another kind, a NULL pointer, ws not 256-byte aligned, n < 1, for DIST /
- * LOWRANK a param that is not an integer in [1, 4096]), UNSUPPORTED (n > 2^20),
+ * LOWRANK / GRAM a param that is not an integer in [1, 4096]), UNSUPPORTED (n > 2^20),
  * CUDA.
  */
 int ustat_factor_matrix(int kind, double param, const double *data, int64_t n, double *F, void *ws,

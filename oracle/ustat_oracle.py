@@ -42,7 +42,7 @@ import math
 import numpy as np
 
 # Factor kinds (plain integers; the same numbering is used by the input module).
-RBF, LINEAR, TANH_DOT, MATRIX, VECTOR, DIST, LOWRANK, COMPLEMENT = 0, 1, 2, 3, 4, 5, 6, 7
+RBF, LINEAR, TANH_DOT, MATRIX, VECTOR, DIST, LOWRANK, COMPLEMENT, GRAM = 0, 1, 2, 3, 4, 5, 6, 7, 8
 
 
 # --------------------------------------------------------------------------------------
@@ -132,7 +132,9 @@ def factor_tensor(kind: int, X: np.ndarray, param: float = 1.0, data=None) -> np
     LOWRANK:  T(i, j) = sum_k P(i, k) Q(j, k), data = [P | Q] with param = the
               number of columns of P (the HOIF factors, Section 4.1).
     COMPLEMENT: T = 1 - A, A = data (the motif kernels' non-edge factor,
-              Section 4.2)."""
+              Section 4.2).
+    GRAM:     T(i, j) = sum_k P(i, k) P(j, k), data = P with param = its number of
+              columns (the symmetric HOIF factor g, Section 4.1)."""
     X = np.asarray(X, dtype=np.float64)
     if kind == RBF:
         diff = X[:, None, :] - X[None, :, :]
@@ -154,6 +156,9 @@ def factor_tensor(kind: int, X: np.ndarray, param: float = 1.0, data=None) -> np
         return D[:, :r] @ D[:, r:2 * r].T
     if kind == COMPLEMENT:
         return 1.0 - np.asarray(data, dtype=np.float64)
+    if kind == GRAM:
+        D = np.asarray(data, dtype=np.float64)
+        return D[:, :int(param)] @ D[:, :int(param)].T
     raise ValueError(kind)
 
 

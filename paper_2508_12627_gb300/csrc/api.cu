@@ -294,11 +294,11 @@ int check_graph_factors(const Plan &P, const ustat_factor *f, int nf, int d) {
         int k = f[i].kind;
         if ((k == USTAT_RBF || k == USTAT_LINEAR) && !(f[i].param > 0.0)) return USTAT_ERR_INVALID_ARG;
         if ((k == USTAT_TANH_DOT || k == USTAT_MATRIX || k == USTAT_VECTOR || k == USTAT_DIST || k == USTAT_LOWRANK ||
-             k == USTAT_COMPLEMENT) &&
+             k == USTAT_COMPLEMENT || k == USTAT_GRAM) &&
             !f[i].data)
             return USTAT_ERR_INVALID_ARG;
-        // DIST and LOWRANK: param is the data's column count (a positive integer)
-        if ((k == USTAT_DIST || k == USTAT_LOWRANK) &&
+        // DIST, LOWRANK and GRAM: param is the data's column count (a positive integer)
+        if ((k == USTAT_DIST || k == USTAT_LOWRANK || k == USTAT_GRAM) &&
             !(f[i].param >= 1.0 && f[i].param <= 4096.0 && f[i].param == (double)(int)f[i].param))
             return USTAT_ERR_INVALID_ARG;
     }
@@ -406,7 +406,8 @@ int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f,
                 }
                 break;
             case OP_LOADMAT:
-                if (f[op.factor].kind == USTAT_DIST || f[op.factor].kind == USTAT_LOWRANK)
+                if (f[op.factor].kind == USTAT_DIST || f[op.factor].kind == USTAT_LOWRANK ||
+                    f[op.factor].kind == USTAT_GRAM)
                     e = launch_pairs(f[op.factor].kind, (const double *)f[op.factor].data, (int)f[op.factor].param, n,
                                      C.fp64, P.sparsify, C.ptr(op.out), err, C.st);
                 else
@@ -1251,7 +1252,7 @@ int ustat_plan_deserialize(const void *buf, size_t len, ustat_plan_t **out) {
         valid = pr.nscal >= 0 && pr.nscal <= kMaxScal;
         for (int q = 0; valid && q < pr.nscal; ++q) valid = pr.scal[q] >= 0 && pr.scal[q] < nslots;
     }
-    for (int k : P.factor_kind) valid = valid && k >= USTAT_RBF && k <= USTAT_COMPLEMENT;
+    for (int k : P.factor_kind) valid = valid && k >= USTAT_RBF && k <= USTAT_GRAM;
     if (!valid) {
         delete p;
         return USTAT_ERR_INVALID_ARG;
@@ -1307,7 +1308,7 @@ int ustat_factor_matrix(int kind, double param, const double *data, int64_t n, d
                         void *stream) {
     if (!data || !F || !ws || n < 1 || ((uintptr_t)ws & 255)) return USTAT_ERR_INVALID_ARG;
     if (n > (int64_t)1 << 20) return USTAT_ERR_UNSUPPORTED;
-    const bool pairs = kind == USTAT_DIST || kind == USTAT_LOWRANK;
+    const bool pairs = kind == USTAT_DIST || kind == USTAT_LOWRANK || kind == USTAT_GRAM;
     if (!pairs && kind != USTAT_COMPLEMENT) return USTAT_ERR_INVALID_ARG;
     if (pairs && !(param >= 1.0 && param <= 4096.0 && param == (double)(int)param)) return USTAT_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1742,7 +1743,7 @@ int batched_check(ustat_batched *b, const void *const *X, int x_dtype, const ust
     if (rc != USTAT_OK) return rc;
     for (int i = 0; i < nf; ++i)
         if (f[i].kind == USTAT_MATRIX || f[i].kind == USTAT_VECTOR || f[i].kind == USTAT_DIST ||
-            f[i].kind == USTAT_LOWRANK || f[i].kind == USTAT_COMPLEMENT)
+            f[i].kind == USTAT_LOWRANK || f[i].kind == USTAT_COMPLEMENT || f[i].kind == USTAT_GRAM)
             return USTAT_ERR_UNSUPPORTED;   // data of one size, not per sample
     for (size_t i = 0; i < b->n.size(); ++i)
         if (!X[i]) return USTAT_ERR_INVALID_ARG;

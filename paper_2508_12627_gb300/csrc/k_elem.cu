@@ -875,7 +875,8 @@ __global__ void diag_kernel(const T *M, int64_t n, double *out) {
 //     dictionary terms;
 //   PAIRS_DIST: F(i, j) = ||y_i - y_j|| from the coordinate differences, data = Y
 //     (n x r): the distance matrices of dCov (Section 4.3), diagonal exactly 0.
-enum { PAIRS_LOWRANK = 0, PAIRS_DIST = 1 };
+//   PAIRS_GRAM: F(i, j) = sum_k P(i, k) P(j, k), data = P (n x r); symmetric.
+enum { PAIRS_LOWRANK = 0, PAIRS_DIST = 1, PAIRS_GRAM = 2 };
 template <typename T>
 __global__ void __launch_bounds__(256) pairs_kernel(int mode, const double *__restrict__ D, int r, int64_t n,
                                                     int zero_diag, T *__restrict__ dst, int *err) {
@@ -902,7 +903,7 @@ __global__ void __launch_bounds__(256) pairs_kernel(int mode, const double *__re
         for (int q = 0; q < 4; ++q) {
             const int rr = ty + 8 * q;
             double a = acc[q];
-            if (mode == PAIRS_LOWRANK) {
+            if (mode != PAIRS_DIST) {
                 for (int k = 0; k < kc; ++k) a = fma(as[rr][k], bs[tx][k], a);
             } else {
                 for (int k = 0; k < kc; ++k) {
@@ -944,6 +945,8 @@ __global__ void factor_diag_kernel(int kind, double inv_param, const void *X, in
                 v = 1.0;
             } else if (kind == USTAT_LOWRANK) {
                 for (int k = 0; k < r; ++k) v = fma(Mc[i * 2 * r + k], Mc[i * 2 * r + r + k], v);
+            } else if (kind == USTAT_GRAM) {
+                for (int k = 0; k < r; ++k) v = fma(Mc[i * r + k], Mc[i * r + k], v);
             } else if (kind == USTAT_DIST) {
                 v = 0.0;
             } else if (kind == USTAT_COMPLEMENT) {
@@ -1131,8 +1134,8 @@ cudaError_t launch_loadmat(const double *src, int64_t n, bool fp64, int zero_dia
 
 cudaError_t launch_pairs(int kind, const double *data, int r, int64_t n, bool fp64, int zero_diag, void *dst,
                          int *err, cudaStream_t s) {
-    if (r < 1 || (kind != USTAT_LOWRANK && kind != USTAT_DIST)) return cudaErrorInvalidValue;
-    const int mode = kind == USTAT_LOWRANK ? PAIRS_LOWRANK : PAIRS_DIST;
+    if (r < 1 || (kind != USTAT_LOWRANK && kind != USTAT_DIST && kind != USTAT_GRAM)) return cudaErrorInvalidValue;
+    const int mode = kind == USTAT_LOWRANK ? PAIRS_LOWRANK : (kind == USTAT_GRAM ? PAIRS_GRAM : PAIRS_DIST);
     dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32)), block(32, 8);
     if (fp64) pairs_kernel<double><<<grid, block, 0, s>>>(mode, data, r, n, zero_diag, (double *)dst, err);
     else pairs_kernel<float><<<grid, block, 0, s>>>(mode, data, r, n, zero_diag, (float *)dst, err);

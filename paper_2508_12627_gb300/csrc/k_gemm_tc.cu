@@ -438,9 +438,10 @@ struct Cfg {
     static constexpr int kSmem = kStages * kStageBytes + 1024 + 512;
 };
 
-// Tile t of the schedule, in closed form.  Full grid: grouped raster (G tile
-// rows per group, column-major inside a group, so concurrently running CTAs share
-// A and B panels).  Symmetric: the upper triangle tm <= tn in row-major order.
+// Tile t of the schedule.  Full grid: grouped raster (G tile rows per group,
+// column-major inside a group, so concurrently running CTAs share A and B
+// panels), in closed form.  Symmetric: the tiles tm <= tn in the same grouped
+// order (a short loop over the groups).
 struct TileWalk {
     int tiles_m, tiles_n, symmetric, G, batch;
     __device__ int per_product() const {
@@ -455,16 +456,33 @@ struct TileWalk {
     }
     __device__ void coords1(int t, int &tm, int &tn) const {
         if (symmetric) {
-            // row r starts at off(r) = r T - r (r - 1) / 2
+            // the tiles on or above the diagonal in groups of G tile rows; inside a
+            // group column by column, each column's rows of the group (a triangle over
+            // the group's first G columns, then full columns), so that the CTAs of a
+            // wave share G A panels and a few B panels, as in the full-grid raster
             const int T = tiles_m;
-            const double b = 2.0 * T + 1.0;
-            int r = (int)((b - sqrt(b * b - 8.0 * t)) * 0.5);
-            if (r < 0) r = 0;
-            while (r > 0 && r * T - r * (r - 1) / 2 > t) --r;
-            while (r + 1 < T && (r + 1) * T - (r + 1) * r / 2 <= t) ++r;
-            tm = r;
-            tn = r + (t - (r * T - r * (r - 1) / 2));
-            return;
+            int r0 = 0;
+            for (;;) {
+                const int g = min(G, T - r0);
+                const int tri = g * (g + 1) / 2;
+                const int cnt = tri + g * (T - r0 - g);
+                if (t < cnt || r0 + g >= T) {
+                    if (t < tri) {
+                        int c = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+                        while (c > 0 && c * (c + 1) / 2 > t) --c;
+                        while ((c + 1) * (c + 2) / 2 <= t) ++c;
+                        tm = r0 + (t - c * (c + 1) / 2);
+                        tn = r0 + c;
+                    } else {
+                        const int v = t - tri;
+                        tm = r0 + v % g;
+                        tn = r0 + g + v / g;
+                    }
+                    return;
+                }
+                t -= cnt;
+                r0 += g;
+            }
         }
         const int per_group = G * tiles_n;
         const int group = t / per_group;

@@ -43,10 +43,10 @@ namespace {
 
 bool kind_pair(int k) {
     return k == USTAT_RBF || k == USTAT_LINEAR || k == USTAT_MATRIX || k == USTAT_DIST || k == USTAT_LOWRANK ||
-           k == USTAT_COMPLEMENT;
+           k == USTAT_COMPLEMENT || k == USTAT_GRAM;
 }
 bool kind_unary(int k) { return k == USTAT_TANH_DOT || k == USTAT_VECTOR; }
-bool kind_symmetric(int k) { return k == USTAT_RBF || k == USTAT_LINEAR || k == USTAT_DIST; }
+bool kind_symmetric(int k) { return k == USTAT_RBF || k == USTAT_LINEAR || k == USTAT_DIST || k == USTAT_GRAM; }
 bool kind_unit_diag(int k) { return k == USTAT_RBF; }
 
 int popc(uint32_t x) { return __builtin_popcount(x); }
@@ -454,7 +454,7 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan, const P
         P.tc_variant[c] = v;
     }
     for (int f = 0; f < g->n_factors; ++f)
-        if (P.factor_kind[f] < USTAT_RBF || P.factor_kind[f] > USTAT_COMPLEMENT) return USTAT_ERR_INVALID_ARG;
+        if (P.factor_kind[f] < USTAT_RBF || P.factor_kind[f] > USTAT_GRAM) return USTAT_ERR_INVALID_ARG;
     std::vector<int> covered(m, 0);
     for (int e = 0; e < g->n_edges; ++e) {
         int a = g->edge_src[e], b = g->edge_dst[e], f = g->edge_factor[e];
@@ -484,7 +484,8 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan, const P
         op.factor = f;
         int k = P.factor_kind[f];
         if (k == USTAT_RBF || k == USTAT_LINEAR) op.kind = OP_KBUILD;
-        else if (k == USTAT_MATRIX || k == USTAT_DIST || k == USTAT_LOWRANK || k == USTAT_COMPLEMENT)
+        else if (k == USTAT_MATRIX || k == USTAT_DIST || k == USTAT_LOWRANK || k == USTAT_COMPLEMENT ||
+                 k == USTAT_GRAM)
             op.kind = OP_LOADMAT;   // matrices from the caller's data
         else if (k == USTAT_TANH_DOT) op.kind = OP_UNARY;
         else op.kind = OP_LOADVEC;

@@ -8,12 +8,13 @@ dictionary phi, the estimator's terms are U-statistics of the chain kernels
     g(X_a, X_b) = A_a phi(Z_a)' A_b phi(Z_b),   f(X_a, X_b) = A_a phi(Z_a)' phi(Z_b) Y_b,
 
 a chain of j - 1 pairwise factors (signature ((1, 2), ..., (j - 1, j))).  The
-factors G = Psi Psi' (symmetric) and F = Psi Theta' (not symmetric), with
-Psi_i = A_i phi(Z_i) and Theta_i = phi(Z_i) Y_i, enter the engine as LOWRANK
-factors: only the n x k terms Psi and Theta are uploaded, and the library builds
-the n x n matrices on the device (the tensorization step); every U_sum is then
-one exact evaluation (all Bell(j) restricted V-statistics and the Moebius
-combination) on the device.
+factors G = Psi Psi' and F = Psi Theta', with Psi_i = A_i phi(Z_i) and
+Theta_i = phi(Z_i) Y_i, enter the engine as a GRAM factor (symmetric: the
+planner reads it untransposed and computes only the upper tiles of symmetric
+products) and a LOWRANK factor: only the n x k terms Psi and Theta are
+uploaded, and the library builds the n x n matrices on the device (the
+tensorization step); every U_sum is then one exact evaluation (all Bell(j)
+restricted V-statistics and the Moebius combination) on the device.
 """
 from __future__ import annotations
 
@@ -41,12 +42,12 @@ def chain_graph(j):
 
 
 def factor_terms(phi, A, Y):
-    """The data of the two LOWRANK factors (float64, n x 2k): [Psi | Psi] for
-    g = Psi Psi' and [Psi | Theta] for f = Psi Theta'."""
+    """The data of the two factors (float64): Psi (n x k) for the GRAM factor
+    g = Psi Psi', and [Psi | Theta] (n x 2k) for the LOWRANK factor f = Psi Theta'."""
     phi = np.asarray(phi, dtype=np.float64)
     Psi = np.asarray(A, dtype=np.float64)[:, None] * phi
     Theta = phi * np.asarray(Y, dtype=np.float64)[:, None]
-    return np.ascontiguousarray(np.hstack([Psi, Psi])), np.ascontiguousarray(np.hstack([Psi, Theta]))
+    return np.ascontiguousarray(Psi), np.ascontiguousarray(np.hstack([Psi, Theta]))
 
 
 def factor_matrices(phi, A, Y):
@@ -54,13 +55,14 @@ def factor_matrices(phi, A, Y):
     callers that hold the matrices themselves (the engine builds them from
     factor_terms)."""
     TG, TF = factor_terms(phi, A, Y)
-    k = TG.shape[1] // 2
-    return TG[:, :k] @ TG[:, k:].T, TF[:, :k] @ TF[:, k:].T
+    k = TG.shape[1]
+    return TG @ TG.T, TF[:, :k] @ TF[:, k:].T
 
 
 class HoifChains:
-    """Device copies of the n x 2k factor terms, one plan per chain length, one
-    workspace; the library builds G and F on the device in every evaluation."""
+    """Device copies of the factor terms (n x k and n x 2k), one plan per chain
+    length, one workspace; the library builds G and F on the device in every
+    evaluation."""
 
     def __init__(self, n, k=16, orders=(2, 3, 4, 5, 6, 7), precision="bf16x4", device="cuda:0"):
         self.n = n
@@ -70,18 +72,19 @@ class HoifChains:
         self.plans = {}
         for j in self.orders:
             g, names = chain_graph(j)
-            self.plans[j] = (us.Plan(g, [us.LOWRANK] * len(names), precision=precision), names)
+            kinds = [us.GRAM if s == "g" else us.LOWRANK for s in names]
+            self.plans[j] = (us.Plan(g, kinds, precision=precision), names)
         need = max(256, max(p.workspace_bytes(n, 1) for p, _ in self.plans.values()))
         self.ws = torch.empty(need, dtype=torch.uint8, device=self.device)
-        self.TG = torch.empty((n, 2 * k), dtype=torch.float64, device=self.device)
-        self.TF = torch.empty_like(self.TG)
+        self.TG = torch.empty((n, k), dtype=torch.float64, device=self.device)
+        self.TF = torch.empty((n, 2 * k), dtype=torch.float64, device=self.device)
         self.X = torch.zeros((n, 1), dtype=torch.float64, device=self.device)
         self.out = {j: torch.empty(2 + p.info["n_parts"], dtype=torch.float64, device=self.device)
                     for j, (p, _) in self.plans.items()}
 
     def set(self, TG, TF, non_blocking=False):
-        """The factor terms [Psi | Psi] and [Psi | Theta] (numpy or host / device
-        tensors, n x 2k float64)."""
+        """The factor terms Psi (n x k) and [Psi | Theta] (n x 2k) (numpy or host /
+        device tensors, float64)."""
         for dst, src in ((self.TG, TG), (self.TF, TF)):
             if not isinstance(src, torch.Tensor):
                 src = torch.from_numpy(np.ascontiguousarray(src, dtype=np.float64))
@@ -91,7 +94,8 @@ class HoifChains:
         """Enqueue U(h_j): out[j] = U_sum, U_mean, V_pi."""
         p, names = self.plans[j]
         st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
-        facs = [(us.LOWRANK, float(self.k), (self.TG if s == "g" else self.TF).data_ptr()) for s in names]
+        facs = [(us.GRAM, float(self.k), self.TG.data_ptr()) if s == "g" else
+                (us.LOWRANK, float(self.k), self.TF.data_ptr()) for s in names]
         o = self.out[j]
         us.ustat_eval(p, self.X.data_ptr(), 0, self.n, 1, facs, self.ws.data_ptr(), self.ws.numel(), st,
                       o.data_ptr(), o.data_ptr() + 16)

@@ -24,7 +24,7 @@ USTAT_ERR_CUDA = -6
 USTAT_ERR_DEVICE_TIMEOUT = -7
 USTAT_ERR_UNSUPPORTED = -8
 
-RBF, LINEAR, TANH_DOT, MATRIX, VECTOR, DIST, LOWRANK, COMPLEMENT = 0, 1, 2, 3, 4, 5, 6, 7
+RBF, LINEAR, TANH_DOT, MATRIX, VECTOR, DIST, LOWRANK, COMPLEMENT, GRAM = 0, 1, 2, 3, 4, 5, 6, 7, 8
 FP64, FP32, TF32, BF16X3, BF16X4, BF16X5 = 0, 1, 2, 3, 4, 5
 PLAN_EXHAUSTIVE, PLAN_MINFILL = 0, 1
 MAX_PARTS = 877   # Bell(7): partitions of the largest supported order m = 7
@@ -415,7 +415,7 @@ def ustat_eval_lean(plan, X_ptr, x_dtype, n, d, factors, panel_rows, ws_ptr, ws_
 
 
 def factor_matrix(kind, param, data_ptr, n, F_ptr, ws_ptr, stream):
-    """ustat_factor_matrix: the n x n float64 matrix of a DIST, LOWRANK or
+    """ustat_factor_matrix: the n x n float64 matrix of a DIST, LOWRANK, GRAM or
     COMPLEMENT factor (device pointers), built on the stream into F_ptr; the
     status word in ws_ptr (>= 256 bytes) is read by status()."""
     _check(lib().ustat_factor_matrix(int(kind), float(param), data_ptr, int(n), F_ptr, ws_ptr, stream),

@@ -29,6 +29,7 @@ VECTOR = 4     # caller-supplied length-n vector
 DIST = 5       # ||y_i - y_j|| between the rows of a caller-supplied n x p matrix Y
 LOWRANK = 6    # sum_k P(i, k) Q(j, k) from caller-supplied n x r matrices, data = [P | Q]
 COMPLEMENT = 7  # 1 - A for a caller-supplied n x n matrix A
+GRAM = 8       # sum_k P(i, k) P(j, k) from a caller-supplied n x r matrix P (symmetric)
 
 
 @dataclass

@@ -427,16 +427,16 @@ def test_input_dtype_and_alignment(eng_mod, prec):
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3", "bf16x4"])
 @pytest.mark.parametrize("n", [5, 130, 300])
 def test_device_built_factor_kinds(eng_mod, n, prec):
-    # the factors the library builds from caller data (DIST, LOWRANK, COMPLEMENT) on
-    # a 4-vertex kernel graph that uses all three, with a ragged tail, against the
-    # oracle's definitions of the same factors
+    # the factors the library builds from caller data (DIST, LOWRANK, COMPLEMENT,
+    # GRAM) on a 4-vertex kernel graph that uses all four, with a ragged tail,
+    # against the oracle's definitions of the same factors
     rng = np.random.default_rng(40 + n)
     Y = rng.standard_normal((n, 5))
     PQ = rng.uniform(0.2, 1.0, (n, 6))
     A = (rng.random((n, n)) < 0.3).astype(float)
     facs = [synth.Factor(synth.DIST, 5.0, Y), synth.Factor(synth.LOWRANK, 3.0, PQ),
-            synth.Factor(synth.COMPLEMENT, 1.0, A)]
-    g = synth.Graph(4, [(0, 1, 0), (1, 2, 1), (2, 3, 2), (3, 0, 1), (0, 2, 0)], [])
+            synth.Factor(synth.COMPLEMENT, 1.0, A), synth.Factor(synth.GRAM, 4.0, PQ[:, 1:5].copy())]
+    g = synth.Graph(4, [(0, 1, 0), (1, 2, 1), (2, 3, 2), (3, 0, 1), (0, 2, 0), (1, 3, 3)], [])
     X = np.zeros((n, 1))
     ref, absref = uo.ustat(g, facs, X), uo.ustat(g, facs, X, absolute=True)
     out = eng_mod.Engine(g, facs, precision=prec).evaluate(X)
@@ -455,7 +455,8 @@ def test_factor_matrix_entry_point(eng_mod, n):
     A = (rng.random((n, n)) < 0.3).astype(float)
     ws = torch.empty(256, dtype=torch.uint8, device="cuda")
     st = torch.cuda.current_stream().cuda_stream
-    for kind, param, data in [(us.DIST, 5.0, Y), (us.LOWRANK, 3.0, PQ), (us.COMPLEMENT, 1.0, A)]:
+    for kind, param, data in [(us.DIST, 5.0, Y), (us.LOWRANK, 3.0, PQ), (us.COMPLEMENT, 1.0, A),
+                              (us.GRAM, 4.0, PQ[:, 1:5].copy())]:
         dd = torch.from_numpy(np.ascontiguousarray(data)).cuda()
         F = torch.full((n, n), float("nan"), dtype=torch.float64, device="cuda")
         us.factor_matrix(kind, param, dd.data_ptr(), n, F.data_ptr(), ws.data_ptr(), st)
@@ -466,8 +467,13 @@ def test_factor_matrix_entry_point(eng_mod, n):
             assert np.array_equal(got, want)
         else:
             # a sum of r float64 terms in another order: a few ulps of the scale
-            scale = (np.abs(Y) ** 2).sum(1).max() ** 0.5 * 2 if kind == us.DIST else \
-                np.abs(PQ[:, :3]).max(1)[:, None] * np.abs(PQ[:, 3:]).max(1)[None, :] * 3
+            if kind == us.DIST:
+                scale = (np.abs(Y) ** 2).sum(1).max() ** 0.5 * 2
+            elif kind == us.LOWRANK:
+                scale = np.abs(PQ[:, :3]).max(1)[:, None] * np.abs(PQ[:, 3:]).max(1)[None, :] * 3
+            else:
+                scale = 4 * np.abs(data).max() ** 2
+                assert np.array_equal(got, got.T)   # declared symmetric: exactly
             assert np.all(np.abs(got - want) <= 1e-14 * scale), kind
     # a NaN in the data: the status word says so
     Y[n // 2, 1] = np.nan

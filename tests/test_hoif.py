@@ -34,11 +34,11 @@ def test_factor_matrices_follow_the_definitions():
     from paper_2508_12627_gb300 import hoif
     phi, A, Y = synth.hoif_sample(40, k=5, seed=3)
     G, F = hoif.factor_matrices(phi, A, Y)
-    # the device factors' data: [Psi | Psi] and [Psi | Theta], whose low-rank
-    # products (the oracle's LOWRANK definition) are g and f
+    # the device factors' data: Psi and [Psi | Theta], whose products (the
+    # oracle's GRAM and LOWRANK definitions) are g and f
     TG, TF = hoif.factor_terms(phi, A, Y)
-    assert TG.shape == (40, 10) and TF.shape == (40, 10)
-    assert np.allclose(uo.factor_tensor(uo.LOWRANK, np.zeros((40, 1)), 5, TG), G, rtol=1e-13, atol=1e-13)
+    assert TG.shape == (40, 5) and TF.shape == (40, 10)
+    assert np.allclose(uo.factor_tensor(uo.GRAM, np.zeros((40, 1)), 5, TG), G, rtol=1e-13, atol=1e-13)
     assert np.allclose(uo.factor_tensor(uo.LOWRANK, np.zeros((40, 1)), 5, TF), F, rtol=1e-13, atol=1e-13)
     for a, b in [(0, 1), (3, 3), (7, 2), (39, 11)]:
         assert abs(G[a, b] - A[a] * A[b] * phi[a] @ phi[b]) <= 1e-12 * (1 + abs(G[a, b]))

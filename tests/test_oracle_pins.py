@@ -414,7 +414,7 @@ def test_einsum_notation_sequence_of_k4():
 def test_device_built_factor_kinds_by_hand():
     # DIST: points on a line at 0, 1, 3 -> |i - j|; points at the corners of a unit
     # square -> 1 and sqrt 2.  LOWRANK: [P | Q] gives P Q'; rank one gives the outer
-    # product.  COMPLEMENT: 1 - A.
+    # product.  COMPLEMENT: 1 - A.  GRAM: P P' by hand.
     D = uo.factor_tensor(uo.DIST, np.zeros((3, 1)), 1, np.array([[0.0], [1.0], [3.0]]))
     assert np.array_equal(D, np.array([[0, 1, 3], [1, 0, 2], [3, 2, 0]], dtype=float))
     sq = uo.factor_tensor(uo.DIST, np.zeros((4, 1)), 2, np.array([[0.0, 0], [1, 0], [0, 1], [1, 1]]))
@@ -428,3 +428,7 @@ def test_device_built_factor_kinds_by_hand():
     assert L2[2, 1] == P[2, 0] * Q[1, 0] + P[2, 1] * Q[1, 1]
     A = np.array([[0.0, 1.0], [1.0, 0.0]])
     assert np.array_equal(uo.factor_tensor(uo.COMPLEMENT, np.zeros((2, 1)), 1, A), np.array([[1.0, 0], [0, 1]]))
+    # GRAM: P P', the squared row norms on the diagonal; the first `param` columns only
+    Gm = uo.factor_tensor(uo.GRAM, np.zeros((3, 1)), 2, P)
+    assert np.array_equal(Gm, np.array([[1.0, 3, 5], [3, 13, 23], [5, 23, 41]]))
+    assert np.array_equal(uo.factor_tensor(uo.GRAM, np.zeros((3, 1)), 1, P), np.outer(P[:, 0], P[:, 0]))
