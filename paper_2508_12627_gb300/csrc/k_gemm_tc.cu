@@ -432,7 +432,9 @@ struct Cfg {
     static constexpr int kBTile = kBN * kRowBytes;          // one plane of B
     static constexpr int kStageBytes = kPlanes * (kATile + kBTile);
     static constexpr int kStages = kTf32 ? 6 : (kMode == 3 ? 3 : (kMode == 4 ? 4 : (kMode == 5 ? 3 : 2)));
-    static constexpr int kBufs = kWide ? 1 : 2;             // accumulator sets
+    // accumulator sets: two (one tile's epilogue beside the next tile's MMAs)
+    // wherever they fit the 512 TMEM columns
+    static constexpr int kBufs = (kWide && kBN == kBM) ? 1 : 2;
     static constexpr int kAccCols = kTf32 ? kBN : (kWide ? 4 * kBN : 2 * kBN);   // hi (+ mid0, mid1) (+ lo)
     static constexpr int kTmemCols = kBufs * kAccCols;
     static constexpr int kSmem = kStages * kStageBytes + 1024 + 512;

@@ -9,6 +9,8 @@
 // shared memory so that every global read is a 128-byte row segment.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "kcommon.cuh"
 #include "kernels.h"
 
@@ -213,6 +215,117 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) mhb_kernel(MhbArg
     }
 }
 
+// The terminal reduction sum_ij prod_t term_t(i, j) a(i) b(j) with transposed
+// terms, on 64 x 64 tiles: the distinct untransposed matrices are read by each
+// thread straight from global memory (16-byte loads along rows), the distinct
+// transposed ones (term M^T: M[j][i]) are read the same way as their mirror tile
+// (rows J, columns I) into shared memory, and each thread forms its 16 entries
+// (four rows, four consecutive columns) with every term raised to its
+// multiplicity.  Each row's four products times b(j) are summed in the storage
+// type and then added in float64 times a(i): one float64 operation per four
+// entries (this part's float64 pipe is a small fraction of its float32 rate).
+struct FredArgs {
+    const void *P[4];   // untransposed distinct matrices
+    int pe[4];          // their multiplicities
+    int np;
+    const void *Q[2];   // transposed distinct matrices
+    int qe[2];
+    int nq;
+    int64_t n;
+    const double *a, *b;
+    double *out;
+};
+
+constexpr int kFT = 64;   // tile edge
+
+template <typename T, bool kVec>
+__global__ void __launch_bounds__(256) fred_kernel(FredArgs g) {
+    extern __shared__ __align__(16) unsigned char fred_smem[];
+    T(*sq)[kFT][kFT + 1] = reinterpret_cast<T(*)[kFT][kFT + 1]>(fred_smem);
+    const int t = threadIdx.x;
+    const int rr = t >> 4;          // rows rr + 16 k of the tile
+    const int cc = (t & 15) * 4;    // columns cc .. cc + 3
+    const int64_t n = g.n;
+    const int64_t NT = (n + kFT - 1) / kFT;
+    double acc = 0.0;
+    for (int64_t tile = blockIdx.x; tile < NT * NT; tile += gridDim.x) {
+        const int64_t i0 = (tile / NT) * kFT, j0 = (tile % NT) * kFT;
+        // four consecutive entries of row `row`, from column `col` on (zero outside)
+        auto load4 = [&](const T *M, int64_t row, int64_t col, T (&v)[4]) {
+            if (row < n && kVec && col + 3 < n) {
+                if constexpr (sizeof(T) == 4) {
+                    const float4 x = *reinterpret_cast<const float4 *>(M + row * n + col);
+                    v[0] = x.x, v[1] = x.y, v[2] = x.z, v[3] = x.w;
+                } else {
+                    const double2 x0 = *reinterpret_cast<const double2 *>(M + row * n + col);
+                    const double2 x1 = *reinterpret_cast<const double2 *>(M + row * n + col + 2);
+                    v[0] = x0.x, v[1] = x0.y, v[2] = x1.x, v[3] = x1.y;
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) v[e] = (row < n && col + e < n) ? M[row * n + col + e] : T(0);
+            }
+        };
+        // the product of the untransposed terms, straight from global memory
+        T v[4][4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[k][e] = T(1);
+        for (int p = 0; p < g.np; ++p) {
+            const T *M = (const T *)g.P[p];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                T x[4];
+                load4(M, i0 + rr + 16 * k, j0 + cc, x);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    T f = x[e];
+                    for (int q = 1; q < g.pe[p]; ++q) f *= x[e];
+                    v[k][e] *= f;
+                }
+            }
+        }
+        // the mirror tiles of the transposed terms into shared memory
+        __syncthreads();   // the previous tile's reads are done
+        for (int q = 0; q < g.nq; ++q) {
+            const T *M = (const T *)g.Q[q];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                T x[4];
+                load4(M, j0 + rr + 16 * k, i0 + cc, x);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) sq[q][rr + 16 * k][cc + e] = x[e];
+            }
+        }
+        __syncthreads();
+        T bj[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int64_t j = j0 + cc + e;
+            bj[e] = j < n ? (g.b ? (T)g.b[j] : T(1)) : T(0);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t i = i0 + rr + 16 * k;
+            if (i >= n) continue;
+            T row = T(0);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                T f = v[k][e];
+                for (int q = 0; q < g.nq; ++q) {
+                    const T y = sq[q][cc + e][rr + 16 * k];   // M_q[j][i]
+                    for (int r = 0; r < g.qe[q]; ++r) f *= y;
+                }
+                row = fma(f, bj[e], row);
+            }
+            acc = fma((double)row, g.a ? g.a[i] : 1.0, acc);
+        }
+    }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) atomicAdd(g.out, s);
+}
+
 }  // namespace
 
 cudaError_t launch_mhb(const MhbArgs &g0, bool fp64, cudaStream_t s) {
@@ -241,8 +354,75 @@ cudaError_t launch_mhb(const MhbArgs &g0, bool fp64, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+namespace {
+
+// FREDUCE with transposed terms on the 64 x 64 tile kernel: the terms grouped into
+// distinct matrices with multiplicities; false where it does not apply (more than
+// two distinct transposed matrices, or none)
+bool launch_fred(const TileTerms &tt, bool fp64, int64_t n, const double *a, const double *b, double *out,
+                 cudaStream_t s, cudaError_t *err) {
+    FredArgs g{};
+    for (int t = 0; t < tt.nt; ++t) {
+        const bool tr = tt.trans[t] != 0;
+        const void **L = tr ? g.Q : g.P;
+        int *E = tr ? g.qe : g.pe;
+        int &cnt = tr ? g.nq : g.np;
+        int f = -1;
+        for (int q = 0; q < cnt; ++q)
+            if (L[q] == tt.M[t]) f = q;
+        if (f < 0) {
+            if (cnt == (tr ? 2 : 4)) return false;
+            L[cnt] = tt.M[t];
+            E[cnt] = 0;
+            f = cnt++;
+        }
+        E[f]++;
+    }
+    if (g.nq == 0) return false;
+    g.n = n;
+    g.a = a;
+    g.b = b;
+    g.out = out;
+    const size_t smem = (size_t)g.nq * kFT * (kFT + 1) * (fp64 ? 8 : 4);
+    static bool attr[64] = {false};
+    int dev = 0;
+    if ((*err = cudaGetDevice(&dev)) != cudaSuccess) return true;
+    if (dev < 0 || dev >= 64) {
+        *err = cudaErrorInvalidDevice;
+        return true;
+    }
+    if (!attr[dev]) {
+        const int big = 2 * kFT * (kFT + 1) * 8;
+        const void *fns[] = {(const void *)fred_kernel<float, true>, (const void *)fred_kernel<float, false>,
+                             (const void *)fred_kernel<double, true>, (const void *)fred_kernel<double, false>};
+        for (const void *f : fns)
+            if ((*err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess)
+                return true;
+        attr[dev] = true;
+    }
+    const int64_t NT = (n + kFT - 1) / kFT;
+    const int64_t tiles = NT * NT;
+    const int grid = (int)std::min<int64_t>(tiles, 152 * 6);
+    const bool vec = n % 4 == 0;
+    if (fp64) {
+        if (vec) fred_kernel<double, true><<<grid, 256, smem, s>>>(g);
+        else fred_kernel<double, false><<<grid, 256, smem, s>>>(g);
+    } else {
+        if (vec) fred_kernel<float, true><<<grid, 256, smem, s>>>(g);
+        else fred_kernel<float, false><<<grid, 256, smem, s>>>(g);
+    }
+    *err = cudaGetLastError();
+    return true;
+}
+
+}  // namespace
+
 cudaError_t launch_tile_op(int mode, const TileTerms &tt, bool fp64, int64_t n, const double *a, const double *b,
                            void *out, cudaStream_t s) {
+    if (mode == TILE_FREDUCE) {
+        cudaError_t e = cudaSuccess;
+        if (launch_fred(tt, fp64, n, a, b, (double *)out, s, &e)) return e;
+    }
     const int64_t nt = (n + 31) / 32;
     int64_t gy = (152 * 8 + nt - 1) / nt;
     if (mode == TILE_HADAMARD) gy = nt;

@@ -371,6 +371,17 @@ def test_gemm_tile_variants(eng_mod, name, n, prec, shape):
         _compare(out, ref, absref, tol_for(name, prec, n), (name, prec, shape, gr))
 
 
+def test_wide_narrow_tiles_double_buffered(eng_mod):
+    # bf16x4 with 128 x 64 tiles keeps two accumulator sets in TMEM: at n = 2500 a
+    # CTA runs several tiles, so both sets and their barriers are used
+    w = synth.workload("c4_rbf", 2500)
+    ref, absref = _oracle(w)
+    eng = eng_mod.Engine(w.graph, w.factors, precision="bf16x4")
+    eng.plan.set_variant(0)
+    out = eng.evaluate(w.X)
+    _compare(out, ref, absref, 1e-8, "c4 n=2500 bf16x4 shape 0")
+
+
 @pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
 @pytest.mark.parametrize("name,n", [("c4_rbf", 5), ("c4_rbf", 63), ("c4_rbf", 65), ("c4_rbf", 129), ("c4_rbf", 300),
                                     ("triangle_rbf", 200), ("k4_cycle_rbf", 72)])
