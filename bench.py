@@ -326,11 +326,13 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
-def batched_measure(precision, dev, steps, warmup, full_line):
+def batched_measure(precision, dev, steps, warmup, full_line, grouped=None):
     """The batched workload: every step replays two captured graphs (4-cycle and
     5-cycle plans over the same 512 samples), after the autotuner has chosen the
-    lane count and the GEMM tile variants.  Returns the bench line (full_line),
-    or a short summary for the per-configuration table."""
+    lane count and the GEMM tile variants.  In bf16x3 the batched object runs in
+    its grouped form (each product step one persistent launch over all 512
+    samples' tiles; grouped=False: the lane form).  Returns the bench line
+    (full_line), or a short summary for the per-configuration table."""
     import numpy as np
     import torch
 
@@ -355,9 +357,13 @@ def batched_measure(precision, dev, steps, warmup, full_line):
     stream = torch.cuda.Stream(dev)
     runs = {}
     tune = {}
+    if grouped is None:
+        grouped = args.precision == "bf16x3"
     for name, g in graphs.items():
         p = us.Plan(g, [synth.RBF], precision=args.precision)
         b = us.Batched(p, ns, d, max_lanes=16)
+        if grouped:
+            b.set_grouped(True)
         ws = torch.empty(b.workspace_bytes(), dtype=torch.uint8, device=dev)
         U = torch.empty((len(ns), 2), dtype=torch.float64, device=dev)
         V = torch.empty((len(ns), p.info["n_parts"]), dtype=torch.float64, device=dev)
@@ -366,7 +372,8 @@ def batched_measure(precision, dev, steps, warmup, full_line):
                                    V.data_ptr())
             b.capture(xp, 0, facs, ws.data_ptr(), ws.numel(), stream.cuda_stream, U.data_ptr(), V.data_ptr())
         tv = [l for l in p.describe().splitlines() if l.startswith("tc_variant=")]
-        tune[name] = {"lanes": lanes, "tuned_ms": ms, "gemm_variants_by_size_class": tv[0][11:] if tv else None}
+        tune[name] = {"lanes": lanes, "tuned_ms": ms, "gemm_variants_by_size_class": tv[0][11:] if tv else None,
+                      "form": "grouped" if grouped else "lanes", "workspace_gb": ws.numel() / 1e9}
         runs[name] = (p, b, ws, U, V)
     torch.cuda.synchronize()
 
@@ -439,7 +446,9 @@ def batched_measure(precision, dev, steps, warmup, full_line):
     if not full_line:
         return {"workload": WORKLOADS["batched"], "precision": args.precision, "evals_per_s": value,
                 "ms_per_step": tot_ms / args.steps, "evals_per_step": evals, "steps": args.steps,
-                "launch": "two CUDA graph replays per step (one per kernel graph), autotuned lanes and GEMM variants",
+                "launch": "two CUDA graph replays per step (one per kernel graph), autotuned lanes and GEMM variants; "
+                          + ("each product step one persistent launch over all samples' tiles" if grouped
+                             else "samples on stream lanes"),
                 "tuning": tune, "roofline": roof, "rel_err_vs_oracle": err}
 
     # end to end: pinned host X -> device, both graphs, U and V back to the host
@@ -477,13 +486,18 @@ def batched_measure(precision, dev, steps, warmup, full_line):
         "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": WORKLOADS["batched"], "samples": len(ns), "d": d, "precision": args.precision,
                    "l2": "inputs and kernel matrices far larger than L2", "parallelism": "single",
+                   "launch": "two CUDA graph replays per step; " + (
+                       "each product step one persistent launch over all samples' tiles, the other steps per "
+                       "sample on stream lanes" if grouped else "samples on stream lanes"),
                    "tuning": tune},
         "tflops": {"algorithmic_plan": fl_plan * args.steps / (tot_ms / 1e3) / 1e12},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": evals / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": int(host.numel() * 8),
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": int(args.steps * sum((r[0].info["n_ops"] + 2) * len(ns) for r in runs.values())),
+        "gpu_launches": int(args.steps * sum(
+            (r[0].info["n_ops"] - (r[0].info["n_gemm"] if grouped else 0) + 2) * len(ns)
+            + (r[0].info["n_gemm"] if grouped else 0) for r in runs.values())),
         "clocks": clk,
         "rel_err_vs_oracle": err,
         "wall_s_timed_region": wall,

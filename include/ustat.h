@@ -399,6 +399,21 @@ int ustat_batched_workspace_bytes(const ustat_batched_t *b, size_t *bytes);
 /* lanes in use; lane_of[i] (may be NULL) receives sample i's lane */
 int ustat_batched_info(const ustat_batched_t *b, int *lanes, int *lane_of);
 int ustat_batched_set_lanes(ustat_batched_t *b, int lanes);
+/*
+ * Grouped form (bf16x3 plans; grouped = 1 on, 0 back to the lane form): every
+ * sample gets its own workspace region (ustat_batched_workspace_bytes grows to
+ * the sum of the samples' workspaces plus the group images), the plan runs step
+ * by step over all samples, and each s = 2 product step is ONE persistent
+ * tensor-core launch over the tiles of all samples' products (largest samples
+ * first), each sample's reductions added to its own scalars; the other steps run
+ * per sample on the lanes.  The group images (per sample: tensor maps and product
+ * arguments, in the workspace) are written by the first run or capture on a
+ * workspace, and again when the workspace or a variant changes: that call copies
+ * them from the host and synchronises the stream, before any capture.  Drops a
+ * captured graph.  Same results as the lane form up to the order of the
+ * reductions' float64 additions.  Errors: UNSUPPORTED for other precisions.
+ */
+int ustat_batched_set_grouped(ustat_batched_t *b, int grouped);
 int ustat_batched_run(ustat_batched_t *b, const void *const *X, int x_dtype, const ustat_factor *factors,
                       int n_factors, void *ws, size_t ws_bytes, void *stream, double *U_out, double *V_out);
 int ustat_batched_capture(ustat_batched_t *b, const void *const *X, int x_dtype,

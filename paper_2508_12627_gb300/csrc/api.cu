@@ -345,355 +345,405 @@ bool row_shard_slots(const Plan &P, std::vector<char> &sharded) {
     return true;
 }
 
-int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f, double *U_out, double *V_out,
-                double *scal_out = nullptr) {
+// The per-evaluation state every step reads: the error word, whether the RBF
+// builds read the caller's X directly, the split width and the diagonal
+// correction of the plan's split slots.
+struct ProgState {
+    int *err = nullptr;
+    bool direct_x = false;
+    int lead = 0;
+    DiagFix D;
+};
+
+// Clears the evaluation's scalars and vectors and converts X where a step needs it.
+int program_prologue(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f, ProgState &S) {
     const Plan &P = C.P;
     const int64_t n = C.n;
     cudaError_t e = cudaMemsetAsync(C.ws, 0, C.L.zero_bytes, C.st);
     if (e != cudaSuccess) return cuda_fail(e);
-    int *err = (int *)(C.ws + C.L.err_off);
+    S.err = (int *)(C.ws + C.L.err_off);
     // float32 storage with RBF builds only: they read the caller's X directly
-    bool direct_x = !C.fp64;
+    S.direct_x = !C.fp64;
     for (const Op &op : P.ops)
-        if (op.kind == OP_KBUILD && f[op.factor].kind != USTAT_RBF) direct_x = false;
-    if (needs_xw(P) && !direct_x) {
+        if (op.kind == OP_KBUILD && f[op.factor].kind != USTAT_RBF) S.direct_x = false;
+    if (needs_xw(P) && !S.direct_x) {
         ProfScope ps(kProfXconvert, C.st);
-        e = launch_xconvert(X, x_dtype, n, C.d, C.ws + C.L.xw_off, C.fp64, err, C.st);
+        e = launch_xconvert(X, x_dtype, n, C.d, C.ws + C.L.xw_off, C.fp64, S.err, C.st);
         if (e != cudaSuccess) return cuda_fail(e);
     }
-    const int lead = split_lead_bits(n);
-    const DiagFix D = diag_fix_of(P, n);
-    for (const Op &op : P.ops) {
-        ProfScope ps(op.kind, C.st);
-        switch (op.kind) {
-            case OP_KBUILD:
-                if (!C.fp64 && f[op.factor].kind == USTAT_RBF) {
-                    int rpow[kMaxRed], rvec[kMaxRed];
-                    double *rout[kMaxRed];
-                    for (int r = 0; r < op.nred; ++r) {
-                        rpow[r] = op.red[r].pow;
-                        rvec[r] = P.slots[op.red[r].out].kind == S_VEC;
-                        rout[r] = C.vec(op.red[r].out);   // scalar and vector slots are float64
-                    }
-                    const int var = P.tc_variant[tc_size_class(n)];
-                    if (!((var >> 5) & 1) && C.d <= 256) {
-                        // default: squared distances from the Gram matrix on the tensor cores
-                        e = launch_kbuild_rbf_tc(X, x_dtype, n, C.d, f[op.factor].param, P.sparsify,
-                                                 (float *)C.ptr(op.out), op.opA >= 0 ? C.ptr(op.opA) : nullptr,
-                                                 C.L.ldp_slices, lead, split_planes_of(P.precision),
-                                                 op.opA >= 0 ? C.scales(op.opA) : nullptr, op.nred, rpow, rvec, rout,
-                                                 op.upper_only, C.ws + C.L.kb_off, err, C.st);
-                        ps.kernels = 2;
-                        break;
-                    }
-                    // variant bit 5: direct differences on the CUDA cores
-                    const float *xf = direct_x ? (x_dtype == 1 ? (const float *)X : nullptr)
-                                               : (const float *)(C.ws + C.L.xw_off);
-                    const double *xd = direct_x && x_dtype == 0 ? (const double *)X : nullptr;
-                    e = launch_kbuild_rbf(xf, xd, n, C.d, f[op.factor].param, P.sparsify,
-                                          (float *)C.ptr(op.out), op.opA >= 0 ? C.ptr(op.opA) : nullptr,
-                                          C.L.ldp_slices, lead, split_planes_of(P.precision),
-                                          op.opA >= 0 ? C.scales(op.opA) : nullptr, op.nred, rpow, rvec, rout,
-                                          op.upper_only, (var >> 4) & 1, err, C.st);
-                } else {
-                    if (op.nred) return USTAT_ERR_UNSUPPORTED;   // the planner fuses only into the RBF build
-                    if (C.fp64 && f[op.factor].kind == USTAT_LINEAR && x_dtype == 1)
-                        e = launch_kbuild_linear_wide((const float *)X, n, C.d, f[op.factor].param, P.sparsify,
-                                                      (double *)C.ptr(op.out), C.st);
-                    else
-                        e = launch_kbuild(f[op.factor].kind, f[op.factor].param, C.ws + C.L.xw_off, C.fp64, n, C.d,
-                                          P.sparsify, C.ptr(op.out), C.st);
+    S.lead = split_lead_bits(n);
+    S.D = diag_fix_of(P, n);
+    return USTAT_OK;
+}
+
+// The tensor-core GEMM arguments of one product step on one evaluation's
+// workspace (all but the tile shape), and the shape its size class selects.
+void tc_gemm_args(const Ctx &C, const Op &op, const ProgState &S, TcGemmArgs &g, int &shape) {
+    const Plan &P = C.P;
+    const int64_t n = C.n;
+    int *err = S.err;
+    const int lead = S.lead;
+    const DiagFix &D = S.D;
+    auto trW = [&](const Term &t) { return (t.mat >= 0 && !P.slots[t.mat].symmetric) ? t.trans : 0; };
+    const bool split = is_split_mode(P.precision);
+    g = TcGemmArgs{};
+    g.n = n;
+    g.ldp = split ? C.L.ldp_slices : C.L.ldp_prep;
+    g.opA = C.ptr(op.opA);
+    g.opB = C.ptr(op.opB);
+    g.scaleA = split ? C.scales(op.opA) : nullptr;
+    g.scaleB = split ? C.scales(op.opB) : nullptr;
+    g.lead_bits = lead;
+    g.err = err;
+    g.C = op.store ? C.ptr(op.out) : nullptr;
+    g.wide = C.fp64;
+    g.nred = op.nred;
+    for (int r = 0; r < op.nred; ++r) {
+        const Red &R = op.red[r];
+        g.red[r] = TcRed{C.ptr(R.W.mat), trW(R.W), C.vec(R.a), C.vec(R.b), R.pow,
+                         (double *)C.ptr(R.out)};
+    }
+    g.symmetric = op.symmetric;
+    if (C.nranks > 1 && !op.store) {
+        g.shard_rank = C.rank;
+        g.shard_count = C.nranks;
+    }
+    if (split && op.opA >= 0 && op.opB >= 0 && (D.removed[op.opA] || D.removed[op.opB])) {
+        // operands split without their diagonal: the epilogue adds the
+        // left-out terms from the operands' sources
+        const Op &sa = P.ops[D.split_op[op.opA]], &sb = P.ops[D.split_op[op.opB]];
+        const bool symA = P.slots[sa.t[0].mat].symmetric, symB = P.slots[sb.t[0].mat].symmetric;
+        const int trA = symA ? 1 : sa.t[0].trans, trB = symB ? 1 : sb.t[0].trans;
+        g.dA = D.removed[op.opA] ? C.diagv(op.opA) : nullptr;
+        g.dB = D.removed[op.opB] ? C.diagv(op.opB) : nullptr;
+        g.MA = C.ptr(sa.t[0].mat);
+        g.MB = C.ptr(sb.t[0].mat);
+        // a symmetric source is read as M[k][j]: consecutive lanes (rows j)
+        // then read consecutive addresses
+        g.rowA = trA && !symA;
+        g.rowB = !trB && !symB;
+        g.uA = C.vec(sa.u);
+        g.uB = C.vec(sb.u);
+    }
+    const int var = P.tc_variant[tc_size_class(n)];
+    g.group_rows = kGroupRows[var & 3];
+    shape = (var >> 2) & 3;
+    if (shape == 1 && op.symmetric) shape = 0;   // 128 x 64 tiles cannot skip symmetric tiles
+}
+
+// One step of a plan on one evaluation's workspace.
+int run_op(const Ctx &C, const Op &op, const ProgState &S, const void *X, int x_dtype, const ustat_factor *f) {
+    const Plan &P = C.P;
+    const int64_t n = C.n;
+    int *err = S.err;
+    const int lead = S.lead;
+    const DiagFix &D = S.D;
+    const bool direct_x = S.direct_x;
+    cudaError_t e = cudaSuccess;
+    ProfScope ps(op.kind, C.st);
+    switch (op.kind) {
+        case OP_KBUILD:
+            if (!C.fp64 && f[op.factor].kind == USTAT_RBF) {
+                int rpow[kMaxRed], rvec[kMaxRed];
+                double *rout[kMaxRed];
+                for (int r = 0; r < op.nred; ++r) {
+                    rpow[r] = op.red[r].pow;
+                    rvec[r] = P.slots[op.red[r].out].kind == S_VEC;
+                    rout[r] = C.vec(op.red[r].out);   // scalar and vector slots are float64
                 }
-                break;
-            case OP_LOADMAT:
-                if (f[op.factor].kind == USTAT_DIST || f[op.factor].kind == USTAT_LOWRANK ||
-                    f[op.factor].kind == USTAT_GRAM)
-                    e = launch_pairs(f[op.factor].kind, (const double *)f[op.factor].data, (int)f[op.factor].param, n,
-                                     C.fp64, P.sparsify, C.ptr(op.out), err, C.st);
-                else
-                    e = launch_loadmat((const double *)f[op.factor].data, n, C.fp64, P.sparsify,
-                                       f[op.factor].kind == USTAT_COMPLEMENT, C.ptr(op.out), err, C.st);
-                break;
-            case OP_UNARY:
-                e = launch_unary_tanh(X, x_dtype, n, C.d, (const double *)f[op.factor].data, C.vec(op.out), err, C.st);
-                break;
-            case OP_LOADVEC:
-                e = launch_copyvec((const double *)f[op.factor].data, n, C.vec(op.out), err, C.st);
-                break;
-            case OP_DIAG:
-                if (op.factor >= 0 && f[op.factor].kind != USTAT_TANH_DOT && f[op.factor].kind != USTAT_VECTOR)
-                    e = launch_factor_diag(f[op.factor].kind, f[op.factor].param, X, x_dtype, C.d,
-                                           (const double *)f[op.factor].data, n, P.sparsify, C.vec(op.out), C.st);
-                else
-                    e = launch_diag(C.ptr(op.t[0].mat), C.fp64, n, C.vec(op.out), C.st);
-                break;
-            case OP_VMUL:
-                e = launch_vmul(C.vec(op.u), C.vec(op.a), n, C.vec(op.out), C.st);
-                break;
-            case OP_VSUM:
-                e = launch_vsum(C.vec(op.u), n, C.vec(op.out), C.st);
-                break;
-            case OP_VDOT:
-                e = launch_vdot(C.vec(op.u), C.vec(op.a), n, C.vec(op.out), C.st);
-                break;
-            case OP_HADAMARD:
-            case OP_GEMV:
-            case OP_FREDUCE: {
-                TileTerms tt{};
-                tt.nt = op.nt;
-                for (int t = 0; t < op.nt; ++t) {
-                    tt.M[t] = C.ptr(op.t[t].mat);
-                    tt.trans[t] = P.slots[op.t[t].mat].symmetric ? 0 : op.t[t].trans;
-                }
-                if (op.kind == OP_HADAMARD)
-                    e = launch_tile_op(TILE_HADAMARD, tt, C.fp64, n, nullptr, nullptr, C.ptr(op.out), C.st);
-                else if (op.kind == OP_GEMV)
-                    e = launch_tile_op(TILE_GEMV, tt, C.fp64, n, C.vec(op.u), nullptr, C.ptr(op.out), C.st);
-                else
-                    e = launch_tile_op(TILE_FREDUCE, tt, C.fp64, n, C.vec(op.a), C.vec(op.b), C.ptr(op.out), C.st);
-                break;
-            }
-            case OP_MHB: {
-                MhbArgs g{};
-                g.n = n;
-                std::vector<int> mats;
-                auto mat_index = [&](int slot) {
-                    for (size_t q = 0; q < mats.size(); ++q)
-                        if (mats[q] == slot) return (int)q;
-                    mats.push_back(slot);
-                    return (int)mats.size() - 1;
-                };
-                const auto &grp = P.groups[op.group];
-                g.nops = (int)grp.size();
-                for (size_t q = 0; q < grp.size(); ++q) {
-                    const Op &m = grp[q];
-                    MhbOp &h = g.op[q];
-                    h.kind = m.kind == OP_GEMV ? TILE_GEMV : TILE_FREDUCE;
-                    h.nt = m.nt;
-                    for (int t = 0; t < m.nt; ++t) h.mat[t] = mat_index(m.t[t].mat);
-                    h.a = m.kind == OP_GEMV ? C.vec(m.u) : C.vec(m.a);
-                    h.b = m.kind == OP_GEMV ? nullptr : C.vec(m.b);
-                    h.out = (double *)C.ptr(m.out);
-                }
-                if (mats.size() > (size_t)kMhbMats) return USTAT_ERR_UNSUPPORTED;
-                g.nmat = (int)mats.size();
-                for (size_t q = 0; q < mats.size(); ++q) g.M[q] = C.ptr(mats[q]);
-                e = launch_mhb(g, C.fp64, C.st);
-                break;
-            }
-            case OP_SPLIT:
-            case OP_PREP: {
-                const Term t = op.t[0];
-                const int tr = P.slots[t.mat].symmetric ? 1 : t.trans;
-                if (op.kind == OP_SPLIT) {
-                    double *dg = D.removed[op.out] ? C.diagv(op.out) : nullptr;
-                    e = launch_split(C.ptr(t.mat), C.fp64, tr, C.vec(op.u), n, C.L.ldp_slices, lead,
-                                     split_planes_of(P.precision), C.ptr(op.out), C.scales(op.out), dg, C.st);
-                    if (dg) ps.kernels = 2;
-                }
-                else
-                    e = launch_prep((const float *)C.ptr(t.mat), tr, C.vec(op.u), n, C.L.ldp_prep,
-                                    (float *)C.ptr(op.out), C.st);
-                break;
-            }
-            case OP_GEMM: {
-                auto trW = [&](const Term &t) { return (t.mat >= 0 && !P.slots[t.mat].symmetric) ? t.trans : 0; };
-                if (is_tc_mode(P.precision)) {
-                    const bool split = is_split_mode(P.precision);
-                    TcGemmArgs g{};
-                    g.n = n;
-                    g.ldp = split ? C.L.ldp_slices : C.L.ldp_prep;
-                    g.opA = C.ptr(op.opA);
-                    g.opB = C.ptr(op.opB);
-                    g.scaleA = split ? C.scales(op.opA) : nullptr;
-                    g.scaleB = split ? C.scales(op.opB) : nullptr;
-                    g.lead_bits = lead;
-                    g.err = err;
-                    g.C = op.store ? C.ptr(op.out) : nullptr;
-                    g.wide = C.fp64;
-                    g.nred = op.nred;
-                    for (int r = 0; r < op.nred; ++r) {
-                        const Red &R = op.red[r];
-                        g.red[r] = TcRed{C.ptr(R.W.mat), trW(R.W), C.vec(R.a), C.vec(R.b), R.pow,
-                                         (double *)C.ptr(R.out)};
-                    }
-                    g.symmetric = op.symmetric;
-                    if (C.nranks > 1 && !op.store) {
-                        g.shard_rank = C.rank;
-                        g.shard_count = C.nranks;
-                    }
-                    if (split && op.opA >= 0 && op.opB >= 0 && (D.removed[op.opA] || D.removed[op.opB])) {
-                        // operands split without their diagonal: the epilogue adds the
-                        // left-out terms from the operands' sources
-                        const Op &sa = P.ops[D.split_op[op.opA]], &sb = P.ops[D.split_op[op.opB]];
-                        const bool symA = P.slots[sa.t[0].mat].symmetric, symB = P.slots[sb.t[0].mat].symmetric;
-                        const int trA = symA ? 1 : sa.t[0].trans, trB = symB ? 1 : sb.t[0].trans;
-                        g.dA = D.removed[op.opA] ? C.diagv(op.opA) : nullptr;
-                        g.dB = D.removed[op.opB] ? C.diagv(op.opB) : nullptr;
-                        g.MA = C.ptr(sa.t[0].mat);
-                        g.MB = C.ptr(sb.t[0].mat);
-                        // a symmetric source is read as M[k][j]: consecutive lanes (rows j)
-                        // then read consecutive addresses
-                        g.rowA = trA && !symA;
-                        g.rowB = !trB && !symB;
-                        g.uA = C.vec(sa.u);
-                        g.uB = C.vec(sb.u);
-                    }
-                    const int var = P.tc_variant[tc_size_class(n)];
-                    g.group_rows = kGroupRows[var & 3];
-                    int shape = (var >> 2) & 3;
-                    if (shape == 1 && op.symmetric) shape = 0;   // 128 x 64 tiles cannot skip symmetric tiles
-                    if (P.precision == USTAT_BF16X3) e = launch_gemm_bf16x3(g, shape, C.st);
-                    else if (P.precision == USTAT_BF16X4) e = launch_gemm_bf16x4(g, shape, C.st);
-                    else if (P.precision == USTAT_BF16X5) e = launch_gemm_bf16x5(g, C.st);
-                    else e = launch_gemm_tf32(g, C.st);
-                } else {
-                    SimtGemmArgs g{};
-                    g.n = n;
-                    g.A = C.ptr(op.A.mat);
-                    g.transA = trW(op.A);
-                    g.B = C.ptr(op.B.mat);
-                    g.transB = trW(op.B);
-                    g.u = C.vec(op.u);
-                    g.C = op.store ? C.ptr(op.out) : nullptr;
-                    g.nred = op.nred;
-                    for (int r = 0; r < op.nred; ++r) {
-                        const Red &R = op.red[r];
-                        g.red[r] = SimtRed{C.ptr(R.W.mat), trW(R.W), C.vec(R.a), C.vec(R.b), R.pow,
-                                           (double *)C.ptr(R.out)};
-                    }
-                    g.symmetric = op.symmetric;
-                    e = launch_gemm_simt(g, C.fp64, C.st);
-                }
-                break;
-            }
-            case OP_GEMM3: {
-                auto tr = [&](const Term &t) { return (t.mat >= 0 && !P.slots[t.mat].symmetric) ? t.trans : 0; };
-                if (is_split_mode(P.precision)) {
-                    // tensor cores: g3_nb products at a time, their A operands split
-                    // per bb into the batch region (planes of all bb back to back)
-                    // (two regions: batch k is split into region k % 2 once the GEMM
-                    // of batch k - 2 has read it; its GEMM runs on the second stream
-                    // after that split, beside the split of batch k + 1)
-                    const int planes = split_planes_of(P.precision);
-                    const size_t plane_bytes = 2 * (size_t)n * C.L.ldp_slices;
-                    const int var = P.tc_variant[tc_size_class(n)];
-                    const bool two = C.L.g3_regions == 2;
-                    SideStream *S = nullptr;
-                    if (two) {
-                        e = side_stream(&S);
-                        if (e != cudaSuccess) break;
-                    }
-                    const cudaStream_t gs = two ? S->st : C.st;
-                    // float64 storage: the A source as a float pair and the weights as
-                    // float, so that neither the split nor the GEMM epilogue of this
-                    // step does float64 arithmetic per entry
-                    auto row_form = [&](const Term &t) { return P.slots[t.mat].symmetric ? 1 : t.trans; };
-                    const bool pair = C.fp64 && C.L.sh_off && row_form(op.A) == 1;
-                    float *shA = nullptr, *shAl = nullptr, *shW = nullptr, *shWbc = nullptr, *shWbd = nullptr;
-                    if (pair) {
-                        const size_t sz = align_up(4 * (size_t)n * n, 1024);
-                        char *sh = C.ws + C.L.sh_off;
-                        shA = (float *)sh;
-                        shAl = (float *)(sh + sz);
-                        shW = (float *)(sh + 2 * sz);
-                        shWbc = (float *)(sh + 3 * sz);
-                        shWbd = (float *)(sh + 4 * sz);
-                        e = launch_f64_pair((const double *)C.ptr(op.A.mat), n * n, shA, shAl, C.st);
-                        if (e == cudaSuccess && op.W.mat >= 0)
-                            e = launch_f64_pair((const double *)C.ptr(op.W.mat), n * n, shW, nullptr, C.st);
-                        if (e == cudaSuccess && op.Wbc.mat >= 0)
-                            e = launch_f64_pair((const double *)C.ptr(op.Wbc.mat), n * n, shWbc, nullptr, C.st);
-                        if (e == cudaSuccess && op.Wbd.mat >= 0)
-                            e = launch_f64_pair((const double *)C.ptr(op.Wbd.mat), n * n, shWbd, nullptr, C.st);
-                        if (e != cudaSuccess) break;
-                    }
-                    int k = 0, last = 0;
-                    // a row shard takes the indices bb_lo .. bb_hi - 1
-                    const int64_t bb_lo = n * C.rank / C.nranks, bb_hi = n * (C.rank + 1) / C.nranks;
-                    for (int64_t bb0 = bb_lo; bb0 < bb_hi && e == cudaSuccess; bb0 += C.L.g3_nb, ++k) {
-                        const int nb = (int)std::min<int64_t>(C.L.g3_nb, bb_hi - bb0);
-                        const int h = two ? (k & 1) : 0;
-                        char *sl = C.ws + C.L.g3_off + (size_t)h * C.L.g3_stride * C.L.g3_nb;
-                        float *sc = (float *)(sl + planes * plane_bytes * C.L.g3_nb);
-                        if (two && k >= 2) e = cudaStreamWaitEvent(C.st, S->gemm_done[h], 0);
-                        if (e != cudaSuccess) break;
-                        // symmetric sources are read along rows (A(i, j) = M[j][i])
-                        if (pair)
-                            e = launch_split_g3_pair(shA, shAl, C.vec(op.u), (const double *)C.ptr(op.Ab.mat),
-                                                     row_form(op.Ab), bb0, nb, n, C.L.ldp_slices, lead, planes, sl,
-                                                     sc, C.st);
-                        else
-                            e = launch_split_g3(C.ptr(op.A.mat), C.fp64, row_form(op.A), C.vec(op.u),
-                                                C.ptr(op.Ab.mat), row_form(op.Ab), bb0, nb, n, C.L.ldp_slices, lead,
-                                                planes, sl, sc, C.st);
-                        if (e == cudaSuccess && two) e = cudaEventRecord(S->split_done[h], C.st);
-                        if (e == cudaSuccess && two) e = cudaStreamWaitEvent(gs, S->split_done[h], 0);
-                        if (e != cudaSuccess) break;
-                        TcGemmArgs g{};
-                        g.n = n;
-                        g.ldp = C.L.ldp_slices;
-                        g.opA = sl;
-                        g.scaleA = sc;
-                        g.opB = C.ptr(op.opB);
-                        g.scaleB = C.scales(op.opB);
-                        g.lead_bits = lead;
-                        g.err = err;
-                        g.nred = 1;
-                        g.red[0] = TcRed{op.W.mat >= 0 && pair ? (const void *)shW : C.ptr(op.W.mat), tr(op.W),
-                                         C.vec(op.a), C.vec(op.b), 1, (double *)C.ptr(op.out)};
-                        // with the float copies the step runs in the float32-storage form of
-                        // the kernel (two accumulator sets, overlapped epilogue) unless
-                        // variant bit 6 keeps the four-accumulator layout
-                        const bool four_acc = ((var >> 6) & 1) || P.precision == USTAT_BF16X5;
-                        g.wide = C.fp64 && !(pair && !four_acc);
-                        g.wide_f32 = pair && four_acc ? 1 : 0;
-                        g.batch = nb;
-                        g.bb0 = (int)bb0;
-                        g.Wbc = op.Wbc.mat >= 0 && pair ? (const void *)shWbc : C.ptr(op.Wbc.mat);
-                        g.transWbc = tr(op.Wbc);
-                        g.Wbd = op.Wbd.mat >= 0 && pair ? (const void *)shWbd : C.ptr(op.Wbd.mat);
-                        g.transWbd = tr(op.Wbd);
-                        g.ub = C.vec(op.ub);
-                        g.group_rows = kGroupRows[var & 3];
-                        if (P.precision == USTAT_BF16X3) e = launch_gemm_bf16x3(g, (var >> 2) & 3, gs);
-                        else if (P.precision == USTAT_BF16X5) e = launch_gemm_bf16x5(g, gs);
-                        else e = launch_gemm_bf16x4(g, (var >> 2) & 3, gs);
-                        if (e == cudaSuccess && two) e = cudaEventRecord(S->gemm_done[h], gs);
-                        last = h;
-                    }
-                    // a split and a GEMM per batch, and the float copies of the step
-                    ps.kernels = 2 * k + (pair ? 1 + (op.W.mat >= 0) + (op.Wbc.mat >= 0) + (op.Wbd.mat >= 0) : 0);
-                    // join: the caller's stream waits for the last GEMM (the second
-                    // stream runs its GEMMs in order)
-                    if (e == cudaSuccess && two && k > 0) e = cudaStreamWaitEvent(C.st, S->gemm_done[last], 0);
+                const int var = P.tc_variant[tc_size_class(n)];
+                if (!((var >> 5) & 1) && C.d <= 256) {
+                    // default: squared distances from the Gram matrix on the tensor cores
+                    e = launch_kbuild_rbf_tc(X, x_dtype, n, C.d, f[op.factor].param, P.sparsify,
+                                             (float *)C.ptr(op.out), op.opA >= 0 ? C.ptr(op.opA) : nullptr,
+                                             C.L.ldp_slices, lead, split_planes_of(P.precision),
+                                             op.opA >= 0 ? C.scales(op.opA) : nullptr, op.nred, rpow, rvec, rout,
+                                             op.upper_only, C.ws + C.L.kb_off, err, C.st);
+                    ps.kernels = 2;
                     break;
                 }
+                // variant bit 5: direct differences on the CUDA cores
+                const float *xf = direct_x ? (x_dtype == 1 ? (const float *)X : nullptr)
+                                           : (const float *)(C.ws + C.L.xw_off);
+                const double *xd = direct_x && x_dtype == 0 ? (const double *)X : nullptr;
+                e = launch_kbuild_rbf(xf, xd, n, C.d, f[op.factor].param, P.sparsify,
+                                      (float *)C.ptr(op.out), op.opA >= 0 ? C.ptr(op.opA) : nullptr,
+                                      C.L.ldp_slices, lead, split_planes_of(P.precision),
+                                      op.opA >= 0 ? C.scales(op.opA) : nullptr, op.nred, rpow, rvec, rout,
+                                      op.upper_only, (var >> 4) & 1, err, C.st);
+            } else {
+                if (op.nred) return USTAT_ERR_UNSUPPORTED;   // the planner fuses only into the RBF build
+                if (C.fp64 && f[op.factor].kind == USTAT_LINEAR && x_dtype == 1)
+                    e = launch_kbuild_linear_wide((const float *)X, n, C.d, f[op.factor].param, P.sparsify,
+                                                  (double *)C.ptr(op.out), C.st);
+                else
+                    e = launch_kbuild(f[op.factor].kind, f[op.factor].param, C.ws + C.L.xw_off, C.fp64, n, C.d,
+                                      P.sparsify, C.ptr(op.out), C.st);
+            }
+            break;
+        case OP_LOADMAT:
+            if (f[op.factor].kind == USTAT_DIST || f[op.factor].kind == USTAT_LOWRANK ||
+                f[op.factor].kind == USTAT_GRAM)
+                e = launch_pairs(f[op.factor].kind, (const double *)f[op.factor].data, (int)f[op.factor].param, n,
+                                 C.fp64, P.sparsify, C.ptr(op.out), err, C.st);
+            else
+                e = launch_loadmat((const double *)f[op.factor].data, n, C.fp64, P.sparsify,
+                                   f[op.factor].kind == USTAT_COMPLEMENT, C.ptr(op.out), err, C.st);
+            break;
+        case OP_UNARY:
+            e = launch_unary_tanh(X, x_dtype, n, C.d, (const double *)f[op.factor].data, C.vec(op.out), err, C.st);
+            break;
+        case OP_LOADVEC:
+            e = launch_copyvec((const double *)f[op.factor].data, n, C.vec(op.out), err, C.st);
+            break;
+        case OP_DIAG:
+            if (op.factor >= 0 && f[op.factor].kind != USTAT_TANH_DOT && f[op.factor].kind != USTAT_VECTOR)
+                e = launch_factor_diag(f[op.factor].kind, f[op.factor].param, X, x_dtype, C.d,
+                                       (const double *)f[op.factor].data, n, P.sparsify, C.vec(op.out), C.st);
+            else
+                e = launch_diag(C.ptr(op.t[0].mat), C.fp64, n, C.vec(op.out), C.st);
+            break;
+        case OP_VMUL:
+            e = launch_vmul(C.vec(op.u), C.vec(op.a), n, C.vec(op.out), C.st);
+            break;
+        case OP_VSUM:
+            e = launch_vsum(C.vec(op.u), n, C.vec(op.out), C.st);
+            break;
+        case OP_VDOT:
+            e = launch_vdot(C.vec(op.u), C.vec(op.a), n, C.vec(op.out), C.st);
+            break;
+        case OP_HADAMARD:
+        case OP_GEMV:
+        case OP_FREDUCE: {
+            TileTerms tt{};
+            tt.nt = op.nt;
+            for (int t = 0; t < op.nt; ++t) {
+                tt.M[t] = C.ptr(op.t[t].mat);
+                tt.trans[t] = P.slots[op.t[t].mat].symmetric ? 0 : op.t[t].trans;
+            }
+            if (op.kind == OP_HADAMARD)
+                e = launch_tile_op(TILE_HADAMARD, tt, C.fp64, n, nullptr, nullptr, C.ptr(op.out), C.st);
+            else if (op.kind == OP_GEMV)
+                e = launch_tile_op(TILE_GEMV, tt, C.fp64, n, C.vec(op.u), nullptr, C.ptr(op.out), C.st);
+            else
+                e = launch_tile_op(TILE_FREDUCE, tt, C.fp64, n, C.vec(op.a), C.vec(op.b), C.ptr(op.out), C.st);
+            break;
+        }
+        case OP_MHB: {
+            MhbArgs g{};
+            g.n = n;
+            std::vector<int> mats;
+            auto mat_index = [&](int slot) {
+                for (size_t q = 0; q < mats.size(); ++q)
+                    if (mats[q] == slot) return (int)q;
+                mats.push_back(slot);
+                return (int)mats.size() - 1;
+            };
+            const auto &grp = P.groups[op.group];
+            g.nops = (int)grp.size();
+            for (size_t q = 0; q < grp.size(); ++q) {
+                const Op &m = grp[q];
+                MhbOp &h = g.op[q];
+                h.kind = m.kind == OP_GEMV ? TILE_GEMV : TILE_FREDUCE;
+                h.nt = m.nt;
+                for (int t = 0; t < m.nt; ++t) h.mat[t] = mat_index(m.t[t].mat);
+                h.a = m.kind == OP_GEMV ? C.vec(m.u) : C.vec(m.a);
+                h.b = m.kind == OP_GEMV ? nullptr : C.vec(m.b);
+                h.out = (double *)C.ptr(m.out);
+            }
+            if (mats.size() > (size_t)kMhbMats) return USTAT_ERR_UNSUPPORTED;
+            g.nmat = (int)mats.size();
+            for (size_t q = 0; q < mats.size(); ++q) g.M[q] = C.ptr(mats[q]);
+            e = launch_mhb(g, C.fp64, C.st);
+            break;
+        }
+        case OP_SPLIT:
+        case OP_PREP: {
+            const Term t = op.t[0];
+            const int tr = P.slots[t.mat].symmetric ? 1 : t.trans;
+            if (op.kind == OP_SPLIT) {
+                double *dg = D.removed[op.out] ? C.diagv(op.out) : nullptr;
+                e = launch_split(C.ptr(t.mat), C.fp64, tr, C.vec(op.u), n, C.L.ldp_slices, lead,
+                                 split_planes_of(P.precision), C.ptr(op.out), C.scales(op.out), dg, C.st);
+                if (dg) ps.kernels = 2;
+            }
+            else
+                e = launch_prep((const float *)C.ptr(t.mat), tr, C.vec(op.u), n, C.L.ldp_prep,
+                                (float *)C.ptr(op.out), C.st);
+            break;
+        }
+        case OP_GEMM: {
+            auto trW = [&](const Term &t) { return (t.mat >= 0 && !P.slots[t.mat].symmetric) ? t.trans : 0; };
+            if (is_tc_mode(P.precision)) {
+                TcGemmArgs g;
+                int shape = 0;
+                tc_gemm_args(C, op, S, g, shape);
+                if (P.precision == USTAT_BF16X3) e = launch_gemm_bf16x3(g, shape, C.st);
+                else if (P.precision == USTAT_BF16X4) e = launch_gemm_bf16x4(g, shape, C.st);
+                else if (P.precision == USTAT_BF16X5) e = launch_gemm_bf16x5(g, C.st);
+                else e = launch_gemm_tf32(g, C.st);
+            } else {
                 SimtGemmArgs g{};
                 g.n = n;
-                g.gemm3 = 1;
                 g.A = C.ptr(op.A.mat);
-                g.transA = tr(op.A);
+                g.transA = trW(op.A);
                 g.B = C.ptr(op.B.mat);
-                g.transB = tr(op.B);
+                g.transB = trW(op.B);
                 g.u = C.vec(op.u);
-                g.Ab = C.ptr(op.Ab.mat);
-                g.transAb = tr(op.Ab);
-                g.nred = 1;
-                g.red[0] = SimtRed{C.ptr(op.W.mat), tr(op.W), C.vec(op.a), C.vec(op.b), 1, (double *)C.ptr(op.out)};
-                g.Wbc = C.ptr(op.Wbc.mat);
-                g.transWbc = tr(op.Wbc);
-                g.Wbd = C.ptr(op.Wbd.mat);
-                g.transWbd = tr(op.Wbd);
-                g.ub = C.vec(op.ub);
+                g.C = op.store ? C.ptr(op.out) : nullptr;
+                g.nred = op.nred;
+                for (int r = 0; r < op.nred; ++r) {
+                    const Red &R = op.red[r];
+                    g.red[r] = SimtRed{C.ptr(R.W.mat), trW(R.W), C.vec(R.a), C.vec(R.b), R.pow,
+                                       (double *)C.ptr(R.out)};
+                }
+                g.symmetric = op.symmetric;
                 e = launch_gemm_simt(g, C.fp64, C.st);
+            }
+            break;
+        }
+        case OP_GEMM3: {
+            auto tr = [&](const Term &t) { return (t.mat >= 0 && !P.slots[t.mat].symmetric) ? t.trans : 0; };
+            if (is_split_mode(P.precision)) {
+                // tensor cores: g3_nb products at a time, their A operands split
+                // per bb into the batch region (planes of all bb back to back)
+                // (two regions: batch k is split into region k % 2 once the GEMM
+                // of batch k - 2 has read it; its GEMM runs on the second stream
+                // after that split, beside the split of batch k + 1)
+                const int planes = split_planes_of(P.precision);
+                const size_t plane_bytes = 2 * (size_t)n * C.L.ldp_slices;
+                const int var = P.tc_variant[tc_size_class(n)];
+                const bool two = C.L.g3_regions == 2;
+                SideStream *S = nullptr;
+                if (two) {
+                    e = side_stream(&S);
+                    if (e != cudaSuccess) break;
+                }
+                const cudaStream_t gs = two ? S->st : C.st;
+                // float64 storage: the A source as a float pair and the weights as
+                // float, so that neither the split nor the GEMM epilogue of this
+                // step does float64 arithmetic per entry
+                auto row_form = [&](const Term &t) { return P.slots[t.mat].symmetric ? 1 : t.trans; };
+                const bool pair = C.fp64 && C.L.sh_off && row_form(op.A) == 1;
+                float *shA = nullptr, *shAl = nullptr, *shW = nullptr, *shWbc = nullptr, *shWbd = nullptr;
+                if (pair) {
+                    const size_t sz = align_up(4 * (size_t)n * n, 1024);
+                    char *sh = C.ws + C.L.sh_off;
+                    shA = (float *)sh;
+                    shAl = (float *)(sh + sz);
+                    shW = (float *)(sh + 2 * sz);
+                    shWbc = (float *)(sh + 3 * sz);
+                    shWbd = (float *)(sh + 4 * sz);
+                    e = launch_f64_pair((const double *)C.ptr(op.A.mat), n * n, shA, shAl, C.st);
+                    if (e == cudaSuccess && op.W.mat >= 0)
+                        e = launch_f64_pair((const double *)C.ptr(op.W.mat), n * n, shW, nullptr, C.st);
+                    if (e == cudaSuccess && op.Wbc.mat >= 0)
+                        e = launch_f64_pair((const double *)C.ptr(op.Wbc.mat), n * n, shWbc, nullptr, C.st);
+                    if (e == cudaSuccess && op.Wbd.mat >= 0)
+                        e = launch_f64_pair((const double *)C.ptr(op.Wbd.mat), n * n, shWbd, nullptr, C.st);
+                    if (e != cudaSuccess) break;
+                }
+                int k = 0, last = 0;
+                // a row shard takes the indices bb_lo .. bb_hi - 1
+                const int64_t bb_lo = n * C.rank / C.nranks, bb_hi = n * (C.rank + 1) / C.nranks;
+                for (int64_t bb0 = bb_lo; bb0 < bb_hi && e == cudaSuccess; bb0 += C.L.g3_nb, ++k) {
+                    const int nb = (int)std::min<int64_t>(C.L.g3_nb, bb_hi - bb0);
+                    const int h = two ? (k & 1) : 0;
+                    char *sl = C.ws + C.L.g3_off + (size_t)h * C.L.g3_stride * C.L.g3_nb;
+                    float *sc = (float *)(sl + planes * plane_bytes * C.L.g3_nb);
+                    if (two && k >= 2) e = cudaStreamWaitEvent(C.st, S->gemm_done[h], 0);
+                    if (e != cudaSuccess) break;
+                    // symmetric sources are read along rows (A(i, j) = M[j][i])
+                    if (pair)
+                        e = launch_split_g3_pair(shA, shAl, C.vec(op.u), (const double *)C.ptr(op.Ab.mat),
+                                                 row_form(op.Ab), bb0, nb, n, C.L.ldp_slices, lead, planes, sl,
+                                                 sc, C.st);
+                    else
+                        e = launch_split_g3(C.ptr(op.A.mat), C.fp64, row_form(op.A), C.vec(op.u),
+                                            C.ptr(op.Ab.mat), row_form(op.Ab), bb0, nb, n, C.L.ldp_slices, lead,
+                                            planes, sl, sc, C.st);
+                    if (e == cudaSuccess && two) e = cudaEventRecord(S->split_done[h], C.st);
+                    if (e == cudaSuccess && two) e = cudaStreamWaitEvent(gs, S->split_done[h], 0);
+                    if (e != cudaSuccess) break;
+                    TcGemmArgs g{};
+                    g.n = n;
+                    g.ldp = C.L.ldp_slices;
+                    g.opA = sl;
+                    g.scaleA = sc;
+                    g.opB = C.ptr(op.opB);
+                    g.scaleB = C.scales(op.opB);
+                    g.lead_bits = lead;
+                    g.err = err;
+                    g.nred = 1;
+                    g.red[0] = TcRed{op.W.mat >= 0 && pair ? (const void *)shW : C.ptr(op.W.mat), tr(op.W),
+                                     C.vec(op.a), C.vec(op.b), 1, (double *)C.ptr(op.out)};
+                    // with the float copies the step runs in the float32-storage form of
+                    // the kernel (two accumulator sets, overlapped epilogue) unless
+                    // variant bit 6 keeps the four-accumulator layout
+                    const bool four_acc = ((var >> 6) & 1) || P.precision == USTAT_BF16X5;
+                    g.wide = C.fp64 && !(pair && !four_acc);
+                    g.wide_f32 = pair && four_acc ? 1 : 0;
+                    g.batch = nb;
+                    g.bb0 = (int)bb0;
+                    g.Wbc = op.Wbc.mat >= 0 && pair ? (const void *)shWbc : C.ptr(op.Wbc.mat);
+                    g.transWbc = tr(op.Wbc);
+                    g.Wbd = op.Wbd.mat >= 0 && pair ? (const void *)shWbd : C.ptr(op.Wbd.mat);
+                    g.transWbd = tr(op.Wbd);
+                    g.ub = C.vec(op.ub);
+                    g.group_rows = kGroupRows[var & 3];
+                    if (P.precision == USTAT_BF16X3) e = launch_gemm_bf16x3(g, (var >> 2) & 3, gs);
+                    else if (P.precision == USTAT_BF16X5) e = launch_gemm_bf16x5(g, gs);
+                    else e = launch_gemm_bf16x4(g, (var >> 2) & 3, gs);
+                    if (e == cudaSuccess && two) e = cudaEventRecord(S->gemm_done[h], gs);
+                    last = h;
+                }
+                // a split and a GEMM per batch, and the float copies of the step
+                ps.kernels = 2 * k + (pair ? 1 + (op.W.mat >= 0) + (op.Wbc.mat >= 0) + (op.Wbd.mat >= 0) : 0);
+                // join: the caller's stream waits for the last GEMM (the second
+                // stream runs its GEMMs in order)
+                if (e == cudaSuccess && two && k > 0) e = cudaStreamWaitEvent(C.st, S->gemm_done[last], 0);
                 break;
             }
-            default:
-                return USTAT_ERR_UNSUPPORTED;
+            SimtGemmArgs g{};
+            g.n = n;
+            g.gemm3 = 1;
+            g.A = C.ptr(op.A.mat);
+            g.transA = tr(op.A);
+            g.B = C.ptr(op.B.mat);
+            g.transB = tr(op.B);
+            g.u = C.vec(op.u);
+            g.Ab = C.ptr(op.Ab.mat);
+            g.transAb = tr(op.Ab);
+            g.nred = 1;
+            g.red[0] = SimtRed{C.ptr(op.W.mat), tr(op.W), C.vec(op.a), C.vec(op.b), 1, (double *)C.ptr(op.out)};
+            g.Wbc = C.ptr(op.Wbc.mat);
+            g.transWbc = tr(op.Wbc);
+            g.Wbd = C.ptr(op.Wbd.mat);
+            g.transWbd = tr(op.Wbd);
+            g.ub = C.vec(op.ub);
+            e = launch_gemm_simt(g, C.fp64, C.st);
+            break;
         }
-        if (e != cudaSuccess) return cuda_fail(e);
+        default:
+            return USTAT_ERR_UNSUPPORTED;
     }
+    if (e != cudaSuccess) return cuda_fail(e);
+    return USTAT_OK;
+}
+
+int run_program(const Ctx &C, const void *X, int x_dtype, const ustat_factor *f, double *U_out, double *V_out,
+                double *scal_out = nullptr) {
+    const Plan &P = C.P;
+    const int64_t n = C.n;
+    ProgState S;
+    int rc = program_prologue(C, X, x_dtype, f, S);
+    if (rc != USTAT_OK) return rc;
+    for (const Op &op : P.ops) {
+        rc = run_op(C, op, S, X, x_dtype, f);
+        if (rc != USTAT_OK) return rc;
+    }
+    int *err = S.err;
+    cudaError_t e = cudaSuccess;
     if (scal_out) {
         // row shard: this rank's scalars; the ones every rank computes whole count
         // on rank 0 only, so that the ranks' arrays sum to the plan's scalars
@@ -1661,6 +1711,17 @@ struct ustat_batched {
     cudaEvent_t fork = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // grouped form (ustat_batched_set_grouped): one workspace region per sample, the
+    // plan run step by step over all samples, every bf16x3 product step as one
+    // persistent launch over all samples' tiles
+    int grouped = 0;
+    std::vector<size_t> soff;                 // per sample: its region's offset
+    std::vector<size_t> goff;                 // per product step: its group image's offset
+    size_t grouped_bytes = 0;
+    std::vector<std::vector<char>> images;    // host copies of the group images
+    std::vector<int> image_tiles, image_shape;
+    const void *image_ws = nullptr;
+    int image_var[4] = {-1, -1, -1, -1};
 };
 
 namespace {
@@ -1689,6 +1750,83 @@ void batched_schedule(ustat_batched *b) {
     }
 }
 
+// the product steps that run as one grouped launch in the grouped form
+bool group_step(const Plan &P, const Op &op) { return P.precision == USTAT_BF16X3 && op.kind == OP_GEMM; }
+
+void batched_grouped_layout(ustat_batched *b) {
+    const Plan &P = b->plan->p;
+    size_t cur = 0;
+    b->soff.assign(b->n.size(), 0);
+    for (size_t i = 0; i < b->n.size(); ++i) {
+        b->soff[i] = cur;
+        cur = align_up(cur + make_layout(P, b->n[i], b->d).total, 1024);
+    }
+    b->goff.clear();
+    for (const Op &op : P.ops)
+        if (group_step(P, op)) {
+            b->goff.push_back(cur);
+            cur = align_up(cur + gemm_group_bytes((int)b->n.size()), 1024);
+        }
+    b->grouped_bytes = cur;
+    b->image_ws = nullptr;
+}
+
+size_t batched_ws_bytes(const ustat_batched *b) {
+    return b->grouped ? b->grouped_bytes : (size_t)b->max_lanes * b->lane_bytes;
+}
+
+// The group images of the product steps for workspace ws: each sample's product
+// arguments (its own region), the largest samples first, built on the host and
+// copied to the workspace on the stream (before any capture: the copies are not
+// part of a graph).  Rebuilt when the workspace or the plan's variants change.
+int batched_group_prepare(ustat_batched *b, char *ws, cudaStream_t st) {
+    const Plan &P = b->plan->p;
+    bool same = b->image_ws == ws;
+    for (int c = 0; c < 4; ++c) same = same && b->image_var[c] == P.tc_variant[c];
+    if (same) return USTAT_OK;
+    const int cnt = (int)b->n.size();
+    std::vector<int> order(cnt);
+    for (int i = 0; i < cnt; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->n[x] > b->n[y]; });
+    b->images.clear();
+    b->image_tiles.clear();
+    b->image_shape.clear();
+    size_t k = 0;
+    for (const Op &op : P.ops) {
+        if (!group_step(P, op)) continue;
+        std::vector<TcGemmArgs> items(cnt);
+        int shape0 = -1;
+        for (int q = 0; q < cnt; ++q) {
+            const int i = order[q];
+            Layout L = make_layout(P, b->n[i], b->d);
+            Ctx C{P, L, ws + b->soff[i], b->n[i], b->d, false, st};
+            ProgState S;
+            S.err = (int *)(C.ws + L.err_off);
+            S.lead = split_lead_bits(b->n[i]);
+            S.D = diag_fix_of(P, b->n[i]);
+            int shape = 0;
+            tc_gemm_args(C, op, S, items[q], shape);
+            if (q == 0) shape0 = shape;   // the largest sample's size class picks the tile shape
+        }
+        if (shape0 == 1 && op.symmetric) shape0 = 0;
+        std::vector<char> host;
+        const int tiles = gemm_group_image(items.data(), cnt, shape0, ws + b->goff[k], host);
+        if (tiles < 0) return USTAT_ERR_UNSUPPORTED;
+        cudaError_t e = cudaMemcpyAsync(ws + b->goff[k], host.data(), host.size(), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e);
+        b->images.push_back(std::move(host));
+        b->image_tiles.push_back(tiles);
+        b->image_shape.push_back(shape0);
+        ++k;
+    }
+    // the pageable host images must outlive their copies
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    b->image_ws = ws;
+    for (int c = 0; c < 4; ++c) b->image_var[c] = P.tc_variant[c];
+    return USTAT_OK;
+}
+
 int batched_setup(ustat_batched *b) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1707,8 +1845,70 @@ int batched_setup(ustat_batched *b) {
     return USTAT_OK;
 }
 
+// The grouped form: every sample in its own region, the plan step by step; the
+// samples' steps on the lanes, each product step one grouped launch on the
+// caller's stream between a join of the lanes and a new fork.
+int batched_body_grouped(ustat_batched *b, const void *const *X, int x_dtype, const ustat_factor *f, char *ws,
+                         cudaStream_t st, double *U_out, double *V_out) {
+    const Plan &P = b->plan->p;
+    const int np = (int)P.parts.size();
+    const int cnt = (int)b->n.size();
+    std::vector<Layout> Ls(cnt);
+    for (int i = 0; i < cnt; ++i) Ls[i] = make_layout(P, b->n[i], b->d);
+    auto ctx = [&](int i) {
+        return Ctx{P, Ls[i], ws + b->soff[i], b->n[i], b->d, wide_storage(P.precision), b->streams[b->lane_of[i]]};
+    };
+    auto fork = [&]() -> cudaError_t {
+        cudaError_t e = cudaEventRecord(b->fork, st);
+        for (int l = 0; l < b->lanes && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(b->streams[l], b->fork, 0);
+        return e;
+    };
+    auto join = [&]() -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        for (int l = 0; l < b->lanes && e == cudaSuccess; ++l) {
+            e = cudaEventRecord(b->joins[l], b->streams[l]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->joins[l], 0);
+        }
+        return e;
+    };
+    cudaError_t e = fork();
+    if (e != cudaSuccess) return cuda_fail(e);
+    std::vector<ProgState> S(cnt);
+    for (int i = 0; i < cnt; ++i) {
+        int rc = program_prologue(ctx(i), X[i], x_dtype, f, S[i]);
+        if (rc != USTAT_OK) return rc;
+    }
+    size_t k = 0;
+    for (const Op &op : P.ops) {
+        if (group_step(P, op)) {
+            e = join();
+            if (e == cudaSuccess) {
+                ProfScope ps(op.kind, st);
+                e = launch_gemm_group(ws + b->goff[k], cnt, b->image_tiles[k], b->image_shape[k], S[0].err, st);
+            }
+            if (e == cudaSuccess) e = fork();
+            if (e != cudaSuccess) return cuda_fail(e);
+            ++k;
+            continue;
+        }
+        for (int i = 0; i < cnt; ++i) {
+            int rc = run_op(ctx(i), op, S[i], X[i], x_dtype, f);
+            if (rc != USTAT_OK) return rc;
+        }
+    }
+    for (int i = 0; i < cnt && e == cudaSuccess; ++i) {
+        const Ctx C = ctx(i);
+        ProfScope ps(kProfCombine, C.st);
+        e = plan_combine(P, Ls[i], (const double *)(C.ws + Ls[i].scal_off), S[i].err, b->n[i], U_out + 2 * i,
+                         V_out ? V_out + (size_t)i * np : nullptr, C.st);
+    }
+    if (e == cudaSuccess) e = join();
+    return e == cudaSuccess ? USTAT_OK : cuda_fail(e);
+}
+
 int batched_body(ustat_batched *b, const void *const *X, int x_dtype, const ustat_factor *f, int nf, char *ws,
                  cudaStream_t st, double *U_out, double *V_out) {
+    if (b->grouped) return batched_body_grouped(b, X, x_dtype, f, ws, st, U_out, V_out);
     const Plan &P = b->plan->p;
     const int np = (int)P.parts.size();
     cudaError_t e = cudaEventRecord(b->fork, st);
@@ -1747,8 +1947,7 @@ int batched_check(ustat_batched *b, const void *const *X, int x_dtype, const ust
             return USTAT_ERR_UNSUPPORTED;   // data of one size, not per sample
     for (size_t i = 0; i < b->n.size(); ++i)
         if (!X[i]) return USTAT_ERR_INVALID_ARG;
-    if (!ws || ((uintptr_t)ws % 256) != 0 || ws_bytes < (size_t)b->max_lanes * b->lane_bytes)
-        return USTAT_ERR_WORKSPACE;
+    if (!ws || ((uintptr_t)ws % 256) != 0 || ws_bytes < batched_ws_bytes(b)) return USTAT_ERR_WORKSPACE;
     return batched_setup(b);
 }
 
@@ -1800,7 +1999,23 @@ void ustat_batched_destroy(ustat_batched_t *b) {
 
 int ustat_batched_workspace_bytes(const ustat_batched_t *b, size_t *bytes) {
     if (!b || !bytes) return USTAT_ERR_INVALID_ARG;
-    *bytes = (size_t)b->max_lanes * b->lane_bytes;
+    *bytes = batched_ws_bytes(b);
+    return USTAT_OK;
+}
+
+int ustat_batched_set_grouped(ustat_batched_t *b, int grouped) {
+    if (!b) return USTAT_ERR_INVALID_ARG;
+    if (grouped && b->plan->p.precision != USTAT_BF16X3) return USTAT_ERR_UNSUPPORTED;
+    b->grouped = grouped != 0;
+    if (b->grouped) batched_grouped_layout(b);
+    if (b->exec) {   // a captured graph of the other form
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    if (b->graph) {
+        cudaGraphDestroy(b->graph);
+        b->graph = nullptr;
+    }
     return USTAT_OK;
 }
 
@@ -1823,6 +2038,7 @@ int ustat_batched_run(ustat_batched_t *b, const void *const *X, int x_dtype, con
                       int n_factors, void *ws, size_t ws_bytes, void *stream, double *U_out, double *V_out) {
     int rc = batched_check(b, X, x_dtype, factors, n_factors, ws, ws_bytes, U_out);
     if (rc != USTAT_OK) return rc;
+    if (b->grouped && (rc = batched_group_prepare(b, (char *)ws, (cudaStream_t)stream)) != USTAT_OK) return rc;
     return batched_body(b, X, x_dtype, factors, n_factors, (char *)ws, (cudaStream_t)stream, U_out, V_out);
 }
 
@@ -1840,6 +2056,7 @@ int ustat_batched_capture(ustat_batched_t *b, const void *const *X, int x_dtype,
         cudaGraphDestroy(b->graph);
         b->graph = nullptr;
     }
+    if (b->grouped && (rc = batched_group_prepare(b, (char *)ws, st)) != USTAT_OK) return rc;
     if (tc_gemm3(b->plan->p)) {
         // the treewidth-3 steps' second stream and events, created before the capture
         SideStream *side = nullptr;
@@ -1882,6 +2099,10 @@ int ustat_batched_autotune(ustat_batched_t *b, const void *const *X, int x_dtype
     if (e != cudaSuccess) return cuda_fail(e);
     // time of one batched evaluation: the best of two after a warm-up
     auto timed = [&](double *ms) -> int {
+        if (b->grouped) {   // the group images follow the variants (built outside the timing)
+            int r = batched_group_prepare(b, (char *)ws, st);
+            if (r != USTAT_OK) return r;
+        }
         double best = 1e300;
         for (int rep = 0; rep < 3; ++rep) {
             cudaError_t ee = cudaEventRecord(t0, st);

@@ -33,6 +33,7 @@
 
 #include <algorithm>
 #include <type_traits>
+#include <vector>
 #include <cstdio>
 #include <cstring>
 
@@ -496,7 +497,21 @@ struct TileWalk {
     }
 };
 
-template <int kMode, bool kWide = false>
+// The group entry holding tile t: start[p] <= t < start[p + 1] (binary search).
+__device__ __forceinline__ int group_find(const int *start, int count, int t) {
+    int lo = 0, hi = count;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (start[mid] <= t) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// kGroup: one persistent launch over the tiles of many products (g.gcount group
+// entries, each with its own sizes, operands, tensor maps and reductions in
+// global memory); otherwise one product (or one s = 3 batch) from g itself.
+template <int kMode, bool kWide = false, bool kGroup = false>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const __grid_constant__ CUtensorMap mapB2, TcGemmArgs g) {
@@ -535,8 +550,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int t_lo = g.tile_hi > 0 ? g.tile_lo : 0;
     const int n_tiles = g.tile_hi > 0 ? g.tile_hi - g.tile_lo : walk.count();
     const int split_tail = g.split_tail;
-    const int total_tiles = n_tiles + split_tail;
+    const int total_tiles = kGroup ? g.gstart[g.gcount] : n_tiles + split_tail;
     constexpr int kHalf = C::kBN / 2;
+    // group entry p of tile t and the tile's coordinates in that product's walk
+    auto gunit = [&](int t, int &p, int &tm, int &tn) {
+        p = group_find(g.gstart, g.gcount, t);
+        const TcGemmArgs &a = g.gargs[p];
+        const TileWalk w{(int)((a.n + kBM - 1) / kBM), (int)((a.n + C::kBN - 1) / C::kBN), a.symmetric,
+                         a.group_rows > 0 ? a.group_rows : 8, 0};
+        int bl;
+        w.coords(t - g.gstart[p], bl, tm, tn);
+    };
     auto unit = [&](int t, int &bl, int &tm, int &tn, int &c_off, int &width) {
         const int f = n_tiles - split_tail;
         if (t < f) {
@@ -586,10 +610,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             // that the MMA warp's first wait runs out with nothing in flight
             for (int t = g.debug_stall ? total_tiles : (int)blockIdx.x; t < total_tiles && !*abort_flag;
                  t += gridDim.x) {
-                int bl, tm, tn, c_off, width;
-                unit(t, bl, tm, tn, c_off, width);
+                int bl = 0, tm, tn, c_off = 0, width = C::kBN, nk = num_k;
+                const CUtensorMap *mA = &mapA, *mB = &mapB, *mB2 = &mapB2;
+                if constexpr (kGroup) {
+                    int p;
+                    gunit(t, p, tm, tn);
+                    nk = (int)(g.gargs[p].ldp / C::kBKElems);
+                    mA = reinterpret_cast<const CUtensorMap *>(g.gmaps) + 2 * p;
+                    mB = mA + 1;
+                } else {
+                    unit(t, bl, tm, tn, c_off, width);
+                }
                 const int za = bl * C::kPlanes;   // the product's A planes (batched s = 3 step)
-                for (int kb = 0; kb < num_k; ++kb, ++it) {
+                for (int kb = 0; kb < nk; ++kb, ++it) {
                     const int s = it % C::kStages;
                     if (it >= (uint32_t)C::kStages &&
                         !mbar_wait(empty_bar(s), ((it / C::kStages) - 1) & 1, abort_flag, wlim))
@@ -598,9 +631,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t sb = sa + C::kPlanes * C::kATile;
                     mbar_expect_tx(full_bar(s), width == C::kBN ? C::kStageBytes
                                                                 : C::kPlanes * (C::kATile + C::kBTile / 2));
-                    tma_load_3d(sa, &mapA, kb * C::kBKElems, tm * kBM, za, full_bar(s));
-                    if (width == C::kBN) tma_load_3d(sb, &mapB, kb * C::kBKElems, tn * C::kBN, 0, full_bar(s));
-                    else tma_load_3d(sb, &mapB2, kb * C::kBKElems, tn * C::kBN + c_off, 0, full_bar(s));
+                    tma_load_3d(sa, mA, kb * C::kBKElems, tm * kBM, za, full_bar(s));
+                    if (width == C::kBN) tma_load_3d(sb, mB, kb * C::kBKElems, tn * C::kBN, 0, full_bar(s));
+                    else tma_load_3d(sb, mB2, kb * C::kBKElems, tn * C::kBN + c_off, 0, full_bar(s));
                     *issued_cnt = it + 1;
                 }
             }
@@ -613,8 +646,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t it = 0, tcount = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
-                int bl, tm, tn, c_off, width;
-                unit(t, bl, tm, tn, c_off, width);
+                int bl = 0, tm, tn, c_off = 0, width = C::kBN, nk = num_k;
+                if constexpr (kGroup) {
+                    int p;
+                    gunit(t, p, tm, tn);
+                    nk = (int)(g.gargs[p].ldp / C::kBKElems);
+                } else {
+                    unit(t, bl, tm, tn, c_off, width);
+                }
+                (void)bl;
                 const uint32_t idesc = width == C::kBN ? idesc_full : idesc_half;
                 const uint32_t b_plane = width == C::kBN ? C::kBTile : C::kBTile / 2;   // bytes per B plane
                 const int buf = tcount % C::kBufs;
@@ -626,7 +666,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc_fence_after();
                 const uint32_t d_hi = tmem + buf * C::kAccCols;
                 const uint32_t d_lo = d_hi + (kWide ? 3 : 1) * C::kBN;
-                for (int kb = 0; kb < num_k; ++kb, ++it) {
+                for (int kb = 0; kb < nk; ++kb, ++it) {
                     const int s = it % C::kStages;
                     if (!mbar_wait(full_bar(s), (it / C::kStages) & 1, abort_flag, wlim)) {
                         ok = false;
@@ -685,9 +725,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int row = 32 * q + lane;
         double total[4] = {0.0, 0.0, 0.0, 0.0};
         uint32_t tcount = 0;
-        for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
-            int bl, tm, tn, c_off, width;
-            unit(t, bl, tm, tn, c_off, width);
+        // one tile's epilogue; g and the sizes are the product's (a group entry's in
+        // a grouped launch)
+        auto epi_tile = [&](const TcGemmArgs &g, const int64_t n, const int64_t jend, const int64_t kend,
+                            const int num_k, const int64_t row0, const int64_t col0, int bl, int tm, int tn,
+                            int c_off, int width) -> bool {
             const int64_t bb = g.bb0 + bl;   // batched s = 3 step: this product's index
             const float *Wbd = (const float *)g.Wbd;
             const int tWbd = g.transWbd;
@@ -698,7 +740,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             int waited = 0;
             if (lane == 0) waited = mbar_wait(tfull_bar(buf), (tcount / C::kBufs) & 1, abort_flag, wlim) ? 1 : 0;
             waited = __shfl_sync(0xffffffffu, waited, 0);
-            if (!waited || *abort_flag) break;
+            if (!waited || *abort_flag) return false;
             tc_fence_after();
             const int64_t j = row0 + (int64_t)tm * kBM + row;
             const bool jok = j < jend;
@@ -941,8 +983,30 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int r = 0; r < 4; ++r) {
                 if (r >= g.nred) break;
                 const double aj = (g.red[r].a && jok) ? g.red[r].a[j] : 1.0;
-                total[r] += tile_acc[r] * aj * wbc * wgt;
+                const double x = tile_acc[r] * aj * wbc * wgt;
+                if constexpr (kGroup) {
+                    // a group entry's own output: this warp's share of the tile
+                    const double sw = warp_sum(x);
+                    if (lane == 0 && !*abort_flag) atomicAdd(g.red[r].out, sw);
+                } else {
+                    total[r] += x;
+                }
             }
+            return true;
+        };
+        for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+            bool ok;
+            if constexpr (kGroup) {
+                int p, tm, tn;
+                gunit(t, p, tm, tn);
+                const TcGemmArgs &a = g.gargs[p];
+                ok = epi_tile(a, a.n, a.n, a.n, (int)(a.ldp / C::kBKElems), 0, 0, 0, tm, tn, 0, C::kBN);
+            } else {
+                int bl, tm, tn, c_off, width;
+                unit(t, bl, tm, tn, c_off, width);
+                ok = epi_tile(g, n, jend, kend, num_k, row0, col0, bl, tm, tn, c_off, width);
+            }
+            if (!ok) break;
             ++tcount;
         }
         // reduce the four epilogue warps' partial sums
@@ -970,6 +1034,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (threadIdx.x == 0) {
             if (g.err) atomicOr(g.err, kErrWordTimeout);
+            if constexpr (kGroup)
+                for (int p = 0; p < g.gcount; ++p)
+                    if (g.gargs[p].err) atomicOr(g.gargs[p].err, kErrWordTimeout);
             // wait (bounded in time) for the copies issued but never consumed, before
             // the shared memory they land in is released
             for (uint32_t i = *consumed_cnt; i < *issued_cnt; ++i)
@@ -1234,6 +1301,96 @@ cudaError_t launch_prep(const float *M, int trans, const double *u, int64_t n, i
     dim3 grid((unsigned)((n + 31) / 32)), block(32, 8);
     operand_cols_kernel<false, float><<<grid, block, 0, s>>>(M, trans, u, n, ldp, 0, 1, nullptr, nullptr, out);
     return cudaGetLastError();
+}
+
+namespace {
+
+size_t round_to(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// The device image of a group: per entry the A and B tensor maps (128 bytes each,
+// 64-byte aligned), then the entries' arguments, then the tile prefix sums.
+size_t group_maps_bytes(int count) { return round_to((size_t)count * 2 * sizeof(CUtensorMap), 256); }
+size_t group_args_bytes(int count) { return round_to((size_t)count * sizeof(TcGemmArgs), 256); }
+
+template <int kMode>
+int group_image_t(const TcGemmArgs *items, int count, const void *dev_base, std::vector<char> &host) {
+    using C = Cfg<kMode, false>;
+    host.assign(gemm_group_bytes(count), 0);
+    CUtensorMap *maps = reinterpret_cast<CUtensorMap *>(host.data());
+    TcGemmArgs *args = reinterpret_cast<TcGemmArgs *>(host.data() + group_maps_bytes(count));
+    int *start = reinterpret_cast<int *>(host.data() + group_maps_bytes(count) + group_args_bytes(count));
+    int64_t total = 0;
+    start[0] = 0;
+    for (int p = 0; p < count; ++p) {
+        TcGemmArgs a = items[p];
+        if (a.batch > 0 || a.rows > 0 || a.shard_count > 1 || a.wide || a.wide_f32 || a.nred < 0 || a.nred > 4)
+            return -1;
+        if (C::kBN != kBM || a.C) a.symmetric = 0;
+        if (!make_map_planes(&maps[2 * p], a.opA, true, C::kPlanes, C::kPlanes, a.n, a.ldp, kBM, C::kRowBytes) ||
+            !make_map_planes(&maps[2 * p + 1], a.opB, true, C::kPlanes, C::kPlanes, a.n, a.ldp, C::kBN,
+                             C::kRowBytes))
+            return -1;
+        const int64_t tm = (a.n + kBM - 1) / kBM, tn = (a.n + C::kBN - 1) / C::kBN;
+        total += a.symmetric ? tm * (tm + 1) / 2 : tm * tn;
+        if (total > (int64_t)1 << 30) return -1;
+        start[p + 1] = (int)total;
+        args[p] = a;
+    }
+    (void)dev_base;
+    return (int)total;
+}
+
+template <int kMode>
+cudaError_t launch_group_t(const void *dev_base, int count, int total_tiles, int *err, cudaStream_t s) {
+    using C = Cfg<kMode, false>;
+    static bool attr[64] = {false};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<kMode, false, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+        if (e != cudaSuccess) return e;
+        attr[dev] = true;
+    }
+    const char *b = (const char *)dev_base;
+    TcGemmArgs g{};
+    g.n = kBM;
+    g.ldp = 64;
+    g.err = err;
+    g.gmaps = b;
+    g.gargs = reinterpret_cast<const TcGemmArgs *>(b + group_maps_bytes(count));
+    g.gstart = reinterpret_cast<const int *>(b + group_maps_bytes(count) + group_args_bytes(count));
+    g.gcount = count;
+    g.wait_limit = g_debug_wait_limit;
+    g.debug_stall = g_debug_stall;
+    // the kernel's own maps are not read in a grouped launch; any valid map will do
+    CUtensorMap dummy;
+    std::memset(&dummy, 0, sizeof(dummy));
+    const int64_t S = sm_count();
+    const int grid = (int)(total_tiles < S ? total_tiles : S);
+    if (grid < 1) return cudaSuccess;
+    tc_gemm_kernel<kMode, false, true><<<grid, kThreads, C::kSmem, s>>>(dummy, dummy, dummy, g);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t gemm_group_bytes(int count) {
+    return group_maps_bytes(count) + group_args_bytes(count) + round_to((size_t)(count + 1) * sizeof(int), 256);
+}
+
+int gemm_group_image(const TcGemmArgs *items, int count, int shape, const void *dev_base, std::vector<char> &host) {
+    if (!items || count < 1) return -1;
+    if (shape == 1) return group_image_t<3>(items, count, dev_base, host);
+    if (shape == 2) return group_image_t<4>(items, count, dev_base, host);
+    return group_image_t<0>(items, count, dev_base, host);
+}
+
+cudaError_t launch_gemm_group(const void *dev_base, int count, int total_tiles, int shape, int *err, cudaStream_t s) {
+    if (!dev_base || count < 1 || total_tiles < 0 || ((uintptr_t)dev_base % 256) != 0) return cudaErrorInvalidValue;
+    if (shape == 1) return launch_group_t<3>(dev_base, count, total_tiles, err, s);
+    if (shape == 2) return launch_group_t<4>(dev_base, count, total_tiles, err, s);
+    return launch_group_t<0>(dev_base, count, total_tiles, err, s);
 }
 
 cudaError_t launch_gemm_bf16x3(const TcGemmArgs &g, int shape, cudaStream_t s) {

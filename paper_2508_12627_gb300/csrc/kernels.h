@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 namespace ustat {
@@ -234,6 +235,12 @@ struct TcGemmArgs {
     // reductions are multiplied by wscale (0: 1).
     int64_t row0, col0, rows, cols;
     double wscale;
+    // grouped launch (set by launch_gemm_group): gcount products, their arguments
+    // and tensor maps (A, B per product) in device memory, tile prefix sums gstart
+    const TcGemmArgs *gargs;
+    const void *gmaps;
+    const int *gstart;
+    int gcount;
 };
 // Test hook of the bounded waits (off by default): every later tensor-core GEMM
 // launch of this process uses `wait_limit` cycles (0 = default) as its wait limit
@@ -246,6 +253,17 @@ long long tc_debug_wait_limit();
 // k-blocks, four stages (bf16x4: 0 = 128 x 64 tiles, two stages; 2 = 128 x 128
 // tiles, 64-byte k-blocks, three stages)
 cudaError_t launch_gemm_bf16x3(const TcGemmArgs &g, int shape, cudaStream_t s);
+// One persistent bf16x3 launch over the tiles of `count` products (a group): the
+// host builds the group's device image (each entry's A and B tensor maps, its
+// arguments, the tile prefix sums) with gemm_group_image for the device address
+// it will be copied to (gemm_group_bytes bytes, 256-byte aligned) and returns the
+// total tile count (-1: an entry the grouped form does not take: batched, window,
+// shard or float64-storage products); launch_gemm_group then runs all tiles, each
+// entry's reductions added to its own outputs.  Entries keep their own error
+// words; a bounded wait that gives up sets every entry's.
+size_t gemm_group_bytes(int count);
+int gemm_group_image(const TcGemmArgs *items, int count, int shape, const void *dev_base, std::vector<char> &host);
+cudaError_t launch_gemm_group(const void *dev_base, int count, int total_tiles, int shape, int *err, cudaStream_t s);
 cudaError_t launch_gemm_bf16x4(const TcGemmArgs &g, int shape, cudaStream_t s);
 // five slices, 128 x 128 tiles, 64-byte k-blocks; float64 storage only
 cudaError_t launch_gemm_bf16x5(const TcGemmArgs &g, cudaStream_t s);

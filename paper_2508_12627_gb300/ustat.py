@@ -85,6 +85,7 @@ EXPORTS = {
     "ustat_batched_workspace_bytes": (_i, [_vp, _P(_sz)]),
     "ustat_batched_info": (_i, [_vp, _P(_i), _P(_i)]),
     "ustat_batched_set_lanes": (_i, [_vp, _i]),
+    "ustat_batched_set_grouped": (_i, [_vp, _i]),
     "ustat_batched_run": (_i, [_vp, _P(_vp), _i, _P(ustat_factor), _i, _vp, _sz, _vp, _vp, _vp]),
     "ustat_batched_capture": (_i, [_vp, _P(_vp), _i, _P(ustat_factor), _i, _vp, _sz, _vp, _vp, _vp]),
     "ustat_batched_replay": (_i, [_vp, _vp]),
@@ -514,6 +515,11 @@ class Batched:
 
     def set_lanes(self, lanes):
         _check(lib().ustat_batched_set_lanes(self.handle, int(lanes)), "ustat_batched_set_lanes")
+
+    def set_grouped(self, grouped=True):
+        """ustat_batched_set_grouped: one persistent launch per product step over
+        all samples' tiles (bf16x3); the workspace grows to one region per sample."""
+        _check(lib().ustat_batched_set_grouped(self.handle, 1 if grouped else 0), "ustat_batched_set_grouped")
 
     def _args(self, X_ptrs, factors):
         if len(X_ptrs) != self.count:

@@ -184,3 +184,97 @@ def test_full_batch_against_stored_oracle_values(us, name):
         assert abs(Uh[i, 0] - rec["U_sum"]) <= 1e-8 * rec["U_abs"], (name, i)
         checked += 1
     assert checked == 8
+
+
+def test_grouped_form_arguments(us):
+    g = synth.cycle4_graph()
+    p = us.Plan(g, [uo.RBF], precision="bf16x3")
+    ns = [300, 700, 129]
+    b = us.Batched(p, ns, 16, max_lanes=2)
+    lane_bytes = b.workspace_bytes()
+    b.set_grouped(True)
+    # one region per sample, plus the group images
+    assert b.workspace_bytes() >= sum(p.workspace_bytes(n, 16) for n in ns)
+    b.set_grouped(False)
+    assert b.workspace_bytes() == lane_bytes
+    p64 = us.Plan(g, [uo.RBF], precision="fp64")
+    with pytest.raises(us.UstatError) as e:
+        us.Batched(p64, ns, 16).set_grouped(True)
+    assert e.value.code == us.USTAT_ERR_UNSUPPORTED
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name", ["c4", "c5"])
+def test_grouped_form_matches_lanes_and_oracle(us, name):
+    # every product step of all samples in one persistent launch: the same digits
+    # and per-entry accumulation as the lane form, the reductions added in another
+    # order; eager, and a captured graph replayed twice
+    import torch
+    ns = [300, 5, 130, 40, 257, 64, 7, 129, 1100, 700]
+    g, p, Xs, Xd, b, ws, U, V, facs = _setup(us, name, "bf16x3", ns)
+    st = torch.cuda.current_stream().cuda_stream
+    xp = [x.data_ptr() for x in Xd]
+    b.run(xp, 0, facs, ws.data_ptr(), ws.numel(), st, U.data_ptr(), V.data_ptr())
+    torch.cuda.synchronize()
+    U0, V0 = U.cpu().numpy(), V.cpu().numpy()
+    b.set_grouped(True)
+    wg = torch.full((b.workspace_bytes(),), 255, dtype=torch.uint8, device="cuda:0")
+    U.fill_(float("nan"))
+    V.fill_(float("nan"))
+    b.run(xp, 0, facs, wg.data_ptr(), wg.numel(), st, U.data_ptr(), V.data_ptr())
+    torch.cuda.synchronize()
+    absV = []
+    for i, X in enumerate(Xs):
+        ab = uo.ustat(g, [synth.Factor(uo.RBF, 2.0 * X.shape[1], None)], X, absolute=True)
+        absV.append(np.maximum(np.array(ab["V"]), 1e-300))
+        assert np.all(np.abs(V[i].cpu().numpy() - V0[i]) <= SAME_PATH_TOL * absV[-1]), (name, i)
+        assert abs(U[i, 0].item() - U0[i, 0]) <= SAME_PATH_TOL * absV[-1].sum(), (name, i)
+        if ns[i] <= 300:
+            ref = uo.ustat(g, [synth.Factor(uo.RBF, 2.0 * X.shape[1], None)], X)
+            assert np.all(np.abs(V[i].cpu().numpy() - np.array(ref["V"])) <= SMALL_N_TOL * absV[-1]), (name, i)
+    U2 = torch.full_like(U, float("nan"))
+    V2 = torch.full_like(V, float("nan"))
+    s2 = torch.cuda.Stream()
+    with torch.cuda.stream(s2):
+        b.capture(xp, 0, facs, wg.data_ptr(), wg.numel(), s2.cuda_stream, U2.data_ptr(), V2.data_ptr())
+        for _ in range(2):
+            V2.fill_(float("nan"))
+            b.replay(s2.cuda_stream)
+    torch.cuda.synchronize()
+    for i in range(len(ns)):
+        assert np.all(np.abs(V2[i].cpu().numpy() - V0[i]) <= SAME_PATH_TOL * absV[i]), (name, i)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name", ["c4", "c5"])
+def test_full_batch_grouped_against_stored_oracle_values(us, name):
+    # all 512 samples of the batched workload, every product step one launch over
+    # all samples' tiles, captured and replayed: the stored oracle values to 1e-8
+    import json
+    import os
+    import torch
+    with open(os.path.join(os.path.dirname(__file__), "golden", "workload_batched.json")) as f:
+        gold = json.load(f)
+    ns = [int(v) for v in synth.batched_sizes(512, 256, 4096, 0)]
+    g, p, Xs, Xd, b, ws, U, V, facs = _setup(us, name, "bf16x3", ns, max_lanes=16)
+    del ws
+    b.set_grouped(True)
+    wg = torch.empty(b.workspace_bytes(), dtype=torch.uint8, device="cuda:0")
+    s2 = torch.cuda.Stream()
+    xp = [x.data_ptr() for x in Xd]
+    with torch.cuda.stream(s2):
+        b.capture(xp, 0, facs, wg.data_ptr(), wg.numel(), s2.cuda_stream, U.data_ptr(), V.data_ptr())
+        b.replay(s2.cuda_stream)
+    torch.cuda.synchronize()
+    Uh, Vh = U.cpu().numpy(), V.cpu().numpy()
+    assert np.all(np.isfinite(Uh)) and np.all(np.isfinite(Vh))
+    checked = 0
+    for rec in gold["samples"]:
+        if rec["graph"] != name:
+            continue
+        i = rec["index"]
+        Vabs = np.array(rec["V_abs"])
+        assert np.all(np.abs(Vh[i] - np.array(rec["V"])) <= 1e-8 * Vabs), (name, i)
+        assert abs(Uh[i, 0] - rec["U_sum"]) <= 1e-8 * rec["U_abs"], (name, i)
+        checked += 1
+    assert checked == 8
