@@ -554,7 +554,7 @@ int run_op(const Ctx &C, const Op &op, const ProgState &S, const void *X, int x_
             if (mats.size() > (size_t)kMhbMats) return USTAT_ERR_UNSUPPORTED;
             g.nmat = (int)mats.size();
             for (size_t q = 0; q < mats.size(); ++q) g.M[q] = C.ptr(mats[q]);
-            e = launch_mhb(g, C.fp64, C.st);
+            e = launch_mhb(g, C.fp64, is_split_mode(P.precision), C.st);
             break;
         }
         case OP_SPLIT:

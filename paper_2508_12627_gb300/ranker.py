@@ -262,6 +262,97 @@ def regrets(recs, score):
     return {k: float(np.mean(v)) for k, v in out.items()}
 
 
+def compare_plans(cases, wts, reps=5, log=None):
+    """Whole plans (all partitions, with the sharing between them) chosen by the
+    exhaustive, min-fill and learned planners, timed on the same inputs: per case
+    {name, m, n, partitions, ms: {planner: ms}, flops: {planner: plan flops},
+    max_rel_diff: the learned plan's largest V difference from the exhaustive
+    plan's, relative to |V|}.  A case is (name, graph, factors, kinds, X, precision)
+    with factors as ustat_eval takes them (device data)."""
+    import torch
+    params = torch.as_tensor(np.asarray(wts["params"], dtype=np.float32), device="cuda")
+    st = torch.cuda.current_stream()
+    out = []
+    for name, g, facs, kinds, X, prec in cases:
+        n, d = X.shape
+        rws = torch.empty(max(256, us.rank_workspace_bytes(g, kinds, prec)), dtype=torch.uint8, device="cuda")
+        plans = {"exhaustive": us.Plan(g, kinds, precision=prec, planner=us.PLAN_EXHAUSTIVE),
+                 "minfill": us.Plan(g, kinds, precision=prec, planner=us.PLAN_MINFILL),
+                 "learned": us.plan_learned(g, kinds, n, params.data_ptr(), wts["hidden"], rws.data_ptr(),
+                                            rws.numel(), st.cuda_stream, precision=prec)}
+        need = max(p.workspace_bytes(n, d) for p in plans.values())
+        ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+        res = {"name": name, "m": g.m, "n": int(n), "partitions": plans["exhaustive"].info["n_parts"], "ms": {},
+               "flops": {}}
+        V = {}
+        for pn, p in plans.items():
+            o = torch.empty(2 + p.info["n_parts"], dtype=torch.float64, device="cuda")
+
+            def run():
+                us.ustat_eval(p, X.data_ptr(), 0 if X.dtype == torch.float64 else 1, n, d, facs, ws.data_ptr(),
+                              ws.numel(), st.cuda_stream, o.data_ptr(), o.data_ptr() + 16)
+            run()
+            ts = []
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(st)
+                run()
+                b.record(st)
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+            res["ms"][pn] = float(np.median(ts))
+            res["flops"][pn] = float(p.flops(n)[0])
+            V[pn] = o[2:].cpu().numpy()
+        res["max_rel_diff"] = float(np.max(np.abs(V["learned"] - V["exhaustive"]) /
+                                           np.maximum(np.abs(V["exhaustive"]), 1e-300)))
+        if log:
+            log(json.dumps(res))
+        out.append(res)
+        del ws
+    return out
+
+
+def comparison_cases(count=20, seed=31):
+    """Configurations 5 (K4 + cycle, n = 1024) and 3 (path + chord, n = 16384) and
+    `count` random connected kernel graphs G(m, p), m = 6 or 7, p in [0.15, 0.55] (RBF edges, up
+    to two tanh unary factors) at n = 2048, or 512 when a partition needs an n^4
+    step."""
+    import torch
+    import synth
+    cases = []
+    for wname in ("k4_cycle_rbf", "path5_chord_linear_tanh"):
+        w = synth.workload(wname)
+        X = torch.as_tensor(np.ascontiguousarray(w.X), device="cuda")
+        keep = []
+        facs = []
+        for f in w.factors:
+            if f.data is not None:
+                t = torch.as_tensor(np.ascontiguousarray(f.data, dtype=np.float64), device="cuda")
+                keep.append(t)
+                facs.append((f.kind, f.param, t.data_ptr()))
+            else:
+                facs.append((f.kind, f.param, 0))
+        cases.append((wname, w.graph, facs, [f.kind for f in w.factors], X, "bf16x3"))
+        cases[-1] = cases[-1] + (keep,)
+    rng = np.random.default_rng(seed)
+    d = 16
+    w = torch.as_tensor(rng.normal(0, 1 / math.sqrt(d), d), device="cuda")
+    while len(cases) < count + 2:
+        m = int(rng.integers(6, 8))
+        g = synth.random_connected_graph(rng, m, float(rng.uniform(0.15, 0.55)), max_unary=2)
+        try:
+            p = us.Plan(g, KINDS, precision="bf16x3")
+        except us.UstatError:   # treewidth above 3
+            continue
+        if p.info["n_parts"] < 2:
+            continue
+        n = 512 if max(p.info["tw"]) >= 3 else 2048
+        X = torch.as_tensor(synth.normal_X(n, d, 100 + len(cases)), device="cuda")
+        cases.append(("random m=%d tw=%d" % (m, max(p.info["tw"])), g, [(RBF, 2.0 * d, 0), (TANH, 0.0, w.data_ptr())],
+                      KINDS, X, "bf16x3", [w]))
+    return [c[:6] for c in cases], [c[6] for c in cases]
+
+
 def load(path=WEIGHTS):
     with open(path) as f:
         return json.load(f)
@@ -278,6 +369,9 @@ def main():
                     help="JSONL file of timing records: the records already in it are used, new ones are appended "
                          "as they are measured (an interrupted run resumes)")
     ap.add_argument("--checkpoint", default=None, help="write the trained network's state (npz) here")
+    ap.add_argument("--compare-plans", default=None, metavar="OUT",
+                    help="time whole plans of the exhaustive, min-fill and learned planners on configurations 5 "
+                         "and 3 and 20 random m = 6-7 graphs, write the results (JSON) to OUT and stop")
     args = ap.parse_args()
     import torch
     from . import build
@@ -286,6 +380,14 @@ def main():
 
     def log(s):
         print(s, flush=True)
+
+    if args.compare_plans:
+        cases, keep = comparison_cases()
+        res = compare_plans(cases, load(), log=log)
+        with open(args.compare_plans, "w") as f:
+            json.dump(res, f, indent=1)
+        del keep
+        return
 
     timer = Timer()
     recs = read_records(args.data) if args.data else []
