@@ -54,7 +54,7 @@ WORKLOADS = {
 # DRAM bytes (read + write) of one launch of the dominant kernel, from the ncu
 # capture summarised in profiles/ for the same workload, precision and kernel
 # version; a workload or kernel without a current capture reports null.
-TRAFFIC = {("c4_rbf", "bf16x3", None): 286.6e6}   # profiles/tc_gemm_bf16x3_c4_n4096.md
+TRAFFIC = {("c4_rbf", "bf16x3", None): 283.6e6}   # profiles/tc_gemm_bf16x3_c4_n4096.md
 
 
 def load_peaks():
@@ -304,12 +304,60 @@ def run_capture(args):
     from paper_2508_12627_gb300 import build as B
     B.build()
     from paper_2508_12627_gb300 import engine
-    w = synth.workload(args.workload)
+    if args.workload == "hoif_chain":
+        from paper_2508_12627_gb300 import hoif
+        n = args.n or 10000
+        phi, A, Y = synth.hoif_sample(n, seed=0)
+        hc = hoif.HoifChains(n, k=phi.shape[1], precision=args.precision)
+        hc.set(*hoif.factor_terms(phi, A, Y))
+        for _ in range(args.capture):
+            for j in hc.orders:
+                hc.launch(j)
+        torch.cuda.synchronize()
+        print("capture done: U_sum(h_7) %.17g" % hc.out[7][0].item())
+        return
+    if args.workload == "motifs4_er":
+        from paper_2508_12627_gb300 import motifs
+        A = synth.er_adjacency(MOTIF_N, MOTIF_P, 0)
+        mc = motifs.MotifCounter(A, precision=args.precision)
+        todo = [synth.MOTIFS[nm] for nm in synth.CONNECTED4]
+        outs = []
+        for k, e in todo:
+            p, _, _ = mc.plan(k, e)
+            outs.append(torch.empty(2 + p.info["n_parts"], dtype=torch.float64, device="cuda"))
+        for _ in range(args.capture):
+            for (k, e), o in zip(todo, outs):
+                mc.launch(k, e, o, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        print("capture done: U_sum %.17g" % outs[0][0].item())
+        return
+    if args.workload == "batched":
+        from paper_2508_12627_gb300 import ustat as us
+        d = 16
+        ns = [int(v) for v in synth.batched_sizes(512, 256, 4096, 0)]
+        Xd = [torch.as_tensor(synth.normal_X(n, d, 1000 + i), device="cuda") for i, n in enumerate(ns)]
+        p = us.Plan(synth.cycle4_graph(), [synth.RBF], precision=args.precision)
+        b = us.Batched(p, ns, d, max_lanes=16)
+        b.set_grouped(True)
+        ws = torch.empty(b.workspace_bytes(), dtype=torch.uint8, device="cuda")
+        U = torch.empty((len(ns), 2), dtype=torch.float64, device="cuda")
+        st = torch.cuda.current_stream().cuda_stream
+        for _ in range(args.capture):
+            b.run([x.data_ptr() for x in Xd], 0, [(synth.RBF, 2.0 * d, 0)], ws.data_ptr(), ws.numel(), st,
+                  U.data_ptr(), None)
+        torch.cuda.synchronize()
+        print("capture done: U_sum[0] %.17g" % U[0, 0].item())
+        return
+    w = synth.workload(args.workload, n=args.n) if args.n else synth.workload(args.workload)
     eng = engine.Engine(w.graph, w.factors, precision=args.precision)
     Xd = eng.to_device(w.X)
     out = torch.empty(2 + eng.n_parts, dtype=torch.float64, device="cuda")
     for _ in range(args.capture):
-        eng.launch(Xd, out)
+        if args.lean:
+            r = eng.evaluate_lean(Xd, panel_rows=args.lean)
+            out[0] = r["U_sum"]
+        else:
+            eng.launch(Xd, out)
     torch.cuda.synchronize()
     print("capture done: U_sum %.17g" % out[0].item())
 
@@ -1163,6 +1211,9 @@ def main():
                     help="tensor-core GEMM variant for every size class (ustat_plan_set_variant)")
     ap.add_argument("--eager", action="store_true",
                     help="dCov workload: launch every evaluation eagerly instead of replaying one CUDA graph")
+    ap.add_argument("--n", type=int, default=0, help="with --capture: the workload's sample size")
+    ap.add_argument("--lean", type=int, default=0,
+                    help="with --capture: the memory-lean evaluation with panels of this many rows")
     ap.add_argument("--capture", type=int, default=0,
                     help="only run this many evaluations (no timing, no JSON): for profiler captures")
     args = ap.parse_args()

@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and bench.py's
 CPU-baseline / reference leg may import this module.  It shares no code with the
 CUDA path (paper_2508_12627_gb300/) and never imports it.
 
-Everything here follows the paper (arXiv 2508.12627) step by step, in float64:
+Everything here restates the paper's definitions (arXiv 2508.12627) in float64:
 
 * U-statistic as the sum over ordered distinct m-tuples (Section 2.1, Definition
   "U-Statistic"); V-statistic over all of [n]^m (Definition "V-Statistic").
@@ -17,8 +17,10 @@ Everything here follows the paper (arXiv 2508.12627) step by step, in float64:
   "Decomposition of U-Statistic into V-Statistics") and, independently, the
   Moebius function of the partition lattice from its defining recursion
   (Appendix E, Definition "Moebius Function").
-* Induced Einsum notation A_pi (Algorithm 3) and V_pi = Einsum(T, A_pi)
-  (Section 3.3, the identity right after Example "A_pi").
+* The restricted V-statistic V_pi: the V-statistic of the kernel with the indices
+  of each block of pi equal (Section 3.3, Definition "Restricted V-Statistic"),
+  written as the Einsum of the quotient signature (the identity right after
+  Example "A_pi").
 * Einsum evaluated by summing out one index at a time along an elimination order
   (Section 3.2, Proposition "complexity_einsum" and its proof in Appendix D);
   a matrix product is used as a library primitive for the sum over v of
@@ -26,7 +28,8 @@ Everything here follows the paper (arXiv 2508.12627) step by step, in float64:
   x (matrix on (v,y)).
 * Sparsified tensors T~ (Lemma "sparsification_trick") and the surviving set
   Pi_m^A (Remark after it, equation "quotient_set").
-* Algorithm 4 (Ustats): U = sum_pi mu_pi V_pi.
+* U = sum_pi mu_pi V_pi over all partitions (Section 3.3, Lemma "Decomposition of
+  U-Statistic into V-Statistics").
 
 Readings where the paper is silent (kept identical on both sides of the test):
 * the RBF kernel is exp(-||x-y||^2 / h) with h = 2d; the linear kernel x.y / h with
@@ -204,12 +207,13 @@ def survives(sig, rgs) -> bool:
 
 
 # --------------------------------------------------------------------------------------
-# Induced notation (Algorithm 3) and the Einsum by one-index-at-a-time elimination
+# The quotient signature (each index replaced by its block; Section 3.3, the induced
+# notation of Example "A_pi") and the Einsum by one-index-at-a-time elimination
 # (Section 3.2, Proposition "complexity_einsum", Appendix D)
 # --------------------------------------------------------------------------------------
 
 def induced_notation(sig, rgs):
-    """Algorithm 3: replace every index by the label of its block."""
+    """The signature with every index replaced by the label of its block."""
     return [(tuple(rgs[i] for i in tup), f) for tup, f in sig]
 
 
@@ -343,7 +347,8 @@ def _sum_out(v, group):
 
 
 # --------------------------------------------------------------------------------------
-# V_pi and U (Section 3.3, Algorithm 4)
+# V_pi and U (Section 3.3, Definition "Restricted V-Statistic" and Lemma
+# "Decomposition of U-Statistic into V-Statistics")
 # --------------------------------------------------------------------------------------
 
 def v_pi(sig, tensors, rgs) -> float:
@@ -355,7 +360,8 @@ def v_pi(sig, tensors, rgs) -> float:
 
 
 def ustat(graph, factors, X, sparse: bool = False, partitions=None, absolute: bool = False):
-    """Algorithm 4 (Ustats), returning a dict with
+    """U = sum_pi mu_pi V_pi (Lemma "Decomposition of U-Statistic into
+    V-Statistics"), returning a dict with
     ``U_sum`` (the paper's unnormalised sum over ordered distinct tuples),
     ``U_mean`` = U_sum / (n)_m, and per-partition ``rgs``, ``mu`` and ``V``.
 

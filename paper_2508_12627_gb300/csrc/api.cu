@@ -554,7 +554,7 @@ int run_op(const Ctx &C, const Op &op, const ProgState &S, const void *X, int x_
             if (mats.size() > (size_t)kMhbMats) return USTAT_ERR_UNSUPPORTED;
             g.nmat = (int)mats.size();
             for (size_t q = 0; q < mats.size(); ++q) g.M[q] = C.ptr(mats[q]);
-            e = launch_mhb(g, C.fp64, is_split_mode(P.precision), C.st);
+            e = launch_mhb(g, C.fp64, C.st);
             break;
         }
         case OP_SPLIT:
@@ -993,13 +993,101 @@ int ustat::status_of_word(int word) {
     return USTAT_OK;
 }
 
+namespace {
+
+// Modelled flops of a lowered program at sample size n.
+double plan_model_flops(const Plan &P, double n) {
+    double f = 0.0;
+    for (auto &op : P.ops) f += op.coef * std::pow(n, op.npow);
+    return f;
+}
+
+std::vector<std::vector<int>> plan_orders_of(const Plan &P) {
+    std::vector<std::vector<int>> orders(P.parts.size());
+    for (size_t pi = 0; pi < P.parts.size(); ++pi)
+        for (int i = 0; i < kMaxM; ++i)
+            if (P.parts[pi].order[i] >= 0) orders[pi].push_back(P.parts[pi].order[i]);
+    return orders;
+}
+
+// The exhaustive planner with sharing chooses each partition's order greedily, in
+// partition order, by the work it adds to the program built so far; that can
+// commit early partitions to products later ones do not share (path + chord:
+// six distinct n^3 products where two suffice).  The same search from the finest
+// partition down is the second candidate (the finest partitions need the most
+// products, and coarser ones then reuse them).  A bounded local search follows:
+// for each partition in turn, each of its distinct elimination sequences is tried
+// with every other partition's order kept, and a change is kept when the whole
+// plan's modelled flops (at n = 8192, where the n^3 and n^4 terms decide) fall;
+// two sweeps at most, and only for plans of at least two n^3 steps and at most
+// 1000 candidate sequences in all (about 2 ms per trial plan).  Float32-storage
+// modes only (see below).
+int build_plan_best(const ustat_graph *g, const ustat_options *o, Plan *out) {
+    int rc = build_plan(g, o, out);
+    if (rc != USTAT_OK || o->planner != USTAT_PLAN_EXHAUSTIVE || !o->cse) return rc;
+    // the float64-storage modes keep the greedy plan: on path + chord the cheaper
+    // plan reduces against the stored product K K where the greedy one fuses those
+    // reductions into products with K o K, and its bf16x4 result measured 6.7e-8 of
+    // V_abs against 1.8e-9 (the storage's accuracy is what those modes are for)
+    if (wide_storage(o->precision)) return rc;
+    {
+        // the same search from the finest partition down
+        PlanRequest rreq;
+        rreq.reverse = true;
+        Plan rev;
+        if (build_plan(g, o, &rev, &rreq) == USTAT_OK &&
+            plan_model_flops(rev, 8192.0) < plan_model_flops(*out, 8192.0) * (1.0 - 1e-9))
+            *out = std::move(rev);
+    }
+    int heavy = 0;
+    for (const Op &op : out->ops) heavy += op.kind == OP_GEMM || op.kind == OP_GEMM3;
+    if (heavy < 2) return rc;
+    std::vector<std::vector<Candidate>> cands;
+    PlanRequest creq;
+    creq.collect = &cands;
+    creq.n = 8192;
+    Plan tmp;
+    if (build_plan(g, o, &tmp, &creq) != USTAT_OK) return rc;
+    size_t total = 0;
+    for (auto &c : cands) total += c.size();
+    if (total > 1000 || cands.size() != out->parts.size()) return rc;
+    std::vector<std::vector<int>> orders = plan_orders_of(*out);
+    double best = plan_model_flops(*out, 8192.0);
+    for (int sweep = 0; sweep < 2; ++sweep) {
+        bool improved = false;
+        for (size_t pi = 0; pi < cands.size(); ++pi) {
+            if (cands[pi].size() < 2) continue;
+            for (const Candidate &cd : cands[pi]) {
+                if (cd.order == orders[pi]) continue;
+                std::vector<std::vector<int>> trial = orders;
+                trial[pi] = cd.order;
+                PlanRequest req;
+                req.forced = &trial;
+                Plan alt;
+                if (build_plan(g, o, &alt, &req) != USTAT_OK) continue;
+                const double f = plan_model_flops(alt, 8192.0);
+                if (f < best * (1.0 - 1e-9)) {
+                    best = f;
+                    orders = std::move(trial);
+                    *out = std::move(alt);
+                    improved = true;
+                }
+            }
+        }
+        if (!improved) break;
+    }
+    return USTAT_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int ustat_plan(const ustat_graph *graph, const ustat_options *opts, ustat_plan_t **out) {
     if (!graph || !opts || !out) return USTAT_ERR_INVALID_ARG;
     ustat_plan_t *p = new (std::nothrow) ustat_plan_t();
     if (!p) return USTAT_ERR_INVALID_ARG;
-    int rc = build_plan(graph, opts, &p->p);
+    int rc = build_plan_best(graph, opts, &p->p);
     if (rc != USTAT_OK) {
         delete p;
         return rc;
@@ -1030,7 +1118,7 @@ int ustat_plan_shard(const ustat_graph *graph, const ustat_options *opts, int sh
     if (!graph || !opts || !out || n_shards < 1 || shard < 0 || shard >= n_shards || n < 1)
         return USTAT_ERR_INVALID_ARG;
     Plan full;
-    int rc = build_plan(graph, opts, &full);
+    int rc = build_plan_best(graph, opts, &full);
     if (rc != USTAT_OK) return rc;
     const int np = (int)full.parts.size();
     if (np > kCombineMaxParts) return USTAT_ERR_UNSUPPORTED;
@@ -1064,20 +1152,19 @@ int ustat_plan_shard(const ustat_graph *graph, const ustat_options *opts, int sh
         group_of[i] = group_of[r];
         groups[group_of[i]].push_back(i);
     }
-    // Cost of a set of groups: the program that evaluates that set alone.  With
-    // many partitions (m = 7: 877) these estimates are many, and each partition
-    // is lowered along the elimination order the full plan chose for it instead
-    // of searching again; groups without an n^3 product then skip the estimate.
+    // Cost of a set of groups: the program that evaluates that set alone, each
+    // partition lowered along the elimination order the full plan chose for it
+    // (the shards compute the full plan's products); with many partitions (m = 7:
+    // 877) groups without an n^3 product skip the estimate.
     const bool many = np > 256;
     std::vector<std::vector<int>> forced(np);
-    if (many)
-        for (int i = 0; i < np; ++i)
-            if (full.parts[i].evaluated)
-                forced[i].assign(full.parts[i].order, full.parts[i].order + full.parts[i].nblocks);
+    for (int i = 0; i < np; ++i)
+        if (full.parts[i].evaluated)
+            forced[i].assign(full.parts[i].order, full.parts[i].order + full.parts[i].nblocks);
     auto cost_of = [&](const std::vector<char> &keep, double *c) {
         PlanRequest req;
         req.keep = &keep;
-        if (many) req.forced = &forced;
+        req.forced = &forced;
         Plan gp;
         int e = build_plan(graph, opts, &gp, &req);
         *c = e == USTAT_OK ? shard_cost(gp, n) : 0.0;
@@ -1151,6 +1238,7 @@ int ustat_plan_shard(const ustat_graph *graph, const ustat_options *opts, int sh
     if (!p) return USTAT_ERR_INVALID_ARG;
     PlanRequest req;
     req.keep = &keep;
+    req.forced = &forced;
     rc = build_plan(graph, opts, &p->p, &req);
     if (rc != USTAT_OK) {
         delete p;

@@ -215,171 +215,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) mhb_kernel(MhbArg
     }
 }
 
-// ---- float64 storage in float32-pair arithmetic
-// GB300's float64 pipe runs at a small fraction of its float32 rate, and the
-// multi-reduction pass of float64-storage matrices spent most of its time there.
-// This form reads the float64 entries, splits each into a float pair by integer
-// operations on its bit fields, and forms the products and sums in double-float
-// float32 arithmetic (about 2^-44 relative), with one float64 operation per row
-// of eight entries.
-
-// x = hi + lo to about 2^-48 relative: hi keeps the top 24 significant bits
-// (truncated), lo the next 29 rounded to float.  |x| below float's normal range
-// gives (0, 0); infinities, NaN and values above float's range take the
-// conversion route (hi = (float)x, lo = 0).
-__device__ __forceinline__ void d2ff(double x, float &hi, float &lo) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const int e = (int)((b >> 52) & 2047u) - 1023;
-    if (e < -126) {
-        hi = 0.f;
-        lo = 0.f;
-        return;
-    }
-    if (e > 127) {
-        hi = (float)x;
-        lo = 0.f;
-        return;
-    }
-    const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
-    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
-    hi = __uint_as_float(sgn | ((unsigned)(e + 127) << 23) | (unsigned)(m >> 29));
-    // the low 29 mantissa bits r are worth r 2^(e - 52): scaled in two exact steps
-    const float r = __uint2float_rn((unsigned)(m & 0x1FFFFFFFu)) * 2.220446049250313e-16f;   // 2^-52
-    const float l = r * __uint_as_float((unsigned)(e + 127) << 23);                            // 2^e
-    lo = sgn ? -l : l;
-}
-
-struct ff {
-    float h, l;
-};
-
-// a b, unnormalised (|l| small against |h|): TwoProd of the high parts plus the cross terms
-__device__ __forceinline__ ff ff_mul(ff a, ff b) {
-    const float p = a.h * b.h;
-    float e = fmaf(a.h, b.h, -p);
-    e = fmaf(a.h, b.l, e);
-    e = fmaf(a.l, b.h, e);
-    return ff{p, e};
-}
-
-// s + x, renormalised (TwoSum of the high parts, then Fast2Sum)
-__device__ __forceinline__ ff ff_add(ff s, ff x) {
-    const float t = __fadd_rn(s.h, x.h);
-    const float bb = __fsub_rn(t, s.h);
-    const float err = __fadd_rn(__fsub_rn(s.h, __fsub_rn(t, bb)), __fsub_rn(x.h, bb));
-    const float lo = err + s.l + x.l;
-    const float h = __fadd_rn(t, lo);
-    return ff{h, __fsub_rn(lo, __fsub_rn(h, t))};
-}
-
-__device__ __forceinline__ double ff_d(ff a) { return (double)a.h + (double)a.l; }
-
-__global__ void __launch_bounds__(256, 1) mhb_ff_kernel(MhbArgs g) {
-    constexpr int CB = 256;   // columns per block: 8 per lane, lane + 32 c
-    __shared__ ff bsm[kMhbOps][CB];
-    __shared__ double colred[8][CB];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t n = g.n;
-    const int64_t j0 = (int64_t)blockIdx.x * CB;
-    for (int o = 0; o < g.nops; ++o)
-        for (int c = threadIdx.x; c < CB; c += 256) {
-            const int64_t j = j0 + c;
-            const double *bv = g.op[o].kind == TILE_FREDUCE ? g.op[o].b : nullptr;
-            ff v{0.f, 0.f};
-            if (j < n) {
-                if (bv) d2ff(bv[j], v.h, v.l);
-                else v.h = 1.f;
-            }
-            bsm[o][c] = v;
-        }
-    __syncthreads();
-    double facc[kMhbOps];
-    ff gacc[kMhbGemv][8];
-#pragma unroll
-    for (int o = 0; o < kMhbOps; ++o) facc[o] = 0.0;
-#pragma unroll
-    for (int q = 0; q < kMhbGemv; ++q)
-#pragma unroll
-        for (int c = 0; c < 8; ++c) gacc[q][c] = ff{0.f, 0.f};
-    for (int64_t i = (int64_t)blockIdx.y * 8 + warp; i < n; i += (int64_t)gridDim.y * 8) {
-        ff vals[kMhbMats][8];
-#pragma unroll
-        for (int m = 0; m < kMhbMats; ++m) {
-            if (m >= g.nmat) break;
-            const double *row = (const double *)g.M[m] + i * n;
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const int64_t j = j0 + lane + 32 * c;
-                d2ff(j < n ? row[j] : 0.0, vals[m][c].h, vals[m][c].l);
-            }
-        }
-        int gi = 0;
-#pragma unroll
-        for (int o = 0; o < kMhbOps; ++o) {
-            if (o >= g.nops) break;
-            const double ai = g.op[o].a ? g.op[o].a[i] : 1.0;
-            ff p[8];
-            bool first = true;
-#pragma unroll
-            for (int m = 0; m < kMhbMats; ++m) {
-                const int e = g.op[o].ex[m];
-                for (int r = 0; r < e; ++r) {
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) p[c] = first ? vals[m][c] : ff_mul(p[c], vals[m][c]);
-                    first = false;
-                }
-            }
-            if (first)
-#pragma unroll
-                for (int c = 0; c < 8; ++c) p[c] = ff{1.f, 0.f};
-            if (g.op[o].kind == TILE_FREDUCE) {
-                ff srow{0.f, 0.f};
-#pragma unroll
-                for (int c = 0; c < 8; ++c) srow = ff_add(srow, ff_mul(p[c], bsm[o][lane + 32 * c]));
-                facc[o] = fma(ff_d(srow), ai, facc[o]);
-            } else {
-                ff af;
-                d2ff(ai, af.h, af.l);
-#pragma unroll
-                for (int q = 0; q < kMhbGemv; ++q)
-                    if (q == gi) {
-#pragma unroll
-                        for (int c = 0; c < 8; ++c) gacc[q][c] = ff_add(gacc[q][c], ff_mul(af, p[c]));
-                    }
-                ++gi;
-            }
-        }
-    }
-#pragma unroll
-    for (int o = 0; o < kMhbOps; ++o) {
-        if (o >= g.nops) break;
-        if (g.op[o].kind != TILE_FREDUCE) continue;
-        const double sblk = block_sum(facc[o]);
-        if (threadIdx.x == 0) atomicAdd(g.op[o].out, sblk);
-    }
-    int gi = 0;
-    for (int o = 0; o < g.nops; ++o) {
-        if (g.op[o].kind != TILE_GEMV) continue;
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < kMhbGemv; ++q)
-            if (q == gi) {
-#pragma unroll
-                for (int c = 0; c < 8; ++c) colred[warp][lane + 32 * c] = ff_d(gacc[q][c]);
-            }
-        __syncthreads();
-        for (int c = threadIdx.x; c < CB; c += 256) {
-            const int64_t j = j0 + c;
-            if (j >= n) continue;
-            double sc = 0.0;
-#pragma unroll
-            for (int w = 0; w < 8; ++w) sc += colred[w][c];
-            atomicAdd(g.op[o].out + j, sc);
-        }
-        ++gi;
-    }
-}
-
 // The terminal reduction sum_ij prod_t term_t(i, j) a(i) b(j) with transposed
 // terms, on 64 x 64 tiles: the distinct untransposed matrices are read by each
 // thread straight from global memory (16-byte loads along rows), the distinct
@@ -493,7 +328,7 @@ __global__ void __launch_bounds__(256) fred_kernel(FredArgs g) {
 
 }  // namespace
 
-cudaError_t launch_mhb(const MhbArgs &g0, bool fp64, bool pair_arith, cudaStream_t s) {
+cudaError_t launch_mhb(const MhbArgs &g0, bool fp64, cudaStream_t s) {
     MhbArgs g = g0;
     if (g.nmat < 1 || g.nmat > kMhbMats || g.nops < 1 || g.nops > kMhbOps) return cudaErrorInvalidValue;
     int ngemv = 0;
@@ -513,8 +348,7 @@ cudaError_t launch_mhb(const MhbArgs &g0, bool fp64, bool pair_arith, cudaStream
     if (gy > maxgy) gy = maxgy;
     if (gy < 1) gy = 1;
     dim3 grid((unsigned)gx, (unsigned)gy);
-    if (fp64 && pair_arith) mhb_ff_kernel<<<grid, 256, 0, s>>>(g);
-    else if (fp64) mhb_kernel<double, false><<<grid, 256, 0, s>>>(g);
+    if (fp64) mhb_kernel<double, false><<<grid, 256, 0, s>>>(g);
     else if (g.n % 4 == 0) mhb_kernel<float, true><<<grid, 256, 0, s>>>(g);
     else mhb_kernel<float, false><<<grid, 256, 0, s>>>(g);
     return cudaGetLastError();

@@ -107,10 +107,7 @@ struct MhbArgs {
     int nops;
     MhbOp op[kMhbOps];
 };
-// fp64: float64 storage; pair_arith (with fp64): the products and sums in
-// double-float float32 arithmetic (the split modes, whose target is far above
-// float64 rounding), else in float64 (the fp64 mode)
-cudaError_t launch_mhb(const MhbArgs &g, bool fp64, bool pair_arith, cudaStream_t s);
+cudaError_t launch_mhb(const MhbArgs &g, bool fp64, cudaStream_t s);
 
 // ---- SIMT GEMMs in float32 / float64 (k_gemm_simt.cu)
 // One fused reduction: *out += sum_jk C(j,k)^pow W(j,k) a(j) b(k)

@@ -511,7 +511,11 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan, const P
     if (req && req->keep && req->keep->size() != parts.size()) return USTAT_ERR_INVALID_ARG;
     if (req && req->collect) req->collect->assign(parts.size(), {});
     std::set<std::tuple<int, int, int, int, int>> products;   // n^3 products in the program
-    for (size_t pi = 0; pi < parts.size(); ++pi) {
+    // partitions are lowered in restricted-growth-string order, or (req->reverse)
+    // from the finest down; the plan keeps them in restricted-growth-string order
+    std::vector<PartRec> parts_out(parts.size());
+    for (size_t step = 0; step < parts.size(); ++step) {
+        const size_t pi = (req && req->reverse) ? parts.size() - 1 - step : step;
         const std::vector<int> &rgs = parts[pi];
         PartRec pr;
         for (int i = 0; i < m; ++i) pr.rgs[i] = rgs[i];
@@ -530,7 +534,7 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan, const P
         pr.tw = exact_treewidth(k, qadj);
         if (req && ((req->finest_only && k != m) || (req->keep && !(*req->keep)[pi]))) {
             pr.evaluated = 0;
-            P.parts.push_back(pr);
+            parts_out[pi] = pr;
             continue;
         }
         // sparsification filter: no block holds both ends of a pairwise factor
@@ -540,7 +544,7 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan, const P
                 if (rgs[g->edge_src[e]] == rgs[g->edge_dst[e]]) surv = false;
             if (!surv) {
                 pr.evaluated = 0;
-                P.parts.push_back(pr);
+                parts_out[pi] = pr;
                 continue;
             }
         }
@@ -875,8 +879,9 @@ int build_plan(const ustat_graph *g, const ustat_options *o, Plan *plan, const P
                     products.insert(std::make_tuple(op.A.mat, op.A.trans, op.B.mat, op.B.trans, op.u));
             }
         }
-        P.parts.push_back(pr);
+        parts_out[pi] = pr;
     }
+    P.parts = std::move(parts_out);
 
     // ---- share n^3 products across partitions
     if (P.cse) {

@@ -162,6 +162,9 @@ struct PlanRequest {
     // partition instead of the candidate list
     const std::vector<int> *feature_order = nullptr;
     int64_t n = 1024;
+    // lower the partitions from the finest down (the sharing-aware search then
+    // meets the partitions that need the most products first)
+    bool reverse = false;
 };
 
 // Planner entry (planner.cpp).  Returns a USTAT_* code.
