@@ -308,13 +308,14 @@ def run_capture(args):
         from paper_2508_12627_gb300 import hoif
         n = args.n or 10000
         phi, A, Y = synth.hoif_sample(n, seed=0)
-        hc = hoif.HoifChains(n, k=phi.shape[1], precision=args.precision)
+        orders = [int(v) for v in args.orders.split(",")] if args.orders else list(range(2, 8))
+        hc = hoif.HoifChains(n, k=phi.shape[1], orders=orders, precision=args.precision)
         hc.set(*hoif.factor_terms(phi, A, Y))
         for _ in range(args.capture):
             for j in hc.orders:
                 hc.launch(j)
         torch.cuda.synchronize()
-        print("capture done: U_sum(h_7) %.17g" % hc.out[7][0].item())
+        print("capture done: U_sum(h_%d) %.17g" % (orders[-1], hc.out[orders[-1]][0].item()))
         return
     if args.workload == "motifs4_er":
         from paper_2508_12627_gb300 import motifs
@@ -1212,6 +1213,7 @@ def main():
     ap.add_argument("--eager", action="store_true",
                     help="dCov workload: launch every evaluation eagerly instead of replaying one CUDA graph")
     ap.add_argument("--n", type=int, default=0, help="with --capture: the workload's sample size")
+    ap.add_argument("--orders", default="", help="with --capture and hoif_chain: the chain orders, e.g. 4 or 2,3")
     ap.add_argument("--lean", type=int, default=0,
                     help="with --capture: the memory-lean evaluation with panels of this many rows")
     ap.add_argument("--capture", type=int, default=0,

@@ -13,6 +13,7 @@
 
 #include "kcommon.cuh"
 #include "kernels.h"
+#include "kmath.cuh"
 
 namespace ustat {
 
@@ -249,7 +250,10 @@ __global__ void __launch_bounds__(256) fred_kernel(FredArgs g) {
     const int64_t NT = (n + kFT - 1) / kFT;
     double acc = 0.0;
     for (int64_t tile = blockIdx.x; tile < NT * NT; tile += gridDim.x) {
-        const int64_t i0 = (tile / NT) * kFT, j0 = (tile % NT) * kFT;
+        // grouped raster: groups of 8 tile rows, column by column inside a group
+        const int64_t grp = tile / (8 * NT), rem = tile % (8 * NT);
+        const int64_t gr = NT - 8 * grp < 8 ? NT - 8 * grp : 8;
+        const int64_t i0 = (8 * grp + rem % gr) * kFT, j0 = (rem / gr) * kFT;
         // four consecutive entries of row `row`, from column `col` on (zero outside)
         auto load4 = [&](const T *M, int64_t row, int64_t col, T (&v)[4]) {
             if (row < n && kVec && col + 3 < n) {
@@ -272,8 +276,11 @@ __global__ void __launch_bounds__(256) fred_kernel(FredArgs g) {
         for (int k = 0; k < 4; ++k)
 #pragma unroll
             for (int e = 0; e < 4; ++e) v[k][e] = T(1);
-        for (int p = 0; p < g.np; ++p) {
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {   // unrolled: the argument arrays stay in registers
+            if (p >= g.np) break;
             const T *M = (const T *)g.P[p];
+            const int ex = g.pe[p];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 T x[4];
@@ -281,14 +288,16 @@ __global__ void __launch_bounds__(256) fred_kernel(FredArgs g) {
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     T f = x[e];
-                    for (int q = 1; q < g.pe[p]; ++q) f *= x[e];
+                    for (int q = 1; q < ex; ++q) f *= x[e];
                     v[k][e] *= f;
                 }
             }
         }
         // the mirror tiles of the transposed terms into shared memory
         __syncthreads();   // the previous tile's reads are done
-        for (int q = 0; q < g.nq; ++q) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            if (q >= g.nq) break;
             const T *M = (const T *)g.Q[q];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -313,15 +322,222 @@ __global__ void __launch_bounds__(256) fred_kernel(FredArgs g) {
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 T f = v[k][e];
-                for (int q = 0; q < g.nq; ++q) {
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    if (q >= g.nq) break;
                     const T y = sq[q][cc + e][rr + 16 * k];   // M_q[j][i]
-                    for (int r = 0; r < g.qe[q]; ++r) f *= y;
+                    const int ex = g.qe[q];
+                    for (int r = 0; r < ex; ++r) f *= y;
                 }
                 row = fma(f, bj[e], row);
             }
             acc = fma((double)row, g.a ? g.a[i] : 1.0, acc);
         }
     }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) atomicAdd(g.out, s);
+}
+
+// The same reduction as a streaming pipeline, for n a multiple of the 16-byte
+// piece (4 floats or 2 doubles) and 16-byte aligned matrices: every term's tile
+// of the next kS - 1 tiles is in flight (cp.async, zero-filled beyond n) while
+// the current one is reduced, so that the kernel keeps enough bytes in flight to
+// stream at the HBM rate.  Tile: kTI rows i x 64 columns j (64 x 64 floats, 32 x
+// 64 doubles: 16 KB per term).  An untransposed term's tile is kept as read
+// (rows i); a transposed term's tile is its mirror (rows j, columns i) with the
+// 16-byte pieces of row j permuted by j mod 8, so that 8 consecutive threads
+// (consecutive j) reading the same piece index hit distinct banks.  Thread
+// (jl, ig) forms the entries (i, j0 + jl) of its kTI / 4 rows: the products of
+// one 16-byte piece of rows (4 or 2) times a(i) are summed in the storage type,
+// then added in float64 times b(j).
+__device__ __forceinline__ void cpa16(void *dst, const void *src, int bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa8(void *dst, const void *src, int bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <typename T>
+struct FredPipe {
+    static constexpr int kE = 16 / (int)sizeof(T);        // elements per 16-byte piece
+    static constexpr int kTI = sizeof(T) == 4 ? 64 : 32;   // tile rows (i)
+    static constexpr int kTJ = 64;                         // tile columns (j)
+    static constexpr int kMat = kTI * kTJ * (int)sizeof(T);
+    static constexpr int kVecBytes = 2 * 64 * 8;           // a(i), b(j) as float64
+    static int stage_bytes(int nm) { return nm * kMat + kVecBytes; }
+};
+
+// kUnit: one untransposed and one transposed term, each to the first power (the
+// common case; no exponent loops)
+template <typename T, int kS, bool kUnit>
+__global__ void __launch_bounds__(256) fredp_kernel(FredArgs g) {
+    using C = FredPipe<T>;
+    constexpr int kE = C::kE, kTI = C::kTI, kTJ = C::kTJ;
+    constexpr bool kF = sizeof(T) == 4;
+    extern __shared__ __align__(128) unsigned char fp_smem[];
+    __shared__ __align__(16) float af[64];   // a(i) of the current tile in float32
+    const int t = threadIdx.x;
+    const int np = kUnit ? 1 : g.np, nq = kUnit ? 1 : g.nq, nm = np + nq;
+    const int stage = nm * C::kMat + C::kVecBytes;
+    const int n = (int)g.n;
+    const int NTI = (n + kTI - 1) / kTI, NTJ = (n + kTJ - 1) / kTJ, tiles = NTI * NTJ;
+    const int G = gridDim.x;
+    // this thread's pieces: untransposed tiles (kTJ / kE pieces per row), mirror tiles (16 per row)
+    constexpr int kPR = kTJ / kE, kPS = 256 / kPR;   // pieces per row, row step between a thread's pieces
+    const int pr0 = t / kPR, pc = t % kPR;
+    const int qr0 = t >> 4, qc = t & 15;
+
+    auto coords = [&](int tile, int &i0, int &j0) {
+        // grouped raster: groups of 8 tile rows, column by column inside a group, so
+        // that the tiles in flight read runs of at least 8 x 256 bytes of both the
+        // untransposed rows and the transposed terms' rows (DRAM page locality)
+        const int grp = tile / (8 * NTJ), rem = tile - grp * 8 * NTJ;
+        const int gr = NTI - 8 * grp < 8 ? NTI - 8 * grp : 8;
+        const int r = gr == 8 ? (rem & 7) : rem % gr, c = gr == 8 ? (rem >> 3) : rem / gr;
+        i0 = (8 * grp + r) * kTI;
+        j0 = c * kTJ;
+    };
+    auto issue = [&](int tile, int st) {
+        unsigned char *base = fp_smem + (size_t)st * stage;
+        int i0, j0;
+        coords(tile, i0, j0);
+#pragma unroll
+        for (int p = 0; p < (kUnit ? 1 : 4); ++p) {
+            if (p >= np) break;
+            const T *M = (const T *)g.P[p];
+            const int gj = j0 + pc * kE;
+            const T *src = M + (int64_t)(i0 + pr0) * n + gj;
+            T *dst = (T *)(base + p * C::kMat) + pr0 * kTJ + pc * kE;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const bool ok = gj < n && i0 + pr0 + m * kPS < n;
+                cpa16(dst + m * kPS * kTJ, ok ? src + (int64_t)m * kPS * n : M, ok ? 16 : 0);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < (kUnit ? 1 : 2); ++q) {
+            if (q >= nq) break;
+            const T *M = (const T *)g.Q[q];
+            const int gi = i0 + qc * kE;
+            const T *src = M + (int64_t)(j0 + qr0) * n + gi;
+            T *dst = (T *)(base + (np + q) * C::kMat);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int r = qr0 + 16 * m;
+                const bool ok = gi < n && j0 + r < n;
+                cpa16(dst + r * kTI + (qc ^ (r & 7)) * kE, ok ? src + (int64_t)16 * m * n : M, ok ? 16 : 0);
+            }
+        }
+        double *av = (double *)(base + nm * C::kMat), *bv = av + 64;
+        if (t < kTI) {
+            const int gi = i0 + t;
+            if (g.a) cpa8(av + t, gi < n ? g.a + gi : g.a, gi < n ? 8 : 0);
+            else av[t] = gi < n ? 1.0 : 0.0;
+        } else if (t >= 64 && t < 64 + kTJ) {
+            const int gj = j0 + (t - 64);
+            if (g.b) cpa8(bv + (t - 64), gj < n ? g.b + gj : g.b, gj < n ? 8 : 0);
+            else bv[t - 64] = gj < n ? 1.0 : 0.0;
+        }
+    };
+
+    int tl = blockIdx.x;
+#pragma unroll
+    for (int s = 0; s < kS - 1; ++s) {
+        if (tl + s * G < tiles) issue(tl + s * G, s);
+        cpa_commit();
+    }
+    const int jl = t & 63, ig = t >> 6;
+    constexpr int kPieces = kTI / 4 / kE;   // 16-byte pieces of rows per thread: 4
+    double acc = 0.0;
+    for (int it = 0; tl < tiles; tl += G, ++it) {
+        cpa_wait<kS - 2>();
+        __syncthreads();   // this tile's stage is complete; the previous stage is free
+        {
+            const int nt = tl + (kS - 1) * G;
+            if (nt < tiles) issue(nt, (it + kS - 1) % kS);
+            cpa_commit();
+        }
+        const unsigned char *base = fp_smem + (size_t)(it % kS) * stage;
+        const T *Ps = (const T *)base;
+        const T *Qs = (const T *)(base + np * C::kMat);
+        const double *av = (const double *)(base + nm * C::kMat);
+        if constexpr (kF) {
+            // a(i) in float32 once per tile (float64 conversions are slow on this part)
+            if (t < kTI) af[t] = (float)av[t];
+            __syncthreads();
+        }
+        const double bj = av[64 + jl];
+        T sum = T(0), err = T(0);   // float32: compensated (TwoSum) sum of the pieces
+#pragma unroll
+        for (int k = 0; k < kPieces; ++k) {
+            const int c = ig * kPieces + k;   // piece index along i
+            T qv[2][kE], ai[kE];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                if (q >= nq) break;
+                const T *src = Qs + q * (kTI * kTJ) + jl * kTI + (c ^ (jl & 7)) * kE;
+                if constexpr (kF) {
+                    const float4 x = *reinterpret_cast<const float4 *>(src);
+                    qv[q][0] = x.x, qv[q][1] = x.y, qv[q][2] = x.z, qv[q][3] = x.w;
+                } else {
+                    const double2 x = *reinterpret_cast<const double2 *>(src);
+                    qv[q][0] = x.x, qv[q][1] = x.y;
+                }
+            }
+            if constexpr (kF) {
+                const float4 x = *reinterpret_cast<const float4 *>(&af[c * kE]);
+                ai[0] = x.x, ai[1] = x.y, ai[2] = x.z, ai[3] = x.w;
+            } else {
+#pragma unroll
+                for (int u = 0; u < kE; ++u) ai[u] = av[c * kE + u];
+            }
+            T grp = T(0);
+#pragma unroll
+            for (int u = 0; u < kE; ++u) {
+                const int i = c * kE + u;
+                T f;
+                if constexpr (kUnit) {
+                    f = Ps[i * kTJ + jl] * qv[0][u];
+                } else {
+                    f = T(1);
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) {
+                        if (p >= np) break;
+                        const T x = Ps[p * (kTI * kTJ) + i * kTJ + jl];
+                        const int ex = g.pe[p];
+                        for (int r = 0; r < ex; ++r) f *= x;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        if (q >= nq) break;
+                        const T y = qv[q][u];
+                        const int ex = g.qe[q];
+                        for (int r = 0; r < ex; ++r) f *= y;
+                    }
+                }
+                grp = fma(f, ai[u], grp);
+            }
+            if constexpr (kF) {
+                float s2, e2;
+                two_sum(sum, grp, s2, e2);
+                sum = s2;
+                err += e2;
+            } else {
+                sum += grp;
+            }
+        }
+        acc = fma((double)sum + (double)err, bj, acc);
+    }
+    cpa_wait<0>();
     const double s = block_sum(acc);
     if (threadIdx.x == 0) atomicAdd(g.out, s);
 }
@@ -399,6 +615,67 @@ bool launch_fred(const TileTerms &tt, bool fp64, int64_t n, const double *a, con
             if ((*err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess)
                 return true;
         attr[dev] = true;
+    }
+    // the streaming pipeline where its 16-byte copies apply
+    bool pipe = n % (fp64 ? 2 : 4) == 0 && n < (int64_t)1 << 20;   // 32-bit tile arithmetic
+    for (int p = 0; p < g.np; ++p) pipe = pipe && ((uintptr_t)g.P[p] & 15) == 0;
+    for (int q = 0; q < g.nq; ++q) pipe = pipe && ((uintptr_t)g.Q[q] & 15) == 0;
+    if (pipe) {
+        static bool pattr[64] = {false};
+        constexpr int kMaxSmem = 220 * 1024;
+        if (!pattr[dev]) {
+            const void *fns[] = {
+                (const void *)fredp_kernel<float, 2, false>,  (const void *)fredp_kernel<float, 3, false>,
+                (const void *)fredp_kernel<float, 4, false>,  (const void *)fredp_kernel<double, 2, false>,
+                (const void *)fredp_kernel<double, 3, false>, (const void *)fredp_kernel<double, 4, false>,
+                (const void *)fredp_kernel<float, 2, true>,   (const void *)fredp_kernel<float, 3, true>,
+                (const void *)fredp_kernel<float, 4, true>,   (const void *)fredp_kernel<double, 2, true>,
+                (const void *)fredp_kernel<double, 3, true>,  (const void *)fredp_kernel<double, 4, true>};
+            for (const void *f : fns)
+                if ((*err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem)) !=
+                    cudaSuccess)
+                    return true;
+            pattr[dev] = true;
+        }
+        const int nm = g.np + g.nq;
+        const int stage = fp64 ? FredPipe<double>::stage_bytes(nm) : FredPipe<float>::stage_bytes(nm);
+        // two blocks per SM with the deepest ring that fits half the shared memory,
+        // else one block with a ring of two or three stages
+        int S = 0, bps = 2;
+        for (int c = 4; c >= 2 && !S; --c)
+            if (c * stage <= kMaxSmem / 2) S = c;
+        if (!S) {
+            bps = 1;
+            S = 3 * stage <= kMaxSmem ? 3 : 2;
+        }
+        const int64_t ti = fp64 ? FredPipe<double>::kTI : FredPipe<float>::kTI;
+        const int64_t tiles = ((n + ti - 1) / ti) * ((n + 63) / 64);
+        const int grid = (int)std::min<int64_t>(tiles, 152 * bps);
+        const size_t sm = (size_t)S * stage;
+        const bool unit = g.np == 1 && g.nq == 1 && g.pe[0] == 1 && g.qe[0] == 1;
+        if (fp64) {
+            if (unit) {
+                if (S == 4) fredp_kernel<double, 4, true><<<grid, 256, sm, s>>>(g);
+                else if (S == 3) fredp_kernel<double, 3, true><<<grid, 256, sm, s>>>(g);
+                else fredp_kernel<double, 2, true><<<grid, 256, sm, s>>>(g);
+            } else {
+                if (S == 4) fredp_kernel<double, 4, false><<<grid, 256, sm, s>>>(g);
+                else if (S == 3) fredp_kernel<double, 3, false><<<grid, 256, sm, s>>>(g);
+                else fredp_kernel<double, 2, false><<<grid, 256, sm, s>>>(g);
+            }
+        } else {
+            if (unit) {
+                if (S == 4) fredp_kernel<float, 4, true><<<grid, 256, sm, s>>>(g);
+                else if (S == 3) fredp_kernel<float, 3, true><<<grid, 256, sm, s>>>(g);
+                else fredp_kernel<float, 2, true><<<grid, 256, sm, s>>>(g);
+            } else {
+                if (S == 4) fredp_kernel<float, 4, false><<<grid, 256, sm, s>>>(g);
+                else if (S == 3) fredp_kernel<float, 3, false><<<grid, 256, sm, s>>>(g);
+                else fredp_kernel<float, 2, false><<<grid, 256, sm, s>>>(g);
+            }
+        }
+        *err = cudaGetLastError();
+        return true;
     }
     const int64_t NT = (n + kFT - 1) / kFT;
     const int64_t tiles = NT * NT;

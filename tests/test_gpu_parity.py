@@ -180,9 +180,11 @@ def test_rank1_integer_factors_bit_exact(eng_mod, prec, n):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
-def test_asymmetric_matrix_factors(eng_mod, prec):
-    # caller-supplied asymmetric factors with mixed orientations (transposed reads)
-    n = 150
+@pytest.mark.parametrize("n", [150, 200, 452])
+def test_asymmetric_matrix_factors(eng_mod, prec, n):
+    # caller-supplied asymmetric factors with mixed orientations (transposed reads);
+    # n = 200 and 452 (multiples of 4, ragged 64-row tiles) take the streaming
+    # reduction in float32 and float64, n = 150 the float32 tile kernel
     rng = np.random.default_rng(21)
     facs = [synth.Factor(uo.MATRIX, data=rng.uniform(0.2, 1.0, (n, n))),
             synth.Factor(uo.VECTOR, data=rng.uniform(0.5, 1.5, n)),
