@@ -216,6 +216,137 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) mhb_kernel(MhbArg
     }
 }
 
+// The float32 form of the same pass for n a multiple of 4, the distinct matrices'
+// count kNM fixed at compile time: each warp loads kR = 4 / kNM rows (of every
+// matrix) before using them, so that every warp keeps about the same number of
+// bytes in flight whatever the matrix count, and no float64 operation remains in
+// the row loop (float64 is a small fraction of this part's float32 rate):
+//   * a(i) becomes float32 by integer operations (d2f_rn);
+//   * a reduction's row piece (eight entries times b(j), summed in float32)
+//     times a(i) is added to a compensated float32 pair (TwoSum), converted to
+//     float64 once at the end.
+template <int kNM>
+__global__ void __launch_bounds__(256, kNM <= 2 ? 2 : 3) mhbp_kernel(MhbArgs g) {
+    constexpr int CB = 256;
+    constexpr int kR = kNM == 1 ? 4 : (kNM == 2 ? 2 : 1);
+    __shared__ __align__(16) float bsm[kMhbOps][CB];
+    __shared__ float colred[8][CB];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t n = g.n;
+    const int64_t j0 = (int64_t)blockIdx.x * CB;
+    auto col = [&](int c) -> int { return 4 * lane + 128 * (c >> 2) + (c & 3); };   // c < 8
+    for (int o = 0; o < g.nops; ++o)
+        for (int c = threadIdx.x; c < CB; c += 256) {
+            const int64_t j = j0 + c;
+            const double *bv = g.op[o].kind == TILE_FREDUCE ? g.op[o].b : nullptr;
+            bsm[o][c] = j < n ? (bv ? d2f_rn(bv[j]) : 1.f) : 0.f;
+        }
+    __syncthreads();
+    float fs[kMhbOps], fe[kMhbOps];
+    float gacc[kMhbGemv][8];
+#pragma unroll
+    for (int o = 0; o < kMhbOps; ++o) fs[o] = fe[o] = 0.f;
+#pragma unroll
+    for (int q = 0; q < kMhbGemv; ++q)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) gacc[q][c] = 0.f;
+    const int64_t step = (int64_t)gridDim.y * 8;
+    for (int64_t i = (int64_t)blockIdx.y * 8 + warp; i < n; i += kR * step) {
+        float vals[kR][kNM][8];
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            const int64_t ir = i + r * step;
+#pragma unroll
+            for (int m = 0; m < kNM; ++m) {
+                const float *row = (const float *)g.M[m] + ir * n;
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int64_t j = j0 + 4 * lane + 128 * q;   // n % 4 == 0: the piece is whole or outside
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (ir < n && j < n) v = *reinterpret_cast<const float4 *>(row + j);
+                    vals[r][m][4 * q + 0] = v.x;
+                    vals[r][m][4 * q + 1] = v.y;
+                    vals[r][m][4 * q + 2] = v.z;
+                    vals[r][m][4 * q + 3] = v.w;
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            const int64_t ir = i + r * step;
+            if (ir >= n) break;
+            int gi = 0;
+#pragma unroll
+            for (int o = 0; o < kMhbOps; ++o) {
+                if (o >= g.nops) break;
+                const float ai = g.op[o].a ? d2f_rn(g.op[o].a[ir]) : 1.f;
+                float p[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) p[c] = 1.f;
+#pragma unroll
+                for (int m = 0; m < kNM; ++m) {
+                    const int e = g.op[o].ex[m];
+                    for (int rr = 0; rr < e; ++rr)
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) p[c] *= vals[r][m][c];
+                }
+                if (g.op[o].kind == TILE_FREDUCE) {
+                    const float4 b0 = *reinterpret_cast<const float4 *>(&bsm[o][4 * lane]);
+                    const float4 b1 = *reinterpret_cast<const float4 *>(&bsm[o][4 * lane + 128]);
+                    float sv = p[0] * b0.x;
+                    sv = fmaf(p[1], b0.y, sv);
+                    sv = fmaf(p[2], b0.z, sv);
+                    sv = fmaf(p[3], b0.w, sv);
+                    sv = fmaf(p[4], b1.x, sv);
+                    sv = fmaf(p[5], b1.y, sv);
+                    sv = fmaf(p[6], b1.z, sv);
+                    sv = fmaf(p[7], b1.w, sv);
+                    float t1, t2;
+                    two_sum(fs[o], sv * ai, t1, t2);
+                    fs[o] = t1;
+                    fe[o] += t2;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < kMhbGemv; ++q)
+                        if (q == gi) {
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) gacc[q][c] = fmaf(ai, p[c], gacc[q][c]);
+                        }
+                    ++gi;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < kMhbOps; ++o) {
+        if (o >= g.nops) break;
+        if (g.op[o].kind != TILE_FREDUCE) continue;
+        const double sd = block_sum((double)fs[o] + (double)fe[o]);
+        if (threadIdx.x == 0) atomicAdd(g.op[o].out, sd);
+    }
+    int gi = 0;
+    for (int o = 0; o < g.nops; ++o) {
+        if (g.op[o].kind != TILE_GEMV) continue;
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kMhbGemv; ++q)
+            if (q == gi) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) colred[warp][col(c)] = gacc[q][c];
+            }
+        __syncthreads();
+        for (int c = threadIdx.x; c < CB; c += 256) {
+            const int64_t j = j0 + c;
+            if (j >= n) continue;
+            double sd = 0.0;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) sd += (double)colred[w][c];
+            atomicAdd(g.op[o].out + j, sd);
+        }
+        ++gi;
+    }
+}
+
 // The terminal reduction sum_ij prod_t term_t(i, j) a(i) b(j) with transposed
 // terms, on 64 x 64 tiles: the distinct untransposed matrices are read by each
 // thread straight from global memory (16-byte loads along rows), the distinct
@@ -564,6 +695,21 @@ cudaError_t launch_mhb(const MhbArgs &g0, bool fp64, cudaStream_t s) {
     if (gy > maxgy) gy = maxgy;
     if (gy < 1) gy = 1;
     dim3 grid((unsigned)gx, (unsigned)gy);
+    if (!fp64 && g.n % 4 == 0) {
+        // one wave: two blocks per SM (one or two matrices, more rows in flight per
+        // warp) or three
+        int64_t gy2 = (152 * (g.nmat <= 2 ? 2 : 3)) / gx;
+        if (gy2 > maxgy) gy2 = maxgy;
+        if (gy2 < 1) gy2 = 1;
+        const dim3 grid2((unsigned)gx, (unsigned)gy2);
+        switch (g.nmat) {
+            case 1: mhbp_kernel<1><<<grid2, 256, 0, s>>>(g); break;
+            case 2: mhbp_kernel<2><<<grid2, 256, 0, s>>>(g); break;
+            case 3: mhbp_kernel<3><<<grid2, 256, 0, s>>>(g); break;
+            default: mhbp_kernel<4><<<grid2, 256, 0, s>>>(g); break;
+        }
+        return cudaGetLastError();
+    }
     if (fp64) mhb_kernel<double, false><<<grid, 256, 0, s>>>(g);
     else if (g.n % 4 == 0) mhb_kernel<float, true><<<grid, 256, 0, s>>>(g);
     else mhb_kernel<float, false><<<grid, 256, 0, s>>>(g);

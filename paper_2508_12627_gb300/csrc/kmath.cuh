@@ -99,6 +99,24 @@ __device__ __forceinline__ double f2d_scaled(float x, int e) {
     return __hiloint2double((int)hw, (int)(b << 29));
 }
 
+// The float32 nearest to x (ties to even), by integer operations on the bit
+// fields: the 52-bit significand is cut to 23 bits and rounded up when the cut
+// part is above half a unit, or exactly half with an odd kept part; a carry out
+// of the significand moves into the exponent (up to infinity above the largest
+// float).  Zeros and values outside float32's normal range (subnormal results,
+// infinities, NaN) take the float64 conversion.
+__device__ __forceinline__ float d2f_rn(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const uint32_t hi = (uint32_t)(b >> 32);
+    const int e = (int)((hi >> 20) & 0x7FFu) - 1023;
+    if (e < -126 || e > 127) return (float)x;
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    uint32_t f = ((uint32_t)(e + 127) << 23) | (uint32_t)(m >> 29);
+    const uint32_t cut = (uint32_t)(m & 0x1FFFFFFFull), half = 0x10000000u;
+    f += (cut > half || (cut == half && (f & 1u))) ? 1u : 0u;
+    return __uint_as_float(f | (hi & 0x80000000u));
+}
+
 // s + t = a + b exactly, s = fl(a + b) (Knuth's TwoSum, six float32 operations)
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &t) {
     s = __fadd_rn(a, b);
