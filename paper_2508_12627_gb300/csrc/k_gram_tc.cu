@@ -97,6 +97,9 @@ struct GramArgs {
     // (j - srow0), plane stride splane elements.  Used by the kWin form only.
     int64_t row0, rows, col0, cols;
     int64_t srow0, splane;
+    // work units (set by the launcher for its grid): units 0 .. nfull - 1 are whole
+    // tiles, units nfull .. units - 1 the column halves of the last tiles
+    int nfull, units;
 };
 
 // Row i of X: its digits (kGP planes of ldx coordinates, zero beyond d), its
@@ -231,6 +234,20 @@ __global__ void __launch_bounds__(kGThreads, 1) gram_rbf_kernel(const __grid_con
             upper_tile(t, T, tm, tn);
         }
     };
+    // Work units: whole tiles, except that the tiles of a last partial wave of at
+    // most half the grid are split into column halves (64 columns each), so that
+    // the last wave takes half a tile's time (whole-matrix form only; the counts
+    // come with the arguments).
+    const int units = win ? total : g.units;
+    auto unit_of = [&](int u, int &tm, int &tn, int &c_off) {
+        if (win || u < g.nfull) {
+            tile_of(u, tm, tn);
+            c_off = -1;   // whole tile
+        } else {
+            tile_of(g.nfull + ((u - g.nfull) >> 1), tm, tn);
+            c_off = ((u - g.nfull) & 1) * (kGT / 2);
+        }
+    };
     const long long wlim = g.wait_limit > 0 ? g.wait_limit : kGWaitLimit;
 
     if (threadIdx.x == 0) {
@@ -264,9 +281,9 @@ __global__ void __launch_bounds__(kGThreads, 1) gram_rbf_kernel(const __grid_con
         if (lane == 0) {
             // ---------------- TMA producer: the tile's row block and column block of X
             uint32_t it = 0;
-            for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
-                int tm, tn;
-                tile_of(t, tm, tn);
+            for (int u = blockIdx.x; u < units && !*abort_flag; u += gridDim.x) {
+                int tm, tn, c_off;
+                unit_of(u, tm, tn, c_off);   // a half loads the whole column block
                 for (int kb = 0; kb < g.num_k; ++kb, ++it) {
                     const int s = it % kGStages;
                     if (it >= (uint32_t)kGStages && !mbar_wait(empty_bar(s), ((it / kGStages) - 1) & 1, abort_flag, wlim))
@@ -282,14 +299,22 @@ __global__ void __launch_bounds__(kGThreads, 1) gram_rbf_kernel(const __grid_con
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer
-            constexpr uint32_t idesc = make_idesc(1u, kGT, kGT);
+            constexpr uint32_t idesc_full = make_idesc(1u, kGT, kGT);
+            constexpr uint32_t idesc_half = make_idesc(1u, kGT, kGT / 2);
             uint32_t it = 0, tcount = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+            for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+                int tm, tn, c_off;
+                unit_of(u, tm, tn, c_off);
+                const uint32_t idesc = c_off < 0 ? idesc_full : idesc_half;
+                // a half multiplies rows c_off .. c_off + 63 of the column block
+                // (whole 8-row swizzle atoms: 64 rows x 64 bytes further on)
+                const uint32_t b_row = c_off < 0 ? 0u : (uint32_t)c_off * kGRowBytes;
                 const int buf = tcount & 1;
                 if (tcount >= 2 && !mbar_wait(tempty_bar(buf), ((tcount >> 1) - 1) & 1, abort_flag, wlim)) break;
                 tc_fence_after();
-                const uint32_t d_hi = tmem + buf * kGAccCols, d_lo = d_hi + kGT;
+                // a half's accumulators sit at its own columns c_off .. c_off + 63
+                const uint32_t d_hi = tmem + buf * kGAccCols + (c_off < 0 ? 0u : (uint32_t)c_off), d_lo = d_hi + kGT;
                 for (int kb = 0; kb < g.num_k; ++kb, ++it) {
                     const int s = it % kGStages;
                     if (!mbar_wait(full_bar(s), (it / kGStages) & 1, abort_flag, wlim)) {
@@ -298,7 +323,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gram_rbf_kernel(const __grid_con
                     }
                     *consumed_cnt = it + 1;
                     tc_fence_after();
-                    const uint32_t sa = base + s * kGStageBytes, sb = sa + kGP * kGTile;
+                    const uint32_t sa = base + s * kGStageBytes, sb = sa + kGP * kGTile + b_row;
 #pragma unroll
                     for (int kk = 0; kk < kGBK / 16; ++kk) {
                         uint64_t ad[kGP], bd[kGP];
@@ -341,14 +366,18 @@ __global__ void __launch_bounds__(kGThreads, 1) gram_rbf_kernel(const __grid_con
         const float cscale = __int_as_float((127 + 1 - 2 * g.lead_x) << 23);   // 2^(1 - 2 w_x)
         double tot[kGMaxRed] = {0.0, 0.0, 0.0, 0.0};
         uint32_t tcount = 0;
-        for (int t = blockIdx.x; t < total; t += gridDim.x) {
-            int tm, tn;
-            tile_of(t, tm, tn);
+        for (int u = blockIdx.x; u < units; u += gridDim.x) {
+            int tm, tn, c_off;
+            unit_of(u, tm, tn, c_off);
+            const bool half = c_off >= 0;
+            // the warp's columns (TMEM columns = tile columns): 32 (two chunks of 16)
+            // of a whole tile, or 16 of a half
+            const int wcol = half ? c_off + 16 * cg : 32 * cg;
             const int buf = tcount & 1;
             // the warp's column data (scale and squared norm of each column's x),
             // fetched while the accumulator may still be in flight
             {
-                const int64_t k = (int64_t)tn * kGT + 32 * cg + lane;   // arrays padded to whole tiles
+                const int64_t k = (int64_t)tn * kGT + wcol + (half ? (lane & 15) : lane);   // arrays padded to whole tiles
                 const float2 nk = g.nrm[k];
                 const float4 cd = make_float4(g.sx[k] * cscale, nk.x, nk.y, 0.f);
                 __syncwarp();   // the previous tile's column data are read
@@ -371,8 +400,8 @@ __global__ void __launch_bounds__(kGThreads, 1) gram_rbf_kernel(const __grid_con
             float tsum[kGMaxRed] = {0.f, 0.f, 0.f, 0.f};
             const uint32_t taddr = tmem + buf * kGAccCols + ((uint32_t)(32 * q) << 16);
 #pragma unroll 1
-            for (int h = 0; h < 2; ++h) {
-                const int c0 = 32 * cg + 16 * h;
+            for (int h = 0; h < (half ? 1 : 2); ++h) {
+                const int c0 = wcol + 16 * h;   // tile column = TMEM column
                 uint32_t hi[16], lo[16];
                 tmem_ld16(taddr + c0, hi);
                 tmem_ld16(taddr + kGT + c0, lo);
@@ -658,6 +687,11 @@ cudaError_t gram_launch(const GramScratch &gs, int64_t n, double param, int zero
     }
     const int64_t S = sm_count();
     const int grid = (int)(tiles < S ? tiles : S);
+    // the last partial wave in column halves where they fit in one wave
+    const int last = rows > 0 ? 0 : (int)(tiles % grid);
+    const bool split = last > 0 && 2 * last <= grid;
+    g.nfull = (int)tiles - (split ? last : 0);
+    g.units = g.nfull + (split ? 2 * last : 0);
     if (rows > 0) gram_rbf_kernel<true><<<grid, kGThreads, kGSmem, s>>>(map, g);
     else gram_rbf_kernel<false><<<grid, kGThreads, kGSmem, s>>>(map, g);
     return cudaGetLastError();
