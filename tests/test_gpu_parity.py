@@ -117,8 +117,10 @@ def test_heavy_tailed_matrix_factor(eng_mod, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3", "bf16x4"])
-@pytest.mark.parametrize("n", [4, 5, 64, 127, 128, 129, 256, 385, 1100, 2049])
+@pytest.mark.parametrize("n", [4, 5, 64, 127, 128, 129, 256, 385, 1100, 2049, 2500])
 def test_c4_sizes_and_ragged_tails(eng_mod, n, prec):
+    # n = 2049 and 2500: the RBF build's last partial wave runs as column halves
+    # (2500: 58 tiles in halves, the last column block 68 columns wide)
     w = synth.workload("c4_rbf", n=n)
     ref, absref = _oracle(w)
     eng = eng_mod.Engine(w.graph, w.factors, precision=prec)
