@@ -31,6 +31,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <algorithm>
 #include <type_traits>
 #include <vector>
@@ -1133,7 +1135,7 @@ cudaError_t launch_tc(const TcGemmArgs &g0, cudaStream_t s) {
         !make_map_planes(&mb, g.opB, bf16, C::kPlanes, C::kPlanes, rb, g.ldp, C::kBN, C::kRowBytes) ||
         !make_map_planes(&mb2, g.opB, bf16, C::kPlanes, C::kPlanes, rb, g.ldp, C::kBN / 2, C::kRowBytes))
         return cudaErrorInvalidValue;
-    static bool attr[64] = {false};
+    static std::atomic<bool> attr[64];   // per device, set once; atomic: host threads may launch concurrently
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr[dev]) {
@@ -1214,7 +1216,7 @@ cudaError_t launch_split_g3(const void *Mv, bool wide, int trans, const double *
         // The split of the next batch runs beside the persistent GEMM, which holds
         // most of each SM's shared memory: these kernels ask for the same L1 /
         // shared-memory split, so that their CTAs can share an SM with the GEMM's.
-        static bool carve[64] = {false};
+        static std::atomic<bool> carve[64];   // per device, set once; atomic: host threads may launch concurrently
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
         if (!carve[dev]) {
@@ -1247,7 +1249,7 @@ cudaError_t launch_split_g3(const void *Mv, bool wide, int trans, const double *
         // A(i, j) = M[j][i]: operand rows are source rows
         const int smem = (int)(sizeof(float) * n);
         if (smem > 48 * 1024) {
-            static bool attr[64] = {false};
+            static std::atomic<bool> attr[64];   // per device, set once; atomic: host threads may launch concurrently
             int dev = 0;
             if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
             if (!attr[dev]) {
@@ -1278,7 +1280,7 @@ cudaError_t launch_split_g3_pair(const float *Mh, const float *Ml, const double 
                                  int64_t bb0, int nb, int64_t n, int64_t ldp, int lead_bits, int planes, void *slices,
                                  float *scales, cudaStream_t s) {
     if (nb < 1 || nb > 65535 || n > kPairSplitMaxN) return cudaErrorInvalidValue;
-    static bool attr[64] = {false};
+    static std::atomic<bool> attr[64];   // per device, set once; atomic: host threads may launch concurrently
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr[dev]) {
@@ -1343,7 +1345,7 @@ int group_image_t(const TcGemmArgs *items, int count, const void *dev_base, std:
 template <int kMode>
 cudaError_t launch_group_t(const void *dev_base, int count, int total_tiles, int *err, cudaStream_t s) {
     using C = Cfg<kMode, false>;
-    static bool attr[64] = {false};
+    static std::atomic<bool> attr[64];   // per device, set once; atomic: host threads may launch concurrently
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr[dev]) {

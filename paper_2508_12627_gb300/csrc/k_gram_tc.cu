@@ -29,6 +29,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "kcommon.cuh"
 #include "kernels.h"
 #include "kmath.cuh"
@@ -639,7 +641,7 @@ cudaError_t gram_launch(const GramScratch &gs, int64_t n, double param, int zero
                         int64_t col0, int64_t cols, int64_t srow0, int64_t splane, int *err, cudaStream_t s) {
     CUtensorMap map;
     if (!make_map_planes(&map, gs.dig, true, kGP, kGP, n, gs.ldx, kGT, kGRowBytes)) return cudaErrorInvalidValue;
-    static bool attr[64] = {false};
+    static std::atomic<bool> attr[64];   // per device, set once; atomic: host threads may launch concurrently
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr[dev]) {

@@ -9,6 +9,8 @@
 // shared memory so that every global read is a 128-byte row segment.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <algorithm>
 
 #include "kcommon.cuh"
@@ -746,7 +748,7 @@ bool launch_fred(const TileTerms &tt, bool fp64, int64_t n, const double *a, con
     g.b = b;
     g.out = out;
     const size_t smem = (size_t)g.nq * kFT * (kFT + 1) * (fp64 ? 8 : 4);
-    static bool attr[64] = {false};
+    static std::atomic<bool> attr[64];   // per device, set once; atomic: host threads may launch concurrently
     int dev = 0;
     if ((*err = cudaGetDevice(&dev)) != cudaSuccess) return true;
     if (dev < 0 || dev >= 64) {
@@ -767,7 +769,7 @@ bool launch_fred(const TileTerms &tt, bool fp64, int64_t n, const double *a, con
     for (int p = 0; p < g.np; ++p) pipe = pipe && ((uintptr_t)g.P[p] & 15) == 0;
     for (int q = 0; q < g.nq; ++q) pipe = pipe && ((uintptr_t)g.Q[q] & 15) == 0;
     if (pipe) {
-        static bool pattr[64] = {false};
+        static std::atomic<bool> pattr[64];   // per device, set once; atomic: host threads may launch concurrently
         constexpr int kMaxSmem = 220 * 1024;
         if (!pattr[dev]) {
             const void *fns[] = {
